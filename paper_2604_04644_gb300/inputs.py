@@ -1,0 +1,231 @@
+"""Seeded synthetic inputs: slab meshes and modal coefficients.
+
+This module holds none of the operator arithmetic. It only builds mesh
+topology and vertex coordinates (integers and grid coordinates) and draws
+counter-based random numbers, so that the CUDA library and the CPU oracle
+can be fed the same inputs.
+
+Mesh recipe (the four-slab construction): the unit cube [0,1]^3 is divided
+into nx*ny*nz cells and the cell layers along z are split into four equal
+slabs.  From the bottom: each cell of slab 0 is one hexahedron, of slab 1 two
+prisms (cut by the cell's y=z diagonal plane, prism axis along x), of slab 2
+six pyramids (one per cell face, apex at the cell centre) and of slab 3 six
+Kuhn tetrahedra around the cell's (0,0,0)-(1,1,1) diagonal.  Every element is
+an affine image of its reference element; ``curved`` marks the elements to
+which the smooth deformation x_i += 0.05 sin(pi x_j) sin(pi x_k) is applied.
+
+Reference vertex order (xi coordinates) used for ``vert``:
+
+* hex   : (-1,-1,-1) (1,-1,-1) (1,1,-1) (-1,1,-1) (-1,-1,1) (1,-1,1) (1,1,1) (-1,1,1)
+* prism : (-1,-1,-1) (1,-1,-1) (1,1,-1) (-1,1,-1) (-1,-1,1) (-1,1,1)
+* pyr   : (-1,-1,-1) (1,-1,-1) (1,1,-1) (-1,1,-1) (-1,-1,1)
+* tet   : (-1,-1,-1) (1,-1,-1) (-1,1,-1) (-1,-1,1)
+
+Shape ids: 0 hex, 1 prism, 2 pyramid, 3 tetrahedron.
+"""
+from __future__ import annotations
+
+import itertools
+
+import numpy as np
+
+HEX, PRISM, PYR, TET = 0, 1, 2, 3
+SHAPE_NAMES = ("hex", "prism", "pyr", "tet")
+N_VERTS = (8, 6, 5, 4)
+# reference vertices adjacent to vertex 0 along xi_1, xi_2, xi_3
+AXIS_VERTS = ((1, 3, 4), (1, 3, 4), (1, 3, 4), (1, 2, 3))
+
+
+def _det3(a, b, c):
+    return float(np.dot(a, np.cross(b, c)))
+
+
+def _orient(shape, X):
+    """Reorder a vertex list so the affine reference map has positive volume."""
+    v1, v2, v3 = AXIS_VERTS[shape]
+    d = _det3(X[v1] - X[0], X[v2] - X[0], X[v3] - X[0])
+    if d > 0:
+        return X, [0, 1, 2, 3, 4, 5, 6, 7][: len(X)]
+    if shape == TET:
+        perm = [0, 2, 1, 3]
+    elif shape == PYR:
+        perm = [0, 3, 2, 1, 4]
+    elif shape == PRISM:
+        # swap the roles of xi_1 and xi_3 inside the triangle
+        perm = [0, 4, 5, 3, 1, 2]
+    else:
+        perm = [0, 3, 2, 1, 4, 7, 6, 5]
+    return X[perm], perm
+
+
+def slab_mesh(nx, ny, nz, order, *, curved=True, deformation=1, slabs=(HEX, PRISM, PYR, TET),
+              order_seed=None, curved_rule=None):
+    """Four-slab mixed mesh of the unit cube.
+
+    order: int (uniform P) or a (lo, hi) tuple meaning P ~ U{lo..hi} per element,
+      drawn with ``order_seed``.
+    curved: bool applied to every element, unless ``curved_rule == 'x_half'``
+      (elements whose cell centre has x < 0.5 are affine, the others curved).
+    Returns a dict with the mesh descriptor arrays (user element order).
+    """
+    if nz % len(slabs):
+        raise ValueError("nz must be divisible by the number of slabs")
+    per = nz // len(slabs)
+    h = np.array([1.0 / nx, 1.0 / ny, 1.0 / nz])
+    gid = lambda i, j, k: (k * (ny + 1) + j) * (nx + 1) + i
+    n_grid = (nx + 1) * (ny + 1) * (nz + 1)
+    grid = np.zeros((n_grid, 3))
+    for k in range(nz + 1):
+        for j in range(ny + 1):
+            for i in range(nx + 1):
+                grid[gid(i, j, k)] = (i * h[0], j * h[1], k * h[2])
+    centres = []
+    shapes, verts, cell_centre = [], [], []
+
+    def emit(shape, ids, coords, cc):
+        coords = np.asarray(coords, dtype=np.float64)
+        _, perm = _orient(shape, coords)
+        ids = [ids[p] for p in perm]
+        row = np.full(8, -1, dtype=np.int64)
+        row[: len(ids)] = ids
+        shapes.append(shape)
+        verts.append(row)
+        cell_centre.append(cc)
+
+    for s, shape in enumerate(slabs):
+        for k in range(s * per, (s + 1) * per):
+            for j in range(ny):
+                for i in range(nx):
+                    c = {(dx, dy, dz): gid(i + dx, j + dy, k + dz)
+                         for dx in (0, 1) for dy in (0, 1) for dz in (0, 1)}
+                    cc = (np.array([i, j, k]) + 0.5) * h
+                    P = lambda key: grid[c[key]]
+                    if shape == HEX:
+                        keys = [(0, 0, 0), (1, 0, 0), (1, 1, 0), (0, 1, 0),
+                                (0, 0, 1), (1, 0, 1), (1, 1, 1), (0, 1, 1)]
+                        emit(HEX, [c[q] for q in keys], [P(q) for q in keys], cc)
+                    elif shape == PRISM:
+                        # triangles in the (y, z) square split by its y = z diagonal
+                        for tri in (((1, 0), (0, 0), (1, 1)), ((0, 1), (1, 1), (0, 0))):
+                            A, B, C = tri
+                            keys = [(0,) + A, (0,) + B, (1,) + B, (1,) + A, (0,) + C, (1,) + C]
+                            emit(PRISM, [c[q] for q in keys], [P(q) for q in keys], cc)
+                    elif shape == PYR:
+                        centres.append(cc)
+                        cid = n_grid + len(centres) - 1
+                        faces = [
+                            [(0, 0, 0), (1, 0, 0), (1, 1, 0), (0, 1, 0)],
+                            [(0, 0, 1), (0, 1, 1), (1, 1, 1), (1, 0, 1)],
+                            [(0, 0, 0), (0, 0, 1), (1, 0, 1), (1, 0, 0)],
+                            [(0, 1, 0), (1, 1, 0), (1, 1, 1), (0, 1, 1)],
+                            [(0, 0, 0), (0, 1, 0), (0, 1, 1), (0, 0, 1)],
+                            [(1, 0, 0), (1, 0, 1), (1, 1, 1), (1, 1, 0)],
+                        ]
+                        for f in faces:
+                            emit(PYR, [c[q] for q in f] + [cid], [P(q) for q in f] + [cc], cc)
+                    else:
+                        for perm in itertools.permutations(range(3)):
+                            p = [0, 0, 0]
+                            path = [tuple(p)]
+                            for ax in perm[:2]:
+                                p[ax] = 1
+                                path.append(tuple(p))
+                            path.append((1, 1, 1))
+                            emit(TET, [c[q] for q in path], [P(q) for q in path], cc)
+    xyz = np.concatenate([grid, np.array(centres).reshape(-1, 3)], axis=0)
+    n_elem = len(shapes)
+    shape_arr = np.array(shapes, dtype=np.uint8)
+    if isinstance(order, tuple):
+        rng = np.random.default_rng(order_seed)
+        P_arr = rng.integers(order[0], order[1] + 1, size=n_elem).astype(np.uint8)
+    else:
+        P_arr = np.full(n_elem, int(order), dtype=np.uint8)
+    Q_arr = (P_arr + 2).astype(np.uint8)
+    cc = np.array(cell_centre)
+    if curved_rule == "x_half":
+        curved_arr = (cc[:, 0] >= 0.5).astype(np.uint8)
+    else:
+        curved_arr = np.full(n_elem, 1 if curved else 0, dtype=np.uint8)
+    return dict(
+        n_elem=n_elem,
+        shape=shape_arr,
+        P=P_arr,
+        Q=Q_arr,
+        vert=np.array(verts, dtype=np.int64),
+        xyz=np.ascontiguousarray(xyz, dtype=np.float64),
+        n_vert=xyz.shape[0],
+        curved=curved_arr,
+        deformation=int(deformation),
+    )
+
+
+def hex_cube_mesh(n, order, *, curved=False, deformation=1):
+    """n*n*n affine hexahedra filling the unit cube (one slab of hexes)."""
+    return slab_mesh(n, n, n, order, curved=curved, deformation=deformation, slabs=(HEX,))
+
+
+def single_element_mesh(shape, order, *, curved=False, deformation=1, scale=1.0, shift=(0.0, 0.0, 0.0),
+                        cell=0):
+    """One element of the given shape taken from a one-cell slab, optionally moved."""
+    m = slab_mesh(1, 1, 1, order, curved=curved, deformation=deformation, slabs=(shape,))
+    keep = min(cell, m["n_elem"] - 1)
+    m["xyz"] = m["xyz"] * scale + np.asarray(shift)
+    for key in ("shape", "P", "Q", "curved", "vert"):
+        m[key] = m[key][keep:keep + 1].copy()
+    m["n_elem"] = 1
+    return m
+
+
+def subset_mesh(mesh, elems):
+    """Mesh made of the listed elements (vertex array shared, order kept)."""
+    elems = np.asarray(elems, dtype=np.int64)
+    out = dict(mesh)
+    for key in ("shape", "P", "Q", "curved", "vert"):
+        out[key] = mesh[key][elems].copy()
+    out["n_elem"] = int(len(elems))
+    return out
+
+
+# ---------------------------------------------------------------------------
+# counter-based random numbers (SplitMix64, Steele, Lea & Flood 2014)
+# ---------------------------------------------------------------------------
+_M64 = np.uint64(0xFFFFFFFFFFFFFFFF)
+
+
+def splitmix64(x):
+    """SplitMix64 output function applied to a uint64 array of counters."""
+    x = np.asarray(x, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = x + np.uint64(0x9E3779B97F4A7C15)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def uniform_pm1(seed, elem, mode):
+    """U[-1,1) value for (seed, element id, mode index); layout independent."""
+    elem = np.asarray(elem, dtype=np.uint64)
+    mode = np.asarray(mode, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        key = (np.uint64(seed) << np.uint64(44)) ^ (elem << np.uint64(12)) ^ mode
+    z = splitmix64(key)
+    u = (z >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+    return 2.0 * u - 1.0
+
+
+def random_coefficients(seed, offsets):
+    """Ragged modal coefficient vector: element e owns [offsets[e], offsets[e+1])."""
+    offsets = np.asarray(offsets, dtype=np.int64)
+    n_elem = len(offsets) - 1
+    counts = np.diff(offsets)
+    elem = np.repeat(np.arange(n_elem, dtype=np.int64), counts)
+    mode = np.arange(offsets[-1], dtype=np.int64) - np.repeat(offsets[:-1], counts)
+    return uniform_pm1(seed, elem, mode)
+
+
+def random_phys(seed, offsets, ncomp=1):
+    """Values at quadrature points, ncomp component vectors stacked (component-major)."""
+    offsets = np.asarray(offsets, dtype=np.int64)
+    out = [random_coefficients(seed * 7 + 3 + c, offsets) for c in range(ncomp)]
+    return np.concatenate(out) if ncomp > 1 else out[0]
