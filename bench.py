@@ -1,0 +1,377 @@
+"""Benchmark: Helmholtz apply throughput (GDOF/s) on the mixed curved mesh.
+
+Workload: the unit cube in 16^3 cells, four slabs (hexes, prisms, pyramids,
+tetrahedra; 15 360 elements), all curved by x_i += 0.05 sin(pi x_j) sin(pi x_k),
+orders P = 1..8 with Q = P + 2, lambda = 1, coefficients U[-1,1) (seed 1002).
+One step = one Helmholtz apply of the whole mesh at each order (8 applies).
+GDOF/s = output elemental DOFs / seconds / 1e9 (the paper's BK metric).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--dtype f64|f32]
+
+Under torchrun (N > 1) every rank runs the full workload on its own GPU (weak
+scaling, no data-path collective); time is the max over ranks.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Helmholtz apply GDOF/s per shape/order, % HBM/FP roofline, vs plain FP64 form"
+ORDERS = list(range(1, 9))
+CELLS = 16
+FP64_PEAK_TFLOPS = 1.25     # GB300 FP64 (vector and tensor) nominal rate, profiling recipe table
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--dtype", default="f64", choices=["f64", "f32"])
+    p.add_argument("--no-table", action="store_true", help="skip the per-shape/order table")
+    p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    return p.parse_args()
+
+
+def dist_init(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "gb300" else "gloo"
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, x, device=None):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            p = [x.strip() for x in l.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = float(p[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def build_workloads(dtype_name, device):
+    import torch
+    from paper_2604_04644_gb300 import hp, inputs
+    dt = hp.HP_FP64 if dtype_name == "f64" else hp.HP_FP32
+    tdt = torch.float64 if dtype_name == "f64" else torch.float32
+    work = []
+    for P in ORDERS:
+        mesh = inputs.slab_mesh(CELLS, CELLS, CELLS, P, curved=True)
+        h = hp.hp_mesh_create(mesh, device)
+        co, po, nc, nph = hp.hp_mesh_layout(h, mesh["n_elem"])
+        op = hp.hp_op_create(h, hp.HP_HELMHOLTZ, hp.HP_STRAT_SUMFAC, dt)
+        uh = inputs.random_coefficients(1002, co)
+        x = torch.tensor(uh, device="cuda:%d" % device, dtype=tdt)
+        y = torch.zeros(nc, device="cuda:%d" % device, dtype=tdt)
+        dofs, flops, bytes_ = hp.hp_op_work(op)
+        nblocks = len(set(zip(mesh["shape"].tolist(), mesh["curved"].tolist())))
+        work.append(dict(P=P, mesh=mesh, h=h, op=op, x=x, y=y, uh=uh, nc=nc, dofs=dofs, flops=flops,
+                         bytes=bytes_, nblocks=nblocks))
+    return work
+
+
+def time_applies(work, steps, warmup, device, world, flush):
+    """Device time of each Helmholtz apply (CUDA events on the launch stream),
+    L2 flushed before every apply (outside the events)."""
+    import torch
+    from paper_2604_04644_gb300 import hp
+    stream = torch.cuda.current_stream(device)
+    for _ in range(warmup):
+        for w in work:
+            flush.zero_()
+            hp.hp_op_apply(w["op"], 1.0, w["x"], w["y"], stream)
+    for w in work:
+        hp.hp_op_sync(w["op"], stream)
+    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in work]
+          for _ in range(steps)]
+    torch.cuda.synchronize(device)
+    barrier(world)
+    torch.cuda.synchronize(device)
+    for s in range(steps):
+        for i, w in enumerate(work):
+            flush.zero_()
+            ev[s][i][0].record(stream)
+            hp.hp_op_apply(w["op"], 1.0, w["x"], w["y"], stream)
+            ev[s][i][1].record(stream)
+    torch.cuda.synchronize(device)
+    barrier(world)
+    torch.cuda.synchronize(device)
+    for w in work:
+        hp.hp_op_sync(w["op"], stream)
+    per = np.array([[ev[s][i][0].elapsed_time(ev[s][i][1]) for i in range(len(work))] for s in range(steps)])
+    return per  # ms, (steps, orders)
+
+
+def time_e2e(work, steps, device):
+    """Same workload through the public API with host buffers: pinned host ->
+    device copy of the coefficients, apply, device -> host copy of the result,
+    all inside the timed region."""
+    import torch
+    from paper_2604_04644_gb300 import hp
+    stream = torch.cuda.current_stream(device)
+    hx = [torch.tensor(w["uh"], dtype=w["x"].dtype).pin_memory() for w in work]
+    hy = [torch.empty(w["nc"], dtype=w["y"].dtype).pin_memory() for w in work]
+    h2d = sum(t.numel() * t.element_size() for t in hx)
+    d2h = sum(t.numel() * t.element_size() for t in hy)
+    torch.cuda.synchronize(device)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(steps):
+        for i, w in enumerate(work):
+            w["x"].copy_(hx[i], non_blocking=True)
+            hp.hp_op_apply(w["op"], 1.0, w["x"], w["y"], stream)
+            hy[i].copy_(w["y"], non_blocking=True)
+    t1.record(stream)
+    torch.cuda.synchronize(device)
+    ms = t0.elapsed_time(t1) / steps
+    dofs = sum(w["dofs"] for w in work)
+    return {"value": dofs / (ms * 1e-3) / 1e9, "unit": "GDOF/s", "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": ms}
+
+
+def shape_order_table(dtype_name, device, reps=5):
+    """Per shape and order GDOF/s on single-shape slabs of the same cells (outside the headline)."""
+    import torch
+    from paper_2604_04644_gb300 import hp, inputs
+    dt = hp.HP_FP64 if dtype_name == "f64" else hp.HP_FP32
+    tdt = torch.float64 if dtype_name == "f64" else torch.float32
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda:%d" % device)
+    stream = torch.cuda.current_stream(device)
+    out = {}
+    names = ("hex", "prism", "pyr", "tet")
+    for s in range(4):
+        for P in ORDERS:
+            mesh = inputs.slab_mesh(CELLS, CELLS, 4, P, curved=True, slabs=(s,) * 4)
+            h = hp.hp_mesh_create(mesh, device)
+            co, po, nc, nph = hp.hp_mesh_layout(h, mesh["n_elem"])
+            op = hp.hp_op_create(h, hp.HP_HELMHOLTZ, hp.HP_STRAT_SUMFAC, dt)
+            x = torch.tensor(inputs.random_coefficients(1002, co), device="cuda:%d" % device, dtype=tdt)
+            y = torch.zeros(nc, device="cuda:%d" % device, dtype=tdt)
+            dofs, flops, bytes_ = hp.hp_op_work(op)
+            ts = []
+            for r in range(reps + 2):
+                flush.zero_()
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                hp.hp_op_apply(op, 1.0, x, y, stream)
+                b.record(stream)
+                b.synchronize()
+                if r >= 2:
+                    ts.append(a.elapsed_time(b))
+            hp.hp_op_sync(op, stream)
+            t = statistics.median(ts) * 1e-3
+            out["%s_P%d" % (names[s], P)] = {"gdofs": round(dofs / t / 1e9, 3), "elements": int(mesh["n_elem"]),
+                                              "tflops": round(flops / t / 1e12, 4), "gbs": round(bytes_ / t / 1e9, 1)}
+            hp.hp_op_destroy(op)
+            hp.hp_mesh_destroy(h)
+    return out
+
+
+def cpu_baseline(target_s=12.0):
+    """The oracle (plain FP64 numpy definition) on a bounded sample of the
+    workload: Helmholtz on a random subset of elements at each order."""
+    from oracle import operators as oracle_ops
+    from paper_2604_04644_gb300 import inputs
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
+    except Exception:
+        cores = os.cpu_count()
+    rng = np.random.default_rng(0)
+    dofs = 0
+    t_total = 0.0
+    per = max(1, int(target_s / len(ORDERS) * 1.0))
+    sample_desc = []
+    for P in ORDERS:
+        mesh = inputs.slab_mesh(CELLS, CELLS, CELLS, P, curved=True)
+        co, po = oracle_ops.layout(mesh)
+        uh = inputs.random_coefficients(1002, co)
+        oracle_ops.apply("helmholtz", mesh, uh, 1.0, elems=[0])     # builds the reference tables (setup)
+        n = 64
+        while True:
+            el = np.sort(rng.choice(mesh["n_elem"], min(n, mesh["n_elem"]), replace=False))
+            t0 = time.perf_counter()
+            oracle_ops.apply("helmholtz", mesh, uh, 1.0, elems=el)
+            dt = time.perf_counter() - t0
+            if dt > per / 4 or n >= mesh["n_elem"]:
+                break
+            n *= 4
+        dofs += int(sum(co[e + 1] - co[e] for e in el))
+        t_total += dt
+        sample_desc.append("P%d:%d" % (P, len(el)))
+    return {"value": dofs / t_total / 1e9, "unit": "GDOF/s", "cores": int(cores), "kind": "oracle",
+            "sample": "Helmholtz on random element subsets of the 16^3 mixed curved mesh (" +
+                      ",".join(sample_desc) + "), %.1f s of CPU work" % t_total}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        pass
+    vals = []
+    t0 = time.time()
+    cb = None
+    for _ in range(max(args.steps, 1)):
+        cb = cpu_baseline(target_s=max(4.0, 60.0 / max(args.steps, 1)))
+        vals.append(cb["value"])
+    v = statistics.median(vals)
+    line = {"metric": METRIC, "value": v, "unit": "GDOF/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": (time.time() - t0) * 1e3 / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": "helmholtz_mixed_16cube_P1-8_curved", "cells": "16x16x16",
+                       "orders": "1..8", "Q": "P+2", "lambda": 1.0, "l2": "n/a (CPU)"},
+            "cpu_baseline": dict(cb, value=v),
+            "e2e": {"value": v, "unit": "GDOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_init(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    import torch
+    torch.cuda.set_device(local)
+    work = build_workloads(args.dtype, local)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda:%d" % local)  # 256 MiB > L2
+    with ClockSampler(local) as clk:
+        per = time_applies(work, args.steps, args.warmup, local, world, flush)
+    ms_step = float(per.sum(axis=1).mean())
+    ms_step = max_over_ranks(world, ms_step, device="cuda:%d" % local)
+    dofs_step = sum(w["dofs"] for w in work)
+    flops_step = sum(w["flops"] for w in work)
+    bytes_step = sum(w["bytes"] for w in work)
+    value = world * dofs_step / (ms_step * 1e-3) / 1e9
+    e2e = time_e2e(work, max(2, args.steps // 2), local)
+    launches = args.steps * sum(w["nblocks"] for w in work)
+    per_order = {}
+    for i, w in enumerate(work):
+        t = float(per[:, i].mean()) * 1e-3
+        per_order["P%d" % w["P"]] = {"gdofs": round(w["dofs"] / t / 1e9, 3),
+                                     "tflops": round(w["flops"] / t / 1e12, 4),
+                                     "gbs": round(w["bytes"] / t / 1e9, 1)}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        hbm_peak, hbm_src = peaks["hbm_gbs"], "measured"
+    except Exception:
+        hbm_peak, hbm_src = 6800.0, "fallback"
+    achieved_tf = flops_step / (ms_step * 1e-3) / 1e12
+    achieved_gbs = bytes_step / (ms_step * 1e-3) / 1e9
+    if args.dtype == "f64":
+        roof = {"bound": "alu", "achieved": round(achieved_tf, 4), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": round(achieved_tf / FP64_PEAK_TFLOPS, 4), "traffic": None,
+                "peak_source": "FP64 nominal 1.25 TFLOP/s (recipe unit table)",
+                "hbm_achieved_gbs": round(achieved_gbs, 1), "hbm_frac_of_measured": round(achieved_gbs / hbm_peak, 4)}
+    else:
+        roof = {"bound": "hbm", "achieved": round(achieved_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(achieved_gbs / hbm_peak, 4), "traffic": None, "peak_source": hbm_src}
+    table = None
+    if rank == 0 and not args.no_table:
+        table = shape_order_table(args.dtype, local)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline()
+    if rank == 0:
+        line = {"metric": METRIC, "value": round(value, 4), "unit": "GDOF/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.dtype,
+                "data": "synthetic",
+                "config": {"workload": "helmholtz_mixed_16cube_P1-8_curved", "cells": "16x16x16",
+                           "elements": int(work[0]["mesh"]["n_elem"]), "orders": "1..8", "Q": "P+2",
+                           "lambda": 1.0, "strategy": "sumfac_collocated",
+                           "l2": "flushed (256 MiB write) before every apply, outside the timed events"},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+                "clocks": clk.summary(), "per_order": per_order, "per_shape_order": table}
+        print(json.dumps(line), flush=True)
+    for w in work:
+        from paper_2604_04644_gb300 import hp
+        hp.hp_op_destroy(w["op"])
+        hp.hp_mesh_destroy(w["h"])
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

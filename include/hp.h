@@ -1,0 +1,180 @@
+/*
+ * hp.h -- C ABI of libhp: element-local spectral/hp operators on mixed
+ * hexahedral / prismatic / pyramidal / tetrahedral meshes, on one NVIDIA GPU.
+ *
+ * The operators are those of Sec. 2 of "Architecture-aware h-to-p
+ * optimisation: spectral/hp element operators for mixed-element meshes":
+ * the elemental mass matrix M = B^T W B (Eq. mass), the Laplacian L of
+ * Eq. (Lap) and the Helmholtz operator H = lambda M + L (Sec. 2.1), evaluated
+ * matrix-free in the collocated form of Eq. (helm1) (Sec. 2.2, Alg. "Helmholtz
+ * implementation by collocated approach"): BwdTrans to the quadrature
+ * points, collocated derivative, pointwise metric, transposed derivative,
+ * and one restriction B^T back to modes.  Prisms, pyramids and tetrahedra
+ * use tensorial modified-Jacobi expansions on collapsed coordinates
+ * (Sec. 2.3, Duffy transformation).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Every function returns an hp_status; nothing throws or exits.  A failed
+ *   call leaves its outputs untouched unless stated otherwise.
+ *   hp_last_error() gives a message for the last failure on this thread.
+ * - Device pointers are plain CUDA device addresses on the mesh's device;
+ *   the caller owns them (allocate them with any allocator, e.g. PyTorch).
+ *   Host pointers are read during the call only.
+ * - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *   stream).  Operator applications are asynchronous on that stream.
+ * - Element order is the caller's ("user order").  The coefficient vector is
+ *   ragged: element e owns [coeff_offset[e], coeff_offset[e+1]).  A
+ *   physical-space vector holds Q^3 values per element at
+ *   [phys_offset[e], phys_offset[e+1]), point (i,j,k) of the collapsed
+ *   coordinates (eta_1, eta_2, eta_3) at i*Q*Q + j*Q + k.  Vector fields
+ *   (three components) are three whole physical-space vectors back to back.
+ * - Mode order inside an element: each mode is a product of 1-D factors
+ *   in (eta_1, eta_2, eta_3) and has a slot key (ka, kb, kc); modes are sorted
+ *   by that key, kc fastest.  ka/kb/kc index the 1-D family of their
+ *   direction: L = (1-z)/2 -> 0, R = (1+z)/2 -> 1, bubble psi_n -> n+1; in a
+ *   warped family W_s (factors L^{s+1} and L^{s+1} R P^{(2s+1,1)}_{r-1}) the
+ *   member index r.  Modes constant in a direction (collapsed vertex, edge
+ *   and face modes) take key 0 there.  The families are those of the
+ *   modified C0 basis of Karniadakis & Sherwin, to which the paper refers
+ *   its 3-D expansions (Sec. 2.3).
+ * - Quadrature: Q = P + 2 points per direction (Sec. 2.1 asks for at least
+ *   P + 2); Gauss-Lobatto-Legendre in non-collapsed directions,
+ *   Gauss-Radau-Jacobi (node -1 included) in collapsed ones.
+ */
+#ifndef HP_H
+#define HP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hp_mesh_s* hp_mesh;
+typedef struct hp_op_s* hp_op;
+
+typedef enum {
+    HP_OK = 0,
+    HP_ERR_ARG = 1,            /* bad argument: null pointer, size or enum out of range */
+    HP_ERR_OOM = 2,            /* device or host allocation failed */
+    HP_ERR_CUDA = 3,           /* a CUDA runtime call failed */
+    HP_ERR_GEOM = 4,           /* element with |J| <= 0 or vertices that are not an affine image */
+    HP_ERR_UNSUPPORTED = 5,    /* valid request that this build does not implement */
+    HP_ERR_TIMEOUT = 6,        /* a bounded device wait gave up (error word set by a kernel) */
+    HP_ERR_DEVICE_BOUNDS = 7,  /* a kernel saw an index outside its tables */
+    HP_ERR_NOT_CONVERGED = 8   /* iterative solve stopped before its tolerance */
+} hp_status;
+
+typedef enum { HP_HEX = 0, HP_PRISM = 1, HP_PYR = 2, HP_TET = 3 } hp_shape;
+
+typedef enum {
+    HP_MASS = 0,                    /* coeff -> coeff : M uhat                                   */
+    HP_LAPLACIAN = 1,               /* coeff -> coeff : L uhat                                   */
+    HP_HELMHOLTZ = 2,               /* coeff -> coeff : (lambda M + L) uhat                      */
+    HP_BWDTRANS = 3,                /* coeff -> phys  : u = B uhat                               */
+    HP_IPRODUCT_WRT_BASE = 4,       /* phys  -> coeff : B^T W f                                  */
+    HP_PHYSDERIV = 5,               /* phys  -> 3 phys: du/dx_i of the Lagrange interpolant      */
+    HP_IPRODUCT_WRT_DERIV_BASE = 6  /* 3 phys -> coeff: sum_i (d phi/d x_i, f_i)                 */
+} hp_opkind;
+
+typedef enum {
+    HP_STRAT_SUMFAC = 0,   /* fused sum-factorised collocated kernel (Alg. collocated Helmholtz)  */
+    HP_STRAT_ELEMAT = 1,   /* reference-element dense matrices, non-collocated (StdMat, Sec. 3.3.1) */
+    HP_STRAT_HYBRID = 2,   /* dense B / B^T with collocated derivatives                           */
+    HP_STRAT_AUTO = 3      /* the library chooses per block                                       */
+} hp_strategy;
+
+typedef enum { HP_FP64 = 0, HP_FP32 = 1, HP_TF32 = 2, HP_BF16 = 3 } hp_dtype;
+
+/* Mesh description (all host arrays, copied by hp_mesh_create).
+ *   n_elem               number of elements (>= 1)
+ *   shape[n_elem]        hp_shape of each element
+ *   P[n_elem], Q[n_elem] expansion order (1..10) and points per direction (must be P + 2)
+ *   vert[n_elem*8]       global vertex ids in reference-vertex order, unused slots -1:
+ *                        hex (-1,-1,-1)(1,-1,-1)(1,1,-1)(-1,1,-1)(-1,-1,1)(1,-1,1)(1,1,1)(-1,1,1)
+ *                        prism (-1,-1,-1)(1,-1,-1)(1,1,-1)(-1,1,-1)(-1,-1,1)(-1,1,1)
+ *                        pyramid (-1,-1,-1)(1,-1,-1)(1,1,-1)(-1,1,-1)(-1,-1,1)
+ *                        tet (-1,-1,-1)(1,-1,-1)(-1,1,-1)(-1,-1,1)
+ *   xyz[3*n_vert]        vertex coordinates, x y z per vertex
+ *   curved[n_elem]       0: the element map is the affine vertex map; 1: apply `deformation`
+ *   deformation          0 none; 1: x_i += 0.05 sin(pi x_j) sin(pi x_k), (i,j,k) cyclic
+ * Every element must be an affine image of its reference element (all vertices
+ * are checked); curved elements are that affine map followed by the deformation. */
+typedef struct {
+    int64_t n_elem;
+    const uint8_t* shape;
+    const uint8_t* P;
+    const uint8_t* Q;
+    const int64_t* vert;
+    const double* xyz;
+    int64_t n_vert;
+    const uint8_t* curved;
+    int32_t deformation;
+} hp_mesh_desc;
+
+/* Create a mesh on CUDA device `device`: validates and copies the description,
+ * groups elements into blocks of equal (shape, P, Q, curved) (paper Sec. 3.3:
+ * blocks of identically structured elements with constant stride), and
+ * builds the reference tables.  Errors: HP_ERR_ARG (bad sizes or ids),
+ * HP_ERR_GEOM (non-affine vertex set or non-positive volume, message names
+ * the element), HP_ERR_UNSUPPORTED (P > 10 or Q != P + 2), HP_ERR_CUDA/OOM. */
+hp_status hp_mesh_create(const hp_mesh_desc* desc, int device, hp_mesh* out);
+
+/* Ragged layout in user order.  Any output pointer may be NULL.
+ *   coeff_offset[n_elem+1], phys_offset[n_elem+1]; n_coeff / n_phys = totals. */
+hp_status hp_mesh_layout(hp_mesh mesh, int64_t* coeff_offset, int64_t* phys_offset,
+                         int64_t* n_coeff, int64_t* n_phys);
+
+/* Geometric factors in FP64 on the device (paper Sec. 2.1 chain rule; the
+ * "six geometric factors as well as the Jacobian" of Sec. 4): for curved
+ * elements, at every quadrature point G_dd' = w|J| sum_i (d eta_d/d x_i)
+ * (d eta_d'/d x_i) (d <= d') and w|J|; for affine elements per element
+ * |J| (d xi/d x)(d xi/d x)^T, |J| and d xi/d x.  Idempotent: the first call
+ * computes, later calls return HP_OK at once.  Synchronises `stream`.
+ * Errors: HP_ERR_GEOM if some |J| <= 0 at a quadrature point (message names
+ * the first such element), HP_ERR_CUDA. */
+hp_status hp_geom_factors(hp_mesh mesh, void* stream);
+
+/* Copy the per-point factors of every element to host memory, in user order:
+ * out7[phys_offset[e]*7 + f*Q^3 + l] for f = G11,G12,G13,G22,G23,G33,w|J|,
+ * and (if out9 != NULL) out9[phys_offset[e]*9 + (3d+i)*Q^3 + l] = d eta_d/d x_i.
+ * Affine elements are expanded to points.  Computes the factors if needed.
+ * Meant for tests; synchronises the device. */
+hp_status hp_geom_copy(hp_mesh mesh, double* out7, double* out9);
+
+/* Create an operator of kind `kind` over all blocks of `mesh`, computing in
+ * `dtype` with `strategy`.  HP_FP64 and HP_FP32 apply to every kind with
+ * HP_STRAT_SUMFAC; arrays passed to hp_op_apply are double (HP_FP64) or
+ * float (HP_FP32).  Errors: HP_ERR_ARG, HP_ERR_UNSUPPORTED (combination not
+ * built), HP_ERR_GEOM / HP_ERR_CUDA from the geometric factors it needs. */
+hp_status hp_op_create(hp_mesh mesh, hp_opkind kind, hp_strategy strategy, hp_dtype dtype,
+                       hp_op* out);
+
+/* out = op(in) on `stream`, asynchronously (one kernel launch per block).
+ * `in`/`out`: device arrays sized by hp_mesh_layout for the op's spaces
+ * (see hp_opkind); they must not overlap.  lambda is used by HP_HELMHOLTZ.
+ * Errors detected before launch: HP_ERR_ARG; launch failure: HP_ERR_CUDA.
+ * Device-side errors latch in the op and are returned by hp_op_sync. */
+hp_status hp_op_apply(hp_op op, double lambda, const void* in, void* out, void* stream);
+
+/* Synchronise `stream` and report any error latched by the op's kernels
+ * (HP_ERR_TIMEOUT, HP_ERR_DEVICE_BOUNDS) or by CUDA. */
+hp_status hp_op_sync(hp_op op, void* stream);
+
+/* Algorithmic work of one hp_op_apply: output DOFs (sum of N_P, or of Q^3 for
+ * physical-space outputs), flops of the sum-factorised collocated algorithm
+ * and the minimum HBM bytes (inputs, outputs, geometric factors), for the
+ * roofline.  Any pointer may be NULL. */
+hp_status hp_op_work(hp_op op, int64_t* out_dofs, double* flops, double* bytes);
+
+void hp_op_destroy(hp_op op);
+void hp_mesh_destroy(hp_mesh mesh);
+const char* hp_status_str(hp_status s);
+const char* hp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HP_H */

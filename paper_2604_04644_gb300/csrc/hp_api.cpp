@@ -1,0 +1,596 @@
+// C ABI of libhp: mesh creation and validation, block grouping, geometric
+// factors, operator creation and application (declarations in include/hp.h).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+
+#include "hp_internal.h"
+
+namespace hp {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+hp_status cuda_fail(cudaError_t e, const char* what) {
+    set_error(std::string(what) + ": " + cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? HP_ERR_OOM : HP_ERR_CUDA;
+}
+
+int nqp(int Q) { return (Q * Q * Q + 3) & ~3; }
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+const int kNV[4] = {8, 6, 5, 4};
+const int kAxis[4][3] = {{1, 3, 4}, {1, 3, 4}, {1, 3, 4}, {1, 2, 3}};
+const double kRef[4][8][3] = {
+    {{-1, -1, -1}, {1, -1, -1}, {1, 1, -1}, {-1, 1, -1}, {-1, -1, 1}, {1, -1, 1}, {1, 1, 1}, {-1, 1, 1}},
+    {{-1, -1, -1}, {1, -1, -1}, {1, 1, -1}, {-1, 1, -1}, {-1, -1, 1}, {-1, 1, 1}},
+    {{-1, -1, -1}, {1, -1, -1}, {1, 1, -1}, {-1, 1, -1}, {-1, -1, 1}},
+    {{-1, -1, -1}, {1, -1, -1}, {-1, 1, -1}, {-1, -1, 1}}};
+
+template <typename T>
+hp_status upload(T** dst, const T* src, size_t count) {
+    *dst = nullptr;
+    if (count == 0) return HP_OK;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(dst), count * sizeof(T));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    if (src) {
+        e = cudaMemcpy(*dst, src, count * sizeof(T), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy");
+    }
+    return HP_OK;
+}
+
+void free_block(Block& b) {
+    cudaFree(b.d_coeff_off);
+    cudaFree(b.d_phys_off);
+    cudaFree(b.d_frame);
+    cudaFree(b.d_geom);
+    cudaFree(b.d_dgeom);
+    cudaFree(b.d_geom32);
+    cudaFree(b.d_dgeom32);
+    b.d_coeff_off = b.d_phys_off = nullptr;
+    b.d_frame = b.d_geom = b.d_dgeom = nullptr;
+    b.d_geom32 = b.d_dgeom32 = nullptr;
+}
+
+int64_t geom_count(const Block& b) { return b.curved ? b.n_elem * 7 * (int64_t)nqp(b.Q) : b.n_elem * 16; }
+int64_t dgeom_count(const Block& b) { return b.curved ? b.n_elem * 9 * (int64_t)nqp(b.Q) : 0; }
+
+hp_status check_device_error(hp_mesh m, unsigned int* d_err, int* d_bad, const char* what) {
+    unsigned int herr = 0;
+    cudaError_t e = cudaMemcpy(&herr, d_err, sizeof(herr), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    if (herr == 0) return HP_OK;
+    cudaMemset(d_err, 0, sizeof(unsigned int));
+    if (herr & DERR_GEOM) {
+        int bad = -1;
+        if (d_bad) cudaMemcpy(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost);
+        set_error(std::string(what) + ": non-positive Jacobian at a quadrature point (block element " +
+                  std::to_string(bad) + ")");
+        return HP_ERR_GEOM;
+    }
+    if (herr & DERR_TIMEOUT) {
+        set_error(std::string(what) + ": a bounded device wait gave up");
+        return HP_ERR_TIMEOUT;
+    }
+    set_error(std::string(what) + ": device bounds check failed");
+    return HP_ERR_DEVICE_BOUNDS;
+}
+
+hp_status compute_geom(hp_mesh m, bool want_deriv, cudaStream_t s) {
+    int* d_bad = nullptr;
+    hp_status st = upload<int>(&d_bad, nullptr, 1);
+    if (st) return st;
+    int big = 0x7fffffff;
+    cudaMemcpy(d_bad, &big, sizeof(int), cudaMemcpyHostToDevice);
+    for (Block& b : m->blocks) {
+        if (!b.d_geom) {
+            st = upload<double>(&b.d_geom, nullptr, geom_count(b));
+            if (st) { cudaFree(d_bad); return st; }
+        }
+        if (want_deriv && b.curved && !b.d_dgeom) {
+            st = upload<double>(&b.d_dgeom, nullptr, dgeom_count(b));
+            if (st) { cudaFree(d_bad); return st; }
+        }
+        const DeviceBlobs& blob = m->blobs.at(b.shape * 16 + b.P);
+        cudaError_t e = launch_geom(b, blob, m->deformation, want_deriv && b.curved, m->d_err, d_bad, s);
+        if (e != cudaSuccess) { cudaFree(d_bad); return cuda_fail(e, "geometry kernel"); }
+        cudaError_t se = cudaStreamSynchronize(s);
+        if (se != cudaSuccess) { cudaFree(d_bad); return cuda_fail(se, "geometry kernel"); }
+        st = check_device_error(m, m->d_err, d_bad, "hp_geom_factors");
+        if (st) {
+            int bad = -1;
+            cudaMemcpy(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost);
+            if (bad >= 0 && bad < b.n_elem)
+                set_error("hp_geom_factors: non-positive Jacobian in element " + std::to_string(b.elems[bad]));
+            cudaFree(d_bad);
+            return st;
+        }
+    }
+    cudaFree(d_bad);
+    m->geom_ready = true;
+    if (want_deriv) m->dgeom_ready = true;
+    m->geom32_ready = false;
+    return HP_OK;
+}
+
+hp_status ensure_geom(hp_mesh m, bool deriv, bool f32, cudaStream_t s) {
+    hp_status st = HP_OK;
+    if (!m->geom_ready || (deriv && !m->dgeom_ready)) {
+        st = compute_geom(m, deriv || m->dgeom_ready, s);
+        if (st) return st;
+    }
+    if (f32 && !m->geom32_ready) {
+        for (Block& b : m->blocks) {
+            cudaFree(b.d_geom32);
+            cudaFree(b.d_dgeom32);
+            b.d_geom32 = b.d_dgeom32 = nullptr;
+            st = upload<float>(&b.d_geom32, nullptr, geom_count(b));
+            if (st) return st;
+            cudaError_t e = launch_to_f32(b.d_geom, b.d_geom32, geom_count(b), s);
+            if (e != cudaSuccess) return cuda_fail(e, "fp32 geometry");
+            if (b.d_dgeom) {
+                st = upload<float>(&b.d_dgeom32, nullptr, dgeom_count(b));
+                if (st) return st;
+                e = launch_to_f32(b.d_dgeom, b.d_dgeom32, dgeom_count(b), s);
+                if (e != cudaSuccess) return cuda_fail(e, "fp32 geometry");
+            }
+        }
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(e, "fp32 geometry");
+        m->geom32_ready = true;
+    }
+    return HP_OK;
+}
+
+bool coeff_in(hp_opkind k) { return k == HP_MASS || k == HP_LAPLACIAN || k == HP_HELMHOLTZ || k == HP_BWDTRANS; }
+bool coeff_out(hp_opkind k) { return k != HP_BWDTRANS && k != HP_PHYSDERIV; }
+bool needs_deriv_geom(hp_opkind k) { return k == HP_PHYSDERIV || k == HP_IPRODUCT_WRT_DERIV_BASE; }
+
+// flops of the sum-factorised collocated algorithm per element (FMA = 2)
+double elem_flops(int shape, int P, hp_opkind k) {
+    const RefTables& t = ref_tables(shape, P);
+    const int n = t.n, Q = t.Q;
+    const double NQ = (double)Q * Q * Q;
+    auto fam_len = [&](int s) { return s == 0 ? n : (s >= P ? 0 : P - s); };
+    double c3 = 0, c2 = 0;
+    for (int a = 0; a < n; ++a) {
+        int blen = shape == HP_TET ? fam_len(t.famb[a]) : n;
+        c2 += blen;
+        for (int b = 0; b < blen; ++b) c3 += fam_len(t.famc[a * n + b]);
+    }
+    double bwd = 2.0 * (c3 * Q + c2 * Q * Q + n * NQ);
+    double deriv = 3.0 * 2.0 * Q * NQ;
+    switch (k) {
+        case HP_BWDTRANS: return bwd;
+        case HP_IPRODUCT_WRT_BASE: return bwd + NQ;
+        case HP_MASS: return 2 * bwd + NQ;
+        case HP_LAPLACIAN: return 2 * bwd + 2 * deriv + 15 * NQ;
+        case HP_HELMHOLTZ: return 2 * bwd + 2 * deriv + 18 * NQ;
+        case HP_PHYSDERIV: return deriv + 15 * NQ;
+        default: return bwd + deriv + 18 * NQ;
+    }
+}
+
+}  // namespace
+}  // namespace hp
+
+using namespace hp;
+
+extern "C" {
+
+const char* hp_status_str(hp_status s) {
+    switch (s) {
+        case HP_OK: return "HP_OK";
+        case HP_ERR_ARG: return "HP_ERR_ARG";
+        case HP_ERR_OOM: return "HP_ERR_OOM";
+        case HP_ERR_CUDA: return "HP_ERR_CUDA";
+        case HP_ERR_GEOM: return "HP_ERR_GEOM";
+        case HP_ERR_UNSUPPORTED: return "HP_ERR_UNSUPPORTED";
+        case HP_ERR_TIMEOUT: return "HP_ERR_TIMEOUT";
+        case HP_ERR_DEVICE_BOUNDS: return "HP_ERR_DEVICE_BOUNDS";
+        case HP_ERR_NOT_CONVERGED: return "HP_ERR_NOT_CONVERGED";
+    }
+    return "HP_ERR_UNKNOWN";
+}
+
+const char* hp_last_error(void) { return g_last_error.c_str(); }
+
+hp_status hp_mesh_create(const hp_mesh_desc* d, int device, hp_mesh* out) {
+    if (!d || !out) { set_error("hp_mesh_create: null argument"); return HP_ERR_ARG; }
+    *out = nullptr;
+    if (d->n_elem < 1 || !d->shape || !d->P || !d->Q || !d->vert || !d->xyz || d->n_vert < 1 || !d->curved) {
+        set_error("hp_mesh_create: bad descriptor (null array or empty mesh)");
+        return HP_ERR_ARG;
+    }
+    if (d->deformation < 0 || d->deformation > 1) { set_error("hp_mesh_create: unknown deformation"); return HP_ERR_ARG; }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        set_error("hp_mesh_create: no such CUDA device");
+        return HP_ERR_ARG;
+    }
+    DeviceGuard guard(device);
+    auto m = new hp_mesh_s();
+    m->device = device;
+    m->n_elem = d->n_elem;
+    m->deformation = d->deformation;
+    m->shape.assign(d->shape, d->shape + d->n_elem);
+    m->P.assign(d->P, d->P + d->n_elem);
+    m->Q.assign(d->Q, d->Q + d->n_elem);
+    m->curved.assign(d->curved, d->curved + d->n_elem);
+    m->coeff_off.assign(d->n_elem + 1, 0);
+    m->phys_off.assign(d->n_elem + 1, 0);
+    std::vector<double> frames(12 * d->n_elem);
+    for (int64_t e = 0; e < d->n_elem; ++e) {
+        int s = d->shape[e], P = d->P[e], Q = d->Q[e];
+        if (s > 3) { set_error("hp_mesh_create: bad shape in element " + std::to_string(e)); delete m; return HP_ERR_ARG; }
+        if (P < 1 || P > PMAX) {
+            set_error("hp_mesh_create: order out of range 1..10 in element " + std::to_string(e));
+            delete m;
+            return P < 1 ? HP_ERR_ARG : HP_ERR_UNSUPPORTED;
+        }
+        if (Q != P + 2) {
+            set_error("hp_mesh_create: only Q = P + 2 is built (element " + std::to_string(e) + ")");
+            delete m;
+            return HP_ERR_UNSUPPORTED;
+        }
+        double X[8][3];
+        double scale = 0.0;
+        for (int v = 0; v < kNV[s]; ++v) {
+            int64_t id = d->vert[e * 8 + v];
+            if (id < 0 || id >= d->n_vert) {
+                set_error("hp_mesh_create: vertex id out of range in element " + std::to_string(e));
+                delete m;
+                return HP_ERR_ARG;
+            }
+            for (int c = 0; c < 3; ++c) X[v][c] = d->xyz[3 * id + c];
+        }
+        double* F = &frames[12 * e];
+        for (int c = 0; c < 3; ++c) F[c] = X[0][c];
+        for (int r = 0; r < 3; ++r)
+            for (int ax = 0; ax < 3; ++ax) {
+                F[3 + r * 3 + ax] = X[kAxis[s][ax]][r] - X[0][r];
+                scale = std::max(scale, std::fabs(F[3 + r * 3 + ax]));
+            }
+        const double* E = F + 3;
+        double det = E[0] * (E[4] * E[8] - E[5] * E[7]) - E[1] * (E[3] * E[8] - E[5] * E[6]) +
+                     E[2] * (E[3] * E[7] - E[4] * E[6]);
+        if (!(det > 1e-300) || !(scale > 0)) {
+            set_error("hp_mesh_create: element " + std::to_string(e) + " has non-positive volume");
+            delete m;
+            return HP_ERR_GEOM;
+        }
+        for (int v = 0; v < kNV[s]; ++v)
+            for (int r = 0; r < 3; ++r) {
+                double y = X[0][r];
+                for (int ax = 0; ax < 3; ++ax) y += E[r * 3 + ax] * 0.5 * (kRef[s][v][ax] + 1.0);
+                if (std::fabs(y - X[v][r]) > 1e-10 * scale) {
+                    set_error("hp_mesh_create: vertices of element " + std::to_string(e) +
+                              " are not an affine image of the reference element");
+                    delete m;
+                    return HP_ERR_GEOM;
+                }
+            }
+        m->coeff_off[e + 1] = m->coeff_off[e] + n_modes(s, P);
+        m->phys_off[e + 1] = m->phys_off[e] + (int64_t)Q * Q * Q;
+    }
+    // blocks of equal (shape, P, curved), in order of first appearance
+    std::map<std::tuple<int, int, int>, int> key2blk;
+    for (int64_t e = 0; e < d->n_elem; ++e) {
+        auto key = std::make_tuple((int)d->shape[e], (int)d->P[e], d->curved[e] ? 1 : 0);
+        auto it = key2blk.find(key);
+        if (it == key2blk.end()) {
+            Block b{};
+            b.shape = d->shape[e];
+            b.P = d->P[e];
+            b.Q = d->Q[e];
+            b.curved = d->curved[e] ? 1 : 0;
+            b.n_elem = 0;
+            m->blocks.push_back(b);
+            it = key2blk.emplace(key, (int)m->blocks.size() - 1).first;
+        }
+        m->blocks[it->second].elems.push_back(e);
+    }
+    hp_status st = HP_OK;
+    for (Block& b : m->blocks) {
+        b.n_elem = (int64_t)b.elems.size();
+        std::vector<int64_t> co(b.n_elem), po(b.n_elem);
+        std::vector<double> fr(12 * b.n_elem);
+        for (int64_t i = 0; i < b.n_elem; ++i) {
+            int64_t e = b.elems[i];
+            co[i] = m->coeff_off[e];
+            po[i] = m->phys_off[e];
+            std::memcpy(&fr[12 * i], &frames[12 * e], 12 * sizeof(double));
+            b.coeff_total += m->coeff_off[e + 1] - m->coeff_off[e];
+            b.phys_total += m->phys_off[e + 1] - m->phys_off[e];
+        }
+        if ((st = upload(&b.d_coeff_off, co.data(), co.size()))) break;
+        if ((st = upload(&b.d_phys_off, po.data(), po.size()))) break;
+        if ((st = upload(&b.d_frame, fr.data(), fr.size()))) break;
+        int key = b.shape * 16 + b.P;
+        if (!m->blobs.count(key)) {
+            const RefTables& t = ref_tables(b.shape, b.P);
+            DeviceBlobs db;
+            std::vector<unsigned char> b64 = make_blob(t, 8), b32 = make_blob(t, 4);
+            unsigned char *p64 = nullptr, *p32 = nullptr;
+            if ((st = upload(&p64, b64.data(), b64.size()))) break;
+            if ((st = upload(&p32, b32.data(), b32.size()))) { cudaFree(p64); break; }
+            db.d64 = p64;
+            db.d32 = p32;
+            db.bytes64 = (int)b64.size();
+            db.bytes32 = (int)b32.size();
+            m->blobs[key] = db;
+        }
+    }
+    if (!st) st = upload<unsigned int>(&m->d_err, nullptr, 1);
+    if (!st) {
+        cudaError_t e = cudaMemset(m->d_err, 0, sizeof(unsigned int));
+        if (e != cudaSuccess) st = cuda_fail(e, "cudaMemset");
+    }
+    if (st) {
+        hp_mesh_destroy(m);
+        return st;
+    }
+    *out = m;
+    return HP_OK;
+}
+
+hp_status hp_mesh_layout(hp_mesh m, int64_t* coeff_offset, int64_t* phys_offset, int64_t* n_coeff,
+                         int64_t* n_phys) {
+    if (!m) { set_error("hp_mesh_layout: null mesh"); return HP_ERR_ARG; }
+    if (coeff_offset) std::memcpy(coeff_offset, m->coeff_off.data(), m->coeff_off.size() * sizeof(int64_t));
+    if (phys_offset) std::memcpy(phys_offset, m->phys_off.data(), m->phys_off.size() * sizeof(int64_t));
+    if (n_coeff) *n_coeff = m->coeff_off.back();
+    if (n_phys) *n_phys = m->phys_off.back();
+    return HP_OK;
+}
+
+hp_status hp_geom_factors(hp_mesh m, void* stream) {
+    if (!m) { set_error("hp_geom_factors: null mesh"); return HP_ERR_ARG; }
+    DeviceGuard guard(m->device);
+    if (m->geom_ready) return HP_OK;
+    return compute_geom(m, false, (cudaStream_t)stream);
+}
+
+hp_status hp_geom_copy(hp_mesh m, double* out7, double* out9) {
+    if (!m || !out7) { set_error("hp_geom_copy: null argument"); return HP_ERR_ARG; }
+    DeviceGuard guard(m->device);
+    hp_status st = ensure_geom(m, out9 != nullptr, false, 0);
+    if (st) return st;
+    for (const Block& b : m->blocks) {
+        const int Q = b.Q, NQ = Q * Q * Q, NQp = nqp(Q);
+        std::vector<double> g(geom_count(b)), h(dgeom_count(b));
+        cudaError_t e = cudaMemcpy(g.data(), b.d_geom, g.size() * sizeof(double), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(e, "hp_geom_copy");
+        if (out9 && b.curved) {
+            e = cudaMemcpy(h.data(), b.d_dgeom, h.size() * sizeof(double), cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) return cuda_fail(e, "hp_geom_copy");
+        }
+        const RefTables& t = ref_tables(b.shape, b.P);
+        for (int64_t i = 0; i < b.n_elem; ++i) {
+            int64_t e0 = b.elems[i];
+            double* o7 = out7 + m->phys_off[e0] * 7;
+            double* o9 = out9 ? out9 + m->phys_off[e0] * 9 : nullptr;
+            if (b.curved) {
+                for (int f = 0; f < 7; ++f)
+                    for (int l = 0; l < NQ; ++l) o7[f * NQ + l] = g[(i * 7 + f) * NQp + l];
+                if (o9)
+                    for (int f = 0; f < 9; ++f)
+                        for (int l = 0; l < NQ; ++l) o9[f * NQ + l] = h[(i * 9 + f) * NQp + l];
+                continue;
+            }
+            // affine: expand the per-element record to the points
+            const double* rec = &g[i * 16];
+            for (int l = 0; l < NQ; ++l) {
+                int ii = l / (Q * Q), jj = (l / Q) % Q, kk = l % Q;
+                double e1 = t.z[0][ii], e2 = t.z[1][jj], e3 = t.z[2][kk];
+                double T[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+                if (b.shape == HP_PRISM) { T[0][0] = 2 / (1 - e3); T[0][2] = (1 + e1) / (1 - e3); }
+                if (b.shape == HP_PYR) {
+                    T[0][0] = 2 / (1 - e3); T[0][2] = (1 + e1) / (1 - e3);
+                    T[1][1] = 2 / (1 - e3); T[1][2] = (1 + e2) / (1 - e3);
+                }
+                if (b.shape == HP_TET) {
+                    double r23 = 2 / ((1 - e2) * (1 - e3));
+                    T[0][0] = 2 * r23; T[0][1] = (1 + e1) * r23; T[0][2] = (1 + e1) * r23;
+                    T[1][1] = 2 / (1 - e3); T[1][2] = (1 + e2) / (1 - e3);
+                }
+                double Gx[3][3];
+                for (int dd = 0; dd < 3; ++dd)
+                    for (int c = 0; c < 3; ++c)
+                        Gx[dd][c] = T[dd][0] * rec[7 + c] + T[dd][1] * rec[10 + c] + T[dd][2] * rec[13 + c];
+                double wJ = t.w[0][ii] * t.w[1][jj] * t.w[2][kk] * rec[6];
+                auto G = [&](int a, int bb) { return wJ * (Gx[a][0] * Gx[bb][0] + Gx[a][1] * Gx[bb][1] + Gx[a][2] * Gx[bb][2]); };
+                o7[0 * NQ + l] = G(0, 0); o7[1 * NQ + l] = G(0, 1); o7[2 * NQ + l] = G(0, 2);
+                o7[3 * NQ + l] = G(1, 1); o7[4 * NQ + l] = G(1, 2); o7[5 * NQ + l] = G(2, 2);
+                o7[6 * NQ + l] = wJ;
+                if (o9)
+                    for (int dd = 0; dd < 3; ++dd)
+                        for (int c = 0; c < 3; ++c) o9[(3 * dd + c) * NQ + l] = Gx[dd][c];
+            }
+        }
+    }
+    return HP_OK;
+}
+
+hp_status hp_op_create(hp_mesh m, hp_opkind kind, hp_strategy strategy, hp_dtype dtype, hp_op* out) {
+    if (!m || !out) { set_error("hp_op_create: null argument"); return HP_ERR_ARG; }
+    *out = nullptr;
+    if ((int)kind < 0 || kind > HP_IPRODUCT_WRT_DERIV_BASE) { set_error("hp_op_create: bad kind"); return HP_ERR_ARG; }
+    if ((int)strategy < 0 || strategy > HP_STRAT_AUTO) { set_error("hp_op_create: bad strategy"); return HP_ERR_ARG; }
+    if ((int)dtype < 0 || dtype > HP_BF16) { set_error("hp_op_create: bad dtype"); return HP_ERR_ARG; }
+    if (strategy == HP_STRAT_AUTO) strategy = HP_STRAT_SUMFAC;
+    if (strategy != HP_STRAT_SUMFAC || (dtype != HP_FP64 && dtype != HP_FP32)) {
+        set_error("hp_op_create: this strategy/dtype combination is not built");
+        return HP_ERR_UNSUPPORTED;
+    }
+    DeviceGuard guard(m->device);
+    hp_status st = ensure_geom(m, needs_deriv_geom(kind), dtype == HP_FP32, 0);
+    if (st) return st;
+    auto op = new hp_op_s();
+    op->mesh = m;
+    op->kind = kind;
+    op->strategy = strategy;
+    op->dtype = dtype;
+    st = upload<unsigned int>(&op->d_err, nullptr, 1);
+    if (!st) cudaMemset(op->d_err, 0, sizeof(unsigned int));
+    if (st) { delete op; return st; }
+    *out = op;
+    return HP_OK;
+}
+
+hp_status hp_op_apply(hp_op op, double lambda, const void* in, void* out, void* stream) {
+    if (!op || !in || !out) { set_error("hp_op_apply: null argument"); return HP_ERR_ARG; }
+    if (in == out) { set_error("hp_op_apply: in and out must not alias"); return HP_ERR_ARG; }
+    hp_mesh m = op->mesh;
+    DeviceGuard guard(m->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t nphys = m->phys_off.back();
+    for (const Block& b : m->blocks) {
+        const DeviceBlobs& blob = m->blobs.at(b.shape * 16 + b.P);
+        cudaError_t e;
+        if (op->dtype == HP_FP64) {
+            SFArgs<double> a{};
+            a.op = op->kind;
+            a.n_elem = b.n_elem;
+            a.lambda = lambda;
+            a.coeff_off = b.d_coeff_off;
+            a.phys_off = b.d_phys_off;
+            a.in = static_cast<const double*>(in);
+            a.out = static_cast<double*>(out);
+            a.n_phys_total = nphys;
+            a.geom = b.d_geom;
+            a.dgeom = b.d_dgeom;
+            a.blob = static_cast<const unsigned char*>(blob.d64);
+            a.blob_bytes = blob.bytes64;
+            a.err = op->d_err;
+            e = sf_launch_f64(b.shape, b.P, !b.curved, a, s);
+        } else {
+            SFArgs<float> a{};
+            a.op = op->kind;
+            a.n_elem = b.n_elem;
+            a.lambda = (float)lambda;
+            a.coeff_off = b.d_coeff_off;
+            a.phys_off = b.d_phys_off;
+            a.in = static_cast<const float*>(in);
+            a.out = static_cast<float*>(out);
+            a.n_phys_total = nphys;
+            a.geom = b.d_geom32;
+            a.dgeom = b.d_dgeom32;
+            a.blob = static_cast<const unsigned char*>(blob.d32);
+            a.blob_bytes = blob.bytes32;
+            a.err = op->d_err;
+            e = sf_launch_f32(b.shape, b.P, !b.curved, a, s);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "hp_op_apply launch");
+    }
+    return HP_OK;
+}
+
+hp_status hp_op_sync(hp_op op, void* stream) {
+    if (!op) { set_error("hp_op_sync: null op"); return HP_ERR_ARG; }
+    DeviceGuard guard(op->mesh->device);
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "hp_op_sync");
+    return check_device_error(op->mesh, op->d_err, nullptr, "hp_op_sync");
+}
+
+hp_status hp_op_work(hp_op op, int64_t* out_dofs, double* flops, double* bytes) {
+    if (!op) { set_error("hp_op_work: null op"); return HP_ERR_ARG; }
+    const hp_mesh m = op->mesh;
+    const double vs = op->dtype == HP_FP64 ? 8.0 : 4.0;
+    int64_t dofs = 0;
+    double fl = 0, by = 0;
+    for (const Block& b : m->blocks) {
+        const double NQ = (double)b.Q * b.Q * b.Q;
+        const double np = (double)n_modes(b.shape, b.P);
+        const double ne = (double)b.n_elem;
+        fl += ne * elem_flops(b.shape, b.P, op->kind);
+        double in_v = coeff_in(op->kind) ? np : (op->kind == HP_IPRODUCT_WRT_DERIV_BASE ? 3 * NQ : NQ);
+        double out_v = coeff_out(op->kind) ? np : (op->kind == HP_PHYSDERIV ? 3 * NQ : NQ);
+        dofs += (int64_t)(ne * (coeff_out(op->kind) ? np : out_v));
+        double geo = 0;
+        switch (op->kind) {
+            case HP_LAPLACIAN:
+            case HP_HELMHOLTZ: geo = b.curved ? 7 * NQ : 7; break;
+            case HP_MASS:
+            case HP_IPRODUCT_WRT_BASE: geo = b.curved ? NQ : 1; break;
+            case HP_PHYSDERIV: geo = b.curved ? 9 * NQ : 9; break;
+            case HP_IPRODUCT_WRT_DERIV_BASE: geo = b.curved ? 10 * NQ : 10; break;
+            default: geo = 0;
+        }
+        by += ne * ((in_v + out_v + geo) * vs + 8.0);
+    }
+    if (out_dofs) *out_dofs = dofs;
+    if (flops) *flops = fl;
+    if (bytes) *bytes = by;
+    return HP_OK;
+}
+
+void hp_op_destroy(hp_op op) {
+    if (!op) return;
+    cudaFree(op->d_err);
+    delete op;
+}
+
+void hp_mesh_destroy(hp_mesh m) {
+    if (!m) return;
+    {
+        DeviceGuard guard(m->device);
+        for (Block& b : m->blocks) free_block(b);
+        for (auto& kv : m->blobs) {
+            cudaFree(kv.second.d64);
+            cudaFree(kv.second.d32);
+        }
+        cudaFree(m->d_err);
+    }
+    delete m;
+}
+
+}  // extern "C"
+
+namespace hp {
+cudaError_t sf_launch_hex_f64(int P, bool affine, const SFArgs<double>& a, cudaStream_t s);
+cudaError_t sf_launch_prism_f64(int P, bool affine, const SFArgs<double>& a, cudaStream_t s);
+cudaError_t sf_launch_pyr_f64(int P, bool affine, const SFArgs<double>& a, cudaStream_t s);
+cudaError_t sf_launch_tet_f64(int P, bool affine, const SFArgs<double>& a, cudaStream_t s);
+cudaError_t sf_launch_hex_f32(int P, bool affine, const SFArgs<float>& a, cudaStream_t s);
+cudaError_t sf_launch_prism_f32(int P, bool affine, const SFArgs<float>& a, cudaStream_t s);
+cudaError_t sf_launch_pyr_f32(int P, bool affine, const SFArgs<float>& a, cudaStream_t s);
+cudaError_t sf_launch_tet_f32(int P, bool affine, const SFArgs<float>& a, cudaStream_t s);
+
+cudaError_t sf_launch_f64(int shape, int P, bool affine, const SFArgs<double>& a, cudaStream_t s) {
+    switch (shape) {
+        case HP_HEX: return sf_launch_hex_f64(P, affine, a, s);
+        case HP_PRISM: return sf_launch_prism_f64(P, affine, a, s);
+        case HP_PYR: return sf_launch_pyr_f64(P, affine, a, s);
+        default: return sf_launch_tet_f64(P, affine, a, s);
+    }
+}
+cudaError_t sf_launch_f32(int shape, int P, bool affine, const SFArgs<float>& a, cudaStream_t s) {
+    switch (shape) {
+        case HP_HEX: return sf_launch_hex_f32(P, affine, a, s);
+        case HP_PRISM: return sf_launch_prism_f32(P, affine, a, s);
+        case HP_PYR: return sf_launch_pyr_f32(P, affine, a, s);
+        default: return sf_launch_tet_f32(P, affine, a, s);
+    }
+}
+}  // namespace hp

@@ -1,0 +1,181 @@
+// Geometric factors in FP64 (paper Sec. 2.1: chain rule grad_x = J^{-T}
+// grad_xi; Sec. 2.3: grad_xi = T grad_eta on collapsed coordinates; the
+// "six geometric factors as well as the Jacobian" loaded per point for
+// deformed elements, Sec. 4).
+//
+// Curved element, per quadrature point l (eta_l, xi_l = xi(eta_l)):
+//   y = X0 + E (xi + 1)/2, J = D Phi(y) E/2,  d xi / d x = J^{-1},
+//   Gx[d][i] = d eta_d / d x_i = sum_a T[d][a] (J^{-1})[a][i],
+//   w|J| = w_l det J,  G_dd' = w|J| sum_i Gx[d][i] Gx[d'][i];
+// stored as [elem][7][NQp] (G11 G12 G13 G22 G23 G33 w|J|) and, for the
+// derivative building blocks, [elem][9][NQp] (Gx row-major).
+// Affine element: per element K = |J| J^{-1} J^{-T} (6), |J| and J^{-1} (9).
+#include "hp_device.cuh"
+
+namespace hp {
+namespace {
+
+__device__ void deform_jacobian(int kind, const double y[3], double Dphi[3][3]) {
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) Dphi[i][j] = (i == j) ? 1.0 : 0.0;
+    if (kind != 1) return;
+    double s[3], c[3];
+    for (int i = 0; i < 3; ++i) sincospi(y[i], &s[i], &c[i]);
+    const double a = 0.05 * 3.14159265358979323846;
+    // Phi_1 = x1 + 0.05 s2 s3, Phi_2 = x2 + 0.05 s3 s1, Phi_3 = x3 + 0.05 s1 s2
+    Dphi[0][1] = a * c[1] * s[2];
+    Dphi[0][2] = a * s[1] * c[2];
+    Dphi[1][2] = a * c[2] * s[0];
+    Dphi[1][0] = a * s[2] * c[0];
+    Dphi[2][0] = a * c[0] * s[1];
+    Dphi[2][1] = a * s[0] * c[1];
+}
+
+__device__ double inv3(const double J[3][3], double Ji[3][3]) {
+    double c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+    double c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+    double c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+    double det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+    double r = 1.0 / det;
+    Ji[0][0] = c00 * r;
+    Ji[1][0] = c01 * r;
+    Ji[2][0] = c02 * r;
+    Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) * r;
+    Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) * r;
+    Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) * r;
+    Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) * r;
+    Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) * r;
+    Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) * r;
+    return det;
+}
+
+template <int SHAPE>
+__global__ void geom_curved_kernel(int Q, int NQp, int64_t n_elem, const double* __restrict__ frame,
+                                   const double* __restrict__ z, const double* __restrict__ w, int kind,
+                                   int want_deriv, double* __restrict__ geom, double* __restrict__ dgeom,
+                                   unsigned int* err, int* bad_elem) {
+    const int NQ = Q * Q * Q;
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= n_elem * NQ) return;
+    int64_t e = idx / NQ;
+    int l = (int)(idx % NQ);
+    int i = l / (Q * Q), j = (l / Q) % Q, k = l % Q;
+    double e1 = z[i], e2 = z[Q + j], e3 = z[2 * Q + k];
+    double xi[3];
+    xi_from_eta<SHAPE>(e1, e2, e3, xi);
+    const double* F = frame + e * 12;
+    double y[3], JA[3][3];
+    for (int r = 0; r < 3; ++r) {
+        y[r] = F[r];
+        for (int d = 0; d < 3; ++d) {
+            y[r] += F[3 + r * 3 + d] * 0.5 * (xi[d] + 1.0);
+            JA[r][d] = 0.5 * F[3 + r * 3 + d];
+        }
+    }
+    double Dp[3][3], J[3][3], Ji[3][3];
+    deform_jacobian(kind, y, Dp);
+    for (int r = 0; r < 3; ++r)
+        for (int d = 0; d < 3; ++d) J[r][d] = Dp[r][0] * JA[0][d] + Dp[r][1] * JA[1][d] + Dp[r][2] * JA[2][d];
+    double det = inv3(J, Ji);
+    if (!(det > 0.0)) {
+        atomicOr(err, DERR_GEOM);
+        atomicMin(bad_elem, (int)e);
+        return;
+    }
+    double T[3][3];
+    deta_dxi<SHAPE, double>(e1, e2, e3, T);
+    double Gx[3][3];
+    for (int d = 0; d < 3; ++d)
+        for (int c = 0; c < 3; ++c) Gx[d][c] = T[d][0] * Ji[0][c] + T[d][1] * Ji[1][c] + T[d][2] * Ji[2][c];
+    double wJ = w[i] * w[Q + j] * w[2 * Q + k] * det;
+    auto dot = [&](int a, int b) { return wJ * (Gx[a][0] * Gx[b][0] + Gx[a][1] * Gx[b][1] + Gx[a][2] * Gx[b][2]); };
+    double* g = geom + e * 7 * (int64_t)NQp + l;
+    g[0 * NQp] = dot(0, 0);
+    g[1 * NQp] = dot(0, 1);
+    g[2 * NQp] = dot(0, 2);
+    g[3 * NQp] = dot(1, 1);
+    g[4 * NQp] = dot(1, 2);
+    g[5 * NQp] = dot(2, 2);
+    g[6 * NQp] = wJ;
+    if (want_deriv) {
+        double* h = dgeom + e * 9 * (int64_t)NQp + l;
+        for (int d = 0; d < 3; ++d)
+            for (int c = 0; c < 3; ++c) h[(3 * d + c) * NQp] = Gx[d][c];
+    }
+}
+
+__global__ void geom_affine_kernel(int64_t n_elem, const double* __restrict__ frame, double* __restrict__ rec,
+                                   unsigned int* err, int* bad_elem) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n_elem) return;
+    const double* F = frame + e * 12;
+    double J[3][3], Ji[3][3];
+    for (int r = 0; r < 3; ++r)
+        for (int d = 0; d < 3; ++d) J[r][d] = 0.5 * F[3 + r * 3 + d];
+    double det = inv3(J, Ji);
+    if (!(det > 0.0)) {
+        atomicOr(err, DERR_GEOM);
+        atomicMin(bad_elem, (int)e);
+        return;
+    }
+    double* o = rec + e * 16;
+    auto K = [&](int a, int b) { return det * (Ji[a][0] * Ji[b][0] + Ji[a][1] * Ji[b][1] + Ji[a][2] * Ji[b][2]); };
+    o[0] = K(0, 0); o[1] = K(0, 1); o[2] = K(0, 2); o[3] = K(1, 1); o[4] = K(1, 2); o[5] = K(2, 2);
+    o[6] = det;
+    for (int a = 0; a < 3; ++a)
+        for (int c = 0; c < 3; ++c) o[7 + 3 * a + c] = Ji[a][c];
+}
+
+__global__ void to_f32_kernel(const double* __restrict__ src, float* __restrict__ dst, int64_t n) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (; i < n; i += stride) dst[i] = (float)src[i];
+}
+
+}  // namespace
+
+cudaError_t launch_geom(const Block& b, const DeviceBlobs& blob, int deformation, bool want_deriv,
+                        unsigned int* d_err, int* d_bad_elem, cudaStream_t s) {
+    if (b.n_elem == 0) return cudaSuccess;
+    if (!b.curved) {
+        int nt = 128;
+        int64_t nb = (b.n_elem + nt - 1) / nt;
+        geom_affine_kernel<<<(unsigned)nb, nt, 0, s>>>(b.n_elem, b.d_frame, b.d_geom, d_err, d_bad_elem);
+        return cudaGetLastError();
+    }
+    const BlobLayout L = blob_layout_c(b.shape, b.P, 8);
+    const double* vals = reinterpret_cast<const double*>(blob.d64);
+    const double* z = vals + L.z;
+    const double* w = vals + L.w;
+    int NQ = b.Q * b.Q * b.Q;
+    int nt = 128;
+    int64_t total = b.n_elem * NQ;
+    unsigned nb = (unsigned)((total + nt - 1) / nt);
+    int NQp = nqp(b.Q);
+    switch (b.shape) {
+        case HP_HEX:
+            geom_curved_kernel<HP_HEX><<<nb, nt, 0, s>>>(b.Q, NQp, b.n_elem, b.d_frame, z, w, deformation,
+                                                         want_deriv, b.d_geom, b.d_dgeom, d_err, d_bad_elem);
+            break;
+        case HP_PRISM:
+            geom_curved_kernel<HP_PRISM><<<nb, nt, 0, s>>>(b.Q, NQp, b.n_elem, b.d_frame, z, w, deformation,
+                                                           want_deriv, b.d_geom, b.d_dgeom, d_err, d_bad_elem);
+            break;
+        case HP_PYR:
+            geom_curved_kernel<HP_PYR><<<nb, nt, 0, s>>>(b.Q, NQp, b.n_elem, b.d_frame, z, w, deformation,
+                                                         want_deriv, b.d_geom, b.d_dgeom, d_err, d_bad_elem);
+            break;
+        default:
+            geom_curved_kernel<HP_TET><<<nb, nt, 0, s>>>(b.Q, NQp, b.n_elem, b.d_frame, z, w, deformation,
+                                                         want_deriv, b.d_geom, b.d_dgeom, d_err, d_bad_elem);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_to_f32(const double* src, float* dst, int64_t n, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    to_f32_kernel<<<1024, 256, 0, s>>>(src, dst, n);
+    return cudaGetLastError();
+}
+
+}  // namespace hp

@@ -1,0 +1,122 @@
+// Internal data structures of libhp (not part of the C ABI).
+#pragma once
+#include <cstdint>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/hp.h"
+#include "hp_blob.h"
+
+namespace hp {
+
+constexpr int PMAX = 10;
+
+// ---------------------------------------------------------------- tables
+// Reference data of one (shape, P) with Q = P + 2, built on the host in FP64.
+// Slot space: the padded (P+1)^3 tensor of 1-D factors (a, b, c), c fastest.
+// Family index of the eta_2 factor of slot (a, .): famb[a]; of the eta_3 factor
+// of slot (a, b, .): famc[a*n+b]; family 0 is {L, R, psi_1..psi_{P-1}}, family
+// s >= 1 the warped W_s, family P is empty (all zero).
+struct RefTables {
+    int shape = 0, P = 0, Q = 0, n = 0, NP = 0, NQ = 0;
+    std::vector<double> z[3], w[3];        // points / weights per direction (Duffy-scaled)
+    std::vector<double> Ta;                // [a][i]        n*Q
+    std::vector<double> Tb;                // [t][b][j]     (P+1)*n*Q
+    std::vector<double> Tc;                // [s][c][k]     (P+1)*n*Q
+    std::vector<double> D[3];              // [i][m]        Q*Q, d/d eta of Lagrange basis
+    std::vector<uint8_t> famb, famc;       // n, n*n
+    std::vector<int16_t> slot2mode;        // n^3, -1 = empty slot
+    std::vector<int16_t> mode_slots;       // NP*4, -1 padded
+};
+
+const RefTables& ref_tables(int shape, int P);
+int n_modes(int shape, int P);
+
+// Serialise the tables in value type T (double or float) into bytes.
+std::vector<unsigned char> make_blob(const RefTables& t, size_t value_size);
+
+// ---------------------------------------------------------------- mesh
+struct Block {
+    int shape, P, Q, curved;
+    int64_t n_elem;
+    std::vector<int64_t> elems;           // user element ids (host)
+    int64_t* d_coeff_off = nullptr;       // [n_elem] coefficient offset of each element
+    int64_t* d_phys_off = nullptr;        // [n_elem] phys offset of each element
+    double* d_frame = nullptr;            // [n_elem][12] X0 (3) + E (3x3, E[i][d])
+    double* d_geom = nullptr;             // curved: [n_elem][7][NQp]; affine: [n_elem][16]
+    double* d_dgeom = nullptr;            // curved only: [n_elem][9][NQp] d eta_d / d x_i
+    float* d_geom32 = nullptr;            // FP32 copies (created on demand)
+    float* d_dgeom32 = nullptr;
+    int64_t coeff_total = 0, phys_total = 0;   // per-block totals (work accounting)
+};
+
+struct DeviceBlobs {
+    void* d64 = nullptr;
+    void* d32 = nullptr;
+    int bytes64 = 0, bytes32 = 0;
+};
+
+}  // namespace hp
+
+struct hp_mesh_s {
+    int device = 0;
+    int64_t n_elem = 0;
+    int deformation = 0;
+    std::vector<uint8_t> shape, P, Q, curved;
+    std::vector<int64_t> coeff_off, phys_off;   // n_elem + 1
+    std::vector<hp::Block> blocks;
+    std::map<int, hp::DeviceBlobs> blobs;       // key shape*16 + P
+    bool geom_ready = false, dgeom_ready = false, geom32_ready = false;
+    unsigned int* d_err = nullptr;              // device error word
+};
+
+struct hp_op_s {
+    hp_mesh mesh = nullptr;
+    hp_opkind kind;
+    hp_strategy strategy;
+    hp_dtype dtype;
+    unsigned int* d_err = nullptr;
+};
+
+namespace hp {
+void set_error(const std::string& msg);
+hp_status cuda_fail(cudaError_t e, const char* what);
+int nqp(int Q);   // padded points per element (multiple of 4)
+
+// device-side error codes (latched in the error word)
+constexpr unsigned int DERR_TIMEOUT = 1u;
+constexpr unsigned int DERR_BOUNDS = 2u;
+constexpr unsigned int DERR_GEOM = 4u;
+
+// launch of the geometry kernel over one block (hp_geom.cu)
+cudaError_t launch_geom(const Block& b, const DeviceBlobs& blob, int deformation, bool want_deriv,
+                        unsigned int* d_err, int* d_bad_elem, cudaStream_t s);
+cudaError_t launch_to_f32(const double* src, float* dst, int64_t n, cudaStream_t s);
+
+// arguments of the sum-factorisation kernels
+template <typename T>
+struct SFArgs {
+    int op;                      // hp_opkind
+    int64_t n_elem;
+    T lambda;
+    const int64_t* coeff_off;    // per block element
+    const int64_t* phys_off;
+    const T* in;
+    T* out;
+    int64_t n_phys_total;        // stride between vector-field components
+    const T* geom;               // curved [e][7][NQp], affine [e][16]
+    const T* dgeom;              // curved [e][9][NQp] (deriv ops), affine: unused
+    const unsigned char* blob;   // table blob (16-byte aligned)
+    int blob_bytes;
+    unsigned int* err;
+};
+
+// per-shape launchers (hp_sf_<shape>.cu)
+cudaError_t sf_launch_f64(int shape, int P, bool affine, const SFArgs<double>& a, cudaStream_t s);
+cudaError_t sf_launch_f32(int shape, int P, bool affine, const SFArgs<float>& a, cudaStream_t s);
+
+}  // namespace hp

@@ -1,0 +1,359 @@
+// Fused sum-factorised element operators (one kernel per block of elements
+// of equal shape and order).
+//
+// Collocated Helmholtz (paper Sec. 2.2 Eq. (helm1); Sec. 3.3, algorithm
+// "Helmholtz implementation by collocated approach"):
+//   u = B uhat                          BwdTrans, three 1-D passes (Sec. 3.3.2)
+//   v_d = D_d u                         StdDeriv, collocation differentiation (Eq. dphitodh)
+//   w_d = sum_d' G_dd' v_d',  t = lambda w|J| u     ApplyMetric (includes W)
+//   u' = sum_d D_d^T w_d + t            SumStdDeriv
+//   out = B^T u'                        Restrict (IProductWRTBase), three 1-D passes
+// Mass skips the derivative steps; the building blocks are the pieces.
+//
+// Collapsed shapes (Sec. 2.3): the modes are generalised tensor products
+// phi = A_a(eta1) F^{t(a)}_b(eta2) F^{s(a,b)}_c(eta3), evaluated on a padded
+// (P+1)^3 slot tensor whose 1-D factor tables depend on the family indices
+// t(a), s(a,b) (zero rows pad the triangular index ranges).  Modes that are
+// constant in eta1 (or eta1 and eta2) -- the collapsed-vertex modes -- occupy
+// 2 (or 4) slots: BwdTrans copies their coefficient into each slot and the
+// restriction sums the slots.
+//
+// GPU organisation (a GB300 design, not the paper's): a persistent grid of
+// CTAs, each staging the reference tables once into shared memory with a
+// 1-D bulk copy (TMA) and then looping over groups of EPB elements; every
+// pass assigns one output entry per thread over the whole group
+// (threaded on output point across EPB elements) with intermediates in
+// shared memory; geometric factors stream from HBM in the metric pass.
+#pragma once
+#include "hp_device.cuh"
+
+namespace hp {
+
+template <int P, typename T>
+struct SFCfg {
+    static constexpr int n = P + 1, Q = P + 2, QQ = Q * Q, NQ = Q * Q * Q, N3 = n * n * n;
+    static constexpr int NT = 256;
+    static constexpr int per_elem_bytes = 5 * NQ * (int)sizeof(T);
+    static constexpr int budget = 56 * 1024;
+    static constexpr int epb0 = budget / per_elem_bytes;
+    static constexpr int EPB = epb0 < 1 ? 1 : (epb0 > 64 ? 64 : epb0);
+};
+
+template <int SHAPE, int P, typename T>
+__host__ __device__ constexpr int sf_smem_bytes() {
+    return 16 + blob_layout_c(SHAPE, P, (int)sizeof(T)).total_bytes + SFCfg<P, T>::EPB * 5 * SFCfg<P, T>::NQ * (int)sizeof(T);
+}
+
+template <int SHAPE, int P, typename T, bool AFFINE>
+__global__ void __launch_bounds__(256) sf_kernel(const SFArgs<T> args) {
+    using C = SFCfg<P, T>;
+    constexpr int n = C::n, Q = C::Q, QQ = C::QQ, NQ = C::NQ, N3 = C::N3, EPB = C::EPB, NT = C::NT;
+    constexpr BlobLayout L = blob_layout_c(SHAPE, P, (int)sizeof(T));
+    constexpr int NP = n_modes_c(SHAPE, P);
+    constexpr int NQp = (NQ + 3) & ~3;
+
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
+    unsigned char* tab = smem + 16;
+    if (!stage_tables(tab, args.blob, L.total_bytes, bar, args.err)) return;
+
+    const T* Ta = reinterpret_cast<const T*>(tab) + L.Ta;
+    const T* Tb = reinterpret_cast<const T*>(tab) + L.Tb;
+    const T* Tc = reinterpret_cast<const T*>(tab) + L.Tc;
+    const T* D0 = reinterpret_cast<const T*>(tab) + L.D;
+    const T* D1 = D0 + QQ;
+    const T* D2 = D0 + 2 * QQ;
+    const T* zt = reinterpret_cast<const T*>(tab) + L.z;
+    const T* wt = reinterpret_cast<const T*>(tab) + L.w;
+    const uint8_t* famb = tab + L.famb;
+    const uint8_t* famc = tab + L.famc;
+    const int16_t* slot2mode = reinterpret_cast<const int16_t*>(tab + L.slot2mode);
+    const int16_t* mode_slots = reinterpret_cast<const int16_t*>(tab + L.mode_slots);
+    T* S1 = reinterpret_cast<T*>(tab + L.total_bytes);   // [EPB][4*NQ]: u, v1, v2, v3
+    T* S2 = S1 + EPB * 4 * NQ;                            // [EPB][NQ]
+
+    const int tid = threadIdx.x;
+    const int op = args.op;
+    const bool coeff_in = (op == HP_MASS || op == HP_LAPLACIAN || op == HP_HELMHOLTZ || op == HP_BWDTRANS);
+    const bool deriv = (op == HP_LAPLACIAN || op == HP_HELMHOLTZ || op == HP_PHYSDERIV);
+    const bool sumderiv = (op == HP_LAPLACIAN || op == HP_HELMHOLTZ || op == HP_IPRODUCT_WRT_DERIV_BASE);
+    const int64_t ngroups = (args.n_elem + EPB - 1) / EPB;
+
+    for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x) {
+        const int64_t e0 = g * EPB;
+        const int ne = (int)min((int64_t)EPB, args.n_elem - e0);
+
+        if (coeff_in) {
+            // gather modal coefficients into the slot tensor
+            for (int idx = tid; idx < EPB * N3; idx += NT) {
+                int e = idx / N3, sl = idx - e * N3;
+                T v = T(0);
+                if (e < ne) {
+                    int m = slot2mode[sl];
+                    if (m >= 0) v = args.in[args.coeff_off[e0 + e] + m];
+                }
+                S2[e * NQ + sl] = v;
+            }
+            __syncthreads();
+            // eta3 pass: f[a][b][k] = sum_c Tc[s(a,b)][c][k] uhat[a][b][c]
+            for (int idx = tid; idx < EPB * n * n * Q; idx += NT) {
+                int e = idx / (n * n * Q), r = idx - e * (n * n * Q);
+                int ab = r / Q, k = r - ab * Q;
+                const T* tc = Tc + famc[ab] * n * Q + k;
+                const T* x = S2 + e * NQ + ab * n;
+                T acc = T(0);
+#pragma unroll
+                for (int c = 0; c < n; ++c) acc += tc[c * Q] * x[c];
+                S1[e * 4 * NQ + r] = acc;
+            }
+            __syncthreads();
+            // eta2 pass: g[a][j][k] = sum_b Tb[t(a)][b][j] f[a][b][k]
+            for (int idx = tid; idx < EPB * n * QQ; idx += NT) {
+                int e = idx / (n * QQ), r = idx - e * (n * QQ);
+                int a = r / QQ, jk = r - a * QQ, j = jk / Q, k = jk - j * Q;
+                const T* tb = Tb + famb[a] * n * Q + j;
+                const T* x = S1 + e * 4 * NQ + a * n * Q + k;
+                T acc = T(0);
+#pragma unroll
+                for (int b = 0; b < n; ++b) acc += tb[b * Q] * x[b * Q];
+                S2[e * NQ + r] = acc;
+            }
+            __syncthreads();
+            // eta1 pass: u[i][j][k] = sum_a Ta[a][i] g[a][j][k]
+            for (int idx = tid; idx < EPB * NQ; idx += NT) {
+                int e = idx / NQ, r = idx - e * NQ;
+                int i = r / QQ, jk = r - i * QQ;
+                const T* x = S2 + e * NQ + jk;
+                T acc = T(0);
+#pragma unroll
+                for (int a = 0; a < n; ++a) acc += Ta[a * Q + i] * x[a * QQ];
+                S1[e * 4 * NQ + r] = acc;
+            }
+            __syncthreads();
+            if (op == HP_BWDTRANS) {
+                for (int idx = tid; idx < EPB * NQ; idx += NT) {
+                    int e = idx / NQ, r = idx - e * NQ;
+                    if (e < ne) args.out[args.phys_off[e0 + e] + r] = S1[e * 4 * NQ + r];
+                }
+                __syncthreads();
+                continue;
+            }
+        } else {
+            const int nc = (op == HP_IPRODUCT_WRT_DERIV_BASE) ? 3 : 1;
+            const int dst = (op == HP_IPRODUCT_WRT_DERIV_BASE) ? 1 : 0;
+            for (int idx = tid; idx < EPB * NQ; idx += NT) {
+                int e = idx / NQ, r = idx - e * NQ;
+                for (int c = 0; c < nc; ++c) {
+                    T v = T(0);
+                    if (e < ne) v = args.in[c * args.n_phys_total + args.phys_off[e0 + e] + r];
+                    S1[e * 4 * NQ + (dst + c) * NQ + r] = v;
+                }
+            }
+            __syncthreads();
+        }
+
+        if (deriv) {
+            // v_d = D_d u (collocation differentiation in eta_1, eta_2, eta_3)
+            for (int idx = tid; idx < EPB * NQ; idx += NT) {
+                int e = idx / NQ, r = idx - e * NQ;
+                int i = r / QQ, jk = r - i * QQ, j = jk / Q, k = jk - j * Q;
+                const T* u = S1 + e * 4 * NQ;
+                T a1 = T(0), a2 = T(0), a3 = T(0);
+#pragma unroll
+                for (int m = 0; m < Q; ++m) {
+                    a1 += D0[i * Q + m] * u[m * QQ + jk];
+                    a2 += D1[j * Q + m] * u[i * QQ + m * Q + k];
+                    a3 += D2[k * Q + m] * u[i * QQ + j * Q + m];
+                }
+                S1[e * 4 * NQ + NQ + r] = a1;
+                S1[e * 4 * NQ + 2 * NQ + r] = a2;
+                S1[e * 4 * NQ + 3 * NQ + r] = a3;
+            }
+            __syncthreads();
+        }
+
+        // pointwise metric
+        for (int idx = tid; idx < EPB * NQ; idx += NT) {
+            int e = idx / NQ, r = idx - e * NQ;
+            if (e >= ne) {
+                S2[e * NQ + r] = T(0);
+                if (sumderiv) {
+                    S1[e * 4 * NQ + NQ + r] = T(0);
+                    S1[e * 4 * NQ + 2 * NQ + r] = T(0);
+                    S1[e * 4 * NQ + 3 * NQ + r] = T(0);
+                }
+                continue;
+            }
+            const int64_t eg = e0 + e;
+            T G[6], wJ, Gx[3][3];
+            const bool need_gx = (op == HP_PHYSDERIV || op == HP_IPRODUCT_WRT_DERIV_BASE);
+            if (AFFINE) {
+                const T* rec = args.geom + eg * 16;
+                int i = r / QQ, jk = r - i * QQ, j = jk / Q, k = jk - j * Q;
+                T Tm[3][3];
+                deta_dxi<SHAPE, T>(zt[i], zt[Q + j], zt[2 * Q + k], Tm);
+                T wl = wt[i] * wt[Q + j] * wt[2 * Q + k];
+                wJ = wl * rec[6];
+                if (op == HP_LAPLACIAN || op == HP_HELMHOLTZ) {
+                    T K[3][3] = {{rec[0], rec[1], rec[2]}, {rec[1], rec[3], rec[4]}, {rec[2], rec[4], rec[5]}};
+                    T M[3][3];
+#pragma unroll
+                    for (int d = 0; d < 3; ++d)
+#pragma unroll
+                        for (int b = 0; b < 3; ++b) M[d][b] = Tm[d][0] * K[0][b] + Tm[d][1] * K[1][b] + Tm[d][2] * K[2][b];
+                    auto gg = [&](int d, int d2) { return wl * (M[d][0] * Tm[d2][0] + M[d][1] * Tm[d2][1] + M[d][2] * Tm[d2][2]); };
+                    G[0] = gg(0, 0); G[1] = gg(0, 1); G[2] = gg(0, 2); G[3] = gg(1, 1); G[4] = gg(1, 2); G[5] = gg(2, 2);
+                }
+                if (need_gx) {
+#pragma unroll
+                    for (int d = 0; d < 3; ++d)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c)
+                            Gx[d][c] = Tm[d][0] * rec[7 + c] + Tm[d][1] * rec[10 + c] + Tm[d][2] * rec[13 + c];
+                }
+            } else {
+                const T* gp = args.geom + eg * 7 * (int64_t)NQp + r;
+                wJ = gp[6 * NQp];
+                if (op == HP_LAPLACIAN || op == HP_HELMHOLTZ) {
+#pragma unroll
+                    for (int f = 0; f < 6; ++f) G[f] = gp[f * NQp];
+                }
+                if (need_gx) {
+                    const T* hp_ = args.dgeom + eg * 9 * (int64_t)NQp + r;
+#pragma unroll
+                    for (int d = 0; d < 3; ++d)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) Gx[d][c] = hp_[(3 * d + c) * NQp];
+                }
+            }
+            T* u = S1 + e * 4 * NQ + r;
+            T uval = u[0];
+            if (op == HP_MASS || op == HP_IPRODUCT_WRT_BASE) {
+                S2[e * NQ + r] = wJ * uval;
+            } else if (op == HP_LAPLACIAN || op == HP_HELMHOLTZ) {
+                T v1 = u[NQ], v2 = u[2 * NQ], v3 = u[3 * NQ];
+                u[NQ] = G[0] * v1 + G[1] * v2 + G[2] * v3;
+                u[2 * NQ] = G[1] * v1 + G[3] * v2 + G[4] * v3;
+                u[3 * NQ] = G[2] * v1 + G[4] * v2 + G[5] * v3;
+                S2[e * NQ + r] = (op == HP_HELMHOLTZ) ? args.lambda * wJ * uval : T(0);
+            } else if (op == HP_PHYSDERIV) {
+                T v1 = u[NQ], v2 = u[2 * NQ], v3 = u[3 * NQ];
+                const int64_t o = args.phys_off[eg] + r;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) args.out[c * args.n_phys_total + o] = Gx[0][c] * v1 + Gx[1][c] * v2 + Gx[2][c] * v3;
+            } else {   // HP_IPRODUCT_WRT_DERIV_BASE: w_d = w|J| sum_i Gx[d][i] f_i
+                T f1 = u[NQ], f2 = u[2 * NQ], f3 = u[3 * NQ];
+#pragma unroll
+                for (int d = 0; d < 3; ++d) u[(d + 1) * NQ] = wJ * (Gx[d][0] * f1 + Gx[d][1] * f2 + Gx[d][2] * f3);
+                S2[e * NQ + r] = T(0);
+            }
+        }
+        __syncthreads();
+        if (op == HP_PHYSDERIV) continue;
+
+        if (sumderiv) {
+            // u' = sum_d D_d^T w_d + t
+            for (int idx = tid; idx < EPB * NQ; idx += NT) {
+                int e = idx / NQ, r = idx - e * NQ;
+                int i = r / QQ, jk = r - i * QQ, j = jk / Q, k = jk - j * Q;
+                const T* w = S1 + e * 4 * NQ;
+                T acc = S2[e * NQ + r];
+#pragma unroll
+                for (int m = 0; m < Q; ++m) {
+                    acc += D0[m * Q + i] * w[NQ + m * QQ + jk];
+                    acc += D1[m * Q + j] * w[2 * NQ + i * QQ + m * Q + k];
+                    acc += D2[m * Q + k] * w[3 * NQ + i * QQ + j * Q + m];
+                }
+                S2[e * NQ + r] = acc;
+            }
+            __syncthreads();
+        }
+
+        // restriction B^T: eta1 pass g'[a][j][k] = sum_i Ta[a][i] u'[i][j][k]
+        for (int idx = tid; idx < EPB * n * QQ; idx += NT) {
+            int e = idx / (n * QQ), r = idx - e * (n * QQ);
+            int a = r / QQ, jk = r - a * QQ;
+            const T* x = S2 + e * NQ + jk;
+            T acc = T(0);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) acc += Ta[a * Q + i] * x[i * QQ];
+            S1[e * 4 * NQ + r] = acc;
+        }
+        __syncthreads();
+        // eta2 pass: f'[a][b][k] = sum_j Tb[t(a)][b][j] g'[a][j][k]
+        for (int idx = tid; idx < EPB * n * n * Q; idx += NT) {
+            int e = idx / (n * n * Q), r = idx - e * (n * n * Q);
+            int ab = r / Q, k = r - ab * Q, a = ab / n, b = ab - a * n;
+            const T* tb = Tb + (famb[a] * n + b) * Q;
+            const T* x = S1 + e * 4 * NQ + a * QQ + k;
+            T acc = T(0);
+#pragma unroll
+            for (int j = 0; j < Q; ++j) acc += tb[j] * x[j * Q];
+            S2[e * NQ + r] = acc;
+        }
+        __syncthreads();
+        // eta3 pass: r[a][b][c] = sum_k Tc[s(a,b)][c][k] f'[a][b][k]
+        for (int idx = tid; idx < EPB * N3; idx += NT) {
+            int e = idx / N3, r = idx - e * N3;
+            int ab = r / n, c = r - ab * n;
+            const T* tc = Tc + (famc[ab] * n + c) * Q;
+            const T* x = S2 + e * NQ + ab * Q;
+            T acc = T(0);
+#pragma unroll
+            for (int k = 0; k < Q; ++k) acc += tc[k] * x[k];
+            S1[e * 4 * NQ + r] = acc;
+        }
+        __syncthreads();
+        // scatter slots to modes (collapsed modes sum their slots)
+        for (int idx = tid; idx < EPB * NP; idx += NT) {
+            int e = idx / NP, m = idx - e * NP;
+            if (e >= ne) continue;
+            const T* rs = S1 + e * 4 * NQ;
+            T acc = T(0);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                int sl = mode_slots[m * 4 + q];
+                if (sl >= 0) acc += rs[sl];
+            }
+            args.out[args.coeff_off[e0 + e] + m] = acc;
+        }
+        __syncthreads();
+    }
+}
+
+template <int SHAPE, int P, typename T, bool AFFINE>
+cudaError_t sf_launch_one(const SFArgs<T>& a, cudaStream_t s) {
+    constexpr int smem = sf_smem_bytes<SHAPE, P, T>();
+    static int grid_cap = 0;
+    auto kern = sf_kernel<SHAPE, P, T, AFFINE>;
+    if (grid_cap == 0) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, SFCfg<P, T>::NT, smem);
+        if (e != cudaSuccess) return e;
+        grid_cap = sms * (per > 0 ? per : 1);
+    }
+    int64_t groups = (a.n_elem + SFCfg<P, T>::EPB - 1) / SFCfg<P, T>::EPB;
+    int grid = (int)(groups < grid_cap ? groups : grid_cap);
+    if (grid <= 0) return cudaSuccess;
+    kern<<<grid, SFCfg<P, T>::NT, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int SHAPE, typename T>
+cudaError_t sf_dispatch(int P, bool affine, const SFArgs<T>& a, cudaStream_t s) {
+#define HP_CASE(PP)                                                               \
+    case PP:                                                                      \
+        return affine ? sf_launch_one<SHAPE, PP, T, true>(a, s) : sf_launch_one<SHAPE, PP, T, false>(a, s);
+    switch (P) {
+        HP_CASE(1) HP_CASE(2) HP_CASE(3) HP_CASE(4) HP_CASE(5)
+        HP_CASE(6) HP_CASE(7) HP_CASE(8) HP_CASE(9) HP_CASE(10)
+        default: return cudaErrorInvalidValue;
+    }
+#undef HP_CASE
+}
+
+}  // namespace hp

@@ -1,0 +1,8 @@
+// Instantiation unit: fused sum-factorised kernels for pyr elements in float.
+#include "hp_sf.cuh"
+
+namespace hp {
+cudaError_t sf_launch_pyr_f32(int P, bool affine, const SFArgs<float>& a, cudaStream_t s) {
+    return sf_dispatch<HP_PYR, float>(P, affine, a, s);
+}
+}  // namespace hp

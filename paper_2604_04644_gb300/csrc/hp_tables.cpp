@@ -1,0 +1,291 @@
+// Reference-element tables: quadrature, 1-D modal families, Lagrange
+// differentiation and the slot <-> mode maps of the four shapes.
+//
+// Quadrature (paper Sec. 2.1: tensor rules with P+2 Gauss-Lobatto points; Sec.
+// 2.3: tensor rules on the collapsed coordinates of the Duffy map).  Zeros of
+// Jacobi polynomials by Newton's method with deflation; Gauss-Lobatto weights
+// from their closed form 2/(Q(Q-1) P_{Q-1}(x)^2); Gauss-Radau-Jacobi weights as
+// integrals of the Lagrange polynomials, computed with a Gauss-Jacobi rule of
+// Q+1 points whose weights use the closed form
+//   w_j = 2^{a+b+1} G(n+a+1) G(n+b+1) / (G(n+a+b+1) n! (1-x_j^2) P_n'(x_j)^2).
+// The Duffy Jacobian is absorbed into the collapsed directions (GRJ with
+// alpha = 1 halved, alpha = 2 quartered).
+//
+// Modal families (modified C0 basis of Karniadakis & Sherwin, cited by the
+// paper for its 3-D expansions): family 0 = {L, R, psi_1..psi_{P-1}},
+// psi_n = L R P^{(1,1)}_{n-1}; family s >= 1 = W_s with W_{s,0} = L^{s+1},
+// W_{s,r} = L^{s+1} R P^{(2s+1,1)}_{r-1} (r = 1..P-1-s).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <stdexcept>
+
+#include "hp_internal.h"
+
+namespace hp {
+namespace {
+
+double jac(int n, double a, double b, double x) {
+    if (n == 0) return 1.0;
+    double p0 = 1.0, p1 = 0.5 * (a - b + (a + b + 2.0) * x);
+    for (int k = 2; k <= n; ++k) {
+        double c = 2.0 * k + a + b;
+        double a1 = 2.0 * k * (k + a + b) * (c - 2.0);
+        double a2 = (c - 1.0) * (a * a - b * b);
+        double a3 = (c - 2.0) * (c - 1.0) * c;
+        double a4 = 2.0 * (k + a - 1.0) * (k + b - 1.0) * c;
+        double p2 = ((a2 + a3 * x) * p1 - a4 * p0) / a1;
+        p0 = p1;
+        p1 = p2;
+    }
+    return p1;
+}
+
+// d/dx P_n^{(a,b)} = (n + a + b + 1)/2 P_{n-1}^{(a+1,b+1)}
+double jac_d(int n, double a, double b, double x) {
+    if (n == 0) return 0.0;
+    return 0.5 * (n + a + b + 1.0) * jac(n - 1, a + 1.0, b + 1.0, x);
+}
+
+std::vector<double> jac_zeros(int n, double a, double b) {
+    std::vector<double> x(n);
+    const double pi = 3.14159265358979323846;
+    for (int k = 0; k < n; ++k) {
+        double r = -std::cos((2.0 * k + 1.0) * pi / (2.0 * n));
+        if (k > 0) r = 0.5 * (r + x[k - 1]);
+        for (int it = 0; it < 200; ++it) {
+            double s = 0.0;
+            for (int j = 0; j < k; ++j) s += 1.0 / (r - x[j]);
+            double p = jac(n, a, b, r);
+            double delta = -p / (jac_d(n, a, b, r) - s * p);
+            r += delta;
+            if (std::fabs(delta) < 1e-16) break;
+        }
+        x[k] = r;
+    }
+    std::sort(x.begin(), x.end());
+    return x;
+}
+
+void gauss_jacobi(int n, double a, double b, std::vector<double>& x, std::vector<double>& w) {
+    x = jac_zeros(n, a, b);
+    w.resize(n);
+    double c = std::pow(2.0, a + b + 1.0) * std::tgamma(n + a + 1.0) * std::tgamma(n + b + 1.0) /
+               (std::tgamma(n + a + b + 1.0) * std::tgamma(n + 1.0));
+    for (int j = 0; j < n; ++j) {
+        double d = jac_d(n, a, b, x[j]);
+        w[j] = c / ((1.0 - x[j] * x[j]) * d * d);
+    }
+}
+
+void gll_rule(int Q, std::vector<double>& x, std::vector<double>& w) {
+    std::vector<double> in = jac_zeros(Q - 2, 1.0, 1.0);
+    x.clear();
+    x.push_back(-1.0);
+    x.insert(x.end(), in.begin(), in.end());
+    x.push_back(1.0);
+    w.resize(Q);
+    for (int i = 0; i < Q; ++i) {
+        double p = jac(Q - 1, 0.0, 0.0, x[i]);
+        w[i] = 2.0 / (Q * (Q - 1.0) * p * p);
+    }
+}
+
+void grj_rule(int Q, int alpha, std::vector<double>& x, std::vector<double>& w) {
+    std::vector<double> in = jac_zeros(Q - 1, (double)alpha, 1.0);
+    x.clear();
+    x.push_back(-1.0);
+    x.insert(x.end(), in.begin(), in.end());
+    std::vector<double> gx, gw;
+    gauss_jacobi(Q + 1, (double)alpha, 0.0, gx, gw);
+    w.assign(Q, 0.0);
+    for (int l = 0; l < Q; ++l) {
+        for (size_t g = 0; g < gx.size(); ++g) {
+            double ell = 1.0;
+            for (int k = 0; k < Q; ++k)
+                if (k != l) ell *= (gx[g] - x[k]) / (x[l] - x[k]);
+            w[l] += gw[g] * ell;
+        }
+    }
+}
+
+// D[i][j] = h_j'(x_i): barycentric form, diagonal by the negative-sum rule
+std::vector<double> lagrange_d(const std::vector<double>& x) {
+    int n = (int)x.size();
+    std::vector<double> c(n, 1.0), D(n * n, 0.0);
+    for (int i = 0; i < n; ++i)
+        for (int k = 0; k < n; ++k)
+            if (k != i) c[i] *= (x[i] - x[k]);
+    for (int i = 0; i < n; ++i) {
+        double s = 0.0;
+        for (int j = 0; j < n; ++j) {
+            if (j == i) continue;
+            D[i * n + j] = c[i] / (c[j] * (x[i] - x[j]));
+            s += D[i * n + j];
+        }
+        D[i * n + i] = -s;
+    }
+    return D;
+}
+
+double fL(double z) { return 0.5 * (1.0 - z); }
+double fR(double z) { return 0.5 * (1.0 + z); }
+
+// member m of family s at z (zero past the end of the family)
+double family(int P, int s, int m, double z) {
+    if (s == 0) {
+        if (m == 0) return fL(z);
+        if (m == 1) return fR(z);
+        if (m <= P) return fL(z) * fR(z) * jac(m - 2, 1.0, 1.0, z);
+        return 0.0;
+    }
+    if (s >= P || m >= P - s) return 0.0;
+    double l = std::pow(fL(z), s + 1);
+    if (m == 0) return l;
+    return l * fR(z) * jac(m - 1, 2.0 * s + 1.0, 1.0, z);
+}
+
+int wA(int a) { return a <= 1 ? 0 : a - 1; }   // weight of member a of family 0
+
+RefTables build(int shape, int P) {
+    RefTables t;
+    t.shape = shape;
+    t.P = P;
+    t.Q = P + 2;
+    t.n = P + 1;
+    const int Q = t.Q, n = t.n;
+    t.NQ = Q * Q * Q;
+    // points per direction
+    std::vector<double> gx, gw, r1x, r1w, r2x, r2w;
+    gll_rule(Q, gx, gw);
+    grj_rule(Q, 1, r1x, r1w);
+    for (double& v : r1w) v *= 0.5;
+    grj_rule(Q, 2, r2x, r2w);
+    for (double& v : r2w) v *= 0.25;
+    t.z[0] = gx; t.w[0] = gw;
+    if (shape == HP_HEX) { t.z[1] = gx; t.w[1] = gw; t.z[2] = gx; t.w[2] = gw; }
+    if (shape == HP_PRISM) { t.z[1] = gx; t.w[1] = gw; t.z[2] = r1x; t.w[2] = r1w; }
+    if (shape == HP_PYR) { t.z[1] = gx; t.w[1] = gw; t.z[2] = r2x; t.w[2] = r2w; }
+    if (shape == HP_TET) { t.z[1] = r1x; t.w[1] = r1w; t.z[2] = r2x; t.w[2] = r2w; }
+    for (int d = 0; d < 3; ++d) t.D[d] = lagrange_d(t.z[d]);
+    // 1-D tables
+    t.Ta.assign(n * Q, 0.0);
+    for (int a = 0; a < n; ++a)
+        for (int i = 0; i < Q; ++i) t.Ta[a * Q + i] = family(P, 0, a, t.z[0][i]);
+    t.Tb.assign((P + 1) * n * Q, 0.0);
+    t.Tc.assign((P + 1) * n * Q, 0.0);
+    for (int s = 0; s <= P; ++s)
+        for (int m = 0; m < n; ++m)
+            for (int q = 0; q < Q; ++q) {
+                t.Tb[(s * n + m) * Q + q] = family(P, s, m, t.z[1][q]);
+                t.Tc[(s * n + m) * Q + q] = family(P, s, m, t.z[2][q]);
+            }
+    // families and slot validity
+    t.famb.assign(n, 0);
+    t.famc.assign(n * n, 0);
+    for (int a = 0; a < n; ++a) {
+        if (shape == HP_TET) t.famb[a] = (uint8_t)wA(a);
+        for (int b = 0; b < n; ++b) {
+            int s = 0;
+            if (shape == HP_PRISM) s = wA(a);
+            if (shape == HP_PYR) s = std::max(wA(a), wA(b));
+            if (shape == HP_TET) {
+                if (a <= 1) s = wA(b);
+                else s = (b < P - wA(a)) ? wA(a) + b : P;
+            }
+            t.famc[a * n + b] = (uint8_t)s;
+        }
+    }
+    // canonical slot of each valid slot (merges of the collapsed modes)
+    std::vector<int> canon(n * n * n, -1);
+    for (int a = 0; a < n; ++a)
+        for (int b = 0; b < n; ++b) {
+            int s = t.famc[a * n + b];
+            bool bvalid = true;
+            if (shape == HP_TET && a >= 2) bvalid = b < P - wA(a);
+            for (int c = 0; c < n; ++c) {
+                bool cvalid = bvalid && (s == 0 ? true : (s < P && c < P - s));
+                if (!cvalid) continue;
+                int ca = a, cb = b, cc = c;
+                if (shape == HP_PRISM && s == 0 && c == 1 && a <= 1) ca = 0;
+                if (shape == HP_PYR && s == 0 && c == 1 && a <= 1 && b <= 1) { ca = 0; cb = 0; }
+                if (shape == HP_TET && a <= 1) {
+                    if (b <= 1 && c == 1) { ca = 0; cb = 0; }
+                    else if (b == 1) ca = 0;
+                }
+                canon[(a * n + b) * n + c] = (ca * n + cb) * n + cc;
+            }
+        }
+    std::vector<int> mode_of(n * n * n, -1);
+    int m = 0;
+    for (int sl = 0; sl < n * n * n; ++sl)
+        if (canon[sl] == sl) mode_of[sl] = m++;
+    t.NP = m;
+    t.slot2mode.assign(n * n * n, -1);
+    t.mode_slots.assign(m * 4, -1);
+    std::vector<int> cnt(m, 0);
+    for (int sl = 0; sl < n * n * n; ++sl) {
+        if (canon[sl] < 0) continue;
+        int md = mode_of[canon[sl]];
+        if (md < 0 || cnt[md] >= 4) throw std::runtime_error("slot map");
+        t.slot2mode[sl] = (int16_t)md;
+        t.mode_slots[md * 4 + cnt[md]++] = (int16_t)sl;
+    }
+    if (t.NP != n_modes(shape, P)) throw std::runtime_error("mode count");
+    return t;
+}
+
+std::mutex g_mu;
+std::map<int, RefTables> g_tables;
+
+}  // namespace
+
+int n_modes(int shape, int P) {
+    switch (shape) {
+        case HP_HEX: return (P + 1) * (P + 1) * (P + 1);
+        case HP_PRISM: return (P + 1) * (P + 1) * (P + 2) / 2;
+        case HP_PYR: return (P + 1) * (P + 2) * (2 * P + 3) / 6;
+        default: return (P + 1) * (P + 2) * (P + 3) / 6;
+    }
+}
+
+const RefTables& ref_tables(int shape, int P) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    int key = shape * 16 + P;
+    auto it = g_tables.find(key);
+    if (it == g_tables.end()) it = g_tables.emplace(key, build(shape, P)).first;
+    return it->second;
+}
+
+std::vector<unsigned char> make_blob(const RefTables& t, size_t vs) {
+    BlobLayout L = blob_layout_c(t.shape, t.P, (int)vs);
+    std::vector<unsigned char> out(L.total_bytes, 0);
+    auto put = [&](int off, const std::vector<double>& v) {
+        for (size_t i = 0; i < v.size(); ++i) {
+            if (vs == 8) {
+                double d = v[i];
+                std::memcpy(&out[(off + i) * 8], &d, 8);
+            } else {
+                float f = (float)v[i];
+                std::memcpy(&out[(off + i) * 4], &f, 4);
+            }
+        }
+    };
+    put(L.Ta, t.Ta);
+    put(L.Tb, t.Tb);
+    put(L.Tc, t.Tc);
+    for (int d = 0; d < 3; ++d) {
+        std::vector<double> tmp(t.D[d]);
+        put(L.D + d * t.Q * t.Q, tmp);
+        put(L.z + d * t.Q, t.z[d]);
+        put(L.w + d * t.Q, t.w[d]);
+    }
+    std::memcpy(&out[L.famb], t.famb.data(), t.famb.size());
+    std::memcpy(&out[L.famc], t.famc.data(), t.famc.size());
+    std::memcpy(&out[L.slot2mode], t.slot2mode.data(), 2 * t.slot2mode.size());
+    std::memcpy(&out[L.mode_slots], t.mode_slots.data(), 2 * t.mode_slots.size());
+    return out;
+}
+
+}  // namespace hp

@@ -1,0 +1,165 @@
+"""ctypes binding of the libhp C ABI (include/hp.h): same names, argument
+marshalling only.  Every operator runs in the library's CUDA kernels; if the
+shared library is missing this module raises at import time.
+
+Device arrays are passed as torch CUDA tensors (or raw integer addresses);
+streams as torch.cuda.Stream, an integer cudaStream_t, or None for the
+current torch stream.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhp.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libhp.so is not built (run __graft_entry__.build() or "
+                      "python -m paper_2604_04644_gb300.build); there is no fallback path")
+_lib = ctypes.CDLL(LIB_PATH)
+
+# enums (values from include/hp.h)
+HP_OK, HP_ERR_ARG, HP_ERR_OOM, HP_ERR_CUDA, HP_ERR_GEOM, HP_ERR_UNSUPPORTED, HP_ERR_TIMEOUT, \
+    HP_ERR_DEVICE_BOUNDS, HP_ERR_NOT_CONVERGED = range(9)
+HP_HEX, HP_PRISM, HP_PYR, HP_TET = range(4)
+HP_MASS, HP_LAPLACIAN, HP_HELMHOLTZ, HP_BWDTRANS, HP_IPRODUCT_WRT_BASE, HP_PHYSDERIV, \
+    HP_IPRODUCT_WRT_DERIV_BASE = range(7)
+HP_STRAT_SUMFAC, HP_STRAT_ELEMAT, HP_STRAT_HYBRID, HP_STRAT_AUTO = range(4)
+HP_FP64, HP_FP32, HP_TF32, HP_BF16 = range(4)
+
+EXPORTED = ["hp_mesh_create", "hp_mesh_layout", "hp_geom_factors", "hp_geom_copy", "hp_op_create",
+            "hp_op_apply", "hp_op_sync", "hp_op_work", "hp_op_destroy", "hp_mesh_destroy",
+            "hp_status_str", "hp_last_error"]
+
+
+class HpError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        msg = _lib.hp_last_error().decode()
+        super().__init__("%s failed: %s (%s)" % (where, _lib.hp_status_str(status).decode(), msg))
+
+
+class hp_mesh_desc(ctypes.Structure):
+    _fields_ = [("n_elem", ctypes.c_int64), ("shape", ctypes.c_void_p), ("P", ctypes.c_void_p),
+                ("Q", ctypes.c_void_p), ("vert", ctypes.c_void_p), ("xyz", ctypes.c_void_p),
+                ("n_vert", ctypes.c_int64), ("curved", ctypes.c_void_p), ("deformation", ctypes.c_int32)]
+
+
+_vp, _i64p, _dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)
+_lib.hp_mesh_create.argtypes = [ctypes.POINTER(hp_mesh_desc), ctypes.c_int, ctypes.POINTER(_vp)]
+_lib.hp_mesh_layout.argtypes = [_vp, _vp, _vp, _i64p, _i64p]
+_lib.hp_geom_factors.argtypes = [_vp, _vp]
+_lib.hp_geom_copy.argtypes = [_vp, _vp, _vp]
+_lib.hp_op_create.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_vp)]
+_lib.hp_op_apply.argtypes = [_vp, ctypes.c_double, _vp, _vp, _vp]
+_lib.hp_op_sync.argtypes = [_vp, _vp]
+_lib.hp_op_work.argtypes = [_vp, _i64p, _dp, _dp]
+_lib.hp_op_destroy.argtypes = [_vp]
+_lib.hp_mesh_destroy.argtypes = [_vp]
+_lib.hp_status_str.argtypes = [ctypes.c_int]
+_lib.hp_status_str.restype = ctypes.c_char_p
+_lib.hp_last_error.restype = ctypes.c_char_p
+for _f in ("hp_mesh_create", "hp_mesh_layout", "hp_geom_factors", "hp_geom_copy", "hp_op_create",
+           "hp_op_apply", "hp_op_sync", "hp_op_work"):
+    getattr(_lib, _f).restype = ctypes.c_int
+
+
+def _check(st, where):
+    if st != HP_OK:
+        raise HpError(st, where)
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError("cannot take the address of %r" % type(x))
+
+
+def _stream(s):
+    if s is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def hp_mesh_create(mesh, device=0):
+    """mesh: dict with the hp_mesh_desc arrays (see paper_2604_04644_gb300.inputs)."""
+    keep = dict(
+        shape=np.ascontiguousarray(mesh["shape"], dtype=np.uint8),
+        P=np.ascontiguousarray(mesh["P"], dtype=np.uint8),
+        Q=np.ascontiguousarray(mesh["Q"], dtype=np.uint8),
+        vert=np.ascontiguousarray(mesh["vert"], dtype=np.int64),
+        xyz=np.ascontiguousarray(mesh["xyz"], dtype=np.float64),
+        curved=np.ascontiguousarray(mesh["curved"], dtype=np.uint8),
+    )
+    d = hp_mesh_desc(int(mesh["n_elem"]), keep["shape"].ctypes.data, keep["P"].ctypes.data,
+                     keep["Q"].ctypes.data, keep["vert"].ctypes.data, keep["xyz"].ctypes.data,
+                     int(keep["xyz"].shape[0]), keep["curved"].ctypes.data, int(mesh["deformation"]))
+    h = _vp()
+    _check(_lib.hp_mesh_create(ctypes.byref(d), int(device), ctypes.byref(h)), "hp_mesh_create")
+    return h.value
+
+
+def hp_mesh_layout(mesh, n_elem):
+    co = np.zeros(n_elem + 1, dtype=np.int64)
+    po = np.zeros(n_elem + 1, dtype=np.int64)
+    nc, nph = ctypes.c_int64(), ctypes.c_int64()
+    _check(_lib.hp_mesh_layout(mesh, co.ctypes.data, po.ctypes.data, ctypes.byref(nc), ctypes.byref(nph)),
+           "hp_mesh_layout")
+    return co, po, nc.value, nph.value
+
+
+def hp_geom_factors(mesh, stream=None):
+    _check(_lib.hp_geom_factors(mesh, _stream(stream)), "hp_geom_factors")
+
+
+def hp_geom_copy(mesh, n_phys, want_deriv=False):
+    out7 = np.zeros(7 * n_phys)
+    out9 = np.zeros(9 * n_phys) if want_deriv else None
+    _check(_lib.hp_geom_copy(mesh, out7.ctypes.data, None if out9 is None else out9.ctypes.data), "hp_geom_copy")
+    return out7, out9
+
+
+def hp_op_create(mesh, kind, strategy=HP_STRAT_SUMFAC, dtype=HP_FP64):
+    h = _vp()
+    _check(_lib.hp_op_create(mesh, int(kind), int(strategy), int(dtype), ctypes.byref(h)), "hp_op_create")
+    return h.value
+
+
+def hp_op_apply(op, lam, x, y, stream=None):
+    _check(_lib.hp_op_apply(op, float(lam), _ptr(x), _ptr(y), _stream(stream)), "hp_op_apply")
+
+
+def hp_op_sync(op, stream=None):
+    _check(_lib.hp_op_sync(op, _stream(stream)), "hp_op_sync")
+
+
+def hp_op_work(op):
+    d, f, b = ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
+    _check(_lib.hp_op_work(op, ctypes.byref(d), ctypes.byref(f), ctypes.byref(b)), "hp_op_work")
+    return d.value, f.value, b.value
+
+
+def hp_op_destroy(op):
+    _lib.hp_op_destroy(op)
+
+
+def hp_mesh_destroy(mesh):
+    _lib.hp_mesh_destroy(mesh)
+
+
+def hp_status_str(s):
+    return _lib.hp_status_str(int(s)).decode()
+
+
+def hp_last_error():
+    return _lib.hp_last_error().decode()

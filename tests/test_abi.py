@@ -1,0 +1,55 @@
+"""The C-ABI library loads on a machine without a GPU and exports every
+function that include/hp.h declares (no compute calls here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    txt = open(os.path.join(ROOT, "include", "hp.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:hp_status|void|const char\s*\*)\s*(hp_\w+)\s*\(", txt, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2604_04644_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for f in ("hp_mesh_create", "hp_geom_factors", "hp_op_apply", "hp_op_create", "hp_mesh_layout"):
+        assert f in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [f for f in declared_functions() if not hasattr(lib, f)]
+    assert not missing, missing
+
+
+def test_status_strings(lib):
+    lib.hp_status_str.restype = ctypes.c_char_p
+    assert lib.hp_status_str(0) == b"HP_OK"
+    assert lib.hp_status_str(4) == b"HP_ERR_GEOM"
+
+
+def test_binding_names_match_header(lib):
+    from paper_2604_04644_gb300 import hp
+    assert sorted(hp.EXPORTED) == sorted(f for f in declared_functions() if f in hp.EXPORTED)
+    for f in hp.EXPORTED:
+        assert hasattr(hp, f)
+
+
+def test_null_arguments_are_rejected_without_gpu(lib):
+    # argument validation happens before any CUDA call
+    lib.hp_mesh_create.restype = ctypes.c_int
+    assert lib.hp_mesh_create(None, 0, None) == 1          # HP_ERR_ARG
+    lib.hp_op_apply.restype = ctypes.c_int
+    lib.hp_op_apply.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    assert lib.hp_op_apply(None, 1.0, None, None, None) == 1
