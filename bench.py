@@ -34,13 +34,21 @@ FP64_PEAK_TFLOPS = 1.25     # GB300 FP64 (vector and tensor) nominal rate, profi
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--steps", type=int, default=50)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--dtype", default="f64", choices=["f64", "f32"])
     p.add_argument("--no-table", action="store_true", help="skip the per-shape/order table")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    return p.parse_args()
+    p.add_argument("--orders", default=None, help="comma-separated orders (default 1..8); for profiling runs")
+    p.add_argument("--cells", type=int, default=None, help="cells per direction (default 16); for profiling runs")
+    a = p.parse_args()
+    global ORDERS, CELLS
+    if a.orders:
+        ORDERS = [int(x) for x in a.orders.split(",")]
+    if a.cells:
+        CELLS = a.cells
+    return a
 
 
 def dist_init(args):
@@ -85,7 +93,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.th = threading.Thread(target=self._read, daemon=True)
             self.th.start()
@@ -357,8 +365,8 @@ def main():
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.dtype,
                 "data": "synthetic",
-                "config": {"workload": "helmholtz_mixed_16cube_P1-8_curved", "cells": "16x16x16",
-                           "elements": int(work[0]["mesh"]["n_elem"]), "orders": "1..8", "Q": "P+2",
+                "config": {"workload": "helmholtz_mixed_%dcube_P%s_curved" % (CELLS, "-".join(map(str, ORDERS))),
+                           "cells": "%dx%dx%d" % (CELLS, CELLS, CELLS), "elements": int(work[0]["mesh"]["n_elem"]), "orders": ",".join(map(str, ORDERS)), "Q": "P+2",
                            "lambda": 1.0, "strategy": "sumfac_collocated",
                            "l2": "flushed (256 MiB write) before every apply, outside the timed events"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
