@@ -40,6 +40,7 @@ def parse():
     p.add_argument("--dtype", default="f64", choices=["f64", "f32"])
     p.add_argument("--no-table", action="store_true", help="skip the per-shape/order table")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    p.add_argument("--no-extra", action="store_true", help="skip the p-adaptive batched measurement")
     p.add_argument("--orders", default=None, help="comma-separated orders (default 1..8); for profiling runs")
     p.add_argument("--cells", type=int, default=None, help="cells per direction (default 16); for profiling runs")
     a = p.parse_args()
@@ -253,6 +254,58 @@ def shape_order_table(dtype_name, device, reps=5):
     return out
 
 
+def padaptive(device, reps=10):
+    """p-adaptive batched apply: 40x40x32 cells of the four-slab mesh (192 000
+    elements), P ~ U{2..8} per element (seed 3), affine for x < 0.5 and curved
+    otherwise, FP64 Helmholtz.  One launch per (shape, P, curved) block on one
+    stream vs one CUDA-graph launch with the blocks as concurrent nodes, with
+    default and autotuned tiles."""
+    import torch
+    from paper_2604_04644_gb300 import hp, inputs
+    mesh = inputs.slab_mesh(40, 40, 32, (2, 8), order_seed=3, curved_rule="x_half")
+    h = hp.hp_mesh_create(mesh, device)
+    co, po, nc, nph = hp.hp_mesh_layout(h, mesh["n_elem"])
+    op = hp.hp_op_create(h, hp.HP_HELMHOLTZ, hp.HP_STRAT_SUMFAC, hp.HP_FP64)
+    x = torch.tensor(inputs.random_coefficients(1003, co), device="cuda:%d" % device)
+    y = torch.zeros(nc, device="cuda:%d" % device, dtype=torch.float64)
+    dofs, flops, bytes_ = hp.hp_op_work(op)
+    stream = torch.cuda.current_stream(device)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda:%d" % device)
+    nblocks = len(set(zip(mesh["shape"].tolist(), mesh["P"].tolist(), mesh["curved"].tolist())))
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        hp.hp_op_sync(op, stream)
+        return statistics.median(ts)
+
+    t_stream = timed(lambda: hp.hp_op_apply(op, 1.0, x, y, stream))
+    t_graph = timed(lambda: hp.hp_op_apply_graph(op, 1.0, x, y, stream))
+    hp.hp_op_tune(op, 1.0, x, y, stream)
+    tiles = hp.hp_op_tiles(op, nblocks)
+    t_tuned = timed(lambda: hp.hp_op_apply_graph(op, 1.0, x, y, stream))
+    hp.hp_op_destroy(op)
+    hp.hp_mesh_destroy(h)
+    g = lambda ms: round(dofs / (ms * 1e-3) / 1e9, 4)
+    return {"workload": "helmholtz_padaptive_40x40x32_P2-8_affine_curved_halves", "elements": int(mesh["n_elem"]),
+            "dofs": int(dofs), "blocks": nblocks, "dtype": "f64",
+            "per_block_launches": {"ms": round(t_stream, 4), "gdofs": g(t_stream)},
+            "graph": {"ms": round(t_graph, 4), "gdofs": g(t_graph)},
+            "graph_autotuned": {"ms": round(t_tuned, 4), "gdofs": g(t_tuned),
+                                "tiles_histogram": np.bincount(tiles, minlength=3).tolist()},
+            "tflops_graph_autotuned": round(flops / (t_tuned * 1e-3) / 1e12, 4)}
+
+
 def cpu_baseline(target_s=12.0):
     """The oracle (plain FP64 numpy definition) on a bounded sample of the
     workload: Helmholtz on a random subset of elements at each order."""
@@ -357,6 +410,9 @@ def main():
     table = None
     if rank == 0 and not args.no_table:
         table = shape_order_table(args.dtype, local)
+    batched = None
+    if rank == 0 and not args.no_extra:
+        batched = padaptive(local)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline()
@@ -370,7 +426,8 @@ def main():
                            "lambda": 1.0, "strategy": "sumfac_collocated",
                            "l2": "flushed (256 MiB write) before every apply, outside the timed events"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-                "clocks": clk.summary(), "per_order": per_order, "per_shape_order": table}
+                "clocks": clk.summary(), "per_order": per_order, "per_shape_order": table,
+                "p_adaptive": batched}
         print(json.dumps(line), flush=True)
     for w in work:
         from paper_2604_04644_gb300 import hp

@@ -127,8 +127,8 @@ hp_status hp_mesh_create(const hp_mesh_desc* desc, int device, hp_mesh* out);
 hp_status hp_mesh_layout(hp_mesh mesh, int64_t* coeff_offset, int64_t* phys_offset,
                          int64_t* n_coeff, int64_t* n_phys);
 
-/* Geometric factors in FP64 on the device (paper Sec. 2.1 chain rule; the
- * "six geometric factors as well as the Jacobian" of Sec. 4): for curved
+/* Geometric factors in FP64 on the device (paper Sec. 2.1 chain rule; Sec. 4 names these
+ * six metric terms and the Jacobian as the geometric data of deformed elements): for curved
  * elements, at every quadrature point G_dd' = w|J| sum_i (d eta_d/d x_i)
  * (d eta_d'/d x_i) (d <= d') and w|J|; for affine elements per element
  * |J| (d xi/d x)(d xi/d x)^T, |J| and d xi/d x.  Idempotent: the first call
@@ -158,6 +158,26 @@ hp_status hp_op_create(hp_mesh mesh, hp_opkind kind, hp_strategy strategy, hp_dt
  * Errors detected before launch: HP_ERR_ARG; launch failure: HP_ERR_CUDA.
  * Device-side errors latch in the op and are returned by hp_op_sync. */
 hp_status hp_op_apply(hp_op op, double lambda, const void* in, void* out, void* stream);
+
+/* Batched apply for meshes with many blocks (p-adaptive / mixed meshes): the
+ * same result as hp_op_apply, launched as one CUDA graph in which every block's
+ * kernel is an independent node, so blocks of different (shape, P, curved) run
+ * concurrently on the GPU.  The graph is built on the first call for a given
+ * (lambda, in, out) -- that call also runs the apply once uncaptured -- and
+ * replayed by later calls with the same arguments; other arguments rebuild it.
+ * Do not call it while `stream` is being captured.  Errors as hp_op_apply. */
+hp_status hp_op_apply_graph(hp_op op, double lambda, const void* in, void* out, void* stream);
+
+/* Autotune: time each block's kernel with each tile variant (elements per CTA
+ * chosen from shared-memory budgets of 56, 20 and 110 KB) on the given arrays
+ * (their contents are overwritten as by hp_op_apply) and keep the fastest per
+ * block.  Synchronises `stream`.  Results are bitwise identical for every tile. */
+hp_status hp_op_tune(hp_op op, double lambda, const void* in, void* out, void* stream);
+
+/* Read (set = 0) or write (set = 1) the tile variant (0..2) of each of the op's
+ * n_blocks blocks (blocks in order of first appearance of (shape, P, curved) in
+ * user element order).  HP_ERR_ARG if n_blocks does not match or a tile is out of range. */
+hp_status hp_op_tiles(hp_op op, int* tiles, int64_t n_blocks, int set);
 
 /* Synchronise `stream` and report any error latched by the op's kernels
  * (HP_ERR_TIMEOUT, HP_ERR_DEVICE_BOUNDS) or by CUDA. */

@@ -190,6 +190,45 @@ double elem_flops(int shape, int P, hp_opkind k) {
     }
 }
 
+cudaError_t launch_block(hp_op op, size_t bi, int tile, double lambda, const void* in, void* out, cudaStream_t s) {
+    hp_mesh m = op->mesh;
+    const Block& b = m->blocks[bi];
+    const DeviceBlobs& blob = m->blobs.at(b.shape * 16 + b.P);
+    const int64_t nphys = m->phys_off.back();
+    if (op->dtype == HP_FP64) {
+        SFArgs<double> a{};
+        a.op = op->kind;
+        a.n_elem = b.n_elem;
+        a.lambda = lambda;
+        a.coeff_off = b.d_coeff_off;
+        a.phys_off = b.d_phys_off;
+        a.in = static_cast<const double*>(in);
+        a.out = static_cast<double*>(out);
+        a.n_phys_total = nphys;
+        a.geom = b.d_geom;
+        a.dgeom = b.d_dgeom;
+        a.blob = static_cast<const unsigned char*>(blob.d64);
+        a.blob_bytes = blob.bytes64;
+        a.err = op->d_err;
+        return sf_launch_f64(b.shape, b.P, !b.curved, tile, a, s);
+    }
+    SFArgs<float> a{};
+    a.op = op->kind;
+    a.n_elem = b.n_elem;
+    a.lambda = (float)lambda;
+    a.coeff_off = b.d_coeff_off;
+    a.phys_off = b.d_phys_off;
+    a.in = static_cast<const float*>(in);
+    a.out = static_cast<float*>(out);
+    a.n_phys_total = nphys;
+    a.geom = b.d_geom32;
+    a.dgeom = b.d_dgeom32;
+    a.blob = static_cast<const unsigned char*>(blob.d32);
+    a.blob_bytes = blob.bytes32;
+    a.err = op->d_err;
+    return sf_launch_f32(b.shape, b.P, !b.curved, tile, a, s);
+}
+
 }  // namespace
 }  // namespace hp
 
@@ -450,6 +489,7 @@ hp_status hp_op_create(hp_mesh m, hp_opkind kind, hp_strategy strategy, hp_dtype
     op->kind = kind;
     op->strategy = strategy;
     op->dtype = dtype;
+    op->tile.assign(m->blocks.size(), 0);
     st = upload<unsigned int>(&op->d_err, nullptr, 1);
     if (!st) cudaMemset(op->d_err, 0, sizeof(unsigned int));
     if (st) { delete op; return st; }
@@ -460,48 +500,120 @@ hp_status hp_op_create(hp_mesh m, hp_opkind kind, hp_strategy strategy, hp_dtype
 hp_status hp_op_apply(hp_op op, double lambda, const void* in, void* out, void* stream) {
     if (!op || !in || !out) { set_error("hp_op_apply: null argument"); return HP_ERR_ARG; }
     if (in == out) { set_error("hp_op_apply: in and out must not alias"); return HP_ERR_ARG; }
-    hp_mesh m = op->mesh;
-    DeviceGuard guard(m->device);
-    cudaStream_t s = (cudaStream_t)stream;
-    const int64_t nphys = m->phys_off.back();
-    for (const Block& b : m->blocks) {
-        const DeviceBlobs& blob = m->blobs.at(b.shape * 16 + b.P);
-        cudaError_t e;
-        if (op->dtype == HP_FP64) {
-            SFArgs<double> a{};
-            a.op = op->kind;
-            a.n_elem = b.n_elem;
-            a.lambda = lambda;
-            a.coeff_off = b.d_coeff_off;
-            a.phys_off = b.d_phys_off;
-            a.in = static_cast<const double*>(in);
-            a.out = static_cast<double*>(out);
-            a.n_phys_total = nphys;
-            a.geom = b.d_geom;
-            a.dgeom = b.d_dgeom;
-            a.blob = static_cast<const unsigned char*>(blob.d64);
-            a.blob_bytes = blob.bytes64;
-            a.err = op->d_err;
-            e = sf_launch_f64(b.shape, b.P, !b.curved, a, s);
-        } else {
-            SFArgs<float> a{};
-            a.op = op->kind;
-            a.n_elem = b.n_elem;
-            a.lambda = (float)lambda;
-            a.coeff_off = b.d_coeff_off;
-            a.phys_off = b.d_phys_off;
-            a.in = static_cast<const float*>(in);
-            a.out = static_cast<float*>(out);
-            a.n_phys_total = nphys;
-            a.geom = b.d_geom32;
-            a.dgeom = b.d_dgeom32;
-            a.blob = static_cast<const unsigned char*>(blob.d32);
-            a.blob_bytes = blob.bytes32;
-            a.err = op->d_err;
-            e = sf_launch_f32(b.shape, b.P, !b.curved, a, s);
-        }
+    DeviceGuard guard(op->mesh->device);
+    for (size_t i = 0; i < op->mesh->blocks.size(); ++i) {
+        cudaError_t e = launch_block(op, i, op->tile[i], lambda, in, out, (cudaStream_t)stream);
         if (e != cudaSuccess) return cuda_fail(e, "hp_op_apply launch");
     }
+    return HP_OK;
+}
+
+hp_status hp_op_tune(hp_op op, double lambda, const void* in, void* out, void* stream) {
+    if (!op || !in || !out) { set_error("hp_op_tune: null argument"); return HP_ERR_ARG; }
+    if (in == out) { set_error("hp_op_tune: in and out must not alias"); return HP_ERR_ARG; }
+    DeviceGuard guard(op->mesh->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    const bool f64 = op->dtype == HP_FP64;
+    for (size_t i = 0; i < op->mesh->blocks.size(); ++i) {
+        const Block& blk = op->mesh->blocks[i];
+        float best = 1e30f;
+        int best_t = 0;
+        std::vector<int> seen;
+        for (int t = 0; t < kTiles; ++t) {
+            int epb = sf_epb_host(blk.P, t, f64);
+            if (std::find(seen.begin(), seen.end(), epb) != seen.end()) continue;
+            seen.push_back(epb);
+            float tot = 0.f;
+            for (int r = 0; r < 5; ++r) {
+                cudaEventRecord(a, s);
+                cudaError_t e = launch_block(op, i, t, lambda, in, out, s);
+                cudaEventRecord(b, s);
+                if (e != cudaSuccess) { cudaEventDestroy(a); cudaEventDestroy(b); return cuda_fail(e, "hp_op_tune"); }
+                cudaError_t se = cudaEventSynchronize(b);
+                if (se != cudaSuccess) { cudaEventDestroy(a); cudaEventDestroy(b); return cuda_fail(se, "hp_op_tune"); }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, a, b);
+                if (r >= 1) tot += ms;     // first launch warms up
+            }
+            if (tot < best) { best = tot; best_t = t; }
+        }
+        op->tile[i] = best_t;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (op->graph) { cudaGraphExecDestroy(op->graph); op->graph = nullptr; }
+    return check_device_error(op->mesh, op->d_err, nullptr, "hp_op_tune");
+}
+
+hp_status hp_op_tiles(hp_op op, int* tiles, int64_t n_blocks, int set) {
+    if (!op || !tiles || n_blocks != (int64_t)op->tile.size()) { set_error("hp_op_tiles: bad argument"); return HP_ERR_ARG; }
+    for (int64_t i = 0; i < n_blocks; ++i) {
+        if (set) {
+            if (tiles[i] < 0 || tiles[i] >= kTiles) { set_error("hp_op_tiles: bad tile"); return HP_ERR_ARG; }
+            op->tile[i] = tiles[i];
+        } else {
+            tiles[i] = op->tile[i];
+        }
+    }
+    if (set && op->graph) { cudaGraphExecDestroy(op->graph); op->graph = nullptr; }
+    return HP_OK;
+}
+
+hp_status hp_op_apply_graph(hp_op op, double lambda, const void* in, void* out, void* stream) {
+    if (!op || !in || !out) { set_error("hp_op_apply_graph: null argument"); return HP_ERR_ARG; }
+    if (in == out) { set_error("hp_op_apply_graph: in and out must not alias"); return HP_ERR_ARG; }
+    DeviceGuard guard(op->mesh->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!op->graph || op->g_in != in || op->g_out != out || op->g_lambda != lambda) {
+        if (op->graph) { cudaGraphExecDestroy(op->graph); op->graph = nullptr; }
+        const size_t nb = op->mesh->blocks.size();
+        // first launches set kernel attributes outside the capture
+        for (size_t i = 0; i < nb; ++i) {
+            cudaError_t e = launch_block(op, i, op->tile[i], lambda, in, out, s);
+            if (e != cudaSuccess) return cuda_fail(e, "hp_op_apply_graph warm-up");
+        }
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(e, "hp_op_apply_graph warm-up");
+        const size_t np = std::min<size_t>(nb, 16);
+        while (op->pool.size() < np) {
+            cudaStream_t t;
+            e = cudaStreamCreateWithFlags(&t, cudaStreamNonBlocking);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
+            op->pool.push_back(t);
+        }
+        cudaStream_t cap;
+        e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
+        std::vector<cudaEvent_t> evs(nb + 1);
+        for (auto& ev : evs) cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaEventRecord(evs[nb], cap);
+            for (size_t i = 0; i < nb && e == cudaSuccess; ++i) {
+                cudaStream_t si = op->pool[i % np];
+                cudaStreamWaitEvent(si, evs[nb], 0);
+                e = launch_block(op, i, op->tile[i], lambda, in, out, si);
+                cudaEventRecord(evs[i], si);
+                cudaStreamWaitEvent(cap, evs[i], 0);
+            }
+            cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+            if (e == cudaSuccess) e = e2;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&op->graph, g, 0);
+        if (g) cudaGraphDestroy(g);
+        for (auto& ev : evs) cudaEventDestroy(ev);
+        cudaStreamDestroy(cap);
+        if (e != cudaSuccess) { op->graph = nullptr; return cuda_fail(e, "hp_op_apply_graph capture"); }
+        op->g_in = in;
+        op->g_out = out;
+        op->g_lambda = lambda;
+    }
+    cudaError_t e = cudaGraphLaunch(op->graph, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
     return HP_OK;
 }
 
@@ -547,6 +659,9 @@ hp_status hp_op_work(hp_op op, int64_t* out_dofs, double* flops, double* bytes) 
 
 void hp_op_destroy(hp_op op) {
     if (!op) return;
+    DeviceGuard guard(op->mesh->device);
+    if (op->graph) cudaGraphExecDestroy(op->graph);
+    for (cudaStream_t t : op->pool) cudaStreamDestroy(t);
     cudaFree(op->d_err);
     delete op;
 }
@@ -568,29 +683,25 @@ void hp_mesh_destroy(hp_mesh m) {
 }  // extern "C"
 
 namespace hp {
-cudaError_t sf_launch_hex_f64(int P, bool affine, const SFArgs<double>& a, cudaStream_t s);
-cudaError_t sf_launch_prism_f64(int P, bool affine, const SFArgs<double>& a, cudaStream_t s);
-cudaError_t sf_launch_pyr_f64(int P, bool affine, const SFArgs<double>& a, cudaStream_t s);
-cudaError_t sf_launch_tet_f64(int P, bool affine, const SFArgs<double>& a, cudaStream_t s);
-cudaError_t sf_launch_hex_f32(int P, bool affine, const SFArgs<float>& a, cudaStream_t s);
-cudaError_t sf_launch_prism_f32(int P, bool affine, const SFArgs<float>& a, cudaStream_t s);
-cudaError_t sf_launch_pyr_f32(int P, bool affine, const SFArgs<float>& a, cudaStream_t s);
-cudaError_t sf_launch_tet_f32(int P, bool affine, const SFArgs<float>& a, cudaStream_t s);
+#define HP_DECL(S, D, T) cudaError_t sf_launch_##S##_##D(int P, bool affine, int tile, const SFArgs<T>& a, cudaStream_t s);
+HP_DECL(hex, f64, double) HP_DECL(prism, f64, double) HP_DECL(pyr, f64, double) HP_DECL(tet, f64, double)
+HP_DECL(hex, f32, float) HP_DECL(prism, f32, float) HP_DECL(pyr, f32, float) HP_DECL(tet, f32, float)
+#undef HP_DECL
 
-cudaError_t sf_launch_f64(int shape, int P, bool affine, const SFArgs<double>& a, cudaStream_t s) {
+cudaError_t sf_launch_f64(int shape, int P, bool affine, int tile, const SFArgs<double>& a, cudaStream_t s) {
     switch (shape) {
-        case HP_HEX: return sf_launch_hex_f64(P, affine, a, s);
-        case HP_PRISM: return sf_launch_prism_f64(P, affine, a, s);
-        case HP_PYR: return sf_launch_pyr_f64(P, affine, a, s);
-        default: return sf_launch_tet_f64(P, affine, a, s);
+        case HP_HEX: return sf_launch_hex_f64(P, affine, tile, a, s);
+        case HP_PRISM: return sf_launch_prism_f64(P, affine, tile, a, s);
+        case HP_PYR: return sf_launch_pyr_f64(P, affine, tile, a, s);
+        default: return sf_launch_tet_f64(P, affine, tile, a, s);
     }
 }
-cudaError_t sf_launch_f32(int shape, int P, bool affine, const SFArgs<float>& a, cudaStream_t s) {
+cudaError_t sf_launch_f32(int shape, int P, bool affine, int tile, const SFArgs<float>& a, cudaStream_t s) {
     switch (shape) {
-        case HP_HEX: return sf_launch_hex_f32(P, affine, a, s);
-        case HP_PRISM: return sf_launch_prism_f32(P, affine, a, s);
-        case HP_PYR: return sf_launch_pyr_f32(P, affine, a, s);
-        default: return sf_launch_tet_f32(P, affine, a, s);
+        case HP_HEX: return sf_launch_hex_f32(P, affine, tile, a, s);
+        case HP_PRISM: return sf_launch_prism_f32(P, affine, tile, a, s);
+        case HP_PYR: return sf_launch_pyr_f32(P, affine, tile, a, s);
+        default: return sf_launch_tet_f32(P, affine, tile, a, s);
     }
 }
 }  // namespace hp

@@ -1,7 +1,6 @@
 // Geometric factors in FP64 (paper Sec. 2.1: chain rule grad_x = J^{-T}
-// grad_xi; Sec. 2.3: grad_xi = T grad_eta on collapsed coordinates; the
-// "six geometric factors as well as the Jacobian" loaded per point for
-// deformed elements, Sec. 4).
+// grad_xi; Sec. 2.3: grad_xi = T grad_eta on collapsed coordinates; Sec. 4:
+// deformed elements load six metric terms and the Jacobian at every point).
 //
 // Curved element, per quadrature point l (eta_l, xi_l = xi(eta_l)):
 //   y = X0 + E (xi + 1)/2, J = D Phi(y) E/2,  d xi / d x = J^{-1},

@@ -80,6 +80,13 @@ struct hp_op_s {
     hp_strategy strategy;
     hp_dtype dtype;
     unsigned int* d_err = nullptr;
+    std::vector<int> tile;                      // tile variant per block
+    // CUDA graph of one apply (blocks as independent nodes), for fixed (lambda, in, out)
+    cudaGraphExec_t graph = nullptr;
+    const void* g_in = nullptr;
+    void* g_out = nullptr;
+    double g_lambda = 0.0;
+    std::vector<cudaStream_t> pool;             // fork streams used while capturing
 };
 
 namespace hp {
@@ -116,7 +123,9 @@ struct SFArgs {
 };
 
 // per-shape launchers (hp_sf_<shape>.cu)
-cudaError_t sf_launch_f64(int shape, int P, bool affine, const SFArgs<double>& a, cudaStream_t s);
-cudaError_t sf_launch_f32(int shape, int P, bool affine, const SFArgs<float>& a, cudaStream_t s);
+cudaError_t sf_launch_f64(int shape, int P, bool affine, int tile, const SFArgs<double>& a, cudaStream_t s);
+cudaError_t sf_launch_f32(int shape, int P, bool affine, int tile, const SFArgs<float>& a, cudaStream_t s);
+int sf_epb_host(int P, int tile, bool f64);
+constexpr int kTiles = 3;
 
 }  // namespace hp

@@ -29,24 +29,30 @@
 
 namespace hp {
 
-template <int P, typename T>
+// Tile variants (chosen per block by the autotuner): the shared-memory budget
+// for the element group, hence elements per CTA (EPB) and CTAs per SM.
+constexpr int kTileBudget[3] = {56 * 1024, 20 * 1024, 110 * 1024};
+constexpr int kNumTiles = 3;
+
+template <int P, typename T, int TILE = 0>
 struct SFCfg {
     static constexpr int n = P + 1, Q = P + 2, QQ = Q * Q, NQ = Q * Q * Q, N3 = n * n * n;
     static constexpr int NT = 256;
     static constexpr int per_elem_bytes = 5 * NQ * (int)sizeof(T);
-    static constexpr int budget = 56 * 1024;
+    static constexpr int budget = kTileBudget[TILE];
     static constexpr int epb0 = budget / per_elem_bytes;
     static constexpr int EPB = epb0 < 1 ? 1 : (epb0 > 64 ? 64 : epb0);
 };
 
-template <int SHAPE, int P, typename T>
+template <int SHAPE, int P, typename T, int TILE>
 __host__ __device__ constexpr int sf_smem_bytes() {
-    return 16 + blob_layout_c(SHAPE, P, (int)sizeof(T)).total_bytes + SFCfg<P, T>::EPB * 5 * SFCfg<P, T>::NQ * (int)sizeof(T);
+    return 16 + blob_layout_c(SHAPE, P, (int)sizeof(T)).total_bytes +
+           SFCfg<P, T, TILE>::EPB * 5 * SFCfg<P, T, TILE>::NQ * (int)sizeof(T);
 }
 
-template <int SHAPE, int P, typename T, bool AFFINE>
+template <int SHAPE, int P, typename T, bool AFFINE, int TILE>
 __global__ void __launch_bounds__(256) sf_kernel(const SFArgs<T> args) {
-    using C = SFCfg<P, T>;
+    using C = SFCfg<P, T, TILE>;
     constexpr int n = C::n, Q = C::Q, QQ = C::QQ, NQ = C::NQ, N3 = C::N3, EPB = C::EPB, NT = C::NT;
     constexpr BlobLayout L = blob_layout_c(SHAPE, P, (int)sizeof(T));
     constexpr int NP = n_modes_c(SHAPE, P);
@@ -321,33 +327,55 @@ __global__ void __launch_bounds__(256) sf_kernel(const SFArgs<T> args) {
     }
 }
 
-template <int SHAPE, int P, typename T, bool AFFINE>
+template <int SHAPE, int P, typename T, bool AFFINE, int TILE>
 cudaError_t sf_launch_one(const SFArgs<T>& a, cudaStream_t s) {
-    constexpr int smem = sf_smem_bytes<SHAPE, P, T>();
+    using C = SFCfg<P, T, TILE>;
+    constexpr int smem = sf_smem_bytes<SHAPE, P, T, TILE>();
     static int grid_cap = 0;
-    auto kern = sf_kernel<SHAPE, P, T, AFFINE>;
+    auto kern = sf_kernel<SHAPE, P, T, AFFINE, TILE>;
     if (grid_cap == 0) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         int dev = 0, sms = 0, per = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, SFCfg<P, T>::NT, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, C::NT, smem);
         if (e != cudaSuccess) return e;
         grid_cap = sms * (per > 0 ? per : 1);
     }
-    int64_t groups = (a.n_elem + SFCfg<P, T>::EPB - 1) / SFCfg<P, T>::EPB;
+    int64_t groups = (a.n_elem + C::EPB - 1) / C::EPB;
     int grid = (int)(groups < grid_cap ? groups : grid_cap);
     if (grid <= 0) return cudaSuccess;
-    kern<<<grid, SFCfg<P, T>::NT, smem, s>>>(a);
+    kern<<<grid, C::NT, smem, s>>>(a);
     return cudaGetLastError();
 }
 
+template <int SHAPE, int P, typename T, bool AFFINE>
+cudaError_t sf_launch_tile(int tile, const SFArgs<T>& a, cudaStream_t s) {
+    switch (tile) {
+        case 1: return sf_launch_one<SHAPE, P, T, AFFINE, 1>(a, s);
+        case 2: return sf_launch_one<SHAPE, P, T, AFFINE, 2>(a, s);
+        default: return sf_launch_one<SHAPE, P, T, AFFINE, 0>(a, s);
+    }
+}
+
+// elements per CTA of a tile variant (host side, for the autotuner)
+template <typename T>
+int sf_epb(int P, int tile) {
+#define HP_EPB(PP) \
+    case PP: return tile == 1 ? SFCfg<PP, T, 1>::EPB : tile == 2 ? SFCfg<PP, T, 2>::EPB : SFCfg<PP, T, 0>::EPB;
+    switch (P) {
+        HP_EPB(1) HP_EPB(2) HP_EPB(3) HP_EPB(4) HP_EPB(5) HP_EPB(6) HP_EPB(7) HP_EPB(8) HP_EPB(9) HP_EPB(10)
+        default: return 1;
+    }
+#undef HP_EPB
+}
+
 template <int SHAPE, typename T>
-cudaError_t sf_dispatch(int P, bool affine, const SFArgs<T>& a, cudaStream_t s) {
-#define HP_CASE(PP)                                                               \
-    case PP:                                                                      \
-        return affine ? sf_launch_one<SHAPE, PP, T, true>(a, s) : sf_launch_one<SHAPE, PP, T, false>(a, s);
+cudaError_t sf_dispatch(int P, bool affine, int tile, const SFArgs<T>& a, cudaStream_t s) {
+#define HP_CASE(PP)                                                                             \
+    case PP:                                                                                    \
+        return affine ? sf_launch_tile<SHAPE, PP, T, true>(tile, a, s) : sf_launch_tile<SHAPE, PP, T, false>(tile, a, s);
     switch (P) {
         HP_CASE(1) HP_CASE(2) HP_CASE(3) HP_CASE(4) HP_CASE(5)
         HP_CASE(6) HP_CASE(7) HP_CASE(8) HP_CASE(9) HP_CASE(10)

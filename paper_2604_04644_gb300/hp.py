@@ -29,8 +29,8 @@ HP_STRAT_SUMFAC, HP_STRAT_ELEMAT, HP_STRAT_HYBRID, HP_STRAT_AUTO = range(4)
 HP_FP64, HP_FP32, HP_TF32, HP_BF16 = range(4)
 
 EXPORTED = ["hp_mesh_create", "hp_mesh_layout", "hp_geom_factors", "hp_geom_copy", "hp_op_create",
-            "hp_op_apply", "hp_op_sync", "hp_op_work", "hp_op_destroy", "hp_mesh_destroy",
-            "hp_status_str", "hp_last_error"]
+            "hp_op_apply", "hp_op_apply_graph", "hp_op_tune", "hp_op_tiles", "hp_op_sync", "hp_op_work",
+            "hp_op_destroy", "hp_mesh_destroy", "hp_status_str", "hp_last_error"]
 
 
 class HpError(RuntimeError):
@@ -53,6 +53,9 @@ _lib.hp_geom_factors.argtypes = [_vp, _vp]
 _lib.hp_geom_copy.argtypes = [_vp, _vp, _vp]
 _lib.hp_op_create.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_vp)]
 _lib.hp_op_apply.argtypes = [_vp, ctypes.c_double, _vp, _vp, _vp]
+_lib.hp_op_apply_graph.argtypes = [_vp, ctypes.c_double, _vp, _vp, _vp]
+_lib.hp_op_tune.argtypes = [_vp, ctypes.c_double, _vp, _vp, _vp]
+_lib.hp_op_tiles.argtypes = [_vp, _vp, ctypes.c_int64, ctypes.c_int]
 _lib.hp_op_sync.argtypes = [_vp, _vp]
 _lib.hp_op_work.argtypes = [_vp, _i64p, _dp, _dp]
 _lib.hp_op_destroy.argtypes = [_vp]
@@ -61,7 +64,7 @@ _lib.hp_status_str.argtypes = [ctypes.c_int]
 _lib.hp_status_str.restype = ctypes.c_char_p
 _lib.hp_last_error.restype = ctypes.c_char_p
 for _f in ("hp_mesh_create", "hp_mesh_layout", "hp_geom_factors", "hp_geom_copy", "hp_op_create",
-           "hp_op_apply", "hp_op_sync", "hp_op_work"):
+           "hp_op_apply", "hp_op_apply_graph", "hp_op_tune", "hp_op_tiles", "hp_op_sync", "hp_op_work"):
     getattr(_lib, _f).restype = ctypes.c_int
 
 
@@ -137,6 +140,21 @@ def hp_op_create(mesh, kind, strategy=HP_STRAT_SUMFAC, dtype=HP_FP64):
 
 def hp_op_apply(op, lam, x, y, stream=None):
     _check(_lib.hp_op_apply(op, float(lam), _ptr(x), _ptr(y), _stream(stream)), "hp_op_apply")
+
+
+def hp_op_apply_graph(op, lam, x, y, stream=None):
+    _check(_lib.hp_op_apply_graph(op, float(lam), _ptr(x), _ptr(y), _stream(stream)), "hp_op_apply_graph")
+
+
+def hp_op_tune(op, lam, x, y, stream=None):
+    _check(_lib.hp_op_tune(op, float(lam), _ptr(x), _ptr(y), _stream(stream)), "hp_op_tune")
+
+
+def hp_op_tiles(op, n_blocks, tiles=None):
+    """Return the per-block tile variants, or set them when ``tiles`` is given."""
+    arr = np.zeros(n_blocks, dtype=np.int32) if tiles is None else np.ascontiguousarray(tiles, dtype=np.int32)
+    _check(_lib.hp_op_tiles(op, arr.ctypes.data, int(n_blocks), 0 if tiles is None else 1), "hp_op_tiles")
+    return arr
 
 
 def hp_op_sync(op, stream=None):
