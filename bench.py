@@ -254,6 +254,50 @@ def shape_order_table(dtype_name, device, reps=5):
     return out
 
 
+def strategy_table(device, orders=(1, 2, 4, 6, 8), reps=3):
+    """GDOF/s per shape and order of the three strategies (sum-factorised
+    collocated, elemental matrix, hybrid) for the mass and Helmholtz operators
+    in FP64, on single-shape 16x16x4-cell curved slabs (the paper's strategy
+    comparison per shape/order, Sec. 4)."""
+    import torch
+    from paper_2604_04644_gb300 import hp, inputs
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda:%d" % device)
+    stream = torch.cuda.current_stream(device)
+    names = ("hex", "prism", "pyr", "tet")
+    out = {}
+    for s in range(4):
+        for P in orders:
+            mesh = inputs.slab_mesh(CELLS, CELLS, 4, P, curved=True, slabs=(s,) * 4)
+            h = hp.hp_mesh_create(mesh, device)
+            co, po, nc, nph = hp.hp_mesh_layout(h, mesh["n_elem"])
+            x = torch.tensor(inputs.random_coefficients(1002, co), device="cuda:%d" % device)
+            y = torch.zeros(nc, device="cuda:%d" % device, dtype=torch.float64)
+            row = {}
+            for opname, kind in (("mass", hp.HP_MASS), ("helmholtz", hp.HP_HELMHOLTZ)):
+                for sname, strat in (("sumfac", hp.HP_STRAT_SUMFAC), ("elemat", hp.HP_STRAT_ELEMAT),
+                                     ("hybrid", hp.HP_STRAT_HYBRID)):
+                    op = hp.hp_op_create(h, kind, strat, hp.HP_FP64)
+                    dofs, flops, _ = hp.hp_op_work(op)
+                    ts = []
+                    for r in range(reps + 1):
+                        flush.zero_()
+                        a = torch.cuda.Event(enable_timing=True)
+                        b = torch.cuda.Event(enable_timing=True)
+                        a.record(stream)
+                        hp.hp_op_apply(op, 1.0, x, y, stream)
+                        b.record(stream)
+                        b.synchronize()
+                        if r:
+                            ts.append(a.elapsed_time(b))
+                    hp.hp_op_sync(op, stream)
+                    hp.hp_op_destroy(op)
+                    t = statistics.median(ts) * 1e-3
+                    row["%s_%s" % (opname, sname)] = round(dofs / t / 1e9, 4)
+            out["%s_P%d" % (names[s], P)] = row
+            hp.hp_mesh_destroy(h)
+    return out
+
+
 def padaptive(device, reps=10):
     """p-adaptive batched apply: 40x40x32 cells of the four-slab mesh (192 000
     elements), P ~ U{2..8} per element (seed 3), affine for x < 0.5 and curved
@@ -411,8 +455,10 @@ def main():
     if rank == 0 and not args.no_table:
         table = shape_order_table(args.dtype, local)
     batched = None
+    strategies = None
     if rank == 0 and not args.no_extra:
         batched = padaptive(local)
+        strategies = strategy_table(local)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline()
@@ -427,7 +473,7 @@ def main():
                            "l2": "flushed (256 MiB write) before every apply, outside the timed events"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                 "clocks": clk.summary(), "per_order": per_order, "per_shape_order": table,
-                "p_adaptive": batched}
+                "p_adaptive": batched, "strategies_gdofs_f64": strategies}
         print(json.dumps(line), flush=True)
     for w in work:
         from paper_2604_04644_gb300 import hp

@@ -165,6 +165,42 @@ bool coeff_in(hp_opkind k) { return k == HP_MASS || k == HP_LAPLACIAN || k == HP
 bool coeff_out(hp_opkind k) { return k != HP_BWDTRANS && k != HP_PHYSDERIV; }
 bool needs_deriv_geom(hp_opkind k) { return k == HP_PHYSDERIV || k == HP_IPRODUCT_WRT_DERIV_BASE; }
 
+hp_status ensure_dense(hp_mesh m) {
+    for (auto& kv : m->blobs) {
+        DeviceBlobs& db = kv.second;
+        if (db.A4_64) continue;
+        int shape = kv.first / 16, P = kv.first % 16;
+        const int NQ = (P + 2) * (P + 2) * (P + 2), NP = n_modes(shape, P);
+        std::vector<double> A = dense_matrices(shape, P);
+        std::vector<double> AT(A.size());
+        for (int q = 0; q < 4; ++q)
+            for (int l = 0; l < NQ; ++l)
+                for (int mm = 0; mm < NP; ++mm) AT[((size_t)mm * 4 + q) * NQ + l] = A[((size_t)q * NQ + l) * NP + mm];
+        std::vector<float> A32(A.begin(), A.end()), AT32(AT.begin(), AT.end());
+        hp_status st;
+        if ((st = upload(&db.A4_64, A.data(), A.size()))) return st;
+        if ((st = upload(&db.A4T_64, AT.data(), AT.size()))) return st;
+        if ((st = upload(&db.A4_32, A32.data(), A32.size()))) return st;
+        if ((st = upload(&db.A4T_32, AT32.data(), AT32.size()))) return st;
+    }
+    return HP_OK;
+}
+
+// flops of the elemental-matrix (hybrid = false) or hybrid strategy per element
+double elem_flops_dense(int shape, int P, hp_opkind k, bool hybrid) {
+    const int Q = P + 2;
+    const double NQ = (double)Q * Q * Q, NP = n_modes(shape, P);
+    const double deriv = 3.0 * 2.0 * Q * NQ;
+    const double mv = 2.0 * NQ * NP;
+    switch (k) {
+        case HP_BWDTRANS: return mv;
+        case HP_IPRODUCT_WRT_BASE: return mv + NQ;
+        case HP_MASS: return 2 * mv + NQ;
+        case HP_LAPLACIAN: return hybrid ? 2 * mv + 2 * deriv + 15 * NQ : 8 * mv + 15 * NQ;
+        default: return hybrid ? 2 * mv + 2 * deriv + 18 * NQ : 8 * mv + 18 * NQ;
+    }
+}
+
 // flops of the sum-factorised collocated algorithm per element (FMA = 2)
 double elem_flops(int shape, int P, hp_opkind k) {
     const RefTables& t = ref_tables(shape, P);
@@ -195,6 +231,27 @@ cudaError_t launch_block(hp_op op, size_t bi, int tile, double lambda, const voi
     const Block& b = m->blocks[bi];
     const DeviceBlobs& blob = m->blobs.at(b.shape * 16 + b.P);
     const int64_t nphys = m->phys_off.back();
+    if (op->strat[bi] != HP_STRAT_SUMFAC) {
+        const bool hybrid = op->strat[bi] == HP_STRAT_HYBRID;
+        if (op->dtype == HP_FP64) {
+            EMArgs<double> a{};
+            a.op = op->kind; a.shape = b.shape; a.P = b.P; a.Q = b.Q; a.NQ = b.Q * b.Q * b.Q;
+            a.NP = n_modes(b.shape, b.P); a.NQp = nqp(b.Q); a.n_elem = b.n_elem; a.lambda = lambda;
+            a.coeff_off = b.d_coeff_off; a.phys_off = b.d_phys_off;
+            a.in = static_cast<const double*>(in); a.out = static_cast<double*>(out);
+            a.geom = b.d_geom; a.A4 = blob.A4_64; a.A4T = blob.A4T_64;
+            a.blob = static_cast<const unsigned char*>(blob.d64); a.err = op->d_err;
+            return emat_launch_f64(hybrid, !b.curved, a, s);
+        }
+        EMArgs<float> a{};
+        a.op = op->kind; a.shape = b.shape; a.P = b.P; a.Q = b.Q; a.NQ = b.Q * b.Q * b.Q;
+        a.NP = n_modes(b.shape, b.P); a.NQp = nqp(b.Q); a.n_elem = b.n_elem; a.lambda = (float)lambda;
+        a.coeff_off = b.d_coeff_off; a.phys_off = b.d_phys_off;
+        a.in = static_cast<const float*>(in); a.out = static_cast<float*>(out);
+        a.geom = b.d_geom32; a.A4 = blob.A4_32; a.A4T = blob.A4T_32;
+        a.blob = static_cast<const unsigned char*>(blob.d32); a.err = op->d_err;
+        return emat_launch_f32(hybrid, !b.curved, a, s);
+    }
     if (op->dtype == HP_FP64) {
         SFArgs<double> a{};
         a.op = op->kind;
@@ -477,19 +534,25 @@ hp_status hp_op_create(hp_mesh m, hp_opkind kind, hp_strategy strategy, hp_dtype
     if ((int)strategy < 0 || strategy > HP_STRAT_AUTO) { set_error("hp_op_create: bad strategy"); return HP_ERR_ARG; }
     if ((int)dtype < 0 || dtype > HP_BF16) { set_error("hp_op_create: bad dtype"); return HP_ERR_ARG; }
     if (strategy == HP_STRAT_AUTO) strategy = HP_STRAT_SUMFAC;
-    if (strategy != HP_STRAT_SUMFAC || (dtype != HP_FP64 && dtype != HP_FP32)) {
+    if (dtype != HP_FP64 && dtype != HP_FP32) {
         set_error("hp_op_create: this strategy/dtype combination is not built");
+        return HP_ERR_UNSUPPORTED;
+    }
+    if (strategy != HP_STRAT_SUMFAC && (kind == HP_PHYSDERIV || kind == HP_IPRODUCT_WRT_DERIV_BASE)) {
+        set_error("hp_op_create: derivative building blocks exist only with HP_STRAT_SUMFAC");
         return HP_ERR_UNSUPPORTED;
     }
     DeviceGuard guard(m->device);
     hp_status st = ensure_geom(m, needs_deriv_geom(kind), dtype == HP_FP32, 0);
     if (st) return st;
+    if (strategy != HP_STRAT_SUMFAC && (st = ensure_dense(m))) return st;
     auto op = new hp_op_s();
     op->mesh = m;
     op->kind = kind;
     op->strategy = strategy;
     op->dtype = dtype;
     op->tile.assign(m->blocks.size(), 0);
+    op->strat.assign(m->blocks.size(), (int)strategy);
     st = upload<unsigned int>(&op->d_err, nullptr, 1);
     if (!st) cudaMemset(op->d_err, 0, sizeof(unsigned int));
     if (st) { delete op; return st; }
@@ -519,6 +582,7 @@ hp_status hp_op_tune(hp_op op, double lambda, const void* in, void* out, void* s
     const bool f64 = op->dtype == HP_FP64;
     for (size_t i = 0; i < op->mesh->blocks.size(); ++i) {
         const Block& blk = op->mesh->blocks[i];
+        if (op->strat[i] != HP_STRAT_SUMFAC) continue;
         float best = 1e30f;
         int best_t = 0;
         std::vector<int> seen;
@@ -635,7 +699,10 @@ hp_status hp_op_work(hp_op op, int64_t* out_dofs, double* flops, double* bytes) 
         const double NQ = (double)b.Q * b.Q * b.Q;
         const double np = (double)n_modes(b.shape, b.P);
         const double ne = (double)b.n_elem;
-        fl += ne * elem_flops(b.shape, b.P, op->kind);
+        size_t bi = &b - &m->blocks[0];
+        const int st = op->strat[bi];
+        fl += ne * (st == HP_STRAT_SUMFAC ? elem_flops(b.shape, b.P, op->kind)
+                                          : elem_flops_dense(b.shape, b.P, op->kind, st == HP_STRAT_HYBRID));
         double in_v = coeff_in(op->kind) ? np : (op->kind == HP_IPRODUCT_WRT_DERIV_BASE ? 3 * NQ : NQ);
         double out_v = coeff_out(op->kind) ? np : (op->kind == HP_PHYSDERIV ? 3 * NQ : NQ);
         dofs += (int64_t)(ne * (coeff_out(op->kind) ? np : out_v));
@@ -674,6 +741,10 @@ void hp_mesh_destroy(hp_mesh m) {
         for (auto& kv : m->blobs) {
             cudaFree(kv.second.d64);
             cudaFree(kv.second.d32);
+            cudaFree(kv.second.A4_64);
+            cudaFree(kv.second.A4T_64);
+            cudaFree(kv.second.A4_32);
+            cudaFree(kv.second.A4T_32);
         }
         cudaFree(m->d_err);
     }

@@ -36,6 +36,9 @@ struct RefTables {
 const RefTables& ref_tables(int shape, int P);
 int n_modes(int shape, int P);
 
+// Dense reference matrices A4[q][l][m] (q = 0: B, q = 1..3: d/d eta_q of B), FP64.
+std::vector<double> dense_matrices(int shape, int P);
+
 // Serialise the tables in value type T (double or float) into bytes.
 std::vector<unsigned char> make_blob(const RefTables& t, size_t value_size);
 
@@ -58,6 +61,12 @@ struct DeviceBlobs {
     void* d64 = nullptr;
     void* d32 = nullptr;
     int bytes64 = 0, bytes32 = 0;
+    // dense reference matrices (created for elemental-matrix / hybrid operators):
+    // A4 [4][NQ][NP] and A4T [NP][4][NQ], in FP64 and FP32
+    double* A4_64 = nullptr;
+    double* A4T_64 = nullptr;
+    float* A4_32 = nullptr;
+    float* A4T_32 = nullptr;
 };
 
 }  // namespace hp
@@ -81,6 +90,7 @@ struct hp_op_s {
     hp_dtype dtype;
     unsigned int* d_err = nullptr;
     std::vector<int> tile;                      // tile variant per block
+    std::vector<int> strat;                     // hp_strategy per block (SUMFAC, ELEMAT, HYBRID)
     // CUDA graph of one apply (blocks as independent nodes), for fixed (lambda, in, out)
     cudaGraphExec_t graph = nullptr;
     const void* g_in = nullptr;
@@ -121,6 +131,25 @@ struct SFArgs {
     int blob_bytes;
     unsigned int* err;
 };
+
+// arguments of the elemental-matrix / hybrid kernels (hp_emat.cu)
+template <typename T>
+struct EMArgs {
+    int op, shape, P, Q, NQ, NP, NQp;
+    int64_t n_elem;
+    T lambda;
+    const int64_t* coeff_off;
+    const int64_t* phys_off;
+    const T* in;
+    T* out;
+    const T* geom;               // as SFArgs
+    const T* A4;                 // [4][NQ][NP]
+    const T* A4T;                // [NP][4][NQ]
+    const unsigned char* blob;   // table blob (for D, z, w)
+    unsigned int* err;
+};
+cudaError_t emat_launch_f64(bool hybrid, bool affine, const EMArgs<double>& a, cudaStream_t s);
+cudaError_t emat_launch_f32(bool hybrid, bool affine, const EMArgs<float>& a, cudaStream_t s);
 
 // per-shape launchers (hp_sf_<shape>.cu)
 cudaError_t sf_launch_f64(int shape, int P, bool affine, int tile, const SFArgs<double>& a, cudaStream_t s);

@@ -258,6 +258,43 @@ const RefTables& ref_tables(int shape, int P) {
     return it->second;
 }
 
+std::vector<double> dense_matrices(int shape, int P) {
+    // A4[q][l][m], q = 0: B = phi_m at point l; q = d + 1: d phi_m / d eta_d at l,
+    // obtained as D_d B (exact: each phi_m lies in the Lagrange span of the points)
+    const RefTables& t = ref_tables(shape, P);
+    const int n = t.n, Q = t.Q, NQ = t.NQ, NP = t.NP;
+    std::vector<double> A(4 * (size_t)NQ * NP, 0.0);
+    for (int m = 0; m < NP; ++m) {
+        for (int q = 0; q < 4; ++q) {
+            int sl = t.mode_slots[m * 4 + q];
+            if (sl < 0) continue;
+            int a = sl / (n * n), b = (sl / n) % n, c = sl % n;
+            int tb = t.famb[a], sc = t.famc[a * n + b];
+            for (int i = 0; i < Q; ++i)
+                for (int j = 0; j < Q; ++j)
+                    for (int k = 0; k < Q; ++k)
+                        A[((size_t)((i * Q + j) * Q + k)) * NP + m] +=
+                            t.Ta[a * Q + i] * t.Tb[(tb * n + b) * Q + j] * t.Tc[(sc * n + c) * Q + k];
+        }
+    }
+    for (int d = 0; d < 3; ++d) {
+        const std::vector<double>& D = t.D[d];
+        for (int i = 0; i < Q; ++i)
+            for (int j = 0; j < Q; ++j)
+                for (int k = 0; k < Q; ++k) {
+                    int l = (i * Q + j) * Q + k;
+                    for (int mm = 0; mm < Q; ++mm) {
+                        int src = d == 0 ? (mm * Q + j) * Q + k : d == 1 ? (i * Q + mm) * Q + k : (i * Q + j) * Q + mm;
+                        double dv = D[(d == 0 ? i : d == 1 ? j : k) * Q + mm];
+                        const double* from = &A[(size_t)src * NP];
+                        double* to = &A[((size_t)(d + 1) * NQ + l) * NP];
+                        for (int m = 0; m < NP; ++m) to[m] += dv * from[m];
+                    }
+                }
+    }
+    return A;
+}
+
 std::vector<unsigned char> make_blob(const RefTables& t, size_t vs) {
     BlobLayout L = blob_layout_c(t.shape, t.P, (int)vs);
     std::vector<unsigned char> out(L.total_bytes, 0);
