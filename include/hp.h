@@ -179,6 +179,54 @@ hp_status hp_op_tune(hp_op op, double lambda, const void* in, void* out, void* s
  * user element order).  HP_ERR_ARG if n_blocks does not match or a tile is out of range. */
 hp_status hp_op_tiles(hp_op op, int* tiles, int64_t n_blocks, int set);
 
+/* Read (set = 0) or write (set = 1) the implementation strategy of each block
+ * (HP_STRAT_SUMFAC, HP_STRAT_ELEMAT or HP_STRAT_HYBRID).  Writing builds the
+ * dense reference matrices if a block needs them.  HP_ERR_UNSUPPORTED for a
+ * dense strategy on a derivative building block. */
+hp_status hp_op_strategies(hp_op op, int* strategies, int64_t n_blocks, int set);
+
+/* ---------------------------------------------------------------- cost model
+ * Not in the paper (which picks a strategy by a fixed rule per operator):
+ * a small MLP, trained by the library's own kernels on timings the library
+ * generates, predicts the log run time of each strategy of a block. */
+typedef struct hp_mlp_s* hp_mlp;
+
+/* Features of each block of an op, 5 floats per block:
+ * shape/3, P/10, curved (0/1), log10(elements)/6, dtype/2 (FP64 = 0). */
+hp_status hp_op_block_features(hp_op op, float* features, int64_t n_blocks);
+
+/* MLP n_in -> n_hidden -> n_hidden -> n_out with ReLU, FP32 parameters on
+ * `device`, He-uniform weights drawn from SplitMix64(seed), zero biases.
+ * Limits: n_in 1..16, n_hidden 32..256 (multiple of 32), n_out 1..8. */
+hp_status hp_mlp_create(int n_in, int n_hidden, int n_out, uint64_t seed, int device, hp_mlp* out);
+/* Sizes of a network (any pointer may be NULL). */
+hp_status hp_mlp_info(hp_mlp mlp, int* n_in, int* n_hidden, int* n_out, int64_t* n_params);
+/* Copy the flat parameter vector (W1[H][n_in], b1[H], W2[H][H], b2[H],
+ * W3[n_out][H], b3[n_out]) to (set = 0) or from (set = 1, resets Adam) host memory. */
+hp_status hp_mlp_params(hp_mlp mlp, float* host, int64_t n_params, int set);
+/* y[batch][n_out] = MLP(x[batch][n_in]); device arrays, 1 <= batch <= 65535. */
+hp_status hp_mlp_forward(hp_mlp mlp, const float* x, int64_t batch, float* y, void* stream);
+/* Gradient of L = mean over batch and outputs of (y - t)^2 w.r.t. the flat
+ * parameters into grad[n_params] (device), and L into loss[1] (device, may be NULL).
+ * Deterministic: per-sample rows summed in sample order. */
+hp_status hp_mlp_grad(hp_mlp mlp, const float* x, const float* t, int64_t batch, float* grad, float* loss,
+                      void* stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on that loss. */
+hp_status hp_mlp_adam_step(hp_mlp mlp, const float* x, const float* t, int64_t batch, float lr, float* loss,
+                           void* stream);
+void hp_mlp_destroy(hp_mlp mlp);
+
+/* Pick each block's strategy as the argmin of the network's 3 outputs (the
+ * predicted log times of SUMFAC, ELEMAT, HYBRID) on the block's features.
+ * Derivative building blocks stay SUMFAC. */
+hp_status hp_op_schedule(hp_op op, hp_mlp mlp, void* stream);
+
+/* Exhaustive schedule: time every strategy of every block on the given arrays
+ * (contents overwritten) and keep the fastest; times_ms[3*block + strategy]
+ * (may be NULL) receives the timings (1e30 for strategies not available). */
+hp_status hp_op_schedule_exhaustive(hp_op op, double lambda, const void* in, void* out, float* times_ms,
+                                    void* stream);
+
 /* Synchronise `stream` and report any error latched by the op's kernels
  * (HP_ERR_TIMEOUT, HP_ERR_DEVICE_BOUNDS) or by CUDA. */
 hp_status hp_op_sync(hp_op op, void* stream);

@@ -681,6 +681,129 @@ hp_status hp_op_apply_graph(hp_op op, double lambda, const void* in, void* out, 
     return HP_OK;
 }
 
+hp_status hp_op_strategies(hp_op op, int* strat, int64_t n_blocks, int set) {
+    if (!op || !strat || n_blocks != (int64_t)op->strat.size()) { set_error("hp_op_strategies: bad argument"); return HP_ERR_ARG; }
+    DeviceGuard guard(op->mesh->device);
+    if (!set) {
+        for (int64_t i = 0; i < n_blocks; ++i) strat[i] = op->strat[i];
+        return HP_OK;
+    }
+    bool dense = false;
+    for (int64_t i = 0; i < n_blocks; ++i) {
+        if (strat[i] < HP_STRAT_SUMFAC || strat[i] > HP_STRAT_HYBRID) { set_error("hp_op_strategies: bad strategy"); return HP_ERR_ARG; }
+        if (strat[i] != HP_STRAT_SUMFAC && needs_deriv_geom(op->kind)) {
+            set_error("hp_op_strategies: derivative building blocks exist only with HP_STRAT_SUMFAC");
+            return HP_ERR_UNSUPPORTED;
+        }
+        dense |= strat[i] != HP_STRAT_SUMFAC;
+    }
+    if (dense) {
+        hp_status st = ensure_dense(op->mesh);
+        if (st) return st;
+    }
+    for (int64_t i = 0; i < n_blocks; ++i) op->strat[i] = strat[i];
+    if (op->graph) { cudaGraphExecDestroy(op->graph); op->graph = nullptr; }
+    return HP_OK;
+}
+
+hp_status hp_op_block_features(hp_op op, float* features, int64_t n_blocks) {
+    if (!op || !features || n_blocks != (int64_t)op->strat.size()) { set_error("hp_op_block_features: bad argument"); return HP_ERR_ARG; }
+    for (int64_t i = 0; i < n_blocks; ++i) {
+        const Block& b = op->mesh->blocks[i];
+        float* f = features + 5 * i;
+        f[0] = b.shape / 3.0f;
+        f[1] = b.P / 10.0f;
+        f[2] = b.curved ? 1.0f : 0.0f;
+        f[3] = (float)(std::log10((double)b.n_elem) / 6.0);
+        f[4] = (op->dtype == HP_FP64 ? 0 : op->dtype) / 2.0f;
+    }
+    return HP_OK;
+}
+
+hp_status hp_op_schedule(hp_op op, hp_mlp mlp, void* stream) {
+    if (!op || !mlp) { set_error("hp_op_schedule: null argument"); return HP_ERR_ARG; }
+    int n_in = 0, n_out = 0;
+    hp_mlp_info(mlp, &n_in, nullptr, &n_out, nullptr);
+    if (n_in != 5 || n_out != 3) { set_error("hp_op_schedule: the network must map 5 features to 3 log-times"); return HP_ERR_ARG; }
+    DeviceGuard guard(op->mesh->device);
+    const int64_t nb = (int64_t)op->strat.size();
+    std::vector<float> f(5 * nb), y(3 * nb);
+    hp_op_block_features(op, f.data(), nb);
+    float *dx = nullptr, *dy = nullptr;
+    hp_status st = upload(&dx, f.data(), f.size());
+    if (!st) st = upload<float>(&dy, nullptr, y.size());
+    if (!st) st = hp_mlp_forward(mlp, dx, nb, dy, stream);
+    if (!st) {
+        cudaError_t e = cudaMemcpyAsync(y.data(), dy, sizeof(float) * y.size(), cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+        if (e != cudaSuccess) st = cuda_fail(e, "hp_op_schedule");
+    }
+    cudaFree(dx);
+    cudaFree(dy);
+    if (st) return st;
+    std::vector<int> choice(nb);
+    for (int64_t i = 0; i < nb; ++i) {
+        int best = 0;
+        if (!needs_deriv_geom(op->kind))
+            for (int k = 1; k < 3; ++k)
+                if (y[3 * i + k] < y[3 * i + best]) best = k;
+        choice[i] = best;
+    }
+    return hp_op_strategies(op, choice.data(), nb, 1);
+}
+
+hp_status hp_op_schedule_exhaustive(hp_op op, double lambda, const void* in, void* out, float* times_ms,
+                                    void* stream) {
+    if (!op || !in || !out) { set_error("hp_op_schedule_exhaustive: null argument"); return HP_ERR_ARG; }
+    if (in == out) { set_error("hp_op_schedule_exhaustive: in and out must not alias"); return HP_ERR_ARG; }
+    DeviceGuard guard(op->mesh->device);
+    const int64_t nb = (int64_t)op->strat.size();
+    const int ns = needs_deriv_geom(op->kind) ? 1 : 3;
+    if (ns > 1) {
+        hp_status st = ensure_dense(op->mesh);
+        if (st) return st;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    std::vector<int> saved = op->strat;
+    std::vector<int> choice(nb, 0);
+    for (int64_t i = 0; i < nb; ++i) {
+        float best = 1e30f;
+        for (int k = 0; k < 3; ++k) {
+            float tot = 1e30f;
+            if (k < ns) {
+                op->strat[i] = k;
+                tot = 0.f;
+                for (int r = 0; r < 3; ++r) {
+                    cudaEventRecord(a, s);
+                    cudaError_t e = launch_block(op, i, op->tile[i], lambda, in, out, s);
+                    cudaEventRecord(b, s);
+                    if (e == cudaSuccess) e = cudaEventSynchronize(b);
+                    if (e != cudaSuccess) {
+                        op->strat = saved;
+                        cudaEventDestroy(a);
+                        cudaEventDestroy(b);
+                        return cuda_fail(e, "hp_op_schedule_exhaustive");
+                    }
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, a, b);
+                    if (r) tot += 0.5f * ms;
+                }
+                if (tot < best) { best = tot; choice[i] = k; }
+            }
+            if (times_ms) times_ms[3 * i + k] = tot;
+        }
+        op->strat[i] = saved[i];
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    hp_status st = check_device_error(op->mesh, op->d_err, nullptr, "hp_op_schedule_exhaustive");
+    if (st) return st;
+    return hp_op_strategies(op, choice.data(), nb, 1);
+}
+
 hp_status hp_op_sync(hp_op op, void* stream) {
     if (!op) { set_error("hp_op_sync: null op"); return HP_ERR_ARG; }
     DeviceGuard guard(op->mesh->device);
