@@ -40,6 +40,8 @@ def parse():
     p.add_argument("--dtype", default="f64", choices=["f64", "f32"])
     p.add_argument("--no-table", action="store_true", help="skip the per-shape/order table")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    p.add_argument("--costmodel", action="store_true",
+                   help="run the learned cost-model pipeline (timings, GPU training, held-out schedules) instead")
     p.add_argument("--no-extra", action="store_true", help="skip the p-adaptive batched measurement")
     p.add_argument("--orders", default=None, help="comma-separated orders (default 1..8); for profiling runs")
     p.add_argument("--cells", type=int, default=None, help="cells per direction (default 16); for profiling runs")
@@ -410,9 +412,44 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def run_costmodel(local):
+    """Learned strategy scheduling: timings over shape x P=1..10 x affine/curved x
+    10^2..10^5 elements x {FP64, FP32} (the library's own kernels), one MLP per
+    operator trained on the GPU by the library's kernels, evaluated on a held-out
+    16x16x32-cell mesh with P ~ U{3..9} and affine/curved halves."""
+    import torch
+    from paper_2604_04644_gb300 import costmodel, hp, inputs
+    torch.cuda.set_device(local)
+    held = inputs.slab_mesh(16, 16, 32, (3, 9), order_seed=4, curved_rule="x_half")
+    res = {}
+    for name, kind in (("helmholtz", hp.HP_HELMHOLTZ), ("mass", hp.HP_MASS)):
+        t0 = time.time()
+        X, T, meta = costmodel.generate_timings(local, kind)
+        t_gen = time.time() - t0
+        t0 = time.time()
+        mlp, hist = costmodel.train(X, T, local)
+        t_train = time.time() - t0
+        pred = costmodel.predict(mlp, X, local)
+        ev64 = costmodel.evaluate_schedules(mlp, held, kind, hp.HP_FP64, local)
+        ev32 = costmodel.evaluate_schedules(mlp, held, kind, hp.HP_FP32, local)
+        res[name] = {"samples": int(len(X)), "extrapolated_entries": int(sum(sum(m["extrapolated"]) for m in meta)),
+                     "timing_s": round(t_gen, 1), "train_s": round(t_train, 1),
+                     "train_loss_first_last": [hist[0][1], hist[-1][1]],
+                     "train_rmse_log10": float(np.sqrt(np.mean((pred - T) ** 2))),
+                     "train_argmin_accuracy": float(np.mean(pred.argmin(1) == T.argmin(1))),
+                     "held_out_f64": ev64, "held_out_f32": ev32}
+        hp.hp_mlp_destroy(mlp)
+    print(json.dumps({"costmodel": res, "held_out_mesh": {"cells": "16x16x32", "elements": int(held["n_elem"]),
+                                                          "orders": "U{3..9}", "curved": "x >= 0.5"}}), flush=True)
+
+
 def main():
     args = parse()
     world, rank, local = dist_init(args)
+    if args.costmodel:
+        if rank == 0:
+            run_costmodel(local)
+        return
     if args.impl == "reference":
         run_reference(args, world, rank)
         return

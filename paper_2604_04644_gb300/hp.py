@@ -29,8 +29,11 @@ HP_STRAT_SUMFAC, HP_STRAT_ELEMAT, HP_STRAT_HYBRID, HP_STRAT_AUTO = range(4)
 HP_FP64, HP_FP32, HP_TF32, HP_BF16 = range(4)
 
 EXPORTED = ["hp_mesh_create", "hp_mesh_layout", "hp_geom_factors", "hp_geom_copy", "hp_op_create",
-            "hp_op_apply", "hp_op_apply_graph", "hp_op_tune", "hp_op_tiles", "hp_op_sync", "hp_op_work",
-            "hp_op_destroy", "hp_mesh_destroy", "hp_status_str", "hp_last_error"]
+            "hp_op_apply", "hp_op_apply_graph", "hp_op_tune", "hp_op_tiles", "hp_op_strategies",
+            "hp_op_block_features", "hp_op_schedule", "hp_op_schedule_exhaustive", "hp_op_sync", "hp_op_work",
+            "hp_op_destroy", "hp_mesh_destroy", "hp_status_str", "hp_last_error",
+            "hp_mlp_create", "hp_mlp_info", "hp_mlp_params", "hp_mlp_forward", "hp_mlp_grad", "hp_mlp_adam_step",
+            "hp_mlp_destroy"]
 
 
 class HpError(RuntimeError):
@@ -56,6 +59,18 @@ _lib.hp_op_apply.argtypes = [_vp, ctypes.c_double, _vp, _vp, _vp]
 _lib.hp_op_apply_graph.argtypes = [_vp, ctypes.c_double, _vp, _vp, _vp]
 _lib.hp_op_tune.argtypes = [_vp, ctypes.c_double, _vp, _vp, _vp]
 _lib.hp_op_tiles.argtypes = [_vp, _vp, ctypes.c_int64, ctypes.c_int]
+_lib.hp_op_strategies.argtypes = [_vp, _vp, ctypes.c_int64, ctypes.c_int]
+_lib.hp_op_block_features.argtypes = [_vp, _vp, ctypes.c_int64]
+_lib.hp_op_schedule.argtypes = [_vp, _vp, _vp]
+_lib.hp_op_schedule_exhaustive.argtypes = [_vp, ctypes.c_double, _vp, _vp, _vp, _vp]
+_lib.hp_mlp_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_int,
+                               ctypes.POINTER(_vp)]
+_lib.hp_mlp_info.argtypes = [_vp, _vp, _vp, _vp, _vp]
+_lib.hp_mlp_params.argtypes = [_vp, _vp, ctypes.c_int64, ctypes.c_int]
+_lib.hp_mlp_forward.argtypes = [_vp, _vp, ctypes.c_int64, _vp, _vp]
+_lib.hp_mlp_grad.argtypes = [_vp, _vp, _vp, ctypes.c_int64, _vp, _vp, _vp]
+_lib.hp_mlp_adam_step.argtypes = [_vp, _vp, _vp, ctypes.c_int64, ctypes.c_float, _vp, _vp]
+_lib.hp_mlp_destroy.argtypes = [_vp]
 _lib.hp_op_sync.argtypes = [_vp, _vp]
 _lib.hp_op_work.argtypes = [_vp, _i64p, _dp, _dp]
 _lib.hp_op_destroy.argtypes = [_vp]
@@ -64,7 +79,9 @@ _lib.hp_status_str.argtypes = [ctypes.c_int]
 _lib.hp_status_str.restype = ctypes.c_char_p
 _lib.hp_last_error.restype = ctypes.c_char_p
 for _f in ("hp_mesh_create", "hp_mesh_layout", "hp_geom_factors", "hp_geom_copy", "hp_op_create",
-           "hp_op_apply", "hp_op_apply_graph", "hp_op_tune", "hp_op_tiles", "hp_op_sync", "hp_op_work"):
+           "hp_op_apply", "hp_op_apply_graph", "hp_op_tune", "hp_op_tiles", "hp_op_sync", "hp_op_work",
+           "hp_op_strategies", "hp_op_block_features", "hp_op_schedule", "hp_op_schedule_exhaustive",
+           "hp_mlp_create", "hp_mlp_info", "hp_mlp_params", "hp_mlp_forward", "hp_mlp_grad", "hp_mlp_adam_step"):
     getattr(_lib, _f).restype = ctypes.c_int
 
 
@@ -181,3 +198,67 @@ def hp_status_str(s):
 
 def hp_last_error():
     return _lib.hp_last_error().decode()
+
+
+def hp_op_strategies(op, n_blocks, strategies=None):
+    """Return the per-block strategies, or set them when ``strategies`` is given."""
+    arr = np.zeros(n_blocks, dtype=np.int32) if strategies is None else np.ascontiguousarray(strategies, np.int32)
+    _check(_lib.hp_op_strategies(op, arr.ctypes.data, int(n_blocks), 0 if strategies is None else 1),
+           "hp_op_strategies")
+    return arr
+
+
+def hp_op_block_features(op, n_blocks):
+    f = np.zeros((n_blocks, 5), dtype=np.float32)
+    _check(_lib.hp_op_block_features(op, f.ctypes.data, int(n_blocks)), "hp_op_block_features")
+    return f
+
+
+def hp_op_schedule(op, mlp, stream=None):
+    _check(_lib.hp_op_schedule(op, mlp, _stream(stream)), "hp_op_schedule")
+
+
+def hp_op_schedule_exhaustive(op, lam, x, y, n_blocks, stream=None):
+    t = np.zeros((n_blocks, 3), dtype=np.float32)
+    _check(_lib.hp_op_schedule_exhaustive(op, float(lam), _ptr(x), _ptr(y), t.ctypes.data, _stream(stream)),
+           "hp_op_schedule_exhaustive")
+    return t
+
+
+def hp_mlp_create(n_in, n_hidden, n_out, seed=0, device=0):
+    h = _vp()
+    _check(_lib.hp_mlp_create(int(n_in), int(n_hidden), int(n_out), int(seed), int(device), ctypes.byref(h)),
+           "hp_mlp_create")
+    return h.value
+
+
+def hp_mlp_info(mlp):
+    a, b, c, d = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int64()
+    _check(_lib.hp_mlp_info(mlp, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)), "hp_mlp_info")
+    return a.value, b.value, c.value, d.value
+
+
+def hp_mlp_params(mlp, params=None):
+    """Return the flat FP32 parameters, or set them when ``params`` is given."""
+    n = hp_mlp_info(mlp)[3]
+    arr = np.zeros(n, dtype=np.float32) if params is None else np.ascontiguousarray(params, dtype=np.float32)
+    _check(_lib.hp_mlp_params(mlp, arr.ctypes.data, int(n), 0 if params is None else 1), "hp_mlp_params")
+    return arr
+
+
+def hp_mlp_forward(mlp, x, batch, y, stream=None):
+    _check(_lib.hp_mlp_forward(mlp, _ptr(x), int(batch), _ptr(y), _stream(stream)), "hp_mlp_forward")
+
+
+def hp_mlp_grad(mlp, x, t, batch, grad, loss=None, stream=None):
+    _check(_lib.hp_mlp_grad(mlp, _ptr(x), _ptr(t), int(batch), _ptr(grad), _ptr(loss), _stream(stream)),
+           "hp_mlp_grad")
+
+
+def hp_mlp_adam_step(mlp, x, t, batch, lr, loss=None, stream=None):
+    _check(_lib.hp_mlp_adam_step(mlp, _ptr(x), _ptr(t), int(batch), float(lr), _ptr(loss), _stream(stream)),
+           "hp_mlp_adam_step")
+
+
+def hp_mlp_destroy(mlp):
+    _lib.hp_mlp_destroy(mlp)

@@ -186,6 +186,28 @@ def subset_mesh(mesh, elems):
     return out
 
 
+def replicated_mesh(shape, order, n_elem, *, curved=True, deformation=1):
+    """n_elem elements of one shape: copies of a one-cell slab's elements on a
+    cubic grid of cells inside [0,1]^3 (vertices not shared; element-local
+    operators only).  Fast for large n_elem (vectorised)."""
+    cell = slab_mesh(1, 1, 1, order, curved=curved, deformation=deformation, slabs=(shape,))
+    per = cell["n_elem"]
+    nv = N_VERTS[shape]
+    n_cells = -(-n_elem // per)
+    m = int(np.ceil(n_cells ** (1.0 / 3.0)))
+    h = 1.0 / m
+    c = np.arange(n_cells)
+    offs = np.stack([c % m, (c // m) % m, c // (m * m)], axis=1) * h            # (n_cells, 3)
+    tmpl = cell["xyz"][cell["vert"][:, :nv]] * h                                  # (per, nv, 3)
+    X = (offs[:, None, None, :] + tmpl[None]).reshape(-1, nv, 3)[:n_elem]        # (n_elem, nv, 3)
+    vert = np.full((n_elem, 8), -1, dtype=np.int64)
+    vert[:, :nv] = np.arange(n_elem * nv, dtype=np.int64).reshape(n_elem, nv)
+    P = np.full(n_elem, int(order), dtype=np.uint8)
+    return dict(n_elem=int(n_elem), shape=np.full(n_elem, shape, dtype=np.uint8), P=P, Q=(P + 2).astype(np.uint8),
+                vert=vert, xyz=np.ascontiguousarray(X.reshape(-1, 3)), n_vert=n_elem * nv,
+                curved=np.full(n_elem, 1 if curved else 0, dtype=np.uint8), deformation=int(deformation))
+
+
 # ---------------------------------------------------------------------------
 # counter-based random numbers (SplitMix64, Steele, Lea & Flood 2014)
 # ---------------------------------------------------------------------------

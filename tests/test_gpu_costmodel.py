@@ -1,0 +1,115 @@
+"""Cost-model network on the GPU: forward and gradient kernels against the
+FP64 oracle, deterministic training, and scheduling through the network and
+by exhaustive search."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import mlp as omlp  # noqa: E402
+from oracle import operators as oracle_ops  # noqa: E402
+from paper_2604_04644_gb300 import inputs  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def hp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2604_04644_gb300 import hp as _hp
+    return _hp
+
+
+def _data(B, n_in=5, n_out=3, seed=0):
+    rng = np.random.default_rng(seed)
+    x = rng.uniform(0, 1, (B, n_in)).astype(np.float32)
+    t = np.stack([np.sin(3 * x[:, 0]) + x[:, 1] ** 2, x[:, 2] - x[:, 3], np.cos(2 * x[:, 4])], axis=1).astype(np.float32)
+    return x, t[:, :n_out]
+
+
+def test_forward_and_gradient_match_oracle(hp):
+    n_in, H, n_out = 5, 64, 3
+    m = hp.hp_mlp_create(n_in, H, n_out, seed=3)
+    try:
+        p = hp.hp_mlp_params(m).astype(np.float64)
+        x, t = _data(37)
+        xd = torch.tensor(x, device="cuda:0")
+        td = torch.tensor(t, device="cuda:0")
+        y = torch.empty((37, n_out), device="cuda:0")
+        hp.hp_mlp_forward(m, xd, 37, y)
+        yo = omlp.forward(p, x.astype(np.float64), n_in, H, n_out)
+        assert np.abs(y.cpu().numpy() - yo).max() <= 1e-5 * max(1.0, np.abs(yo).max())
+        g = torch.empty(len(p), device="cuda:0")
+        loss = torch.empty(1, device="cuda:0")
+        hp.hp_mlp_grad(m, xd, td, 37, g, loss)
+        go = omlp.grad(p, x.astype(np.float64), t.astype(np.float64), n_in, H, n_out)
+        lo = omlp.loss(p, x.astype(np.float64), t.astype(np.float64), n_in, H, n_out)
+        assert np.abs(g.cpu().numpy() - go).max() <= 1e-4 * np.abs(go).max()
+        assert abs(loss.item() - lo) <= 1e-5 * lo
+    finally:
+        hp.hp_mlp_destroy(m)
+
+
+def test_training_reduces_loss_and_is_deterministic(hp):
+    x, t = _data(256, seed=1)
+    xd = torch.tensor(x, device="cuda:0")
+    td = torch.tensor(t, device="cuda:0")
+    finals = []
+    for rep in range(2):
+        m = hp.hp_mlp_create(5, 64, 3, seed=11)
+        loss = torch.empty(1, device="cuda:0")
+        hp.hp_mlp_grad(m, xd, td, 256, torch.empty(hp.hp_mlp_info(m)[3], device="cuda:0"), loss)
+        l0 = loss.item()
+        for _ in range(600):
+            hp.hp_mlp_adam_step(m, xd, td, 256, 3e-3, loss)
+        finals.append((loss.item(), hp.hp_mlp_params(m)))
+        hp.hp_mlp_destroy(m)
+        assert finals[-1][0] < 0.05 * l0
+    assert finals[0][0] == finals[1][0]
+    assert np.array_equal(finals[0][1], finals[1][1])
+
+
+def test_schedule_by_network_and_exhaustive(hp):
+    mesh = inputs.slab_mesh(2, 2, 4, (1, 3), order_seed=2, curved_rule="x_half")
+    nb = len(set(zip(mesh["shape"].tolist(), mesh["P"].tolist(), mesh["curved"].tolist())))
+    h = hp.hp_mesh_create(mesh, 0)
+    m = hp.hp_mlp_create(5, 32, 3, seed=1)
+    try:
+        co, po, nc, nph = hp.hp_mesh_layout(h, mesh["n_elem"])
+        uh = inputs.random_coefficients(5, co)
+        ref = oracle_ops.apply("helmholtz", mesh, uh, 1.0)
+        op = hp.hp_op_create(h, hp.HP_HELMHOLTZ)
+        # a network whose output is constant with the hybrid entry smallest
+        p = np.zeros(hp.hp_mlp_info(m)[3], dtype=np.float32)
+        p[-3:] = [1.0, 2.0, 0.5]
+        hp.hp_mlp_params(m, p)
+        hp.hp_op_schedule(op, m)
+        assert (hp.hp_op_strategies(op, nb) == hp.HP_STRAT_HYBRID).all()
+        x = torch.tensor(uh, device="cuda:0")
+        y = torch.full((nc,), np.nan, device="cuda:0", dtype=torch.float64)
+        hp.hp_op_apply(op, 1.0, x, y)
+        hp.hp_op_sync(op)
+        assert np.abs(y.cpu().numpy() - ref).max() <= 1e-12 * np.abs(ref).max()
+        times = hp.hp_op_schedule_exhaustive(op, 1.0, x, y, nb)
+        best = hp.hp_op_strategies(op, nb)
+        assert (best == times.argmin(axis=1)).all()
+        y2 = torch.full_like(y, np.nan)
+        hp.hp_op_apply(op, 1.0, x, y2)
+        hp.hp_op_sync(op)
+        assert np.abs(y2.cpu().numpy() - ref).max() <= 1e-12 * np.abs(ref).max()
+        hp.hp_op_destroy(op)
+        # derivative building blocks keep the sum-factorised strategy
+        op = hp.hp_op_create(h, hp.HP_PHYSDERIV)
+        hp.hp_op_schedule(op, m)
+        assert (hp.hp_op_strategies(op, nb) == hp.HP_STRAT_SUMFAC).all()
+        hp.hp_op_destroy(op)
+    finally:
+        hp.hp_mlp_destroy(m)
+        hp.hp_mesh_destroy(h)
+
+
+def test_mlp_argument_checks(hp):
+    with pytest.raises(hp.HpError):
+        hp.hp_mlp_create(5, 48, 3)          # hidden not a multiple of 32
+    with pytest.raises(hp.HpError):
+        hp.hp_mlp_create(40, 64, 3)
