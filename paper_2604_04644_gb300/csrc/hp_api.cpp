@@ -226,6 +226,14 @@ double elem_flops(int shape, int P, hp_opkind k) {
     }
 }
 
+template <typename T>
+void fill_const_tables(const Block& b, SFArgs<T>& a) {
+    const RefTables& t = ref_tables(b.shape, b.P);
+    for (int d = 0; d < 3; ++d)
+        for (size_t i = 0; i < t.D[d].size(); ++i) a.cD[d][i] = (T)t.D[d][i];
+    for (size_t i = 0; i < t.Ta.size(); ++i) a.cTa[i] = (T)t.Ta[i];
+}
+
 cudaError_t launch_block(hp_op op, size_t bi, int tile, double lambda, const void* in, void* out, cudaStream_t s) {
     hp_mesh m = op->mesh;
     const Block& b = m->blocks[bi];
@@ -267,6 +275,7 @@ cudaError_t launch_block(hp_op op, size_t bi, int tile, double lambda, const voi
         a.blob = static_cast<const unsigned char*>(blob.d64);
         a.blob_bytes = blob.bytes64;
         a.err = op->d_err;
+        fill_const_tables(b, a);
         return sf_launch_f64(b.shape, b.P, !b.curved, tile, a, s);
     }
     SFArgs<float> a{};
@@ -283,6 +292,7 @@ cudaError_t launch_block(hp_op op, size_t bi, int tile, double lambda, const voi
     a.blob = static_cast<const unsigned char*>(blob.d32);
     a.blob_bytes = blob.bytes32;
     a.err = op->d_err;
+    fill_const_tables(b, a);
     return sf_launch_f32(b.shape, b.P, !b.curved, tile, a, s);
 }
 

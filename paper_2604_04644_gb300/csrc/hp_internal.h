@@ -130,6 +130,10 @@ struct SFArgs {
     const unsigned char* blob;   // table blob (16-byte aligned)
     int blob_bytes;
     unsigned int* err;
+    // differentiation matrices D_d[i][m] and the eta1 table A[a][i] of the block,
+    // read by the kernels as constant-bank operands (Q <= 12, n <= 11)
+    T cD[3][144];
+    T cTa[132];
 };
 
 // arguments of the elemental-matrix / hybrid kernels (hp_emat.cu)

@@ -51,7 +51,7 @@ __host__ __device__ constexpr int sf_smem_bytes() {
 }
 
 template <int SHAPE, int P, typename T, bool AFFINE, int TILE>
-__global__ void __launch_bounds__(256) sf_kernel(const SFArgs<T> args) {
+__global__ void __launch_bounds__(256) sf_kernel(const __grid_constant__ SFArgs<T> args) {
     using C = SFCfg<P, T, TILE>;
     constexpr int n = C::n, Q = C::Q, QQ = C::QQ, NQ = C::NQ, N3 = C::N3, EPB = C::EPB, NT = C::NT;
     constexpr BlobLayout L = blob_layout_c(SHAPE, P, (int)sizeof(T));
@@ -125,15 +125,22 @@ __global__ void __launch_bounds__(256) sf_kernel(const SFArgs<T> args) {
                 S2[e * NQ + r] = acc;
             }
             __syncthreads();
-            // eta1 pass: u[i][j][k] = sum_a Ta[a][i] g[a][j][k]
-            for (int idx = tid; idx < EPB * NQ; idx += NT) {
-                int e = idx / NQ, r = idx - e * NQ;
-                int i = r / QQ, jk = r - i * QQ;
+            // eta1 pass: u[i][j][k] = sum_a Ta[a][i] g[a][j][k]; one (j,k) line per
+            // thread, the table as constant-bank operands
+            for (int idx = tid; idx < EPB * QQ; idx += NT) {
+                int e = idx / QQ, jk = idx - e * QQ;
                 const T* x = S2 + e * NQ + jk;
-                T acc = T(0);
+                T g[n];
 #pragma unroll
-                for (int a = 0; a < n; ++a) acc += Ta[a * Q + i] * x[a * QQ];
-                S1[e * 4 * NQ + r] = acc;
+                for (int a = 0; a < n; ++a) g[a] = x[a * QQ];
+                T* u = S1 + e * 4 * NQ + jk;
+#pragma unroll
+                for (int i = 0; i < Q; ++i) {
+                    T acc = T(0);
+#pragma unroll
+                    for (int a = 0; a < n; ++a) acc += args.cTa[a * Q + i] * g[a];
+                    u[i * QQ] = acc;
+                }
             }
             __syncthreads();
             if (op == HP_BWDTRANS) {
@@ -159,21 +166,52 @@ __global__ void __launch_bounds__(256) sf_kernel(const SFArgs<T> args) {
         }
 
         if (deriv) {
-            // v_d = D_d u (collocation differentiation in eta_1, eta_2, eta_3)
-            for (int idx = tid; idx < EPB * NQ; idx += NT) {
-                int e = idx / NQ, r = idx - e * NQ;
-                int i = r / QQ, jk = r - i * QQ, j = jk / Q, k = jk - j * Q;
-                const T* u = S1 + e * 4 * NQ;
-                T a1 = T(0), a2 = T(0), a3 = T(0);
+            // v_d = D_d u (collocation differentiation), one line per thread and
+            // direction, D as constant-bank operands
+            for (int idx = tid; idx < EPB * QQ; idx += NT) {     // eta1 lines (j,k)
+                int e = idx / QQ, jk = idx - e * QQ;
+                const T* u = S1 + e * 4 * NQ + jk;
+                T x[Q];
 #pragma unroll
-                for (int m = 0; m < Q; ++m) {
-                    a1 += D0[i * Q + m] * u[m * QQ + jk];
-                    a2 += D1[j * Q + m] * u[i * QQ + m * Q + k];
-                    a3 += D2[k * Q + m] * u[i * QQ + j * Q + m];
+                for (int m = 0; m < Q; ++m) x[m] = u[m * QQ];
+                T* v = S1 + e * 4 * NQ + NQ + jk;
+#pragma unroll
+                for (int i = 0; i < Q; ++i) {
+                    T acc = T(0);
+#pragma unroll
+                    for (int m = 0; m < Q; ++m) acc += args.cD[0][i * Q + m] * x[m];
+                    v[i * QQ] = acc;
                 }
-                S1[e * 4 * NQ + NQ + r] = a1;
-                S1[e * 4 * NQ + 2 * NQ + r] = a2;
-                S1[e * 4 * NQ + 3 * NQ + r] = a3;
+            }
+            for (int idx = tid; idx < EPB * QQ; idx += NT) {     // eta2 lines (i,k)
+                int e = idx / QQ, ik = idx - e * QQ, i = ik / Q, k = ik - i * Q;
+                const T* u = S1 + e * 4 * NQ + i * QQ + k;
+                T x[Q];
+#pragma unroll
+                for (int m = 0; m < Q; ++m) x[m] = u[m * Q];
+                T* v = S1 + e * 4 * NQ + 2 * NQ + i * QQ + k;
+#pragma unroll
+                for (int j = 0; j < Q; ++j) {
+                    T acc = T(0);
+#pragma unroll
+                    for (int m = 0; m < Q; ++m) acc += args.cD[1][j * Q + m] * x[m];
+                    v[j * Q] = acc;
+                }
+            }
+            for (int idx = tid; idx < EPB * QQ; idx += NT) {     // eta3 lines (i,j)
+                int e = idx / QQ, ij = idx - e * QQ;
+                const T* u = S1 + e * 4 * NQ + ij * Q;
+                T x[Q];
+#pragma unroll
+                for (int m = 0; m < Q; ++m) x[m] = u[m];
+                T* v = S1 + e * 4 * NQ + 3 * NQ + ij * Q;
+#pragma unroll
+                for (int k = 0; k < Q; ++k) {
+                    T acc = T(0);
+#pragma unroll
+                    for (int m = 0; m < Q; ++m) acc += args.cD[2][k * Q + m] * x[m];
+                    v[k] = acc;
+                }
             }
             __syncthreads();
         }
@@ -258,32 +296,72 @@ __global__ void __launch_bounds__(256) sf_kernel(const SFArgs<T> args) {
         if (op == HP_PHYSDERIV) continue;
 
         if (sumderiv) {
-            // u' = sum_d D_d^T w_d + t
-            for (int idx = tid; idx < EPB * NQ; idx += NT) {
-                int e = idx / NQ, r = idx - e * NQ;
-                int i = r / QQ, jk = r - i * QQ, j = jk / Q, k = jk - j * Q;
-                const T* w = S1 + e * 4 * NQ;
-                T acc = S2[e * NQ + r];
+            // u' = t + sum_d D_d^T w_d: one accumulating line pass per direction
+            for (int idx = tid; idx < EPB * QQ; idx += NT) {     // eta1 lines (j,k)
+                int e = idx / QQ, jk = idx - e * QQ;
+                const T* w = S1 + e * 4 * NQ + NQ + jk;
+                T x[Q];
 #pragma unroll
-                for (int m = 0; m < Q; ++m) {
-                    acc += D0[m * Q + i] * w[NQ + m * QQ + jk];
-                    acc += D1[m * Q + j] * w[2 * NQ + i * QQ + m * Q + k];
-                    acc += D2[m * Q + k] * w[3 * NQ + i * QQ + j * Q + m];
+                for (int m = 0; m < Q; ++m) x[m] = w[m * QQ];
+                T* o = S2 + e * NQ + jk;
+#pragma unroll
+                for (int i = 0; i < Q; ++i) {
+                    T acc = o[i * QQ];
+#pragma unroll
+                    for (int m = 0; m < Q; ++m) acc += args.cD[0][m * Q + i] * x[m];
+                    o[i * QQ] = acc;
                 }
-                S2[e * NQ + r] = acc;
+            }
+            __syncthreads();
+            for (int idx = tid; idx < EPB * QQ; idx += NT) {     // eta2 lines (i,k)
+                int e = idx / QQ, ik = idx - e * QQ, i = ik / Q, k = ik - i * Q;
+                const T* w = S1 + e * 4 * NQ + 2 * NQ + i * QQ + k;
+                T x[Q];
+#pragma unroll
+                for (int m = 0; m < Q; ++m) x[m] = w[m * Q];
+                T* o = S2 + e * NQ + i * QQ + k;
+#pragma unroll
+                for (int j = 0; j < Q; ++j) {
+                    T acc = o[j * Q];
+#pragma unroll
+                    for (int m = 0; m < Q; ++m) acc += args.cD[1][m * Q + j] * x[m];
+                    o[j * Q] = acc;
+                }
+            }
+            __syncthreads();
+            for (int idx = tid; idx < EPB * QQ; idx += NT) {     // eta3 lines (i,j)
+                int e = idx / QQ, ij = idx - e * QQ;
+                const T* w = S1 + e * 4 * NQ + 3 * NQ + ij * Q;
+                T x[Q];
+#pragma unroll
+                for (int m = 0; m < Q; ++m) x[m] = w[m];
+                T* o = S2 + e * NQ + ij * Q;
+#pragma unroll
+                for (int k = 0; k < Q; ++k) {
+                    T acc = o[k];
+#pragma unroll
+                    for (int m = 0; m < Q; ++m) acc += args.cD[2][m * Q + k] * x[m];
+                    o[k] = acc;
+                }
             }
             __syncthreads();
         }
 
-        // restriction B^T: eta1 pass g'[a][j][k] = sum_i Ta[a][i] u'[i][j][k]
-        for (int idx = tid; idx < EPB * n * QQ; idx += NT) {
-            int e = idx / (n * QQ), r = idx - e * (n * QQ);
-            int a = r / QQ, jk = r - a * QQ;
+        // restriction B^T: eta1 pass g'[a][j][k] = sum_i Ta[a][i] u'[i][j][k], one (j,k) line per thread
+        for (int idx = tid; idx < EPB * QQ; idx += NT) {
+            int e = idx / QQ, jk = idx - e * QQ;
             const T* x = S2 + e * NQ + jk;
-            T acc = T(0);
+            T uq[Q];
 #pragma unroll
-            for (int i = 0; i < Q; ++i) acc += Ta[a * Q + i] * x[i * QQ];
-            S1[e * 4 * NQ + r] = acc;
+            for (int i = 0; i < Q; ++i) uq[i] = x[i * QQ];
+            T* g = S1 + e * 4 * NQ + jk;
+#pragma unroll
+            for (int a = 0; a < n; ++a) {
+                T acc = T(0);
+#pragma unroll
+                for (int i = 0; i < Q; ++i) acc += args.cTa[a * Q + i] * uq[i];
+                g[a * QQ] = acc;
+            }
         }
         __syncthreads();
         // eta2 pass: f'[a][b][k] = sum_j Tb[t(a)][b][j] g'[a][j][k]
