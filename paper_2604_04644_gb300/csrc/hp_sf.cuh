@@ -57,6 +57,10 @@ __global__ void __launch_bounds__(256) sf_kernel(const __grid_constant__ SFArgs<
     constexpr BlobLayout L = blob_layout_c(SHAPE, P, (int)sizeof(T));
     constexpr int NP = n_modes_c(SHAPE, P);
     constexpr int NQp = (NQ + 3) & ~3;
+    // FP32: register-blocked line passes with constant-bank tables (the shared
+    // memory load pipe is the limit); FP64: one output per thread (more parallel
+    // tasks to keep the FP64 pipe, the limit there, busy)
+    constexpr bool LINES = sizeof(T) == 4;
 
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
@@ -125,6 +129,7 @@ __global__ void __launch_bounds__(256) sf_kernel(const __grid_constant__ SFArgs<
                 S2[e * NQ + r] = acc;
             }
             __syncthreads();
+            if constexpr (LINES) {
             // eta1 pass: u[i][j][k] = sum_a Ta[a][i] g[a][j][k]; one (j,k) line per
             // thread, the table as constant-bank operands
             for (int idx = tid; idx < EPB * QQ; idx += NT) {
@@ -143,6 +148,19 @@ __global__ void __launch_bounds__(256) sf_kernel(const __grid_constant__ SFArgs<
                 }
             }
             __syncthreads();
+            } else {
+            // eta1 pass: u[i][j][k] = sum_a Ta[a][i] g[a][j][k]
+            for (int idx = tid; idx < EPB * NQ; idx += NT) {
+                int e = idx / NQ, r = idx - e * NQ;
+                int i = r / QQ, jk = r - i * QQ;
+                const T* x = S2 + e * NQ + jk;
+                T acc = T(0);
+#pragma unroll
+                for (int a = 0; a < n; ++a) acc += Ta[a * Q + i] * x[a * QQ];
+                S1[e * 4 * NQ + r] = acc;
+            }
+            __syncthreads();
+            }
             if (op == HP_BWDTRANS) {
                 for (int idx = tid; idx < EPB * NQ; idx += NT) {
                     int e = idx / NQ, r = idx - e * NQ;
@@ -165,6 +183,7 @@ __global__ void __launch_bounds__(256) sf_kernel(const __grid_constant__ SFArgs<
             __syncthreads();
         }
 
+        if constexpr (LINES) {
         if (deriv) {
             // v_d = D_d u (collocation differentiation), one line per thread and
             // direction, D as constant-bank operands
@@ -214,6 +233,29 @@ __global__ void __launch_bounds__(256) sf_kernel(const __grid_constant__ SFArgs<
                 }
             }
             __syncthreads();
+        }
+
+        } else {
+        if (deriv) {
+            // v_d = D_d u (collocation differentiation in eta_1, eta_2, eta_3)
+            for (int idx = tid; idx < EPB * NQ; idx += NT) {
+                int e = idx / NQ, r = idx - e * NQ;
+                int i = r / QQ, jk = r - i * QQ, j = jk / Q, k = jk - j * Q;
+                const T* u = S1 + e * 4 * NQ;
+                T a1 = T(0), a2 = T(0), a3 = T(0);
+#pragma unroll
+                for (int m = 0; m < Q; ++m) {
+                    a1 += D0[i * Q + m] * u[m * QQ + jk];
+                    a2 += D1[j * Q + m] * u[i * QQ + m * Q + k];
+                    a3 += D2[k * Q + m] * u[i * QQ + j * Q + m];
+                }
+                S1[e * 4 * NQ + NQ + r] = a1;
+                S1[e * 4 * NQ + 2 * NQ + r] = a2;
+                S1[e * 4 * NQ + 3 * NQ + r] = a3;
+            }
+            __syncthreads();
+        }
+
         }
 
         // pointwise metric
@@ -295,6 +337,7 @@ __global__ void __launch_bounds__(256) sf_kernel(const __grid_constant__ SFArgs<
         __syncthreads();
         if (op == HP_PHYSDERIV) continue;
 
+        if constexpr (LINES) {
         if (sumderiv) {
             // u' = t + sum_d D_d^T w_d: one accumulating line pass per direction
             for (int idx = tid; idx < EPB * QQ; idx += NT) {     // eta1 lines (j,k)
@@ -347,6 +390,28 @@ __global__ void __launch_bounds__(256) sf_kernel(const __grid_constant__ SFArgs<
             __syncthreads();
         }
 
+        } else {
+        if (sumderiv) {
+            // u' = sum_d D_d^T w_d + t
+            for (int idx = tid; idx < EPB * NQ; idx += NT) {
+                int e = idx / NQ, r = idx - e * NQ;
+                int i = r / QQ, jk = r - i * QQ, j = jk / Q, k = jk - j * Q;
+                const T* w = S1 + e * 4 * NQ;
+                T acc = S2[e * NQ + r];
+#pragma unroll
+                for (int m = 0; m < Q; ++m) {
+                    acc += D0[m * Q + i] * w[NQ + m * QQ + jk];
+                    acc += D1[m * Q + j] * w[2 * NQ + i * QQ + m * Q + k];
+                    acc += D2[m * Q + k] * w[3 * NQ + i * QQ + j * Q + m];
+                }
+                S2[e * NQ + r] = acc;
+            }
+            __syncthreads();
+        }
+
+        }
+
+        if constexpr (LINES) {
         // restriction B^T: eta1 pass g'[a][j][k] = sum_i Ta[a][i] u'[i][j][k], one (j,k) line per thread
         for (int idx = tid; idx < EPB * QQ; idx += NT) {
             int e = idx / QQ, jk = idx - e * QQ;
@@ -364,6 +429,19 @@ __global__ void __launch_bounds__(256) sf_kernel(const __grid_constant__ SFArgs<
             }
         }
         __syncthreads();
+        } else {
+        // restriction B^T: eta1 pass g'[a][j][k] = sum_i Ta[a][i] u'[i][j][k]
+        for (int idx = tid; idx < EPB * n * QQ; idx += NT) {
+            int e = idx / (n * QQ), r = idx - e * (n * QQ);
+            int a = r / QQ, jk = r - a * QQ;
+            const T* x = S2 + e * NQ + jk;
+            T acc = T(0);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) acc += Ta[a * Q + i] * x[i * QQ];
+            S1[e * 4 * NQ + r] = acc;
+        }
+        __syncthreads();
+        }
         // eta2 pass: f'[a][b][k] = sum_j Tb[t(a)][b][j] g'[a][j][k]
         for (int idx = tid; idx < EPB * n * n * Q; idx += NT) {
             int e = idx / (n * n * Q), r = idx - e * (n * n * Q);
