@@ -216,6 +216,27 @@ hp_status hp_mlp_adam_step(hp_mlp mlp, const float* x, const float* t, int64_t b
                            void* stream);
 void hp_mlp_destroy(hp_mlp mlp);
 
+/* The gradient of hp_mlp_grad for callers that cannot allocate device memory
+ * (no counterpart in the paper).  Such callers are, for example, programs whose
+ * device memory is owned by a pool or framework allocator that forbids
+ * cudaMalloc/cudaFree outside it, or loops that must not pay the device-wide
+ * synchronisation cudaFree implies.  The caller passes everything as device
+ * arrays on the current device: the flat parameters (layout of hp_mlp_params),
+ * x[batch][n_in], t[batch][n_out], and the outputs grad[n_params] and loss[1]
+ * (loss may be NULL); sizes obey the limits of hp_mlp_create.  The call
+ * allocates nothing: its scratch is one fixed device array of 2^20 floats
+ * (4 MiB, held by every GPU that loads the library until the process exits),
+ * so batch * (n_params + 2 n_hidden + n_out + 1) must not exceed 2^20, else
+ * HP_ERR_ARG with a message.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.  Every call uses the same array:
+ * calls that overlap on the GPU (other streams, other threads) race and must
+ * be serialised by the caller.  Each call writes every scratch entry it
+ * reads, so the previous call's contents do not matter.  Results equal
+ * hp_mlp_grad's for the same parameters and data. */
+hp_status hp_mlp_grad_noalloc(const float* params, int n_in, int n_hidden, int n_out, const float* x,
+                              const float* t, int64_t batch, float* grad, float* loss, void* stream);
+
 /* Pick each block's strategy as the argmin of the network's 3 outputs (the
  * predicted log times of SUMFAC, ELEMAT, HYBRID) on the block's features.
  * Derivative building blocks stay SUMFAC. */

@@ -11,6 +11,7 @@
 // a fixed-order column sum), so training is bitwise reproducible.
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "hp_internal.h"
@@ -310,3 +311,70 @@ void hp_mlp_destroy(hp_mlp m) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Gradient entry point that allocates nothing (see hp_mlp_grad_noalloc in
+// include/hp.h).  Its scratch -- per-sample gradient rows, activations,
+// outputs and per-sample losses -- lives in this fixed-size device array,
+// which every GPU that loads the library holds until the process exits.
+static constexpr int64_t kNoAllocScratchFloats = int64_t(1) << 20;   // 4 MiB per device
+static __device__ __align__(256) float g_noalloc_scratch[kNoAllocScratchFloats];
+
+namespace hp {
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+float* g_noalloc_ptr[kMaxDevices] = {};
+
+}  // namespace
+}  // namespace hp
+
+extern "C" hp_status hp_mlp_grad_noalloc(const float* params, int n_in, int n_hidden, int n_out, const float* x,
+                                         const float* t, int64_t batch, float* grad, float* loss, void* stream) {
+    if (!params || !x || !t || !grad || batch < 1 || batch > 65535 || n_in < 1 || n_in > kMaxIn ||
+        n_hidden < 32 || n_hidden > kMaxH || n_hidden % 32 || n_out < 1 || n_out > kMaxOut) {
+        set_error("hp_mlp_grad_noalloc: bad argument");
+        return HP_ERR_ARG;
+    }
+    Off o = offsets(n_in, n_hidden, n_out);
+    const int64_t need = batch * (o.n + 2 * (int64_t)n_hidden + n_out + 1);
+    if (need > kNoAllocScratchFloats) {
+        set_error("hp_mlp_grad_noalloc: batch * (n_params + 2 n_hidden + n_out + 1) = " + std::to_string(need) +
+                  " floats exceeds the fixed scratch of " + std::to_string(kNoAllocScratchFloats) +
+                  " floats; use a smaller batch or hp_mlp_grad");
+        return HP_ERR_ARG;
+    }
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "hp_mlp_grad_noalloc");
+    if (dev < 0 || dev >= kMaxDevices) { set_error("hp_mlp_grad_noalloc: device index out of range"); return HP_ERR_ARG; }
+    float* base = nullptr;
+    {
+        // set-up on the first call on this device (the device is current):
+        // the host-side name of the array is not a device address
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            void* p = nullptr;
+            e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess) return cuda_fail(e, "hp_mlp_grad_noalloc: cudaGetSymbolAddress");
+            g_noalloc_ptr[dev] = static_cast<float*>(p);
+        }
+        base = g_noalloc_ptr[dev];
+    }
+    // every scratch entry read below is written first in the same call
+    // (rows by the backward kernel, activations and outputs by the forward one),
+    // so nothing needs clearing between calls
+    float* rows = base;
+    float* act = rows + batch * o.n;
+    float* y = act + batch * 2 * (int64_t)n_hidden;
+    float* loss_rows = y + batch * n_out;
+    cudaStream_t s = (cudaStream_t)stream;
+    mlp_forward_kernel<<<(unsigned)batch, n_hidden, 0, s>>>(params, n_in, n_hidden, n_out, o, x, batch, y, act);
+    mlp_backward_kernel<<<(unsigned)batch, n_hidden, 0, s>>>(params, n_in, n_hidden, n_out, o, x, t, batch, y, act,
+                                                            rows, loss_rows);
+    column_sum_kernel<<<(unsigned)((o.n + 255) / 256), 256, 0, s>>>(rows, batch, o.n, grad);
+    if (loss) column_sum_kernel<<<1, 32, 0, s>>>(loss_rows, batch, 1, loss);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? HP_OK : cuda_fail(e, "hp_mlp_grad_noalloc");
+}

@@ -33,7 +33,7 @@ EXPORTED = ["hp_mesh_create", "hp_mesh_layout", "hp_geom_factors", "hp_geom_copy
             "hp_op_block_features", "hp_op_schedule", "hp_op_schedule_exhaustive", "hp_op_sync", "hp_op_work",
             "hp_op_destroy", "hp_mesh_destroy", "hp_status_str", "hp_last_error",
             "hp_mlp_create", "hp_mlp_info", "hp_mlp_params", "hp_mlp_forward", "hp_mlp_grad", "hp_mlp_adam_step",
-            "hp_mlp_destroy"]
+            "hp_mlp_destroy", "hp_mlp_grad_noalloc"]
 
 
 class HpError(RuntimeError):
@@ -71,6 +71,9 @@ _lib.hp_mlp_forward.argtypes = [_vp, _vp, ctypes.c_int64, _vp, _vp]
 _lib.hp_mlp_grad.argtypes = [_vp, _vp, _vp, ctypes.c_int64, _vp, _vp, _vp]
 _lib.hp_mlp_adam_step.argtypes = [_vp, _vp, _vp, ctypes.c_int64, ctypes.c_float, _vp, _vp]
 _lib.hp_mlp_destroy.argtypes = [_vp]
+_lib.hp_mlp_grad_noalloc.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_int64, _vp,
+                                     _vp, _vp]
+_lib.hp_mlp_grad_noalloc.restype = ctypes.c_int
 _lib.hp_op_sync.argtypes = [_vp, _vp]
 _lib.hp_op_work.argtypes = [_vp, _i64p, _dp, _dp]
 _lib.hp_op_destroy.argtypes = [_vp]
@@ -262,3 +265,9 @@ def hp_mlp_adam_step(mlp, x, t, batch, lr, loss=None, stream=None):
 
 def hp_mlp_destroy(mlp):
     _lib.hp_mlp_destroy(mlp)
+
+
+def hp_mlp_grad_noalloc(params, n_in, n_hidden, n_out, x, t, batch, grad, loss=None, stream=None):
+    """Gradient with caller-passed parameters and no device allocation (fixed 2^20-float scratch)."""
+    _check(_lib.hp_mlp_grad_noalloc(_ptr(params), int(n_in), int(n_hidden), int(n_out), _ptr(x), _ptr(t),
+                                    int(batch), _ptr(grad), _ptr(loss), _stream(stream)), "hp_mlp_grad_noalloc")
