@@ -248,6 +248,64 @@ hp_status hp_op_schedule(hp_op op, hp_mlp mlp, void* stream);
 hp_status hp_op_schedule_exhaustive(hp_op op, double lambda, const void* in, void* out, float* times_ms,
                                     void* stream);
 
+/* Physical coordinates of every quadrature point (device array 3*n_phys,
+ * component-major: xyz[c*n_phys + phys_offset[e] + l]); the affine vertex map
+ * followed, for curved elements, by the mesh's deformation. */
+hp_status hp_mesh_points(hp_mesh mesh, double* xyz, void* stream);
+
+/* ---------------------------------------------------------------- assembled solve
+ * The global C0 problem behind the weak form of Sec. 2.1:
+ * (grad u, grad v) + lambda (u, v) = (f, v), homogeneous Dirichlet conditions
+ * on the boundary faces (faces that belong to one element). */
+typedef struct hp_c0_s* hp_c0;
+
+/* Global C0 numbering of a conforming mesh with one order P on all elements:
+ * one DOF per vertex, P-1 per edge, (P-1)^2 per quad face, (P-1)(P-2)/2 per
+ * triangular face, and the element interiors; global order vertices, edges,
+ * faces, interiors.  Each local coefficient maps to (gid, sign): u_local =
+ * sign * u_global[gid].  Triangular faces must have their collapsed vertex at
+ * the face's largest global vertex id (the slab generator ensures it).
+ * HP_ERR_UNSUPPORTED for mixed orders or non-conforming orientations. */
+hp_status hp_c0_create(hp_mesh mesh, hp_c0* out);
+hp_status hp_c0_info(hp_c0 c0, int64_t* n_global, int64_t* n_boundary);
+/* The same numbering computed on the host from a mesh description, without a
+ * GPU: gid[n_coeff], sign[n_coeff] and boundary[n_global] (the caller sizes
+ * boundary with n_coeff entries, an upper bound of n_global). */
+hp_status hp_c0_map_host(const hp_mesh_desc* desc, int64_t* gid, int8_t* sign, uint8_t* boundary, int64_t* n_global);
+/* Host copies of the maps: gid[n_coeff], sign[n_coeff], boundary[n_global] (any may be NULL). */
+hp_status hp_c0_maps(hp_c0 c0, int64_t* gid, int8_t* sign, uint8_t* boundary);
+/* local = A global (device FP64 arrays). */
+hp_status hp_c0_gather(hp_c0 c0, const double* global, double* local, void* stream);
+/* global = A^T local, summing the local copies of each global DOF in a fixed
+ * order (deterministic); Dirichlet entries set to 0 if mask_boundary. */
+hp_status hp_c0_assemble(hp_c0 c0, const double* local, double* global, int mask_boundary, void* stream);
+
+typedef struct {
+    double tol;            /* stop at ||b - A x|| <= tol ||b|| (FP64 residual)                 */
+    int max_iter;          /* FP64 CG: iteration limit                                          */
+    int mixed;             /* 0: Jacobi-PCG in FP64; 1: FP64 refinement of FP32 Jacobi-PCG      */
+    double inner_tol;      /* mixed: relative tolerance of each FP32 solve                      */
+    int inner_max_iter;    /* mixed: iteration limit of each FP32 solve                         */
+    int max_refinements;   /* mixed: refinement steps                                           */
+} hp_solve_opts;
+
+typedef struct {
+    int iterations;        /* CG iterations (mixed: total FP32 iterations)                      */
+    int inner_iterations;  /* mixed: total FP32 iterations                                      */
+    int refinements;       /* mixed: FP64 residual evaluations used                             */
+    double rel_residual;   /* final ||b - A x|| / ||b||, in FP64                                */
+} hp_solve_stats;
+
+/* Solve A x = rhs for the assembled lambda M + L (lambda >= 0) with the
+ * element operators of this library.  rhs, x: device FP64 global vectors
+ * (x holds the initial guess; its Dirichlet entries are set to 0).  The first
+ * solve for a lambda builds the Jacobi diagonal (element diagonals summed).
+ * Synchronises `stream`.  HP_ERR_NOT_CONVERGED if the tolerance is not met
+ * (x holds the last iterate, stats the residual). */
+hp_status hp_solve(hp_c0 c0, double lambda, const double* rhs, double* x, const hp_solve_opts* opts,
+                   hp_solve_stats* stats, void* stream);
+void hp_c0_destroy(hp_c0 c0);
+
 /* Synchronise `stream` and report any error latched by the op's kernels
  * (HP_ERR_TIMEOUT, HP_ERR_DEVICE_BOUNDS) or by CUDA. */
 hp_status hp_op_sync(hp_op op, void* stream);

@@ -342,6 +342,7 @@ hp_status hp_mesh_create(const hp_mesh_desc* d, int device, hp_mesh* out) {
     m->P.assign(d->P, d->P + d->n_elem);
     m->Q.assign(d->Q, d->Q + d->n_elem);
     m->curved.assign(d->curved, d->curved + d->n_elem);
+    m->vert.assign(d->vert, d->vert + 8 * d->n_elem);
     m->coeff_off.assign(d->n_elem + 1, 0);
     m->phys_off.assign(d->n_elem + 1, 0);
     std::vector<double> frames(12 * d->n_elem);
@@ -688,6 +689,17 @@ hp_status hp_op_apply_graph(hp_op op, double lambda, const void* in, void* out, 
     }
     cudaError_t e = cudaGraphLaunch(op->graph, s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+    return HP_OK;
+}
+
+hp_status hp_mesh_points(hp_mesh m, double* xyz, void* stream) {
+    if (!m || !xyz) { set_error("hp_mesh_points: null argument"); return HP_ERR_ARG; }
+    DeviceGuard guard(m->device);
+    for (const Block& b : m->blocks) {
+        cudaError_t e = launch_points(b, m->blobs.at(b.shape * 16 + b.P), m->deformation, xyz, m->phys_off.back(),
+                                      (cudaStream_t)stream);
+        if (e != cudaSuccess) return cuda_fail(e, "hp_mesh_points");
+    }
     return HP_OK;
 }
 

@@ -278,6 +278,31 @@ __global__ void __launch_bounds__(kNT) hyb_kernel(const EMArgs<T> a, int E) {
     }
 }
 
+// diag of (lambda M + L) of each element: sum over points of
+// lambda w|J| B_lm^2 + sum_dd' G_dd' (D_d B)_lm (D_d' B)_lm; one thread per (element, mode)
+template <int SHAPE, bool AFFINE>
+__global__ void elem_diag_kernel(int64_t n_elem, int P, int Q, int NP, int NQp, const int64_t* __restrict__ coeff_off,
+                                 const double* __restrict__ geom, const double* __restrict__ A4,
+                                 const double* __restrict__ zt, const double* __restrict__ wt, double lambda,
+                                 double* __restrict__ diag) {
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= n_elem * NP) return;
+    int64_t e = idx / NP;
+    int m = (int)(idx % NP);
+    const int NQ = Q * Q * Q;
+    double acc = 0.0;
+    for (int l = 0; l < NQ; ++l) {
+        double G[6], wJ;
+        point_metric<SHAPE, double, AFFINE>(geom, e, l, NQp, Q, zt, wt, true, G, wJ);
+        double b = A4[(int64_t)l * NP + m];
+        double d1 = A4[((int64_t)NQ + l) * NP + m], d2 = A4[((int64_t)2 * NQ + l) * NP + m],
+               d3 = A4[((int64_t)3 * NQ + l) * NP + m];
+        acc += lambda * wJ * b * b + G[0] * d1 * d1 + G[3] * d2 * d2 + G[5] * d3 * d3 +
+               2.0 * (G[1] * d1 * d2 + G[2] * d1 * d3 + G[4] * d2 * d3);
+    }
+    diag[coeff_off[e] + m] = acc;
+}
+
 template <typename K>
 int grid_for(K kern, int smem, int64_t groups) {
     int dev = 0, sms = 0, per = 0;
@@ -329,6 +354,32 @@ cudaError_t launch_any(bool hybrid, bool affine, const EMArgs<T>& a, cudaStream_
 }
 
 }  // namespace
+
+cudaError_t launch_elem_diag(const Block& b, const DeviceBlobs& blob, double lambda, double* diag, cudaStream_t s) {
+    if (b.n_elem == 0) return cudaSuccess;
+    const int NP = n_modes(b.shape, b.P), Q = b.Q;
+    const BlobLayout L = blob_layout_c(b.shape, b.P, 8);
+    const double* zt = reinterpret_cast<const double*>(blob.d64) + L.z;
+    const double* wt = reinterpret_cast<const double*>(blob.d64) + L.w;
+    int nt = 128;
+    unsigned nb = (unsigned)((b.n_elem * NP + nt - 1) / nt);
+    const int NQp = nqp(Q);
+#define HP_DIAG(S)                                                                                               \
+    if (b.curved)                                                                                                \
+        elem_diag_kernel<S, false><<<nb, nt, 0, s>>>(b.n_elem, b.P, Q, NP, NQp, b.d_coeff_off, b.d_geom,         \
+                                                     blob.A4_64, zt, wt, lambda, diag);                          \
+    else                                                                                                         \
+        elem_diag_kernel<S, true><<<nb, nt, 0, s>>>(b.n_elem, b.P, Q, NP, NQp, b.d_coeff_off, b.d_geom,          \
+                                                    blob.A4_64, zt, wt, lambda, diag);
+    switch (b.shape) {
+        case HP_HEX: HP_DIAG(HP_HEX) break;
+        case HP_PRISM: HP_DIAG(HP_PRISM) break;
+        case HP_PYR: HP_DIAG(HP_PYR) break;
+        default: HP_DIAG(HP_TET)
+    }
+#undef HP_DIAG
+    return cudaGetLastError();
+}
 
 cudaError_t emat_launch_f64(bool hybrid, bool affine, const EMArgs<double>& a, cudaStream_t s) {
     return launch_any<double>(hybrid, affine, a, s);

@@ -125,6 +125,34 @@ __global__ void geom_affine_kernel(int64_t n_elem, const double* __restrict__ fr
         for (int c = 0; c < 3; ++c) o[7 + 3 * a + c] = Ji[a][c];
 }
 
+template <int SHAPE>
+__global__ void points_kernel(int Q, int64_t n_elem, const double* __restrict__ frame, const int64_t* __restrict__ phys_off,
+                              const double* __restrict__ z, int kind, int curved, double* __restrict__ xyz, int64_t n_phys) {
+    const int NQ = Q * Q * Q;
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= n_elem * NQ) return;
+    int64_t e = idx / NQ;
+    int l = (int)(idx % NQ);
+    int i = l / (Q * Q), j = (l / Q) % Q, k = l % Q;
+    double xi[3];
+    xi_from_eta<SHAPE>(z[i], z[Q + j], z[2 * Q + k], xi);
+    const double* F = frame + e * 12;
+    double y[3];
+    for (int r = 0; r < 3; ++r) {
+        y[r] = F[r];
+        for (int d = 0; d < 3; ++d) y[r] += F[3 + r * 3 + d] * 0.5 * (xi[d] + 1.0);
+    }
+    double o[3] = {y[0], y[1], y[2]};
+    if (curved && kind == 1) {
+        double s[3], c[3];
+        for (int r = 0; r < 3; ++r) sincospi(y[r], &s[r], &c[r]);
+        o[0] += 0.05 * s[1] * s[2];
+        o[1] += 0.05 * s[2] * s[0];
+        o[2] += 0.05 * s[0] * s[1];
+    }
+    for (int r = 0; r < 3; ++r) xyz[r * n_phys + phys_off[e] + l] = o[r];
+}
+
 __global__ void to_f32_kernel(const double* __restrict__ src, float* __restrict__ dst, int64_t n) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -167,6 +195,22 @@ cudaError_t launch_geom(const Block& b, const DeviceBlobs& blob, int deformation
         default:
             geom_curved_kernel<HP_TET><<<nb, nt, 0, s>>>(b.Q, NQp, b.n_elem, b.d_frame, z, w, deformation,
                                                          want_deriv, b.d_geom, b.d_dgeom, d_err, d_bad_elem);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_points(const Block& b, const DeviceBlobs& blob, int deformation, double* xyz,
+                          int64_t n_phys_total, cudaStream_t s) {
+    if (b.n_elem == 0) return cudaSuccess;
+    const BlobLayout L = blob_layout_c(b.shape, b.P, 8);
+    const double* z = reinterpret_cast<const double*>(blob.d64) + L.z;
+    int NQ = b.Q * b.Q * b.Q, nt = 128;
+    unsigned nb = (unsigned)((b.n_elem * NQ + nt - 1) / nt);
+    switch (b.shape) {
+        case HP_HEX: points_kernel<HP_HEX><<<nb, nt, 0, s>>>(b.Q, b.n_elem, b.d_frame, b.d_phys_off, z, deformation, b.curved, xyz, n_phys_total); break;
+        case HP_PRISM: points_kernel<HP_PRISM><<<nb, nt, 0, s>>>(b.Q, b.n_elem, b.d_frame, b.d_phys_off, z, deformation, b.curved, xyz, n_phys_total); break;
+        case HP_PYR: points_kernel<HP_PYR><<<nb, nt, 0, s>>>(b.Q, b.n_elem, b.d_frame, b.d_phys_off, z, deformation, b.curved, xyz, n_phys_total); break;
+        default: points_kernel<HP_TET><<<nb, nt, 0, s>>>(b.Q, b.n_elem, b.d_frame, b.d_phys_off, z, deformation, b.curved, xyz, n_phys_total);
     }
     return cudaGetLastError();
 }

@@ -36,6 +36,11 @@ struct RefTables {
 const RefTables& ref_tables(int shape, int P);
 int n_modes(int shape, int P);
 
+// All modes of (shape, P) at one reference point xi (not at a collapse point).
+void eval_modes(int shape, int P, const double xi[3], double* out);
+// Member m of 1-D family s (0: L, R, psi; s >= 1: warped W_s) at z.
+double family_value(int P, int s, int m, double z);
+
 // Dense reference matrices A4[q][l][m] (q = 0: B, q = 1..3: d/d eta_q of B), FP64.
 std::vector<double> dense_matrices(int shape, int P);
 
@@ -77,6 +82,7 @@ struct hp_mesh_s {
     int deformation = 0;
     std::vector<uint8_t> shape, P, Q, curved;
     std::vector<int64_t> coeff_off, phys_off;   // n_elem + 1
+    std::vector<int64_t> vert;                  // n_elem * 8 global vertex ids (for the C0 map)
     std::vector<hp::Block> blocks;
     std::map<int, hp::DeviceBlobs> blobs;       // key shape*16 + P
     bool geom_ready = false, dgeom_ready = false, geom32_ready = false;
@@ -113,6 +119,14 @@ constexpr unsigned int DERR_GEOM = 4u;
 cudaError_t launch_geom(const Block& b, const DeviceBlobs& blob, int deformation, bool want_deriv,
                         unsigned int* d_err, int* d_bad_elem, cudaStream_t s);
 cudaError_t launch_to_f32(const double* src, float* dst, int64_t n, cudaStream_t s);
+// physical coordinates of the quadrature points of a block, xyz[c*n_phys_total + phys_off + l]
+cudaError_t launch_points(const Block& b, const DeviceBlobs& blob, int deformation, double* xyz,
+                          int64_t n_phys_total, cudaStream_t s);
+// element diagonals of lambda M + L (FP64) into local coefficient slots
+cudaError_t launch_elem_diag(const Block& b, const DeviceBlobs& blob, double lambda, double* diag, cudaStream_t s);
+// C0 numbering (hp_c0.cpp)
+hp_status build_c0(const hp_mesh m, const std::vector<int64_t>& vert, std::vector<int64_t>& gid,
+                   std::vector<int8_t>& sign, std::vector<uint8_t>& boundary, int64_t& n_global);
 
 // arguments of the sum-factorisation kernels
 template <typename T>

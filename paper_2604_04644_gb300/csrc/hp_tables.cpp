@@ -258,6 +258,31 @@ const RefTables& ref_tables(int shape, int P) {
     return it->second;
 }
 
+double family_value(int P, int s, int m, double z) { return family(P, s, m, z); }
+
+void eval_modes(int shape, int P, const double xi[3], double* out) {
+    // eta(xi) of the collapsed coordinates, then the generalised tensor product
+    double e1 = xi[0], e2 = xi[1], e3 = xi[2];
+    if (shape == HP_PRISM) e1 = 2.0 * (1.0 + xi[0]) / (1.0 - xi[2]) - 1.0;
+    if (shape == HP_PYR) {
+        e1 = 2.0 * (1.0 + xi[0]) / (1.0 - xi[2]) - 1.0;
+        e2 = 2.0 * (1.0 + xi[1]) / (1.0 - xi[2]) - 1.0;
+    }
+    if (shape == HP_TET) {
+        e1 = 2.0 * (1.0 + xi[0]) / (-xi[1] - xi[2]) - 1.0;
+        e2 = 2.0 * (1.0 + xi[1]) / (1.0 - xi[2]) - 1.0;
+    }
+    const RefTables& t = ref_tables(shape, P);
+    const int n = t.n;
+    for (int m = 0; m < t.NP; ++m) out[m] = 0.0;
+    for (int sl = 0; sl < n * n * n; ++sl) {
+        int m = t.slot2mode[sl];
+        if (m < 0) continue;
+        int a = sl / (n * n), b = (sl / n) % n, c = sl % n;
+        out[m] += family(P, 0, a, e1) * family(P, t.famb[a], b, e2) * family(P, t.famc[a * n + b], c, e3);
+    }
+}
+
 std::vector<double> dense_matrices(int shape, int P) {
     // A4[q][l][m], q = 0: B = phi_m at point l; q = d + 1: d phi_m / d eta_d at l,
     // obtained as D_d B (exact: each phi_m lies in the Lagrange span of the points)

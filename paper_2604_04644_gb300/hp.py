@@ -33,7 +33,8 @@ EXPORTED = ["hp_mesh_create", "hp_mesh_layout", "hp_geom_factors", "hp_geom_copy
             "hp_op_block_features", "hp_op_schedule", "hp_op_schedule_exhaustive", "hp_op_sync", "hp_op_work",
             "hp_op_destroy", "hp_mesh_destroy", "hp_status_str", "hp_last_error",
             "hp_mlp_create", "hp_mlp_info", "hp_mlp_params", "hp_mlp_forward", "hp_mlp_grad", "hp_mlp_adam_step",
-            "hp_mlp_destroy", "hp_mlp_grad_noalloc"]
+            "hp_mlp_destroy", "hp_mlp_grad_noalloc", "hp_mesh_points", "hp_c0_create", "hp_c0_info",
+            "hp_c0_map_host", "hp_c0_maps", "hp_c0_gather", "hp_c0_assemble", "hp_solve", "hp_c0_destroy"]
 
 
 class HpError(RuntimeError):
@@ -271,3 +272,104 @@ def hp_mlp_grad_noalloc(params, n_in, n_hidden, n_out, x, t, batch, grad, loss=N
     """Gradient with caller-passed parameters and no device allocation (fixed 2^20-float scratch)."""
     _check(_lib.hp_mlp_grad_noalloc(_ptr(params), int(n_in), int(n_hidden), int(n_out), _ptr(x), _ptr(t),
                                     int(batch), _ptr(grad), _ptr(loss), _stream(stream)), "hp_mlp_grad_noalloc")
+
+
+class hp_solve_opts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("mixed", ctypes.c_int),
+                ("inner_tol", ctypes.c_double), ("inner_max_iter", ctypes.c_int), ("max_refinements", ctypes.c_int)]
+
+
+class hp_solve_stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("inner_iterations", ctypes.c_int), ("refinements", ctypes.c_int),
+                ("rel_residual", ctypes.c_double)]
+
+
+_lib.hp_mesh_points.argtypes = [_vp, _vp, _vp]
+_lib.hp_c0_create.argtypes = [_vp, ctypes.POINTER(_vp)]
+_lib.hp_c0_info.argtypes = [_vp, _vp, _vp]
+_lib.hp_c0_map_host.argtypes = [ctypes.POINTER(hp_mesh_desc), _vp, _vp, _vp, _vp]
+_lib.hp_c0_maps.argtypes = [_vp, _vp, _vp, _vp]
+_lib.hp_c0_gather.argtypes = [_vp, _vp, _vp, _vp]
+_lib.hp_c0_assemble.argtypes = [_vp, _vp, _vp, ctypes.c_int, _vp]
+_lib.hp_solve.argtypes = [_vp, ctypes.c_double, _vp, _vp, ctypes.POINTER(hp_solve_opts),
+                          ctypes.POINTER(hp_solve_stats), _vp]
+_lib.hp_c0_destroy.argtypes = [_vp]
+for _f in ("hp_mesh_points", "hp_c0_create", "hp_c0_info", "hp_c0_map_host", "hp_c0_maps", "hp_c0_gather",
+           "hp_c0_assemble", "hp_solve"):
+    getattr(_lib, _f).restype = ctypes.c_int
+
+
+def _desc(mesh):
+    keep = dict(shape=np.ascontiguousarray(mesh["shape"], dtype=np.uint8),
+                P=np.ascontiguousarray(mesh["P"], dtype=np.uint8),
+                Q=np.ascontiguousarray(mesh["Q"], dtype=np.uint8),
+                vert=np.ascontiguousarray(mesh["vert"], dtype=np.int64),
+                xyz=np.ascontiguousarray(mesh["xyz"], dtype=np.float64),
+                curved=np.ascontiguousarray(mesh["curved"], dtype=np.uint8))
+    d = hp_mesh_desc(int(mesh["n_elem"]), keep["shape"].ctypes.data, keep["P"].ctypes.data,
+                     keep["Q"].ctypes.data, keep["vert"].ctypes.data, keep["xyz"].ctypes.data,
+                     int(keep["xyz"].shape[0]), keep["curved"].ctypes.data, int(mesh["deformation"]))
+    return d, keep
+
+
+def hp_mesh_points(mesh, xyz, stream=None):
+    _check(_lib.hp_mesh_points(mesh, _ptr(xyz), _stream(stream)), "hp_mesh_points")
+
+
+def hp_c0_map_host(mesh, n_coeff):
+    """Host-side C0 numbering: (gid, sign, boundary, n_global)."""
+    d, keep = _desc(mesh)
+    gid = np.zeros(n_coeff, dtype=np.int64)
+    sign = np.zeros(n_coeff, dtype=np.int8)
+    bnd = np.zeros(n_coeff, dtype=np.uint8)
+    ng = ctypes.c_int64()
+    _check(_lib.hp_c0_map_host(ctypes.byref(d), gid.ctypes.data, sign.ctypes.data, bnd.ctypes.data,
+                               ctypes.byref(ng)), "hp_c0_map_host")
+    return gid, sign, bnd[:ng.value].copy(), ng.value
+
+
+def hp_c0_create(mesh):
+    h = _vp()
+    _check(_lib.hp_c0_create(mesh, ctypes.byref(h)), "hp_c0_create")
+    return h.value
+
+
+def hp_c0_info(c0):
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    _check(_lib.hp_c0_info(c0, ctypes.byref(a), ctypes.byref(b)), "hp_c0_info")
+    return a.value, b.value
+
+
+def hp_c0_maps(c0, n_coeff):
+    ng = hp_c0_info(c0)[0]
+    gid = np.zeros(n_coeff, dtype=np.int64)
+    sign = np.zeros(n_coeff, dtype=np.int8)
+    bnd = np.zeros(ng, dtype=np.uint8)
+    _check(_lib.hp_c0_maps(c0, gid.ctypes.data, sign.ctypes.data, bnd.ctypes.data), "hp_c0_maps")
+    return gid, sign, bnd
+
+
+def hp_c0_gather(c0, glob, loc, stream=None):
+    _check(_lib.hp_c0_gather(c0, _ptr(glob), _ptr(loc), _stream(stream)), "hp_c0_gather")
+
+
+def hp_c0_assemble(c0, loc, glob, mask_boundary=True, stream=None):
+    _check(_lib.hp_c0_assemble(c0, _ptr(loc), _ptr(glob), 1 if mask_boundary else 0, _stream(stream)),
+           "hp_c0_assemble")
+
+
+def hp_solve(c0, lam, rhs, x, tol=1e-10, max_iter=20000, mixed=False, inner_tol=1e-5, inner_max_iter=20000,
+             max_refinements=20, stream=None):
+    """Returns (status, stats); raises for errors other than HP_ERR_NOT_CONVERGED."""
+    o = hp_solve_opts(float(tol), int(max_iter), 1 if mixed else 0, float(inner_tol), int(inner_max_iter),
+                      int(max_refinements))
+    st = hp_solve_stats()
+    rc = _lib.hp_solve(c0, float(lam), _ptr(rhs), _ptr(x), ctypes.byref(o), ctypes.byref(st), _stream(stream))
+    if rc not in (HP_OK, HP_ERR_NOT_CONVERGED):
+        raise HpError(rc, "hp_solve")
+    return rc, dict(iterations=st.iterations, inner_iterations=st.inner_iterations, refinements=st.refinements,
+                    rel_residual=st.rel_residual)
+
+
+def hp_c0_destroy(c0):
+    _lib.hp_c0_destroy(c0)

@@ -251,3 +251,130 @@ def random_phys(seed, offsets, ncomp=1):
     offsets = np.asarray(offsets, dtype=np.int64)
     out = [random_coefficients(seed * 7 + 3 + c, offsets) for c in range(ncomp)]
     return np.concatenate(out) if ncomp > 1 else out[0]
+
+
+# ---------------------------------------------------------------------------
+# conforming four-slab mesh (for C0 assembly)
+# ---------------------------------------------------------------------------
+def _kuhn_split(face):
+    """Two triangles of a cube face given as 4 corner (ids, local xyz) in cyclic
+    order, split by the diagonal joining the corners of smallest and largest
+    local x+y+z (the diagonal the Kuhn tetrahedra of both adjacent cubes use)."""
+    sums = [sum(c[1]) for c in face]
+    lo = int(np.argmin(sums))
+    hi = (lo + 2) % 4
+    a, b = (lo + 1) % 4, (lo + 3) % 4
+    return [(face[lo][0], face[a][0], face[hi][0]), (face[lo][0], face[b][0], face[hi][0])]
+
+
+def c0_slab_mesh(n, order, *, curved=True, deformation=1, nx=None, ny=None):
+    """Conforming mixed mesh of the unit cube in n*n*n cells (n divisible by 4):
+    slabs of hexes, prisms, pyramids and tetrahedra along z as in slab_mesh, plus
+    a transition layer (the first tet-slab layer) where each cube holds the
+    pyramid on its bottom face and ten tetrahedra: the other five faces split by
+    their Kuhn diagonal, each half joined to the cube centre.  Local vertex
+    orders make shared faces agree for a C0 modal basis: every tetrahedron has
+    its two largest global ids at local vertices 2 and 3 (vertex 3 largest), every
+    prism triangle has its largest id at the collapsed local vertices (4, 5), and
+    pyramid apexes (cube centres) have ids above all grid vertices.  Element
+    orientation is made positive by swapping local vertices 0 and 1 (tets) or the
+    two non-collapsed triangle vertices (prisms)."""
+    if n % 4:
+        raise ValueError("n must be divisible by 4")
+    nx = n if nx is None else nx
+    ny = n if ny is None else ny
+    per = n // 4
+    hv = np.array([1.0 / nx, 1.0 / ny, 1.0 / n])
+    NX, NY, NZ = nx + 1, ny + 1, n + 1
+    gid = lambda i, j, k: (k * NY + j) * NX + i
+    I, J, K = np.meshgrid(np.arange(NX), np.arange(NY), np.arange(NZ), indexing="ij")
+    grid = np.zeros((NX * NY * NZ, 3))
+    grid[gid(I, J, K).ravel()] = np.stack([I.ravel(), J.ravel(), K.ravel()], axis=1) * hv
+    shapes, verts = [], []
+    centres = []
+
+    def cells(k0, k1):
+        i, j, k = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(k0, k1), indexing="ij")
+        return i.ravel(), j.ravel(), k.ravel()
+
+    def corner(i, j, k, d):
+        return gid(i + d[0], j + d[1], k + d[2])
+
+    def add(shape, V):
+        V = np.asarray(V, dtype=np.int64)
+        row = np.full((V.shape[0], 8), -1, dtype=np.int64)
+        row[:, :V.shape[1]] = V
+        shapes.append(np.full(V.shape[0], shape, dtype=np.uint8))
+        verts.append(row)
+
+    # hexes
+    i, j, k = cells(0, per)
+    keys = [(0, 0, 0), (1, 0, 0), (1, 1, 0), (0, 1, 0), (0, 0, 1), (1, 0, 1), (1, 1, 1), (0, 1, 1)]
+    add(HEX, np.stack([corner(i, j, k, d) for d in keys], axis=1))
+    # prisms: triangles in the (y, z) square split by the y = z diagonal; the
+    # collapsed vertex is the triangle's corner of largest id, here (y, z) = (1, 1)
+    i, j, k = cells(per, 2 * per)
+    for A, B in (((1, 0), (0, 0)), ((0, 1), (0, 0))):
+        C = (1, 1)
+        V = np.stack([corner(i, j, k, (0,) + A), corner(i, j, k, (0,) + B), corner(i, j, k, (1,) + B),
+                      corner(i, j, k, (1,) + A), corner(i, j, k, (0,) + C), corner(i, j, k, (1,) + C)], axis=1)
+        add(PRISM, V)
+    # pyramids: 6 per cube around the centre; centres numbered after the grid
+    pyr_faces = [
+        [(0, 0, 0), (1, 0, 0), (1, 1, 0), (0, 1, 0)], [(0, 0, 1), (0, 1, 1), (1, 1, 1), (1, 0, 1)],
+        [(0, 0, 0), (0, 0, 1), (1, 0, 1), (1, 0, 0)], [(0, 1, 0), (1, 1, 0), (1, 1, 1), (0, 1, 1)],
+        [(0, 0, 0), (0, 1, 0), (0, 1, 1), (0, 0, 1)], [(1, 0, 0), (1, 0, 1), (1, 1, 1), (1, 1, 0)]]
+    i, j, k = cells(2 * per, 3 * per)
+    c0 = NX * NY * NZ
+    cid = c0 + np.arange(len(i))
+    centres.append(np.stack([i + 0.5, j + 0.5, k + 0.5], axis=1) * hv)
+    for f in pyr_faces:
+        add(PYR, np.stack([corner(i, j, k, d) for d in f] + [cid], axis=1))
+    # transition layer: bottom pyramid + 10 tets per cube
+    i, j, k = cells(3 * per, 3 * per + 1)
+    c0 = NX * NY * NZ + sum(len(c) for c in centres)
+    cid = c0 + np.arange(len(i))
+    centres.append(np.stack([i + 0.5, j + 0.5, k + 0.5], axis=1) * hv)
+    add(PYR, np.stack([corner(i, j, k, d) for d in pyr_faces[0]] + [cid], axis=1))
+    tets = []
+    for f in pyr_faces[1:]:
+        face = [(d, d) for d in f]
+        for tri in _kuhn_split(face):
+            tets.append(np.stack([corner(i, j, k, d) for d in tri] + [cid], axis=1))
+    # Kuhn tets in the remaining layers
+    i, j, k = cells(3 * per + 1, n)
+    for perm in itertools.permutations(range(3)):
+        p = [0, 0, 0]
+        path = [tuple(p)]
+        for ax in perm[:2]:
+            p[ax] = 1
+            path.append(tuple(p))
+        path.append((1, 1, 1))
+        tets.append(np.stack([corner(i, j, k, d) for d in path], axis=1))
+    xyz = np.concatenate([grid] + centres, axis=0)
+    T = np.concatenate(tets, axis=0)
+    T = np.sort(T, axis=1)                          # ascending ids: vertex 3 largest, 2 second
+    X = xyz[T]
+    det = np.einsum("ij,ij->i", X[:, 1] - X[:, 0], np.cross(X[:, 2] - X[:, 0], X[:, 3] - X[:, 0]))
+    swap = det < 0
+    T[swap, 0], T[swap, 1] = T[swap, 1].copy(), T[swap, 0].copy()
+    add(TET, T)
+    shape = np.concatenate(shapes)
+    vert = np.concatenate(verts)
+    # positive orientation for the other shapes: prisms swap the two
+    # non-collapsed triangle vertices (0<->1, 3<->2), pyramids reverse the base
+    Xv = lambda e, v: xyz[vert[e, v]]
+    for s, v1, v2, v3, perm in ((PRISM, 1, 3, 4, [1, 0, 3, 2, 4, 5, 6, 7]), (PYR, 1, 3, 4, [0, 3, 2, 1, 4, 5, 6, 7]),
+                                (HEX, 1, 3, 4, [0, 3, 2, 1, 4, 7, 6, 5])):
+        e = np.nonzero(shape == s)[0]
+        if len(e) == 0:
+            continue
+        d = np.einsum("ij,ij->i", Xv(e, v1) - Xv(e, 0), np.cross(Xv(e, v3) - Xv(e, 0), Xv(e, v2) - Xv(e, 0)))
+        # d = (E1 . (E3 x E2)) = -det(E1, E2, E3)
+        bad = e[d > 0]
+        vert[bad] = vert[bad][:, perm]
+    n_elem = len(shape)
+    P = np.full(n_elem, int(order), dtype=np.uint8)
+    return dict(n_elem=n_elem, shape=shape, P=P, Q=(P + 2).astype(np.uint8), vert=vert,
+                xyz=np.ascontiguousarray(xyz), n_vert=xyz.shape[0],
+                curved=np.full(n_elem, 1 if curved else 0, dtype=np.uint8), deformation=int(deformation))
