@@ -42,6 +42,8 @@ def parse():
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     p.add_argument("--costmodel", action="store_true",
                    help="run the learned cost-model pipeline (timings, GPU training, held-out schedules) instead")
+    p.add_argument("--solve", action="store_true",
+                   help="assembled Helmholtz solve (time to 1e-10): FP64 PCG vs mixed FP32 PCG + FP64 refinement")
     p.add_argument("--no-extra", action="store_true", help="skip the p-adaptive batched measurement")
     p.add_argument("--orders", default=None, help="comma-separated orders (default 1..8); for profiling runs")
     p.add_argument("--cells", type=int, default=None, help="cells per direction (default 16); for profiling runs")
@@ -443,9 +445,68 @@ def run_costmodel(local):
                                                           "orders": "U{3..9}", "curved": "x >= 0.5"}}), flush=True)
 
 
+def run_solve(local, cells, order=4, lam=1.0, tol=1e-10):
+    """Time to solution of the C0-assembled Helmholtz problem on the conforming
+    four-slab mesh (cells^3 cells + pyramid-to-tet transition layer, curved),
+    P = order, f = (3 pi^2 + lambda) sin(pi x) sin(pi y) sin(pi z)."""
+    import torch
+    from paper_2604_04644_gb300 import hp, inputs
+    torch.cuda.set_device(local)
+    dev = "cuda:%d" % local
+    t0 = time.time()
+    mesh = inputs.c0_slab_mesh(cells, order, curved=True)
+    h = hp.hp_mesh_create(mesh, local)
+    co, po, nc, nph = hp.hp_mesh_layout(h, mesh["n_elem"])
+    t_mesh = time.time() - t0
+    t0 = time.time()
+    c0 = hp.hp_c0_create(h)
+    ng, nb = hp.hp_c0_info(c0)
+    t_c0 = time.time() - t0
+    xyz = torch.empty(3 * nph, device=dev, dtype=torch.float64)
+    hp.hp_mesh_points(h, xyz)
+    x, y, z = xyz.view(3, -1)
+    f = (3 * np.pi ** 2 + lam) * torch.sin(np.pi * x) * torch.sin(np.pi * y) * torch.sin(np.pi * z)
+    del xyz, x, y, z
+    ip = hp.hp_op_create(h, hp.HP_IPRODUCT_WRT_BASE)
+    bl = torch.empty(nc, device=dev, dtype=torch.float64)
+    hp.hp_op_apply(ip, 1.0, f.contiguous(), bl)
+    hp.hp_op_destroy(ip)
+    del f
+    b = torch.empty(ng, device=dev, dtype=torch.float64)
+    hp.hp_c0_assemble(c0, bl, b, True)
+    del bl
+    out = {"workload": "helmholtz_c0_solve_%dcube_P%d_curved" % (cells, order), "elements": int(mesh["n_elem"]),
+           "local_dofs": int(nc), "global_dofs": int(ng), "dirichlet_dofs": int(nb), "tol": tol,
+           "setup_s": {"mesh": round(t_mesh, 2), "c0_map": round(t_c0, 2)}}
+    # warm-up (builds the Jacobi diagonal, operators and workspaces) then timed solves
+    xw = torch.zeros(ng, device=dev, dtype=torch.float64)
+    hp.hp_solve(c0, lam, b, xw, tol=1e-2, mixed=True, inner_tol=1e-1, max_refinements=1)
+    hp.hp_solve(c0, lam, b, xw, tol=1e-2)
+    sols = {}
+    for name, kw in (("fp64_pcg", dict(mixed=False)), ("mixed_fp32_pcg_fp64_ir", dict(mixed=True, inner_tol=1e-4))):
+        xs = torch.zeros(ng, device=dev, dtype=torch.float64)
+        torch.cuda.synchronize(dev)
+        t0 = time.time()
+        rc, st = hp.hp_solve(c0, lam, b, xs, tol=tol, **kw)
+        torch.cuda.synchronize(dev)
+        dt = time.time() - t0
+        out[name] = dict(st, seconds=round(dt, 4), status=hp.hp_status_str(rc))
+        sols[name] = xs
+    d = sols["fp64_pcg"] - sols["mixed_fp32_pcg_fp64_ir"]
+    out["rel_diff_mixed_vs_fp64"] = float(d.norm() / sols["fp64_pcg"].norm())
+    out["speedup_mixed_vs_fp64"] = round(out["fp64_pcg"]["seconds"] / out["mixed_fp32_pcg_fp64_ir"]["seconds"], 3)
+    hp.hp_c0_destroy(c0)
+    hp.hp_mesh_destroy(h)
+    print(json.dumps({"solve": out}), flush=True)
+
+
 def main():
     args = parse()
     world, rank, local = dist_init(args)
+    if args.solve:
+        if rank == 0:
+            run_solve(local, args.cells or 64)
+        return
     if args.costmodel:
         if rank == 0:
             run_costmodel(local)

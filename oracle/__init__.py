@@ -15,4 +15,4 @@ CUDA library; the only common module is the seeded input generator.
 Parity status: every function here is pinned by ``tests/test_oracle_*.py``
 (closed forms, invariants, brute-force cross-checks); none is unpinned.
 """
-from . import jacobi, quadrature, basis, geometry, operators, mlp  # noqa: F401
+from . import jacobi, quadrature, basis, geometry, operators, mlp, assembly  # noqa: F401

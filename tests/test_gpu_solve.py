@@ -1,0 +1,142 @@
+"""Assembled Helmholtz solve on the GPU: gather/assembly maps, FP64 PCG and
+mixed FP32 PCG + FP64 refinement against the oracle's independent
+(null-space) solve, and spectral convergence to a manufactured solution."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import assembly, operators as oracle_ops  # noqa: E402
+from paper_2604_04644_gb300 import inputs  # noqa: E402
+
+LAM = 1.0
+
+
+@pytest.fixture(scope="module")
+def hp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2604_04644_gb300 import hp as _hp
+    return _hp
+
+
+def u_exact(x, y, z):
+    return np.sin(np.pi * x) * np.sin(np.pi * y) * np.sin(np.pi * z)
+
+
+def f_rhs(x, y, z):
+    return (3 * np.pi ** 2 + LAM) * u_exact(x, y, z)
+
+
+class Problem:
+    """Mesh, C0 map and right-hand side assembled with the library's kernels."""
+
+    def __init__(self, hp, mesh):
+        self.hp, self.mesh = hp, mesh
+        self.h = hp.hp_mesh_create(mesh, 0)
+        self.co, self.po, self.nc, self.nph = hp.hp_mesh_layout(self.h, mesh["n_elem"])
+        self.c0 = hp.hp_c0_create(self.h)
+        self.ng, self.nb = hp.hp_c0_info(self.c0)
+        xyz = torch.empty(3 * self.nph, device="cuda:0", dtype=torch.float64)
+        hp.hp_mesh_points(self.h, xyz)
+        x, y, z = xyz.view(3, -1)
+        f = (3 * np.pi ** 2 + LAM) * torch.sin(np.pi * x) * torch.sin(np.pi * y) * torch.sin(np.pi * z)
+        self.xyz = xyz
+        ip = hp.hp_op_create(self.h, hp.HP_IPRODUCT_WRT_BASE)
+        bl = torch.empty(self.nc, device="cuda:0", dtype=torch.float64)
+        hp.hp_op_apply(ip, 1.0, f.contiguous(), bl)
+        hp.hp_op_destroy(ip)
+        self.b = torch.empty(self.ng, device="cuda:0", dtype=torch.float64)
+        hp.hp_c0_assemble(self.c0, bl, self.b, True)
+        self.bwd = hp.hp_op_create(self.h, hp.HP_BWDTRANS)
+
+    def values(self, xg):
+        """Solution values at the quadrature points from a global vector."""
+        loc = torch.empty(self.nc, device="cuda:0", dtype=torch.float64)
+        self.hp.hp_c0_gather(self.c0, xg, loc)
+        out = torch.empty(self.nph, device="cuda:0", dtype=torch.float64)
+        self.hp.hp_op_apply(self.bwd, 1.0, loc, out)
+        torch.cuda.synchronize()
+        return out.cpu().numpy()
+
+    def close(self):
+        self.hp.hp_op_destroy(self.bwd)
+        self.hp.hp_c0_destroy(self.c0)
+        self.hp.hp_mesh_destroy(self.h)
+
+
+def test_gather_and_assembly_match_host_maps(hp):
+    mesh = inputs.c0_slab_mesh(4, 3, curved=True)
+    pr = Problem(hp, mesh)
+    try:
+        gid, sign, bnd = hp.hp_c0_maps(pr.c0, pr.nc)
+        gid2, sign2, bnd2, ng2 = hp.hp_c0_map_host(mesh, pr.nc)
+        assert ng2 == pr.ng and np.array_equal(gid, gid2) and np.array_equal(sign, sign2) and np.array_equal(bnd, bnd2)
+        rng = np.random.default_rng(0)
+        g = rng.uniform(-1, 1, pr.ng)
+        loc = torch.empty(pr.nc, device="cuda:0", dtype=torch.float64)
+        hp.hp_c0_gather(pr.c0, torch.tensor(g, device="cuda:0"), loc)
+        np.testing.assert_array_equal(loc.cpu().numpy(), sign * g[gid])      # integer map: exact
+        l = rng.uniform(-1, 1, pr.nc)
+        out = torch.empty(pr.ng, device="cuda:0", dtype=torch.float64)
+        hp.hp_c0_assemble(pr.c0, torch.tensor(l, device="cuda:0"), out, False)
+        ref = np.zeros(pr.ng)
+        np.add.at(ref, gid, sign * l)
+        np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=0, atol=1e-14)
+        hp.hp_c0_assemble(pr.c0, torch.tensor(l, device="cuda:0"), out, True)
+        assert (out.cpu().numpy()[bnd > 0] == 0).all()
+    finally:
+        pr.close()
+
+
+@pytest.mark.parametrize("mixed", [False, True])
+def test_solve_matches_oracle(hp, mixed):
+    mesh = inputs.c0_slab_mesh(8, 3, curved=True, nx=1, ny=1)
+    pr = Problem(hp, mesh)
+    try:
+        x = torch.zeros(pr.ng, device="cuda:0", dtype=torch.float64)
+        rc, stats = hp.hp_solve(pr.c0, LAM, pr.b, x, tol=1e-12, mixed=mixed, inner_tol=1e-4)
+        assert rc == hp.HP_OK and stats["rel_residual"] <= 1e-12, stats
+        vals = pr.values(x)
+        ul = assembly.solve(mesh, LAM, f_rhs)
+        ref = oracle_ops.apply("bwd_trans", mesh, ul)
+        assert np.abs(vals - ref).max() <= 1e-9 * np.abs(ref).max()
+    finally:
+        pr.close()
+
+
+def test_manufactured_convergence_and_mixed_equals_fp64(hp):
+    errs = []
+    for P in (2, 3, 4, 5):
+        mesh = inputs.c0_slab_mesh(4, P, curved=False)
+        pr = Problem(hp, mesh)
+        try:
+            x64 = torch.zeros(pr.ng, device="cuda:0", dtype=torch.float64)
+            rc, s64 = hp.hp_solve(pr.c0, LAM, pr.b, x64, tol=1e-10)
+            assert rc == hp.HP_OK
+            xm = torch.zeros_like(x64)
+            rc, sm = hp.hp_solve(pr.c0, LAM, pr.b, xm, tol=1e-10, mixed=True, inner_tol=1e-4)
+            assert rc == hp.HP_OK and sm["refinements"] >= 1
+            v64 = pr.values(x64)
+            vm = pr.values(xm)
+            assert np.abs(v64 - vm).max() <= 1e-8 * np.abs(v64).max()
+            pts = pr.xyz.view(3, -1).cpu().numpy()
+            errs.append(np.abs(v64 - u_exact(*pts)).max())
+        finally:
+            pr.close()
+    for a, b in zip(errs, errs[1:]):
+        assert b < a / 2.5, errs
+
+
+def test_solver_argument_checks(hp):
+    mesh = inputs.c0_slab_mesh(4, 2, curved=False)
+    pr = Problem(hp, mesh)
+    try:
+        x = torch.zeros(pr.ng, device="cuda:0", dtype=torch.float64)
+        with pytest.raises(hp.HpError):
+            hp.hp_solve(pr.c0, LAM, pr.b, x, tol=-1.0)
+        rc, st = hp.hp_solve(pr.c0, LAM, pr.b, x, tol=1e-14, max_iter=2)
+        assert rc == hp.HP_ERR_NOT_CONVERGED and st["iterations"] == 2
+    finally:
+        pr.close()
