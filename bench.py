@@ -491,6 +491,8 @@ def run_solve(local, cells, order=4, lam=1.0, tol=1e-10):
         torch.cuda.synchronize(dev)
         dt = time.time() - t0
         out[name] = dict(st, seconds=round(dt, 4), status=hp.hp_status_str(rc))
+        if rc:
+            out[name]["error"] = hp.hp_last_error()
         sols[name] = xs
     d = sols["fp64_pcg"] - sols["mixed_fp32_pcg_fp64_ir"]
     out["rel_diff_mixed_vs_fp64"] = float(d.norm() / sols["fp64_pcg"].norm())

@@ -280,6 +280,11 @@ hp_status hp_c0_gather(hp_c0 c0, const double* global, double* local, void* stre
  * order (deterministic); Dirichlet entries set to 0 if mask_boundary. */
 hp_status hp_c0_assemble(hp_c0 c0, const double* local, double* global, int mask_boundary, void* stream);
 
+/* Diagonal of lambda M + L: assembled (the Jacobi preconditioner; local = 0,
+ * diag[n_global], Dirichlet entries included) or per element (local = 1,
+ * diag[n_coeff], the diagonals of the element matrices in the coefficient layout). */
+hp_status hp_c0_diagonal(hp_c0 c0, double lambda, double* diag, int local, void* stream);
+
 typedef struct {
     double tol;            /* stop at ||b - A x|| <= tol ||b|| (FP64 residual)                 */
     int max_iter;          /* FP64 CG: iteration limit                                          */

@@ -11,6 +11,7 @@
 // pipe).
 #include <algorithm>
 #include <cmath>
+#include <string>
 #include <vector>
 
 #include "hp_internal.h"
@@ -61,6 +62,18 @@ __global__ void assemble_kernel(int64_t n, const int64_t* __restrict__ rowptr, c
         T acc = T(0);
         if (!(mask && bnd[r]))
             for (int64_t k = rowptr[r]; k < rowptr[r + 1]; ++k) acc += csign[k] > 0 ? l[col[k]] : -l[col[k]];
+        g[r] = acc;
+    }
+}
+
+// diagonal of A^T H A: each local copy contributes sign^2 = 1 times its element diagonal
+__global__ void assemble_diag_kernel(int64_t n, const int64_t* __restrict__ rowptr, const int64_t* __restrict__ col,
+                                     const double* __restrict__ l, double* __restrict__ g) {
+    int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (; r < n; r += stride) {
+        double acc = 0.0;
+        for (int64_t k = rowptr[r]; k < rowptr[r + 1]; ++k) acc += l[col[k]];
         g[r] = acc;
     }
 }
@@ -193,8 +206,8 @@ hp_status prepare(hp_c0 c, double lambda, bool mixed, cudaStream_t s) {
             cudaError_t e = launch_elem_diag(b, c->mesh->blobs.at(b.shape * 16 + b.P), lambda, c->d_loc64[0], s);
             if (e != cudaSuccess) return cuda_fail(e, "element diagonal");
         }
-        assemble_kernel<double><<<blocks_for(c->n_global), 256, 0, s>>>(c->n_global, c->d_rowptr, c->d_col,
-                                                                      c->d_csign, c->d_bnd, 0, c->d_loc64[0], c->d_diag);
+        assemble_diag_kernel<<<blocks_for(c->n_global), 256, 0, s>>>(c->n_global, c->d_rowptr, c->d_col,
+                                                                    c->d_loc64[0], c->d_diag);
         cudaError_t e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return cuda_fail(e, "element diagonal");
         c->diag_lambda = lambda;
@@ -231,7 +244,8 @@ hp_status pcg(hp_c0 c, hp_op op, double lambda, const T* b, T* x, T* r, T* z, T*
         double pq = 0;
         if ((st = dot(c, p, q, n, &pq, s))) return st;
         if (!(pq > 0)) {
-            set_error("hp_solve: CG breakdown (p^T A p <= 0 or not finite)");
+            set_error("hp_solve: CG breakdown (p^T A p = " + std::to_string(pq) + " at iteration " +
+                      std::to_string(it) + ", r.z = " + std::to_string(rz) + ", ||b|| = " + std::to_string(bnorm) + ")");
             return HP_ERR_NOT_CONVERGED;
         }
         const double alpha = rz / pq;
@@ -252,6 +266,7 @@ hp_status pcg(hp_c0 c, hp_op op, double lambda, const T* b, T* x, T* r, T* z, T*
         rz = rz_new;
         xpby_kernel<T><<<blocks_for(n), 256, 0, s>>>(n, z, (T)beta, p);
     }
+    set_error("hp_solve: CG did not reach the tolerance in the iteration limit");
     return HP_ERR_NOT_CONVERGED;
 }
 
@@ -357,6 +372,24 @@ hp_status hp_c0_assemble(hp_c0 c, const double* local, double* global, int mask_
     return e == cudaSuccess ? HP_OK : cuda_fail(e, "hp_c0_assemble");
 }
 
+hp_status hp_c0_diagonal(hp_c0 c, double lambda, double* diag, int local, void* stream) {
+    if (!c || !diag) { set_error("hp_c0_diagonal: null argument"); return HP_ERR_ARG; }
+    cudaSetDevice(c->mesh->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    hp_status st = prepare(c, lambda, false, s);
+    if (st) return st;
+    cudaError_t e;
+    if (local) {
+        for (const Block& b : c->mesh->blocks) {
+            e = launch_elem_diag(b, c->mesh->blobs.at(b.shape * 16 + b.P), lambda, diag, s);
+            if (e != cudaSuccess) return cuda_fail(e, "hp_c0_diagonal");
+        }
+        return HP_OK;
+    }
+    e = cudaMemcpyAsync(diag, c->d_diag, sizeof(double) * c->n_global, cudaMemcpyDeviceToDevice, s);
+    return e == cudaSuccess ? HP_OK : cuda_fail(e, "hp_c0_diagonal");
+}
+
 hp_status hp_solve(hp_c0 c, double lambda, const double* rhs, double* x, const hp_solve_opts* opts,
                    hp_solve_stats* stats, void* stream) {
     if (!c || !rhs || !x || !opts) { set_error("hp_solve: null argument"); return HP_ERR_ARG; }
@@ -423,7 +456,6 @@ hp_status hp_solve(hp_c0 c, double lambda, const double* rhs, double* x, const h
         if (st) set_error("hp_solve: refinement did not reach the tolerance");
     }
     if (stats) *stats = S;
-    if (st == HP_ERR_NOT_CONVERGED && !opts->mixed) set_error("hp_solve: CG did not reach the tolerance");
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "hp_solve");
     return st;

@@ -34,7 +34,7 @@ EXPORTED = ["hp_mesh_create", "hp_mesh_layout", "hp_geom_factors", "hp_geom_copy
             "hp_op_destroy", "hp_mesh_destroy", "hp_status_str", "hp_last_error",
             "hp_mlp_create", "hp_mlp_info", "hp_mlp_params", "hp_mlp_forward", "hp_mlp_grad", "hp_mlp_adam_step",
             "hp_mlp_destroy", "hp_mlp_grad_noalloc", "hp_mesh_points", "hp_c0_create", "hp_c0_info",
-            "hp_c0_map_host", "hp_c0_maps", "hp_c0_gather", "hp_c0_assemble", "hp_solve", "hp_c0_destroy"]
+            "hp_c0_map_host", "hp_c0_maps", "hp_c0_gather", "hp_c0_assemble", "hp_solve", "hp_c0_destroy", "hp_c0_diagonal"]
 
 
 class HpError(RuntimeError):
@@ -294,6 +294,8 @@ _lib.hp_c0_assemble.argtypes = [_vp, _vp, _vp, ctypes.c_int, _vp]
 _lib.hp_solve.argtypes = [_vp, ctypes.c_double, _vp, _vp, ctypes.POINTER(hp_solve_opts),
                           ctypes.POINTER(hp_solve_stats), _vp]
 _lib.hp_c0_destroy.argtypes = [_vp]
+_lib.hp_c0_diagonal.argtypes = [_vp, ctypes.c_double, _vp, ctypes.c_int, _vp]
+_lib.hp_c0_diagonal.restype = ctypes.c_int
 for _f in ("hp_mesh_points", "hp_c0_create", "hp_c0_info", "hp_c0_map_host", "hp_c0_maps", "hp_c0_gather",
            "hp_c0_assemble", "hp_solve"):
     getattr(_lib, _f).restype = ctypes.c_int
@@ -373,3 +375,7 @@ def hp_solve(c0, lam, rhs, x, tol=1e-10, max_iter=20000, mixed=False, inner_tol=
 
 def hp_c0_destroy(c0):
     _lib.hp_c0_destroy(c0)
+
+
+def hp_c0_diagonal(c0, lam, diag, local=False, stream=None):
+    _check(_lib.hp_c0_diagonal(c0, float(lam), _ptr(diag), 1 if local else 0, _stream(stream)), "hp_c0_diagonal")

@@ -199,3 +199,16 @@ def test_error_paths(hp):
         assert ei.value.status == hp.HP_ERR_ARG
     finally:
         hp.hp_mesh_destroy(h)
+
+
+@pytest.mark.parametrize("P", [2, 4, 5])
+@pytest.mark.parametrize("curved", [False, True])
+def test_fp64_on_conforming_mesh_orientations(hp, P, curved):
+    """The conforming mesh's element orientations (vertices sorted by id, swaps
+    for positive volume) against the oracle, Helmholtz and mass."""
+    mesh = inputs.c0_slab_mesh(4, P, curved=curved)
+    for opname in ("helmholtz", "mass"):
+        x = make_input(mesh, opname, 500 + P)
+        ref = oracle_ops.apply(opname, mesh, x, 1.0)
+        y = run_op(hp, mesh, opname, x, 1.0)
+        assert rel_err(y, ref) <= FP64_TOL, (opname, rel_err(y, ref))
