@@ -56,13 +56,16 @@ def parse():
     return a
 
 
-def dist_init(args):
+def dist_init(args, backend=None):
+    """One process per GPU (torchrun environment); NCCL for the GPU arm, gloo
+    for the CPU reference arm (and for the host-path tests)."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch.distributed as dist
-        backend = "nccl" if args.impl == "gb300" else "gloo"
+        if backend is None:
+            backend = "nccl" if args.impl == "gb300" else "gloo"
         dist.init_process_group(backend=backend)
     return world, rank, local
 
@@ -81,6 +84,14 @@ def max_over_ranks(world, x, device=None):
     t = torch.tensor([x], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def weak_scaling_value(world, dofs_per_rank, ms_step, device=None):
+    """Whole-job throughput under weak scaling: every rank applies the same
+    workload to its own GPU; the step time is the slowest rank's.  Returns
+    (max-over-ranks ms per step, total GDOF/s over all ranks)."""
+    ms_max = max_over_ranks(world, ms_step, device=device)
+    return ms_max, world * dofs_per_rank / (ms_max * 1e-3) / 1e9
 
 
 class ClockSampler:
@@ -522,12 +533,11 @@ def main():
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda:%d" % local)  # 256 MiB > L2
     with ClockSampler(local) as clk:
         per = time_applies(work, args.steps, args.warmup, local, world, flush)
-    ms_step = float(per.sum(axis=1).mean())
-    ms_step = max_over_ranks(world, ms_step, device="cuda:%d" % local)
     dofs_step = sum(w["dofs"] for w in work)
     flops_step = sum(w["flops"] for w in work)
     bytes_step = sum(w["bytes"] for w in work)
-    value = world * dofs_step / (ms_step * 1e-3) / 1e9
+    ms_step, value = weak_scaling_value(world, dofs_step, float(per.sum(axis=1).mean()),
+                                        device="cuda:%d" % local)
     e2e = time_e2e(work, max(2, args.steps // 2), local)
     launches = args.steps * sum(w["nblocks"] for w in work)
     per_order = {}
