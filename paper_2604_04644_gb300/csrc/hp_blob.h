@@ -11,9 +11,37 @@ __host__ __device__ constexpr int n_modes_c(int shape, int P) {
                       : (P + 1) * (P + 2) * (P + 3) / 6;
 }
 
+// Index structure of the collapsed shapes at compile time: weight of member a
+// of family 0, family of the eta2 factor of slot (a, .), family of the eta3
+// factor of slot (a, b, .), family lengths, and the number of valid (a, b)
+// pairs and valid slots (the triangular / pyramidal index ranges).
+__host__ __device__ constexpr int wA_c(int a) { return a <= 1 ? 0 : a - 1; }
+__host__ __device__ constexpr int famlen_c(int P, int s) { return s == 0 ? P + 1 : (s >= P ? 0 : P - s); }
+__host__ __device__ constexpr int famb_c(int shape, int a) { return shape == 3 ? wA_c(a) : 0; }
+__host__ __device__ constexpr int lenb_c(int shape, int P, int a) { return famlen_c(P, famb_c(shape, a)); }
+__host__ __device__ constexpr int famc_c(int shape, int P, int a, int b) {
+    return shape == 0 ? 0
+         : shape == 1 ? wA_c(a)
+         : shape == 2 ? (wA_c(a) > wA_c(b) ? wA_c(a) : wA_c(b))
+         : (a <= 1 ? wA_c(b) : (b < P - wA_c(a) ? wA_c(a) + b : P));
+}
+__host__ __device__ constexpr int npairs_c(int shape, int P) {
+    int t = 0;
+    for (int a = 0; a <= P; ++a) t += lenb_c(shape, P, a);
+    return t;
+}
+__host__ __device__ constexpr int nvalid_c(int shape, int P) {
+    int t = 0;
+    for (int a = 0; a <= P; ++a)
+        for (int b = 0; b < lenb_c(shape, P, a); ++b) t += famlen_c(P, famc_c(shape, P, a, b));
+    return t;
+}
+
 struct BlobLayout {
     int Ta, Tb, Tc, D, z, w, total_vals;                  // offsets in values
-    int famb, famc, slot2mode, mode_slots, total_bytes;   // offsets in bytes
+    int famb, famc, slot2mode, mode_slots;                // offsets in bytes
+    int pairs, valid, poff, porder, total_bytes;          // valid (a,b) pairs and slots (int32), pair
+                                                          // offset per a (int16), pairs by length (uint8)
 };
 
 __host__ __device__ constexpr int align16c(int x) { return (x + 15) & ~15; }
@@ -35,6 +63,12 @@ __host__ __device__ constexpr BlobLayout blob_layout_c(int shape, int P, int vs)
     b = (b + 1) & ~1;
     L.slot2mode = b; b += 2 * n * n * n;
     L.mode_slots = b; b += 2 * 4 * n_modes_c(shape, P);
+    b = (b + 3) & ~3;
+    const bool lists = shape != 0;                  // the hexahedron has no padding to skip
+    L.pairs = b; b += lists ? 4 * npairs_c(shape, P) : 0;
+    L.valid = b; b += lists ? 4 * nvalid_c(shape, P) : 0;
+    L.poff = b; b += lists ? 2 * (n + 1) : 0;
+    L.porder = b; b += lists ? npairs_c(shape, P) : 0;
     L.total_bytes = align16c(b);
     return L;
 }

@@ -79,6 +79,12 @@ __global__ void __launch_bounds__(256) sf_kernel(const __grid_constant__ SFArgs<
     const uint8_t* famc = tab + L.famc;
     const int16_t* slot2mode = reinterpret_cast<const int16_t*>(tab + L.slot2mode);
     const int16_t* mode_slots = reinterpret_cast<const int16_t*>(tab + L.mode_slots);
+    // valid index sets of the collapsed shapes (the hexahedron indexes directly)
+    constexpr int NPR = npairs_c(SHAPE, P), NVL = nvalid_c(SHAPE, P);
+    const int32_t* pairs = reinterpret_cast<const int32_t*>(tab + L.pairs);
+    const int32_t* valid = reinterpret_cast<const int32_t*>(tab + L.valid);
+    const int16_t* poff = reinterpret_cast<const int16_t*>(tab + L.poff);
+    const uint8_t* porder = tab + L.porder;
     T* S1 = reinterpret_cast<T*>(tab + L.total_bytes);   // [EPB][4*NQ]: u, v1, v2, v3
     T* S2 = S1 + EPB * 4 * NQ;                            // [EPB][NQ]
 
@@ -105,27 +111,53 @@ __global__ void __launch_bounds__(256) sf_kernel(const __grid_constant__ SFArgs<
                 S2[e * NQ + sl] = v;
             }
             __syncthreads();
-            // eta3 pass: f[a][b][k] = sum_c Tc[s(a,b)][c][k] uhat[a][b][c]
-            for (int idx = tid; idx < EPB * n * n * Q; idx += NT) {
-                int e = idx / (n * n * Q), r = idx - e * (n * n * Q);
-                int ab = r / Q, k = r - ab * Q;
-                const T* tc = Tc + famc[ab] * n * Q + k;
-                const T* x = S2 + e * NQ + ab * n;
+            // eta3 pass over the valid (a,b) pairs p (compact, a-major):
+            // f[p][k] = sum_{c < len(p)} Tc[s(a,b)][c][k] uhat[a][b][c]; pairs taken
+            // in order of decreasing length so that a warp's loops end together
+            for (int idx = tid; idx < EPB * NPR * Q; idx += NT) {
+                int e = idx / (NPR * Q), r = idx - e * (NPR * Q);
+                int pp = r / Q, k = r - pp * Q;
                 T acc = T(0);
+                if constexpr (SHAPE == 0) {
+                    const T* tc = Tc + k;
+                    const T* x = S2 + e * NQ + pp * n;
 #pragma unroll
-                for (int c = 0; c < n; ++c) acc += tc[c * Q] * x[c];
-                S1[e * 4 * NQ + r] = acc;
+                    for (int c = 0; c < n; ++c) acc += tc[c * Q] * x[c];
+                    S1[e * 4 * NQ + pp * Q + k] = acc;
+                } else {
+                    const int p = porder[pp], pr = pairs[p];
+                    const int len = pr >> 24;
+                    const T* tc = Tc + ((pr >> 16) & 0xff) * n * Q + k;
+                    const T* x = S2 + e * NQ + (pr & 0xffff) * n;
+#pragma unroll
+                    for (int c = 0; c < n; ++c) {
+                        if (c >= len) break;
+                        acc += tc[c * Q] * x[c];
+                    }
+                    S1[e * 4 * NQ + p * Q + k] = acc;
+                }
             }
             __syncthreads();
-            // eta2 pass: g[a][j][k] = sum_b Tb[t(a)][b][j] f[a][b][k]
+            // eta2 pass: g[a][j][k] = sum_{b < len_b(a)} Tb[t(a)][b][j] f[p(a,b)][k]
             for (int idx = tid; idx < EPB * n * QQ; idx += NT) {
                 int e = idx / (n * QQ), r = idx - e * (n * QQ);
                 int a = r / QQ, jk = r - a * QQ, j = jk / Q, k = jk - j * Q;
-                const T* tb = Tb + famb[a] * n * Q + j;
-                const T* x = S1 + e * 4 * NQ + a * n * Q + k;
                 T acc = T(0);
+                if constexpr (SHAPE != HP_TET) {       // every (a, b) pair is valid
+                    const T* tb = Tb + j;
+                    const T* x = S1 + e * 4 * NQ + a * n * Q + k;
 #pragma unroll
-                for (int b = 0; b < n; ++b) acc += tb[b * Q] * x[b * Q];
+                    for (int b = 0; b < n; ++b) acc += tb[b * Q] * x[b * Q];
+                } else {
+                    const int p0 = poff[a], lb = poff[a + 1] - p0;
+                    const T* tb = Tb + famb[a] * n * Q + j;
+                    const T* x = S1 + e * 4 * NQ + p0 * Q + k;
+#pragma unroll
+                    for (int b = 0; b < n; ++b) {
+                        if (b >= lb) break;
+                        acc += tb[b * Q] * x[b * Q];
+                    }
+                }
                 S2[e * NQ + r] = acc;
             }
             __syncthreads();
@@ -442,10 +474,13 @@ __global__ void __launch_bounds__(256) sf_kernel(const __grid_constant__ SFArgs<
         }
         __syncthreads();
         }
-        // eta2 pass: f'[a][b][k] = sum_j Tb[t(a)][b][j] g'[a][j][k]
-        for (int idx = tid; idx < EPB * n * n * Q; idx += NT) {
-            int e = idx / (n * n * Q), r = idx - e * (n * n * Q);
-            int ab = r / Q, k = r - ab * Q, a = ab / n, b = ab - a * n;
+        // eta2 pass over the valid pairs p = (a,b): f'[p][k] = sum_j Tb[t(a)][b][j] g'[a][j][k]
+        for (int idx = tid; idx < EPB * NPR * Q; idx += NT) {
+            int e = idx / (NPR * Q), r = idx - e * (NPR * Q);
+            int p = r / Q, k = r - p * Q;
+            int ab = p;
+            if constexpr (SHAPE != 0) ab = pairs[p] & 0xffff;
+            const int a = ab / n, b = ab - a * n;
             const T* tb = Tb + (famb[a] * n + b) * Q;
             const T* x = S1 + e * 4 * NQ + a * QQ + k;
             T acc = T(0);
@@ -454,16 +489,20 @@ __global__ void __launch_bounds__(256) sf_kernel(const __grid_constant__ SFArgs<
             S2[e * NQ + r] = acc;
         }
         __syncthreads();
-        // eta3 pass: r[a][b][c] = sum_k Tc[s(a,b)][c][k] f'[a][b][k]
-        for (int idx = tid; idx < EPB * N3; idx += NT) {
-            int e = idx / N3, r = idx - e * N3;
-            int ab = r / n, c = r - ab * n;
-            const T* tc = Tc + (famc[ab] * n + c) * Q;
-            const T* x = S2 + e * NQ + ab * Q;
+        // eta3 pass over the valid slots (a,b,c): r[a][b][c] = sum_k Tc[s(a,b)][c][k] f'[p(a,b)][k]
+        for (int idx = tid; idx < EPB * NVL; idx += NT) {
+            int e = idx / NVL, v = idx - e * NVL;
+            int sl = v, p = v / n, sc = 0, c = v - p * n;
+            if constexpr (SHAPE != 0) {
+                const int vv = valid[v];
+                sl = vv & 2047; p = (vv >> 11) & 127; sc = (vv >> 18) & 15; c = (vv >> 22) & 15;
+            }
+            const T* tc = Tc + (sc * n + c) * Q;
+            const T* x = S2 + e * NQ + p * Q;
             T acc = T(0);
 #pragma unroll
             for (int k = 0; k < Q; ++k) acc += tc[k] * x[k];
-            S1[e * 4 * NQ + r] = acc;
+            S1[e * 4 * NQ + sl] = acc;
         }
         __syncthreads();
         // scatter slots to modes (collapsed modes sum their slots)

@@ -347,6 +347,38 @@ std::vector<unsigned char> make_blob(const RefTables& t, size_t vs) {
     std::memcpy(&out[L.famc], t.famc.data(), t.famc.size());
     std::memcpy(&out[L.slot2mode], t.slot2mode.data(), 2 * t.slot2mode.size());
     std::memcpy(&out[L.mode_slots], t.mode_slots.data(), 2 * t.mode_slots.size());
+    // Valid index sets of the collapsed shapes, for passes that skip the
+    // padding: pairs (a-major, b ascending) = ab | famc << 16 | family length
+    // << 24; slots = ab*n + c | pair << 11 | famc << 18 | c << 22; poff[a] =
+    // first pair of a; porder = pairs by decreasing family length.
+    std::vector<int32_t> pairs, valid;
+    std::vector<int16_t> poff;
+    const int n = t.n;
+    for (int a = 0; a < n; ++a) {
+        poff.push_back((int16_t)pairs.size());
+        for (int b = 0; b < lenb_c(t.shape, t.P, a); ++b) {
+            int sc = famc_c(t.shape, t.P, a, b), len = famlen_c(t.P, sc);
+            if (sc != t.famc[a * n + b]) throw std::runtime_error("family table mismatch");
+            int p = (int)pairs.size();
+            pairs.push_back((a * n + b) | (sc << 16) | (len << 24));
+            for (int c = 0; c < len; ++c) valid.push_back(((a * n + b) * n + c) | (p << 11) | (sc << 18) | (c << 22));
+        }
+    }
+    poff.push_back((int16_t)pairs.size());
+    if ((int)pairs.size() != npairs_c(t.shape, t.P) || (int)valid.size() != nvalid_c(t.shape, t.P))
+        throw std::runtime_error("valid slot count mismatch");
+    std::vector<char> is_valid(n * n * n, 0);
+    for (int32_t v : valid) is_valid[v & 2047] = 1;
+    for (int sl = 0; sl < n * n * n; ++sl)   // every mode slot is a valid slot
+        if (t.slot2mode[sl] >= 0 && !is_valid[sl]) throw std::runtime_error("mode slot outside the valid range");
+    std::vector<uint8_t> porder(pairs.size());
+    for (size_t p = 0; p < pairs.size(); ++p) porder[p] = (uint8_t)p;
+    std::stable_sort(porder.begin(), porder.end(), [&](uint8_t x, uint8_t y) { return (pairs[x] >> 24) > (pairs[y] >> 24); });
+    if (t.shape == HP_HEX) return out;
+    std::memcpy(&out[L.pairs], pairs.data(), 4 * pairs.size());
+    std::memcpy(&out[L.valid], valid.data(), 4 * valid.size());
+    std::memcpy(&out[L.poff], poff.data(), 2 * poff.size());
+    std::memcpy(&out[L.porder], porder.data(), porder.size());
     return out;
 }
 
