@@ -231,7 +231,7 @@ void fill_const_tables(const Block& b, SFArgs<T>& a) {
     const RefTables& t = ref_tables(b.shape, b.P);
     for (int d = 0; d < 3; ++d)
         for (size_t i = 0; i < t.D[d].size(); ++i) a.cD[d][i] = (T)t.D[d][i];
-    for (size_t i = 0; i < t.Ta.size(); ++i) a.cTa[i] = (T)t.Ta[i];
+    for (size_t i = 0; i < t.Tp.size(); ++i) a.cTa[i] = (T)t.Tp[i];
 }
 
 cudaError_t launch_block(hp_op op, size_t bi, int tile, double lambda, const void* in, void* out, cudaStream_t s) {

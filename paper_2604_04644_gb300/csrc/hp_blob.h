@@ -38,7 +38,7 @@ __host__ __device__ constexpr int nvalid_c(int shape, int P) {
 }
 
 struct BlobLayout {
-    int Ta, Tb, Tc, D, z, w, total_vals;                  // offsets in values
+    int Ta, Td, Tb, Tc, D, z, w, total_vals;              // offsets in values (Ta: parity form)
     int famb, famc, slot2mode, mode_slots;                // offsets in bytes
     int pairs, valid, poff, porder, total_bytes;          // valid (a,b) pairs and slots (int32), pair
                                                           // offset per a (int16), pairs by length (uint8)
@@ -51,6 +51,7 @@ __host__ __device__ constexpr BlobLayout blob_layout_c(int shape, int P, int vs)
     const int n = P + 1, Q = P + 2;
     int o = 0;
     L.Ta = o; o += n * Q;
+    L.Td = o; o += n * Q;
     L.Tb = o; o += (P + 1) * n * Q;
     L.Tc = o; o += (P + 1) * n * Q;
     L.D = o; o += 3 * Q * Q;

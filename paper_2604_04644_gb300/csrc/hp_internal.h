@@ -25,6 +25,7 @@ struct RefTables {
     int shape = 0, P = 0, Q = 0, n = 0, NP = 0, NQ = 0;
     std::vector<double> z[3], w[3];        // points / weights per direction (Duffy-scaled)
     std::vector<double> Ta;                // [a][i]        n*Q
+    std::vector<double> Tp, Td;            // [a][i]        n*Q, eta1 table in parity form and its derivative
     std::vector<double> Tb;                // [t][b][j]     (P+1)*n*Q
     std::vector<double> Tc;                // [s][c][k]     (P+1)*n*Q
     std::vector<double> D[3];              // [i][m]        Q*Q, d/d eta of Lagrange basis

@@ -54,6 +54,7 @@ template <int SHAPE, int P, typename T, bool AFFINE, int TILE>
 __global__ void __launch_bounds__(256) sf_kernel(const __grid_constant__ SFArgs<T> args) {
     using C = SFCfg<P, T, TILE>;
     constexpr int n = C::n, Q = C::Q, QQ = C::QQ, NQ = C::NQ, N3 = C::N3, EPB = C::EPB, NT = C::NT;
+    constexpr int NN = n * n, Qh = (Q + 1) / 2;   // Qh: even-odd pairs (i, Q-1-i) along eta1
     constexpr BlobLayout L = blob_layout_c(SHAPE, P, (int)sizeof(T));
     constexpr int NP = n_modes_c(SHAPE, P);
     constexpr int NQp = (NQ + 3) & ~3;
@@ -67,7 +68,8 @@ __global__ void __launch_bounds__(256) sf_kernel(const __grid_constant__ SFArgs<
     unsigned char* tab = smem + 16;
     if (!stage_tables(tab, args.blob, L.total_bytes, bar, args.err)) return;
 
-    const T* Ta = reinterpret_cast<const T*>(tab) + L.Ta;
+    const T* Ta = reinterpret_cast<const T*>(tab) + L.Ta;   // parity form {1/2, -z/2, psi_2..}
+    const T* Td = reinterpret_cast<const T*>(tab) + L.Td;   // its eta1 derivative
     const T* Tb = reinterpret_cast<const T*>(tab) + L.Tb;
     const T* Tc = reinterpret_cast<const T*>(tab) + L.Tc;
     const T* D0 = reinterpret_cast<const T*>(tab) + L.D;
@@ -93,6 +95,7 @@ __global__ void __launch_bounds__(256) sf_kernel(const __grid_constant__ SFArgs<
     const bool coeff_in = (op == HP_MASS || op == HP_LAPLACIAN || op == HP_HELMHOLTZ || op == HP_BWDTRANS);
     const bool deriv = (op == HP_LAPLACIAN || op == HP_HELMHOLTZ || op == HP_PHYSDERIV);
     const bool sumderiv = (op == HP_LAPLACIAN || op == HP_HELMHOLTZ || op == HP_IPRODUCT_WRT_DERIV_BASE);
+    const bool merged = !LINES && deriv && coeff_in;   // v1 comes out of the eta1 pass
     const int64_t ngroups = (args.n_elem + EPB - 1) / EPB;
 
     for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x) {
@@ -101,12 +104,19 @@ __global__ void __launch_bounds__(256) sf_kernel(const __grid_constant__ SFArgs<
 
         if (coeff_in) {
             // gather modal coefficients into the slot tensor
+            // (slots a = 0, 1 take the sum and the difference of the two coefficients,
+            // the inputs of the parity-form eta1 table)
             for (int idx = tid; idx < EPB * N3; idx += NT) {
                 int e = idx / N3, sl = idx - e * N3;
                 T v = T(0);
                 if (e < ne) {
                     int m = slot2mode[sl];
-                    if (m >= 0) v = args.in[args.coeff_off[e0 + e] + m];
+                    if (m >= 0) {
+                        const T* cin = args.in + args.coeff_off[e0 + e];
+                        if (sl >= 2 * NN) v = cin[m];
+                        else if (sl < NN) v = cin[m] + cin[slot2mode[sl + NN]];
+                        else v = cin[slot2mode[sl - NN]] - cin[m];
+                    }
                 }
                 S2[e * NQ + sl] = v;
             }
@@ -181,15 +191,32 @@ __global__ void __launch_bounds__(256) sf_kernel(const __grid_constant__ SFArgs<
             }
             __syncthreads();
             } else {
-            // eta1 pass: u[i][j][k] = sum_a Ta[a][i] g[a][j][k]
-            for (int idx = tid; idx < EPB * NQ; idx += NT) {
-                int e = idx / NQ, r = idx - e * NQ;
-                int i = r / QQ, jk = r - i * QQ;
+            // eta1 pass in even-odd pairs (i, Q-1-i): row a of the parity table has
+            // parity (-1)^a, so u_i = E + O and u_{Q-1-i} = E - O with E, O the sums
+            // over the even and odd rows; the derivative operators take
+            // v1 = du/d eta1 = sum_a Td[a][i] g[a] in the same pass (exact for the
+            // degree-P rows, replaces the collocation derivative along eta1)
+            for (int idx = tid; idx < EPB * Qh * QQ; idx += NT) {
+                int e = idx / (Qh * QQ), r = idx - e * (Qh * QQ);
+                int i = r / QQ, jk = r - i * QQ, i2 = Q - 1 - i;
                 const T* x = S2 + e * NQ + jk;
-                T acc = T(0);
+                T ev = T(0), od = T(0);
 #pragma unroll
-                for (int a = 0; a < n; ++a) acc += Ta[a * Q + i] * x[a * QQ];
-                S1[e * 4 * NQ + r] = acc;
+                for (int a = 0; a < n; a += 2) ev += Ta[a * Q + i] * x[a * QQ];
+#pragma unroll
+                for (int a = 1; a < n; a += 2) od += Ta[a * Q + i] * x[a * QQ];
+                T* u = S1 + e * 4 * NQ + jk;
+                u[i * QQ] = ev + od;
+                if (i2 != i) u[i2 * QQ] = ev - od;
+                if (merged) {
+                    T dv = T(0), dd = T(0);
+#pragma unroll
+                    for (int a = 1; a < n; a += 2) dv += Td[a * Q + i] * x[a * QQ];
+#pragma unroll
+                    for (int a = 2; a < n; a += 2) dd += Td[a * Q + i] * x[a * QQ];
+                    u[NQ + i * QQ] = dv + dd;
+                    if (i2 != i) u[NQ + i2 * QQ] = dv - dd;
+                }
             }
             __syncthreads();
             }
@@ -269,19 +296,24 @@ __global__ void __launch_bounds__(256) sf_kernel(const __grid_constant__ SFArgs<
 
         } else {
         if (deriv) {
-            // v_d = D_d u (collocation differentiation in eta_1, eta_2, eta_3)
+            // v_d = D_d u (collocation differentiation in eta_2, eta_3, and in eta_1
+            // when v1 did not come out of the eta1 pass)
             for (int idx = tid; idx < EPB * NQ; idx += NT) {
                 int e = idx / NQ, r = idx - e * NQ;
                 int i = r / QQ, jk = r - i * QQ, j = jk / Q, k = jk - j * Q;
                 const T* u = S1 + e * 4 * NQ;
-                T a1 = T(0), a2 = T(0), a3 = T(0);
+                T a2 = T(0), a3 = T(0);
 #pragma unroll
                 for (int m = 0; m < Q; ++m) {
-                    a1 += D0[i * Q + m] * u[m * QQ + jk];
                     a2 += D1[j * Q + m] * u[i * QQ + m * Q + k];
                     a3 += D2[k * Q + m] * u[i * QQ + j * Q + m];
                 }
-                S1[e * 4 * NQ + NQ + r] = a1;
+                if (!merged) {
+                    T a1 = T(0);
+#pragma unroll
+                    for (int m = 0; m < Q; ++m) a1 += D0[i * Q + m] * u[m * QQ + jk];
+                    S1[e * 4 * NQ + NQ + r] = a1;
+                }
                 S1[e * 4 * NQ + 2 * NQ + r] = a2;
                 S1[e * 4 * NQ + 3 * NQ + r] = a3;
             }
@@ -424,19 +456,33 @@ __global__ void __launch_bounds__(256) sf_kernel(const __grid_constant__ SFArgs<
 
         } else {
         if (sumderiv) {
-            // u' = sum_d D_d^T w_d + t
-            for (int idx = tid; idx < EPB * NQ; idx += NT) {
-                int e = idx / NQ, r = idx - e * NQ;
-                int i = r / QQ, jk = r - i * QQ, j = jk / Q, k = jk - j * Q;
+            // y = t + D_2^T w_2 + D_3^T w_3 in even-odd pairs (i, Q-1-i) along eta1,
+            // stored as sums at i and differences at Q-1-i, and the same sweep of
+            // w_1; the eta1 restriction applies [Tp | Td] to (y, w_1), which takes
+            // the place of D_1^T w_1 (u' = y + D_1^T w_1)
+            for (int idx = tid; idx < EPB * Qh * QQ; idx += NT) {
+                int e = idx / (Qh * QQ), r = idx - e * (Qh * QQ);
+                int i = r / QQ, jk = r - i * QQ, j = jk / Q, k = jk - j * Q, i2 = Q - 1 - i;
                 const T* w = S1 + e * 4 * NQ;
-                T acc = S2[e * NQ + r];
+                T* ys = S2 + e * NQ + jk;
+                T y1 = ys[i * QQ], y2 = ys[i2 * QQ];
 #pragma unroll
                 for (int m = 0; m < Q; ++m) {
-                    acc += D0[m * Q + i] * w[NQ + m * QQ + jk];
-                    acc += D1[m * Q + j] * w[2 * NQ + i * QQ + m * Q + k];
-                    acc += D2[m * Q + k] * w[3 * NQ + i * QQ + j * Q + m];
+                    y1 += D1[m * Q + j] * w[2 * NQ + i * QQ + m * Q + k];
+                    y1 += D2[m * Q + k] * w[3 * NQ + i * QQ + j * Q + m];
+                    y2 += D1[m * Q + j] * w[2 * NQ + i2 * QQ + m * Q + k];
+                    y2 += D2[m * Q + k] * w[3 * NQ + i2 * QQ + j * Q + m];
                 }
-                S2[e * NQ + r] = acc;
+                if (i2 != i) {
+                    T* w1 = S1 + e * 4 * NQ + NQ + jk;
+                    const T wa = w1[i * QQ], wb = w1[i2 * QQ];
+                    ys[i * QQ] = y1 + y2;
+                    ys[i2 * QQ] = y1 - y2;
+                    w1[i * QQ] = wa + wb;
+                    w1[i2 * QQ] = wa - wb;
+                } else {
+                    ys[i * QQ] = y1;
+                }
             }
             __syncthreads();
         }
@@ -459,6 +505,27 @@ __global__ void __launch_bounds__(256) sf_kernel(const __grid_constant__ SFArgs<
                 for (int i = 0; i < Q; ++i) acc += args.cTa[a * Q + i] * uq[i];
                 g[a * QQ] = acc;
             }
+        }
+        __syncthreads();
+        } else if (sumderiv) {
+        // restriction B^T along eta1 from the even-odd sweeps:
+        // g'[a] = sum_{i < Qh} Tp[a][i] y^{+-}_i + Td[a][i] w_1^{-+}_i, the sum or
+        // difference taken by the parity of the row (the middle point of odd Q
+        // meets an exact zero in the row of the wrong parity)
+        for (int idx = tid; idx < EPB * n * QQ; idx += NT) {
+            int e = idx / (n * QQ), r = idx - e * (n * QQ);
+            int a = r / QQ, jk = r - a * QQ;
+            const bool even = (a & 1) == 0;
+            const T* ys = S2 + e * NQ + jk;
+            const T* ws = S1 + e * 4 * NQ + NQ + jk;
+            T acc = T(0);
+#pragma unroll
+            for (int i = 0; i < Qh; ++i) {
+                const int iy = even ? i : Q - 1 - i, iw = even ? Q - 1 - i : i;
+                acc += Ta[a * Q + i] * ys[iy * QQ];
+                acc += Td[a * Q + i] * ws[iw * QQ];
+            }
+            S1[e * 4 * NQ + r] = acc;
         }
         __syncthreads();
         } else {
@@ -514,7 +581,12 @@ __global__ void __launch_bounds__(256) sf_kernel(const __grid_constant__ SFArgs<
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 int sl = mode_slots[m * 4 + q];
-                if (sl >= 0) acc += rs[sl];
+                if (sl < 0) continue;
+                // slots a = 0, 1 hold the restrictions against 1/2 and -z/2:
+                // L = 1/2 - z/2 takes their sum, R = 1/2 + z/2 their difference
+                if (sl >= 2 * NN) acc += rs[sl];
+                else if (sl < NN) acc += rs[sl] + rs[sl + NN];
+                else acc += rs[sl - NN] - rs[sl];
             }
             args.out[args.coeff_off[e0 + e] + m] = acc;
         }

@@ -90,6 +90,12 @@ void gll_rule(int Q, std::vector<double>& x, std::vector<double>& w) {
         double p = jac(Q - 1, 0.0, 0.0, x[i]);
         w[i] = 2.0 / (Q * (Q - 1.0) * p * p);
     }
+    // exact symmetry about 0 (the even-odd passes rely on z_{Q-1-i} = -z_i)
+    for (int i = 0; i < Q / 2; ++i) {
+        double a = 0.5 * (x[Q - 1 - i] - x[i]), b = 0.5 * (w[i] + w[Q - 1 - i]);
+        x[i] = -a; x[Q - 1 - i] = a; w[i] = b; w[Q - 1 - i] = b;
+    }
+    if (Q % 2) x[Q / 2] = 0.0;
 }
 
 void grj_rule(int Q, int alpha, std::vector<double>& x, std::vector<double>& w) {
@@ -173,6 +179,38 @@ RefTables build(int shape, int P) {
     t.Ta.assign(n * Q, 0.0);
     for (int a = 0; a < n; ++a)
         for (int i = 0; i < Q; ++i) t.Ta[a * Q + i] = family(P, 0, a, t.z[0][i]);
+    // parity form of the eta1 table (GLL points, symmetric about 0): the vertex
+    // pair {L, R} becomes {1/2, -z/2} (the coefficients of the slots a = 0, 1
+    // enter as their sum and difference), so row a has parity (-1)^a; Td is
+    // its derivative, row a of parity (-1)^(a+1).  Mirrored entries are set
+    // from the first half, entries of the wrong parity at z = 0 are exact zeros.
+    {
+        const int Qh = (Q + 1) / 2;
+        t.Tp.assign(n * Q, 0.0);
+        t.Td.assign(n * Q, 0.0);
+        for (int i = 0; i < Q; ++i) {
+            t.Tp[0 * Q + i] = 0.5;
+            t.Tp[1 * Q + i] = -0.5 * t.z[0][i];
+            for (int a = 2; a < n; ++a) t.Tp[a * Q + i] = t.Ta[a * Q + i];
+        }
+        for (int a = 0; a < n; ++a)
+            for (int i = 0; i < Q; ++i) {
+                double d = 0.0;
+                for (int m = 0; m < Q; ++m) d += t.D[0][i * Q + m] * t.Tp[a * Q + m];
+                t.Td[a * Q + i] = a == 0 ? 0.0 : (a == 1 ? -0.5 : d);
+            }
+        for (int a = 0; a < n; ++a) {
+            const double sp = (a % 2) ? -1.0 : 1.0;          // parity of Tp row a; Td has -sp
+            for (int i = 0; i < Qh; ++i) {
+                const int i2 = Q - 1 - i;
+                double tp = 0.5 * (t.Tp[a * Q + i] + sp * t.Tp[a * Q + i2]);
+                double td = 0.5 * (t.Td[a * Q + i] - sp * t.Td[a * Q + i2]);
+                if (i == i2) { if (sp < 0) tp = 0.0; else td = 0.0; }
+                t.Tp[a * Q + i] = tp; t.Tp[a * Q + i2] = sp * tp;
+                t.Td[a * Q + i] = td; t.Td[a * Q + i2] = -sp * td;
+            }
+        }
+    }
     t.Tb.assign((P + 1) * n * Q, 0.0);
     t.Tc.assign((P + 1) * n * Q, 0.0);
     for (int s = 0; s <= P; ++s)
@@ -334,7 +372,8 @@ std::vector<unsigned char> make_blob(const RefTables& t, size_t vs) {
             }
         }
     };
-    put(L.Ta, t.Ta);
+    put(L.Ta, t.Tp);
+    put(L.Td, t.Td);
     put(L.Tb, t.Tb);
     put(L.Tc, t.Tc);
     for (int d = 0; d < 3; ++d) {
