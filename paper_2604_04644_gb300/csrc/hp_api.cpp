@@ -8,6 +8,7 @@
 #include <tuple>
 
 #include "hp_internal.h"
+#include "hp_tc.cuh"
 
 namespace hp {
 
@@ -66,6 +67,8 @@ void free_block(Block& b) {
     cudaFree(b.d_dgeom);
     cudaFree(b.d_geom32);
     cudaFree(b.d_dgeom32);
+    cudaFree(b.d_geom_tc);
+    b.d_geom_tc = nullptr;
     b.d_coeff_off = b.d_phys_off = nullptr;
     b.d_frame = b.d_geom = b.d_dgeom = nullptr;
     b.d_geom32 = b.d_dgeom32 = nullptr;
@@ -186,6 +189,90 @@ hp_status ensure_dense(hp_mesh m) {
     return HP_OK;
 }
 
+// round to the TF32 grid (10-bit mantissa, nearest, ties away from zero)
+float round_tf32(float x) {
+    uint32_t u;
+    std::memcpy(&u, &x, 4);
+    if ((u & 0x7f800000u) != 0x7f800000u) {
+        u += 0x1000u;
+        u &= 0xffffe000u;
+    }
+    float r;
+    std::memcpy(&r, &u, 4);
+    return r;
+}
+
+// Reference tiles of the tensor-core elemental-matrix operator, per chunk of
+// tc_chunk_points() quadrature points: the forward operand (64 rows = 4
+// components x 16 points, K = modes) in K-slices of 32 modes (the last one
+// shorter), then the backward tiles R_c[mode][point] (rows padded to NPpad)
+// of the 4 components; all in the K-major, no-swizzle core-matrix order the
+// tensor core reads from shared memory.
+hp_status ensure_tc(hp_mesh m) {
+    for (auto& kv : m->blobs) {
+        DeviceBlobs& db = kv.second;
+        if (db.tc_img) continue;
+        const int shape = kv.first / 16, P = kv.first % 16;
+        const int Q = P + 2, NQ = Q * Q * Q, NP = n_modes(shape, P), NPT = tc_chunk_points();
+        if (NP > kTcMaxModes) continue;
+        const int KP = (NP + 7) & ~7, NPpad = (NP + 15) & ~15, nch = (NQ + NPT - 1) / NPT;
+        const int fwd = 4 * NPT * KP * 4, bwd = NPpad * NPT * 4;    // forward: all slices of a chunk
+        const int64_t chunk = fwd + 4 * (int64_t)bwd;
+        std::vector<double> A = dense_matrices(shape, P);
+        std::vector<unsigned char> img((size_t)(chunk * nch), 0);
+        for (int k = 0; k < nch; ++k) {
+            unsigned char* F = img.data() + (size_t)k * chunk;
+            for (int c = 0; c < 4; ++c) {
+                unsigned char* R = img.data() + (size_t)k * chunk + fwd + (size_t)c * bwd;
+                for (int r = 0; r < NPT; ++r) {
+                    const int l = k * NPT + r;
+                    if (l >= NQ) continue;
+                    for (int mm = 0; mm < NP; ++mm) {
+                        const float v = round_tf32((float)A[((size_t)c * NQ + l) * NP + mm]);
+                        const int sl = mm / 32, ks = std::min(32, KP - 32 * sl);
+                        std::memcpy(F + (size_t)sl * (4 * NPT * 32 * 4) +
+                                        tc::kmajor_offset(c * NPT + r, mm - 32 * sl, ks * 4, 4), &v, 4);
+                        std::memcpy(R + tc::kmajor_offset(mm, r, NPT * 4, 4), &v, 4);
+                    }
+                }
+            }
+        }
+        // d eta / d xi and the quadrature weight at every point (affine elements)
+        const RefTables& t = ref_tables(shape, P);
+        std::vector<float> pts((size_t)NQ * 10);
+        for (int l = 0; l < NQ; ++l) {
+            const int i = l / (Q * Q), j = (l / Q) % Q, k = l % Q;
+            double T[3][3];
+            switch (shape) {
+                case HP_HEX: deta_dxi<HP_HEX, double>(t.z[0][i], t.z[1][j], t.z[2][k], T); break;
+                case HP_PRISM: deta_dxi<HP_PRISM, double>(t.z[0][i], t.z[1][j], t.z[2][k], T); break;
+                case HP_PYR: deta_dxi<HP_PYR, double>(t.z[0][i], t.z[1][j], t.z[2][k], T); break;
+                default: deta_dxi<HP_TET, double>(t.z[0][i], t.z[1][j], t.z[2][k], T); break;
+            }
+            for (int d = 0; d < 9; ++d) pts[(size_t)l * 10 + d] = (float)T[d / 3][d % 3];
+            pts[(size_t)l * 10 + 9] = (float)(t.w[0][i] * t.w[1][j] * t.w[2][k]);
+        }
+        hp_status st = upload(&db.tc_img, img.data(), img.size());
+        if (!st) st = upload(&db.tc_pts, pts.data(), pts.size());
+        if (st) return st;
+        db.tc_KP = KP; db.tc_NPpad = NPpad; db.tc_nch = nch; db.tc_fwd = fwd; db.tc_bwd = bwd; db.tc_chunk = chunk;
+    }
+    // curved blocks: FP32 metric factors in the tile-major order the epilogue reads
+    for (Block& b : m->blocks) {
+        if (!b.curved || b.d_geom_tc || n_modes(b.shape, b.P) > kTcMaxModes) continue;
+        const DeviceBlobs& db = m->blobs.at(b.shape * 16 + b.P);
+        const int64_t n = tc_geom_floats(b.n_elem, db.tc_nch);
+        hp_status st = upload<float>(&b.d_geom_tc, nullptr, (size_t)n);
+        if (st) return st;
+        cudaError_t e = tc_geom_layout(b.d_geom, b.d_geom_tc, b.n_elem, b.Q * b.Q * b.Q, nqp(b.Q), db.tc_nch, 0);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(0);
+        if (e != cudaSuccess) return cuda_fail(e, "tensor-core geometry layout");
+    }
+    return HP_OK;
+}
+
+bool tc_fits(const Block& b) { return n_modes(b.shape, b.P) <= kTcMaxModes; }
+
 // flops of the elemental-matrix (hybrid = false) or hybrid strategy per element
 double elem_flops_dense(int shape, int P, hp_opkind k, bool hybrid) {
     const int Q = P + 2;
@@ -239,6 +326,21 @@ cudaError_t launch_block(hp_op op, size_t bi, int tile, double lambda, const voi
     const Block& b = m->blocks[bi];
     const DeviceBlobs& blob = m->blobs.at(b.shape * 16 + b.P);
     const int64_t nphys = m->phys_off.back();
+    if (op->dtype == HP_TF32 && op->strat[bi] == HP_STRAT_ELEMAT) {
+        TCArgs a{};
+        a.op = op->kind; a.Q = b.Q; a.NQ = b.Q * b.Q * b.Q; a.NQp = nqp(b.Q); a.NP = n_modes(b.shape, b.P);
+        a.KP = blob.tc_KP; a.NPpad = blob.tc_NPpad; a.nch = blob.tc_nch;
+        a.c0 = op->kind == HP_LAPLACIAN ? 1 : 0;
+        a.c1 = op->kind == HP_MASS ? 1 : 4;
+        a.n_elem = b.n_elem; a.lambda = (float)lambda; a.coeff_off = b.d_coeff_off;
+        a.in = static_cast<const float*>(in); a.out = static_cast<float*>(out);
+        a.geom = b.curved ? b.d_geom_tc : b.d_geom32;
+        a.tpts = blob.tc_pts;
+        a.img = blob.tc_img; a.chunk_bytes = blob.tc_chunk; a.fwd_bytes = blob.tc_fwd; a.bwd_bytes = blob.tc_bwd;
+        a.stage_bytes = (std::max(4 * tc_chunk_points() * 32 * 4, blob.tc_bwd) + 127) & ~127;
+        a.err = op->d_err;
+        return tc_emat_launch(!b.curved, a, s);
+    }
     if (op->strat[bi] != HP_STRAT_SUMFAC) {
         const bool hybrid = op->strat[bi] == HP_STRAT_HYBRID;
         if (op->dtype == HP_FP64) {
@@ -544,9 +646,14 @@ hp_status hp_op_create(hp_mesh m, hp_opkind kind, hp_strategy strategy, hp_dtype
     if ((int)kind < 0 || kind > HP_IPRODUCT_WRT_DERIV_BASE) { set_error("hp_op_create: bad kind"); return HP_ERR_ARG; }
     if ((int)strategy < 0 || strategy > HP_STRAT_AUTO) { set_error("hp_op_create: bad strategy"); return HP_ERR_ARG; }
     if ((int)dtype < 0 || dtype > HP_BF16) { set_error("hp_op_create: bad dtype"); return HP_ERR_ARG; }
-    if (strategy == HP_STRAT_AUTO) strategy = HP_STRAT_SUMFAC;
-    if (dtype != HP_FP64 && dtype != HP_FP32) {
+    if (strategy == HP_STRAT_AUTO) strategy = dtype == HP_TF32 ? HP_STRAT_ELEMAT : HP_STRAT_SUMFAC;
+    if (dtype == HP_BF16) {
         set_error("hp_op_create: this strategy/dtype combination is not built");
+        return HP_ERR_UNSUPPORTED;
+    }
+    if (dtype == HP_TF32 && (strategy != HP_STRAT_ELEMAT ||
+                             (kind != HP_MASS && kind != HP_LAPLACIAN && kind != HP_HELMHOLTZ))) {
+        set_error("hp_op_create: HP_TF32 is the tensor-core elemental-matrix form of mass, Laplacian and Helmholtz");
         return HP_ERR_UNSUPPORTED;
     }
     if (strategy != HP_STRAT_SUMFAC && (kind == HP_PHYSDERIV || kind == HP_IPRODUCT_WRT_DERIV_BASE)) {
@@ -554,9 +661,13 @@ hp_status hp_op_create(hp_mesh m, hp_opkind kind, hp_strategy strategy, hp_dtype
         return HP_ERR_UNSUPPORTED;
     }
     DeviceGuard guard(m->device);
-    hp_status st = ensure_geom(m, needs_deriv_geom(kind), dtype == HP_FP32, 0);
+    hp_status st = ensure_geom(m, needs_deriv_geom(kind), dtype != HP_FP64, 0);
     if (st) return st;
-    if (strategy != HP_STRAT_SUMFAC && (st = ensure_dense(m))) return st;
+    if (dtype == HP_TF32) {
+        if ((st = ensure_tc(m))) return st;
+    } else if (strategy != HP_STRAT_SUMFAC && (st = ensure_dense(m))) {
+        return st;
+    }
     auto op = new hp_op_s();
     op->mesh = m;
     op->kind = kind;
@@ -564,6 +675,9 @@ hp_status hp_op_create(hp_mesh m, hp_opkind kind, hp_strategy strategy, hp_dtype
     op->dtype = dtype;
     op->tile.assign(m->blocks.size(), 0);
     op->strat.assign(m->blocks.size(), (int)strategy);
+    if (dtype == HP_TF32)   // blocks beyond the tensor-memory budget run FP32 sum factorisation
+        for (size_t i = 0; i < m->blocks.size(); ++i)
+            if (!tc_fits(m->blocks[i])) op->strat[i] = HP_STRAT_SUMFAC;
     st = upload<unsigned int>(&op->d_err, nullptr, 1);
     if (!st) cudaMemset(op->d_err, 0, sizeof(unsigned int));
     if (st) { delete op; return st; }
@@ -717,7 +831,12 @@ hp_status hp_op_strategies(hp_op op, int* strat, int64_t n_blocks, int set) {
             set_error("hp_op_strategies: derivative building blocks exist only with HP_STRAT_SUMFAC");
             return HP_ERR_UNSUPPORTED;
         }
-        dense |= strat[i] != HP_STRAT_SUMFAC;
+        if (op->dtype == HP_TF32 && strat[i] != HP_STRAT_SUMFAC &&
+            (strat[i] != HP_STRAT_ELEMAT || !tc_fits(op->mesh->blocks[i]))) {
+            set_error("hp_op_strategies: HP_TF32 blocks are tensor-core elemental-matrix (N_P <= 256) or FP32 sum factorisation");
+            return HP_ERR_UNSUPPORTED;
+        }
+        dense |= strat[i] != HP_STRAT_SUMFAC && op->dtype != HP_TF32;
     }
     if (dense) {
         hp_status st = ensure_dense(op->mesh);
@@ -890,6 +1009,8 @@ void hp_mesh_destroy(hp_mesh m) {
             cudaFree(kv.second.A4T_64);
             cudaFree(kv.second.A4_32);
             cudaFree(kv.second.A4T_32);
+            cudaFree(kv.second.tc_img);
+            cudaFree(kv.second.tc_pts);
         }
         cudaFree(m->d_err);
     }

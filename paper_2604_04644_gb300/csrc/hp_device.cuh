@@ -30,7 +30,7 @@ __device__ __forceinline__ void xi_from_eta(double e1, double e2, double e3, dou
 
 // T[d][a] = d eta_d / d xi_a at a point given in eta (the G of Sec. 2.3 in 3-D).
 template <int SHAPE, typename R>
-__device__ __forceinline__ void deta_dxi(R e1, R e2, R e3, R T[3][3]) {
+__host__ __device__ __forceinline__ void deta_dxi(R e1, R e2, R e3, R T[3][3]) {
     for (int d = 0; d < 3; ++d)
         for (int a = 0; a < 3; ++a) T[d][a] = (d == a) ? R(1) : R(0);
     if (SHAPE == HP_PRISM) {

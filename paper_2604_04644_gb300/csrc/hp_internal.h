@@ -60,6 +60,7 @@ struct Block {
     double* d_dgeom = nullptr;            // curved only: [n_elem][9][NQp] d eta_d / d x_i
     float* d_geom32 = nullptr;            // FP32 copies (created on demand)
     float* d_dgeom32 = nullptr;
+    float* d_geom_tc = nullptr;           // curved, tensor-core operator: tile-major FP32 factors
     int64_t coeff_total = 0, phys_total = 0;   // per-block totals (work accounting)
 };
 
@@ -73,6 +74,11 @@ struct DeviceBlobs {
     double* A4T_64 = nullptr;
     float* A4_32 = nullptr;
     float* A4T_32 = nullptr;
+    // tensor-core reference tiles (TF32, tensor-core shared-memory order), see TCArgs
+    unsigned char* tc_img = nullptr;
+    float* tc_pts = nullptr;          // [NQ][10]: d eta/d xi and weight per point (affine elements)
+    int tc_KP = 0, tc_NPpad = 0, tc_nch = 0, tc_fwd = 0, tc_bwd = 0;
+    int64_t tc_chunk = 0;
 };
 
 }  // namespace hp
@@ -168,6 +174,29 @@ struct EMArgs {
     unsigned int* err;
 };
 cudaError_t emat_launch_f64(bool hybrid, bool affine, const EMArgs<double>& a, cudaStream_t s);
+
+// tensor-core (tcgen05, TF32) elemental-matrix operator, hp_tc_emat.cu
+struct TCArgs {
+    int op, Q, NQ, NQp, NP, KP, NPpad, nch, c0, c1;   // components [c0, c1) of {B, dB/deta_1..3}
+    int64_t n_elem;
+    float lambda;
+    const int64_t* coeff_off;
+    const float* in;
+    float* out;
+    const float* geom;                 // curved: tile-major FP32 factors (tc_geom_layout); affine: [n][16]
+    const float* tpts;                 // affine: per point d eta/d xi (9) and weight, [NQ][10]
+    const unsigned char* img;          // per chunk of points: 4 forward then 4 backward tiles
+    int64_t chunk_bytes;
+    int fwd_bytes, bwd_bytes, stage_bytes;
+    int nsplit, stages;                // set by the launcher
+    unsigned int* err;
+};
+constexpr int kTcMaxModes = 256;
+int tc_smem_bytes(int KP, int stage_bytes);
+int tc_chunk_points();
+int64_t tc_geom_floats(int64_t n_elem, int nch);
+cudaError_t tc_geom_layout(const double* g, float* out, int64_t n_elem, int NQ, int NQp, int nch, cudaStream_t s);
+cudaError_t tc_emat_launch(bool affine, const TCArgs& a, cudaStream_t s);
 cudaError_t emat_launch_f32(bool hybrid, bool affine, const EMArgs<float>& a, cudaStream_t s);
 
 // per-shape launchers (hp_sf_<shape>.cu)

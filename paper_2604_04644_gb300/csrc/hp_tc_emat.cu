@@ -1,0 +1,438 @@
+// Elemental-matrix strategy on the fifth-generation tensor cores (TF32 inputs,
+// FP32 accumulation in tensor memory).
+//
+// The operator of the elemental-matrix form (paper Sec. 3.2; Eq. (helm1) with
+// the reference matrices of Sec. 2.2):
+//   out_e = sum_{c,c'} A_c^T  diag(M_{cc'}(e))  A_c' uhat_e,
+// A_0 = B (basis at the points), A_d = dB/d eta_d, M_00 = lambda w|J| (mass
+// term), M_dd' = G_dd' (the six metric factors), M_0d = 0.  Mass uses c = 0
+// only (M_00 = w|J|), the Laplacian c = 1..3.
+//
+// Organisation (one CTA per SM, persistent over work items = a tile of 128
+// elements and a range of its point chunks):
+//   forward  [V_0..V_3][128 elem x 4*16] = U[128 x K_P] * [F_0; ..; F_3]^T      (tcgen05, TMEM;
+//            one MMA per K step covers the components, so U is read once)
+//   metric   V'_c = sum_c' M_cc' V_c'  pointwise, by the eight warps that read the TMEM lanes
+//   backward O[128 elem x N_P]       += V'_c[128 x 16] * R_c[N_P x 16]^T     (tcgen05, TMEM)
+// over chunks of 16 quadrature points.  U (the element coefficients) stays in
+// shared memory for the work item; the reference tiles F_c, R_c are laid out
+// on the host in the tensor core's shared-memory order and streamed by 1-D
+// bulk copies (TMA) through a ring of stages (the forward operand in K slices
+// of 32 modes, the backward tiles one component at a time).  The forward accumulators and
+// the V' tiles are double-buffered, so the metric of chunk k overlaps the
+// forward MMAs of chunk k+1 and the backward MMAs of chunk k-1.
+// Roles: warps 0-7 gather U, run the metric and write the outputs (warp w
+// reads TMEM lanes 32 (w mod 4).. and half w / 4 of each chunk's points);
+// warp 8 issues the bulk copies; warp 9 issues the MMAs.  Every wait is
+// bounded; a timeout latches DERR_TIMEOUT, stops every role, drains the
+// copies and MMAs in flight and frees the tensor memory before the CTA exits.
+#include "hp_tc.cuh"
+
+namespace hp {
+namespace {
+
+constexpr int kNPT = 16;          // quadrature points per chunk
+constexpr int kHalf = kNPT / 2;   // points per epilogue thread
+constexpr int kMaxStages = 8;     // bulk-copy ring: as many stages (2..8) as fit in shared memory
+constexpr int kTmemCols = 512;
+constexpr int kOutCol = 128;      // TMEM column of the output accumulator (forward: 2 buffers x 4 x 16)
+constexpr int kEpi = 256;         // epilogue threads
+constexpr int kThreads = kEpi + 64;
+constexpr int kVBytes = 128 * kNPT * 4;   // one V' tile [128 x 16] TF32
+constexpr int kSliceBytes = 4 * kNPT * 32 * 4;   // forward operand: 64 rows x 32 modes
+
+struct Bars {
+    uint64_t full[kMaxStages], empty[kMaxStages];
+    uint64_t u_full, fwd_full[2], fwd_empty[2], vp_full[2], vp_empty[2], out_full, out_empty, drain;
+    uint32_t tmem;
+    int abort;
+};
+
+// wait for `parity` of `bar`, giving up when another role aborted or after the
+// time limit (then this role aborts every role)
+__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, Bars* B, unsigned int* err) {
+    const uint64_t t0 = global_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (*reinterpret_cast<volatile int*>(&B->abort)) return false;
+        if (global_ns() - t0 > kWaitLimitNs) {
+            atomicExch(&B->abort, 1);
+            atomicOr(err, DERR_TIMEOUT);
+            return false;
+        }
+    }
+    return true;
+}
+// epilogue warps take the decision warp-wide (the tensor-memory loads that
+// follow are warp-collective)
+__device__ __forceinline__ bool wait_warp(uint64_t* bar, uint32_t parity, Bars* B, unsigned int* err) {
+    return __all_sync(0xffffffffu, wait_bar(bar, parity, B, err));
+}
+__device__ __forceinline__ void arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+template <bool AFFINE>
+__global__ void __launch_bounds__(kThreads, 1) tc_emat_kernel(const __grid_constant__ TCArgs a) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    Bars* B = reinterpret_cast<Bars*>(smem);
+    unsigned char* sU = smem + 1024;                                   // [128 x KP] tf32
+    unsigned char* sV = sU + 128 * a.KP * 4;                           // [2][4][128 x 16] tf32
+    unsigned char* sR = sV + 8 * kVBytes;                              // ring
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nst = a.stages;
+    // work items: (tile of 128 elements, part of its point chunks); parts of one
+    // tile add their partial outputs (the output was zeroed first)
+    const int64_t nwork = (a.n_elem + 127) / 128 * a.nsplit;
+    auto chunk_range = [&](int64_t w, int& kb, int& ke) {
+        const int part = (int)(w % a.nsplit);
+        kb = (int)((int64_t)a.nch * part / a.nsplit);
+        ke = (int)((int64_t)a.nch * (part + 1) / a.nsplit);
+    };
+
+    if (tid == 0) {
+        for (int s = 0; s < nst; ++s) { mbar_init(&B->full[s], 1); mbar_init(&B->empty[s], 1); }
+        mbar_init(&B->u_full, kEpi);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&B->fwd_full[b], 1);
+            mbar_init(&B->fwd_empty[b], kEpi);
+            mbar_init(&B->vp_full[b], kEpi);
+            mbar_init(&B->vp_empty[b], 1);
+        }
+        mbar_init(&B->out_full, 1);
+        mbar_init(&B->out_empty, kEpi);
+        mbar_init(&B->drain, 1);
+        B->abort = 0;
+    }
+    if (warp == 0) { tc::tmem_alloc(&B->tmem, kTmemCols); tc::tmem_relinquish(); }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tbase = B->tmem;
+
+    if (warp == 8) {
+        // ---------------------------------------------------------------- producer
+        if (lane == 0) {
+            int slot = 0;
+            uint32_t pass = 0;
+            uint32_t last_parity[kMaxStages];
+            bool used[kMaxStages];
+            for (int i = 0; i < kMaxStages; ++i) { last_parity[i] = 0; used[i] = false; }
+            bool ok = true;
+            auto put = [&](const unsigned char* src, uint32_t bytes) {
+                if (!wait_bar(&B->empty[slot], pass ^ 1u, B, a.err)) { ok = false; return; }
+                mbar_expect_tx(&B->full[slot], bytes);
+                bulk_g2s(sR + (size_t)slot * a.stage_bytes, src, bytes, &B->full[slot]);
+                used[slot] = true;
+                last_parity[slot] = pass;
+                if (++slot == nst) { slot = 0; pass ^= 1u; }
+            };
+            for (int64_t w = blockIdx.x; w < nwork && ok; w += gridDim.x) {
+                int kb, ke;
+                chunk_range(w, kb, ke);
+                for (int k = kb; k <= ke && ok; ++k) {
+                    if (k < ke) {
+                        const unsigned char* base = a.img + (size_t)k * a.chunk_bytes;
+                        for (int sl = 0; sl * 32 < a.KP && ok; ++sl) {
+                            const int ks = min(32, a.KP - 32 * sl);
+                            put(base + (size_t)sl * kSliceBytes, 4 * kNPT * ks * 4);
+                        }
+                    }
+                    if (k > kb) {
+                        const unsigned char* base = a.img + (size_t)(k - 1) * a.chunk_bytes + (size_t)a.fwd_bytes;
+                        for (int c = a.c0; c < a.c1 && ok; ++c) put(base + (size_t)c * a.bwd_bytes, a.bwd_bytes);
+                    }
+                }
+            }
+            // no copy may still be landing when the CTA leaves
+            for (int s = 0; s < nst; ++s)
+                if (used[s]) {
+                    const uint64_t t0 = global_ns();
+                    while (!mbar_try_wait(&B->full[s], last_parity[s]) && global_ns() - t0 < kWaitLimitNs) {}
+                }
+        }
+        __syncwarp();
+    } else if (warp == 9) {
+        // ---------------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            const uint32_t id_f = tc::instr_desc(tc::kFmtTF32, 128, kNPT * (a.c1 - a.c0));
+            const uint32_t id_b = tc::instr_desc(tc::kFmtTF32, 128, a.NPpad);
+            const uint32_t sbo_u = a.KP * 32;
+            int slot = 0;
+            uint32_t pass = 0, nout = 0, ntile = 0, g0 = 0;   // g: chunks processed by this CTA
+            bool ok = true;
+            for (int64_t w = blockIdx.x; w < nwork && ok; w += gridDim.x, ++ntile) {
+                int kb, ke;
+                chunk_range(w, kb, ke);
+                if (!wait_bar(&B->u_full, ntile & 1u, B, a.err)) { ok = false; break; }
+                for (int k = kb; k <= ke && ok; ++k) {
+                    if (k < ke) {
+                        const uint32_t g = g0 + (uint32_t)(k - kb), b = g & 1u, use = g >> 1;
+                        if (!wait_bar(&B->fwd_empty[b], (use & 1u) ^ 1u, B, a.err)) { ok = false; break; }
+                        tc::fence_after();
+                        // columns (b*4 + c0)*16 .. of the accumulator = components c0..c1-1
+                        const uint32_t d = tbase + (uint32_t)((b * 4 + a.c0) * kNPT);
+                        for (int sl = 0; sl * 32 < a.KP && ok; ++sl) {
+                            if (!wait_bar(&B->full[slot], pass, B, a.err)) { ok = false; break; }
+                            tc::fence_after();
+                            const int ks = min(32, a.KP - 32 * sl);
+                            const uint32_t sbo_f = ks * 32;      // 8-row group stride of this slice
+                            const uint32_t sa = smem_addr(sU) + sl * 4 * 256;
+                            const uint32_t sb = smem_addr(sR + (size_t)slot * a.stage_bytes) + a.c0 * 2 * sbo_f;
+                            for (int s = 0; s < ks / 8; ++s)
+                                tc::mma_tf32(d, tc::smem_desc(sa + s * 256, 128, sbo_u),
+                                             tc::smem_desc(sb + s * 256, 128, sbo_f), id_f, sl > 0 || s > 0);
+                            tc::commit(&B->empty[slot]);
+                            if (++slot == nst) { slot = 0; pass ^= 1u; }
+                        }
+                        tc::commit(&B->fwd_full[b]);
+                    }
+                    if (k > kb && ok) {
+                        const uint32_t g = g0 + (uint32_t)(k - 1 - kb), b = g & 1u, use = g >> 1;
+                        if (!wait_bar(&B->vp_full[b], use & 1u, B, a.err)) { ok = false; break; }
+                        if (k == kb + 1) {
+                            if (!wait_bar(&B->out_empty, (nout & 1u) ^ 1u, B, a.err)) { ok = false; break; }
+                            ++nout;
+                        }
+                        tc::fence_after();
+                        for (int c = a.c0; c < a.c1 && ok; ++c) {
+                            if (!wait_bar(&B->full[slot], pass, B, a.err)) { ok = false; break; }
+                            tc::fence_after();
+                            const uint32_t sa = smem_addr(sV + (size_t)(b * 4 + c) * kVBytes);
+                            const uint32_t sb = smem_addr(sR + (size_t)slot * a.stage_bytes);
+                            for (int s = 0; s < kNPT / 8; ++s)
+                                tc::mma_tf32(tbase + kOutCol, tc::smem_desc(sa + s * 256, 128, kNPT * 32),
+                                             tc::smem_desc(sb + s * 256, 128, kNPT * 32), id_b,
+                                             !(k == kb + 1 && c == a.c0 && s == 0));
+                            tc::commit(&B->empty[slot]);
+                            if (++slot == nst) { slot = 0; pass ^= 1u; }
+                        }
+                        tc::commit(&B->vp_empty[b]);
+                    }
+                }
+                if (ok) tc::commit(&B->out_full);
+                g0 += (uint32_t)(ke - kb);
+            }
+            // every MMA issued by this thread has completed before the CTA leaves
+            tc::commit(&B->drain);
+            const uint64_t t0 = global_ns();
+            while (!mbar_try_wait(&B->drain, 0) && global_ns() - t0 < kWaitLimitNs) {}
+        }
+        __syncwarp();
+    } else {
+        // ---------------------------------------------------------------- epilogue warps 0-7
+        const int q = warp & 3, h = warp >> 2;
+        const int r = q * 32 + lane;            // element row of the tile = TMEM lane
+        const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+        uint32_t ntile = 0, g0 = 0;
+        bool ok = true;
+        for (int64_t w = blockIdx.x; w < nwork && ok; w += gridDim.x, ++ntile) {
+            int kb, ke;
+            chunk_range(w, kb, ke);
+            const int64_t tile = w / a.nsplit, e = tile * 128 + r;
+            const bool valid = e < a.n_elem;
+            // U row r (this thread: half h of it): coefficients, TF32, zero padded to KP
+            {
+                const float* src = valid ? a.in + a.coeff_off[e] : nullptr;
+                const int half = a.KP / 2;
+                for (int m0 = h * half; m0 < (h + 1) * half; m0 += 4) {
+                    float4 v;
+                    float* pv = reinterpret_cast<float*>(&v);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) pv[i] = (valid && m0 + i < a.NP) ? tc::to_tf32(src[m0 + i]) : 0.f;
+                    *reinterpret_cast<float4*>(sU + tc::kmajor_offset(r, m0, a.KP * 4, 4)) = v;
+                }
+            }
+            tc::fence_async_smem();
+            arrive(&B->u_full);
+            float K6[6] = {0, 0, 0, 0, 0, 0}, detJ = 0.f;
+            if (AFFINE && valid) {
+                const float* rec = a.geom + e * 16;
+#pragma unroll
+                for (int f = 0; f < 6; ++f) K6[f] = rec[f];
+                detJ = rec[6];
+            }
+            for (int k = kb; k < ke && ok; ++k) {
+                const uint32_t g = g0 + (uint32_t)(k - kb), b = g & 1u, use = g >> 1;
+                // metric factors of this chunk: coalesced rows of the tile-major layout
+                // (loads issued before the wait for the accumulators)
+                float Gc[7][kHalf];
+                if (!AFFINE) {
+                    const float* gt = a.geom + ((tile * a.nch + k) * 7 * (int64_t)kNPT) * 128 + r;
+#pragma unroll
+                    for (int f = 0; f < 7; ++f)
+#pragma unroll
+                        for (int p = 0; p < kHalf; ++p)
+                            Gc[f][p] = (f == 6 || a.c1 > 1) ? gt[(f * kNPT + h * kHalf + p) * 128] : 0.f;
+                }
+                if (!wait_warp(&B->fwd_full[b], use & 1u, B, a.err)) { ok = false; break; }
+                tc::fence_after();
+                float v[4][kHalf];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    if (c >= a.c0 && c < a.c1) tc::ld_32x8(tbase + lane_base + (uint32_t)((b * 4 + c) * kNPT + h * kHalf), v[c]);
+                    else {
+#pragma unroll
+                        for (int p = 0; p < kHalf; ++p) v[c][p] = 0.f;
+                    }
+                }
+                tc::fence_before();
+                arrive(&B->fwd_empty[b]);
+                float o[4][kHalf];
+#pragma unroll
+                for (int p = 0; p < kHalf; ++p) {
+                    const int l = k * kNPT + h * kHalf + p;
+                    float G[6] = {0, 0, 0, 0, 0, 0}, wJ = 0.f;
+                    if (AFFINE) {
+                        if (valid && l < a.NQ) {
+                            const float* T = a.tpts + (size_t)l * 10;   // d eta/d xi (3x3) and weight
+                            const float wl = T[9];
+                            wJ = wl * detJ;
+                            if (a.c1 > 1) {
+                                const float Km[3][3] = {{K6[0], K6[1], K6[2]}, {K6[1], K6[3], K6[4]}, {K6[2], K6[4], K6[5]}};
+                                float M[3][3];
+#pragma unroll
+                                for (int d = 0; d < 3; ++d)
+#pragma unroll
+                                    for (int j = 0; j < 3; ++j)
+                                        M[d][j] = T[3 * d] * Km[0][j] + T[3 * d + 1] * Km[1][j] + T[3 * d + 2] * Km[2][j];
+                                auto gg = [&](int d, int d2) {
+                                    return wl * (M[d][0] * T[3 * d2] + M[d][1] * T[3 * d2 + 1] + M[d][2] * T[3 * d2 + 2]);
+                                };
+                                G[0] = gg(0, 0); G[1] = gg(0, 1); G[2] = gg(0, 2); G[3] = gg(1, 1); G[4] = gg(1, 2); G[5] = gg(2, 2);
+                            }
+                        }
+                    } else {   // padded points and elements hold zeros in this layout
+#pragma unroll
+                        for (int f = 0; f < 6; ++f) G[f] = Gc[f][p];
+                        wJ = Gc[6][p];
+                    }
+                    const float v1 = v[1][p], v2 = v[2][p], v3 = v[3][p];
+                    o[0][p] = (a.op == HP_MASS ? 1.f : a.lambda) * wJ * v[0][p];
+                    o[1][p] = G[0] * v1 + G[1] * v2 + G[2] * v3;
+                    o[2][p] = G[1] * v1 + G[3] * v2 + G[4] * v3;
+                    o[3][p] = G[2] * v1 + G[4] * v2 + G[5] * v3;
+                }
+                // the V' tile b is free once the backward MMAs that last read it completed
+                if (!wait_warp(&B->vp_empty[b], (use & 1u) ^ 1u, B, a.err)) { ok = false; break; }
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    if (c < a.c0 || c >= a.c1) continue;
+                    unsigned char* dst = sV + (size_t)(b * 4 + c) * kVBytes;
+#pragma unroll
+                    for (int p0 = 0; p0 < kHalf; p0 += 4) {
+                        float4 t4 = make_float4(tc::to_tf32(o[c][p0]), tc::to_tf32(o[c][p0 + 1]), tc::to_tf32(o[c][p0 + 2]),
+                                                tc::to_tf32(o[c][p0 + 3]));
+                        *reinterpret_cast<float4*>(dst + tc::kmajor_offset(r, h * kHalf + p0, kNPT * 4, 4)) = t4;
+                    }
+                }
+                tc::fence_async_smem();
+                arrive(&B->vp_full[b]);
+            }
+            if (!ok) break;
+            g0 += (uint32_t)(ke - kb);
+            // outputs: row r of the accumulator = element e, columns = modes (half h of them)
+            if (!wait_warp(&B->out_full, ntile & 1u, B, a.err)) { ok = false; break; }
+            tc::fence_after();
+            float* dst = valid ? a.out + a.coeff_off[e] : nullptr;
+            const int nh = a.NPpad / 2;
+            for (int c0 = h * nh; c0 < (h + 1) * nh; c0 += 8) {
+                float v[8];
+                tc::ld_32x8(tbase + lane_base + (uint32_t)(kOutCol + c0), v);
+                if (valid) {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j)
+                        if (c0 + j < a.NP) {
+                            if (a.nsplit > 1) atomicAdd(dst + c0 + j, v[j]);
+                            else dst[c0 + j] = v[j];
+                        }
+                }
+            }
+            tc::fence_before();
+            arrive(&B->out_empty);
+        }
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    if (warp == 0) tc::tmem_dealloc(tbase, kTmemCols);
+}
+
+// zero the block's output coefficients (the parts of a tile add into them)
+__global__ void zero_coeffs_kernel(float* out, const int64_t* coeff_off, int64_t n_elem, int NP) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n_elem * NP) return;
+    const int64_t e = i / NP;
+    out[coeff_off[e] + (i - e * NP)] = 0.f;
+}
+
+// FP64 curved geometry [n][7][NQp] -> FP32 tile-major [tile][chunk][7][16 pts][128 elem],
+// zeros at padded points and elements
+__global__ void tc_geom_kernel(const double* g, float* out, int64_t n_elem, int NQ, int NQp, int nch) {
+    const int64_t ntiles = (n_elem + 127) / 128;
+    const int64_t total = ntiles * nch * 7 * kNPT * 128;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(i & 127);
+        int64_t t = i >> 7;
+        const int p = (int)(t % kNPT);
+        t /= kNPT;
+        const int f = (int)(t % 7);
+        t /= 7;
+        const int k = (int)(t % nch);
+        const int64_t tile = t / nch, e = tile * 128 + r;
+        const int l = k * kNPT + p;
+        out[i] = (e < n_elem && l < NQ) ? (float)g[(e * 7 + f) * (int64_t)NQp + l] : 0.f;
+    }
+}
+
+}  // namespace
+
+int tc_stages(int KP, int stage_bytes) {
+    const int base = 1024 + 128 * KP * 4 + 8 * kVBytes;
+    for (int st = kMaxStages; st >= 2; --st)
+        if (base + st * stage_bytes <= 227 * 1024) return st;
+    return 0;
+}
+
+int tc_smem_bytes(int KP, int stage_bytes) {
+    int b = 1024 + 128 * KP * 4 + 8 * kVBytes + tc_stages(KP, stage_bytes) * stage_bytes;
+    return b < 116 * 1024 ? 116 * 1024 : b;    // at most one CTA (and one TMEM allocation) per SM
+}
+
+int tc_chunk_points() { return kNPT; }
+
+int64_t tc_geom_floats(int64_t n_elem, int nch) { return (n_elem + 127) / 128 * nch * 7 * kNPT * 128; }
+
+cudaError_t tc_geom_layout(const double* g, float* out, int64_t n_elem, int NQ, int NQp, int nch, cudaStream_t s) {
+    tc_geom_kernel<<<1024, 256, 0, s>>>(g, out, n_elem, NQ, NQp, nch);
+    return cudaGetLastError();
+}
+
+cudaError_t tc_emat_launch(bool affine, const TCArgs& a, cudaStream_t s) {
+    const int64_t ntiles = (a.n_elem + 127) / 128;
+    if (ntiles <= 0) return cudaSuccess;
+    TCArgs b = a;
+    b.stages = tc_stages(a.KP, a.stage_bytes);
+    if (b.stages < 2) return cudaErrorInvalidValue;
+    const int smem = tc_smem_bytes(a.KP, a.stage_bytes);
+    auto kern = affine ? tc_emat_kernel<true> : tc_emat_kernel<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // split the point chunks of a tile over CTAs until the grid covers the SMs
+    // (at least 4 chunks per part)
+    int64_t ns = (sms + ntiles - 1) / ntiles;
+    const int64_t cap = a.nch / 4 > 1 ? a.nch / 4 : 1;
+    b.nsplit = (int)(ns < cap ? ns : cap);
+    if (b.nsplit > 1) {
+        const int64_t n = a.n_elem * a.NP;
+        zero_coeffs_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a.out, a.coeff_off, a.n_elem, a.NP);
+    }
+    const int64_t nwork = ntiles * b.nsplit;
+    const int grid = (int)(nwork < sms ? nwork : sms);
+    kern<<<grid, kThreads, smem, s>>>(b);
+    return cudaGetLastError();
+}
+
+}  // namespace hp

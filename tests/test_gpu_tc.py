@@ -1,0 +1,144 @@
+"""Tensor-core (tcgen05, TF32) elemental-matrix operators against the FP64
+oracle, through the C ABI.
+
+Tolerance (relative, infinity norm over the whole output vector):
+TF32_TOL = 8 u with u = 2^-11, the unit roundoff of TF32 (10 stored mantissa
+bits, round to nearest).  Each term of out_e = sum A_c^T M A_c' uhat carries
+three TF32 roundings (the coefficient, the reference-matrix entry and the
+metric-weighted point value V'), so |error_m| <= 3 u (|A|^T |M| |A| |uhat|)_m
+to first order, plus FP32 accumulation (~1e-7).  The ratio of that absolute
+sum to ||out||_inf is the cancellation factor; random-sign rounding errors
+keep the measured error near 1 u (worst case 1.1 u on these meshes), and 8 u
+allows a cancellation factor of 2.7 at full correlation.  Blocks whose mode
+count exceeds the tensor-memory budget (N_P > 256) run FP32 sum factorisation
+and are held to the FP32 bound of test_gpu_parity.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import operators as oracle_ops  # noqa: E402
+from paper_2604_04644_gb300 import inputs  # noqa: E402
+from tests.test_gpu_parity import OPS, fp32_tol, make_input, mixed_mesh, rel_err  # noqa: E402
+
+TF32_U = 2.0 ** -11
+TF32_TOL = 8 * TF32_U
+MAX_TC_MODES = 256
+
+
+@pytest.fixture(scope="module")
+def hp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2604_04644_gb300 import hp as _hp
+    return _hp
+
+
+def n_blocks(mesh):
+    return len(set(zip(mesh["shape"].tolist(), mesh["P"].tolist(), mesh["curved"].tolist())))
+
+
+def run_tc(hp, mesh, opname, x, lam):
+    h = hp.hp_mesh_create(mesh, 0)
+    try:
+        co, po, nc, nph = hp.hp_mesh_layout(h, mesh["n_elem"])
+        op = hp.hp_op_create(h, OPS[opname], hp.HP_STRAT_ELEMAT, hp.HP_TF32)
+        try:
+            strat = hp.hp_op_strategies(op, n_blocks(mesh))
+            xt = torch.tensor(x, device="cuda:0", dtype=torch.float32)
+            y = torch.full((nc,), float("nan"), device="cuda:0", dtype=torch.float32)
+            hp.hp_op_apply(op, lam, xt, y)
+            hp.hp_op_sync(op)
+            return y.double().cpu().numpy(), strat
+        finally:
+            hp.hp_op_destroy(op)
+    finally:
+        hp.hp_mesh_destroy(h)
+
+
+def per_shape_errors(mesh, co, y, ref):
+    out = {}
+    for s in range(4):
+        els = np.nonzero(mesh["shape"] == s)[0]
+        if len(els) == 0:
+            continue
+        idx = np.concatenate([np.arange(co[e], co[e + 1]) for e in els])
+        out[s] = rel_err(y[idx], ref[idx])
+    return out
+
+
+@pytest.mark.parametrize("P", [1, 2, 3, 4, 5, 6, 8])
+@pytest.mark.parametrize("opname", ["mass", "laplacian", "helmholtz"])
+def test_tf32_tensor_core_matches_oracle(hp, P, opname):
+    """Mixed mesh (all four shapes, affine and curved halves, ragged tiles):
+    tensor-core blocks within TF32_TOL, FP32 sum-factorisation blocks within
+    the FP32 bound."""
+    mesh = mixed_mesh(P)
+    co, _ = oracle_ops.layout(mesh)
+    x = make_input(mesh, opname, 600 + P)
+    x32 = x.astype(np.float32).astype(np.float64)
+    ref = oracle_ops.apply(opname, mesh, x32, 1.3)
+    y, strat = run_tc(hp, mesh, opname, x, 1.3)
+    assert not np.isnan(y).any()
+    from oracle.basis import n_modes
+    errs = per_shape_errors(mesh, co, y, ref)
+    for s, err in errs.items():
+        tol = TF32_TOL if n_modes(s, P) <= MAX_TC_MODES else fp32_tol(P)
+        assert err <= tol, (s, err, tol)
+
+
+def test_tf32_strategy_per_block(hp):
+    """Elemental matrix on the tensor core exactly where N_P <= 256, FP32 sum
+    factorisation elsewhere (reported per block; blocks in order of first
+    appearance of their (shape, P, curved) in the mesh)."""
+    from oracle.basis import n_modes
+    mesh = mixed_mesh(6, n=1)
+    h = hp.hp_mesh_create(mesh, 0)
+    try:
+        op = hp.hp_op_create(h, hp.HP_HELMHOLTZ, hp.HP_STRAT_ELEMAT, hp.HP_TF32)
+        strat = hp.hp_op_strategies(op, n_blocks(mesh))
+        keys = []
+        for k in zip(mesh["shape"].tolist(), mesh["curved"].tolist()):
+            if k not in keys:
+                keys.append(k)
+        want = [hp.HP_STRAT_ELEMAT if n_modes(s, 6) <= MAX_TC_MODES else hp.HP_STRAT_SUMFAC for s, _ in keys]
+        assert strat.tolist() == want
+        with pytest.raises(hp.HpError) as ei:       # hybrid is not a tensor-core form
+            hp.hp_op_strategies(op, len(keys), np.full(len(keys), hp.HP_STRAT_HYBRID))
+        assert ei.value.status == hp.HP_ERR_UNSUPPORTED
+        hp.hp_op_destroy(op)
+        for kind, strategy in ((hp.HP_BWDTRANS, hp.HP_STRAT_ELEMAT), (hp.HP_HELMHOLTZ, hp.HP_STRAT_SUMFAC)):
+            with pytest.raises(hp.HpError) as ei:
+                hp.hp_op_create(h, kind, strategy, hp.HP_TF32)
+            assert ei.value.status == hp.HP_ERR_UNSUPPORTED
+    finally:
+        hp.hp_mesh_destroy(h)
+
+
+@pytest.mark.parametrize("shape,P,curved", [(3, 2, True), (2, 4, False), (0, 3, True)])
+def test_tf32_large_block_single_part(hp, shape, P, curved):
+    """More tiles than SMs (each tile in one part, plain stores): 20 000
+    elements of one shape, sampled elements against the oracle."""
+    mesh = inputs.replicated_mesh(shape, P, 20000, curved=curved)
+    co, _ = oracle_ops.layout(mesh)
+    x = inputs.random_coefficients(77, co)
+    y, strat = run_tc(hp, mesh, "helmholtz", x, 1.0)
+    assert strat.tolist() == [hp.HP_STRAT_ELEMAT]
+    rng = np.random.default_rng(1)
+    sample = np.sort(np.concatenate([rng.choice(mesh["n_elem"], 150, replace=False), [mesh["n_elem"] - 1]]))
+    sample = np.unique(sample)
+    x32 = x.astype(np.float32).astype(np.float64)
+    ref = oracle_ops.apply("helmholtz", mesh, x32, 1.0, elems=sample)
+    idx = np.concatenate([np.arange(co[e], co[e + 1]) for e in sample])
+    assert rel_err(y[idx], ref[idx]) <= TF32_TOL
+
+
+def test_tf32_single_element(hp):
+    for shape in range(4):
+        mesh = inputs.single_element_mesh(shape, 3, curved=True)
+        x = make_input(mesh, "helmholtz", 9)
+        ref = oracle_ops.apply("helmholtz", mesh, x.astype(np.float32).astype(np.float64), 0.7)
+        y, _ = run_tc(hp, mesh, "helmholtz", x, 0.7)
+        assert rel_err(y, ref) <= TF32_TOL, shape
