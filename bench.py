@@ -269,6 +269,45 @@ def shape_order_table(dtype_name, device, reps=5):
     return out
 
 
+def precision_forms(work64, device, reps=10):
+    """The reduced-precision forms on the same mesh and coefficients as the FP64
+    workload: FP32 sum factorisation and the TF32 tensor-core elemental-matrix
+    operator (blocks over 256 modes: FP32 sum factorisation), GDOF/s (L2
+    flushed between applies) and the relative error against the FP64 result."""
+    import torch
+    from paper_2604_04644_gb300 import hp
+    dev = "cuda:%d" % device
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    out = {}
+    for w in work64:
+        y64 = torch.zeros_like(w["y"])
+        hp.hp_op_apply(w["op"], 1.0, w["x"], y64)
+        x32 = w["x"].float()
+        y32 = torch.zeros(w["nc"], device=dev, dtype=torch.float32)
+        row = {}
+        for name, strat, dt in (("fp32_sumfac", hp.HP_STRAT_SUMFAC, hp.HP_FP32),
+                                ("tf32_tensor_core", hp.HP_STRAT_ELEMAT, hp.HP_TF32)):
+            op = hp.hp_op_create(w["h"], hp.HP_HELMHOLTZ, strat, dt)
+            for _ in range(3):
+                hp.hp_op_apply(op, 1.0, x32, y32)
+            ts = []
+            for _ in range(reps):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                hp.hp_op_apply(op, 1.0, x32, y32)
+                b.record()
+                torch.cuda.synchronize(dev)
+                ts.append(a.elapsed_time(b))
+            hp.hp_op_sync(op)
+            err = float((y32.double() - y64).abs().max() / y64.abs().max())
+            row[name] = {"gdofs": round(w["dofs"] / (statistics.median(ts) * 1e-3) / 1e9, 3),
+                         "rel_err_vs_fp64": float("%.3g" % err)}
+            hp.hp_op_destroy(op)
+        out["P%d" % w["P"]] = row
+    return out
+
+
 def strategy_table(device, orders=(1, 2, 4, 6, 8), reps=3):
     """GDOF/s per shape and order of the three strategies (sum-factorised
     collocated, elemental matrix, hybrid) for the mass and Helmholtz operators
@@ -354,9 +393,31 @@ def padaptive(device, reps=10):
     tiles = hp.hp_op_tiles(op, nblocks)
     t_tuned = timed(lambda: hp.hp_op_apply_graph(op, 1.0, x, y, stream))
     hp.hp_op_destroy(op)
+    # reduced-precision forms of the same batched apply (graph launches), with
+    # their error against the FP64 result: FP32 sum factorisation; TF32 on the
+    # tensor cores (elemental matrices, FP32 sum factorisation for blocks over
+    # 256 modes); TF32 with each block's strategy chosen by measurement
+    y64 = y.clone()
+    x32 = x.float()
+    y32 = torch.zeros(nc, device="cuda:%d" % device, dtype=torch.float32)
+    forms = {}
+    for name, strat, dt, sched in (("fp32_sumfac", hp.HP_STRAT_SUMFAC, hp.HP_FP32, False),
+                                   ("tf32_tensor_core", hp.HP_STRAT_ELEMAT, hp.HP_TF32, False),
+                                   ("tf32_scheduled", hp.HP_STRAT_ELEMAT, hp.HP_TF32, True)):
+        op = hp.hp_op_create(h, hp.HP_HELMHOLTZ, strat, dt)
+        if sched:
+            hp.hp_op_schedule_exhaustive(op, 1.0, x32, y32, nblocks, stream)
+        ms = timed(lambda: hp.hp_op_apply_graph(op, 1.0, x32, y32, stream))
+        st = hp.hp_op_strategies(op, nblocks)
+        err = float((y32.double() - y64).abs().max() / y64.abs().max())
+        forms[name] = {"ms": round(ms, 4), "gdofs": round(dofs / (ms * 1e-3) / 1e9, 4),
+                       "rel_err_vs_fp64": float("%.3g" % err),
+                       "blocks_on_tensor_core": int((st == hp.HP_STRAT_ELEMAT).sum()) if dt == hp.HP_TF32 else 0}
+        hp.hp_op_destroy(op)
     hp.hp_mesh_destroy(h)
     g = lambda ms: round(dofs / (ms * 1e-3) / 1e9, 4)
     return {"workload": "helmholtz_padaptive_40x40x32_P2-8_affine_curved_halves", "elements": int(mesh["n_elem"]),
+            "reduced_precision_graph": forms,
             "dofs": int(dofs), "blocks": nblocks, "dtype": "f64",
             "per_block_launches": {"ms": round(t_stream, 4), "gdofs": g(t_stream)},
             "graph": {"ms": round(t_graph, 4), "gdofs": g(t_graph)},
@@ -491,10 +552,12 @@ def run_solve(local, cells, order=4, lam=1.0, tol=1e-10):
            "setup_s": {"mesh": round(t_mesh, 2), "c0_map": round(t_c0, 2)}}
     # warm-up (builds the Jacobi diagonal, operators and workspaces) then timed solves
     xw = torch.zeros(ng, device=dev, dtype=torch.float64)
+    hp.hp_solve(c0, lam, b, xw, tol=1e-2, mixed=2, inner_tol=1e-1, max_refinements=1)
     hp.hp_solve(c0, lam, b, xw, tol=1e-2, mixed=True, inner_tol=1e-1, max_refinements=1)
     hp.hp_solve(c0, lam, b, xw, tol=1e-2)
     sols = {}
-    for name, kw in (("fp64_pcg", dict(mixed=False)), ("mixed_fp32_pcg_fp64_ir", dict(mixed=True, inner_tol=1e-4))):
+    for name, kw in (("fp64_pcg", dict(mixed=False)), ("mixed_fp32_pcg_fp64_ir", dict(mixed=True, inner_tol=1e-4)),
+                     ("mixed_tf32_tensor_core_pcg_fp64_ir", dict(mixed=2, inner_tol=1e-3))):
         xs = torch.zeros(ng, device=dev, dtype=torch.float64)
         torch.cuda.synchronize(dev)
         t0 = time.time()
@@ -505,9 +568,10 @@ def run_solve(local, cells, order=4, lam=1.0, tol=1e-10):
         if rc:
             out[name]["error"] = hp.hp_last_error()
         sols[name] = xs
-    d = sols["fp64_pcg"] - sols["mixed_fp32_pcg_fp64_ir"]
-    out["rel_diff_mixed_vs_fp64"] = float(d.norm() / sols["fp64_pcg"].norm())
-    out["speedup_mixed_vs_fp64"] = round(out["fp64_pcg"]["seconds"] / out["mixed_fp32_pcg_fp64_ir"]["seconds"], 3)
+    for name, tag in (("mixed_fp32_pcg_fp64_ir", "mixed"), ("mixed_tf32_tensor_core_pcg_fp64_ir", "tf32_tc")):
+        d = sols["fp64_pcg"] - sols[name]
+        out["rel_diff_%s_vs_fp64" % tag] = float(d.norm() / sols["fp64_pcg"].norm())
+        out["speedup_%s_vs_fp64" % tag] = round(out["fp64_pcg"]["seconds"] / out[name]["seconds"], 3)
     hp.hp_c0_destroy(c0)
     hp.hp_mesh_destroy(h)
     print(json.dumps({"solve": out}), flush=True)
@@ -566,9 +630,12 @@ def main():
         table = shape_order_table(args.dtype, local)
     batched = None
     strategies = None
+    forms = None
     if rank == 0 and not args.no_extra:
         batched = padaptive(local)
         strategies = strategy_table(local)
+        if args.dtype == "f64":
+            forms = precision_forms(work, local)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline()
@@ -583,7 +650,7 @@ def main():
                            "l2": "flushed (256 MiB write) before every apply, outside the timed events"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                 "clocks": clk.summary(), "per_order": per_order, "per_shape_order": table,
-                "p_adaptive": batched, "strategies_gdofs_f64": strategies}
+                "p_adaptive": batched, "strategies_gdofs_f64": strategies, "precision_forms": forms}
         print(json.dumps(line), flush=True)
     for w in work:
         from paper_2604_04644_gb300 import hp

@@ -86,6 +86,12 @@ typedef enum {
     HP_STRAT_AUTO = 3      /* the library chooses per block                                       */
 } hp_strategy;
 
+/* Compute type.  HP_FP64: IEEE double throughout (the oracle-parity form).
+ * HP_FP32: single precision (CUDA cores), float arrays.  HP_TF32: the
+ * elemental-matrix strategy on the tensor cores (tcgen05, Blackwell):
+ * coefficients, reference matrices and metric-weighted point values rounded
+ * to TF32 (10-bit mantissa), products accumulated in FP32 in tensor memory;
+ * float arrays; relative error a few units of 2^-11.  HP_BF16: not built. */
 typedef enum { HP_FP64 = 0, HP_FP32 = 1, HP_TF32 = 2, HP_BF16 = 3 } hp_dtype;
 
 /* Mesh description (all host arrays, copied by hp_mesh_create).
@@ -147,8 +153,12 @@ hp_status hp_geom_copy(hp_mesh mesh, double* out7, double* out9);
 /* Create an operator of kind `kind` over all blocks of `mesh`, computing in
  * `dtype` with `strategy`.  HP_FP64 and HP_FP32 apply to every kind with
  * HP_STRAT_SUMFAC; arrays passed to hp_op_apply are double (HP_FP64) or
- * float (HP_FP32).  Errors: HP_ERR_ARG, HP_ERR_UNSUPPORTED (combination not
- * built), HP_ERR_GEOM / HP_ERR_CUDA from the geometric factors it needs. */
+ * float (HP_FP32, HP_TF32).  HP_TF32 takes HP_STRAT_ELEMAT (or AUTO) and the
+ * kinds HP_MASS, HP_LAPLACIAN, HP_HELMHOLTZ: blocks with at most 256 modes per
+ * element run the tensor-core elemental-matrix kernel, larger ones FP32 sum
+ * factorisation (hp_op_strategies reports which).  Errors: HP_ERR_ARG,
+ * HP_ERR_UNSUPPORTED (combination not built), HP_ERR_GEOM / HP_ERR_CUDA from
+ * the geometric factors it needs. */
 hp_status hp_op_create(hp_mesh mesh, hp_opkind kind, hp_strategy strategy, hp_dtype dtype,
                        hp_op* out);
 
@@ -182,7 +192,9 @@ hp_status hp_op_tiles(hp_op op, int* tiles, int64_t n_blocks, int set);
 /* Read (set = 0) or write (set = 1) the implementation strategy of each block
  * (HP_STRAT_SUMFAC, HP_STRAT_ELEMAT or HP_STRAT_HYBRID).  Writing builds the
  * dense reference matrices if a block needs them.  HP_ERR_UNSUPPORTED for a
- * dense strategy on a derivative building block. */
+ * dense strategy on a derivative building block, and for an HP_TF32 operator
+ * for anything but HP_STRAT_SUMFAC (FP32) or HP_STRAT_ELEMAT (tensor core,
+ * blocks of at most 256 modes). */
 hp_status hp_op_strategies(hp_op op, int* strategies, int64_t n_blocks, int set);
 
 /* ---------------------------------------------------------------- cost model
@@ -288,7 +300,9 @@ hp_status hp_c0_diagonal(hp_c0 c0, double lambda, double* diag, int local, void*
 typedef struct {
     double tol;            /* stop at ||b - A x|| <= tol ||b|| (FP64 residual)                 */
     int max_iter;          /* FP64 CG: iteration limit                                          */
-    int mixed;             /* 0: Jacobi-PCG in FP64; 1: FP64 refinement of FP32 Jacobi-PCG      */
+    int mixed;             /* 0: Jacobi-PCG in FP64; 1: FP64 refinement of FP32 Jacobi-PCG      *
+                            * (sum-factorised FP32 operator); 2: the same with the TF32         *
+                            * tensor-core operator inside (HP_TF32, elemental matrices)          */
     double inner_tol;      /* mixed: relative tolerance of each FP32 solve                      */
     int inner_max_iter;    /* mixed: iteration limit of each FP32 solve                         */
     int max_refinements;   /* mixed: refinement steps                                           */

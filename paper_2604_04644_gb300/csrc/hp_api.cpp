@@ -273,6 +273,16 @@ hp_status ensure_tc(hp_mesh m) {
 
 bool tc_fits(const Block& b) { return n_modes(b.shape, b.P) <= kTcMaxModes; }
 
+// strategy k (HP_STRAT_SUMFAC / ELEMAT / HYBRID) is built for block i of op:
+// derivative building blocks are sum-factorised only; a TF32 operator has FP32
+// sum factorisation and the tensor-core elemental matrix (N_P <= 256)
+bool strategy_available(const hp_op_s* op, size_t i, int k) {
+    if (k == HP_STRAT_SUMFAC) return true;
+    if (needs_deriv_geom(op->kind)) return false;
+    if (op->dtype == HP_TF32) return k == HP_STRAT_ELEMAT && tc_fits(op->mesh->blocks[i]);
+    return true;
+}
+
 // flops of the elemental-matrix (hybrid = false) or hybrid strategy per element
 double elem_flops_dense(int shape, int P, hp_opkind k, bool hybrid) {
     const int Q = P + 2;
@@ -885,9 +895,8 @@ hp_status hp_op_schedule(hp_op op, hp_mlp mlp, void* stream) {
     std::vector<int> choice(nb);
     for (int64_t i = 0; i < nb; ++i) {
         int best = 0;
-        if (!needs_deriv_geom(op->kind))
-            for (int k = 1; k < 3; ++k)
-                if (y[3 * i + k] < y[3 * i + best]) best = k;
+        for (int k = 1; k < 3; ++k)
+            if (strategy_available(op, (size_t)i, k) && y[3 * i + k] < y[3 * i + best]) best = k;
         choice[i] = best;
     }
     return hp_op_strategies(op, choice.data(), nb, 1);
@@ -899,8 +908,7 @@ hp_status hp_op_schedule_exhaustive(hp_op op, double lambda, const void* in, voi
     if (in == out) { set_error("hp_op_schedule_exhaustive: in and out must not alias"); return HP_ERR_ARG; }
     DeviceGuard guard(op->mesh->device);
     const int64_t nb = (int64_t)op->strat.size();
-    const int ns = needs_deriv_geom(op->kind) ? 1 : 3;
-    if (ns > 1) {
+    if (!needs_deriv_geom(op->kind) && op->dtype != HP_TF32) {
         hp_status st = ensure_dense(op->mesh);
         if (st) return st;
     }
@@ -914,7 +922,7 @@ hp_status hp_op_schedule_exhaustive(hp_op op, double lambda, const void* in, voi
         float best = 1e30f;
         for (int k = 0; k < 3; ++k) {
             float tot = 1e30f;
-            if (k < ns) {
+            if (strategy_available(op, (size_t)i, k)) {
                 op->strat[i] = k;
                 tot = 0.f;
                 for (int r = 0; r < 3; ++r) {

@@ -30,6 +30,7 @@ struct hp_c0_s {
     uint8_t* d_bnd = nullptr;
     // solver state (created on first solve)
     hp_op op64 = nullptr, op32 = nullptr;
+    int op32_mode = 0;                 // 1: FP32 sum factorisation, 2: TF32 tensor-core elemental matrices
     double diag_lambda = -1.0;
     double* d_diag = nullptr;          // assembled Jacobi diagonal (global)
     double* d_loc64[2] = {nullptr, nullptr};
@@ -181,10 +182,19 @@ hp_status alloc(T** p, int64_t n) {
     return e == cudaSuccess ? HP_OK : cuda_fail(e, "hp_solve workspace");
 }
 
-hp_status prepare(hp_c0 c, double lambda, bool mixed, cudaStream_t s) {
+hp_status prepare(hp_c0 c, double lambda, int mixed, cudaStream_t s) {
     hp_status st;
     if (!c->op64 && (st = hp_op_create(c->mesh, HP_HELMHOLTZ, HP_STRAT_SUMFAC, HP_FP64, &c->op64))) return st;
-    if (mixed && !c->op32 && (st = hp_op_create(c->mesh, HP_HELMHOLTZ, HP_STRAT_SUMFAC, HP_FP32, &c->op32))) return st;
+    if (mixed && c->op32 && c->op32_mode != mixed) {
+        hp_op_destroy(c->op32);
+        c->op32 = nullptr;
+    }
+    if (mixed && !c->op32) {
+        st = mixed == 2 ? hp_op_create(c->mesh, HP_HELMHOLTZ, HP_STRAT_ELEMAT, HP_TF32, &c->op32)
+                        : hp_op_create(c->mesh, HP_HELMHOLTZ, HP_STRAT_SUMFAC, HP_FP32, &c->op32);
+        if (st) return st;
+        c->op32_mode = mixed;
+    }
     if (!c->d_red && (st = alloc(&c->d_red, kRedBlocks + 1))) return st;
     for (int i = 0; i < 2; ++i)
         if (!c->d_loc64[i] && (st = alloc(&c->d_loc64[i], c->n_local))) return st;
@@ -393,14 +403,14 @@ hp_status hp_c0_diagonal(hp_c0 c, double lambda, double* diag, int local, void* 
 hp_status hp_solve(hp_c0 c, double lambda, const double* rhs, double* x, const hp_solve_opts* opts,
                    hp_solve_stats* stats, void* stream) {
     if (!c || !rhs || !x || !opts) { set_error("hp_solve: null argument"); return HP_ERR_ARG; }
-    if (!(opts->tol > 0) || opts->max_iter < 1 || (opts->mixed && (!(opts->inner_tol > 0) || opts->inner_max_iter < 1 ||
-                                                                    opts->max_refinements < 1))) {
+    if (!(opts->tol > 0) || opts->max_iter < 1 || opts->mixed < 0 || opts->mixed > 2 ||
+        (opts->mixed && (!(opts->inner_tol > 0) || opts->inner_max_iter < 1 || opts->max_refinements < 1))) {
         set_error("hp_solve: bad options");
         return HP_ERR_ARG;
     }
     cudaSetDevice(c->mesh->device);
     cudaStream_t s = (cudaStream_t)stream;
-    hp_status st = prepare(c, lambda, opts->mixed != 0, s);
+    hp_status st = prepare(c, lambda, opts->mixed, s);
     if (st) return st;
     const int64_t n = c->n_global;
     hp_solve_stats S{};
