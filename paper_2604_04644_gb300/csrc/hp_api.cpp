@@ -204,10 +204,10 @@ float round_tf32(float x) {
 
 // Reference tiles of the tensor-core elemental-matrix operator, per chunk of
 // tc_chunk_points() quadrature points: the forward operand (64 rows = 4
-// components x 16 points, K = modes) in K-slices of 32 modes (the last one
-// shorter), then the backward tiles R_c[mode][point] (rows padded to NPpad)
-// of the 4 components; all in the K-major, no-swizzle core-matrix order the
-// tensor core reads from shared memory.
+// components x 16 points, K = modes) in K-slices of 32 modes (zero padded),
+// 128-byte swizzled, then the backward tiles R_c[mode][point] (rows padded to
+// NPpad, 16 points = 64-byte swizzled rows) of the 4 components; the K-major
+// swizzled order the tensor core reads from shared memory.
 hp_status ensure_tc(hp_mesh m) {
     for (auto& kv : m->blobs) {
         DeviceBlobs& db = kv.second;
@@ -215,8 +215,9 @@ hp_status ensure_tc(hp_mesh m) {
         const int shape = kv.first / 16, P = kv.first % 16;
         const int Q = P + 2, NQ = Q * Q * Q, NP = n_modes(shape, P), NPT = tc_chunk_points();
         if (NP > kTcMaxModes) continue;
-        const int KP = (NP + 7) & ~7, NPpad = (NP + 15) & ~15, nch = (NQ + NPT - 1) / NPT;
-        const int fwd = 4 * NPT * KP * 4, bwd = NPpad * NPT * 4;    // forward: all slices of a chunk
+        const int KP = (NP + 31) & ~31, NPpad = (NP + 15) & ~15, nch = (NQ + NPT - 1) / NPT;
+        const int slice = 4 * NPT * 32 * 4;                    // 64 rows x 128 bytes
+        const int fwd = (KP / 32) * slice, bwd = NPpad * NPT * 4;
         const int64_t chunk = fwd + 4 * (int64_t)bwd;
         std::vector<double> A = dense_matrices(shape, P);
         std::vector<unsigned char> img((size_t)(chunk * nch), 0);
@@ -229,10 +230,8 @@ hp_status ensure_tc(hp_mesh m) {
                     if (l >= NQ) continue;
                     for (int mm = 0; mm < NP; ++mm) {
                         const float v = round_tf32((float)A[((size_t)c * NQ + l) * NP + mm]);
-                        const int sl = mm / 32, ks = std::min(32, KP - 32 * sl);
-                        std::memcpy(F + (size_t)sl * (4 * NPT * 32 * 4) +
-                                        tc::kmajor_offset(c * NPT + r, mm - 32 * sl, ks * 4, 4), &v, 4);
-                        std::memcpy(R + tc::kmajor_offset(mm, r, NPT * 4, 4), &v, 4);
+                        std::memcpy(F + (size_t)(mm / 32) * slice + tc::sw128_offset(c * NPT + r, mm % 32), &v, 4);
+                        std::memcpy(R + tc::sw64_offset(mm, r), &v, 4);
                     }
                 }
             }
@@ -347,7 +346,7 @@ cudaError_t launch_block(hp_op op, size_t bi, int tile, double lambda, const voi
         a.geom = b.curved ? b.d_geom_tc : b.d_geom32;
         a.tpts = blob.tc_pts;
         a.img = blob.tc_img; a.chunk_bytes = blob.tc_chunk; a.fwd_bytes = blob.tc_fwd; a.bwd_bytes = blob.tc_bwd;
-        a.stage_bytes = (std::max(4 * tc_chunk_points() * 32 * 4, blob.tc_bwd) + 127) & ~127;
+        a.stage_bytes = (std::max(4 * tc_chunk_points() * 32 * 4, blob.tc_bwd) + 1023) & ~1023;
         a.err = op->d_err;
         return tc_emat_launch(!b.curved, a, s);
     }

@@ -3,11 +3,14 @@
 // instruction descriptor of kind::tf32 / kind::f16 MMAs with FP32
 // accumulation, commit to an mbarrier, and tensor-memory loads.
 //
-// Operand layout used throughout: K-major, no swizzle.  A tile of R rows and
-// K columns is stored as 8-row x 16-byte core matrices (each one a contiguous
-// 128-byte block, row r of the core matrix at byte 16 r); core matrices that
-// are neighbours along K are LBO bytes apart, neighbours along the rows
-// (the next 8-row group) SBO bytes apart.
+// Operand layouts: K-major, either without swizzle (a tile of R rows and K
+// columns stored as 8-row x 16-byte core matrices, each a contiguous 128-byte
+// block; core matrices that are neighbours along K are LBO bytes apart,
+// neighbours along the rows SBO bytes apart) or with the 128-byte / 64-byte
+// swizzle (rows of 128 / 64 bytes, 8-row atoms of 1024 / 512 bytes at
+// 1024-byte aligned bases; the 16-byte chunk c of row r sits at chunk
+// c ^ (r mod 8), resp. c ^ ((r / 2) mod 4), so that the tensor core reads
+// rows of different atoms from different shared-memory banks).
 #pragma once
 #include <cstdint>
 #include "hp_device.cuh"
@@ -19,6 +22,15 @@ namespace tc {
 // bytes per row (a multiple of 16); elements of `es` bytes
 __host__ __device__ constexpr uint32_t kmajor_offset(uint32_t r, uint32_t k, uint32_t kbytes, uint32_t es) {
     return (r >> 3) * (kbytes * 8) + ((k * es) >> 4) * 128 + (r & 7) * 16 + ((k * es) & 15);
+}
+
+// byte offset of 4-byte element (r, k) in a K-major tile with 128-byte
+// swizzle (k < 32) and 64-byte swizzle (k < 16)
+__host__ __device__ constexpr uint32_t sw128_offset(uint32_t r, uint32_t k) {
+    return r * 128 + ((((k * 4) >> 4) ^ (r & 7)) << 4) + ((k * 4) & 15);
+}
+__host__ __device__ constexpr uint32_t sw64_offset(uint32_t r, uint32_t k) {
+    return r * 64 + ((((k * 4) >> 4) ^ ((r >> 1) & 3)) << 4) + ((k * 4) & 15);
 }
 
 __device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {   // one full warp
@@ -40,6 +52,19 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
     d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
     d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
     d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// Descriptor of a swizzled K-major operand: start address (a K step of the
+// MMA moves it by 32 bytes inside the swizzle row), SBO = 8-row atom stride,
+// mode 2 = 128-byte swizzle, 4 = 64-byte swizzle; the leading offset is unused.
+constexpr uint32_t kSw128 = 2, kSw64 = 4;
+__device__ __forceinline__ uint64_t smem_desc_sw(uint32_t saddr, uint32_t sbo, uint32_t mode) {
+    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)mode << 61;
     return d;
 }
 

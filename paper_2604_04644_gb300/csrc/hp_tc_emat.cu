@@ -39,7 +39,7 @@ constexpr int kOutCol = 128;      // TMEM column of the output accumulator (forw
 constexpr int kEpi = 256;         // epilogue threads
 constexpr int kThreads = kEpi + 64;
 constexpr int kVBytes = 128 * kNPT * 4;   // one V' tile [128 x 16] TF32
-constexpr int kSliceBytes = 4 * kNPT * 32 * 4;   // forward operand: 64 rows x 32 modes
+constexpr int kSliceBytes = 4 * kNPT * 32 * 4;   // forward operand: 64 rows x 32 modes (128-byte rows)
 
 struct Bars {
     uint64_t full[kMaxStages], empty[kMaxStages];
@@ -73,10 +73,12 @@ __device__ __forceinline__ void arrive(uint64_t* bar) {
 
 template <bool AFFINE>
 __global__ void __launch_bounds__(kThreads, 1) tc_emat_kernel(const __grid_constant__ TCArgs a) {
-    extern __shared__ __align__(1024) unsigned char smem[];
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // the swizzle patterns are taken from shared-memory address bits: align to 1 KB
+    unsigned char* smem = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
     Bars* B = reinterpret_cast<Bars*>(smem);
-    unsigned char* sU = smem + 1024;                                   // [128 x KP] tf32
-    unsigned char* sV = sU + 128 * a.KP * 4;                           // [2][4][128 x 16] tf32
+    unsigned char* sU = smem + 1024;                                   // KP/32 blocks [128 x 32] tf32, 128 B swizzle
+    unsigned char* sV = sU + 128 * a.KP * 4;                           // [2][4][128 x 16] tf32, 64 B swizzle
     unsigned char* sR = sV + 8 * kVBytes;                              // ring
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nst = a.stages;
@@ -132,10 +134,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_emat_kernel(const __grid_const
                 for (int k = kb; k <= ke && ok; ++k) {
                     if (k < ke) {
                         const unsigned char* base = a.img + (size_t)k * a.chunk_bytes;
-                        for (int sl = 0; sl * 32 < a.KP && ok; ++sl) {
-                            const int ks = min(32, a.KP - 32 * sl);
-                            put(base + (size_t)sl * kSliceBytes, 4 * kNPT * ks * 4);
-                        }
+                        for (int sl = 0; sl * 32 < a.KP && ok; ++sl) put(base + (size_t)sl * kSliceBytes, kSliceBytes);
                     }
                     if (k > kb) {
                         const unsigned char* base = a.img + (size_t)(k - 1) * a.chunk_bytes + (size_t)a.fwd_bytes;
@@ -156,7 +155,6 @@ __global__ void __launch_bounds__(kThreads, 1) tc_emat_kernel(const __grid_const
         if (lane == 0) {
             const uint32_t id_f = tc::instr_desc(tc::kFmtTF32, 128, kNPT * (a.c1 - a.c0));
             const uint32_t id_b = tc::instr_desc(tc::kFmtTF32, 128, a.NPpad);
-            const uint32_t sbo_u = a.KP * 32;
             int slot = 0;
             uint32_t pass = 0, nout = 0, ntile = 0, g0 = 0;   // g: chunks processed by this CTA
             bool ok = true;
@@ -174,13 +172,12 @@ __global__ void __launch_bounds__(kThreads, 1) tc_emat_kernel(const __grid_const
                         for (int sl = 0; sl * 32 < a.KP && ok; ++sl) {
                             if (!wait_bar(&B->full[slot], pass, B, a.err)) { ok = false; break; }
                             tc::fence_after();
-                            const int ks = min(32, a.KP - 32 * sl);
-                            const uint32_t sbo_f = ks * 32;      // 8-row group stride of this slice
-                            const uint32_t sa = smem_addr(sU) + sl * 4 * 256;
-                            const uint32_t sb = smem_addr(sR + (size_t)slot * a.stage_bytes) + a.c0 * 2 * sbo_f;
-                            for (int s = 0; s < ks / 8; ++s)
-                                tc::mma_tf32(d, tc::smem_desc(sa + s * 256, 128, sbo_u),
-                                             tc::smem_desc(sb + s * 256, 128, sbo_f), id_f, sl > 0 || s > 0);
+                            // K block sl of U (128 rows x 128 B) and rows 16 c0.. of the slice
+                            const uint32_t sa = smem_addr(sU) + sl * 128 * 128;
+                            const uint32_t sb = smem_addr(sR + (size_t)slot * a.stage_bytes) + a.c0 * 2 * 1024;
+                            for (int s = 0; s < 4; ++s)
+                                tc::mma_tf32(d, tc::smem_desc_sw(sa + s * 32, 1024, tc::kSw128),
+                                             tc::smem_desc_sw(sb + s * 32, 1024, tc::kSw128), id_f, sl > 0 || s > 0);
                             tc::commit(&B->empty[slot]);
                             if (++slot == nst) { slot = 0; pass ^= 1u; }
                         }
@@ -200,8 +197,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_emat_kernel(const __grid_const
                             const uint32_t sa = smem_addr(sV + (size_t)(b * 4 + c) * kVBytes);
                             const uint32_t sb = smem_addr(sR + (size_t)slot * a.stage_bytes);
                             for (int s = 0; s < kNPT / 8; ++s)
-                                tc::mma_tf32(tbase + kOutCol, tc::smem_desc(sa + s * 256, 128, kNPT * 32),
-                                             tc::smem_desc(sb + s * 256, 128, kNPT * 32), id_b,
+                                tc::mma_tf32(tbase + kOutCol, tc::smem_desc_sw(sa + s * 32, 512, tc::kSw64),
+                                             tc::smem_desc_sw(sb + s * 32, 512, tc::kSw64), id_b,
                                              !(k == kb + 1 && c == a.c0 && s == 0));
                             tc::commit(&B->empty[slot]);
                             if (++slot == nst) { slot = 0; pass ^= 1u; }
@@ -239,7 +236,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_emat_kernel(const __grid_const
                     float* pv = reinterpret_cast<float*>(&v);
 #pragma unroll
                     for (int i = 0; i < 4; ++i) pv[i] = (valid && m0 + i < a.NP) ? tc::to_tf32(src[m0 + i]) : 0.f;
-                    *reinterpret_cast<float4*>(sU + tc::kmajor_offset(r, m0, a.KP * 4, 4)) = v;
+                    *reinterpret_cast<float4*>(sU + (m0 >> 5) * 128 * 128 + tc::sw128_offset(r, m0 & 31)) = v;
                 }
             }
             tc::fence_async_smem();
@@ -251,18 +248,33 @@ __global__ void __launch_bounds__(kThreads, 1) tc_emat_kernel(const __grid_const
                 for (int f = 0; f < 6; ++f) K6[f] = rec[f];
                 detJ = rec[6];
             }
+            // metric factors of a chunk: this thread's 8 points of each factor are
+            // 32 contiguous bytes of the tile-major layout; the next chunk's are
+            // fetched while the current one is processed
+            float Gn[7][kHalf], Gc[7][kHalf];
+            auto load_geom = [&](int k) {
+                const float4* gt = reinterpret_cast<const float4*>(
+                    a.geom + (((tile * a.nch + k) * 7) * 128 + r) * (int64_t)kNPT + h * kHalf);
+#pragma unroll
+                for (int f = 0; f < 7; ++f) {
+                    float4 x0 = make_float4(0.f, 0.f, 0.f, 0.f), x1 = x0;
+                    if (f == 6 || a.c1 > 1) {
+                        x0 = __ldg(gt + f * 128 * kNPT / 4);
+                        x1 = __ldg(gt + f * 128 * kNPT / 4 + 1);
+                    }
+                    Gn[f][0] = x0.x; Gn[f][1] = x0.y; Gn[f][2] = x0.z; Gn[f][3] = x0.w;
+                    Gn[f][4] = x1.x; Gn[f][5] = x1.y; Gn[f][6] = x1.z; Gn[f][7] = x1.w;
+                }
+            };
+            if (!AFFINE && kb < ke) load_geom(kb);
             for (int k = kb; k < ke && ok; ++k) {
                 const uint32_t g = g0 + (uint32_t)(k - kb), b = g & 1u, use = g >> 1;
-                // metric factors of this chunk: coalesced rows of the tile-major layout
-                // (loads issued before the wait for the accumulators)
-                float Gc[7][kHalf];
                 if (!AFFINE) {
-                    const float* gt = a.geom + ((tile * a.nch + k) * 7 * (int64_t)kNPT) * 128 + r;
 #pragma unroll
                     for (int f = 0; f < 7; ++f)
 #pragma unroll
-                        for (int p = 0; p < kHalf; ++p)
-                            Gc[f][p] = (f == 6 || a.c1 > 1) ? gt[(f * kNPT + h * kHalf + p) * 128] : 0.f;
+                        for (int p = 0; p < kHalf; ++p) Gc[f][p] = Gn[f][p];
+                    if (k + 1 < ke) load_geom(k + 1);
                 }
                 if (!wait_warp(&B->fwd_full[b], use & 1u, B, a.err)) { ok = false; break; }
                 tc::fence_after();
@@ -322,7 +334,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_emat_kernel(const __grid_const
                     for (int p0 = 0; p0 < kHalf; p0 += 4) {
                         float4 t4 = make_float4(tc::to_tf32(o[c][p0]), tc::to_tf32(o[c][p0 + 1]), tc::to_tf32(o[c][p0 + 2]),
                                                 tc::to_tf32(o[c][p0 + 3]));
-                        *reinterpret_cast<float4*>(dst + tc::kmajor_offset(r, h * kHalf + p0, kNPT * 4, 4)) = t4;
+                        *reinterpret_cast<float4*>(dst + tc::sw64_offset(r, h * kHalf + p0)) = t4;
                     }
                 }
                 tc::fence_async_smem();
@@ -365,16 +377,16 @@ __global__ void zero_coeffs_kernel(float* out, const int64_t* coeff_off, int64_t
     out[coeff_off[e] + (i - e * NP)] = 0.f;
 }
 
-// FP64 curved geometry [n][7][NQp] -> FP32 tile-major [tile][chunk][7][16 pts][128 elem],
+// FP64 curved geometry [n][7][NQp] -> FP32 tile-major [tile][chunk][7][128 elem][16 pts],
 // zeros at padded points and elements
 __global__ void tc_geom_kernel(const double* g, float* out, int64_t n_elem, int NQ, int NQp, int nch) {
     const int64_t ntiles = (n_elem + 127) / 128;
     const int64_t total = ntiles * nch * 7 * kNPT * 128;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-        const int r = (int)(i & 127);
-        int64_t t = i >> 7;
-        const int p = (int)(t % kNPT);
-        t /= kNPT;
+        const int p = (int)(i % kNPT);
+        int64_t t = i / kNPT;
+        const int r = (int)(t & 127);
+        t >>= 7;
         const int f = (int)(t % 7);
         t /= 7;
         const int k = (int)(t % nch);
@@ -387,14 +399,14 @@ __global__ void tc_geom_kernel(const double* g, float* out, int64_t n_elem, int 
 }  // namespace
 
 int tc_stages(int KP, int stage_bytes) {
-    const int base = 1024 + 128 * KP * 4 + 8 * kVBytes;
+    const int base = 2048 + 128 * KP * 4 + 8 * kVBytes;      // alignment slack + barriers + U + V
     for (int st = kMaxStages; st >= 2; --st)
         if (base + st * stage_bytes <= 227 * 1024) return st;
     return 0;
 }
 
 int tc_smem_bytes(int KP, int stage_bytes) {
-    int b = 1024 + 128 * KP * 4 + 8 * kVBytes + tc_stages(KP, stage_bytes) * stage_bytes;
+    int b = 2048 + 128 * KP * 4 + 8 * kVBytes + tc_stages(KP, stage_bytes) * stage_bytes;
     return b < 116 * 1024 ? 116 * 1024 : b;    // at most one CTA (and one TMEM allocation) per SM
 }
 
