@@ -335,6 +335,22 @@ hp_status hp_op_sync(hp_op op, void* stream);
  * roofline.  Any pointer may be NULL. */
 hp_status hp_op_work(hp_op op, int64_t* out_dofs, double* flops, double* bytes);
 
+/* The same accounting for one block (block >= 0; -1 = the whole operator, as
+ * hp_op_work), plus its element count and exec_flops: the floating-point
+ * operations the block's kernel issues (FMA = 2), which the FP64
+ * sum-factorised kernel brings below the collocated count `flops` by the
+ * even-odd symmetry of the GLL direction and by skipping the padding of the
+ * collapsed index ranges.  Blocks are numbered as in hp_op_tiles.  Any output
+ * pointer may be NULL.  Errors: HP_ERR_ARG. */
+hp_status hp_op_block_work(hp_op op, int64_t block, int64_t* n_elem, int64_t* out_dofs, double* flops,
+                           double* exec_flops, double* bytes);
+
+/* Apply the operator to the elements of one block only (one kernel launch,
+ * as hp_op_apply does for every block in turn); outputs of other blocks are
+ * left untouched.  Launching every block in order is hp_op_apply; used to time
+ * the kernels one by one.  Errors as hp_op_apply, HP_ERR_ARG for a bad block. */
+hp_status hp_op_apply_block(hp_op op, int64_t block, double lambda, const void* in, void* out, void* stream);
+
 void hp_op_destroy(hp_op op);
 void hp_mesh_destroy(hp_mesh mesh);
 const char* hp_status_str(hp_status s);

@@ -322,6 +322,36 @@ double elem_flops(int shape, int P, hp_opkind k) {
     }
 }
 
+// floating-point operations the sum-factorisation kernel issues per element
+// (FMA = 2): the compact eta3/eta2 passes over the valid index sets; in FP64
+// the even-odd eta1 pass (u, and du/deta1 for the derivative operators, from
+// the parity-form table), collocated derivatives along eta2 and eta3 only,
+// the paired transposed pass with its even-odd sweeps and the eta1
+// restriction of (y, w1); in FP32 the line passes of the plain algorithm
+double elem_flops_exec(int shape, int P, hp_opkind k, bool fp64) {
+    const int n = P + 1, Q = P + 2, Qh = (Q + 1) / 2;
+    const double NQ = (double)Q * Q * Q, QQ = (double)Q * Q;
+    const double npr = npairs_c(shape, P), nvl = nvalid_c(shape, P);
+    const double b3 = 2.0 * Q * nvl, b2 = 2.0 * QQ * npr;
+    const double r3 = b3, r2 = 2.0 * Q * Q * npr;
+    if (!fp64 || k == HP_PHYSDERIV || k == HP_IPRODUCT_WRT_DERIV_BASE) return elem_flops(shape, P, k);
+    const double u1 = Qh * QQ * (2.0 * n + 2.0);                 // eta1 pass, u only
+    const double v1 = Qh * QQ * (2.0 * (n - 1) + 2.0);           // du/deta1 in the same pass
+    const double r1_plain = 2.0 * Q * n * QQ;
+    switch (k) {
+        case HP_BWDTRANS: return b3 + b2 + u1;
+        case HP_IPRODUCT_WRT_BASE: return NQ + r1_plain + r2 + r3;
+        case HP_MASS: return b3 + b2 + u1 + NQ + r1_plain + r2 + r3;
+        default: {
+            const double d = 4.0 * Q * NQ;                           // eta2, eta3 derivatives
+            const double dt = Qh * QQ * (8.0 * Q + 4.0);              // paired transposed pass + sweeps
+            const double r1 = 4.0 * Qh * n * QQ;                      // eta1 restriction of (y, w1)
+            const double metric = (k == HP_HELMHOLTZ ? 18.0 : 15.0) * NQ;
+            return b3 + b2 + u1 + v1 + d + metric + dt + r1 + r2 + r3;
+        }
+    }
+}
+
 template <typename T>
 void fill_const_tables(const Block& b, SFArgs<T>& a) {
     const RefTables& t = ref_tables(b.shape, b.P);
@@ -960,20 +990,37 @@ hp_status hp_op_sync(hp_op op, void* stream) {
     return check_device_error(op->mesh, op->d_err, nullptr, "hp_op_sync");
 }
 
-hp_status hp_op_work(hp_op op, int64_t* out_dofs, double* flops, double* bytes) {
-    if (!op) { set_error("hp_op_work: null op"); return HP_ERR_ARG; }
+hp_status hp_op_apply_block(hp_op op, int64_t block, double lambda, const void* in, void* out, void* stream) {
+    if (!op || !in || !out) { set_error("hp_op_apply_block: null argument"); return HP_ERR_ARG; }
+    if (in == out) { set_error("hp_op_apply_block: in and out must not alias"); return HP_ERR_ARG; }
+    if (block < 0 || block >= (int64_t)op->mesh->blocks.size()) { set_error("hp_op_apply_block: bad block"); return HP_ERR_ARG; }
+    DeviceGuard guard(op->mesh->device);
+    cudaError_t e = launch_block(op, (size_t)block, op->tile[block], lambda, in, out, (cudaStream_t)stream);
+    return e == cudaSuccess ? HP_OK : cuda_fail(e, "hp_op_apply_block launch");
+}
+
+hp_status hp_op_block_work(hp_op op, int64_t block, int64_t* n_elem, int64_t* out_dofs, double* flops,
+                           double* exec_flops, double* bytes) {
+    if (!op || block < -1 || block >= (int64_t)op->mesh->blocks.size()) {
+        set_error("hp_op_block_work: bad argument");
+        return HP_ERR_ARG;
+    }
     const hp_mesh m = op->mesh;
     const double vs = op->dtype == HP_FP64 ? 8.0 : 4.0;
-    int64_t dofs = 0;
-    double fl = 0, by = 0;
+    int64_t dofs = 0, ne_tot = 0;
+    double fl = 0, fx = 0, by = 0;
     for (const Block& b : m->blocks) {
+        size_t bi = &b - &m->blocks[0];
+        if (block >= 0 && (int64_t)bi != block) continue;
         const double NQ = (double)b.Q * b.Q * b.Q;
         const double np = (double)n_modes(b.shape, b.P);
         const double ne = (double)b.n_elem;
-        size_t bi = &b - &m->blocks[0];
+        ne_tot += b.n_elem;
         const int st = op->strat[bi];
-        fl += ne * (st == HP_STRAT_SUMFAC ? elem_flops(b.shape, b.P, op->kind)
-                                          : elem_flops_dense(b.shape, b.P, op->kind, st == HP_STRAT_HYBRID));
+        const double fd = st == HP_STRAT_SUMFAC ? elem_flops(b.shape, b.P, op->kind)
+                                                : elem_flops_dense(b.shape, b.P, op->kind, st == HP_STRAT_HYBRID);
+        fl += ne * fd;
+        fx += ne * (st == HP_STRAT_SUMFAC ? elem_flops_exec(b.shape, b.P, op->kind, op->dtype == HP_FP64) : fd);
         double in_v = coeff_in(op->kind) ? np : (op->kind == HP_IPRODUCT_WRT_DERIV_BASE ? 3 * NQ : NQ);
         double out_v = coeff_out(op->kind) ? np : (op->kind == HP_PHYSDERIV ? 3 * NQ : NQ);
         dofs += (int64_t)(ne * (coeff_out(op->kind) ? np : out_v));
@@ -989,10 +1036,17 @@ hp_status hp_op_work(hp_op op, int64_t* out_dofs, double* flops, double* bytes) 
         }
         by += ne * ((in_v + out_v + geo) * vs + 8.0);
     }
+    if (n_elem) *n_elem = ne_tot;
     if (out_dofs) *out_dofs = dofs;
     if (flops) *flops = fl;
+    if (exec_flops) *exec_flops = fx;
     if (bytes) *bytes = by;
     return HP_OK;
+}
+
+hp_status hp_op_work(hp_op op, int64_t* out_dofs, double* flops, double* bytes) {
+    if (!op) { set_error("hp_op_work: null op"); return HP_ERR_ARG; }
+    return hp_op_block_work(op, -1, nullptr, out_dofs, flops, nullptr, bytes);
 }
 
 void hp_op_destroy(hp_op op) {

@@ -31,6 +31,7 @@ HP_FP64, HP_FP32, HP_TF32, HP_BF16 = range(4)
 EXPORTED = ["hp_mesh_create", "hp_mesh_layout", "hp_geom_factors", "hp_geom_copy", "hp_op_create",
             "hp_op_apply", "hp_op_apply_graph", "hp_op_tune", "hp_op_tiles", "hp_op_strategies",
             "hp_op_block_features", "hp_op_schedule", "hp_op_schedule_exhaustive", "hp_op_sync", "hp_op_work",
+            "hp_op_block_work", "hp_op_apply_block",
             "hp_op_destroy", "hp_mesh_destroy", "hp_status_str", "hp_last_error",
             "hp_mlp_create", "hp_mlp_info", "hp_mlp_params", "hp_mlp_forward", "hp_mlp_grad", "hp_mlp_adam_step",
             "hp_mlp_destroy", "hp_mlp_grad_noalloc", "hp_mesh_points", "hp_c0_create", "hp_c0_info",
@@ -77,6 +78,8 @@ _lib.hp_mlp_grad_noalloc.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_i
 _lib.hp_mlp_grad_noalloc.restype = ctypes.c_int
 _lib.hp_op_sync.argtypes = [_vp, _vp]
 _lib.hp_op_work.argtypes = [_vp, _i64p, _dp, _dp]
+_lib.hp_op_block_work.argtypes = [_vp, ctypes.c_int64, _i64p, _i64p, _dp, _dp, _dp]
+_lib.hp_op_apply_block.argtypes = [_vp, ctypes.c_int64, ctypes.c_double, _vp, _vp, _vp]
 _lib.hp_op_destroy.argtypes = [_vp]
 _lib.hp_mesh_destroy.argtypes = [_vp]
 _lib.hp_status_str.argtypes = [ctypes.c_int]
@@ -84,7 +87,7 @@ _lib.hp_status_str.restype = ctypes.c_char_p
 _lib.hp_last_error.restype = ctypes.c_char_p
 for _f in ("hp_mesh_create", "hp_mesh_layout", "hp_geom_factors", "hp_geom_copy", "hp_op_create",
            "hp_op_apply", "hp_op_apply_graph", "hp_op_tune", "hp_op_tiles", "hp_op_sync", "hp_op_work",
-           "hp_op_strategies", "hp_op_block_features", "hp_op_schedule", "hp_op_schedule_exhaustive",
+           "hp_op_block_work", "hp_op_apply_block", "hp_op_strategies", "hp_op_block_features", "hp_op_schedule", "hp_op_schedule_exhaustive",
            "hp_mlp_create", "hp_mlp_info", "hp_mlp_params", "hp_mlp_forward", "hp_mlp_grad", "hp_mlp_adam_step"):
     getattr(_lib, _f).restype = ctypes.c_int
 
@@ -186,6 +189,23 @@ def hp_op_work(op):
     d, f, b = ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
     _check(_lib.hp_op_work(op, ctypes.byref(d), ctypes.byref(f), ctypes.byref(b)), "hp_op_work")
     return d.value, f.value, b.value
+
+
+def hp_op_block_work(op, block):
+    """(n_elem, output DOFs, collocated flops, executed flops, bytes) of one
+    block (-1: the whole operator)."""
+    n = ctypes.c_int64(0)
+    d = ctypes.c_int64(0)
+    f = ctypes.c_double(0)
+    fx = ctypes.c_double(0)
+    b = ctypes.c_double(0)
+    _check(_lib.hp_op_block_work(op, int(block), ctypes.byref(n), ctypes.byref(d), ctypes.byref(f), ctypes.byref(fx),
+                                 ctypes.byref(b)), "hp_op_block_work")
+    return n.value, d.value, f.value, fx.value, b.value
+
+
+def hp_op_apply_block(op, block, lam, x, y, stream=None):
+    _check(_lib.hp_op_apply_block(op, int(block), float(lam), _ptr(x), _ptr(y), _stream(stream)), "hp_op_apply_block")
 
 
 def hp_op_destroy(op):
