@@ -55,6 +55,9 @@ def parse():
     p.add_argument("--solve", action="store_true",
                    help="assembled Helmholtz solve (time to 1e-10): FP64 PCG vs mixed FP32 PCG + FP64 refinement")
     p.add_argument("--no-extra", action="store_true", help="skip the p-adaptive batched measurement")
+    p.add_argument("--profile-case", default=None, choices=["tc_tet8"],
+                   help="run one small case for a profiler capture instead (tc_tet8: TF32 tensor-core Helmholtz, "
+                        "19 456 curved tets, P = 8, three applies)")
     p.add_argument("--orders", default=None, help="comma-separated orders (default 1..8); for profiling runs")
     p.add_argument("--cells", type=int, default=None, help="cells per direction (default 16); for profiling runs")
     a = p.parse_args()
@@ -597,9 +600,32 @@ def run_solve(local, cells, order=4, lam=1.0, tol=1e-10):
     print(json.dumps({"solve": out}), flush=True)
 
 
+def run_profile_case(name, local):
+    """A small, fixed case for an ncu capture (a few hundred MB on the device)."""
+    import torch
+    from paper_2604_04644_gb300 import hp, inputs
+    torch.cuda.set_device(local)
+    mesh = inputs.replicated_mesh(3, 8, 19456, curved=True)
+    h = hp.hp_mesh_create(mesh, local)
+    co, po, nc, nph = hp.hp_mesh_layout(h, mesh["n_elem"])
+    x = torch.tensor(inputs.random_coefficients(5, co), device="cuda:%d" % local, dtype=torch.float32)
+    y = torch.zeros(nc, device="cuda:%d" % local, dtype=torch.float32)
+    op = hp.hp_op_create(h, hp.HP_HELMHOLTZ, hp.HP_STRAT_ELEMAT, hp.HP_TF32)
+    for _ in range(3):
+        hp.hp_op_apply(op, 1.0, x, y)
+    hp.hp_op_sync(op)
+    hp.hp_op_destroy(op)
+    hp.hp_mesh_destroy(h)
+    print(json.dumps({"profile_case": name, "elements": int(mesh["n_elem"]), "ok": True}), flush=True)
+
+
 def main():
     args = parse()
     world, rank, local = dist_init(args)
+    if args.profile_case:
+        if rank == 0:
+            run_profile_case(args.profile_case, local)
+        return
     if args.solve:
         if rank == 0:
             run_solve(local, args.cells or 64)
