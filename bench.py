@@ -511,7 +511,8 @@ def run_reference(args, world, rank):
 
 def run_costmodel(local):
     """Learned strategy scheduling: timings over shape x P=1..10 x affine/curved x
-    10^2..10^5 elements x {FP64, FP32} (the library's own kernels), one MLP per
+    10^2..10^6 elements x {FP64, FP32, TF32} (the library's own kernels; 10^6
+    extrapolated from 10^5), one MLP per
     operator trained on the GPU by the library's kernels, evaluated on a held-out
     16x16x32-cell mesh with P ~ U{3..9} and affine/curved halves."""
     import torch
@@ -529,12 +530,14 @@ def run_costmodel(local):
         pred = costmodel.predict(mlp, X, local)
         ev64 = costmodel.evaluate_schedules(mlp, held, kind, hp.HP_FP64, local)
         ev32 = costmodel.evaluate_schedules(mlp, held, kind, hp.HP_FP32, local)
+        evtf = costmodel.evaluate_schedules(mlp, held, kind, hp.HP_TF32, local)
         res[name] = {"samples": int(len(X)), "extrapolated_entries": int(sum(sum(m["extrapolated"]) for m in meta)),
                      "timing_s": round(t_gen, 1), "train_s": round(t_train, 1),
                      "train_loss_first_last": [hist[0][1], hist[-1][1]],
                      "train_rmse_log10": float(np.sqrt(np.mean((pred - T) ** 2))),
                      "train_argmin_accuracy": float(np.mean(pred.argmin(1) == T.argmin(1))),
-                     "held_out_f64": ev64, "held_out_f32": ev32}
+                     "samples_measured": int(sum(1 for m in meta if not all(m["extrapolated"]))),
+                     "held_out_f64": ev64, "held_out_f32": ev32, "held_out_tf32": evtf}
         hp.hp_mlp_destroy(mlp)
     print(json.dumps({"costmodel": res, "held_out_mesh": {"cells": "16x16x32", "elements": int(held["n_elem"]),
                                                           "orders": "U{3..9}", "curved": "x >= 0.5"}}), flush=True)

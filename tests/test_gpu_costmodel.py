@@ -113,3 +113,38 @@ def test_mlp_argument_checks(hp):
         hp.hp_mlp_create(5, 48, 3)          # hidden not a multiple of 32
     with pytest.raises(hp.HpError):
         hp.hp_mlp_create(40, 64, 3)
+
+
+def test_tf32_schedules_only_built_strategies(hp):
+    """A TF32 operator has FP32 sum factorisation and the tensor-core elemental
+    matrix (blocks of at most 256 modes): both schedulers choose among those
+    only, whatever the network predicts for the hybrid strategy."""
+    from oracle.basis import n_modes
+    mesh = inputs.slab_mesh(2, 2, 4, (2, 7), order_seed=5, curved_rule="x_half")
+    keys = []
+    for k in zip(mesh["shape"].tolist(), mesh["P"].tolist(), mesh["curved"].tolist()):
+        if k not in keys:
+            keys.append(k)
+    nb = len(keys)
+    fits = np.array([n_modes(s, P) <= 256 for s, P, _ in keys])
+    h = hp.hp_mesh_create(mesh, 0)
+    m = hp.hp_mlp_create(5, 32, 3, seed=1)
+    try:
+        co, po, nc, nph = hp.hp_mesh_layout(h, mesh["n_elem"])
+        op = hp.hp_op_create(h, hp.HP_HELMHOLTZ, hp.HP_STRAT_ELEMAT, hp.HP_TF32)
+        p = np.zeros(hp.hp_mlp_info(m)[3], dtype=np.float32)
+        p[-3:] = [2.0, 1.0, 0.5]          # hybrid smallest, then the elemental matrix
+        hp.hp_mlp_params(m, p)
+        hp.hp_op_schedule(op, m)
+        st = hp.hp_op_strategies(op, nb)
+        assert (st[fits] == hp.HP_STRAT_ELEMAT).all() and (st[~fits] == hp.HP_STRAT_SUMFAC).all()
+        x = torch.tensor(inputs.random_coefficients(5, co), device="cuda:0", dtype=torch.float32)
+        y = torch.zeros(nc, device="cuda:0", dtype=torch.float32)
+        times = hp.hp_op_schedule_exhaustive(op, 1.0, x, y, nb)
+        assert (times[:, 2] >= 1e29).all() and (times[~fits, 1] >= 1e29).all()
+        best = hp.hp_op_strategies(op, nb)
+        assert (best == times.argmin(axis=1)).all() and (best != hp.HP_STRAT_HYBRID).all()
+        hp.hp_op_destroy(op)
+    finally:
+        hp.hp_mlp_destroy(m)
+        hp.hp_mesh_destroy(h)
