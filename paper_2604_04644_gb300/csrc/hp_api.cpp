@@ -327,10 +327,7 @@ double elem_flops(int shape, int P, hp_opkind k) {
 // the even-odd eta1 pass (u, and du/deta1 for the derivative operators, from
 // the parity-form table), collocated derivatives along eta2 and eta3 only,
 // the paired transposed pass with its even-odd sweeps and the eta1
-// restriction of (y, w1); for hexahedra, prisms and pyramids also eta2 in
-// even-odd form (g and dg/deta2 from one pass, du/deta2 from the eta1 pass,
-// w2 restricted through eta1 and eta2 instead of D^T); in FP32 the line
-// passes of the plain algorithm
+// restriction of (y, w1); in FP32 the line passes of the plain algorithm
 double elem_flops_exec(int shape, int P, hp_opkind k, bool fp64) {
     const int n = P + 1, Q = P + 2, Qh = (Q + 1) / 2;
     const double NQ = (double)Q * Q * Q, QQ = (double)Q * Q;
@@ -341,27 +338,15 @@ double elem_flops_exec(int shape, int P, hp_opkind k, bool fp64) {
     const double u1 = Qh * QQ * (2.0 * n + 2.0);                 // eta1 pass, u only
     const double v1 = Qh * QQ * (2.0 * (n - 1) + 2.0);           // du/deta1 in the same pass
     const double r1_plain = 2.0 * Q * n * QQ;
-    // hexahedra, prisms, pyramids: eta2 in even-odd form too
-    const bool eo2 = shape != HP_TET;
-    const double b2e = n * Qh * Q * (2.0 * n + 2.0);               // paired eta2 pass, g only
     switch (k) {
-        case HP_BWDTRANS: return b3 + (eo2 ? b2e : b2) + u1;
+        case HP_BWDTRANS: return b3 + b2 + u1;
         case HP_IPRODUCT_WRT_BASE: return NQ + r1_plain + r2 + r3;
-        case HP_MASS: return b3 + (eo2 ? b2e : b2) + u1 + NQ + r1_plain + r2 + r3;
+        case HP_MASS: return b3 + b2 + u1 + NQ + r1_plain + r2 + r3;
         default: {
-            const double metric = (k == HP_HELMHOLTZ ? 18.0 : 15.0) * NQ;
-            if (eo2) {
-                const double b2d = n * Qh * Q * (4.0 * n + 2.0);        // g and dg/deta2
-                const double v2 = Qh * QQ * (2.0 * n + 2.0);           // du/deta2 in the eta1 pass
-                const double d = 2.0 * Q * NQ;                         // eta3 derivative only
-                const double dt = Qh * QQ * (4.0 * Q + 6.0);           // D_3^T pairs + sweeps of y, w1, w2
-                const double r1 = n * Qh * Q * (12.0 * Qh + 4.0);      // (y, w1) and w2, paired in eta2
-                const double r2e = npr * Q * 4.0 * Qh;                 // parity eta2 restriction of (gA, gB)
-                return b3 + b2d + u1 + v1 + v2 + d + metric + dt + r1 + r2e + r3;
-            }
             const double d = 4.0 * Q * NQ;                           // eta2, eta3 derivatives
             const double dt = Qh * QQ * (8.0 * Q + 4.0);              // paired transposed pass + sweeps
             const double r1 = 4.0 * Qh * n * QQ;                      // eta1 restriction of (y, w1)
+            const double metric = (k == HP_HELMHOLTZ ? 18.0 : 15.0) * NQ;
             return b3 + b2 + u1 + v1 + d + metric + dt + r1 + r2 + r3;
         }
     }

@@ -96,10 +96,6 @@ __global__ void __launch_bounds__(256) sf_kernel(const __grid_constant__ SFArgs<
     const bool deriv = (op == HP_LAPLACIAN || op == HP_HELMHOLTZ || op == HP_PHYSDERIV);
     const bool sumderiv = (op == HP_LAPLACIAN || op == HP_HELMHOLTZ || op == HP_IPRODUCT_WRT_DERIV_BASE);
     const bool merged = !LINES && deriv && coeff_in;   // v1 comes out of the eta1 pass
-    // FP64 hexahedra, prisms and pyramids: eta2 is a GLL direction with family
-    // 0 as well, handled in even-odd form like eta1 (sum/difference of the b =
-    // 0, 1 slots, parity tables, du/deta2 from the eta2 pass)
-    constexpr bool EO2 = !LINES && SHAPE != HP_TET;
     const int64_t ngroups = (args.n_elem + EPB - 1) / EPB;
 
     for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x) {
@@ -117,27 +113,9 @@ __global__ void __launch_bounds__(256) sf_kernel(const __grid_constant__ SFArgs<
                     int m = slot2mode[sl];
                     if (m >= 0) {
                         const T* cin = args.in + args.coeff_off[e0 + e];
-                        if constexpr (EO2) {
-                            // sum / difference over a in {0, 1} and over b in {0, 1}
-                            const int a = sl / NN, b = (sl / n) % n;
-                            const int na = a <= 1 ? 2 : 1, nb = b <= 1 ? 2 : 1;
-                            const int base = sl - (a <= 1 ? a * NN : 0) - (b <= 1 ? b * n : 0);
-#pragma unroll
-                            for (int ia = 0; ia < 2; ++ia) {
-                                if (ia >= na) break;
-#pragma unroll
-                                for (int ib = 0; ib < 2; ++ib) {
-                                    if (ib >= nb) break;
-                                    const int s2 = base + (a <= 1 ? ia * NN : 0) + (b <= 1 ? ib * n : 0);
-                                    const T x = cin[slot2mode[s2]];
-                                    v += ((a == 1 && ia == 1) != (b == 1 && ib == 1)) ? -x : x;
-                                }
-                            }
-                        } else {
-                            if (sl >= 2 * NN) v = cin[m];
-                            else if (sl < NN) v = cin[m] + cin[slot2mode[sl + NN]];
-                            else v = cin[slot2mode[sl - NN]] - cin[m];
-                        }
+                        if (sl >= 2 * NN) v = cin[m];
+                        else if (sl < NN) v = cin[m] + cin[slot2mode[sl + NN]];
+                        else v = cin[slot2mode[sl - NN]] - cin[m];
                     }
                 }
                 S2[e * NQ + sl] = v;
@@ -170,35 +148,6 @@ __global__ void __launch_bounds__(256) sf_kernel(const __grid_constant__ SFArgs<
                 }
             }
             __syncthreads();
-            if constexpr (EO2) {
-            // eta2 pass in even-odd pairs (j, Q-1-j) with the parity table (rows of
-            // parity (-1)^b): g = sum_b Tp[b][j] f[a][b][k], and for the derivative
-            // operators g' = sum_b Td[b][j] f[a][b][k] (to v2 = du/deta2), kept in
-            // the v3 region until the D pass
-            for (int idx = tid; idx < EPB * n * Qh * Q; idx += NT) {
-                int e = idx / (n * Qh * Q), r = idx - e * (n * Qh * Q);
-                int a = r / (Qh * Q), jk = r - a * (Qh * Q), j = jk / Q, k = jk - j * Q, j2 = Q - 1 - j;
-                const T* x = S1 + e * 4 * NQ + a * n * Q + k;
-                T ev = T(0), od = T(0);
-#pragma unroll
-                for (int b = 0; b < n; b += 2) ev += Ta[b * Q + j] * x[b * Q];
-#pragma unroll
-                for (int b = 1; b < n; b += 2) od += Ta[b * Q + j] * x[b * Q];
-                T* gg = S2 + e * NQ + a * QQ + k;
-                gg[j * Q] = ev + od;
-                if (j2 != j) gg[j2 * Q] = ev - od;
-                if (merged) {
-                    T dv = T(0), dd = T(0);
-#pragma unroll
-                    for (int b = 1; b < n; b += 2) dv += Td[b * Q + j] * x[b * Q];
-#pragma unroll
-                    for (int b = 2; b < n; b += 2) dd += Td[b * Q + j] * x[b * Q];
-                    T* gd = S1 + e * 4 * NQ + 3 * NQ + a * QQ + k;
-                    gd[j * Q] = dv + dd;
-                    if (j2 != j) gd[j2 * Q] = dv - dd;
-                }
-            }
-            } else {
             // eta2 pass: g[a][j][k] = sum_{b < len_b(a)} Tb[t(a)][b][j] f[p(a,b)][k]
             for (int idx = tid; idx < EPB * n * QQ; idx += NT) {
                 int e = idx / (n * QQ), r = idx - e * (n * QQ);
@@ -220,7 +169,6 @@ __global__ void __launch_bounds__(256) sf_kernel(const __grid_constant__ SFArgs<
                     }
                 }
                 S2[e * NQ + r] = acc;
-            }
             }
             __syncthreads();
             if constexpr (LINES) {
@@ -268,16 +216,6 @@ __global__ void __launch_bounds__(256) sf_kernel(const __grid_constant__ SFArgs<
                     for (int a = 2; a < n; a += 2) dd += Td[a * Q + i] * x[a * QQ];
                     u[NQ + i * QQ] = dv + dd;
                     if (i2 != i) u[NQ + i2 * QQ] = dv - dd;
-                    if constexpr (EO2) {       // v2 = du/deta2 = sum_a Tp[a][i] g'[a]
-                        const T* xd = S1 + e * 4 * NQ + 3 * NQ + jk;
-                        T e2 = T(0), o2 = T(0);
-#pragma unroll
-                        for (int a = 0; a < n; a += 2) e2 += Ta[a * Q + i] * xd[a * QQ];
-#pragma unroll
-                        for (int a = 1; a < n; a += 2) o2 += Ta[a * Q + i] * xd[a * QQ];
-                        u[2 * NQ + i * QQ] = e2 + o2;
-                        if (i2 != i) u[2 * NQ + i2 * QQ] = e2 - o2;
-                    }
                 }
             }
             __syncthreads();
@@ -364,14 +302,11 @@ __global__ void __launch_bounds__(256) sf_kernel(const __grid_constant__ SFArgs<
                 int e = idx / NQ, r = idx - e * NQ;
                 int i = r / QQ, jk = r - i * QQ, j = jk / Q, k = jk - j * Q;
                 const T* u = S1 + e * 4 * NQ;
-                T a3 = T(0);
+                T a2 = T(0), a3 = T(0);
 #pragma unroll
-                for (int m = 0; m < Q; ++m) a3 += D2[k * Q + m] * u[i * QQ + j * Q + m];
-                if (!(EO2 && merged)) {     // v2 came out of the eta2 / eta1 passes otherwise
-                    T a2 = T(0);
-#pragma unroll
-                    for (int m = 0; m < Q; ++m) a2 += D1[j * Q + m] * u[i * QQ + m * Q + k];
-                    S1[e * 4 * NQ + 2 * NQ + r] = a2;
+                for (int m = 0; m < Q; ++m) {
+                    a2 += D1[j * Q + m] * u[i * QQ + m * Q + k];
+                    a3 += D2[k * Q + m] * u[i * QQ + j * Q + m];
                 }
                 if (!merged) {
                     T a1 = T(0);
@@ -379,6 +314,7 @@ __global__ void __launch_bounds__(256) sf_kernel(const __grid_constant__ SFArgs<
                     for (int m = 0; m < Q; ++m) a1 += D0[i * Q + m] * u[m * QQ + jk];
                     S1[e * 4 * NQ + NQ + r] = a1;
                 }
+                S1[e * 4 * NQ + 2 * NQ + r] = a2;
                 S1[e * 4 * NQ + 3 * NQ + r] = a3;
             }
             __syncthreads();
@@ -532,11 +468,9 @@ __global__ void __launch_bounds__(256) sf_kernel(const __grid_constant__ SFArgs<
                 T y1 = ys[i * QQ], y2 = ys[i2 * QQ];
 #pragma unroll
                 for (int m = 0; m < Q; ++m) {
-                    if constexpr (!EO2) {     // EO2: w_2 goes through the eta1 / eta2 restrictions instead
-                        y1 += D1[m * Q + j] * w[2 * NQ + i * QQ + m * Q + k];
-                        y2 += D1[m * Q + j] * w[2 * NQ + i2 * QQ + m * Q + k];
-                    }
+                    y1 += D1[m * Q + j] * w[2 * NQ + i * QQ + m * Q + k];
                     y1 += D2[m * Q + k] * w[3 * NQ + i * QQ + j * Q + m];
+                    y2 += D1[m * Q + j] * w[2 * NQ + i2 * QQ + m * Q + k];
                     y2 += D2[m * Q + k] * w[3 * NQ + i2 * QQ + j * Q + m];
                 }
                 if (i2 != i) {
@@ -546,12 +480,6 @@ __global__ void __launch_bounds__(256) sf_kernel(const __grid_constant__ SFArgs<
                     ys[i2 * QQ] = y1 - y2;
                     w1[i * QQ] = wa + wb;
                     w1[i2 * QQ] = wa - wb;
-                    if constexpr (EO2) {
-                        T* w2 = S1 + e * 4 * NQ + 2 * NQ + jk;
-                        const T xa = w2[i * QQ], xb = w2[i2 * QQ];
-                        w2[i * QQ] = xa + xb;
-                        w2[i2 * QQ] = xa - xb;
-                    }
                 } else {
                     ys[i * QQ] = y1;
                 }
@@ -576,44 +504,6 @@ __global__ void __launch_bounds__(256) sf_kernel(const __grid_constant__ SFArgs<
 #pragma unroll
                 for (int i = 0; i < Q; ++i) acc += args.cTa[a * Q + i] * uq[i];
                 g[a * QQ] = acc;
-            }
-        }
-        __syncthreads();
-        } else if (EO2 && sumderiv) {
-        // restriction along eta1 in even-odd pairs (j, Q-1-j) of eta2 as well:
-        // gA[a] = sum_{i < Qh} Tp[a][i] y + Td[a][i] w_1 (as below) and
-        // gB[a] = sum_{i < Qh} Tp[a][i] w_2, each stored as sums at j and
-        // differences at Q-1-j for the parity-form eta2 restriction (gB in the
-        // w_3 region, consumed by the transposed pass)
-        for (int idx = tid; idx < EPB * n * Qh * Q; idx += NT) {
-            int e = idx / (n * Qh * Q), r = idx - e * (n * Qh * Q);
-            int a = r / (Qh * Q), jk = r - a * (Qh * Q), j = jk / Q, k = jk - j * Q, j2 = Q - 1 - j;
-            const bool even = (a & 1) == 0;
-            const T* ys = S2 + e * NQ + k;
-            const T* w1s = S1 + e * 4 * NQ + NQ + k;
-            const T* w2s = S1 + e * 4 * NQ + 2 * NQ + k;
-            T A1 = T(0), A2 = T(0), B1 = T(0), B2 = T(0);
-#pragma unroll
-            for (int i = 0; i < Qh; ++i) {
-                const int iy = even ? i : Q - 1 - i, iw = even ? Q - 1 - i : i;
-                const T tp = Ta[a * Q + i], td = Td[a * Q + i];
-                A1 += tp * ys[iy * QQ + j * Q];
-                A1 += td * w1s[iw * QQ + j * Q];
-                A2 += tp * ys[iy * QQ + j2 * Q];
-                A2 += td * w1s[iw * QQ + j2 * Q];
-                B1 += tp * w2s[iy * QQ + j * Q];
-                B2 += tp * w2s[iy * QQ + j2 * Q];
-            }
-            T* gA = S1 + e * 4 * NQ + a * QQ + k;
-            T* gB = S1 + e * 4 * NQ + 3 * NQ + a * QQ + k;
-            if (j2 != j) {
-                gA[j * Q] = A1 + A2;
-                gA[j2 * Q] = A1 - A2;
-                gB[j * Q] = B1 + B2;
-                gB[j2 * Q] = B1 - B2;
-            } else {
-                gA[j * Q] = A1;
-                gB[j * Q] = B1;
             }
         }
         __syncthreads();
@@ -651,32 +541,6 @@ __global__ void __launch_bounds__(256) sf_kernel(const __grid_constant__ SFArgs<
         }
         __syncthreads();
         }
-        if constexpr (EO2) {
-        // eta2 restriction with the parity table: every (a, b) pair is valid,
-        // p = a n + b.  Derivative operators: f'[p][k] = sum_{j < Qh} Tp[b][j] gA^{+-}
-        // + Td[b][j] gB^{-+} (replaces D_2^T w_2); others: sum_j Tp[b][j] g'[a][j][k]
-        for (int idx = tid; idx < EPB * NPR * Q; idx += NT) {
-            int e = idx / (NPR * Q), r = idx - e * (NPR * Q);
-            int p = r / Q, k = r - p * Q, a = p / n, b = p - a * n;
-            const T* gA = S1 + e * 4 * NQ + a * QQ + k;
-            T acc = T(0);
-            if (sumderiv) {
-                const bool even = (b & 1) == 0;
-                const T* gB = S1 + e * 4 * NQ + 3 * NQ + a * QQ + k;
-#pragma unroll
-                for (int j = 0; j < Qh; ++j) {
-                    const int ja = even ? j : Q - 1 - j, jb = even ? Q - 1 - j : j;
-                    acc += Ta[b * Q + j] * gA[ja * Q];
-                    acc += Td[b * Q + j] * gB[jb * Q];
-                }
-            } else {
-#pragma unroll
-                for (int j = 0; j < Q; ++j) acc += Ta[b * Q + j] * gA[j * Q];
-            }
-            S2[e * NQ + r] = acc;
-        }
-        __syncthreads();
-        } else {
         // eta2 pass over the valid pairs p = (a,b): f'[p][k] = sum_j Tb[t(a)][b][j] g'[a][j][k]
         for (int idx = tid; idx < EPB * NPR * Q; idx += NT) {
             int e = idx / (NPR * Q), r = idx - e * (NPR * Q);
@@ -692,7 +556,6 @@ __global__ void __launch_bounds__(256) sf_kernel(const __grid_constant__ SFArgs<
             S2[e * NQ + r] = acc;
         }
         __syncthreads();
-        }
         // eta3 pass over the valid slots (a,b,c): r[a][b][c] = sum_k Tc[s(a,b)][c][k] f'[p(a,b)][k]
         for (int idx = tid; idx < EPB * NVL; idx += NT) {
             int e = idx / NVL, v = idx - e * NVL;
@@ -721,26 +584,9 @@ __global__ void __launch_bounds__(256) sf_kernel(const __grid_constant__ SFArgs<
                 if (sl < 0) continue;
                 // slots a = 0, 1 hold the restrictions against 1/2 and -z/2:
                 // L = 1/2 - z/2 takes their sum, R = 1/2 + z/2 their difference
-                // (and likewise over b = 0, 1 where eta2 is in parity form)
-                if constexpr (EO2) {
-                    const int a = sl / NN, b = (sl / n) % n;
-                    const int na = a <= 1 ? 2 : 1, nb = b <= 1 ? 2 : 1;
-                    const int base = sl - (a <= 1 ? a * NN : 0) - (b <= 1 ? b * n : 0);
-#pragma unroll
-                    for (int ia = 0; ia < 2; ++ia) {
-                        if (ia >= na) break;
-#pragma unroll
-                        for (int ib = 0; ib < 2; ++ib) {
-                            if (ib >= nb) break;
-                            const T x = rs[base + (a <= 1 ? ia * NN : 0) + (b <= 1 ? ib * n : 0)];
-                            acc += ((a == 1 && ia == 1) != (b == 1 && ib == 1)) ? -x : x;
-                        }
-                    }
-                } else {
-                    if (sl >= 2 * NN) acc += rs[sl];
-                    else if (sl < NN) acc += rs[sl] + rs[sl + NN];
-                    else acc += rs[sl - NN] - rs[sl];
-                }
+                if (sl >= 2 * NN) acc += rs[sl];
+                else if (sl < NN) acc += rs[sl] + rs[sl + NN];
+                else acc += rs[sl - NN] - rs[sl];
             }
             args.out[args.coeff_off[e0 + e] + m] = acc;
         }
