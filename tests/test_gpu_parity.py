@@ -212,3 +212,28 @@ def test_fp64_on_conforming_mesh_orientations(hp, P, curved):
         ref = oracle_ops.apply(opname, mesh, x, 1.0)
         y = run_op(hp, mesh, opname, x, 1.0)
         assert rel_err(y, ref) <= FP64_TOL, (opname, rel_err(y, ref))
+
+
+@pytest.mark.parametrize("opname", ["mass", "helmholtz"])
+def test_unit_cube_of_64_affine_hexes(hp, opname):
+    """64 affine hexahedra (4x4x4 structured [0,1]^3), P = 4, Q = 6, lambda = 1,
+    coefficients U[-1,1) from seed 1001: FP64 against the oracle at 1e-12, and
+    the TF32 tensor-core form at 8 units of TF32 rounding."""
+    mesh = inputs.hex_cube_mesh(4, 4)
+    co, _ = oracle_ops.layout(mesh)
+    x = inputs.random_coefficients(1001, co)
+    ref = oracle_ops.apply(opname, mesh, x, 1.0)
+    y = run_op(hp, mesh, opname, x, 1.0)
+    assert rel_err(y, ref) <= FP64_TOL
+    h = hp.hp_mesh_create(mesh, 0)
+    try:
+        op = hp.hp_op_create(h, OPS[opname], hp.HP_STRAT_ELEMAT, hp.HP_TF32)
+        xt = torch.tensor(x, device="cuda:0", dtype=torch.float32)
+        y32 = torch.full((len(x),), float("nan"), device="cuda:0", dtype=torch.float32)
+        hp.hp_op_apply(op, 1.0, xt, y32)
+        hp.hp_op_sync(op)
+        hp.hp_op_destroy(op)
+    finally:
+        hp.hp_mesh_destroy(h)
+    ref32 = oracle_ops.apply(opname, mesh, x.astype(np.float32).astype(np.float64), 1.0)
+    assert rel_err(y32.double().cpu().numpy(), ref32) <= 8 * 2.0 ** -11

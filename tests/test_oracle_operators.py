@@ -253,3 +253,17 @@ def test_mesh_apply_matches_block_apply_and_subset():
         np.testing.assert_allclose(part[coeff[e]:coeff[e + 1]], full[coeff[e]:coeff[e + 1]], rtol=0, atol=1e-14)
     lin = 2.0 * ops.apply("mass", mesh, uh) + ops.apply("laplacian", mesh, uh)
     assert np.abs(full - lin).max() <= 1e-13 * np.abs(full).max()
+
+
+def test_unit_cube_of_64_hexes_volume():
+    """The 4x4x4 affine hex mesh of [0,1]^3 at P = 4 (Q = 6): the constant 1 on
+    every element (vertex modes = 1) gives uhat_e . (M uhat)_e = 1/64 per
+    hexahedron and 1 over the cube."""
+    mesh = inputs.hex_cube_mesh(4, 4)
+    co, _ = ops.layout(mesh)
+    uh1 = vertex_coeffs(0, 4, np.ones(8))
+    uh = np.tile(uh1, mesh["n_elem"])
+    Mu = ops.apply("mass", mesh, uh, 1.0)
+    per = np.array([uh[co[e]:co[e + 1]] @ Mu[co[e]:co[e + 1]] for e in range(mesh["n_elem"])])
+    assert mesh["n_elem"] == 64 and np.allclose(per, 1.0 / 64, rtol=1e-13, atol=0)
+    assert per.sum() == pytest.approx(1.0, rel=1e-13)
