@@ -18,9 +18,10 @@
 // shared memory for the work item; the reference tiles F_c, R_c are laid out
 // on the host in the tensor core's shared-memory order and streamed by 1-D
 // bulk copies (TMA) through a ring of stages (the forward operand in K slices
-// of 32 modes, the backward tiles one component at a time).  The forward accumulators and
-// the V' tiles are double-buffered, so the metric of chunk k overlaps the
-// forward MMAs of chunk k+1 and the backward MMAs of chunk k-1.
+// of 32 modes, the backward tiles one component at a time).  Three forward
+// accumulators are in flight and the V' tiles are double-buffered, so the
+// forward MMAs run two chunks ahead of the metric and the metric of chunk k
+// overlaps the backward MMAs of chunk k-1.
 // Roles: warps 0-7 gather U, run the metric and write the outputs (warp w
 // reads TMEM lanes 32 (w mod 4).. and half w / 4 of each chunk's points);
 // warp 8 issues the bulk copies; warp 9 issues the MMAs.  Every wait is
@@ -35,7 +36,8 @@ constexpr int kNPT = 16;          // quadrature points per chunk
 constexpr int kHalf = kNPT / 2;   // points per epilogue thread
 constexpr int kMaxStages = 8;     // bulk-copy ring: as many stages (2..8) as fit in shared memory
 constexpr int kTmemCols = 512;
-constexpr int kOutCol = 128;      // TMEM column of the output accumulator (forward: 2 buffers x 4 x 16)
+constexpr int kFwdBufs = 3;       // forward accumulators in flight: the forward MMAs run two chunks ahead
+constexpr int kOutCol = kFwdBufs * 4 * 16;   // TMEM column of the output accumulator
 constexpr int kEpi = 256;         // epilogue threads
 constexpr int kThreads = kEpi + 64;
 constexpr int kVBytes = 128 * kNPT * 4;   // one V' tile [128 x 16] TF32
@@ -43,7 +45,7 @@ constexpr int kSliceBytes = 4 * kNPT * 32 * 4;   // forward operand: 64 rows x 3
 
 struct Bars {
     uint64_t full[kMaxStages], empty[kMaxStages];
-    uint64_t u_full, fwd_full[2], fwd_empty[2], vp_full[2], vp_empty[2], out_full, out_empty, drain;
+    uint64_t u_full, fwd_full[kFwdBufs], fwd_empty[kFwdBufs], vp_full[2], vp_empty[2], out_full, out_empty, drain;
     uint32_t tmem;
     int abort;
 };
@@ -94,9 +96,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_emat_kernel(const __grid_const
     if (tid == 0) {
         for (int s = 0; s < nst; ++s) { mbar_init(&B->full[s], 1); mbar_init(&B->empty[s], 1); }
         mbar_init(&B->u_full, kEpi);
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < kFwdBufs; ++b) {
             mbar_init(&B->fwd_full[b], 1);
             mbar_init(&B->fwd_empty[b], kEpi);
+        }
+        for (int b = 0; b < 2; ++b) {
             mbar_init(&B->vp_full[b], kEpi);
             mbar_init(&B->vp_empty[b], 1);
         }
@@ -131,13 +135,15 @@ __global__ void __launch_bounds__(kThreads, 1) tc_emat_kernel(const __grid_const
             for (int64_t w = blockIdx.x; w < nwork && ok; w += gridDim.x) {
                 int kb, ke;
                 chunk_range(w, kb, ke);
-                for (int k = kb; k <= ke && ok; ++k) {
-                    if (k < ke) {
-                        const unsigned char* base = a.img + (size_t)k * a.chunk_bytes;
+                // the MMA issuer's order: forward of chunk t, backward of chunk t - (kFwdBufs - 1)
+                for (int t = kb; t < ke + kFwdBufs - 1 && ok; ++t) {
+                    if (t < ke) {
+                        const unsigned char* base = a.img + (size_t)t * a.chunk_bytes;
                         for (int sl = 0; sl * 32 < a.KP && ok; ++sl) put(base + (size_t)sl * kSliceBytes, kSliceBytes);
                     }
-                    if (k > kb) {
-                        const unsigned char* base = a.img + (size_t)(k - 1) * a.chunk_bytes + (size_t)a.fwd_bytes;
+                    const int kbw = t - (kFwdBufs - 1);
+                    if (kbw >= kb) {
+                        const unsigned char* base = a.img + (size_t)kbw * a.chunk_bytes + (size_t)a.fwd_bytes;
                         for (int c = a.c0; c < a.c1 && ok; ++c) put(base + (size_t)c * a.bwd_bytes, a.bwd_bytes);
                     }
                 }
@@ -162,9 +168,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_emat_kernel(const __grid_const
                 int kb, ke;
                 chunk_range(w, kb, ke);
                 if (!wait_bar(&B->u_full, ntile & 1u, B, a.err)) { ok = false; break; }
-                for (int k = kb; k <= ke && ok; ++k) {
-                    if (k < ke) {
-                        const uint32_t g = g0 + (uint32_t)(k - kb), b = g & 1u, use = g >> 1;
+                for (int t = kb; t < ke + kFwdBufs - 1 && ok; ++t) {
+                    if (t < ke) {
+                        const int k = t;
+                        const uint32_t g = g0 + (uint32_t)(k - kb), b = g % kFwdBufs, use = g / kFwdBufs;
                         if (!wait_bar(&B->fwd_empty[b], (use & 1u) ^ 1u, B, a.err)) { ok = false; break; }
                         tc::fence_after();
                         // columns (b*4 + c0)*16 .. of the accumulator = components c0..c1-1
@@ -183,10 +190,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_emat_kernel(const __grid_const
                         }
                         tc::commit(&B->fwd_full[b]);
                     }
-                    if (k > kb && ok) {
-                        const uint32_t g = g0 + (uint32_t)(k - 1 - kb), b = g & 1u, use = g >> 1;
+                    const int k = t - (kFwdBufs - 1);          // backward of chunk k
+                    if (k >= kb && ok) {
+                        const uint32_t g = g0 + (uint32_t)(k - kb), b = g & 1u, use = g >> 1;
                         if (!wait_bar(&B->vp_full[b], use & 1u, B, a.err)) { ok = false; break; }
-                        if (k == kb + 1) {
+                        if (k == kb) {
                             if (!wait_bar(&B->out_empty, (nout & 1u) ^ 1u, B, a.err)) { ok = false; break; }
                             ++nout;
                         }
@@ -199,7 +207,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_emat_kernel(const __grid_const
                             for (int s = 0; s < kNPT / 8; ++s)
                                 tc::mma_tf32(tbase + kOutCol, tc::smem_desc_sw(sa + s * 32, 512, tc::kSw64),
                                              tc::smem_desc_sw(sb + s * 32, 512, tc::kSw64), id_b,
-                                             !(k == kb + 1 && c == a.c0 && s == 0));
+                                             !(k == kb && c == a.c0 && s == 0));
                             tc::commit(&B->empty[slot]);
                             if (++slot == nst) { slot = 0; pass ^= 1u; }
                         }
@@ -269,6 +277,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_emat_kernel(const __grid_const
             if (!AFFINE && kb < ke) load_geom(kb);
             for (int k = kb; k < ke && ok; ++k) {
                 const uint32_t g = g0 + (uint32_t)(k - kb), b = g & 1u, use = g >> 1;
+                const uint32_t bf = g % kFwdBufs, usef = g / kFwdBufs;     // forward accumulator buffer
                 if (!AFFINE) {
 #pragma unroll
                     for (int f = 0; f < 7; ++f)
@@ -276,19 +285,19 @@ __global__ void __launch_bounds__(kThreads, 1) tc_emat_kernel(const __grid_const
                         for (int p = 0; p < kHalf; ++p) Gc[f][p] = Gn[f][p];
                     if (k + 1 < ke) load_geom(k + 1);
                 }
-                if (!wait_warp(&B->fwd_full[b], use & 1u, B, a.err)) { ok = false; break; }
+                if (!wait_warp(&B->fwd_full[bf], usef & 1u, B, a.err)) { ok = false; break; }
                 tc::fence_after();
                 float v[4][kHalf];
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
-                    if (c >= a.c0 && c < a.c1) tc::ld_32x8(tbase + lane_base + (uint32_t)((b * 4 + c) * kNPT + h * kHalf), v[c]);
+                    if (c >= a.c0 && c < a.c1) tc::ld_32x8(tbase + lane_base + (uint32_t)((bf * 4 + c) * kNPT + h * kHalf), v[c]);
                     else {
 #pragma unroll
                         for (int p = 0; p < kHalf; ++p) v[c][p] = 0.f;
                     }
                 }
                 tc::fence_before();
-                arrive(&B->fwd_empty[b]);
+                arrive(&B->fwd_empty[bf]);
                 float o[4][kHalf];
 #pragma unroll
                 for (int p = 0; p < kHalf; ++p) {
