@@ -309,7 +309,8 @@ def precision_forms(work64, device, reps=10):
         y32 = torch.zeros(w["nc"], device=dev, dtype=torch.float32)
         row = {}
         for name, strat, dt in (("fp32_sumfac", hp.HP_STRAT_SUMFAC, hp.HP_FP32),
-                                ("tf32_tensor_core", hp.HP_STRAT_ELEMAT, hp.HP_TF32)):
+                                ("tf32_tensor_core", hp.HP_STRAT_ELEMAT, hp.HP_TF32),
+                                ("bf16_tensor_core", hp.HP_STRAT_ELEMAT, hp.HP_BF16)):
             op = hp.hp_op_create(w["h"], hp.HP_HELMHOLTZ, strat, dt)
             for _ in range(3):
                 hp.hp_op_apply(op, 1.0, x32, y32)
@@ -426,7 +427,8 @@ def padaptive(device, reps=10):
     forms = {}
     for name, strat, dt, sched in (("fp32_sumfac", hp.HP_STRAT_SUMFAC, hp.HP_FP32, False),
                                    ("tf32_tensor_core", hp.HP_STRAT_ELEMAT, hp.HP_TF32, False),
-                                   ("tf32_scheduled", hp.HP_STRAT_ELEMAT, hp.HP_TF32, True)):
+                                   ("tf32_scheduled", hp.HP_STRAT_ELEMAT, hp.HP_TF32, True),
+                                   ("bf16_tensor_core", hp.HP_STRAT_ELEMAT, hp.HP_BF16, False)):
         op = hp.hp_op_create(h, hp.HP_HELMHOLTZ, strat, dt)
         if sched:
             hp.hp_op_schedule_exhaustive(op, 1.0, x32, y32, nblocks, stream)
@@ -435,7 +437,7 @@ def padaptive(device, reps=10):
         err = float((y32.double() - y64).abs().max() / y64.abs().max())
         forms[name] = {"ms": round(ms, 4), "gdofs": round(dofs / (ms * 1e-3) / 1e9, 4),
                        "rel_err_vs_fp64": float("%.3g" % err),
-                       "blocks_on_tensor_core": int((st == hp.HP_STRAT_ELEMAT).sum()) if dt == hp.HP_TF32 else 0}
+                       "blocks_on_tensor_core": int((st == hp.HP_STRAT_ELEMAT).sum()) if dt in (hp.HP_TF32, hp.HP_BF16) else 0}
         hp.hp_op_destroy(op)
     hp.hp_mesh_destroy(h)
     g = lambda ms: round(dofs / (ms * 1e-3) / 1e9, 4)
@@ -578,12 +580,14 @@ def run_solve(local, cells, order=4, lam=1.0, tol=1e-10):
            "setup_s": {"mesh": round(t_mesh, 2), "c0_map": round(t_c0, 2)}}
     # warm-up (builds the Jacobi diagonal, operators and workspaces) then timed solves
     xw = torch.zeros(ng, device=dev, dtype=torch.float64)
+    hp.hp_solve(c0, lam, b, xw, tol=1e-2, mixed=3, inner_tol=1e-1, max_refinements=1)
     hp.hp_solve(c0, lam, b, xw, tol=1e-2, mixed=2, inner_tol=1e-1, max_refinements=1)
     hp.hp_solve(c0, lam, b, xw, tol=1e-2, mixed=True, inner_tol=1e-1, max_refinements=1)
     hp.hp_solve(c0, lam, b, xw, tol=1e-2)
     sols = {}
     for name, kw in (("fp64_pcg", dict(mixed=False)), ("mixed_fp32_pcg_fp64_ir", dict(mixed=True, inner_tol=1e-4)),
-                     ("mixed_tf32_tensor_core_pcg_fp64_ir", dict(mixed=2, inner_tol=1e-3))):
+                     ("mixed_tf32_tensor_core_pcg_fp64_ir", dict(mixed=2, inner_tol=1e-3)),
+                     ("mixed_bf16_tensor_core_pcg_fp64_ir", dict(mixed=3, inner_tol=1e-2))):
         xs = torch.zeros(ng, device=dev, dtype=torch.float64)
         torch.cuda.synchronize(dev)
         t0 = time.time()
@@ -594,7 +598,8 @@ def run_solve(local, cells, order=4, lam=1.0, tol=1e-10):
         if rc:
             out[name]["error"] = hp.hp_last_error()
         sols[name] = xs
-    for name, tag in (("mixed_fp32_pcg_fp64_ir", "mixed"), ("mixed_tf32_tensor_core_pcg_fp64_ir", "tf32_tc")):
+    for name, tag in (("mixed_fp32_pcg_fp64_ir", "mixed"), ("mixed_tf32_tensor_core_pcg_fp64_ir", "tf32_tc"),
+                      ("mixed_bf16_tensor_core_pcg_fp64_ir", "bf16_tc")):
         d = sols["fp64_pcg"] - sols[name]
         out["rel_diff_%s_vs_fp64" % tag] = float(d.norm() / sols["fp64_pcg"].norm())
         out["speedup_%s_vs_fp64" % tag] = round(out["fp64_pcg"]["seconds"] / out[name]["seconds"], 3)

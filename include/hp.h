@@ -87,11 +87,12 @@ typedef enum {
 } hp_strategy;
 
 /* Compute type.  HP_FP64: IEEE double throughout (the oracle-parity form).
- * HP_FP32: single precision (CUDA cores), float arrays.  HP_TF32: the
- * elemental-matrix strategy on the tensor cores (tcgen05, Blackwell):
+ * HP_FP32: single precision (CUDA cores), float arrays.  HP_TF32 / HP_BF16:
+ * the elemental-matrix strategy on the tensor cores (tcgen05, Blackwell):
  * coefficients, reference matrices and metric-weighted point values rounded
- * to TF32 (10-bit mantissa), products accumulated in FP32 in tensor memory;
- * float arrays; relative error a few units of 2^-11.  HP_BF16: not built. */
+ * to TF32 (10-bit mantissa) or BF16 (7-bit mantissa), products accumulated in
+ * FP32 in tensor memory; float arrays; relative error a few units of 2^-11
+ * (TF32) or 2^-8 (BF16). */
 typedef enum { HP_FP64 = 0, HP_FP32 = 1, HP_TF32 = 2, HP_BF16 = 3 } hp_dtype;
 
 /* Mesh description (all host arrays, copied by hp_mesh_create).
@@ -153,7 +154,7 @@ hp_status hp_geom_copy(hp_mesh mesh, double* out7, double* out9);
 /* Create an operator of kind `kind` over all blocks of `mesh`, computing in
  * `dtype` with `strategy`.  HP_FP64 and HP_FP32 apply to every kind with
  * HP_STRAT_SUMFAC; arrays passed to hp_op_apply are double (HP_FP64) or
- * float (HP_FP32, HP_TF32).  HP_TF32 takes HP_STRAT_ELEMAT (or AUTO) and the
+ * float (HP_FP32, HP_TF32, HP_BF16).  HP_TF32 and HP_BF16 take HP_STRAT_ELEMAT (or AUTO) and the
  * kinds HP_MASS, HP_LAPLACIAN, HP_HELMHOLTZ: blocks with at most 256 modes per
  * element run the tensor-core elemental-matrix kernel, larger ones FP32 sum
  * factorisation (hp_op_strategies reports which).  Errors: HP_ERR_ARG,
@@ -301,8 +302,8 @@ typedef struct {
     double tol;            /* stop at ||b - A x|| <= tol ||b|| (FP64 residual)                 */
     int max_iter;          /* FP64 CG: iteration limit                                          */
     int mixed;             /* 0: Jacobi-PCG in FP64; 1: FP64 refinement of FP32 Jacobi-PCG      *
-                            * (sum-factorised FP32 operator); 2: the same with the TF32         *
-                            * tensor-core operator inside (HP_TF32, elemental matrices)          */
+                            * (sum-factorised FP32 operator); 2 / 3: the same with the TF32 /   *
+                            * BF16 tensor-core operator inside (HP_TF32 / HP_BF16)               */
     double inner_tol;      /* mixed: relative tolerance of each FP32 solve                      */
     int inner_max_iter;    /* mixed: iteration limit of each FP32 solve                         */
     int max_refinements;   /* mixed: refinement steps                                           */

@@ -202,25 +202,44 @@ float round_tf32(float x) {
     return r;
 }
 
-// Reference tiles of the tensor-core elemental-matrix operator, per chunk of
-// tc_chunk_points() quadrature points: the forward operand (64 rows = 4
-// components x 16 points, K = modes) in K-slices of 32 modes (zero padded),
-// 128-byte swizzled, then the backward tiles R_c[mode][point] (rows padded to
-// NPpad, 16 points = 64-byte swizzled rows) of the 4 components; the K-major
+// round to bfloat16 (8 significant bits, nearest, ties to even); finite inputs
+uint16_t round_bf16(float x) {
+    uint32_t u;
+    std::memcpy(&u, &x, 4);
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+
+// Reference tiles of the tensor-core elemental-matrix operator for operands of
+// es bytes (4: TF32, 2: BF16), per chunk of tc_chunk_points() quadrature
+// points: the forward operand (64 rows = 4 components x 16 points, K = modes)
+// in K-slices of 128 bytes of modes (zero padded), 128-byte swizzled, then the
+// backward tiles R_c[mode][point] (rows padded to NPpad; 16 points = 64-byte
+// (TF32) or 32-byte (BF16) swizzled rows) of the 4 components: the K-major
 // swizzled order the tensor core reads from shared memory.
-hp_status ensure_tc(hp_mesh m) {
+hp_status ensure_tc(hp_mesh m, int es) {
     for (auto& kv : m->blobs) {
         DeviceBlobs& db = kv.second;
-        if (db.tc_img) continue;
         const int shape = kv.first / 16, P = kv.first % 16;
         const int Q = P + 2, NQ = Q * Q * Q, NP = n_modes(shape, P), NPT = tc_chunk_points();
         if (NP > kTcMaxModes) continue;
-        const int KP = (NP + 31) & ~31, NPpad = (NP + 15) & ~15, nch = (NQ + NPT - 1) / NPT;
-        const int slice = 4 * NPT * 32 * 4;                    // 64 rows x 128 bytes
-        const int fwd = (KP / 32) * slice, bwd = NPpad * NPT * 4;
+        const int KR = 128 / es, vrow = NPT * es;
+        const int KP = (NP + KR - 1) / KR * KR, NPpad = (NP + 15) & ~15, nch = (NQ + NPT - 1) / NPT;
+        const int slice = 4 * NPT * 128;                       // 64 rows x 128 bytes
+        const int fwd = (KP / KR) * slice, bwd = NPpad * vrow;
         const int64_t chunk = fwd + 4 * (int64_t)bwd;
+        if ((es == 4 && db.tc_img) || (es == 2 && db.tc_img16)) continue;
         std::vector<double> A = dense_matrices(shape, P);
         std::vector<unsigned char> img((size_t)(chunk * nch), 0);
+        auto put = [&](unsigned char* dst, double x) {
+            if (es == 4) {
+                const float v = round_tf32((float)x);
+                std::memcpy(dst, &v, 4);
+            } else {
+                const uint16_t v = round_bf16((float)x);
+                std::memcpy(dst, &v, 2);
+            }
+        };
         for (int k = 0; k < nch; ++k) {
             unsigned char* F = img.data() + (size_t)k * chunk;
             for (int c = 0; c < 4; ++c) {
@@ -229,13 +248,25 @@ hp_status ensure_tc(hp_mesh m) {
                     const int l = k * NPT + r;
                     if (l >= NQ) continue;
                     for (int mm = 0; mm < NP; ++mm) {
-                        const float v = round_tf32((float)A[((size_t)c * NQ + l) * NP + mm]);
-                        std::memcpy(F + (size_t)(mm / 32) * slice + tc::sw128_offset(c * NPT + r, mm % 32), &v, 4);
-                        std::memcpy(R + tc::sw64_offset(mm, r), &v, 4);
+                        const double x = A[((size_t)c * NQ + l) * NP + mm];
+                        const int row = c * NPT + r, kk = mm % KR;
+                        put(F + (size_t)(mm / KR) * slice + row * 128 + ((((kk * es) >> 4) ^ (row & 7)) << 4) + ((kk * es) & 15), x);
+                        const uint32_t rv = es == 4 ? tc::sw64_offset(mm, r)
+                                                    : mm * 32 + ((((r * 2) >> 4) ^ ((mm >> 2) & 1)) << 4) + ((r * 2) & 15);
+                        put(R + rv, x);
                     }
                 }
             }
         }
+        hp_status st0 = upload(es == 4 ? &db.tc_img : &db.tc_img16, img.data(), img.size());
+        if (st0) return st0;
+        if (es == 4) {
+            db.tc_KP = KP; db.tc_fwd = fwd; db.tc_bwd = bwd; db.tc_chunk = chunk;
+        } else {
+            db.tc_KP16 = KP; db.tc_fwd16 = fwd; db.tc_bwd16 = bwd; db.tc_chunk16 = chunk;
+        }
+        db.tc_NPpad = NPpad; db.tc_nch = nch;
+        if (db.tc_pts) continue;
         // d eta / d xi and the quadrature weight at every point (affine elements)
         const RefTables& t = ref_tables(shape, P);
         std::vector<float> pts((size_t)NQ * 10);
@@ -251,10 +282,8 @@ hp_status ensure_tc(hp_mesh m) {
             for (int d = 0; d < 9; ++d) pts[(size_t)l * 10 + d] = (float)T[d / 3][d % 3];
             pts[(size_t)l * 10 + 9] = (float)(t.w[0][i] * t.w[1][j] * t.w[2][k]);
         }
-        hp_status st = upload(&db.tc_img, img.data(), img.size());
-        if (!st) st = upload(&db.tc_pts, pts.data(), pts.size());
+        hp_status st = upload(&db.tc_pts, pts.data(), pts.size());
         if (st) return st;
-        db.tc_KP = KP; db.tc_NPpad = NPpad; db.tc_nch = nch; db.tc_fwd = fwd; db.tc_bwd = bwd; db.tc_chunk = chunk;
     }
     // curved blocks: FP32 metric factors in the tile-major order the epilogue reads
     for (Block& b : m->blocks) {
@@ -278,7 +307,7 @@ bool tc_fits(const Block& b) { return n_modes(b.shape, b.P) <= kTcMaxModes; }
 bool strategy_available(const hp_op_s* op, size_t i, int k) {
     if (k == HP_STRAT_SUMFAC) return true;
     if (needs_deriv_geom(op->kind)) return false;
-    if (op->dtype == HP_TF32) return k == HP_STRAT_ELEMAT && tc_fits(op->mesh->blocks[i]);
+    if (op->dtype == HP_TF32 || op->dtype == HP_BF16) return k == HP_STRAT_ELEMAT && tc_fits(op->mesh->blocks[i]);
     return true;
 }
 
@@ -365,18 +394,23 @@ cudaError_t launch_block(hp_op op, size_t bi, int tile, double lambda, const voi
     const Block& b = m->blocks[bi];
     const DeviceBlobs& blob = m->blobs.at(b.shape * 16 + b.P);
     const int64_t nphys = m->phys_off.back();
-    if (op->dtype == HP_TF32 && op->strat[bi] == HP_STRAT_ELEMAT) {
+    if ((op->dtype == HP_TF32 || op->dtype == HP_BF16) && op->strat[bi] == HP_STRAT_ELEMAT) {
+        const bool bf = op->dtype == HP_BF16;
         TCArgs a{};
         a.op = op->kind; a.Q = b.Q; a.NQ = b.Q * b.Q * b.Q; a.NQp = nqp(b.Q); a.NP = n_modes(b.shape, b.P);
-        a.KP = blob.tc_KP; a.NPpad = blob.tc_NPpad; a.nch = blob.tc_nch;
+        a.KP = bf ? blob.tc_KP16 : blob.tc_KP; a.NPpad = blob.tc_NPpad; a.nch = blob.tc_nch;
+        a.es = bf ? 2 : 4;
         a.c0 = op->kind == HP_LAPLACIAN ? 1 : 0;
         a.c1 = op->kind == HP_MASS ? 1 : 4;
         a.n_elem = b.n_elem; a.lambda = (float)lambda; a.coeff_off = b.d_coeff_off;
         a.in = static_cast<const float*>(in); a.out = static_cast<float*>(out);
         a.geom = b.curved ? b.d_geom_tc : b.d_geom32;
         a.tpts = blob.tc_pts;
-        a.img = blob.tc_img; a.chunk_bytes = blob.tc_chunk; a.fwd_bytes = blob.tc_fwd; a.bwd_bytes = blob.tc_bwd;
-        a.stage_bytes = (std::max(4 * tc_chunk_points() * 32 * 4, blob.tc_bwd) + 1023) & ~1023;
+        a.img = bf ? blob.tc_img16 : blob.tc_img;
+        a.chunk_bytes = bf ? blob.tc_chunk16 : blob.tc_chunk;
+        a.fwd_bytes = bf ? blob.tc_fwd16 : blob.tc_fwd;
+        a.bwd_bytes = bf ? blob.tc_bwd16 : blob.tc_bwd;
+        a.stage_bytes = (std::max(4 * tc_chunk_points() * 128, a.bwd_bytes) + 1023) & ~1023;
         a.err = op->d_err;
         return tc_emat_launch(!b.curved, a, s);
     }
@@ -685,14 +719,11 @@ hp_status hp_op_create(hp_mesh m, hp_opkind kind, hp_strategy strategy, hp_dtype
     if ((int)kind < 0 || kind > HP_IPRODUCT_WRT_DERIV_BASE) { set_error("hp_op_create: bad kind"); return HP_ERR_ARG; }
     if ((int)strategy < 0 || strategy > HP_STRAT_AUTO) { set_error("hp_op_create: bad strategy"); return HP_ERR_ARG; }
     if ((int)dtype < 0 || dtype > HP_BF16) { set_error("hp_op_create: bad dtype"); return HP_ERR_ARG; }
-    if (strategy == HP_STRAT_AUTO) strategy = dtype == HP_TF32 ? HP_STRAT_ELEMAT : HP_STRAT_SUMFAC;
-    if (dtype == HP_BF16) {
-        set_error("hp_op_create: this strategy/dtype combination is not built");
-        return HP_ERR_UNSUPPORTED;
-    }
-    if (dtype == HP_TF32 && (strategy != HP_STRAT_ELEMAT ||
+    const bool tcore = dtype == HP_TF32 || dtype == HP_BF16;
+    if (strategy == HP_STRAT_AUTO) strategy = tcore ? HP_STRAT_ELEMAT : HP_STRAT_SUMFAC;
+    if (tcore && (strategy != HP_STRAT_ELEMAT ||
                              (kind != HP_MASS && kind != HP_LAPLACIAN && kind != HP_HELMHOLTZ))) {
-        set_error("hp_op_create: HP_TF32 is the tensor-core elemental-matrix form of mass, Laplacian and Helmholtz");
+        set_error("hp_op_create: HP_TF32 / HP_BF16 are the tensor-core elemental-matrix form of mass, Laplacian and Helmholtz");
         return HP_ERR_UNSUPPORTED;
     }
     if (strategy != HP_STRAT_SUMFAC && (kind == HP_PHYSDERIV || kind == HP_IPRODUCT_WRT_DERIV_BASE)) {
@@ -702,8 +733,8 @@ hp_status hp_op_create(hp_mesh m, hp_opkind kind, hp_strategy strategy, hp_dtype
     DeviceGuard guard(m->device);
     hp_status st = ensure_geom(m, needs_deriv_geom(kind), dtype != HP_FP64, 0);
     if (st) return st;
-    if (dtype == HP_TF32) {
-        if ((st = ensure_tc(m))) return st;
+    if (tcore) {
+        if ((st = ensure_tc(m, dtype == HP_BF16 ? 2 : 4))) return st;
     } else if (strategy != HP_STRAT_SUMFAC && (st = ensure_dense(m))) {
         return st;
     }
@@ -714,7 +745,7 @@ hp_status hp_op_create(hp_mesh m, hp_opkind kind, hp_strategy strategy, hp_dtype
     op->dtype = dtype;
     op->tile.assign(m->blocks.size(), 0);
     op->strat.assign(m->blocks.size(), (int)strategy);
-    if (dtype == HP_TF32)   // blocks beyond the tensor-memory budget run FP32 sum factorisation
+    if (tcore)   // blocks beyond the tensor-memory budget run FP32 sum factorisation
         for (size_t i = 0; i < m->blocks.size(); ++i)
             if (!tc_fits(m->blocks[i])) op->strat[i] = HP_STRAT_SUMFAC;
     st = upload<unsigned int>(&op->d_err, nullptr, 1);
@@ -870,12 +901,12 @@ hp_status hp_op_strategies(hp_op op, int* strat, int64_t n_blocks, int set) {
             set_error("hp_op_strategies: derivative building blocks exist only with HP_STRAT_SUMFAC");
             return HP_ERR_UNSUPPORTED;
         }
-        if (op->dtype == HP_TF32 && strat[i] != HP_STRAT_SUMFAC &&
+        if ((op->dtype == HP_TF32 || op->dtype == HP_BF16) && strat[i] != HP_STRAT_SUMFAC &&
             (strat[i] != HP_STRAT_ELEMAT || !tc_fits(op->mesh->blocks[i]))) {
-            set_error("hp_op_strategies: HP_TF32 blocks are tensor-core elemental-matrix (N_P <= 256) or FP32 sum factorisation");
+            set_error("hp_op_strategies: HP_TF32 / HP_BF16 blocks are tensor-core elemental-matrix (N_P <= 256) or FP32 sum factorisation");
             return HP_ERR_UNSUPPORTED;
         }
-        dense |= strat[i] != HP_STRAT_SUMFAC && op->dtype != HP_TF32;
+        dense |= strat[i] != HP_STRAT_SUMFAC && op->dtype != HP_TF32 && op->dtype != HP_BF16;
     }
     if (dense) {
         hp_status st = ensure_dense(op->mesh);
@@ -937,7 +968,7 @@ hp_status hp_op_schedule_exhaustive(hp_op op, double lambda, const void* in, voi
     if (in == out) { set_error("hp_op_schedule_exhaustive: in and out must not alias"); return HP_ERR_ARG; }
     DeviceGuard guard(op->mesh->device);
     const int64_t nb = (int64_t)op->strat.size();
-    if (!needs_deriv_geom(op->kind) && op->dtype != HP_TF32) {
+    if (!needs_deriv_geom(op->kind) && op->dtype != HP_TF32 && op->dtype != HP_BF16) {
         hp_status st = ensure_dense(op->mesh);
         if (st) return st;
     }
@@ -1071,6 +1102,7 @@ void hp_mesh_destroy(hp_mesh m) {
             cudaFree(kv.second.A4_32);
             cudaFree(kv.second.A4T_32);
             cudaFree(kv.second.tc_img);
+            cudaFree(kv.second.tc_img16);
             cudaFree(kv.second.tc_pts);
         }
         cudaFree(m->d_err);

@@ -75,7 +75,10 @@ struct DeviceBlobs {
     float* A4_32 = nullptr;
     float* A4T_32 = nullptr;
     // tensor-core reference tiles (TF32, tensor-core shared-memory order), see TCArgs
-    unsigned char* tc_img = nullptr;
+    unsigned char* tc_img = nullptr;            // TF32 tiles
+    unsigned char* tc_img16 = nullptr;          // BF16 tiles (same order, 2-byte elements)
+    int tc_KP16 = 0, tc_fwd16 = 0, tc_bwd16 = 0;
+    int64_t tc_chunk16 = 0;
     float* tc_pts = nullptr;          // [NQ][10]: d eta/d xi and weight per point (affine elements)
     int tc_KP = 0, tc_NPpad = 0, tc_nch = 0, tc_fwd = 0, tc_bwd = 0;
     int64_t tc_chunk = 0;
@@ -188,11 +191,12 @@ struct TCArgs {
     const unsigned char* img;          // per chunk of points: 4 forward then 4 backward tiles
     int64_t chunk_bytes;
     int fwd_bytes, bwd_bytes, stage_bytes;
+    int es;                            // operand bytes: 4 TF32, 2 BF16
     int nsplit, stages;                // set by the launcher
     unsigned int* err;
 };
 constexpr int kTcMaxModes = 256;
-int tc_smem_bytes(int KP, int stage_bytes);
+int tc_smem_bytes(int KP, int stage_bytes, int es);
 int tc_chunk_points();
 int64_t tc_geom_floats(int64_t n_elem, int nch);
 cudaError_t tc_geom_layout(const double* g, float* out, int64_t n_elem, int NQ, int NQp, int nch, cudaStream_t s);

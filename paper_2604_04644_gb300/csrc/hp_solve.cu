@@ -30,7 +30,7 @@ struct hp_c0_s {
     uint8_t* d_bnd = nullptr;
     // solver state (created on first solve)
     hp_op op64 = nullptr, op32 = nullptr;
-    int op32_mode = 0;                 // 1: FP32 sum factorisation, 2: TF32 tensor-core elemental matrices
+    int op32_mode = 0;                 // 1: FP32 sum factorisation, 2 / 3: TF32 / BF16 tensor-core elemental matrices
     double diag_lambda = -1.0;
     double* d_diag = nullptr;          // assembled Jacobi diagonal (global)
     double* d_loc64[2] = {nullptr, nullptr};
@@ -190,7 +190,8 @@ hp_status prepare(hp_c0 c, double lambda, int mixed, cudaStream_t s) {
         c->op32 = nullptr;
     }
     if (mixed && !c->op32) {
-        st = mixed == 2 ? hp_op_create(c->mesh, HP_HELMHOLTZ, HP_STRAT_ELEMAT, HP_TF32, &c->op32)
+        st = mixed == 3 ? hp_op_create(c->mesh, HP_HELMHOLTZ, HP_STRAT_ELEMAT, HP_BF16, &c->op32)
+           : mixed == 2 ? hp_op_create(c->mesh, HP_HELMHOLTZ, HP_STRAT_ELEMAT, HP_TF32, &c->op32)
                         : hp_op_create(c->mesh, HP_HELMHOLTZ, HP_STRAT_SUMFAC, HP_FP32, &c->op32);
         if (st) return st;
         c->op32_mode = mixed;
@@ -403,7 +404,7 @@ hp_status hp_c0_diagonal(hp_c0 c, double lambda, double* diag, int local, void* 
 hp_status hp_solve(hp_c0 c, double lambda, const double* rhs, double* x, const hp_solve_opts* opts,
                    hp_solve_stats* stats, void* stream) {
     if (!c || !rhs || !x || !opts) { set_error("hp_solve: null argument"); return HP_ERR_ARG; }
-    if (!(opts->tol > 0) || opts->max_iter < 1 || opts->mixed < 0 || opts->mixed > 2 ||
+    if (!(opts->tol > 0) || opts->max_iter < 1 || opts->mixed < 0 || opts->mixed > 3 ||
         (opts->mixed && (!(opts->inner_tol > 0) || opts->inner_max_iter < 1 || opts->max_refinements < 1))) {
         set_error("hp_solve: bad options");
         return HP_ERR_ARG;

@@ -58,7 +58,7 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
 // Descriptor of a swizzled K-major operand: start address (a K step of the
 // MMA moves it by 32 bytes inside the swizzle row), SBO = 8-row atom stride,
 // mode 2 = 128-byte swizzle, 4 = 64-byte swizzle; the leading offset is unused.
-constexpr uint32_t kSw128 = 2, kSw64 = 4;
+constexpr uint32_t kSw128 = 2, kSw64 = 4, kSw32 = 6;
 __device__ __forceinline__ uint64_t smem_desc_sw(uint32_t saddr, uint32_t sbo, uint32_t mode) {
     uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
     d |= (uint64_t)1 << 16;

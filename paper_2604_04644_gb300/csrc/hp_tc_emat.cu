@@ -27,6 +27,8 @@
 // warp 8 issues the bulk copies; warp 9 issues the MMAs.  Every wait is
 // bounded; a timeout latches DERR_TIMEOUT, stops every role, drains the
 // copies and MMAs in flight and frees the tensor memory before the CTA exits.
+#include <cuda_bf16.h>
+
 #include "hp_tc.cuh"
 
 namespace hp {
@@ -40,8 +42,50 @@ constexpr int kFwdBufs = 3;       // forward accumulators in flight: the forward
 constexpr int kOutCol = kFwdBufs * 4 * 16;   // TMEM column of the output accumulator
 constexpr int kEpi = 256;         // epilogue threads
 constexpr int kThreads = kEpi + 64;
-constexpr int kVBytes = 128 * kNPT * 4;   // one V' tile [128 x 16] TF32
-constexpr int kSliceBytes = 4 * kNPT * 32 * 4;   // forward operand: 64 rows x 32 modes (128-byte rows)
+constexpr int kSliceBytes = 4 * kNPT * 128;   // forward operand slice: 64 rows x 128 bytes of modes
+
+// Operand element type: TF32 (ES = 4, kind::tf32, K = 8 per MMA) or BF16
+// (ES = 2, kind::f16, K = 16 per MMA); every MMA K step is 32 bytes.  The
+// 16-point tiles (V', backward R) have rows of 16 ES bytes: 64-byte swizzle
+// for TF32, 32-byte swizzle for BF16.
+template <int ES>
+struct Op {
+    static constexpr int KR = 128 / ES;                   // modes per 128-byte row (slice width)
+    static constexpr int VROW = kNPT * ES;                // bytes per row of a 16-point tile
+    static constexpr int VBYTES = 128 * VROW;             // one V' tile
+    static constexpr uint32_t VSW = ES == 4 ? tc::kSw64 : tc::kSw32;
+    static constexpr uint32_t FMT = ES == 4 ? tc::kFmtTF32 : tc::kFmtBF16;
+    __device__ static void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+        if constexpr (ES == 4) tc::mma_tf32(d, a, b, id, acc);
+        else tc::mma_bf16(d, a, b, id, acc);
+    }
+    // byte offset of element (r, k) in a 128-byte swizzled row block
+    __device__ static uint32_t off128(uint32_t r, uint32_t k) {
+        return r * 128 + ((((k * ES) >> 4) ^ (r & 7)) << 4) + ((k * ES) & 15);
+    }
+    // byte offset of the 16-byte chunk holding points p..p+16/ES-1 of row r of a 16-point tile
+    __device__ static uint32_t offv(uint32_t r, uint32_t p) {
+        if constexpr (ES == 4) return tc::sw64_offset(r, p);
+        else return r * 32 + ((((p * 2) >> 4) ^ ((r >> 2) & 1)) << 4);
+    }
+    // 16 bytes of operands from 16 / ES floats
+    __device__ static uint4 pack(const float* x) {
+        uint4 u;
+        if constexpr (ES == 4) {
+            u.x = __float_as_uint(tc::to_tf32(x[0])); u.y = __float_as_uint(tc::to_tf32(x[1]));
+            u.z = __float_as_uint(tc::to_tf32(x[2])); u.w = __float_as_uint(tc::to_tf32(x[3]));
+        } else {
+            uint32_t w[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const __nv_bfloat162 h2 = __floats2bfloat162_rn(x[2 * i], x[2 * i + 1]);
+                w[i] = *reinterpret_cast<const uint32_t*>(&h2);
+            }
+            u = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+        return u;
+    }
+};
 
 struct Bars {
     uint64_t full[kMaxStages], empty[kMaxStages];
@@ -73,15 +117,16 @@ __device__ __forceinline__ void arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
-template <bool AFFINE>
+template <bool AFFINE, int ES>
 __global__ void __launch_bounds__(kThreads, 1) tc_emat_kernel(const __grid_constant__ TCArgs a) {
+    using O = Op<ES>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // the swizzle patterns are taken from shared-memory address bits: align to 1 KB
     unsigned char* smem = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
     Bars* B = reinterpret_cast<Bars*>(smem);
     unsigned char* sU = smem + 1024;                                   // KP/32 blocks [128 x 32] tf32, 128 B swizzle
-    unsigned char* sV = sU + 128 * a.KP * 4;                           // [2][4][128 x 16] tf32, 64 B swizzle
-    unsigned char* sR = sV + 8 * kVBytes;                              // ring
+    unsigned char* sV = sU + 128 * a.KP * ES;                          // [2][4][128 x 16], 64 / 32 B swizzle
+    unsigned char* sR = sV + 8 * O::VBYTES;                            // ring
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nst = a.stages;
     // work items: (tile of 128 elements, part of its point chunks); parts of one
@@ -139,7 +184,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_emat_kernel(const __grid_const
                 for (int t = kb; t < ke + kFwdBufs - 1 && ok; ++t) {
                     if (t < ke) {
                         const unsigned char* base = a.img + (size_t)t * a.chunk_bytes;
-                        for (int sl = 0; sl * 32 < a.KP && ok; ++sl) put(base + (size_t)sl * kSliceBytes, kSliceBytes);
+                        for (int sl = 0; sl * O::KR < a.KP && ok; ++sl) put(base + (size_t)sl * kSliceBytes, kSliceBytes);
                     }
                     const int kbw = t - (kFwdBufs - 1);
                     if (kbw >= kb) {
@@ -159,8 +204,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_emat_kernel(const __grid_const
     } else if (warp == 9) {
         // ---------------------------------------------------------------- MMA issuer
         if (lane == 0) {
-            const uint32_t id_f = tc::instr_desc(tc::kFmtTF32, 128, kNPT * (a.c1 - a.c0));
-            const uint32_t id_b = tc::instr_desc(tc::kFmtTF32, 128, a.NPpad);
+            const uint32_t id_f = tc::instr_desc(O::FMT, 128, kNPT * (a.c1 - a.c0));
+            const uint32_t id_b = tc::instr_desc(O::FMT, 128, a.NPpad);
             int slot = 0;
             uint32_t pass = 0, nout = 0, ntile = 0, g0 = 0;   // g: chunks processed by this CTA
             bool ok = true;
@@ -176,15 +221,15 @@ __global__ void __launch_bounds__(kThreads, 1) tc_emat_kernel(const __grid_const
                         tc::fence_after();
                         // columns (b*4 + c0)*16 .. of the accumulator = components c0..c1-1
                         const uint32_t d = tbase + (uint32_t)((b * 4 + a.c0) * kNPT);
-                        for (int sl = 0; sl * 32 < a.KP && ok; ++sl) {
+                        for (int sl = 0; sl * O::KR < a.KP && ok; ++sl) {
                             if (!wait_bar(&B->full[slot], pass, B, a.err)) { ok = false; break; }
                             tc::fence_after();
                             // K block sl of U (128 rows x 128 B) and rows 16 c0.. of the slice
                             const uint32_t sa = smem_addr(sU) + sl * 128 * 128;
                             const uint32_t sb = smem_addr(sR + (size_t)slot * a.stage_bytes) + a.c0 * 2 * 1024;
                             for (int s = 0; s < 4; ++s)
-                                tc::mma_tf32(d, tc::smem_desc_sw(sa + s * 32, 1024, tc::kSw128),
-                                             tc::smem_desc_sw(sb + s * 32, 1024, tc::kSw128), id_f, sl > 0 || s > 0);
+                                O::mma(d, tc::smem_desc_sw(sa + s * 32, 1024, tc::kSw128),
+                                       tc::smem_desc_sw(sb + s * 32, 1024, tc::kSw128), id_f, sl > 0 || s > 0);
                             tc::commit(&B->empty[slot]);
                             if (++slot == nst) { slot = 0; pass ^= 1u; }
                         }
@@ -202,12 +247,12 @@ __global__ void __launch_bounds__(kThreads, 1) tc_emat_kernel(const __grid_const
                         for (int c = a.c0; c < a.c1 && ok; ++c) {
                             if (!wait_bar(&B->full[slot], pass, B, a.err)) { ok = false; break; }
                             tc::fence_after();
-                            const uint32_t sa = smem_addr(sV + (size_t)(b * 4 + c) * kVBytes);
+                            const uint32_t sa = smem_addr(sV + (size_t)(b * 4 + c) * O::VBYTES);
                             const uint32_t sb = smem_addr(sR + (size_t)slot * a.stage_bytes);
-                            for (int s = 0; s < kNPT / 8; ++s)
-                                tc::mma_tf32(tbase + kOutCol, tc::smem_desc_sw(sa + s * 32, 512, tc::kSw64),
-                                             tc::smem_desc_sw(sb + s * 32, 512, tc::kSw64), id_b,
-                                             !(k == kb && c == a.c0 && s == 0));
+                            for (int s = 0; s < O::VROW / 32; ++s)
+                                O::mma(tbase + kOutCol, tc::smem_desc_sw(sa + s * 32, 8 * O::VROW, O::VSW),
+                                       tc::smem_desc_sw(sb + s * 32, 8 * O::VROW, O::VSW), id_b,
+                                       !(k == kb && c == a.c0 && s == 0));
                             tc::commit(&B->empty[slot]);
                             if (++slot == nst) { slot = 0; pass ^= 1u; }
                         }
@@ -239,12 +284,12 @@ __global__ void __launch_bounds__(kThreads, 1) tc_emat_kernel(const __grid_const
             {
                 const float* src = valid ? a.in + a.coeff_off[e] : nullptr;
                 const int half = a.KP / 2;
-                for (int m0 = h * half; m0 < (h + 1) * half; m0 += 4) {
-                    float4 v;
-                    float* pv = reinterpret_cast<float*>(&v);
+                constexpr int KC = 16 / ES;                   // modes per 16-byte chunk
+                for (int m0 = h * half; m0 < (h + 1) * half; m0 += KC) {
+                    float x[KC];
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) pv[i] = (valid && m0 + i < a.NP) ? tc::to_tf32(src[m0 + i]) : 0.f;
-                    *reinterpret_cast<float4*>(sU + (m0 >> 5) * 128 * 128 + tc::sw128_offset(r, m0 & 31)) = v;
+                    for (int i = 0; i < KC; ++i) x[i] = (valid && m0 + i < a.NP) ? src[m0 + i] : 0.f;
+                    *reinterpret_cast<uint4*>(sU + (m0 / O::KR) * 128 * 128 + O::off128(r, m0 % O::KR)) = O::pack(x);
                 }
             }
             tc::fence_async_smem();
@@ -338,13 +383,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_emat_kernel(const __grid_const
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
                     if (c < a.c0 || c >= a.c1) continue;
-                    unsigned char* dst = sV + (size_t)(b * 4 + c) * kVBytes;
+                    unsigned char* dst = sV + (size_t)(b * 4 + c) * O::VBYTES;
 #pragma unroll
-                    for (int p0 = 0; p0 < kHalf; p0 += 4) {
-                        float4 t4 = make_float4(tc::to_tf32(o[c][p0]), tc::to_tf32(o[c][p0 + 1]), tc::to_tf32(o[c][p0 + 2]),
-                                                tc::to_tf32(o[c][p0 + 3]));
-                        *reinterpret_cast<float4*>(dst + tc::sw64_offset(r, h * kHalf + p0)) = t4;
-                    }
+                    for (int p0 = 0; p0 < kHalf; p0 += 16 / ES)
+                        *reinterpret_cast<uint4*>(dst + O::offv(r, h * kHalf + p0)) = O::pack(&o[c][p0]);
                 }
                 tc::fence_async_smem();
                 arrive(&B->vp_full[b]);
@@ -407,15 +449,15 @@ __global__ void tc_geom_kernel(const double* g, float* out, int64_t n_elem, int 
 
 }  // namespace
 
-int tc_stages(int KP, int stage_bytes) {
-    const int base = 2048 + 128 * KP * 4 + 8 * kVBytes;      // alignment slack + barriers + U + V
+int tc_stages(int KP, int stage_bytes, int es) {
+    const int base = 2048 + 128 * KP * es + 8 * 128 * kNPT * es;      // alignment slack + barriers + U + V'
     for (int st = kMaxStages; st >= 2; --st)
         if (base + st * stage_bytes <= 227 * 1024) return st;
     return 0;
 }
 
-int tc_smem_bytes(int KP, int stage_bytes) {
-    int b = 2048 + 128 * KP * 4 + 8 * kVBytes + tc_stages(KP, stage_bytes) * stage_bytes;
+int tc_smem_bytes(int KP, int stage_bytes, int es) {
+    int b = 2048 + 128 * KP * es + 8 * 128 * kNPT * es + tc_stages(KP, stage_bytes, es) * stage_bytes;
     return b < 116 * 1024 ? 116 * 1024 : b;    // at most one CTA (and one TMEM allocation) per SM
 }
 
@@ -432,10 +474,11 @@ cudaError_t tc_emat_launch(bool affine, const TCArgs& a, cudaStream_t s) {
     const int64_t ntiles = (a.n_elem + 127) / 128;
     if (ntiles <= 0) return cudaSuccess;
     TCArgs b = a;
-    b.stages = tc_stages(a.KP, a.stage_bytes);
+    b.stages = tc_stages(a.KP, a.stage_bytes, a.es);
     if (b.stages < 2) return cudaErrorInvalidValue;
-    const int smem = tc_smem_bytes(a.KP, a.stage_bytes);
-    auto kern = affine ? tc_emat_kernel<true> : tc_emat_kernel<false>;
+    const int smem = tc_smem_bytes(a.KP, a.stage_bytes, a.es);
+    auto kern = a.es == 2 ? (affine ? tc_emat_kernel<true, 2> : tc_emat_kernel<false, 2>)
+                          : (affine ? tc_emat_kernel<true, 4> : tc_emat_kernel<false, 4>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0;

@@ -384,7 +384,7 @@ def hp_solve(c0, lam, rhs, x, tol=1e-10, max_iter=20000, mixed=False, inner_tol=
              max_refinements=20, stream=None):
     """Returns (status, stats); raises for errors other than HP_ERR_NOT_CONVERGED.
     mixed: 0 / False FP64 PCG, 1 / True FP32 inner PCG with FP64 refinement,
-    2 the same with the TF32 tensor-core inner operator."""
+    2 / 3 the same with the TF32 / BF16 tensor-core inner operator."""
     o = hp_solve_opts(float(tol), int(max_iter), int(mixed), float(inner_tol), int(inner_max_iter),
                       int(max_refinements))
     st = hp_solve_stats()

@@ -1,5 +1,5 @@
-"""Tensor-core (tcgen05, TF32) elemental-matrix operators against the FP64
-oracle, through the C ABI.
+"""Tensor-core (tcgen05, TF32 and BF16) elemental-matrix operators against the
+FP64 oracle, through the C ABI.
 
 Tolerance (relative, infinity norm over the whole output vector):
 TF32_TOL = 8 u with u = 2^-11, the unit roundoff of TF32 (10 stored mantissa
@@ -11,7 +11,8 @@ sum to ||out||_inf is the cancellation factor; random-sign rounding errors
 keep the measured error near 1 u (worst case 1.1 u on these meshes), and 8 u
 allows a cancellation factor of 2.7 at full correlation.  Blocks whose mode
 count exceeds the tensor-memory budget (N_P > 256) run FP32 sum factorisation
-and are held to the FP32 bound of test_gpu_parity.
+and are held to the FP32 bound of test_gpu_parity.  BF16 (8 significant
+bits) takes the same argument with u = 2^-8: BF16_TOL = 8 u.
 """
 import numpy as np
 import pytest
@@ -25,6 +26,8 @@ from tests.test_gpu_parity import OPS, fp32_tol, make_input, mixed_mesh, rel_err
 
 TF32_U = 2.0 ** -11
 TF32_TOL = 8 * TF32_U
+BF16_U = 2.0 ** -8          # 8 significant bits, round to nearest
+BF16_TOL = 8 * BF16_U
 MAX_TC_MODES = 256
 
 
@@ -40,11 +43,11 @@ def n_blocks(mesh):
     return len(set(zip(mesh["shape"].tolist(), mesh["P"].tolist(), mesh["curved"].tolist())))
 
 
-def run_tc(hp, mesh, opname, x, lam):
+def run_tc(hp, mesh, opname, x, lam, dtype=None):
     h = hp.hp_mesh_create(mesh, 0)
     try:
         co, po, nc, nph = hp.hp_mesh_layout(h, mesh["n_elem"])
-        op = hp.hp_op_create(h, OPS[opname], hp.HP_STRAT_ELEMAT, hp.HP_TF32)
+        op = hp.hp_op_create(h, OPS[opname], hp.HP_STRAT_ELEMAT, hp.HP_TF32 if dtype is None else dtype)
         try:
             strat = hp.hp_op_strategies(op, n_blocks(mesh))
             xt = torch.tensor(x, device="cuda:0", dtype=torch.float32)
@@ -69,23 +72,24 @@ def per_shape_errors(mesh, co, y, ref):
     return out
 
 
+@pytest.mark.parametrize("prec", ["tf32", "bf16"])
 @pytest.mark.parametrize("P", [1, 2, 3, 4, 5, 6, 8])
 @pytest.mark.parametrize("opname", ["mass", "laplacian", "helmholtz"])
-def test_tf32_tensor_core_matches_oracle(hp, P, opname):
+def test_tensor_core_matches_oracle(hp, P, opname, prec):
     """Mixed mesh (all four shapes, affine and curved halves, ragged tiles):
-    tensor-core blocks within TF32_TOL, FP32 sum-factorisation blocks within
-    the FP32 bound."""
+    tensor-core blocks within TF32_TOL / BF16_TOL, FP32 sum-factorisation
+    blocks within the FP32 bound."""
     mesh = mixed_mesh(P)
     co, _ = oracle_ops.layout(mesh)
     x = make_input(mesh, opname, 600 + P)
     x32 = x.astype(np.float32).astype(np.float64)
     ref = oracle_ops.apply(opname, mesh, x32, 1.3)
-    y, strat = run_tc(hp, mesh, opname, x, 1.3)
+    y, strat = run_tc(hp, mesh, opname, x, 1.3, hp.HP_TF32 if prec == "tf32" else hp.HP_BF16)
     assert not np.isnan(y).any()
     from oracle.basis import n_modes
     errs = per_shape_errors(mesh, co, y, ref)
     for s, err in errs.items():
-        tol = TF32_TOL if n_modes(s, P) <= MAX_TC_MODES else fp32_tol(P)
+        tol = (TF32_TOL if prec == "tf32" else BF16_TOL) if n_modes(s, P) <= MAX_TC_MODES else fp32_tol(P)
         assert err <= tol, (s, err, tol)
 
 
@@ -117,14 +121,15 @@ def test_tf32_strategy_per_block(hp):
         hp.hp_mesh_destroy(h)
 
 
-@pytest.mark.parametrize("shape,P,curved", [(3, 2, True), (2, 4, False), (0, 3, True)])
-def test_tf32_large_block_single_part(hp, shape, P, curved):
+@pytest.mark.parametrize("shape,P,curved,prec", [(3, 2, True, "tf32"), (2, 4, False, "tf32"), (0, 3, True, "tf32"),
+                                                (3, 4, True, "bf16"), (1, 5, False, "bf16")])
+def test_large_block_single_part(hp, shape, P, curved, prec):
     """More tiles than SMs (each tile in one part, plain stores): 20 000
     elements of one shape, sampled elements against the oracle."""
     mesh = inputs.replicated_mesh(shape, P, 20000, curved=curved)
     co, _ = oracle_ops.layout(mesh)
     x = inputs.random_coefficients(77, co)
-    y, strat = run_tc(hp, mesh, "helmholtz", x, 1.0)
+    y, strat = run_tc(hp, mesh, "helmholtz", x, 1.0, hp.HP_TF32 if prec == "tf32" else hp.HP_BF16)
     assert strat.tolist() == [hp.HP_STRAT_ELEMAT]
     rng = np.random.default_rng(1)
     sample = np.sort(np.concatenate([rng.choice(mesh["n_elem"], 150, replace=False), [mesh["n_elem"] - 1]]))
@@ -132,7 +137,7 @@ def test_tf32_large_block_single_part(hp, shape, P, curved):
     x32 = x.astype(np.float32).astype(np.float64)
     ref = oracle_ops.apply("helmholtz", mesh, x32, 1.0, elems=sample)
     idx = np.concatenate([np.arange(co[e], co[e + 1]) for e in sample])
-    assert rel_err(y[idx], ref[idx]) <= TF32_TOL
+    assert rel_err(y[idx], ref[idx]) <= (TF32_TOL if prec == "tf32" else BF16_TOL)
 
 
 def test_tf32_single_element(hp):
