@@ -237,3 +237,36 @@ def test_unit_cube_of_64_affine_hexes(hp, opname):
         hp.hp_mesh_destroy(h)
     ref32 = oracle_ops.apply(opname, mesh, x.astype(np.float32).astype(np.float64), 1.0)
     assert rel_err(y32.double().cpu().numpy(), ref32) <= 8 * 2.0 ** -11
+
+
+def test_apply_block_and_block_work(hp):
+    """Launching every block in turn (hp_op_apply_block) gives hp_op_apply's
+    result bit for bit; per-block work sums to the operator's; the executed
+    FP64 operations are at most the collocated count; bad blocks are refused."""
+    mesh = mixed_mesh(5)
+    co, _ = oracle_ops.layout(mesh)
+    x = make_input(mesh, "helmholtz", 31)
+    h = hp.hp_mesh_create(mesh, 0)
+    try:
+        op = hp.hp_op_create(h, hp.HP_HELMHOLTZ)
+        nb = len(set(zip(mesh["shape"].tolist(), mesh["P"].tolist(), mesh["curved"].tolist())))
+        xt = torch.tensor(x, device="cuda:0")
+        y1 = torch.full((len(x),), float("nan"), device="cuda:0", dtype=torch.float64)
+        y2 = torch.full_like(y1, float("nan"))
+        hp.hp_op_apply(op, 1.0, xt, y1)
+        for b in range(nb):
+            hp.hp_op_apply_block(op, b, 1.0, xt, y2)
+        hp.hp_op_sync(op)
+        assert torch.equal(y1, y2)
+        tot = hp.hp_op_block_work(op, -1)
+        parts = [hp.hp_op_block_work(op, b) for b in range(nb)]
+        assert sum(p[0] for p in parts) == mesh["n_elem"] == tot[0]
+        assert sum(p[1] for p in parts) == tot[1] == hp.hp_op_work(op)[0]
+        assert abs(sum(p[2] for p in parts) - tot[2]) <= 1e-9 * tot[2]
+        assert all(0 < p[3] <= p[2] for p in parts)
+        with pytest.raises(hp.HpError) as ei:
+            hp.hp_op_apply_block(op, nb, 1.0, xt, y2)
+        assert ei.value.status == hp.HP_ERR_ARG
+        hp.hp_op_destroy(op)
+    finally:
+        hp.hp_mesh_destroy(h)
