@@ -410,7 +410,9 @@ cudaError_t launch_block(hp_op op, size_t bi, int tile, double lambda, const voi
         a.chunk_bytes = bf ? blob.tc_chunk16 : blob.tc_chunk;
         a.fwd_bytes = bf ? blob.tc_fwd16 : blob.tc_fwd;
         a.bwd_bytes = bf ? blob.tc_bwd16 : blob.tc_bwd;
-        a.stage_bytes = (std::max(4 * tc_chunk_points() * 128, a.bwd_bytes) + 1023) & ~1023;
+        // BF16: one stage per chunk (its whole forward operand, read again by the
+        // backward MMAs); TF32: forward slices and backward tiles separately
+        a.stage_bytes = bf ? a.fwd_bytes : (std::max(4 * tc_chunk_points() * 128, a.bwd_bytes) + 1023) & ~1023;
         a.err = op->d_err;
         return tc_emat_launch(!b.curved, a, s);
     }

@@ -68,6 +68,18 @@ __device__ __forceinline__ uint64_t smem_desc_sw(uint32_t saddr, uint32_t sbo, u
     return d;
 }
 
+// Swizzled descriptor with an explicit leading offset (MN-major operands:
+// LBO = stride between swizzle atoms along MN, SBO = stride between 8-row
+// groups along K)
+__device__ __forceinline__ uint64_t smem_desc_sw_lbo(uint32_t saddr, uint32_t lbo, uint32_t sbo, uint32_t mode) {
+    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)mode << 61;
+    return d;
+}
+
 // Instruction descriptor: FP32 accumulator, A and B of format `fmt`
 // (kind::f16: 0 = F16, 1 = BF16; kind::tf32: 2 = TF32), both K-major,
 // N (multiple of 16 for M = 128, 8..256) and M (64 or 128).

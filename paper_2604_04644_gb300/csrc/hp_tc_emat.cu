@@ -17,8 +17,10 @@
 // over chunks of 16 quadrature points.  U (the element coefficients) stays in
 // shared memory for the work item; the reference tiles F_c, R_c are laid out
 // on the host in the tensor core's shared-memory order and streamed by 1-D
-// bulk copies (TMA) through a ring of stages (the forward operand in K slices
-// of 32 modes, the backward tiles one component at a time).  Three forward
+// bulk copies (TMA) through a ring of stages (TF32: the forward operand in K
+// slices of 32 modes, the backward tiles one component at a time; BF16: one
+// stage per chunk holding its whole forward operand, which the backward MMAs
+// read again as an MN-major operand, so no backward tiles are streamed).  Three forward
 // accumulators are in flight and the V' tiles are double-buffered, so the
 // forward MMAs run two chunks ahead of the metric and the metric of chunk k
 // overlaps the backward MMAs of chunk k-1.
@@ -180,7 +182,12 @@ __global__ void __launch_bounds__(kThreads, 1) tc_emat_kernel(const __grid_const
             for (int64_t w = blockIdx.x; w < nwork && ok; w += gridDim.x) {
                 int kb, ke;
                 chunk_range(w, kb, ke);
-                // the MMA issuer's order: forward of chunk t, backward of chunk t - (kFwdBufs - 1)
+                // the MMA issuer's order: forward of chunk t, backward of chunk t - (kFwdBufs - 1);
+                // BF16: one stage per chunk (all forward slices), read again by the backward
+                if constexpr (ES == 2) {
+                    for (int t = kb; t < ke && ok; ++t) put(a.img + (size_t)t * a.chunk_bytes, (uint32_t)a.fwd_bytes);
+                    continue;
+                }
                 for (int t = kb; t < ke + kFwdBufs - 1 && ok; ++t) {
                     if (t < ke) {
                         const unsigned char* base = a.img + (size_t)t * a.chunk_bytes;
@@ -213,6 +220,56 @@ __global__ void __launch_bounds__(kThreads, 1) tc_emat_kernel(const __grid_const
                 int kb, ke;
                 chunk_range(w, kb, ke);
                 if (!wait_bar(&B->u_full, ntile & 1u, B, a.err)) { ok = false; break; }
+                if constexpr (ES == 2) {
+                    // one ring stage per chunk: forward MMAs read its slices K-major;
+                    // kFwdBufs - 1 chunks later the backward MMAs read the same stage
+                    // MN-major (N = modes: 64-mode atoms one slice apart; K = the
+                    // component's 16 points) and release it
+                    const uint32_t id_bt = id_b | (1u << 16);                     // B operand MN-major
+                    for (int t = kb; t < ke + kFwdBufs - 1 && ok; ++t) {
+                        if (t < ke) {
+                            const uint32_t g = g0 + (uint32_t)(t - kb), b = g % kFwdBufs, use = g / kFwdBufs;
+                            const uint32_t st = g % nst, par = (g / nst) & 1u;
+                            if (!wait_bar(&B->fwd_empty[b], (use & 1u) ^ 1u, B, a.err)) { ok = false; break; }
+                            if (!wait_bar(&B->full[st], par, B, a.err)) { ok = false; break; }
+                            tc::fence_after();
+                            const uint32_t d = tbase + (uint32_t)((b * 4 + a.c0) * kNPT);
+                            const uint32_t stage = smem_addr(sR + (size_t)st * a.stage_bytes);
+                            for (int sl = 0; sl * O::KR < a.KP; ++sl) {
+                                const uint32_t sa = smem_addr(sU) + sl * 128 * 128;
+                                const uint32_t sb = stage + sl * kSliceBytes + a.c0 * 2 * 1024;
+                                for (int s = 0; s < 4; ++s)
+                                    O::mma(d, tc::smem_desc_sw(sa + s * 32, 1024, tc::kSw128),
+                                           tc::smem_desc_sw(sb + s * 32, 1024, tc::kSw128), id_f, sl > 0 || s > 0);
+                            }
+                            tc::commit(&B->fwd_full[b]);
+                        }
+                        const int k = t - (kFwdBufs - 1);
+                        if (k >= kb && ok) {
+                            const uint32_t g = g0 + (uint32_t)(k - kb), b = g & 1u, use = g >> 1;
+                            const uint32_t st = g % nst;
+                            if (!wait_bar(&B->vp_full[b], use & 1u, B, a.err)) { ok = false; break; }
+                            if (k == kb) {
+                                if (!wait_bar(&B->out_empty, (nout & 1u) ^ 1u, B, a.err)) { ok = false; break; }
+                                ++nout;
+                            }
+                            tc::fence_after();
+                            const uint32_t stage = smem_addr(sR + (size_t)st * a.stage_bytes);
+                            for (int c = a.c0; c < a.c1; ++c) {
+                                const uint32_t sa = smem_addr(sV + (size_t)(b * 4 + c) * O::VBYTES);
+                                // LBO: next 64-mode atom (next slice); SBO: next 8 points
+                                const uint64_t db = tc::smem_desc_sw_lbo(stage + c * 2 * 1024, kSliceBytes, 1024, tc::kSw128);
+                                O::mma(tbase + kOutCol, tc::smem_desc_sw(sa, 8 * O::VROW, O::VSW), db, id_bt,
+                                       !(k == kb && c == a.c0));
+                            }
+                            tc::commit(&B->empty[st]);
+                            tc::commit(&B->vp_empty[b]);
+                        }
+                    }
+                    if (ok) tc::commit(&B->out_full);
+                    g0 += (uint32_t)(ke - kb);
+                    continue;
+                }
                 for (int t = kb; t < ke + kFwdBufs - 1 && ok; ++t) {
                     if (t < ke) {
                         const int k = t;
@@ -475,7 +532,8 @@ cudaError_t tc_emat_launch(bool affine, const TCArgs& a, cudaStream_t s) {
     if (ntiles <= 0) return cudaSuccess;
     TCArgs b = a;
     b.stages = tc_stages(a.KP, a.stage_bytes, a.es);
-    if (b.stages < 2) return cudaErrorInvalidValue;
+    // BF16 holds a chunk's stage until its backward MMAs, kFwdBufs - 1 chunks later
+    if (b.stages < (a.es == 2 ? kFwdBufs + 1 : 2)) return cudaErrorInvalidValue;
     const int smem = tc_smem_bytes(a.KP, a.stage_bytes, a.es);
     auto kern = a.es == 2 ? (affine ? tc_emat_kernel<true, 2> : tc_emat_kernel<false, 2>)
                           : (affine ? tc_emat_kernel<true, 4> : tc_emat_kernel<false, 4>);
