@@ -266,33 +266,23 @@ hp_status ensure_tc(hp_mesh m, int es) {
             db.tc_KP16 = KP; db.tc_fwd16 = fwd; db.tc_bwd16 = bwd; db.tc_chunk16 = chunk;
         }
         db.tc_NPpad = NPpad; db.tc_nch = nch;
-        if (db.tc_pts) continue;
-        // d eta / d xi and the quadrature weight at every point (affine elements)
-        const RefTables& t = ref_tables(shape, P);
-        std::vector<float> pts((size_t)NQ * 10);
-        for (int l = 0; l < NQ; ++l) {
-            const int i = l / (Q * Q), j = (l / Q) % Q, k = l % Q;
-            double T[3][3];
-            switch (shape) {
-                case HP_HEX: deta_dxi<HP_HEX, double>(t.z[0][i], t.z[1][j], t.z[2][k], T); break;
-                case HP_PRISM: deta_dxi<HP_PRISM, double>(t.z[0][i], t.z[1][j], t.z[2][k], T); break;
-                case HP_PYR: deta_dxi<HP_PYR, double>(t.z[0][i], t.z[1][j], t.z[2][k], T); break;
-                default: deta_dxi<HP_TET, double>(t.z[0][i], t.z[1][j], t.z[2][k], T); break;
-            }
-            for (int d = 0; d < 9; ++d) pts[(size_t)l * 10 + d] = (float)T[d / 3][d % 3];
-            pts[(size_t)l * 10 + 9] = (float)(t.w[0][i] * t.w[1][j] * t.w[2][k]);
-        }
-        hp_status st = upload(&db.tc_pts, pts.data(), pts.size());
-        if (st) return st;
     }
-    // curved blocks: FP32 metric factors in the tile-major order the epilogue reads
+    // FP32 metric factors at every point in the tile-major order the epilogue
+    // reads: copied from the curved factors, expanded from the affine records
     for (Block& b : m->blocks) {
-        if (!b.curved || b.d_geom_tc || n_modes(b.shape, b.P) > kTcMaxModes) continue;
+        if (b.d_geom_tc || n_modes(b.shape, b.P) > kTcMaxModes) continue;
         const DeviceBlobs& db = m->blobs.at(b.shape * 16 + b.P);
         const int64_t n = tc_geom_floats(b.n_elem, db.tc_nch);
         hp_status st = upload<float>(&b.d_geom_tc, nullptr, (size_t)n);
         if (st) return st;
-        cudaError_t e = tc_geom_layout(b.d_geom, b.d_geom_tc, b.n_elem, b.Q * b.Q * b.Q, nqp(b.Q), db.tc_nch, 0);
+        cudaError_t e;
+        if (b.curved) {
+            e = tc_geom_layout(b.d_geom, b.d_geom_tc, b.n_elem, b.Q * b.Q * b.Q, nqp(b.Q), db.tc_nch, 0);
+        } else {
+            const BlobLayout L = blob_layout_c(b.shape, b.P, 8);
+            const double* v64 = static_cast<const double*>(db.d64);
+            e = tc_geom_layout_affine(b.shape, b.d_geom, v64 + L.z, v64 + L.w, b.Q, b.d_geom_tc, b.n_elem, db.tc_nch, 0);
+        }
         if (e == cudaSuccess) e = cudaStreamSynchronize(0);
         if (e != cudaSuccess) return cuda_fail(e, "tensor-core geometry layout");
     }
@@ -404,8 +394,7 @@ cudaError_t launch_block(hp_op op, size_t bi, int tile, double lambda, const voi
         a.c1 = op->kind == HP_MASS ? 1 : 4;
         a.n_elem = b.n_elem; a.lambda = (float)lambda; a.coeff_off = b.d_coeff_off;
         a.in = static_cast<const float*>(in); a.out = static_cast<float*>(out);
-        a.geom = b.curved ? b.d_geom_tc : b.d_geom32;
-        a.tpts = blob.tc_pts;
+        a.geom = b.d_geom_tc;
         a.img = bf ? blob.tc_img16 : blob.tc_img;
         a.chunk_bytes = bf ? blob.tc_chunk16 : blob.tc_chunk;
         a.fwd_bytes = bf ? blob.tc_fwd16 : blob.tc_fwd;
@@ -414,7 +403,7 @@ cudaError_t launch_block(hp_op op, size_t bi, int tile, double lambda, const voi
         // backward MMAs); TF32: forward slices and backward tiles separately
         a.stage_bytes = bf ? a.fwd_bytes : (std::max(4 * tc_chunk_points() * 128, a.bwd_bytes) + 1023) & ~1023;
         a.err = op->d_err;
-        return tc_emat_launch(!b.curved, a, s);
+        return tc_emat_launch(a, s);
     }
     if (op->strat[bi] != HP_STRAT_SUMFAC) {
         const bool hybrid = op->strat[bi] == HP_STRAT_HYBRID;
@@ -1105,7 +1094,6 @@ void hp_mesh_destroy(hp_mesh m) {
             cudaFree(kv.second.A4T_32);
             cudaFree(kv.second.tc_img);
             cudaFree(kv.second.tc_img16);
-            cudaFree(kv.second.tc_pts);
         }
         cudaFree(m->d_err);
     }

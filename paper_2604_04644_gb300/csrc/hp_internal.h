@@ -60,7 +60,7 @@ struct Block {
     double* d_dgeom = nullptr;            // curved only: [n_elem][9][NQp] d eta_d / d x_i
     float* d_geom32 = nullptr;            // FP32 copies (created on demand)
     float* d_dgeom32 = nullptr;
-    float* d_geom_tc = nullptr;           // curved, tensor-core operator: tile-major FP32 factors
+    float* d_geom_tc = nullptr;           // tensor-core operator: tile-major FP32 factors (curved and affine)
     int64_t coeff_total = 0, phys_total = 0;   // per-block totals (work accounting)
 };
 
@@ -79,7 +79,6 @@ struct DeviceBlobs {
     unsigned char* tc_img16 = nullptr;          // BF16 tiles (same order, 2-byte elements)
     int tc_KP16 = 0, tc_fwd16 = 0, tc_bwd16 = 0;
     int64_t tc_chunk16 = 0;
-    float* tc_pts = nullptr;          // [NQ][10]: d eta/d xi and weight per point (affine elements)
     int tc_KP = 0, tc_NPpad = 0, tc_nch = 0, tc_fwd = 0, tc_bwd = 0;
     int64_t tc_chunk = 0;
 };
@@ -186,8 +185,7 @@ struct TCArgs {
     const int64_t* coeff_off;
     const float* in;
     float* out;
-    const float* geom;                 // curved: tile-major FP32 factors (tc_geom_layout); affine: [n][16]
-    const float* tpts;                 // affine: per point d eta/d xi (9) and weight, [NQ][10]
+    const float* geom;                 // tile-major FP32 factors (tc_geom_layout / tc_geom_layout_affine)
     const unsigned char* img;          // per chunk of points: 4 forward then 4 backward tiles
     int64_t chunk_bytes;
     int fwd_bytes, bwd_bytes, stage_bytes;
@@ -200,7 +198,9 @@ int tc_smem_bytes(int KP, int stage_bytes, int es);
 int tc_chunk_points();
 int64_t tc_geom_floats(int64_t n_elem, int nch);
 cudaError_t tc_geom_layout(const double* g, float* out, int64_t n_elem, int NQ, int NQp, int nch, cudaStream_t s);
-cudaError_t tc_emat_launch(bool affine, const TCArgs& a, cudaStream_t s);
+cudaError_t tc_geom_layout_affine(int shape, const double* rec, const double* z, const double* w, int Q, float* out,
+                                  int64_t n_elem, int nch, cudaStream_t s);
+cudaError_t tc_emat_launch(const TCArgs& a, cudaStream_t s);
 cudaError_t emat_launch_f32(bool hybrid, bool affine, const EMArgs<float>& a, cudaStream_t s);
 
 // per-shape launchers (hp_sf_<shape>.cu)

@@ -119,7 +119,7 @@ __device__ __forceinline__ void arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
-template <bool AFFINE, int ES>
+template <int ES>
 __global__ void __launch_bounds__(kThreads, 1) tc_emat_kernel(const __grid_constant__ TCArgs a) {
     using O = Op<ES>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -351,13 +351,6 @@ __global__ void __launch_bounds__(kThreads, 1) tc_emat_kernel(const __grid_const
             }
             tc::fence_async_smem();
             arrive(&B->u_full);
-            float K6[6] = {0, 0, 0, 0, 0, 0}, detJ = 0.f;
-            if (AFFINE && valid) {
-                const float* rec = a.geom + e * 16;
-#pragma unroll
-                for (int f = 0; f < 6; ++f) K6[f] = rec[f];
-                detJ = rec[6];
-            }
             // metric factors of a chunk: this thread's 8 points of each factor are
             // 32 contiguous bytes of the tile-major layout; the next chunk's are
             // fetched while the current one is processed
@@ -376,17 +369,15 @@ __global__ void __launch_bounds__(kThreads, 1) tc_emat_kernel(const __grid_const
                     Gn[f][4] = x1.x; Gn[f][5] = x1.y; Gn[f][6] = x1.z; Gn[f][7] = x1.w;
                 }
             };
-            if (!AFFINE && kb < ke) load_geom(kb);
+            if (kb < ke) load_geom(kb);
             for (int k = kb; k < ke && ok; ++k) {
                 const uint32_t g = g0 + (uint32_t)(k - kb), b = g & 1u, use = g >> 1;
                 const uint32_t bf = g % kFwdBufs, usef = g / kFwdBufs;     // forward accumulator buffer
-                if (!AFFINE) {
 #pragma unroll
-                    for (int f = 0; f < 7; ++f)
+                for (int f = 0; f < 7; ++f)
 #pragma unroll
-                        for (int p = 0; p < kHalf; ++p) Gc[f][p] = Gn[f][p];
-                    if (k + 1 < ke) load_geom(k + 1);
-                }
+                    for (int p = 0; p < kHalf; ++p) Gc[f][p] = Gn[f][p];
+                if (k + 1 < ke) load_geom(k + 1);
                 if (!wait_warp(&B->fwd_full[bf], usef & 1u, B, a.err)) { ok = false; break; }
                 tc::fence_after();
                 float v[4][kHalf];
@@ -403,32 +394,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_emat_kernel(const __grid_const
                 float o[4][kHalf];
 #pragma unroll
                 for (int p = 0; p < kHalf; ++p) {
-                    const int l = k * kNPT + h * kHalf + p;
-                    float G[6] = {0, 0, 0, 0, 0, 0}, wJ = 0.f;
-                    if (AFFINE) {
-                        if (valid && l < a.NQ) {
-                            const float* T = a.tpts + (size_t)l * 10;   // d eta/d xi (3x3) and weight
-                            const float wl = T[9];
-                            wJ = wl * detJ;
-                            if (a.c1 > 1) {
-                                const float Km[3][3] = {{K6[0], K6[1], K6[2]}, {K6[1], K6[3], K6[4]}, {K6[2], K6[4], K6[5]}};
-                                float M[3][3];
+                    // padded points and elements hold zeros in the tile-major layout
+                    float G[6];
 #pragma unroll
-                                for (int d = 0; d < 3; ++d)
-#pragma unroll
-                                    for (int j = 0; j < 3; ++j)
-                                        M[d][j] = T[3 * d] * Km[0][j] + T[3 * d + 1] * Km[1][j] + T[3 * d + 2] * Km[2][j];
-                                auto gg = [&](int d, int d2) {
-                                    return wl * (M[d][0] * T[3 * d2] + M[d][1] * T[3 * d2 + 1] + M[d][2] * T[3 * d2 + 2]);
-                                };
-                                G[0] = gg(0, 0); G[1] = gg(0, 1); G[2] = gg(0, 2); G[3] = gg(1, 1); G[4] = gg(1, 2); G[5] = gg(2, 2);
-                            }
-                        }
-                    } else {   // padded points and elements hold zeros in this layout
-#pragma unroll
-                        for (int f = 0; f < 6; ++f) G[f] = Gc[f][p];
-                        wJ = Gc[6][p];
-                    }
+                    for (int f = 0; f < 6; ++f) G[f] = Gc[f][p];
+                    const float wJ = Gc[6][p];
                     const float v1 = v[1][p], v2 = v[2][p], v3 = v[3][p];
                     o[0][p] = (a.op == HP_MASS ? 1.f : a.lambda) * wJ * v[0][p];
                     o[1][p] = G[0] * v1 + G[1] * v2 + G[2] * v3;
@@ -504,6 +474,42 @@ __global__ void tc_geom_kernel(const double* g, float* out, int64_t n_elem, int 
     }
 }
 
+// Affine elements: the factors at every point from the element record [16]
+// (|J| J^-1 J^-T, |J|, J^-1) and d eta / d xi at the point, in FP64, stored in
+// the same tile-major FP32 layout as the curved factors.
+template <int SHAPE>
+__global__ void tc_geom_affine_kernel(const double* rec, const double* z, const double* w, int Q, float* out,
+                                      int64_t n_elem, int nch) {
+    const int NQ = Q * Q * Q, QQ = Q * Q;
+    const int64_t ntiles = (n_elem + 127) / 128;
+    const int64_t total = ntiles * nch * kNPT * 128;          // one thread per (tile, chunk, element, point)
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int p = (int)(i % kNPT);
+        int64_t t = i / kNPT;
+        const int r = (int)(t & 127);
+        t >>= 7;
+        const int k = (int)(t % nch);
+        const int64_t tile = t / nch, e = tile * 128 + r;
+        const int l = k * kNPT + p;
+        double G[7] = {0, 0, 0, 0, 0, 0, 0};
+        if (e < n_elem && l < NQ) {
+            const int ii = l / QQ, jj = (l / Q) % Q, kk = l % Q;
+            double Tm[3][3];
+            deta_dxi<SHAPE, double>(z[ii], z[Q + jj], z[2 * Q + kk], Tm);
+            const double wl = w[ii] * w[Q + jj] * w[2 * Q + kk];
+            const double* R = rec + e * 16;
+            const double Km[3][3] = {{R[0], R[1], R[2]}, {R[1], R[3], R[4]}, {R[2], R[4], R[5]}};
+            double M[3][3];
+            for (int d = 0; d < 3; ++d)
+                for (int j = 0; j < 3; ++j) M[d][j] = Tm[d][0] * Km[0][j] + Tm[d][1] * Km[1][j] + Tm[d][2] * Km[2][j];
+            auto gg = [&](int d, int d2) { return wl * (M[d][0] * Tm[d2][0] + M[d][1] * Tm[d2][1] + M[d][2] * Tm[d2][2]); };
+            G[0] = gg(0, 0); G[1] = gg(0, 1); G[2] = gg(0, 2); G[3] = gg(1, 1); G[4] = gg(1, 2); G[5] = gg(2, 2);
+            G[6] = wl * R[6];
+        }
+        for (int f = 0; f < 7; ++f) out[(((tile * nch + k) * 7 + f) * 128 + r) * (int64_t)kNPT + p] = (float)G[f];
+    }
+}
+
 }  // namespace
 
 int tc_stages(int KP, int stage_bytes, int es) {
@@ -527,7 +533,18 @@ cudaError_t tc_geom_layout(const double* g, float* out, int64_t n_elem, int NQ, 
     return cudaGetLastError();
 }
 
-cudaError_t tc_emat_launch(bool affine, const TCArgs& a, cudaStream_t s) {
+cudaError_t tc_geom_layout_affine(int shape, const double* rec, const double* z, const double* w, int Q, float* out,
+                                  int64_t n_elem, int nch, cudaStream_t s) {
+    switch (shape) {
+        case HP_HEX: tc_geom_affine_kernel<HP_HEX><<<1024, 256, 0, s>>>(rec, z, w, Q, out, n_elem, nch); break;
+        case HP_PRISM: tc_geom_affine_kernel<HP_PRISM><<<1024, 256, 0, s>>>(rec, z, w, Q, out, n_elem, nch); break;
+        case HP_PYR: tc_geom_affine_kernel<HP_PYR><<<1024, 256, 0, s>>>(rec, z, w, Q, out, n_elem, nch); break;
+        default: tc_geom_affine_kernel<HP_TET><<<1024, 256, 0, s>>>(rec, z, w, Q, out, n_elem, nch); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t tc_emat_launch(const TCArgs& a, cudaStream_t s) {
     const int64_t ntiles = (a.n_elem + 127) / 128;
     if (ntiles <= 0) return cudaSuccess;
     TCArgs b = a;
@@ -535,8 +552,7 @@ cudaError_t tc_emat_launch(bool affine, const TCArgs& a, cudaStream_t s) {
     // BF16 holds a chunk's stage until its backward MMAs, kFwdBufs - 1 chunks later
     if (b.stages < (a.es == 2 ? kFwdBufs + 1 : 2)) return cudaErrorInvalidValue;
     const int smem = tc_smem_bytes(a.KP, a.stage_bytes, a.es);
-    auto kern = a.es == 2 ? (affine ? tc_emat_kernel<true, 2> : tc_emat_kernel<false, 2>)
-                          : (affine ? tc_emat_kernel<true, 4> : tc_emat_kernel<false, 4>);
+    auto kern = a.es == 2 ? tc_emat_kernel<2> : tc_emat_kernel<4>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0;
