@@ -68,7 +68,9 @@ void free_block(Block& b) {
     cudaFree(b.d_geom32);
     cudaFree(b.d_dgeom32);
     cudaFree(b.d_geom_tc);
+    cudaFree(b.d_gscale_tc);
     b.d_geom_tc = nullptr;
+    b.d_gscale_tc = nullptr;
     b.d_coeff_off = b.d_phys_off = nullptr;
     b.d_frame = b.d_geom = b.d_dgeom = nullptr;
     b.d_geom32 = b.d_dgeom32 = nullptr;
@@ -267,22 +269,18 @@ hp_status ensure_tc(hp_mesh m, int es) {
         }
         db.tc_NPpad = NPpad; db.tc_nch = nch;
     }
-    // FP32 metric factors at every point in the tile-major order the epilogue
-    // reads: copied from the curved factors, expanded from the affine records
+    // FP16 metric factors (scaled per element) at every point in the tile-major
+    // order the epilogue reads: from the curved factors or the affine records
     for (Block& b : m->blocks) {
         if (b.d_geom_tc || n_modes(b.shape, b.P) > kTcMaxModes) continue;
         const DeviceBlobs& db = m->blobs.at(b.shape * 16 + b.P);
-        const int64_t n = tc_geom_floats(b.n_elem, db.tc_nch);
-        hp_status st = upload<float>(&b.d_geom_tc, nullptr, (size_t)n);
+        hp_status st = upload<uint16_t>(&b.d_geom_tc, nullptr, (size_t)tc_geom_halves(b.n_elem, db.tc_nch));
+        if (!st) st = upload<float>(&b.d_gscale_tc, nullptr, (size_t)((b.n_elem + 127) / 128 * 128));
         if (st) return st;
-        cudaError_t e;
-        if (b.curved) {
-            e = tc_geom_layout(b.d_geom, b.d_geom_tc, b.n_elem, b.Q * b.Q * b.Q, nqp(b.Q), db.tc_nch, 0);
-        } else {
-            const BlobLayout L = blob_layout_c(b.shape, b.P, 8);
-            const double* v64 = static_cast<const double*>(db.d64);
-            e = tc_geom_layout_affine(b.shape, b.d_geom, v64 + L.z, v64 + L.w, b.Q, b.d_geom_tc, b.n_elem, db.tc_nch, 0);
-        }
+        const BlobLayout L = blob_layout_c(b.shape, b.P, 8);
+        const double* v64 = static_cast<const double*>(db.d64);
+        cudaError_t e = tc_geom_layout16(b.shape, b.curved != 0, b.d_geom, nqp(b.Q), v64 + L.z, v64 + L.w, b.Q,
+                                         b.d_geom_tc, b.d_gscale_tc, b.n_elem, db.tc_nch, 0);
         if (e == cudaSuccess) e = cudaStreamSynchronize(0);
         if (e != cudaSuccess) return cuda_fail(e, "tensor-core geometry layout");
     }
@@ -394,7 +392,8 @@ cudaError_t launch_block(hp_op op, size_t bi, int tile, double lambda, const voi
         a.c1 = op->kind == HP_MASS ? 1 : 4;
         a.n_elem = b.n_elem; a.lambda = (float)lambda; a.coeff_off = b.d_coeff_off;
         a.in = static_cast<const float*>(in); a.out = static_cast<float*>(out);
-        a.geom = b.d_geom_tc;
+        a.geom16 = b.d_geom_tc;
+        a.gscale = b.d_gscale_tc;
         a.img = bf ? blob.tc_img16 : blob.tc_img;
         a.chunk_bytes = bf ? blob.tc_chunk16 : blob.tc_chunk;
         a.fwd_bytes = bf ? blob.tc_fwd16 : blob.tc_fwd;

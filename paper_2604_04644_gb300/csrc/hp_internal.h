@@ -60,7 +60,8 @@ struct Block {
     double* d_dgeom = nullptr;            // curved only: [n_elem][9][NQp] d eta_d / d x_i
     float* d_geom32 = nullptr;            // FP32 copies (created on demand)
     float* d_dgeom32 = nullptr;
-    float* d_geom_tc = nullptr;           // tensor-core operator: tile-major FP32 factors (curved and affine)
+    uint16_t* d_geom_tc = nullptr;        // tensor-core operator: tile-major FP16 factors (curved and affine)
+    float* d_gscale_tc = nullptr;         // and their per-element scales 2^-k_e
     int64_t coeff_total = 0, phys_total = 0;   // per-block totals (work accounting)
 };
 
@@ -185,21 +186,21 @@ struct TCArgs {
     const int64_t* coeff_off;
     const float* in;
     float* out;
-    const float* geom;                 // tile-major FP32 factors (tc_geom_layout / tc_geom_layout_affine)
+    const uint16_t* geom16;            // tile-major FP16 factors, scaled per element (tc_geom_layout16)
+    const float* gscale;               // [tiles x 128] 2^-k_e: undoes element e's scale
     const unsigned char* img;          // per chunk of points: 4 forward then 4 backward tiles
     int64_t chunk_bytes;
     int fwd_bytes, bwd_bytes, stage_bytes;
     int es;                            // operand bytes: 4 TF32, 2 BF16
-    int nsplit, stages;                // set by the launcher
+    int nsplit, stages, ubufs;         // set by the launcher
     unsigned int* err;
 };
 constexpr int kTcMaxModes = 256;
 int tc_smem_bytes(int KP, int stage_bytes, int es);
 int tc_chunk_points();
-int64_t tc_geom_floats(int64_t n_elem, int nch);
-cudaError_t tc_geom_layout(const double* g, float* out, int64_t n_elem, int NQ, int NQp, int nch, cudaStream_t s);
-cudaError_t tc_geom_layout_affine(int shape, const double* rec, const double* z, const double* w, int Q, float* out,
-                                  int64_t n_elem, int nch, cudaStream_t s);
+int64_t tc_geom_halves(int64_t n_elem, int nch);
+cudaError_t tc_geom_layout16(int shape, bool curved, const double* g, int NQp, const double* z, const double* w, int Q,
+                             uint16_t* out, float* isc, int64_t n_elem, int nch, cudaStream_t s);
 cudaError_t tc_emat_launch(const TCArgs& a, cudaStream_t s);
 cudaError_t emat_launch_f32(bool hybrid, bool affine, const EMArgs<float>& a, cudaStream_t s);
 

@@ -30,6 +30,8 @@
 // bounded; a timeout latches DERR_TIMEOUT, stops every role, drains the
 // copies and MMAs in flight and frees the tensor memory before the CTA exits.
 #include <cuda_bf16.h>
+#include <type_traits>
+#include <cuda_fp16.h>
 
 #include "hp_tc.cuh"
 
@@ -70,6 +72,11 @@ struct Op {
         if constexpr (ES == 4) return tc::sw64_offset(r, p);
         else return r * 32 + ((((p * 2) >> 4) ^ ((r >> 2) & 1)) << 4);
     }
+    // one operand element
+    __device__ static void put(unsigned char* p, float x) {
+        if constexpr (ES == 4) *reinterpret_cast<float*>(p) = tc::to_tf32(x);
+        else *reinterpret_cast<__nv_bfloat16*>(p) = __float2bfloat16_rn(x);
+    }
     // 16 bytes of operands from 16 / ES floats
     __device__ static uint4 pack(const float* x) {
         uint4 u;
@@ -89,9 +96,18 @@ struct Op {
     }
 };
 
+// position in a ring of n buffers and the parity of its current pass
+struct Ring {
+    uint32_t n, i = 0, ph = 0;
+    __device__ void next() {
+        if (++i == n) { i = 0; ph ^= 1u; }
+    }
+};
+
 struct Bars {
     uint64_t full[kMaxStages], empty[kMaxStages];
-    uint64_t u_full, fwd_full[kFwdBufs], fwd_empty[kFwdBufs], vp_full[2], vp_empty[2], out_full, out_empty, drain;
+    uint64_t epi;                      // the eight epilogue warps among themselves
+    uint64_t u_full[2], fwd_full[kFwdBufs], fwd_empty[kFwdBufs], vp_full[2], vp_empty[2], out_full, out_empty, drain;
     uint32_t tmem;
     int abort;
 };
@@ -99,6 +115,7 @@ struct Bars {
 // wait for `parity` of `bar`, giving up when another role aborted or after the
 // time limit (then this role aborts every role)
 __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, Bars* B, unsigned int* err) {
+    if (mbar_try_wait(bar, parity)) return true;        // the common case reads no timer
     const uint64_t t0 = global_ns();
     while (!mbar_try_wait(bar, parity)) {
         if (*reinterpret_cast<volatile int*>(&B->abort)) return false;
@@ -119,6 +136,7 @@ __device__ __forceinline__ void arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
+
 template <int ES>
 __global__ void __launch_bounds__(kThreads, 1) tc_emat_kernel(const __grid_constant__ TCArgs a) {
     using O = Op<ES>;
@@ -126,8 +144,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_emat_kernel(const __grid_const
     // the swizzle patterns are taken from shared-memory address bits: align to 1 KB
     unsigned char* smem = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
     Bars* B = reinterpret_cast<Bars*>(smem);
-    unsigned char* sU = smem + 1024;                                   // KP/32 blocks [128 x 32] tf32, 128 B swizzle
-    unsigned char* sV = sU + 128 * a.KP * ES;                          // [2][4][128 x 16], 64 / 32 B swizzle
+    unsigned char* sU = smem + 1024;                                   // [ubufs][KP / KR][128 x 128 B], 128 B swizzle
+    unsigned char* sV = sU + a.ubufs * 128 * a.KP * ES;                // [2][4][128 x 16], 64 / 32 B swizzle
     unsigned char* sR = sV + 8 * O::VBYTES;                            // ring
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nst = a.stages;
@@ -142,7 +160,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_emat_kernel(const __grid_const
 
     if (tid == 0) {
         for (int s = 0; s < nst; ++s) { mbar_init(&B->full[s], 1); mbar_init(&B->empty[s], 1); }
-        mbar_init(&B->u_full, kEpi);
+        for (int j = 0; j < 2; ++j) mbar_init(&B->u_full[j], kEpi);
         for (int b = 0; b < kFwdBufs; ++b) {
             mbar_init(&B->fwd_full[b], 1);
             mbar_init(&B->fwd_empty[b], kEpi);
@@ -154,6 +172,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_emat_kernel(const __grid_const
         mbar_init(&B->out_full, 1);
         mbar_init(&B->out_empty, kEpi);
         mbar_init(&B->drain, 1);
+        mbar_init(&B->epi, kEpi);
         B->abort = 0;
     }
     if (warp == 0) { tc::tmem_alloc(&B->tmem, kTmemCols); tc::tmem_relinquish(); }
@@ -213,111 +232,100 @@ __global__ void __launch_bounds__(kThreads, 1) tc_emat_kernel(const __grid_const
         if (lane == 0) {
             const uint32_t id_f = tc::instr_desc(O::FMT, 128, kNPT * (a.c1 - a.c0));
             const uint32_t id_b = tc::instr_desc(O::FMT, 128, a.NPpad);
-            int slot = 0;
-            uint32_t pass = 0, nout = 0, ntile = 0, g0 = 0;   // g: chunks processed by this CTA
+            const uint32_t id_bt = id_b | (1u << 16);                     // B operand MN-major
+            // descriptors are built once: an operand x bytes past a base adds x / 16
+            // to the start-address field (shared addresses stay below 256 KB, so
+            // the 14-bit field never carries)
+            const uint64_t dU = tc::smem_desc_sw(smem_addr(sU), 1024, tc::kSw128);
+            const uint64_t dF = tc::smem_desc_sw(smem_addr(sR) + a.c0 * 2 * 1024, 1024, tc::kSw128);
+            const uint64_t dV = tc::smem_desc_sw(smem_addr(sV), 8 * O::VROW, O::VSW);
+            // BF16 backward: the chunk's stage read MN-major (N = modes: 64-mode atoms
+            // one slice apart, LBO; K = the component's 16 points, 8-point groups 1 KB
+            // apart, SBO); TF32 backward: streamed K-major tiles
+            const uint64_t dRt = tc::smem_desc_sw_lbo(smem_addr(sR), kSliceBytes, 1024, tc::kSw128);
+            const uint64_t dRb = tc::smem_desc_sw(smem_addr(sR), 8 * O::VROW, O::VSW);
+            const uint32_t nsl = (uint32_t)((a.KP + O::KR - 1) / O::KR);
+            const uint32_t st16 = (uint32_t)a.stage_bytes >> 4, u16 = (uint32_t)(128 * a.KP * ES) >> 4;
+            constexpr uint32_t v16 = O::VBYTES >> 4, sl16 = kSliceBytes >> 4;
+            // fb: forward accumulators, vb: V' tiles, fs / bs: ring stages taken by
+            // the forward / released by the backward (BF16), ub: U buffers
+            Ring fb{kFwdBufs}, vb{2}, fs{(uint32_t)nst}, bs{(uint32_t)nst}, ub{(uint32_t)a.ubufs};
+            uint32_t nout = 0;
             bool ok = true;
-            for (int64_t w = blockIdx.x; w < nwork && ok; w += gridDim.x, ++ntile) {
+            for (int64_t w = blockIdx.x; w < nwork && ok; w += gridDim.x) {
                 int kb, ke;
                 chunk_range(w, kb, ke);
-                if (!wait_bar(&B->u_full, ntile & 1u, B, a.err)) { ok = false; break; }
-                if constexpr (ES == 2) {
-                    // one ring stage per chunk: forward MMAs read its slices K-major;
-                    // kFwdBufs - 1 chunks later the backward MMAs read the same stage
-                    // MN-major (N = modes: 64-mode atoms one slice apart; K = the
-                    // component's 16 points) and release it
-                    const uint32_t id_bt = id_b | (1u << 16);                     // B operand MN-major
-                    for (int t = kb; t < ke + kFwdBufs - 1 && ok; ++t) {
-                        if (t < ke) {
-                            const uint32_t g = g0 + (uint32_t)(t - kb), b = g % kFwdBufs, use = g / kFwdBufs;
-                            const uint32_t st = g % nst, par = (g / nst) & 1u;
-                            if (!wait_bar(&B->fwd_empty[b], (use & 1u) ^ 1u, B, a.err)) { ok = false; break; }
-                            if (!wait_bar(&B->full[st], par, B, a.err)) { ok = false; break; }
-                            tc::fence_after();
-                            const uint32_t d = tbase + (uint32_t)((b * 4 + a.c0) * kNPT);
-                            const uint32_t stage = smem_addr(sR + (size_t)st * a.stage_bytes);
-                            for (int sl = 0; sl * O::KR < a.KP; ++sl) {
-                                const uint32_t sa = smem_addr(sU) + sl * 128 * 128;
-                                const uint32_t sb = stage + sl * kSliceBytes + a.c0 * 2 * 1024;
-                                for (int s = 0; s < 4; ++s)
-                                    O::mma(d, tc::smem_desc_sw(sa + s * 32, 1024, tc::kSw128),
-                                           tc::smem_desc_sw(sb + s * 32, 1024, tc::kSw128), id_f, sl > 0 || s > 0);
-                            }
-                            tc::commit(&B->fwd_full[b]);
-                        }
-                        const int k = t - (kFwdBufs - 1);
-                        if (k >= kb && ok) {
-                            const uint32_t g = g0 + (uint32_t)(k - kb), b = g & 1u, use = g >> 1;
-                            const uint32_t st = g % nst;
-                            if (!wait_bar(&B->vp_full[b], use & 1u, B, a.err)) { ok = false; break; }
-                            if (k == kb) {
-                                if (!wait_bar(&B->out_empty, (nout & 1u) ^ 1u, B, a.err)) { ok = false; break; }
-                                ++nout;
-                            }
-                            tc::fence_after();
-                            const uint32_t stage = smem_addr(sR + (size_t)st * a.stage_bytes);
-                            for (int c = a.c0; c < a.c1; ++c) {
-                                const uint32_t sa = smem_addr(sV + (size_t)(b * 4 + c) * O::VBYTES);
-                                // LBO: next 64-mode atom (next slice); SBO: next 8 points
-                                const uint64_t db = tc::smem_desc_sw_lbo(stage + c * 2 * 1024, kSliceBytes, 1024, tc::kSw128);
-                                O::mma(tbase + kOutCol, tc::smem_desc_sw(sa, 8 * O::VROW, O::VSW), db, id_bt,
-                                       !(k == kb && c == a.c0));
-                            }
-                            tc::commit(&B->empty[st]);
-                            tc::commit(&B->vp_empty[b]);
-                        }
-                    }
-                    if (ok) tc::commit(&B->out_full);
-                    g0 += (uint32_t)(ke - kb);
-                    continue;
-                }
+                if (!wait_bar(&B->u_full[ub.i], ub.ph, B, a.err)) { ok = false; break; }
+                const uint64_t dUw = dU + ub.i * u16;
+                ub.next();
+                // forward of chunk t, then backward of chunk t - (kFwdBufs - 1)
                 for (int t = kb; t < ke + kFwdBufs - 1 && ok; ++t) {
                     if (t < ke) {
-                        const int k = t;
-                        const uint32_t g = g0 + (uint32_t)(k - kb), b = g % kFwdBufs, use = g / kFwdBufs;
-                        if (!wait_bar(&B->fwd_empty[b], (use & 1u) ^ 1u, B, a.err)) { ok = false; break; }
-                        tc::fence_after();
-                        // columns (b*4 + c0)*16 .. of the accumulator = components c0..c1-1
-                        const uint32_t d = tbase + (uint32_t)((b * 4 + a.c0) * kNPT);
-                        for (int sl = 0; sl * O::KR < a.KP && ok; ++sl) {
-                            if (!wait_bar(&B->full[slot], pass, B, a.err)) { ok = false; break; }
+                        if (!wait_bar(&B->fwd_empty[fb.i], fb.ph ^ 1u, B, a.err)) { ok = false; break; }
+                        // columns (fb*4 + c0)*16 .. of the accumulator = components c0..c1-1
+                        const uint32_t d = tbase + (fb.i * 4 + (uint32_t)a.c0) * kNPT;
+                        if constexpr (ES == 2) {
+                            // one ring stage per chunk holding every K slice
+                            if (!wait_bar(&B->full[fs.i], fs.ph, B, a.err)) { ok = false; break; }
                             tc::fence_after();
-                            // K block sl of U (128 rows x 128 B) and rows 16 c0.. of the slice
-                            const uint32_t sa = smem_addr(sU) + sl * 128 * 128;
-                            const uint32_t sb = smem_addr(sR + (size_t)slot * a.stage_bytes) + a.c0 * 2 * 1024;
-                            for (int s = 0; s < 4; ++s)
-                                O::mma(d, tc::smem_desc_sw(sa + s * 32, 1024, tc::kSw128),
-                                       tc::smem_desc_sw(sb + s * 32, 1024, tc::kSw128), id_f, sl > 0 || s > 0);
-                            tc::commit(&B->empty[slot]);
-                            if (++slot == nst) { slot = 0; pass ^= 1u; }
+                            const uint64_t dFs = dF + fs.i * st16;
+                            for (uint32_t sl = 0; sl < nsl; ++sl)
+#pragma unroll
+                                for (uint32_t s = 0; s < 4; ++s)
+                                    O::mma(d, dUw + (sl * 1024 + s * 2), dFs + (sl * sl16 + s * 2), id_f, sl > 0 || s > 0);
+                            fs.next();
+                        } else {
+                            // one ring stage per K slice, released as soon as it is read
+                            for (uint32_t sl = 0; sl < nsl && ok; ++sl) {
+                                if (!wait_bar(&B->full[fs.i], fs.ph, B, a.err)) { ok = false; break; }
+                                tc::fence_after();
+                                const uint64_t dFs = dF + fs.i * st16;
+#pragma unroll
+                                for (uint32_t s = 0; s < 4; ++s)
+                                    O::mma(d, dUw + (sl * 1024 + s * 2), dFs + s * 2, id_f, sl > 0 || s > 0);
+                                tc::commit(&B->empty[fs.i]);
+                                fs.next();
+                            }
+                            if (!ok) break;
                         }
-                        tc::commit(&B->fwd_full[b]);
+                        tc::commit(&B->fwd_full[fb.i]);
+                        fb.next();
                     }
-                    const int k = t - (kFwdBufs - 1);          // backward of chunk k
-                    if (k >= kb && ok) {
-                        const uint32_t g = g0 + (uint32_t)(k - kb), b = g & 1u, use = g >> 1;
-                        if (!wait_bar(&B->vp_full[b], use & 1u, B, a.err)) { ok = false; break; }
+                    const int k = t - (kFwdBufs - 1);
+                    if (k >= kb) {
+                        if (!wait_bar(&B->vp_full[vb.i], vb.ph, B, a.err)) { ok = false; break; }
                         if (k == kb) {
                             if (!wait_bar(&B->out_empty, (nout & 1u) ^ 1u, B, a.err)) { ok = false; break; }
                             ++nout;
                         }
                         tc::fence_after();
-                        for (int c = a.c0; c < a.c1 && ok; ++c) {
-                            if (!wait_bar(&B->full[slot], pass, B, a.err)) { ok = false; break; }
-                            tc::fence_after();
-                            const uint32_t sa = smem_addr(sV + (size_t)(b * 4 + c) * O::VBYTES);
-                            const uint32_t sb = smem_addr(sR + (size_t)slot * a.stage_bytes);
-                            for (int s = 0; s < O::VROW / 32; ++s)
-                                O::mma(tbase + kOutCol, tc::smem_desc_sw(sa + s * 32, 8 * O::VROW, O::VSW),
-                                       tc::smem_desc_sw(sb + s * 32, 8 * O::VROW, O::VSW), id_b,
-                                       !(k == kb && c == a.c0 && s == 0));
-                            tc::commit(&B->empty[slot]);
-                            if (++slot == nst) { slot = 0; pass ^= 1u; }
+                        const uint64_t dVb = dV + vb.i * 4 * v16;
+                        if constexpr (ES == 2) {
+                            const uint64_t dRs = dRt + bs.i * st16;
+                            for (int c = a.c0; c < a.c1; ++c)
+                                O::mma(tbase + kOutCol, dVb + (uint32_t)c * v16, dRs + (uint32_t)c * 128, id_bt,
+                                       !(k == kb && c == a.c0));
+                            tc::commit(&B->empty[bs.i]);
+                            bs.next();
+                        } else {
+                            for (int c = a.c0; c < a.c1 && ok; ++c) {
+                                if (!wait_bar(&B->full[fs.i], fs.ph, B, a.err)) { ok = false; break; }
+                                tc::fence_after();
+                                const uint64_t dRs = dRb + fs.i * st16;
+#pragma unroll
+                                for (uint32_t s = 0; s < O::VROW / 32; ++s)
+                                    O::mma(tbase + kOutCol, dVb + (uint32_t)c * v16 + s * 2, dRs + s * 2, id_b,
+                                           !(k == kb && c == a.c0 && s == 0));
+                                tc::commit(&B->empty[fs.i]);
+                                fs.next();
+                            }
+                            if (!ok) break;
                         }
-                        tc::commit(&B->vp_empty[b]);
+                        tc::commit(&B->vp_empty[vb.i]);
+                        vb.next();
                     }
                 }
                 if (ok) tc::commit(&B->out_full);
-                g0 += (uint32_t)(ke - kb);
             }
             // every MMA issued by this thread has completed before the CTA leaves
             tc::commit(&B->drain);
@@ -330,83 +338,110 @@ __global__ void __launch_bounds__(kThreads, 1) tc_emat_kernel(const __grid_const
         const int q = warp & 3, h = warp >> 2;
         const int r = q * 32 + lane;            // element row of the tile = TMEM lane
         const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+        constexpr uint32_t kAll = 0xffffffffu;
+        // coefficient offsets of rows 16 warp .. 16 warp + 15 of work item wi's
+        // tile: lane i < 16 holds row 16 warp + i's (-1 past the last element)
+        auto row_offsets = [&](int64_t wi) -> int64_t {
+            const int64_t e = (wi / a.nsplit) * 128 + warp * 16 + lane;
+            return (lane < 16 && e < a.n_elem) ? a.coeff_off[e] : (int64_t)-1;
+        };
+        // U of a tile into buffer j, coalesced: each warp copies the coefficient
+        // rows of its 16 elements (offsets `offs`, lanes along the modes; RB rows
+        // of up to 32 JJ modes with all their loads in flight at a time), rounded
+        // to the operand type and zero padded to KP
+        auto gather_rows = [&](auto RBc, auto JJc, unsigned char* dU, int64_t offs) {
+            constexpr int RB = decltype(RBc)::value, JJ = decltype(JJc)::value;
+            for (int i0 = 0; i0 < 16; i0 += RB) {
+                float x[RB][JJ];
+#pragma unroll
+                for (int ii = 0; ii < RB; ++ii) {
+                    const int64_t off = __shfl_sync(kAll, offs, i0 + ii);
+#pragma unroll
+                    for (int jj = 0; jj < JJ; ++jj) {
+                        const int m = lane + 32 * jj;
+                        x[ii][jj] = (off >= 0 && m < a.NP) ? __ldg(a.in + off + m) : 0.f;
+                    }
+                }
+#pragma unroll
+                for (int ii = 0; ii < RB; ++ii) {
+                    const int row = warp * 16 + i0 + ii;
+#pragma unroll
+                    for (int jj = 0; jj < JJ; ++jj) {
+                        const int m = lane + 32 * jj;
+                        if (32 * jj < a.KP) O::put(dU + (m / O::KR) * 128 * 128 + O::off128(row, m % O::KR), x[ii][jj]);
+                    }
+                }
+            }
+        };
+        auto gather_u = [&](int j, int64_t offs) {
+            unsigned char* dU = sU + (size_t)j * 128 * a.KP * ES;
+            if (a.KP <= 128) gather_rows(std::integral_constant<int, 8>{}, std::integral_constant<int, 4>{}, dU, offs);
+            else gather_rows(std::integral_constant<int, 4>{}, std::integral_constant<int, kTcMaxModes / 32>{}, dU, offs);
+            tc::fence_async_smem();
+            arrive(&B->u_full[j]);
+        };
+        // barrier of the epilogue warps alone, bounded like every other wait (a
+        // warp that left after a timeout never arrives; the others see the abort)
+        uint32_t nepi = 0;
+        auto epi_sync = [&]() -> bool {
+            arrive(&B->epi);
+            return wait_warp(&B->epi, (nepi++) & 1u, B, a.err);
+        };
+        const float lam = a.op == HP_MASS ? 1.f : a.lambda;
         uint32_t ntile = 0, g0 = 0;
         bool ok = true;
+        // row offsets of the current work item, and of the next one fetched a tile ahead
+        int64_t offs = blockIdx.x < nwork ? row_offsets(blockIdx.x) : (int64_t)-1;
         for (int64_t w = blockIdx.x; w < nwork && ok; w += gridDim.x, ++ntile) {
             int kb, ke;
             chunk_range(w, kb, ke);
-            const int64_t tile = w / a.nsplit, e = tile * 128 + r;
-            const bool valid = e < a.n_elem;
-            // U row r (this thread: half h of it): coefficients, TF32, zero padded to KP
-            {
-                const float* src = valid ? a.in + a.coeff_off[e] : nullptr;
-                const int half = a.KP / 2;
-                constexpr int KC = 16 / ES;                   // modes per 16-byte chunk
-                for (int m0 = h * half; m0 < (h + 1) * half; m0 += KC) {
-                    float x[KC];
-#pragma unroll
-                    for (int i = 0; i < KC; ++i) x[i] = (valid && m0 + i < a.NP) ? src[m0 + i] : 0.f;
-                    *reinterpret_cast<uint4*>(sU + (m0 / O::KR) * 128 * 128 + O::off128(r, m0 % O::KR)) = O::pack(x);
-                }
-            }
-            tc::fence_async_smem();
-            arrive(&B->u_full);
-            // metric factors of a chunk: this thread's 8 points of each factor are
-            // 32 contiguous bytes of the tile-major layout; the next chunk's are
-            // fetched while the current one is processed
-            float Gn[7][kHalf], Gc[7][kHalf];
-            auto load_geom = [&](int k) {
-                const float4* gt = reinterpret_cast<const float4*>(
-                    a.geom + (((tile * a.nch + k) * 7) * 128 + r) * (int64_t)kNPT + h * kHalf);
-#pragma unroll
-                for (int f = 0; f < 7; ++f) {
-                    float4 x0 = make_float4(0.f, 0.f, 0.f, 0.f), x1 = x0;
-                    if (f == 6 || a.c1 > 1) {
-                        x0 = __ldg(gt + f * 128 * kNPT / 4);
-                        x1 = __ldg(gt + f * 128 * kNPT / 4 + 1);
-                    }
-                    Gn[f][0] = x0.x; Gn[f][1] = x0.y; Gn[f][2] = x0.z; Gn[f][3] = x0.w;
-                    Gn[f][4] = x1.x; Gn[f][5] = x1.y; Gn[f][6] = x1.z; Gn[f][7] = x1.w;
-                }
-            };
-            if (kb < ke) load_geom(kb);
-            for (int k = kb; k < ke && ok; ++k) {
-                const uint32_t g = g0 + (uint32_t)(k - kb), b = g & 1u, use = g >> 1;
-                const uint32_t bf = g % kFwdBufs, usef = g / kFwdBufs;     // forward accumulator buffer
+            const int64_t tile = w / a.nsplit;
+            const bool more = w + gridDim.x < nwork;
+            const int64_t offs_next = more ? row_offsets(w + gridDim.x) : (int64_t)-1;
+            // one U buffer: gathered once the previous tile's MMAs completed; two:
+            // the next tile's U is gathered while this tile's last MMAs run
+            if (a.ubufs == 1 || ntile == 0) gather_u(0, offs);
+            const float isc = a.gscale[tile * 128 + r];     // 2^-k of element r's FP16 factors (0: padding)
+            const uint4* gt = reinterpret_cast<const uint4*>(a.geom16) + (tile * a.nch * 14 + h) * 128 + r;
+            // the seven factors of chunk k at this thread's 8 points: 16 bytes each
+            auto load_geom = [&](int k, uint4 (&G)[7]) {
 #pragma unroll
                 for (int f = 0; f < 7; ++f)
-#pragma unroll
-                    for (int p = 0; p < kHalf; ++p) Gc[f][p] = Gn[f][p];
-                if (k + 1 < ke) load_geom(k + 1);
-                if (!wait_warp(&B->fwd_full[bf], usef & 1u, B, a.err)) { ok = false; break; }
+                    G[f] = (f == 6 || a.c1 > 1) ? __ldg(gt + ((int64_t)k * 7 + f) * 256) : make_uint4(0u, 0u, 0u, 0u);
+            };
+            // metric of chunk k: forward accumulator -> V' tile (components
+            // outside [c0, c1) are computed from unused columns and discarded)
+            auto process = [&](int k, const uint4 (&Gh)[7]) -> bool {
+                const uint32_t g = g0 + (uint32_t)(k - kb), b = g & 1u, use = g >> 1;
+                const uint32_t bf = g % kFwdBufs, usef = g / kFwdBufs;     // forward accumulator buffer
+                if (!wait_warp(&B->fwd_full[bf], usef & 1u, B, a.err)) return false;
                 tc::fence_after();
                 float v[4][kHalf];
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    if (c >= a.c0 && c < a.c1) tc::ld_32x8(tbase + lane_base + (uint32_t)((bf * 4 + c) * kNPT + h * kHalf), v[c]);
-                    else {
-#pragma unroll
-                        for (int p = 0; p < kHalf; ++p) v[c][p] = 0.f;
-                    }
-                }
+                tc::ld_32x8_x4(tbase + lane_base + (uint32_t)(bf * 4 * kNPT + h * kHalf), kNPT, v);
                 tc::fence_before();
                 arrive(&B->fwd_empty[bf]);
                 float o[4][kHalf];
 #pragma unroll
-                for (int p = 0; p < kHalf; ++p) {
-                    // padded points and elements hold zeros in the tile-major layout
-                    float G[6];
+                for (int p2 = 0; p2 < kHalf / 2; ++p2) {
+                    float2 G[7];
 #pragma unroll
-                    for (int f = 0; f < 6; ++f) G[f] = Gc[f][p];
-                    const float wJ = Gc[6][p];
-                    const float v1 = v[1][p], v2 = v[2][p], v3 = v[3][p];
-                    o[0][p] = (a.op == HP_MASS ? 1.f : a.lambda) * wJ * v[0][p];
-                    o[1][p] = G[0] * v1 + G[1] * v2 + G[2] * v3;
-                    o[2][p] = G[1] * v1 + G[3] * v2 + G[4] * v3;
-                    o[3][p] = G[2] * v1 + G[4] * v2 + G[5] * v3;
+                    for (int f = 0; f < 7; ++f) {
+                        const uint32_t wd = p2 == 0 ? Gh[f].x : p2 == 1 ? Gh[f].y : p2 == 2 ? Gh[f].z : Gh[f].w;
+                        G[f] = __half22float2(*reinterpret_cast<const __half2*>(&wd));
+                    }
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) {
+                        const int p = 2 * p2 + j;
+                        auto gf = [&](int f) { return j ? G[f].y : G[f].x; };
+                        const float v1 = v[1][p], v2 = v[2][p], v3 = v[3][p];
+                        o[0][p] = lam * isc * gf(6) * v[0][p];
+                        o[1][p] = isc * (gf(0) * v1 + gf(1) * v2 + gf(2) * v3);
+                        o[2][p] = isc * (gf(1) * v1 + gf(3) * v2 + gf(4) * v3);
+                        o[3][p] = isc * (gf(2) * v1 + gf(4) * v2 + gf(5) * v3);
+                    }
                 }
                 // the V' tile b is free once the backward MMAs that last read it completed
-                if (!wait_warp(&B->vp_empty[b], (use & 1u) ^ 1u, B, a.err)) { ok = false; break; }
+                if (!wait_warp(&B->vp_empty[b], (use & 1u) ^ 1u, B, a.err)) return false;
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
                     if (c < a.c0 || c >= a.c1) continue;
@@ -417,28 +452,63 @@ __global__ void __launch_bounds__(kThreads, 1) tc_emat_kernel(const __grid_const
                 }
                 tc::fence_async_smem();
                 arrive(&B->vp_full[b]);
+                return true;
+            };
+            // factors two chunks ahead: three register sets in rotation
+            uint4 ga[7], gb[7], gc[7];
+            if (kb < ke) load_geom(kb, ga);
+            if (kb + 1 < ke) load_geom(kb + 1, gb);
+            for (int k = kb; k < ke; k += 3) {
+                if (k + 2 < ke) load_geom(k + 2, gc);
+                if (!(ok = process(k, ga)) || k + 1 >= ke) break;
+                if (k + 3 < ke) load_geom(k + 3, ga);
+                if (!(ok = process(k + 1, gb)) || k + 2 >= ke) break;
+                if (k + 4 < ke) load_geom(k + 4, gb);
+                if (!(ok = process(k + 2, gc))) break;
             }
             if (!ok) break;
             g0 += (uint32_t)(ke - kb);
-            // outputs: row r of the accumulator = element e, columns = modes (half h of them)
+            if (a.ubufs == 2 && more) gather_u((int)((ntile + 1) & 1u), offs_next);
+            // outputs: row r of the accumulator = element r of the tile, columns =
+            // modes; staged CB columns at a time through the V' tiles (free from
+            // the tile's last backward MMA to the next tile's first V' write) so
+            // that each warp stores whole coefficient rows (coalesced)
             if (!wait_warp(&B->out_full, ntile & 1u, B, a.err)) { ok = false; break; }
             tc::fence_after();
-            float* dst = valid ? a.out + a.coeff_off[e] : nullptr;
-            const int nh = a.NPpad / 2;
-            for (int c0 = h * nh; c0 < (h + 1) * nh; c0 += 8) {
-                float v[8];
-                tc::ld_32x8(tbase + lane_base + (uint32_t)(kOutCol + c0), v);
-                if (valid) {
+            float* stage = reinterpret_cast<float*>(sV);
+            constexpr int CB = 8 * O::VBYTES / (128 * 4);
+            for (int cb = 0; cb < a.NPpad; cb += CB) {
+                // row r, columns h CB/2 .. of the pass; 16-byte chunks XOR-swizzled by row
 #pragma unroll
-                    for (int j = 0; j < 8; ++j)
-                        if (c0 + j < a.NP) {
-                            if (a.nsplit > 1) atomicAdd(dst + c0 + j, v[j]);
-                            else dst[c0 + j] = v[j];
-                        }
+                for (int c = 0; c < CB / 2; c += 16) {
+                    const int cc = h * (CB / 2) + c;
+                    if (cb + cc < a.NPpad) {             // warp-uniform; NPpad is a multiple of 16
+                        float v[16];
+                        tc::ld_32x16(tbase + lane_base + (uint32_t)(kOutCol + cb + cc), v);
+#pragma unroll
+                        for (int i = 0; i < 16; i += 4)
+                            *reinterpret_cast<float4*>(stage + r * CB + ((((cc + i) >> 2) ^ (r & 7)) << 2)) =
+                                make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+                    }
                 }
+                if (!(ok = epi_sync())) break;
+                for (int i = 0; i < 16; ++i) {
+                    const int64_t off = __shfl_sync(kAll, offs, i);
+                    if (off < 0) continue;                  // warp-uniform
+                    const int row = warp * 16 + i;
+                    for (int m = lane; m < CB; m += 32) {
+                        if (cb + m >= a.NP) break;
+                        const float val = stage[row * CB + (((m >> 2) ^ (row & 7)) << 2) + (m & 3)];
+                        if (a.nsplit > 1) atomicAdd(a.out + off + cb + m, val);
+                        else a.out[off + cb + m] = val;
+                    }
+                }
+                if (!(ok = epi_sync())) break;
             }
+            if (!ok) break;
             tc::fence_before();
             arrive(&B->out_empty);
+            offs = offs_next;
         }
     }
     tc::fence_before();
@@ -455,100 +525,132 @@ __global__ void zero_coeffs_kernel(float* out, const int64_t* coeff_off, int64_t
     out[coeff_off[e] + (i - e * NP)] = 0.f;
 }
 
-// FP64 curved geometry [n][7][NQp] -> FP32 tile-major [tile][chunk][7][128 elem][16 pts],
-// zeros at padded points and elements
-__global__ void tc_geom_kernel(const double* g, float* out, int64_t n_elem, int NQ, int NQp, int nch) {
-    const int64_t ntiles = (n_elem + 127) / 128;
-    const int64_t total = ntiles * nch * 7 * kNPT * 128;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-        const int p = (int)(i % kNPT);
-        int64_t t = i / kNPT;
-        const int r = (int)(t & 127);
-        t >>= 7;
-        const int f = (int)(t % 7);
-        t /= 7;
-        const int k = (int)(t % nch);
-        const int64_t tile = t / nch, e = tile * 128 + r;
-        const int l = k * kNPT + p;
-        out[i] = (e < n_elem && l < NQ) ? (float)g[(e * 7 + f) * (int64_t)NQp + l] : 0.f;
+// Metric factors for the tensor-core forms: the seven factors of every point
+// (the six unique entries of G and w|J|) in FP16 with one power-of-two scale
+// per element.  The operands round to 11 (TF32) or 8 (BF16) significant bits,
+// so FP16's 11 keep the factors as accurate as the operands at half the bytes
+// of FP32.  Element e's factors are multiplied by 2^k_e with
+// k_e = 14 - floor(log2 max|G_e|): the largest lies in [2^14, 2^15) (FP16 ends
+// at 65504) and only entries below 2^-28 of it fall into FP16's subnormal
+// range; the epilogue multiplies its outputs by 2^-k_e (exact in FP32).
+// Layout [tile][chunk][7 factors][2 point halves][128 elements][8 points],
+// 16 bytes per (factor, half, element); padded points and elements stay zero
+// (the buffer is cleared first), and so does the scale of a padded element.
+__host__ __device__ constexpr int64_t geom16_index(int64_t tile, int k, int f, int p, int r, int nch) {
+    return ((((tile * nch + k) * 7 + f) * 2 + (p >> 3)) * 128 + r) * 8 + (p & 7);
+}
+
+// factors of element e at point l: curved from the FP64 factors [n][7][NQp];
+// affine from the element record [16] (|J| J^-1 J^-T, |J|, J^-1) and
+// d eta / d xi at the point, in FP64
+template <int SHAPE, bool CURVED>
+__device__ __forceinline__ void point_factors(const double* g, int NQp, const double* z, const double* w, int Q,
+                                              int64_t e, int l, double (&G)[7]) {
+    if constexpr (CURVED) {
+#pragma unroll
+        for (int f = 0; f < 7; ++f) G[f] = g[(e * 7 + f) * (int64_t)NQp + l];
+    } else {
+        const int QQ = Q * Q;
+        const int ii = l / QQ, jj = (l / Q) % Q, kk = l % Q;
+        double Tm[3][3];
+        deta_dxi<SHAPE, double>(z[ii], z[Q + jj], z[2 * Q + kk], Tm);
+        const double wl = w[ii] * w[Q + jj] * w[2 * Q + kk];
+        const double* R = g + e * 16;
+        const double Km[3][3] = {{R[0], R[1], R[2]}, {R[1], R[3], R[4]}, {R[2], R[4], R[5]}};
+        double M[3][3];
+        for (int d = 0; d < 3; ++d)
+            for (int j = 0; j < 3; ++j) M[d][j] = Tm[d][0] * Km[0][j] + Tm[d][1] * Km[1][j] + Tm[d][2] * Km[2][j];
+        auto gg = [&](int d, int d2) { return wl * (M[d][0] * Tm[d2][0] + M[d][1] * Tm[d2][1] + M[d][2] * Tm[d2][2]); };
+        G[0] = gg(0, 0); G[1] = gg(0, 1); G[2] = gg(0, 2); G[3] = gg(1, 1); G[4] = gg(1, 2); G[5] = gg(2, 2);
+        G[6] = wl * R[6];
     }
 }
 
-// Affine elements: the factors at every point from the element record [16]
-// (|J| J^-1 J^-T, |J|, J^-1) and d eta / d xi at the point, in FP64, stored in
-// the same tile-major FP32 layout as the curved factors.
-template <int SHAPE>
-__global__ void tc_geom_affine_kernel(const double* rec, const double* z, const double* w, int Q, float* out,
-                                      int64_t n_elem, int nch) {
-    const int NQ = Q * Q * Q, QQ = Q * Q;
-    const int64_t ntiles = (n_elem + 127) / 128;
-    const int64_t total = ntiles * nch * kNPT * 128;          // one thread per (tile, chunk, element, point)
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-        const int p = (int)(i % kNPT);
-        int64_t t = i / kNPT;
-        const int r = (int)(t & 127);
-        t >>= 7;
-        const int k = (int)(t % nch);
-        const int64_t tile = t / nch, e = tile * 128 + r;
-        const int l = k * kNPT + p;
-        double G[7] = {0, 0, 0, 0, 0, 0, 0};
-        if (e < n_elem && l < NQ) {
-            const int ii = l / QQ, jj = (l / Q) % Q, kk = l % Q;
-            double Tm[3][3];
-            deta_dxi<SHAPE, double>(z[ii], z[Q + jj], z[2 * Q + kk], Tm);
-            const double wl = w[ii] * w[Q + jj] * w[2 * Q + kk];
-            const double* R = rec + e * 16;
-            const double Km[3][3] = {{R[0], R[1], R[2]}, {R[1], R[3], R[4]}, {R[2], R[4], R[5]}};
-            double M[3][3];
-            for (int d = 0; d < 3; ++d)
-                for (int j = 0; j < 3; ++j) M[d][j] = Tm[d][0] * Km[0][j] + Tm[d][1] * Km[1][j] + Tm[d][2] * Km[2][j];
-            auto gg = [&](int d, int d2) { return wl * (M[d][0] * Tm[d2][0] + M[d][1] * Tm[d2][1] + M[d][2] * Tm[d2][2]); };
-            G[0] = gg(0, 0); G[1] = gg(0, 1); G[2] = gg(0, 2); G[3] = gg(1, 1); G[4] = gg(1, 2); G[5] = gg(2, 2);
-            G[6] = wl * R[6];
+// one warp per element: the element's largest factor, then the scaled values
+template <int SHAPE, bool CURVED>
+__global__ void tc_geom16_kernel(const double* g, int NQp, const double* z, const double* w, int Q, uint16_t* out,
+                                 float* isc, int64_t n_elem, int nch) {
+    const int NQ = Q * Q * Q, lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x / 32);
+    for (int64_t e = blockIdx.x * (int64_t)(blockDim.x / 32) + threadIdx.x / 32; e < n_elem; e += nw) {
+        double mx = 0.0;
+        for (int l = lane; l < NQ; l += 32) {
+            double G[7];
+            point_factors<SHAPE, CURVED>(g, NQp, z, w, Q, e, l, G);
+            for (int f = 0; f < 7; ++f) mx = fmax(mx, fabs(G[f]));
         }
-        for (int f = 0; f < 7; ++f) out[(((tile * nch + k) * 7 + f) * 128 + r) * (int64_t)kNPT + p] = (float)G[f];
+        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        const int k = mx > 0.0 ? 14 - ilogb(mx) : 0;
+        const int64_t tile = e >> 7;
+        const int r = (int)(e & 127);
+        for (int l = lane; l < NQ; l += 32) {
+            double G[7];
+            point_factors<SHAPE, CURVED>(g, NQp, z, w, Q, e, l, G);
+            for (int f = 0; f < 7; ++f)
+                out[geom16_index(tile, l / kNPT, f, l % kNPT, r, nch)] =
+                    __half_as_ushort(__float2half_rn((float)ldexp(G[f], k)));
+        }
+        if (lane == 0) isc[e] = (float)ldexp(1.0, -k);
     }
+}
+
+template <int SHAPE>
+cudaError_t geom16_shape(bool curved, const double* g, int NQp, const double* z, const double* w, int Q,
+                         uint16_t* out, float* isc, int64_t n_elem, int nch, cudaStream_t s) {
+    const int64_t blocks = (n_elem + 7) / 8;
+    const unsigned grid = (unsigned)(blocks < 8192 ? blocks : 8192);
+    if (curved) tc_geom16_kernel<SHAPE, true><<<grid, 256, 0, s>>>(g, NQp, z, w, Q, out, isc, n_elem, nch);
+    else tc_geom16_kernel<SHAPE, false><<<grid, 256, 0, s>>>(g, NQp, z, w, Q, out, isc, n_elem, nch);
+    return cudaGetLastError();
 }
 
 }  // namespace
 
-int tc_stages(int KP, int stage_bytes, int es) {
-    const int base = 2048 + 128 * KP * es + 8 * 128 * kNPT * es;      // alignment slack + barriers + U + V'
+// ring stages (2..kMaxStages) that fit beside ubufs U buffers and the V' tiles
+int tc_stages(int KP, int stage_bytes, int es, int ubufs) {
+    const int base = 2048 + ubufs * 128 * KP * es + 8 * 128 * kNPT * es;   // alignment slack + barriers + U + V'
     for (int st = kMaxStages; st >= 2; --st)
         if (base + st * stage_bytes <= 227 * 1024) return st;
     return 0;
 }
 
+// a second U buffer where it leaves a deep ring (or costs no stage)
+int tc_ubufs(int KP, int stage_bytes, int es) {
+    const int s2 = tc_stages(KP, stage_bytes, es, 2);
+    return (s2 >= 6 || s2 == tc_stages(KP, stage_bytes, es, 1)) ? 2 : 1;
+}
+
 int tc_smem_bytes(int KP, int stage_bytes, int es) {
-    int b = 2048 + 128 * KP * es + 8 * 128 * kNPT * es + tc_stages(KP, stage_bytes, es) * stage_bytes;
+    const int ub = tc_ubufs(KP, stage_bytes, es);
+    int b = 2048 + ub * 128 * KP * es + 8 * 128 * kNPT * es + tc_stages(KP, stage_bytes, es, ub) * stage_bytes;
     return b < 116 * 1024 ? 116 * 1024 : b;    // at most one CTA (and one TMEM allocation) per SM
 }
 
 int tc_chunk_points() { return kNPT; }
 
-int64_t tc_geom_floats(int64_t n_elem, int nch) { return (n_elem + 127) / 128 * nch * 7 * kNPT * 128; }
+int64_t tc_geom_halves(int64_t n_elem, int nch) { return (n_elem + 127) / 128 * nch * 7 * kNPT * 128; }
 
-cudaError_t tc_geom_layout(const double* g, float* out, int64_t n_elem, int NQ, int NQp, int nch, cudaStream_t s) {
-    tc_geom_kernel<<<1024, 256, 0, s>>>(g, out, n_elem, NQ, NQp, nch);
-    return cudaGetLastError();
-}
-
-cudaError_t tc_geom_layout_affine(int shape, const double* rec, const double* z, const double* w, int Q, float* out,
-                                  int64_t n_elem, int nch, cudaStream_t s) {
+cudaError_t tc_geom_layout16(int shape, bool curved, const double* g, int NQp, const double* z, const double* w, int Q,
+                             uint16_t* out, float* isc, int64_t n_elem, int nch, cudaStream_t s) {
+    if (n_elem <= 0) return cudaSuccess;
+    const int64_t ntiles = (n_elem + 127) / 128;
+    cudaError_t e = cudaMemsetAsync(out, 0, (size_t)tc_geom_halves(n_elem, nch) * sizeof(uint16_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(isc, 0, (size_t)ntiles * 128 * sizeof(float), s);
+    if (e != cudaSuccess) return e;
     switch (shape) {
-        case HP_HEX: tc_geom_affine_kernel<HP_HEX><<<1024, 256, 0, s>>>(rec, z, w, Q, out, n_elem, nch); break;
-        case HP_PRISM: tc_geom_affine_kernel<HP_PRISM><<<1024, 256, 0, s>>>(rec, z, w, Q, out, n_elem, nch); break;
-        case HP_PYR: tc_geom_affine_kernel<HP_PYR><<<1024, 256, 0, s>>>(rec, z, w, Q, out, n_elem, nch); break;
-        default: tc_geom_affine_kernel<HP_TET><<<1024, 256, 0, s>>>(rec, z, w, Q, out, n_elem, nch); break;
+        case HP_HEX: return geom16_shape<HP_HEX>(curved, g, NQp, z, w, Q, out, isc, n_elem, nch, s);
+        case HP_PRISM: return geom16_shape<HP_PRISM>(curved, g, NQp, z, w, Q, out, isc, n_elem, nch, s);
+        case HP_PYR: return geom16_shape<HP_PYR>(curved, g, NQp, z, w, Q, out, isc, n_elem, nch, s);
+        default: return geom16_shape<HP_TET>(curved, g, NQp, z, w, Q, out, isc, n_elem, nch, s);
     }
-    return cudaGetLastError();
 }
 
 cudaError_t tc_emat_launch(const TCArgs& a, cudaStream_t s) {
     const int64_t ntiles = (a.n_elem + 127) / 128;
     if (ntiles <= 0) return cudaSuccess;
     TCArgs b = a;
-    b.stages = tc_stages(a.KP, a.stage_bytes, a.es);
+    b.ubufs = tc_ubufs(a.KP, a.stage_bytes, a.es);
+    b.stages = tc_stages(a.KP, a.stage_bytes, a.es, b.ubufs);
     // BF16 holds a chunk's stage until its backward MMAs, kFwdBufs - 1 chunks later
     if (b.stages < (a.es == 2 ? kFwdBufs + 1 : 2)) return cudaErrorInvalidValue;
     const int smem = tc_smem_bytes(a.KP, a.stage_bytes, a.es);

@@ -5,11 +5,12 @@ Tolerance (relative, infinity norm over the whole output vector):
 TF32_TOL = 8 u with u = 2^-11, the unit roundoff of TF32 (10 stored mantissa
 bits, round to nearest).  Each term of out_e = sum A_c^T M A_c' uhat carries
 three TF32 roundings (the coefficient, the reference-matrix entry and the
-metric-weighted point value V'), so |error_m| <= 3 u (|A|^T |M| |A| |uhat|)_m
-to first order, plus FP32 accumulation (~1e-7).  The ratio of that absolute
-sum to ||out||_inf is the cancellation factor; random-sign rounding errors
-keep the measured error near 1 u (worst case 1.1 u on these meshes), and 8 u
-allows a cancellation factor of 2.7 at full correlation.  Blocks whose mode
+metric-weighted point value V') and the rounding of the metric factor to FP16
+(11 significant bits after a per-element power-of-two scale, so at most u as
+well), so |error_m| <= 4 u (|A|^T |M| |A| |uhat|)_m to first order, plus FP32
+accumulation (~1e-7).  The ratio of that absolute sum to ||out||_inf is the
+cancellation factor; random-sign rounding errors keep the measured error near
+1 u, and 8 u allows a cancellation factor of 2 at full correlation.  Blocks whose mode
 count exceeds the tensor-memory budget (N_P > 256) run FP32 sum factorisation
 and are held to the FP32 bound of test_gpu_parity.  BF16 (8 significant
 bits) takes the same argument with u = 2^-8: BF16_TOL = 8 u.
