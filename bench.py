@@ -36,6 +36,16 @@ SHAPES = ("hex", "prism", "pyr", "tet")
 MEASURED_TRAFFIC = {"sf_kernel<pyr,P8,f64>": 371970816}
 
 
+# small, fixed cases for ncu captures (a few hundred MB on the device):
+# name -> (shape, P, elements, strategy, dtype)
+PROFILE_CASES = {
+    "tc_tet8": (3, 8, 19456, "ELEMAT", "TF32"),
+    "tc16_tet8": (3, 8, 19456, "ELEMAT", "BF16"),
+    "sf32_hex4": (0, 4, 65536, "SUMFAC", "FP32"),
+    "sf32_tet4": (3, 4, 65536, "SUMFAC", "FP32"),
+}
+
+
 def hp_block_work(op, block):
     from paper_2604_04644_gb300 import hp
     return hp.hp_op_block_work(op, block)
@@ -55,9 +65,10 @@ def parse():
     p.add_argument("--solve", action="store_true",
                    help="assembled Helmholtz solve (time to 1e-10): FP64 PCG vs mixed FP32 PCG + FP64 refinement")
     p.add_argument("--no-extra", action="store_true", help="skip the p-adaptive batched measurement")
-    p.add_argument("--profile-case", default=None, choices=["tc_tet8"],
-                   help="run one small case for a profiler capture instead (tc_tet8: TF32 tensor-core Helmholtz, "
-                        "19 456 curved tets, P = 8, three applies)")
+    p.add_argument("--profile-case", default=None, choices=sorted(PROFILE_CASES),
+                   help="run one small case for a profiler capture instead (tc_tet8 / tc16_tet8: TF32 / BF16 "
+                        "tensor-core Helmholtz, 19 456 curved tets, P = 8; sf32_hex4 / sf32_tet4: FP32 sum "
+                        "factorisation, 65 536 curved hexes / tets, P = 4; three applies)")
     p.add_argument("--orders", default=None, help="comma-separated orders (default 1..8); for profiling runs")
     p.add_argument("--cells", type=int, default=None, help="cells per direction (default 16); for profiling runs")
     a = p.parse_args()
@@ -228,29 +239,52 @@ def time_applies(work, steps, warmup, device, world, flush):
 def time_e2e(work, steps, device):
     """Same workload through the public API with host buffers: pinned host ->
     device copy of the coefficients, apply, device -> host copy of the result,
-    all inside the timed region."""
+    all inside the timed region.  The copies run on their own streams (one per
+    direction), so one order's copies overlap the other orders' applies; each
+    copy in waits for the previous step's apply of its order to free the input,
+    each apply for its input and for the previous step's copy out of its output."""
     import torch
     from paper_2604_04644_gb300 import hp
-    stream = torch.cuda.current_stream(device)
+    comp = torch.cuda.current_stream(device)
+    s_in, s_out = torch.cuda.Stream(device), torch.cuda.Stream(device)
     hx = [torch.tensor(w["uh"], dtype=w["x"].dtype).pin_memory() for w in work]
     hy = [torch.empty(w["nc"], dtype=w["y"].dtype).pin_memory() for w in work]
     h2d = sum(t.numel() * t.element_size() for t in hx)
     d2h = sum(t.numel() * t.element_size() for t in hy)
+    in_done = [torch.cuda.Event() for _ in work]
+    applied = [torch.cuda.Event() for _ in work]
+    out_done = [torch.cuda.Event() for _ in work]
     torch.cuda.synchronize(device)
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
-    t0.record(stream)
-    for _ in range(steps):
+    t0.record(comp)
+    s_in.wait_stream(comp)
+    s_out.wait_stream(comp)
+    for step in range(steps):
         for i, w in enumerate(work):
-            w["x"].copy_(hx[i], non_blocking=True)
-            hp.hp_op_apply(w["op"], 1.0, w["x"], w["y"], stream)
-            hy[i].copy_(w["y"], non_blocking=True)
-    t1.record(stream)
+            with torch.cuda.stream(s_in):
+                if step > 0:
+                    s_in.wait_event(applied[i])
+                w["x"].copy_(hx[i], non_blocking=True)
+                in_done[i].record(s_in)
+            comp.wait_event(in_done[i])
+            if step > 0:
+                comp.wait_event(out_done[i])
+            hp.hp_op_apply(w["op"], 1.0, w["x"], w["y"], comp)
+            applied[i].record(comp)
+            with torch.cuda.stream(s_out):
+                s_out.wait_event(applied[i])
+                hy[i].copy_(w["y"], non_blocking=True)
+                out_done[i].record(s_out)
+    comp.wait_stream(s_in)
+    comp.wait_stream(s_out)
+    t1.record(comp)
     torch.cuda.synchronize(device)
     ms = t0.elapsed_time(t1) / steps
     dofs = sum(w["dofs"] for w in work)
     return {"value": dofs / (ms * 1e-3) / 1e9, "unit": "GDOF/s", "h2d_bytes_per_step": int(h2d),
-            "d2h_bytes_per_step": int(d2h), "ms_per_step": ms}
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": ms,
+            "copies": "own streams per direction, overlapping the other orders' applies"}
 
 
 def shape_order_table(dtype_name, device, reps=5):
@@ -609,16 +643,17 @@ def run_solve(local, cells, order=4, lam=1.0, tol=1e-10):
 
 
 def run_profile_case(name, local):
-    """A small, fixed case for an ncu capture (a few hundred MB on the device)."""
+    """One block of curved elements, three Helmholtz applies (the capture takes one)."""
     import torch
     from paper_2604_04644_gb300 import hp, inputs
     torch.cuda.set_device(local)
-    mesh = inputs.replicated_mesh(3, 8, 19456, curved=True)
+    shape, P, n, strat, dt = PROFILE_CASES[name]
+    mesh = inputs.replicated_mesh(shape, P, n, curved=True)
     h = hp.hp_mesh_create(mesh, local)
     co, po, nc, nph = hp.hp_mesh_layout(h, mesh["n_elem"])
     x = torch.tensor(inputs.random_coefficients(5, co), device="cuda:%d" % local, dtype=torch.float32)
     y = torch.zeros(nc, device="cuda:%d" % local, dtype=torch.float32)
-    op = hp.hp_op_create(h, hp.HP_HELMHOLTZ, hp.HP_STRAT_ELEMAT, hp.HP_TF32)
+    op = hp.hp_op_create(h, hp.HP_HELMHOLTZ, getattr(hp, "HP_STRAT_" + strat), getattr(hp, "HP_" + dt))
     for _ in range(3):
         hp.hp_op_apply(op, 1.0, x, y)
     hp.hp_op_sync(op)
