@@ -160,6 +160,25 @@ __device__ __forceinline__ void ld_32x8_x4(uint32_t taddr, uint32_t stride, floa
     for (int i = 0; i < 32; ++i) v[i / 8][i % 8] = __uint_as_float(r[i]);
 }
 
+// four 32 x 4 loads at columns taddr + i * stride (i = 0..3) and one wait
+__device__ __forceinline__ void ld_32x4_x4(uint32_t taddr, uint32_t stride, float (&v)[4][4]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%16];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%4,%5,%6,%7}, [%17];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%8,%9,%10,%11}, [%18];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%12,%13,%14,%15}, [%19];\n"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr), "r"(taddr + stride), "r"(taddr + 2 * stride), "r"(taddr + 3 * stride)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i / 4][i % 4] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void ld_x4(uint32_t taddr, uint32_t stride, float (&v)[4][4]) { ld_32x4_x4(taddr, stride, v); }
+__device__ __forceinline__ void ld_x4(uint32_t taddr, uint32_t stride, float (&v)[4][8]) { ld_32x8_x4(taddr, stride, v); }
+
 // round to the TF32 grid (10-bit mantissa, nearest, ties away)
 __device__ __forceinline__ float to_tf32(float x) {
     uint32_t r;

@@ -24,9 +24,11 @@
 // accumulators are in flight and the V' tiles are double-buffered, so the
 // forward MMAs run two chunks ahead of the metric and the metric of chunk k
 // overlaps the backward MMAs of chunk k-1.
-// Roles: warps 0-7 gather U, run the metric and write the outputs (warp w
-// reads TMEM lanes 32 (w mod 4).. and half w / 4 of each chunk's points);
-// warp 8 issues the bulk copies; warp 9 issues the MMAs.  Every wait is
+// Roles: warps 0-15 gather U, run the metric and write the outputs (warp w
+// reads TMEM lanes 32 (w mod 4).. and points 4 (w / 4).. of each chunk: four
+// warps per TMEM lane quarter, so each scheduler holds four of them to hide
+// the latency of the tensor-memory loads and the factor loads); warp 16 issues
+// the bulk copies; warp 17 issues the MMAs.  Every wait is
 // bounded; a timeout latches DERR_TIMEOUT, stops every role, drains the
 // copies and MMAs in flight and frees the tensor memory before the CTA exits.
 #include <cuda_bf16.h>
@@ -39,13 +41,16 @@ namespace hp {
 namespace {
 
 constexpr int kNPT = 16;          // quadrature points per chunk
-constexpr int kHalf = kNPT / 2;   // points per epilogue thread
+constexpr int kEpiWarps = 16;     // epilogue warps: kGroups per TMEM lane quarter
+constexpr int kGroups = kEpiWarps / 4;
+constexpr int kPts = kNPT / kGroups;     // points of a chunk per epilogue thread
+constexpr int kRows = 128 / kEpiWarps;   // tile rows per epilogue warp (coefficient gather and output)
 constexpr int kMaxStages = 8;     // bulk-copy ring: as many stages (2..8) as fit in shared memory
 constexpr int kTmemCols = 512;
 constexpr int kFwdBufs = 3;       // forward accumulators in flight: the forward MMAs run two chunks ahead
 constexpr int kOutCol = kFwdBufs * 4 * 16;   // TMEM column of the output accumulator
-constexpr int kEpi = 256;         // epilogue threads
-constexpr int kThreads = kEpi + 64;
+constexpr int kEpi = 32 * kEpiWarps;   // epilogue threads
+constexpr int kThreads = kEpi + 64;     // + the producer warp and the MMA warp
 constexpr int kSliceBytes = 4 * kNPT * 128;   // forward operand slice: 64 rows x 128 bytes of modes
 
 // Operand element type: TF32 (ES = 4, kind::tf32, K = 8 per MMA) or BF16
@@ -71,6 +76,17 @@ struct Op {
     __device__ static uint32_t offv(uint32_t r, uint32_t p) {
         if constexpr (ES == 4) return tc::sw64_offset(r, p);
         else return r * 32 + ((((p * 2) >> 4) ^ ((r >> 2) & 1)) << 4);
+    }
+    // kPts consecutive points p.. of row r of a 16-point tile
+    __device__ static void put_pts(unsigned char* tile, uint32_t r, uint32_t p, const float* x) {
+        if constexpr (ES * kPts >= 16) {
+#pragma unroll
+            for (int p0 = 0; p0 < kPts; p0 += 16 / ES) *reinterpret_cast<uint4*>(tile + offv(r, p + p0)) = pack(x + p0);
+        } else {      // BF16, 4 points: the half of a 16-byte chunk at (p mod 8) * 2
+            const __nv_bfloat162 h0 = __floats2bfloat162_rn(x[0], x[1]), h1 = __floats2bfloat162_rn(x[2], x[3]);
+            *reinterpret_cast<uint2*>(tile + offv(r, p) + (p & 7) * 2) =
+                make_uint2(*reinterpret_cast<const uint32_t*>(&h0), *reinterpret_cast<const uint32_t*>(&h1));
+        }
     }
     // one operand element
     __device__ static void put(unsigned char* p, float x) {
@@ -103,6 +119,12 @@ struct Ring {
         if (++i == n) { i = 0; ph ^= 1u; }
     }
 };
+
+// this thread's kPts FP16 metric factors of one factor: 8 bytes (4 points) or 16 (8 points)
+using GV = std::conditional_t<kPts == 8, uint4, uint2>;
+__device__ __forceinline__ GV ldg_gv(const GV* p) { return __ldg(p); }
+__device__ __forceinline__ uint32_t gv_word(const uint4& g, int i) { return i == 0 ? g.x : i == 1 ? g.y : i == 2 ? g.z : g.w; }
+__device__ __forceinline__ uint32_t gv_word(const uint2& g, int i) { return i == 0 ? g.x : g.y; }
 
 struct Bars {
     uint64_t full[kMaxStages], empty[kMaxStages];
@@ -181,7 +203,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_emat_kernel(const __grid_const
     tc::fence_after();
     const uint32_t tbase = B->tmem;
 
-    if (warp == 8) {
+    if (warp == kEpiWarps) {
         // ---------------------------------------------------------------- producer
         if (lane == 0) {
             int slot = 0;
@@ -227,7 +249,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_emat_kernel(const __grid_const
                 }
         }
         __syncwarp();
-    } else if (warp == 9) {
+    } else if (warp == kEpiWarps + 1) {
         // ---------------------------------------------------------------- MMA issuer
         if (lane == 0) {
             const uint32_t id_f = tc::instr_desc(O::FMT, 128, kNPT * (a.c1 - a.c0));
@@ -334,24 +356,25 @@ __global__ void __launch_bounds__(kThreads, 1) tc_emat_kernel(const __grid_const
         }
         __syncwarp();
     } else {
-        // ---------------------------------------------------------------- epilogue warps 0-7
+        // ---------------------------------------------------------------- epilogue warps
+        // warp w reads TMEM lane quarter q = w mod 4 and points h kPts .. of each chunk
         const int q = warp & 3, h = warp >> 2;
         const int r = q * 32 + lane;            // element row of the tile = TMEM lane
         const uint32_t lane_base = (uint32_t)(q * 32) << 16;
         constexpr uint32_t kAll = 0xffffffffu;
-        // coefficient offsets of rows 16 warp .. 16 warp + 15 of work item wi's
-        // tile: lane i < 16 holds row 16 warp + i's (-1 past the last element)
+        // coefficient offsets of rows kRows warp .. of work item wi's tile: lane
+        // i < kRows holds row kRows warp + i's (-1 past the last element)
         auto row_offsets = [&](int64_t wi) -> int64_t {
-            const int64_t e = (wi / a.nsplit) * 128 + warp * 16 + lane;
-            return (lane < 16 && e < a.n_elem) ? a.coeff_off[e] : (int64_t)-1;
+            const int64_t e = (wi / a.nsplit) * 128 + warp * kRows + lane;
+            return (lane < kRows && e < a.n_elem) ? a.coeff_off[e] : (int64_t)-1;
         };
         // U of a tile into buffer j, coalesced: each warp copies the coefficient
-        // rows of its 16 elements (offsets `offs`, lanes along the modes; RB rows
-        // of up to 32 JJ modes with all their loads in flight at a time), rounded
-        // to the operand type and zero padded to KP
+        // rows of its kRows elements (offsets `offs`, lanes along the modes; RB
+        // rows of up to 32 JJ modes with all their loads in flight at a time),
+        // rounded to the operand type and zero padded to KP
         auto gather_rows = [&](auto RBc, auto JJc, unsigned char* dU, int64_t offs) {
             constexpr int RB = decltype(RBc)::value, JJ = decltype(JJc)::value;
-            for (int i0 = 0; i0 < 16; i0 += RB) {
+            for (int i0 = 0; i0 < kRows; i0 += RB) {
                 float x[RB][JJ];
 #pragma unroll
                 for (int ii = 0; ii < RB; ++ii) {
@@ -364,7 +387,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_emat_kernel(const __grid_const
                 }
 #pragma unroll
                 for (int ii = 0; ii < RB; ++ii) {
-                    const int row = warp * 16 + i0 + ii;
+                    const int row = warp * kRows + i0 + ii;
 #pragma unroll
                     for (int jj = 0; jj < JJ; ++jj) {
                         const int m = lane + 32 * jj;
@@ -402,31 +425,31 @@ __global__ void __launch_bounds__(kThreads, 1) tc_emat_kernel(const __grid_const
             // the next tile's U is gathered while this tile's last MMAs run
             if (a.ubufs == 1 || ntile == 0) gather_u(0, offs);
             const float isc = a.gscale[tile * 128 + r];     // 2^-k of element r's FP16 factors (0: padding)
-            const uint4* gt = reinterpret_cast<const uint4*>(a.geom16) + (tile * a.nch * 14 + h) * 128 + r;
-            // the seven factors of chunk k at this thread's 8 points: 16 bytes each
-            auto load_geom = [&](int k, uint4 (&G)[7]) {
+            const GV* gt = reinterpret_cast<const GV*>(a.geom16) + (tile * a.nch * 7 * kGroups + h) * 128 + r;
+            // the seven factors of chunk k at this thread's kPts points (kPts halves each)
+            auto load_geom = [&](int k, GV (&G)[7]) {
 #pragma unroll
                 for (int f = 0; f < 7; ++f)
-                    G[f] = (f == 6 || a.c1 > 1) ? __ldg(gt + ((int64_t)k * 7 + f) * 256) : make_uint4(0u, 0u, 0u, 0u);
+                    G[f] = (f == 6 || a.c1 > 1) ? ldg_gv(gt + ((int64_t)k * 7 + f) * (kGroups * 128)) : GV{};
             };
             // metric of chunk k: forward accumulator -> V' tile (components
             // outside [c0, c1) are computed from unused columns and discarded)
-            auto process = [&](int k, const uint4 (&Gh)[7]) -> bool {
+            auto process = [&](int k, const GV (&Gh)[7]) -> bool {
                 const uint32_t g = g0 + (uint32_t)(k - kb), b = g & 1u, use = g >> 1;
                 const uint32_t bf = g % kFwdBufs, usef = g / kFwdBufs;     // forward accumulator buffer
                 if (!wait_warp(&B->fwd_full[bf], usef & 1u, B, a.err)) return false;
                 tc::fence_after();
-                float v[4][kHalf];
-                tc::ld_32x8_x4(tbase + lane_base + (uint32_t)(bf * 4 * kNPT + h * kHalf), kNPT, v);
+                float v[4][kPts];
+                tc::ld_x4(tbase + lane_base + (uint32_t)(bf * 4 * kNPT + h * kPts), kNPT, v);
                 tc::fence_before();
                 arrive(&B->fwd_empty[bf]);
-                float o[4][kHalf];
+                float o[4][kPts];
 #pragma unroll
-                for (int p2 = 0; p2 < kHalf / 2; ++p2) {
+                for (int p2 = 0; p2 < kPts / 2; ++p2) {
                     float2 G[7];
 #pragma unroll
                     for (int f = 0; f < 7; ++f) {
-                        const uint32_t wd = p2 == 0 ? Gh[f].x : p2 == 1 ? Gh[f].y : p2 == 2 ? Gh[f].z : Gh[f].w;
+                        const uint32_t wd = gv_word(Gh[f], p2);
                         G[f] = __half22float2(*reinterpret_cast<const __half2*>(&wd));
                     }
 #pragma unroll
@@ -445,17 +468,14 @@ __global__ void __launch_bounds__(kThreads, 1) tc_emat_kernel(const __grid_const
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
                     if (c < a.c0 || c >= a.c1) continue;
-                    unsigned char* dst = sV + (size_t)(b * 4 + c) * O::VBYTES;
-#pragma unroll
-                    for (int p0 = 0; p0 < kHalf; p0 += 16 / ES)
-                        *reinterpret_cast<uint4*>(dst + O::offv(r, h * kHalf + p0)) = O::pack(&o[c][p0]);
+                    O::put_pts(sV + (size_t)(b * 4 + c) * O::VBYTES, r, h * kPts, o[c]);
                 }
                 tc::fence_async_smem();
                 arrive(&B->vp_full[b]);
                 return true;
             };
             // factors two chunks ahead: three register sets in rotation
-            uint4 ga[7], gb[7], gc[7];
+            GV ga[7], gb[7], gc[7];
             if (kb < ke) load_geom(kb, ga);
             if (kb + 1 < ke) load_geom(kb + 1, gb);
             for (int k = kb; k < ke; k += 3) {
@@ -478,10 +498,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_emat_kernel(const __grid_const
             float* stage = reinterpret_cast<float*>(sV);
             constexpr int CB = 8 * O::VBYTES / (128 * 4);
             for (int cb = 0; cb < a.NPpad; cb += CB) {
-                // row r, columns h CB/2 .. of the pass; 16-byte chunks XOR-swizzled by row
+                // row r, columns h CB / kGroups .. of the pass; 16-byte chunks XOR-swizzled by row
 #pragma unroll
-                for (int c = 0; c < CB / 2; c += 16) {
-                    const int cc = h * (CB / 2) + c;
+                for (int c = 0; c < CB / kGroups; c += 16) {
+                    const int cc = h * (CB / kGroups) + c;
                     if (cb + cc < a.NPpad) {             // warp-uniform; NPpad is a multiple of 16
                         float v[16];
                         tc::ld_32x16(tbase + lane_base + (uint32_t)(kOutCol + cb + cc), v);
@@ -492,10 +512,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_emat_kernel(const __grid_const
                     }
                 }
                 if (!(ok = epi_sync())) break;
-                for (int i = 0; i < 16; ++i) {
+                for (int i = 0; i < kRows; ++i) {
                     const int64_t off = __shfl_sync(kAll, offs, i);
                     if (off < 0) continue;                  // warp-uniform
-                    const int row = warp * 16 + i;
+                    const int row = warp * kRows + i;
                     for (int m = lane; m < CB; m += 32) {
                         if (cb + m >= a.NP) break;
                         const float val = stage[row * CB + (((m >> 2) ^ (row & 7)) << 2) + (m & 3)];
@@ -533,11 +553,12 @@ __global__ void zero_coeffs_kernel(float* out, const int64_t* coeff_off, int64_t
 // k_e = 14 - floor(log2 max|G_e|): the largest lies in [2^14, 2^15) (FP16 ends
 // at 65504) and only entries below 2^-28 of it fall into FP16's subnormal
 // range; the epilogue multiplies its outputs by 2^-k_e (exact in FP32).
-// Layout [tile][chunk][7 factors][2 point halves][128 elements][8 points],
-// 16 bytes per (factor, half, element); padded points and elements stay zero
+// Layout [tile][chunk][7 factors][kGroups point groups][128 elements][kPts
+// points], one epilogue thread's points of a factor contiguous and a warp's 32
+// elements adjacent; padded points and elements stay zero
 // (the buffer is cleared first), and so does the scale of a padded element.
 __host__ __device__ constexpr int64_t geom16_index(int64_t tile, int k, int f, int p, int r, int nch) {
-    return ((((tile * nch + k) * 7 + f) * 2 + (p >> 3)) * 128 + r) * 8 + (p & 7);
+    return ((((tile * nch + k) * 7 + f) * kGroups + p / kPts) * 128 + r) * kPts + p % kPts;
 }
 
 // factors of element e at point l: curved from the FP64 factors [n][7][NQp];
