@@ -157,6 +157,12 @@ __device__ __forceinline__ bool wait_warp(uint64_t* bar, uint32_t parity, Bars* 
 __device__ __forceinline__ void arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
+// one arrival for the whole warp: every lane's earlier writes (and fences) are
+// ordered before lane 0's arrival by the warp barrier
+__device__ __forceinline__ void arrive_warp(uint64_t* bar) {
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) arrive(bar);
+}
 
 
 template <int ES>
@@ -182,19 +188,19 @@ __global__ void __launch_bounds__(kThreads, 1) tc_emat_kernel(const __grid_const
 
     if (tid == 0) {
         for (int s = 0; s < nst; ++s) { mbar_init(&B->full[s], 1); mbar_init(&B->empty[s], 1); }
-        for (int j = 0; j < 2; ++j) mbar_init(&B->u_full[j], kEpi);
+        for (int j = 0; j < 2; ++j) mbar_init(&B->u_full[j], kEpiWarps);
         for (int b = 0; b < kFwdBufs; ++b) {
             mbar_init(&B->fwd_full[b], 1);
-            mbar_init(&B->fwd_empty[b], kEpi);
+            mbar_init(&B->fwd_empty[b], kEpiWarps);
         }
         for (int b = 0; b < 2; ++b) {
-            mbar_init(&B->vp_full[b], kEpi);
+            mbar_init(&B->vp_full[b], kEpiWarps);
             mbar_init(&B->vp_empty[b], 1);
         }
         mbar_init(&B->out_full, 1);
-        mbar_init(&B->out_empty, kEpi);
+        mbar_init(&B->out_empty, kEpiWarps);
         mbar_init(&B->drain, 1);
-        mbar_init(&B->epi, kEpi);
+        mbar_init(&B->epi, kEpiWarps);
         B->abort = 0;
     }
     if (warp == 0) { tc::tmem_alloc(&B->tmem, kTmemCols); tc::tmem_relinquish(); }
@@ -401,13 +407,13 @@ __global__ void __launch_bounds__(kThreads, 1) tc_emat_kernel(const __grid_const
             if (a.KP <= 128) gather_rows(std::integral_constant<int, 8>{}, std::integral_constant<int, 4>{}, dU, offs);
             else gather_rows(std::integral_constant<int, 4>{}, std::integral_constant<int, kTcMaxModes / 32>{}, dU, offs);
             tc::fence_async_smem();
-            arrive(&B->u_full[j]);
+            arrive_warp(&B->u_full[j]);
         };
         // barrier of the epilogue warps alone, bounded like every other wait (a
         // warp that left after a timeout never arrives; the others see the abort)
         uint32_t nepi = 0;
         auto epi_sync = [&]() -> bool {
-            arrive(&B->epi);
+            arrive_warp(&B->epi);
             return wait_warp(&B->epi, (nepi++) & 1u, B, a.err);
         };
         const float lam = a.op == HP_MASS ? 1.f : a.lambda;
@@ -442,7 +448,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_emat_kernel(const __grid_const
                 float v[4][kPts];
                 tc::ld_x4(tbase + lane_base + (uint32_t)(bf * 4 * kNPT + h * kPts), kNPT, v);
                 tc::fence_before();
-                arrive(&B->fwd_empty[bf]);
+                arrive_warp(&B->fwd_empty[bf]);
                 float o[4][kPts];
 #pragma unroll
                 for (int p2 = 0; p2 < kPts / 2; ++p2) {
@@ -471,7 +477,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_emat_kernel(const __grid_const
                     O::put_pts(sV + (size_t)(b * 4 + c) * O::VBYTES, r, h * kPts, o[c]);
                 }
                 tc::fence_async_smem();
-                arrive(&B->vp_full[b]);
+                arrive_warp(&B->vp_full[b]);
                 return true;
             };
             // factors two chunks ahead: three register sets in rotation
@@ -527,7 +533,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_emat_kernel(const __grid_const
             }
             if (!ok) break;
             tc::fence_before();
-            arrive(&B->out_empty);
+            arrive_warp(&B->out_empty);
             offs = offs_next;
         }
     }
