@@ -480,17 +480,31 @@ __global__ void __launch_bounds__(kThreads, 1) tc_emat_kernel(const __grid_const
                 arrive_warp(&B->vp_full[b]);
                 return true;
             };
-            // factors two chunks ahead: three register sets in rotation
-            GV ga[7], gb[7], gc[7];
-            if (kb < ke) load_geom(kb, ga);
-            if (kb + 1 < ke) load_geom(kb + 1, gb);
-            for (int k = kb; k < ke; k += 3) {
-                if (k + 2 < ke) load_geom(k + 2, gc);
-                if (!(ok = process(k, ga)) || k + 1 >= ke) break;
-                if (k + 3 < ke) load_geom(k + 3, ga);
-                if (!(ok = process(k + 1, gb)) || k + 2 >= ke) break;
-                if (k + 4 < ke) load_geom(k + 4, gb);
-                if (!(ok = process(k + 2, gc))) break;
+            if constexpr (ES == 2) {
+                // factors one chunk ahead: two register sets in rotation (with
+                // sixteen epilogue warps the shorter BF16 chunks hide the load,
+                // and the registers saved avoid spills)
+                GV ga[7], gb[7];
+                if (kb < ke) load_geom(kb, ga);
+                for (int k = kb; k < ke; k += 2) {
+                    if (k + 1 < ke) load_geom(k + 1, gb);
+                    if (!(ok = process(k, ga)) || k + 1 >= ke) break;
+                    if (k + 2 < ke) load_geom(k + 2, ga);
+                    if (!(ok = process(k + 1, gb))) break;
+                }
+            } else {
+                // factors two chunks ahead: three register sets in rotation
+                GV ga[7], gb[7], gc[7];
+                if (kb < ke) load_geom(kb, ga);
+                if (kb + 1 < ke) load_geom(kb + 1, gb);
+                for (int k = kb; k < ke; k += 3) {
+                    if (k + 2 < ke) load_geom(k + 2, gc);
+                    if (!(ok = process(k, ga)) || k + 1 >= ke) break;
+                    if (k + 3 < ke) load_geom(k + 3, ga);
+                    if (!(ok = process(k + 1, gb)) || k + 2 >= ke) break;
+                    if (k + 4 < ke) load_geom(k + 4, gb);
+                    if (!(ok = process(k + 2, gc))) break;
+                }
             }
             if (!ok) break;
             g0 += (uint32_t)(ke - kb);
