@@ -50,8 +50,18 @@ __host__ __device__ constexpr int sf_smem_bytes() {
            SFCfg<P, T, TILE>::EPB * 5 * SFCfg<P, T, TILE>::NQ * (int)sizeof(T);
 }
 
+// FP32: as many CTAs per SM as the tile's shared memory admits (at most four, 64
+// registers a thread), so that the loads batched per thread do not take
+// registers from occupancy; FP64: no target
+template <int SHAPE, int P, typename T, int TILE>
+__host__ __device__ constexpr int sf_min_blocks() {
+    if (sizeof(T) != 4) return 0;
+    const int b = (228 * 1024) / (sf_smem_bytes<SHAPE, P, T, TILE>() + 1024);
+    return b < 1 ? 1 : (b > 4 ? 4 : b);
+}
+
 template <int SHAPE, int P, typename T, bool AFFINE, int TILE>
-__global__ void __launch_bounds__(256) sf_kernel(const __grid_constant__ SFArgs<T> args) {
+__global__ void __launch_bounds__(256, (sf_min_blocks<SHAPE, P, T, TILE>())) sf_kernel(const __grid_constant__ SFArgs<T> args) {
     using C = SFCfg<P, T, TILE>;
     constexpr int n = C::n, Q = C::Q, QQ = C::QQ, NQ = C::NQ, N3 = C::N3, EPB = C::EPB, NT = C::NT;
     constexpr int NN = n * n, Qh = (Q + 1) / 2;   // Qh: even-odd pairs (i, Q-1-i) along eta1
@@ -62,6 +72,7 @@ __global__ void __launch_bounds__(256) sf_kernel(const __grid_constant__ SFArgs<
     // memory load pipe is the limit); FP64: one output per thread (more parallel
     // tasks to keep the FP64 pipe, the limit there, busy)
     constexpr bool LINES = sizeof(T) == 4;
+    constexpr int kU = 4;      // FP32: loop iterations per thread whose global loads are issued together
 
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
@@ -106,6 +117,35 @@ __global__ void __launch_bounds__(256) sf_kernel(const __grid_constant__ SFArgs<
             // gather modal coefficients into the slot tensor
             // (slots a = 0, 1 take the sum and the difference of the two coefficients,
             // the inputs of the parity-form eta1 table)
+            if constexpr (LINES) {
+                // FP32 (the passes are cheap, the memory latency is not): kU slots
+                // per thread have their loads issued before any is stored
+                for (int base = tid; base < EPB * N3; base += NT * kU) {
+                    T v[kU];
+#pragma unroll
+                    for (int u = 0; u < kU; ++u) {
+                        const int idx = base + u * NT;
+                        v[u] = T(0);
+                        if (idx < EPB * N3) {
+                            const int e = idx / N3, sl = idx - e * N3, m = slot2mode[sl];
+                            if (e < ne && m >= 0) {
+                                const T* cin = args.in + __ldg(args.coeff_off + e0 + e);
+                                if (sl >= 2 * NN) v[u] = __ldg(cin + m);
+                                else if (sl < NN) v[u] = __ldg(cin + m) + __ldg(cin + slot2mode[sl + NN]);
+                                else v[u] = __ldg(cin + slot2mode[sl - NN]) - __ldg(cin + m);
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < kU; ++u) {
+                        const int idx = base + u * NT;
+                        if (idx < EPB * N3) {
+                            const int e = idx / N3;
+                            S2[e * NQ + idx - e * N3] = v[u];
+                        }
+                    }
+                }
+            } else
             for (int idx = tid; idx < EPB * N3; idx += NT) {
                 int e = idx / N3, sl = idx - e * N3;
                 T v = T(0);
@@ -323,6 +363,54 @@ __global__ void __launch_bounds__(256) sf_kernel(const __grid_constant__ SFArgs<
         }
 
         // pointwise metric
+        bool metric_done = false;
+        if constexpr (LINES && !AFFINE) {
+            if (op == HP_MASS || op == HP_LAPLACIAN || op == HP_HELMHOLTZ) {
+                // FP32: the factors of kU points per thread are loaded before any is
+                // used, so their HBM latencies overlap
+                const bool lap = op != HP_MASS;
+                for (int base = tid; base < EPB * NQ; base += NT * kU) {
+                    T G[kU][7];
+#pragma unroll
+                    for (int u = 0; u < kU; ++u) {
+                        const int idx = base + u * NT, e = idx / NQ, r = idx - e * NQ;
+#pragma unroll
+                        for (int f = 0; f < 7; ++f) G[u][f] = T(0);
+                        if (idx < EPB * NQ && e < ne) {
+                            const T* gp = args.geom + (e0 + e) * 7 * (int64_t)NQp + r;
+                            G[u][6] = __ldg(gp + 6 * NQp);
+                            if (lap) {
+#pragma unroll
+                                for (int f = 0; f < 6; ++f) G[u][f] = __ldg(gp + f * NQp);
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < kU; ++u) {
+                        const int idx = base + u * NT, e = idx / NQ, r = idx - e * NQ;
+                        if (idx >= EPB * NQ) break;
+                        T* uu = S1 + e * 4 * NQ + r;
+                        if (e >= ne) {
+                            S2[e * NQ + r] = T(0);
+                            if (lap) { uu[NQ] = T(0); uu[2 * NQ] = T(0); uu[3 * NQ] = T(0); }
+                            continue;
+                        }
+                        const T uval = uu[0];
+                        if (!lap) {
+                            S2[e * NQ + r] = G[u][6] * uval;
+                            continue;
+                        }
+                        const T v1 = uu[NQ], v2 = uu[2 * NQ], v3 = uu[3 * NQ];
+                        uu[NQ] = G[u][0] * v1 + G[u][1] * v2 + G[u][2] * v3;
+                        uu[2 * NQ] = G[u][1] * v1 + G[u][3] * v2 + G[u][4] * v3;
+                        uu[3 * NQ] = G[u][2] * v1 + G[u][4] * v2 + G[u][5] * v3;
+                        S2[e * NQ + r] = (op == HP_HELMHOLTZ) ? args.lambda * G[u][6] * uval : T(0);
+                    }
+                }
+                metric_done = true;
+            }
+        }
+        if (!metric_done)
         for (int idx = tid; idx < EPB * NQ; idx += NT) {
             int e = idx / NQ, r = idx - e * NQ;
             if (e >= ne) {
@@ -573,6 +661,41 @@ __global__ void __launch_bounds__(256) sf_kernel(const __grid_constant__ SFArgs<
         }
         __syncthreads();
         // scatter slots to modes (collapsed modes sum their slots)
+        auto mode_sum = [&](int e, int m) {
+            const T* rs = S1 + e * 4 * NQ;
+            T acc = T(0);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                int sl = mode_slots[m * 4 + q];
+                if (sl < 0) continue;
+                // slots a = 0, 1 hold the restrictions against 1/2 and -z/2:
+                // L = 1/2 - z/2 takes their sum, R = 1/2 + z/2 their difference
+                if (sl >= 2 * NN) acc += rs[sl];
+                else if (sl < NN) acc += rs[sl] + rs[sl + NN];
+                else acc += rs[sl - NN] - rs[sl];
+            }
+            return acc;
+        };
+        if constexpr (LINES) {
+            // FP32: the output offsets of kU modes per thread are loaded together
+            for (int base = tid; base < EPB * NP; base += NT * kU) {
+                int64_t off[kU];
+                T acc[kU];
+#pragma unroll
+                for (int u = 0; u < kU; ++u) {
+                    const int idx = base + u * NT, e = idx / NP, m = idx - e * NP;
+                    off[u] = -1;
+                    acc[u] = T(0);
+                    if (idx < EPB * NP && e < ne) {
+                        off[u] = __ldg(args.coeff_off + e0 + e) + m;
+                        acc[u] = mode_sum(e, m);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < kU; ++u)
+                    if (off[u] >= 0) args.out[off[u]] = acc[u];
+            }
+        } else
         for (int idx = tid; idx < EPB * NP; idx += NT) {
             int e = idx / NP, m = idx - e * NP;
             if (e >= ne) continue;
@@ -582,8 +705,6 @@ __global__ void __launch_bounds__(256) sf_kernel(const __grid_constant__ SFArgs<
             for (int q = 0; q < 4; ++q) {
                 int sl = mode_slots[m * 4 + q];
                 if (sl < 0) continue;
-                // slots a = 0, 1 hold the restrictions against 1/2 and -z/2:
-                // L = 1/2 - z/2 takes their sum, R = 1/2 + z/2 their difference
                 if (sl >= 2 * NN) acc += rs[sl];
                 else if (sl < NN) acc += rs[sl] + rs[sl + NN];
                 else acc += rs[sl - NN] - rs[sl];
