@@ -91,8 +91,9 @@ typedef enum {
  * the elemental-matrix strategy on the tensor cores (tcgen05, Blackwell):
  * coefficients, reference matrices and metric-weighted point values rounded
  * to TF32 (10-bit mantissa) or BF16 (7-bit mantissa), products accumulated in
- * FP32 in tensor memory; float arrays; relative error a few units of 2^-11
- * (TF32) or 2^-8 (BF16). */
+ * FP32 in tensor memory, metric factors kept in FP16 with one power-of-two
+ * scale per element (11 significant bits); float arrays; relative error a
+ * few units of 2^-11 (TF32) or 2^-8 (BF16). */
 typedef enum { HP_FP64 = 0, HP_FP32 = 1, HP_TF32 = 2, HP_BF16 = 3 } hp_dtype;
 
 /* Mesh description (all host arrays, copied by hp_mesh_create).

@@ -128,7 +128,7 @@ __device__ __forceinline__ uint32_t gv_word(const uint2& g, int i) { return i ==
 
 struct Bars {
     uint64_t full[kMaxStages], empty[kMaxStages];
-    uint64_t epi;                      // the eight epilogue warps among themselves
+    uint64_t epi;                      // the epilogue warps among themselves
     uint64_t u_full[2], fwd_full[kFwdBufs], fwd_empty[kFwdBufs], vp_full[2], vp_empty[2], out_full, out_empty, drain;
     uint32_t tmem;
     int abort;
