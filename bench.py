@@ -459,13 +459,19 @@ def padaptive(device, reps=10):
     x32 = x.float()
     y32 = torch.zeros(nc, device="cuda:%d" % device, dtype=torch.float32)
     forms = {}
-    for name, strat, dt, sched in (("fp32_sumfac", hp.HP_STRAT_SUMFAC, hp.HP_FP32, False),
-                                   ("tf32_tensor_core", hp.HP_STRAT_ELEMAT, hp.HP_TF32, False),
-                                   ("tf32_scheduled", hp.HP_STRAT_ELEMAT, hp.HP_TF32, True),
-                                   ("bf16_tensor_core", hp.HP_STRAT_ELEMAT, hp.HP_BF16, False)):
+    # scheduled forms: "exhaustive" times every block alone; "graph" searches on
+    # the time of the whole concurrent graph (coordinate descent over blocks)
+    for name, strat, dt, sched in (("fp32_sumfac", hp.HP_STRAT_SUMFAC, hp.HP_FP32, None),
+                                   ("tf32_tensor_core", hp.HP_STRAT_ELEMAT, hp.HP_TF32, None),
+                                   ("tf32_scheduled", hp.HP_STRAT_ELEMAT, hp.HP_TF32, "exhaustive"),
+                                   ("tf32_graph_scheduled", hp.HP_STRAT_ELEMAT, hp.HP_TF32, "graph"),
+                                   ("bf16_tensor_core", hp.HP_STRAT_ELEMAT, hp.HP_BF16, None),
+                                   ("bf16_graph_scheduled", hp.HP_STRAT_ELEMAT, hp.HP_BF16, "graph")):
         op = hp.hp_op_create(h, hp.HP_HELMHOLTZ, strat, dt)
-        if sched:
+        if sched == "exhaustive":
             hp.hp_op_schedule_exhaustive(op, 1.0, x32, y32, nblocks, stream)
+        elif sched == "graph":
+            hp.hp_op_schedule_graph(op, 1.0, x32, y32, 5, 2, stream)
         ms = timed(lambda: hp.hp_op_apply_graph(op, 1.0, x32, y32, stream))
         st = hp.hp_op_strategies(op, nblocks)
         err = float((y32.double() - y64).abs().max() / y64.abs().max())

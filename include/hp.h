@@ -262,6 +262,19 @@ hp_status hp_op_schedule(hp_op op, hp_mlp mlp, void* stream);
 hp_status hp_op_schedule_exhaustive(hp_op op, double lambda, const void* in, void* out, float* times_ms,
                                     void* stream);
 
+/* Graph-aware schedule (not in the paper): coordinate descent on the time of
+ * the whole concurrent graph launch of hp_op_apply_graph.  Starting from the
+ * current strategies, each block in turn tries every other strategy built for
+ * it and keeps one only if the graph's median time over `reps` timed launches
+ * (after a warm-up) drops by more than 1 %; `passes` sweeps over the blocks.
+ * Per-block times taken alone (hp_op_schedule_exhaustive) miss the overlap of
+ * the blocks that run concurrently in the graph.  in/out as for
+ * hp_op_apply_graph (contents overwritten); *ms (may be NULL) receives the
+ * final median graph time.  Errors: HP_ERR_ARG (reps outside 1..64, passes
+ * outside 1..8, null or aliasing arrays), HP_ERR_CUDA. */
+hp_status hp_op_schedule_graph(hp_op op, double lambda, const void* in, void* out, int reps, int passes, float* ms,
+                               void* stream);
+
 /* Physical coordinates of every quadrature point (device array 3*n_phys,
  * component-major: xyz[c*n_phys + phys_offset[e] + l]); the affine vertex map
  * followed, for curved elements, by the mesh's deformation. */

@@ -1003,6 +1003,67 @@ hp_status hp_op_schedule_exhaustive(hp_op op, double lambda, const void* in, voi
     return hp_op_strategies(op, choice.data(), nb, 1);
 }
 
+hp_status hp_op_schedule_graph(hp_op op, double lambda, const void* in, void* out, int reps, int passes, float* ms,
+                               void* stream) {
+    if (!op || !in || !out || in == out) { set_error("hp_op_schedule_graph: null or aliasing arrays"); return HP_ERR_ARG; }
+    if (reps < 1 || reps > 64 || passes < 1 || passes > 8) { set_error("hp_op_schedule_graph: reps or passes out of range"); return HP_ERR_ARG; }
+    DeviceGuard guard(op->mesh->device);
+    if (!needs_deriv_geom(op->kind) && op->dtype != HP_TF32 && op->dtype != HP_BF16) {
+        hp_status st = ensure_dense(op->mesh);
+        if (st) return st;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    // median graph time of the current strategies (the graph is rebuilt first)
+    auto time_graph = [&](float& t) -> hp_status {
+        if (op->graph) { cudaGraphExecDestroy(op->graph); op->graph = nullptr; }
+        hp_status st = hp_op_apply_graph(op, lambda, in, out, stream);
+        if (st) return st;
+        std::vector<float> v;
+        for (int r = 0; r < reps; ++r) {
+            cudaEventRecord(a, s);
+            st = hp_op_apply_graph(op, lambda, in, out, stream);
+            cudaEventRecord(b, s);
+            cudaError_t e = cudaEventSynchronize(b);
+            if (st) return st;
+            if (e != cudaSuccess) return cuda_fail(e, "hp_op_schedule_graph");
+            float x = 0.f;
+            cudaEventElapsedTime(&x, a, b);
+            v.push_back(x);
+        }
+        std::sort(v.begin(), v.end());
+        t = v[v.size() / 2];
+        return HP_OK;
+    };
+    float best = 0.f;
+    hp_status st = time_graph(best);
+    for (int pass = 0; pass < passes && !st; ++pass) {
+        bool changed = false;
+        for (size_t i = 0; i < op->strat.size() && !st; ++i) {
+            const int cur = op->strat[i];
+            for (int k = 0; k < 3 && !st; ++k) {
+                if (k == op->strat[i] || !strategy_available(op, i, k)) continue;
+                const int prev = op->strat[i];
+                op->strat[i] = k;
+                float t = 0.f;
+                st = time_graph(t);
+                if (!st && t < 0.99f * best) best = t;
+                else op->strat[i] = prev;
+            }
+            changed = changed || op->strat[i] != cur;
+        }
+        if (!changed) break;
+    }
+    if (op->graph) { cudaGraphExecDestroy(op->graph); op->graph = nullptr; }   // built for a trial
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (st) return st;
+    if (ms) *ms = best;
+    return check_device_error(op->mesh, op->d_err, nullptr, "hp_op_schedule_graph");
+}
+
 hp_status hp_op_sync(hp_op op, void* stream) {
     if (!op) { set_error("hp_op_sync: null op"); return HP_ERR_ARG; }
     DeviceGuard guard(op->mesh->device);

@@ -30,7 +30,8 @@ HP_FP64, HP_FP32, HP_TF32, HP_BF16 = range(4)
 
 EXPORTED = ["hp_mesh_create", "hp_mesh_layout", "hp_geom_factors", "hp_geom_copy", "hp_op_create",
             "hp_op_apply", "hp_op_apply_graph", "hp_op_tune", "hp_op_tiles", "hp_op_strategies",
-            "hp_op_block_features", "hp_op_schedule", "hp_op_schedule_exhaustive", "hp_op_sync", "hp_op_work",
+            "hp_op_block_features", "hp_op_schedule", "hp_op_schedule_exhaustive", "hp_op_schedule_graph",
+            "hp_op_sync", "hp_op_work",
             "hp_op_block_work", "hp_op_apply_block",
             "hp_op_destroy", "hp_mesh_destroy", "hp_status_str", "hp_last_error",
             "hp_mlp_create", "hp_mlp_info", "hp_mlp_params", "hp_mlp_forward", "hp_mlp_grad", "hp_mlp_adam_step",
@@ -65,6 +66,7 @@ _lib.hp_op_strategies.argtypes = [_vp, _vp, ctypes.c_int64, ctypes.c_int]
 _lib.hp_op_block_features.argtypes = [_vp, _vp, ctypes.c_int64]
 _lib.hp_op_schedule.argtypes = [_vp, _vp, _vp]
 _lib.hp_op_schedule_exhaustive.argtypes = [_vp, ctypes.c_double, _vp, _vp, _vp, _vp]
+_lib.hp_op_schedule_graph.argtypes = [_vp, ctypes.c_double, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp]
 _lib.hp_mlp_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_int,
                                ctypes.POINTER(_vp)]
 _lib.hp_mlp_info.argtypes = [_vp, _vp, _vp, _vp, _vp]
@@ -88,7 +90,7 @@ _lib.hp_last_error.restype = ctypes.c_char_p
 for _f in ("hp_mesh_create", "hp_mesh_layout", "hp_geom_factors", "hp_geom_copy", "hp_op_create",
            "hp_op_apply", "hp_op_apply_graph", "hp_op_tune", "hp_op_tiles", "hp_op_sync", "hp_op_work",
            "hp_op_block_work", "hp_op_apply_block", "hp_op_strategies", "hp_op_block_features", "hp_op_schedule", "hp_op_schedule_exhaustive",
-           "hp_mlp_create", "hp_mlp_info", "hp_mlp_params", "hp_mlp_forward", "hp_mlp_grad", "hp_mlp_adam_step"):
+           "hp_op_schedule_graph", "hp_mlp_create", "hp_mlp_info", "hp_mlp_params", "hp_mlp_forward", "hp_mlp_grad", "hp_mlp_adam_step"):
     getattr(_lib, _f).restype = ctypes.c_int
 
 
@@ -247,6 +249,14 @@ def hp_op_schedule_exhaustive(op, lam, x, y, n_blocks, stream=None):
     _check(_lib.hp_op_schedule_exhaustive(op, float(lam), _ptr(x), _ptr(y), t.ctypes.data, _stream(stream)),
            "hp_op_schedule_exhaustive")
     return t
+
+
+def hp_op_schedule_graph(op, lam, x, y, reps=5, passes=1, stream=None):
+    """Coordinate descent on the concurrent graph's time; returns its final median ms."""
+    t = ctypes.c_float(0.0)
+    _check(_lib.hp_op_schedule_graph(op, float(lam), _ptr(x), _ptr(y), int(reps), int(passes), ctypes.byref(t),
+                                     _stream(stream)), "hp_op_schedule_graph")
+    return t.value
 
 
 def hp_mlp_create(n_in, n_hidden, n_out, seed=0, device=0):

@@ -148,3 +148,53 @@ def test_tf32_schedules_only_built_strategies(hp):
     finally:
         hp.hp_mlp_destroy(m)
         hp.hp_mesh_destroy(h)
+
+
+def test_graph_schedule_keeps_valid_strategies_and_results(hp):
+    """The graph-aware search chooses only strategies built for each block (TF32:
+    FP32 sum factorisation or the tensor-core elemental matrix, the latter only
+    up to 256 modes), returns a positive graph time, rejects bad arguments, and
+    the scheduled graph still matches the FP64 oracle within each block's bound
+    (TF32_TOL on tensor-core blocks, the FP32 bound elsewhere)."""
+    from oracle import operators as oracle_ops
+    from oracle.basis import n_modes
+    from tests.test_gpu_parity import fp32_tol, rel_err
+    from tests.test_gpu_tc import TF32_TOL
+    mesh = inputs.slab_mesh(2, 2, 4, (2, 7), order_seed=5, curved_rule="x_half")
+    keys = []
+    for k in zip(mesh["shape"].tolist(), mesh["P"].tolist(), mesh["curved"].tolist()):
+        if k not in keys:
+            keys.append(k)
+    nb = len(keys)
+    fits = np.array([n_modes(s, P) <= 256 for s, P, _ in keys])
+    h = hp.hp_mesh_create(mesh, 0)
+    try:
+        co, po, nc, nph = hp.hp_mesh_layout(h, mesh["n_elem"])
+        op = hp.hp_op_create(h, hp.HP_HELMHOLTZ, hp.HP_STRAT_ELEMAT, hp.HP_TF32)
+        try:
+            uh = inputs.random_coefficients(11, co)
+            x = torch.tensor(uh, device="cuda:0", dtype=torch.float32)
+            y = torch.zeros(nc, device="cuda:0", dtype=torch.float32)
+            for reps, passes in ((0, 1), (5, 0), (65, 1)):
+                with pytest.raises(hp.HpError) as ei:
+                    hp.hp_op_schedule_graph(op, 1.0, x, y, reps, passes)
+                assert ei.value.status == hp.HP_ERR_ARG
+            ms = hp.hp_op_schedule_graph(op, 1.0, x, y, 3, 2)
+            assert ms > 0
+            st = hp.hp_op_strategies(op, nb)
+            assert np.isin(st, [hp.HP_STRAT_SUMFAC, hp.HP_STRAT_ELEMAT]).all()
+            assert (st[~fits] == hp.HP_STRAT_SUMFAC).all()
+            y.zero_()
+            hp.hp_op_apply_graph(op, 1.3, x, y)
+            hp.hp_op_sync(op)
+            ref = oracle_ops.apply("helmholtz", mesh, uh.astype(np.float32).astype(np.float64), 1.3)
+            out = y.double().cpu().numpy()
+            for (s, P, c), strat in zip(keys, st):
+                els = np.nonzero((mesh["shape"] == s) & (mesh["P"] == P) & (mesh["curved"] == c))[0]
+                idx = np.concatenate([np.arange(co[e], co[e + 1]) for e in els])
+                tol = TF32_TOL if strat == hp.HP_STRAT_ELEMAT else fp32_tol(P)
+                assert rel_err(out[idx], ref[idx]) <= tol, (s, P, c, strat)
+        finally:
+            hp.hp_op_destroy(op)
+    finally:
+        hp.hp_mesh_destroy(h)
