@@ -41,6 +41,7 @@ MEASURED_TRAFFIC = {"sf_kernel<pyr,P8,f64>": 372166400}
 PROFILE_CASES = {
     "tc_tet8": (3, 8, 19456, "ELEMAT", "TF32"),
     "tc16_tet8": (3, 8, 19456, "ELEMAT", "BF16"),
+    "tc16_hex4": (0, 4, 65536, "ELEMAT", "BF16"),
     "sf32_hex4": (0, 4, 65536, "SUMFAC", "FP32"),
     "sf32_tet4": (3, 4, 65536, "SUMFAC", "FP32"),
 }
@@ -67,7 +68,7 @@ def parse():
     p.add_argument("--no-extra", action="store_true", help="skip the p-adaptive batched measurement")
     p.add_argument("--profile-case", default=None, choices=sorted(PROFILE_CASES),
                    help="run one small case for a profiler capture instead (tc_tet8 / tc16_tet8: TF32 / BF16 "
-                        "tensor-core Helmholtz, 19 456 curved tets, P = 8; sf32_hex4 / sf32_tet4: FP32 sum "
+                        "tensor-core Helmholtz, 19 456 curved tets, P = 8; tc16_hex4: BF16, 65 536 curved hexes, P = 4; sf32_hex4 / sf32_tet4: FP32 sum "
                         "factorisation, 65 536 curved hexes / tets, P = 4; three applies)")
     p.add_argument("--orders", default=None, help="comma-separated orders (default 1..8); for profiling runs")
     p.add_argument("--cells", type=int, default=None, help="cells per direction (default 16); for profiling runs")
