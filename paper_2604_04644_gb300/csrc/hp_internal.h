@@ -196,7 +196,6 @@ struct TCArgs {
     unsigned int* err;
 };
 constexpr int kTcMaxModes = 256;
-int tc_smem_bytes(int KP, int stage_bytes, int es);
 int tc_chunk_points();
 int64_t tc_geom_halves(int64_t n_elem, int nch);
 cudaError_t tc_geom_layout16(int shape, bool curved, const double* g, int NQp, const double* z, const double* w, int Q,

@@ -24,11 +24,13 @@
 // accumulators are in flight and the V' tiles are double-buffered, so the
 // forward MMAs run two chunks ahead of the metric and the metric of chunk k
 // overlaps the backward MMAs of chunk k-1.
-// Roles: warps 0-15 gather U, run the metric and write the outputs (warp w
-// reads TMEM lanes 32 (w mod 4).. and points 4 (w / 4).. of each chunk: four
-// warps per TMEM lane quarter, so each scheduler holds four of them to hide
-// the latency of the tensor-memory loads and the factor loads); warp 16 issues
-// the bulk copies; warp 17 issues the MMAs.  Every wait is
+// Roles: warps 0..EW-1 gather U, run the metric and write the outputs (warp
+// w reads TMEM lanes 32 (w mod 4).. and points kPts (w / 4).. of each chunk;
+// EW = 16, one CTA per SM: four warps per lane quarter, 4 points each, so each
+// scheduler holds four of them to hide the tensor-memory and factor loads;
+// EW = 8, two CTAs per SM for BF16 blocks of at most 64 modes: two pipelines
+// per SM overlap their hand-offs); warp EW issues the bulk copies; warp EW + 1
+// issues the MMAs.  Every wait is
 // bounded; a timeout latches DERR_TIMEOUT, stops every role, drains the
 // copies and MMAs in flight and frees the tensor memory before the CTA exits.
 #include <cuda_bf16.h>
@@ -41,17 +43,28 @@ namespace hp {
 namespace {
 
 constexpr int kNPT = 16;          // quadrature points per chunk
-constexpr int kEpiWarps = 16;     // epilogue warps: kGroups per TMEM lane quarter
-constexpr int kGroups = kEpiWarps / 4;
-constexpr int kPts = kNPT / kGroups;     // points of a chunk per epilogue thread
-constexpr int kRows = 128 / kEpiWarps;   // tile rows per epilogue warp (coefficient gather and output)
 constexpr int kMaxStages = 8;     // bulk-copy ring: as many stages (2..8) as fit in shared memory
-constexpr int kTmemCols = 512;
 constexpr int kFwdBufs = 3;       // forward accumulators in flight: the forward MMAs run two chunks ahead
 constexpr int kOutCol = kFwdBufs * 4 * 16;   // TMEM column of the output accumulator
-constexpr int kEpi = 32 * kEpiWarps;   // epilogue threads
-constexpr int kThreads = kEpi + 64;     // + the producer warp and the MMA warp
 constexpr int kSliceBytes = 4 * kNPT * 128;   // forward operand slice: 64 rows x 128 bytes of modes
+// metric-factor layout: runs of kGeoPts points, kGeoGroups runs per chunk
+constexpr int kGeoGroups = 4, kGeoPts = kNPT / kGeoGroups;
+
+// Epilogue shape: EW epilogue warps, EW / 4 per TMEM lane quarter, each thread
+// taking kPts points of a chunk.  EW = 16: one CTA per SM holding all 512 TMEM
+// columns; EW = 8: two CTAs per SM with 256 columns each (blocks of at most 64
+// modes, whose output accumulator fits beside the forward ones), so that two
+// MMA / epilogue pipelines overlap their hand-offs on one SM.
+template <int EW>
+struct Epi {
+    static constexpr int kGroups = EW / 4;
+    static constexpr int kPts = kNPT / kGroups;      // points of a chunk per epilogue thread
+    static constexpr int kRows = 128 / EW;           // tile rows per warp (coefficient gather and output)
+    static constexpr int kEpi = 32 * EW;             // epilogue threads
+    static constexpr int kThreads = kEpi + 64;       // + the producer warp and the MMA warp
+    static constexpr int kCtas = EW == 16 ? 1 : 2;   // CTAs per SM
+    static constexpr int kTmemCols = 512 / kCtas;
+};
 
 // Operand element type: TF32 (ES = 4, kind::tf32, K = 8 per MMA) or BF16
 // (ES = 2, kind::f16, K = 16 per MMA); every MMA K step is 32 bytes.  The
@@ -77,11 +90,12 @@ struct Op {
         if constexpr (ES == 4) return tc::sw64_offset(r, p);
         else return r * 32 + ((((p * 2) >> 4) ^ ((r >> 2) & 1)) << 4);
     }
-    // kPts consecutive points p.. of row r of a 16-point tile
+    // NPTS consecutive points p.. of row r of a 16-point tile
+    template <int NPTS>
     __device__ static void put_pts(unsigned char* tile, uint32_t r, uint32_t p, const float* x) {
-        if constexpr (ES * kPts >= 16) {
+        if constexpr (ES * NPTS >= 16) {
 #pragma unroll
-            for (int p0 = 0; p0 < kPts; p0 += 16 / ES) *reinterpret_cast<uint4*>(tile + offv(r, p + p0)) = pack(x + p0);
+            for (int p0 = 0; p0 < NPTS; p0 += 16 / ES) *reinterpret_cast<uint4*>(tile + offv(r, p + p0)) = pack(x + p0);
         } else {      // BF16, 4 points: the half of a 16-byte chunk at (p mod 8) * 2
             const __nv_bfloat162 h0 = __floats2bfloat162_rn(x[0], x[1]), h1 = __floats2bfloat162_rn(x[2], x[3]);
             *reinterpret_cast<uint2*>(tile + offv(r, p) + (p & 7) * 2) =
@@ -120,9 +134,9 @@ struct Ring {
     }
 };
 
-// this thread's kPts FP16 metric factors of one factor: 8 bytes (4 points) or 16 (8 points)
-using GV = std::conditional_t<kPts == 8, uint4, uint2>;
-__device__ __forceinline__ GV ldg_gv(const GV* p) { return __ldg(p); }
+// an epilogue thread's NP FP16 metric factors of one factor: 8 bytes (4 points) or 16 (8 points)
+template <int NP>
+using GVt = std::conditional_t<NP == 8, uint4, uint2>;
 __device__ __forceinline__ uint32_t gv_word(const uint4& g, int i) { return i == 0 ? g.x : i == 1 ? g.y : i == 2 ? g.z : g.w; }
 __device__ __forceinline__ uint32_t gv_word(const uint2& g, int i) { return i == 0 ? g.x : g.y; }
 
@@ -165,9 +179,12 @@ __device__ __forceinline__ void arrive_warp(uint64_t* bar) {
 }
 
 
-template <int ES>
-__global__ void __launch_bounds__(kThreads, 1) tc_emat_kernel(const __grid_constant__ TCArgs a) {
+template <int ES, int EW>
+__global__ void __launch_bounds__(Epi<EW>::kThreads, Epi<EW>::kCtas) tc_emat_kernel(const __grid_constant__ TCArgs a) {
     using O = Op<ES>;
+    using E = Epi<EW>;
+    constexpr int kGroups = E::kGroups, kPts = E::kPts, kRows = E::kRows;
+    using GV = GVt<kPts>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // the swizzle patterns are taken from shared-memory address bits: align to 1 KB
     unsigned char* smem = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
@@ -188,28 +205,28 @@ __global__ void __launch_bounds__(kThreads, 1) tc_emat_kernel(const __grid_const
 
     if (tid == 0) {
         for (int s = 0; s < nst; ++s) { mbar_init(&B->full[s], 1); mbar_init(&B->empty[s], 1); }
-        for (int j = 0; j < 2; ++j) mbar_init(&B->u_full[j], kEpiWarps);
+        for (int j = 0; j < 2; ++j) mbar_init(&B->u_full[j], EW);
         for (int b = 0; b < kFwdBufs; ++b) {
             mbar_init(&B->fwd_full[b], 1);
-            mbar_init(&B->fwd_empty[b], kEpiWarps);
+            mbar_init(&B->fwd_empty[b], EW);
         }
         for (int b = 0; b < 2; ++b) {
-            mbar_init(&B->vp_full[b], kEpiWarps);
+            mbar_init(&B->vp_full[b], EW);
             mbar_init(&B->vp_empty[b], 1);
         }
         mbar_init(&B->out_full, 1);
-        mbar_init(&B->out_empty, kEpiWarps);
+        mbar_init(&B->out_empty, EW);
         mbar_init(&B->drain, 1);
-        mbar_init(&B->epi, kEpiWarps);
+        mbar_init(&B->epi, EW);
         B->abort = 0;
     }
-    if (warp == 0) { tc::tmem_alloc(&B->tmem, kTmemCols); tc::tmem_relinquish(); }
+    if (warp == 0) { tc::tmem_alloc(&B->tmem, E::kTmemCols); tc::tmem_relinquish(); }
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
     const uint32_t tbase = B->tmem;
 
-    if (warp == kEpiWarps) {
+    if (warp == EW) {
         // ---------------------------------------------------------------- producer
         if (lane == 0) {
             int slot = 0;
@@ -255,7 +272,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_emat_kernel(const __grid_const
                 }
         }
         __syncwarp();
-    } else if (warp == kEpiWarps + 1) {
+    } else if (warp == EW + 1) {
         // ---------------------------------------------------------------- MMA issuer
         if (lane == 0) {
             const uint32_t id_f = tc::instr_desc(O::FMT, 128, kNPT * (a.c1 - a.c0));
@@ -431,16 +448,27 @@ __global__ void __launch_bounds__(kThreads, 1) tc_emat_kernel(const __grid_const
             // the next tile's U is gathered while this tile's last MMAs run
             if (a.ubufs == 1 || ntile == 0) gather_u(0, offs);
             const float isc = a.gscale[tile * 128 + r];     // 2^-k of element r's FP16 factors (0: padding)
-            const GV* gt = reinterpret_cast<const GV*>(a.geom16) + (tile * a.nch * 7 * kGroups + h) * 128 + r;
+            // this thread's points h kPts.. are kPts / kGeoPts runs of the factor layout
+            const uint2* gt = reinterpret_cast<const uint2*>(a.geom16) +
+                              (tile * a.nch * 7 * kGeoGroups + h * (kPts / kGeoPts)) * 128 + r;
             // the seven factors of chunk k at this thread's kPts points (kPts halves each)
             auto load_geom = [&](int k, GV (&G)[7]) {
 #pragma unroll
-                for (int f = 0; f < 7; ++f)
-                    G[f] = (f == 6 || a.c1 > 1) ? ldg_gv(gt + ((int64_t)k * 7 + f) * (kGroups * 128)) : GV{};
+                for (int f = 0; f < 7; ++f) {
+                    const uint2* q = gt + ((int64_t)k * 7 + f) * (kGeoGroups * 128);
+                    const bool need = f == 6 || a.c1 > 1;
+                    if constexpr (kPts == kGeoPts) {
+                        G[f] = need ? __ldg(q) : uint2{0u, 0u};
+                    } else {
+                        const uint2 lo = need ? __ldg(q) : uint2{0u, 0u}, hi = need ? __ldg(q + 128) : uint2{0u, 0u};
+                        G[f] = make_uint4(lo.x, lo.y, hi.x, hi.y);
+                    }
+                }
             };
             // metric of chunk k: forward accumulator -> V' tile (components
             // outside [c0, c1) are computed from unused columns and discarded)
-            auto process = [&](int k, const GV (&Gh)[7]) -> bool {
+            // after_metric runs once the factors Gh are consumed (one-set rotation)
+            auto process = [&](int k, GV (&Gh)[7], auto&& after_metric) -> bool {
                 const uint32_t g = g0 + (uint32_t)(k - kb), b = g & 1u, use = g >> 1;
                 const uint32_t bf = g % kFwdBufs, usef = g / kFwdBufs;     // forward accumulator buffer
                 if (!wait_warp(&B->fwd_full[bf], usef & 1u, B, a.err)) return false;
@@ -469,18 +497,28 @@ __global__ void __launch_bounds__(kThreads, 1) tc_emat_kernel(const __grid_const
                         o[3][p] = isc * (gf(2) * v1 + gf(4) * v2 + gf(5) * v3);
                     }
                 }
+                after_metric();
                 // the V' tile b is free once the backward MMAs that last read it completed
                 if (!wait_warp(&B->vp_empty[b], (use & 1u) ^ 1u, B, a.err)) return false;
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
                     if (c < a.c0 || c >= a.c1) continue;
-                    O::put_pts(sV + (size_t)(b * 4 + c) * O::VBYTES, r, h * kPts, o[c]);
+                    O::template put_pts<kPts>(sV + (size_t)(b * 4 + c) * O::VBYTES, r, h * kPts, o[c]);
                 }
                 tc::fence_async_smem();
                 arrive_warp(&B->vp_full[b]);
                 return true;
             };
-            if constexpr (ES == 2) {
+            auto none = [] {};
+            if constexpr (EW == 8) {
+                // one register set (two CTAs per SM leave 96 registers a thread): the
+                // next chunk's factors are loaded as soon as the metric consumed these
+                GV ga[7];
+                if (kb < ke) load_geom(kb, ga);
+                for (int k = kb; k < ke; ++k) {
+                    if (!(ok = process(k, ga, [&] { if (k + 1 < ke) load_geom(k + 1, ga); }))) break;
+                }
+            } else if constexpr (ES == 2) {
                 // factors one chunk ahead: two register sets in rotation (with
                 // sixteen epilogue warps the shorter BF16 chunks hide the load,
                 // and the registers saved avoid spills)
@@ -488,9 +526,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_emat_kernel(const __grid_const
                 if (kb < ke) load_geom(kb, ga);
                 for (int k = kb; k < ke; k += 2) {
                     if (k + 1 < ke) load_geom(k + 1, gb);
-                    if (!(ok = process(k, ga)) || k + 1 >= ke) break;
+                    if (!(ok = process(k, ga, none)) || k + 1 >= ke) break;
                     if (k + 2 < ke) load_geom(k + 2, ga);
-                    if (!(ok = process(k + 1, gb))) break;
+                    if (!(ok = process(k + 1, gb, none))) break;
                 }
             } else {
                 // factors two chunks ahead: three register sets in rotation
@@ -499,11 +537,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_emat_kernel(const __grid_const
                 if (kb + 1 < ke) load_geom(kb + 1, gb);
                 for (int k = kb; k < ke; k += 3) {
                     if (k + 2 < ke) load_geom(k + 2, gc);
-                    if (!(ok = process(k, ga)) || k + 1 >= ke) break;
+                    if (!(ok = process(k, ga, none)) || k + 1 >= ke) break;
                     if (k + 3 < ke) load_geom(k + 3, ga);
-                    if (!(ok = process(k + 1, gb)) || k + 2 >= ke) break;
+                    if (!(ok = process(k + 1, gb, none)) || k + 2 >= ke) break;
                     if (k + 4 < ke) load_geom(k + 4, gb);
-                    if (!(ok = process(k + 2, gc))) break;
+                    if (!(ok = process(k + 2, gc, none))) break;
                 }
             }
             if (!ok) break;
@@ -554,7 +592,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_emat_kernel(const __grid_const
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
-    if (warp == 0) tc::tmem_dealloc(tbase, kTmemCols);
+    if (warp == 0) tc::tmem_dealloc(tbase, E::kTmemCols);
 }
 
 // zero the block's output coefficients (the parts of a tile add into them)
@@ -573,12 +611,12 @@ __global__ void zero_coeffs_kernel(float* out, const int64_t* coeff_off, int64_t
 // k_e = 14 - floor(log2 max|G_e|): the largest lies in [2^14, 2^15) (FP16 ends
 // at 65504) and only entries below 2^-28 of it fall into FP16's subnormal
 // range; the epilogue multiplies its outputs by 2^-k_e (exact in FP32).
-// Layout [tile][chunk][7 factors][kGroups point groups][128 elements][kPts
-// points], one epilogue thread's points of a factor contiguous and a warp's 32
+// Layout [tile][chunk][7 factors][kGeoGroups point runs][128 elements][kGeoPts
+// points], an epilogue thread's run of a factor contiguous and a warp's 32
 // elements adjacent; padded points and elements stay zero
 // (the buffer is cleared first), and so does the scale of a padded element.
 __host__ __device__ constexpr int64_t geom16_index(int64_t tile, int k, int f, int p, int r, int nch) {
-    return ((((tile * nch + k) * 7 + f) * kGroups + p / kPts) * 128 + r) * kPts + p % kPts;
+    return ((((tile * nch + k) * 7 + f) * kGeoGroups + p / kGeoPts) * 128 + r) * kGeoPts + p % kGeoPts;
 }
 
 // factors of element e at point l: curved from the FP64 factors [n][7][NQp];
@@ -647,24 +685,45 @@ cudaError_t geom16_shape(bool curved, const double* g, int NQp, const double* z,
 
 }  // namespace
 
+// Shared memory a CTA may take: all of the SM's (one CTA per SM) or half of it
+// (two).  The smallest request keeps the tensor-memory allocations of the CTAs
+// that share an SM within its 512 columns: a one-CTA kernel (512 columns)
+// leaves less than a two-CTA kernel's CTA (256 columns) needs, and two-CTA
+// CTAs leave no room for a third.
+constexpr int kSmemCap1 = 227 * 1024, kSmemCap2 = 113 * 1024;
+constexpr int kSmemMin1 = 152 * 1024, kSmemMin2 = 77 * 1024;
+
 // ring stages (2..kMaxStages) that fit beside ubufs U buffers and the V' tiles
-int tc_stages(int KP, int stage_bytes, int es, int ubufs) {
+int tc_stages(int KP, int stage_bytes, int es, int ubufs, int cap) {
     const int base = 2048 + ubufs * 128 * KP * es + 8 * 128 * kNPT * es;   // alignment slack + barriers + U + V'
     for (int st = kMaxStages; st >= 2; --st)
-        if (base + st * stage_bytes <= 227 * 1024) return st;
+        if (base + st * stage_bytes <= cap) return st;
     return 0;
 }
 
-// a second U buffer where it leaves a deep ring (or costs no stage)
-int tc_ubufs(int KP, int stage_bytes, int es) {
-    const int s2 = tc_stages(KP, stage_bytes, es, 2);
-    return (s2 >= 6 || s2 == tc_stages(KP, stage_bytes, es, 1)) ? 2 : 1;
-}
-
-int tc_smem_bytes(int KP, int stage_bytes, int es) {
-    const int ub = tc_ubufs(KP, stage_bytes, es);
-    int b = 2048 + ub * 128 * KP * es + 8 * 128 * kNPT * es + tc_stages(KP, stage_bytes, es, ub) * stage_bytes;
-    return b < 116 * 1024 ? 116 * 1024 : b;    // at most one CTA (and one TMEM allocation) per SM
+// launch plan: CTAs per SM, U buffers, ring stages, dynamic shared memory.
+// Two CTAs per SM for BF16 blocks whose output accumulator fits beside the
+// forward ones in 256 columns (N_P <= 64) and whose buffers fit half the SM;
+// a second U buffer where it leaves a deep ring (or costs no stage).
+struct TcPlan {
+    int ctas, ubufs, stages, smem;
+};
+TcPlan tc_plan(int KP, int NPpad, int stage_bytes, int es) {
+    const int need = es == 2 ? kFwdBufs + 1 : 2;    // BF16 holds a stage kFwdBufs - 1 chunks
+    for (int ctas = 2; ctas >= 1; --ctas) {
+        if (ctas == 2 && !(es == 2 && NPpad <= kOutCol / 3 && kOutCol + NPpad <= 256)) continue;
+        const int cap = ctas == 2 ? kSmemCap2 : kSmemCap1;
+        const int s1 = tc_stages(KP, stage_bytes, es, 1, cap);
+        if (s1 < need) continue;
+        const int s2 = tc_stages(KP, stage_bytes, es, 2, cap);
+        const int ub = (s2 >= 6 || (s2 == s1 && s2 >= need)) ? 2 : 1;
+        const int st = ub == 2 ? s2 : s1;
+        int smem = 2048 + ub * 128 * KP * es + 8 * 128 * kNPT * es + st * stage_bytes;
+        const int mn = ctas == 2 ? kSmemMin2 : kSmemMin1;
+        if (smem < mn) smem = mn;
+        return {ctas, ub, st, smem};
+    }
+    return {1, 1, 0, 0};
 }
 
 int tc_chunk_points() { return kNPT; }
@@ -690,20 +749,21 @@ cudaError_t tc_emat_launch(const TCArgs& a, cudaStream_t s) {
     const int64_t ntiles = (a.n_elem + 127) / 128;
     if (ntiles <= 0) return cudaSuccess;
     TCArgs b = a;
-    b.ubufs = tc_ubufs(a.KP, a.stage_bytes, a.es);
-    b.stages = tc_stages(a.KP, a.stage_bytes, a.es, b.ubufs);
-    // BF16 holds a chunk's stage until its backward MMAs, kFwdBufs - 1 chunks later
-    if (b.stages < (a.es == 2 ? kFwdBufs + 1 : 2)) return cudaErrorInvalidValue;
-    const int smem = tc_smem_bytes(a.KP, a.stage_bytes, a.es);
-    auto kern = a.es == 2 ? tc_emat_kernel<2> : tc_emat_kernel<4>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    const TcPlan pl = tc_plan(a.KP, a.NPpad, a.stage_bytes, a.es);
+    if (pl.stages == 0) return cudaErrorInvalidValue;
+    b.ubufs = pl.ubufs;
+    b.stages = pl.stages;
+    auto kern = a.es == 4 ? tc_emat_kernel<4, 16> : pl.ctas == 2 ? tc_emat_kernel<2, 8> : tc_emat_kernel<2, 16>;
+    const int threads = pl.ctas == 2 ? Epi<8>::kThreads : Epi<16>::kThreads;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, pl.smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    // split the point chunks of a tile over CTAs until the grid covers the SMs
-    // (at least 4 chunks per part)
-    int64_t ns = (sms + ntiles - 1) / ntiles;
+    const int slots = sms * pl.ctas;
+    // split the point chunks of a tile over CTAs until the grid covers the
+    // CTA slots (at least 4 chunks per part)
+    int64_t ns = (slots + ntiles - 1) / ntiles;
     const int64_t cap = a.nch / 4 > 1 ? a.nch / 4 : 1;
     b.nsplit = (int)(ns < cap ? ns : cap);
     if (b.nsplit > 1) {
@@ -711,8 +771,8 @@ cudaError_t tc_emat_launch(const TCArgs& a, cudaStream_t s) {
         zero_coeffs_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a.out, a.coeff_off, a.n_elem, a.NP);
     }
     const int64_t nwork = ntiles * b.nsplit;
-    const int grid = (int)(nwork < sms ? nwork : sms);
-    kern<<<grid, kThreads, smem, s>>>(b);
+    const int grid = (int)(nwork < slots ? nwork : slots);
+    kern<<<grid, threads, pl.smem, s>>>(b);
     return cudaGetLastError();
 }
 
