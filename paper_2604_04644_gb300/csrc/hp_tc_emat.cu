@@ -702,16 +702,18 @@ int tc_stages(int KP, int stage_bytes, int es, int ubufs, int cap) {
 }
 
 // launch plan: CTAs per SM, U buffers, ring stages, dynamic shared memory.
-// Two CTAs per SM for BF16 blocks whose output accumulator fits beside the
-// forward ones in 256 columns (N_P <= 64) and whose buffers fit half the SM;
+// Two CTAs per SM (allow2: the block has at least two tiles per SM, so both
+// slots fill without splitting tiles) for BF16 blocks whose output accumulator
+// fits beside the forward ones in 256 columns (N_P <= 64) and whose buffers
+// fit half the SM;
 // a second U buffer where it leaves a deep ring (or costs no stage).
 struct TcPlan {
     int ctas, ubufs, stages, smem;
 };
-TcPlan tc_plan(int KP, int NPpad, int stage_bytes, int es) {
+TcPlan tc_plan(int KP, int NPpad, int stage_bytes, int es, bool allow2) {
     const int need = es == 2 ? kFwdBufs + 1 : 2;    // BF16 holds a stage kFwdBufs - 1 chunks
     for (int ctas = 2; ctas >= 1; --ctas) {
-        if (ctas == 2 && !(es == 2 && NPpad <= kOutCol / 3 && kOutCol + NPpad <= 256)) continue;
+        if (ctas == 2 && !(allow2 && es == 2 && NPpad <= kOutCol / 3 && kOutCol + NPpad <= 256)) continue;
         const int cap = ctas == 2 ? kSmemCap2 : kSmemCap1;
         const int s1 = tc_stages(KP, stage_bytes, es, 1, cap);
         if (s1 < need) continue;
@@ -749,7 +751,10 @@ cudaError_t tc_emat_launch(const TCArgs& a, cudaStream_t s) {
     const int64_t ntiles = (a.n_elem + 127) / 128;
     if (ntiles <= 0) return cudaSuccess;
     TCArgs b = a;
-    const TcPlan pl = tc_plan(a.KP, a.NPpad, a.stage_bytes, a.es);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const TcPlan pl = tc_plan(a.KP, a.NPpad, a.stage_bytes, a.es, ntiles >= 2 * (int64_t)sms);
     if (pl.stages == 0) return cudaErrorInvalidValue;
     b.ubufs = pl.ubufs;
     b.stages = pl.stages;
@@ -757,9 +762,6 @@ cudaError_t tc_emat_launch(const TCArgs& a, cudaStream_t s) {
     const int threads = pl.ctas == 2 ? Epi<8>::kThreads : Epi<16>::kThreads;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, pl.smem);
     if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int slots = sms * pl.ctas;
     // split the point chunks of a tile over CTAs until the grid covers the
     // CTA slots (at least 4 chunks per part)

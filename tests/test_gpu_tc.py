@@ -148,3 +148,21 @@ def test_tf32_single_element(hp):
         ref = oracle_ops.apply("helmholtz", mesh, x.astype(np.float32).astype(np.float64), 0.7)
         y, _ = run_tc(hp, mesh, "helmholtz", x, 0.7)
         assert rel_err(y, ref) <= TF32_TOL, shape
+
+
+@pytest.mark.parametrize("shape,P,curved", [(3, 2, True), (3, 4, True), (2, 4, False)])
+def test_bf16_two_ctas_per_sm(hp, shape, P, curved):
+    """BF16 blocks of at most 64 modes with at least two 128-element tiles per SM
+    (40 960 elements = 320 tiles on 152 SMs) run two CTAs per SM with eight
+    epilogue warps each: sampled elements against the oracle within BF16_TOL."""
+    mesh = inputs.replicated_mesh(shape, P, 40960, curved=curved)
+    co, _ = oracle_ops.layout(mesh)
+    x = inputs.random_coefficients(91, co)
+    y, strat = run_tc(hp, mesh, "helmholtz", x, 0.9, hp.HP_BF16)
+    assert strat.tolist() == [hp.HP_STRAT_ELEMAT]
+    assert not np.isnan(y).any()
+    rng = np.random.default_rng(7)
+    sample = np.unique(np.concatenate([rng.choice(mesh["n_elem"], 120, replace=False), [0, mesh["n_elem"] - 1]]))
+    ref = oracle_ops.apply("helmholtz", mesh, x.astype(np.float32).astype(np.float64), 0.9, elems=sample)
+    idx = np.concatenate([np.arange(co[e], co[e + 1]) for e in sample])
+    assert rel_err(y[idx], ref[idx]) <= BF16_TOL
