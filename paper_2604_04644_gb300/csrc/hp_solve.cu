@@ -7,8 +7,10 @@
 // CSR transpose of the gather map in a fixed order (deterministic), with
 // Dirichlet rows zeroed.  Jacobi-preconditioned CG in FP64, or iterative
 // refinement with an FP64 residual around Jacobi-PCG solves in FP32 (the
-// element operator then runs in FP32, HBM-bound, instead of on the slow FP64
-// pipe).
+// element operator then runs in FP32 sum factorisation or on the TF32 / BF16
+// tensor cores instead of on the slow FP64 pipe).  Where every index fits 32
+// bits the CG loop runs on 4-byte signed maps with fused kernels and one host
+// round trip per iteration (pcg_fused).
 #include <algorithm>
 #include <cmath>
 #include <string>
