@@ -10,6 +10,13 @@ GDOF/s = output elemental DOFs / seconds / 1e9 (the paper's BK metric).
 
 Under torchrun (N > 1) every rank runs the full workload on its own GPU (weak
 scaling, no data-path collective); time is the max over ranks.
+
+Besides the timed step, rank 0 of a one-GPU run adds (unless --no-extra):
+per shape/order GDOF/s, the 192 000-element p-adaptive batched apply (FP64 and
+the reduced-precision graph forms), a strategy table, the FP32 / TF32 / BF16
+forms of the bench mesh with their error against FP64, and the time to solution
+of the assembled Helmholtz problem on ~1M elements (FP64 PCG against the
+mixed-precision forms, --no-solve skips it).
 """
 import argparse
 import json
@@ -65,7 +72,9 @@ def parse():
                    help="run the learned cost-model pipeline (timings, GPU training, held-out schedules) instead")
     p.add_argument("--solve", action="store_true",
                    help="assembled Helmholtz solve (time to 1e-10): FP64 PCG vs mixed FP32 PCG + FP64 refinement")
-    p.add_argument("--no-extra", action="store_true", help="skip the p-adaptive batched measurement")
+    p.add_argument("--no-extra", action="store_true",
+                   help="skip the p-adaptive, strategy, precision and time-to-solution measurements")
+    p.add_argument("--no-solve", action="store_true", help="skip the time-to-solution measurement (64^3 cells)")
     p.add_argument("--profile-case", default=None, choices=sorted(PROFILE_CASES),
                    help="run one small case for a profiler capture instead (tc_tet8 / tc16_tet8: TF32 / BF16 "
                         "tensor-core Helmholtz, 19 456 curved tets, P = 8; tc16_hex4: BF16, 65 536 curved hexes, P = 4; sf32_hex4 / sf32_tet4: FP32 sum "
@@ -646,7 +655,7 @@ def run_solve(local, cells, order=4, lam=1.0, tol=1e-10):
         out["speedup_%s_vs_fp64" % tag] = round(out["fp64_pcg"]["seconds"] / out[name]["seconds"], 3)
     hp.hp_c0_destroy(c0)
     hp.hp_mesh_destroy(h)
-    print(json.dumps({"solve": out}), flush=True)
+    return out
 
 
 def run_profile_case(name, local):
@@ -678,7 +687,7 @@ def main():
         return
     if args.solve:
         if rank == 0:
-            run_solve(local, args.cells or 64)
+            print(json.dumps({"solve": run_solve(local, args.cells or 64)}), flush=True)
         return
     if args.costmodel:
         if rank == 0:
@@ -756,6 +765,11 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline()
+    # time to solution of the assembled problem (64^3 cells, ~1M elements, P = 4):
+    # FP64 PCG against the mixed-precision forms, on one GPU only
+    solve = None
+    if rank == 0 and world == 1 and not args.no_extra and not args.no_solve:
+        solve = run_solve(local, 64)
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 4), "unit": "GDOF/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
@@ -767,7 +781,8 @@ def main():
                            "l2": "flushed (256 MiB write) before every apply, outside the timed events"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                 "clocks": clk.summary(), "per_order": per_order, "per_shape_order": table,
-                "p_adaptive": batched, "strategies_gdofs_f64": strategies, "precision_forms": forms}
+                "p_adaptive": batched, "strategies_gdofs_f64": strategies, "precision_forms": forms,
+                "time_to_solution": solve}
         print(json.dumps(line), flush=True)
     for w in work:
         from paper_2604_04644_gb300 import hp
