@@ -73,6 +73,7 @@ __global__ void __launch_bounds__(256, (sf_min_blocks<SHAPE, P, T, TILE>())) sf_
     // tasks to keep the FP64 pipe, the limit there, busy)
     constexpr bool LINES = sizeof(T) == 4;
     constexpr int kU = 4;      // FP32: loop iterations per thread whose global loads are issued together
+    constexpr int kUG = 8;     // the same for the coefficient gather (one batch for most blocks)
 
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
@@ -118,12 +119,12 @@ __global__ void __launch_bounds__(256, (sf_min_blocks<SHAPE, P, T, TILE>())) sf_
             // (slots a = 0, 1 take the sum and the difference of the two coefficients,
             // the inputs of the parity-form eta1 table)
             if constexpr (LINES) {
-                // FP32 (the passes are cheap, the memory latency is not): kU slots
+                // FP32 (the passes are cheap, the memory latency is not): kUG slots
                 // per thread have their loads issued before any is stored
-                for (int base = tid; base < EPB * N3; base += NT * kU) {
-                    T v[kU];
+                for (int base = tid; base < EPB * N3; base += NT * kUG) {
+                    T v[kUG];
 #pragma unroll
-                    for (int u = 0; u < kU; ++u) {
+                    for (int u = 0; u < kUG; ++u) {
                         const int idx = base + u * NT;
                         v[u] = T(0);
                         if (idx < EPB * N3) {
@@ -137,7 +138,7 @@ __global__ void __launch_bounds__(256, (sf_min_blocks<SHAPE, P, T, TILE>())) sf_
                         }
                     }
 #pragma unroll
-                    for (int u = 0; u < kU; ++u) {
+                    for (int u = 0; u < kUG; ++u) {
                         const int idx = base + u * NT;
                         if (idx < EPB * N3) {
                             const int e = idx / N3;
