@@ -180,3 +180,25 @@ def test_jacobi_diagonal_matches_unit_vector_applies(hp, P):
         assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max(), np.argmax(np.abs(got - ref))
     finally:
         pr.close()
+
+
+@pytest.mark.parametrize("mixed", [0, 3])
+def test_solve_is_deterministic(hp, mixed):
+    """The CG loop's reductions use a fixed grid and sum in a fixed order, and
+    alpha / beta stay on the device: two solves from the same start give the
+    same iterates bit for bit and the same statistics."""
+    mesh = inputs.c0_slab_mesh(4, 4, curved=True)
+    pr = Problem(hp, mesh)
+    try:
+        xs, st = [], []
+        for _ in range(2):
+            x = torch.zeros(pr.ng, device="cuda:0", dtype=torch.float64)
+            rc, stats = hp.hp_solve(pr.c0, LAM, pr.b, x, tol=1e-11, mixed=mixed, inner_tol=1e-2 if mixed else 1e-4)
+            assert rc == hp.HP_OK, stats
+            xs.append(x.cpu().numpy())
+            st.append(stats)
+        assert np.array_equal(xs[0], xs[1])
+        assert st[0] == st[1]
+        assert st[0]["rel_residual"] <= 1e-11
+    finally:
+        pr.close()
