@@ -182,23 +182,30 @@ def test_jacobi_diagonal_matches_unit_vector_applies(hp, P):
         pr.close()
 
 
-@pytest.mark.parametrize("mixed", [0, 3])
+@pytest.mark.parametrize("mixed", [0, 1, 3])
 def test_solve_is_deterministic(hp, mixed):
     """The CG loop's reductions use a fixed grid and sum in a fixed order, and
-    alpha / beta stay on the device: two solves from the same start give the
-    same iterates bit for bit and the same statistics."""
+    alpha / beta stay on the device: with the FP64 or FP32 sum-factorised
+    operator two solves from the same start give the same iterates bit for bit
+    and the same statistics.  The tensor-core operator adds the partial outputs
+    of a tile split over CTAs with FP32 atomics (order not fixed, differences at
+    FP32 rounding, far below BF16's): there the two solutions agree to the
+    solve's tolerance."""
     mesh = inputs.c0_slab_mesh(4, 4, curved=True)
     pr = Problem(hp, mesh)
     try:
         xs, st = [], []
         for _ in range(2):
             x = torch.zeros(pr.ng, device="cuda:0", dtype=torch.float64)
-            rc, stats = hp.hp_solve(pr.c0, LAM, pr.b, x, tol=1e-11, mixed=mixed, inner_tol=1e-2 if mixed else 1e-4)
+            rc, stats = hp.hp_solve(pr.c0, LAM, pr.b, x, tol=1e-11, mixed=mixed, inner_tol=1e-2 if mixed == 3 else 1e-4)
             assert rc == hp.HP_OK, stats
             xs.append(x.cpu().numpy())
             st.append(stats)
-        assert np.array_equal(xs[0], xs[1])
-        assert st[0] == st[1]
-        assert st[0]["rel_residual"] <= 1e-11
+        assert st[0]["rel_residual"] <= 1e-11 and st[1]["rel_residual"] <= 1e-11
+        if mixed in (0, 1):
+            assert np.array_equal(xs[0], xs[1])
+            assert st[0] == st[1]
+        else:
+            assert np.abs(xs[0] - xs[1]).max() <= 1e-9 * np.abs(xs[0]).max()
     finally:
         pr.close()
