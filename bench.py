@@ -75,6 +75,9 @@ def parse():
     p.add_argument("--no-extra", action="store_true",
                    help="skip the p-adaptive, strategy, precision and time-to-solution measurements")
     p.add_argument("--no-solve", action="store_true", help="skip the time-to-solution measurement (64^3 cells)")
+    p.add_argument("--block-table", action="store_true",
+                   help="GDOF/s of FP32 sum factorisation and the TF32 / BF16 tensor-core operator on large "
+                        "single-shape blocks instead")
     p.add_argument("--profile-case", default=None, choices=sorted(PROFILE_CASES),
                    help="run one small case for a profiler capture instead (tc_tet8 / tc16_tet8: TF32 / BF16 "
                         "tensor-core Helmholtz, 19 456 curved tets, P = 8; tc16_hex4: BF16, 65 536 curved hexes, P = 4; sf32_hex4 / sf32_tet4: FP32 sum "
@@ -658,6 +661,51 @@ def run_solve(local, cells, order=4, lam=1.0, tol=1e-10):
     return out
 
 
+# large single-shape blocks of the per-block precision table: (shape, P, elements)
+BLOCK_TABLE = [(3, 2, 65536), (3, 4, 65536), (3, 6, 32768), (3, 8, 32768), (2, 4, 65536), (2, 6, 32768),
+               (1, 4, 65536), (0, 4, 65536), (0, 5, 32768)]
+
+
+def run_block_table(local, reps=10):
+    """Helmholtz GDOF/s of FP32 sum factorisation and the TF32 / BF16 tensor-core
+    operator on large single-shape blocks, curved and affine (L2 flushed before
+    every apply; median of `reps`), one JSON line per block."""
+    import torch
+    from paper_2604_04644_gb300 import hp, inputs
+    torch.cuda.set_device(local)
+    dev = "cuda:%d" % local
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    for shape, P, n in BLOCK_TABLE:
+        for curved in (True, False):
+            mesh = inputs.replicated_mesh(shape, P, n, curved=curved)
+            h = hp.hp_mesh_create(mesh, local)
+            co, po, nc, nph = hp.hp_mesh_layout(h, mesh["n_elem"])
+            x = torch.tensor(inputs.random_coefficients(5, co), device=dev, dtype=torch.float32)
+            y = torch.zeros(nc, device=dev, dtype=torch.float32)
+            line = {"shape": SHAPES[shape], "P": P, "curved": curved, "elements": n}
+            for name, strat, dt in (("fp32_sumfac", hp.HP_STRAT_SUMFAC, hp.HP_FP32),
+                                    ("tf32_tensor_core", hp.HP_STRAT_ELEMAT, hp.HP_TF32),
+                                    ("bf16_tensor_core", hp.HP_STRAT_ELEMAT, hp.HP_BF16)):
+                op = hp.hp_op_create(h, hp.HP_HELMHOLTZ, strat, dt)
+                for _ in range(3):
+                    hp.hp_op_apply(op, 1.0, x, y)
+                ts = []
+                for _ in range(reps):
+                    flush.zero_()
+                    a = torch.cuda.Event(enable_timing=True)
+                    b = torch.cuda.Event(enable_timing=True)
+                    a.record()
+                    hp.hp_op_apply(op, 1.0, x, y)
+                    b.record()
+                    b.synchronize()
+                    ts.append(a.elapsed_time(b))
+                hp.hp_op_sync(op)
+                line[name] = round(nc / (statistics.median(ts) * 1e-3) / 1e9, 2)
+                hp.hp_op_destroy(op)
+            hp.hp_mesh_destroy(h)
+            print(json.dumps({"block_table": line}), flush=True)
+
+
 def run_profile_case(name, local):
     """One block of curved elements, three Helmholtz applies (the capture takes one)."""
     import torch
@@ -684,6 +732,10 @@ def main():
     if args.profile_case:
         if rank == 0:
             run_profile_case(args.profile_case, local)
+        return
+    if args.block_table:
+        if rank == 0:
+            run_block_table(local)
         return
     if args.solve:
         if rank == 0:
