@@ -3,14 +3,11 @@
 // instruction descriptor of kind::tf32 / kind::f16 MMAs with FP32
 // accumulation, commit to an mbarrier, and tensor-memory loads.
 //
-// Operand layouts: K-major, either without swizzle (a tile of R rows and K
-// columns stored as 8-row x 16-byte core matrices, each a contiguous 128-byte
-// block; core matrices that are neighbours along K are LBO bytes apart,
-// neighbours along the rows SBO bytes apart) or with the 128-byte / 64-byte
-// swizzle (rows of 128 / 64 bytes, 8-row atoms of 1024 / 512 bytes at
-// 1024-byte aligned bases; the 16-byte chunk c of row r sits at chunk
-// c ^ (r mod 8), resp. c ^ ((r / 2) mod 4), so that the tensor core reads
-// rows of different atoms from different shared-memory banks).
+// Operand layouts: swizzled, K-major or (for the BF16 backward operand)
+// MN-major: rows of 128 / 64 / 32 bytes in 8-row atoms at 1024-byte aligned
+// bases; with the 128-byte swizzle the 16-byte chunk c of row r sits at chunk
+// c ^ (r mod 8), with the 64-byte one at c ^ ((r / 2) mod 4), so that the
+// tensor core reads the rows of an atom from different shared-memory banks.
 #pragma once
 #include <cstdint>
 #include "hp_device.cuh"
@@ -18,17 +15,8 @@
 namespace hp {
 namespace tc {
 
-// byte offset of element (r, k) of a K-major no-swizzle tile with `kbytes`
-// bytes per row (a multiple of 16); elements of `es` bytes
-__host__ __device__ constexpr uint32_t kmajor_offset(uint32_t r, uint32_t k, uint32_t kbytes, uint32_t es) {
-    return (r >> 3) * (kbytes * 8) + ((k * es) >> 4) * 128 + (r & 7) * 16 + ((k * es) & 15);
-}
-
-// byte offset of 4-byte element (r, k) in a K-major tile with 128-byte
-// swizzle (k < 32) and 64-byte swizzle (k < 16)
-__host__ __device__ constexpr uint32_t sw128_offset(uint32_t r, uint32_t k) {
-    return r * 128 + ((((k * 4) >> 4) ^ (r & 7)) << 4) + ((k * 4) & 15);
-}
+// byte offset of 4-byte element (r, k) in a K-major tile with the 64-byte
+// swizzle (k < 16)
 __host__ __device__ constexpr uint32_t sw64_offset(uint32_t r, uint32_t k) {
     return r * 64 + ((((k * 4) >> 4) ^ ((r >> 1) & 3)) << 4) + ((k * 4) & 15);
 }
@@ -43,16 +31,6 @@ __device__ __forceinline__ void tmem_relinquish() {   // one full warp
 }
 __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {   // the allocating warp
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
-}
-
-// Shared-memory matrix descriptor: start address, leading (K) and stride
-// (8-row group) byte offsets, descriptor version 1, no swizzle.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-    d |= (uint64_t)1 << 46;
-    return d;
 }
 
 // Descriptor of a swizzled K-major operand: start address (a K step of the
@@ -127,17 +105,6 @@ __device__ __forceinline__ void ld_32x16(uint32_t taddr, float (&v)[16]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// 32 lanes x 8 consecutive 32-bit columns
-__device__ __forceinline__ void ld_32x8(uint32_t taddr, float (&v)[8]) {
-    uint32_t r[8];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-                 : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 // four 32 x 8 loads at columns taddr + i * stride (i = 0..3) and one wait:
