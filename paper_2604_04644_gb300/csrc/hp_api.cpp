@@ -275,7 +275,7 @@ hp_status ensure_tc(hp_mesh m, int es) {
         if (b.d_geom_tc || n_modes(b.shape, b.P) > kTcMaxModes) continue;
         const DeviceBlobs& db = m->blobs.at(b.shape * 16 + b.P);
         hp_status st = upload<uint16_t>(&b.d_geom_tc, nullptr, (size_t)tc_geom_halves(b.n_elem, db.tc_nch));
-        if (!st) st = upload<float>(&b.d_gscale_tc, nullptr, (size_t)((b.n_elem + 127) / 128 * 128));
+        if (!st) st = upload<float>(&b.d_gscale_tc, nullptr, (size_t)((b.n_elem + 127) / 128 * 128 * 2));
         if (st) return st;
         const BlobLayout L = blob_layout_c(b.shape, b.P, 8);
         const double* v64 = static_cast<const double*>(db.d64);

@@ -61,7 +61,7 @@ struct Block {
     float* d_geom32 = nullptr;            // FP32 copies (created on demand)
     float* d_dgeom32 = nullptr;
     uint16_t* d_geom_tc = nullptr;        // tensor-core operator: tile-major FP16 factors (curved and affine)
-    float* d_gscale_tc = nullptr;         // and their per-element scales 2^-k_e
+    float* d_gscale_tc = nullptr;         // and their per-element scales (Laplacian factors, w|J|)
     int64_t coeff_total = 0, phys_total = 0;   // per-block totals (work accounting)
 };
 
@@ -187,7 +187,7 @@ struct TCArgs {
     const float* in;
     float* out;
     const uint16_t* geom16;            // tile-major FP16 factors, scaled per element (tc_geom_layout16)
-    const float* gscale;               // [tiles x 128] 2^-k_e: undoes element e's scale
+    const float* gscale;               // [tiles x 128][2] 2^-k of element e's Laplacian factors and of its w|J|
     const unsigned char* img;          // per chunk of points: 4 forward then 4 backward tiles
     int64_t chunk_bytes;
     int fwd_bytes, bwd_bytes, stage_bytes;

@@ -447,7 +447,9 @@ __global__ void __launch_bounds__(Epi<EW>::kThreads, Epi<EW>::kCtas) tc_emat_ker
             // one U buffer: gathered once the previous tile's MMAs completed; two:
             // the next tile's U is gathered while this tile's last MMAs run
             if (a.ubufs == 1 || ntile == 0) gather_u(0, offs);
-            const float isc = a.gscale[tile * 128 + r];     // 2^-k of element r's FP16 factors (0: padding)
+            // 2^-k of element r's FP16 Laplacian factors and of its w|J| (0: padding)
+            const float2 isc2 = *reinterpret_cast<const float2*>(a.gscale + 2 * (tile * 128 + r));
+            const float isc = isc2.x, iscm = isc2.y;
             // this thread's points h kPts.. are kPts / kGeoPts runs of the factor layout
             const uint2* gt = reinterpret_cast<const uint2*>(a.geom16) +
                               (tile * a.nch * 7 * kGeoGroups + h * (kPts / kGeoPts)) * 128 + r;
@@ -491,7 +493,7 @@ __global__ void __launch_bounds__(Epi<EW>::kThreads, Epi<EW>::kCtas) tc_emat_ker
                         const int p = 2 * p2 + j;
                         auto gf = [&](int f) { return j ? G[f].y : G[f].x; };
                         const float v1 = v[1][p], v2 = v[2][p], v3 = v[3][p];
-                        o[0][p] = lam * isc * gf(6) * v[0][p];
+                        o[0][p] = lam * iscm * gf(6) * v[0][p];
                         o[1][p] = isc * (gf(0) * v1 + gf(1) * v2 + gf(2) * v3);
                         o[2][p] = isc * (gf(1) * v1 + gf(3) * v2 + gf(4) * v3);
                         o[3][p] = isc * (gf(2) * v1 + gf(4) * v2 + gf(5) * v3);
@@ -604,13 +606,15 @@ __global__ void zero_coeffs_kernel(float* out, const int64_t* coeff_off, int64_t
 }
 
 // Metric factors for the tensor-core forms: the seven factors of every point
-// (the six unique entries of G and w|J|) in FP16 with one power-of-two scale
+// (the six unique entries of G and w|J|) in FP16 with two power-of-two scales
 // per element.  The operands round to 11 (TF32) or 8 (BF16) significant bits,
 // so FP16's 11 keep the factors as accurate as the operands at half the bytes
-// of FP32.  Element e's factors are multiplied by 2^k_e with
-// k_e = 14 - floor(log2 max|G_e|): the largest lies in [2^14, 2^15) (FP16 ends
-// at 65504) and only entries below 2^-28 of it fall into FP16's subnormal
-// range; the epilogue multiplies its outputs by 2^-k_e (exact in FP32).
+// of FP32.  Element e's six Laplacian factors are multiplied by 2^k with
+// k = 14 - floor(log2 max|G|), its w|J| by 2^k' from its own maximum (the two
+// differ by h^2, so one scale would push w|J| into FP16's subnormals on small
+// elements): each group's largest lies in [2^14, 2^15) (FP16 ends at 65504)
+// and only entries below 2^-28 of it are subnormal; the epilogue multiplies
+// its outputs by 2^-k, 2^-k' (exact in FP32).
 // Layout [tile][chunk][7 factors][kGeoGroups point runs][128 elements][kGeoPts
 // points], an epilogue thread's run of a factor contiguous and a warp's 32
 // elements adjacent; padded points and elements stay zero
@@ -645,21 +649,28 @@ __device__ __forceinline__ void point_factors(const double* g, int NQp, const do
     }
 }
 
-// one warp per element: the element's largest factor, then the scaled values
+// one warp per element: the largest of its six Laplacian factors and its
+// largest w|J|, each group scaled by its own power of two (w|J| ~ h^3 and the
+// G ~ h differ by h^2, which one scale would push into FP16's subnormals on
+// small elements), then the scaled values; isc[2e], isc[2e + 1] undo the scales
 template <int SHAPE, bool CURVED>
 __global__ void tc_geom16_kernel(const double* g, int NQp, const double* z, const double* w, int Q, uint16_t* out,
                                  float* isc, int64_t n_elem, int nch) {
     const int NQ = Q * Q * Q, lane = threadIdx.x & 31;
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x / 32);
     for (int64_t e = blockIdx.x * (int64_t)(blockDim.x / 32) + threadIdx.x / 32; e < n_elem; e += nw) {
-        double mx = 0.0;
+        double mg = 0.0, mm = 0.0;
         for (int l = lane; l < NQ; l += 32) {
             double G[7];
             point_factors<SHAPE, CURVED>(g, NQp, z, w, Q, e, l, G);
-            for (int f = 0; f < 7; ++f) mx = fmax(mx, fabs(G[f]));
+            for (int f = 0; f < 6; ++f) mg = fmax(mg, fabs(G[f]));
+            mm = fmax(mm, fabs(G[6]));
         }
-        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        const int k = mx > 0.0 ? 14 - ilogb(mx) : 0;
+        for (int o = 16; o > 0; o >>= 1) {
+            mg = fmax(mg, __shfl_xor_sync(0xffffffffu, mg, o));
+            mm = fmax(mm, __shfl_xor_sync(0xffffffffu, mm, o));
+        }
+        const int kg = mg > 0.0 ? 14 - ilogb(mg) : 0, km = mm > 0.0 ? 14 - ilogb(mm) : 0;
         const int64_t tile = e >> 7;
         const int r = (int)(e & 127);
         for (int l = lane; l < NQ; l += 32) {
@@ -667,9 +678,12 @@ __global__ void tc_geom16_kernel(const double* g, int NQp, const double* z, cons
             point_factors<SHAPE, CURVED>(g, NQp, z, w, Q, e, l, G);
             for (int f = 0; f < 7; ++f)
                 out[geom16_index(tile, l / kNPT, f, l % kNPT, r, nch)] =
-                    __half_as_ushort(__float2half_rn((float)ldexp(G[f], k)));
+                    __half_as_ushort(__float2half_rn((float)ldexp(G[f], f < 6 ? kg : km)));
         }
-        if (lane == 0) isc[e] = (float)ldexp(1.0, -k);
+        if (lane == 0) {
+            isc[2 * e] = (float)ldexp(1.0, -kg);
+            isc[2 * e + 1] = (float)ldexp(1.0, -km);
+        }
     }
 }
 
@@ -737,7 +751,7 @@ cudaError_t tc_geom_layout16(int shape, bool curved, const double* g, int NQp, c
     if (n_elem <= 0) return cudaSuccess;
     const int64_t ntiles = (n_elem + 127) / 128;
     cudaError_t e = cudaMemsetAsync(out, 0, (size_t)tc_geom_halves(n_elem, nch) * sizeof(uint16_t), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(isc, 0, (size_t)ntiles * 128 * sizeof(float), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(isc, 0, (size_t)ntiles * 128 * 2 * sizeof(float), s);
     if (e != cudaSuccess) return e;
     switch (shape) {
         case HP_HEX: return geom16_shape<HP_HEX>(curved, g, NQp, z, w, Q, out, isc, n_elem, nch, s);

@@ -166,3 +166,22 @@ def test_bf16_two_ctas_per_sm(hp, shape, P, curved):
     ref = oracle_ops.apply("helmholtz", mesh, x.astype(np.float32).astype(np.float64), 0.9, elems=sample)
     idx = np.concatenate([np.arange(co[e], co[e + 1]) for e in sample])
     assert rel_err(y[idx], ref[idx]) <= BF16_TOL
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16"])
+@pytest.mark.parametrize("opname,lam", [("mass", 1.0), ("helmholtz", 5e11)])
+def test_tensor_core_small_elements(hp, prec, opname, lam):
+    """Elements of size h ~ 1e-5 (the mixed mesh scaled by 2e-5): w|J| ~ h^3
+    and the Laplacian factors ~ h differ by ~1e10, so each group keeps its own
+    power-of-two scale in FP16 (one shared scale would leave w|J| subnormal).
+    The mass operator and a Helmholtz operator whose two terms are of one size
+    (lambda = 5e11) stay within the tolerance of their form."""
+    base = mixed_mesh(3)
+    mesh = dict(base)
+    mesh["xyz"] = base["xyz"] * 2e-5
+    co, _ = oracle_ops.layout(mesh)
+    x = make_input(mesh, opname, 17)
+    ref = oracle_ops.apply(opname, mesh, x.astype(np.float32).astype(np.float64), lam)
+    y, _ = run_tc(hp, mesh, opname, x, lam, hp.HP_TF32 if prec == "tf32" else hp.HP_BF16)
+    assert not np.isnan(y).any()
+    assert rel_err(y, ref) <= (TF32_TOL if prec == "tf32" else BF16_TOL)
