@@ -249,6 +249,14 @@ const Match& match_of(int shape, int P, int kind, int ent, const std::vector<int
     return it->second;
 }
 
+// integer key of (shape, entity kind, local entity, canonical local vertex
+// order): 2 + 2 + 4 bits, then up to four 3-bit vertex ids and their count
+uint32_t match_key(int shape, int kind, int ent, const int* lv, int n) {
+    uint32_t k = (uint32_t)shape | ((uint32_t)kind << 2) | ((uint32_t)ent << 4) | ((uint32_t)n << 8);
+    for (int i = 0; i < n; ++i) k |= (uint32_t)lv[i] << (11 + 3 * i);
+    return k;
+}
+
 struct ArrHash {
     size_t operator()(const std::array<int64_t, 4>& a) const {
         uint64_t h = 1469598103934665603ull;
@@ -258,6 +266,56 @@ struct ArrHash {
         }
         return (size_t)h;
     }
+};
+
+// Open-addressing hash map from up to four int64 ids to the index of first
+// insertion (linear probing, capacity a power of two, at most half full):
+// entities are numbered in order of first appearance, as with any map.
+class EntityMap {
+public:
+    explicit EntityMap(size_t expect) { rehash(std::max<size_t>(64, 2 * expect)); }
+    int64_t size() const { return n_; }
+    // index of `k`, inserting it with the next index when absent; *fresh tells which
+    int64_t find_or_insert(const std::array<int64_t, 4>& k, bool* fresh) {
+        if (2 * (n_ + 1) > cap_) rehash(2 * cap_);
+        size_t i = slot(k);
+        while (used_[i]) {
+            if (keys_[i] == k) { *fresh = false; return vals_[i]; }
+            i = (i + 1) & (cap_ - 1);
+        }
+        used_[i] = 1;
+        keys_[i] = k;
+        vals_[i] = n_;
+        *fresh = true;
+        return n_++;
+    }
+
+private:
+    size_t slot(const std::array<int64_t, 4>& k) const { return ArrHash()(k) & (cap_ - 1); }
+    void rehash(size_t want) {
+        size_t c = 64;
+        while (c < want) c <<= 1;
+        std::vector<std::array<int64_t, 4>> ok = std::move(keys_);
+        std::vector<int64_t> ov = std::move(vals_);
+        std::vector<uint8_t> ou = std::move(used_);
+        cap_ = c;
+        keys_.assign(cap_, {});
+        vals_.assign(cap_, 0);
+        used_.assign(cap_, 0);
+        for (size_t j = 0; j < ou.size(); ++j)
+            if (ou[j]) {
+                size_t i = slot(ok[j]);
+                while (used_[i]) i = (i + 1) & (cap_ - 1);
+                used_[i] = 1;
+                keys_[i] = ok[j];
+                vals_[i] = ov[j];
+            }
+    }
+    size_t cap_ = 0;
+    int64_t n_ = 0;
+    std::vector<std::array<int64_t, 4>> keys_;
+    std::vector<int64_t> vals_;
+    std::vector<uint8_t> used_;
 };
 
 }  // namespace
@@ -278,8 +336,7 @@ hp_status build_c0(const hp_mesh m, const std::vector<int64_t>& vert, std::vecto
     gid.assign(n_local, -1);
     sign.assign(n_local, 1);
     // entity numbering
-    std::unordered_map<int64_t, int64_t> vmap;
-    std::unordered_map<std::array<int64_t, 4>, int64_t, ArrHash> emap, fmap;
+    EntityMap vmap((size_t)ne * 2), emap((size_t)ne * 4), fmap((size_t)ne * 4);
     std::vector<int> fcount;
     std::vector<int> ftype;    // 0 quad, 1 tri
     // per local coefficient: (class 0..3, entity index, canonical index)
@@ -287,42 +344,58 @@ hp_status build_c0(const hp_mesh m, const std::vector<int64_t>& vert, std::vecto
     std::vector<int64_t> lent(n_local, -1);
     std::vector<int32_t> lcan(n_local, 0);
     int64_t n_interior = 0;
+    // per call: the classes of each shape and the matches seen so far by integer key
+    // (the shared caches are keyed by vectors in ordered maps, slow for every element)
+    const Classes* cls[4] = {nullptr, nullptr, nullptr, nullptr};
+    std::unordered_map<uint32_t, const Match*> fast;
+    auto match_fast = [&](int s, int kind, int ent, const int* lv, int n, const std::vector<int>& modes) -> const Match& {
+        const uint32_t k = match_key(s, kind, ent, lv, n);
+        auto it = fast.find(k);
+        if (it != fast.end()) return *it->second;
+        const Match& M = match_of(s, P, kind, ent, std::vector<int>(lv, lv + n), modes);
+        fast.emplace(k, &M);
+        return M;
+    };
+    // face index of (element, local face), for the boundary pass
+    std::vector<int64_t> elem_face((size_t)ne * 6, -1);
     for (int64_t e = 0; e < ne; ++e) {
         const int s = m->shape[e];
-        const Classes& C = classes_of(s, P);
+        if (!cls[s]) cls[s] = &classes_of(s, P);
+        const Classes& C = *cls[s];
         const Topo& T = topo(s);
         const int64_t base = m->coeff_off[e];
         const int64_t* g = &vert[e * 8];
         for (int v = 0; v < kNVert[s]; ++v) {
             if (C.vertex_mode[v].size() != 1) { set_error("hp_c0_create: vertex mode classification failed"); return HP_ERR_UNSUPPORTED; }
-            auto it = vmap.find(g[v]);
-            if (it == vmap.end()) it = vmap.emplace(g[v], (int64_t)vmap.size()).first;
+            bool fresh;
+            const int64_t vi = vmap.find_or_insert({g[v], -1, -1, -1}, &fresh);
             int mm = C.vertex_mode[v][0];
             lclass[base + mm] = 0;
-            lent[base + mm] = it->second;
+            lent[base + mm] = vi;
         }
         for (size_t ed = 0; ed < T.edges.size(); ++ed) {
             int la = T.edges[ed][0], lb = T.edges[ed][1];
             if (g[la] > g[lb]) std::swap(la, lb);
-            std::array<int64_t, 4> key = {g[la], g[lb], -1, -1};
-            auto it = emap.find(key);
-            if (it == emap.end()) it = emap.emplace(key, (int64_t)emap.size()).first;
-            const Match& M = match_of(s, P, 0, (int)ed, {la, lb}, C.edge_modes[ed]);
+            bool fresh;
+            const int64_t ei = emap.find_or_insert({g[la], g[lb], -1, -1}, &fresh);
+            const int lvq[2] = {la, lb};
+            const Match& M = match_fast(s, 0, (int)ed, lvq, 2, C.edge_modes[ed]);
             if (!M.ok) { set_error("hp_c0_create: edge trace is not a signed permutation"); return HP_ERR_UNSUPPORTED; }
             for (size_t i = 0; i < M.mode.size(); ++i) {
                 lclass[base + M.mode[i]] = 1;
-                lent[base + M.mode[i]] = it->second;
+                lent[base + M.mode[i]] = ei;
                 lcan[base + M.mode[i]] = M.canon[i];
                 sign[base + M.mode[i]] = (int8_t)M.sign[i];
             }
         }
         for (size_t f = 0; f < T.faces.size(); ++f) {
             const auto& lvf = T.faces[f];
-            std::vector<int> canon;
+            int canon[4];
+            const int nfv = (int)lvf.size();
             std::array<int64_t, 4> key = {-1, -1, -1, -1};
-            if (lvf.size() == 3) {
-                canon = lvf;
-                std::sort(canon.begin(), canon.end(), [&](int x, int y) { return g[x] < g[y]; });
+            if (nfv == 3) {
+                for (int i = 0; i < 3; ++i) canon[i] = lvf[i];
+                std::sort(canon, canon + 3, [&](int x, int y) { return g[x] < g[y]; });
                 for (int i = 0; i < 3; ++i) key[i] = g[canon[i]];
             } else {
                 int o = 0;
@@ -330,19 +403,20 @@ hp_status build_c0(const hp_mesh m, const std::vector<int64_t>& vert, std::vecto
                     if (g[lvf[i]] < g[lvf[o]]) o = i;
                 int nA = lvf[(o + 1) % 4], nB = lvf[(o + 3) % 4];
                 int sN = g[nA] < g[nB] ? nA : nB, tN = g[nA] < g[nB] ? nB : nA;
-                canon = {lvf[o], sN, lvf[(o + 2) % 4], tN};
-                std::vector<int64_t> ids = {g[lvf[0]], g[lvf[1]], g[lvf[2]], g[lvf[3]]};
+                canon[0] = lvf[o]; canon[1] = sN; canon[2] = lvf[(o + 2) % 4]; canon[3] = tN;
+                std::array<int64_t, 4> ids = {g[lvf[0]], g[lvf[1]], g[lvf[2]], g[lvf[3]]};
                 std::sort(ids.begin(), ids.end());
-                for (int i = 0; i < 4; ++i) key[i] = ids[i];
+                key = ids;
             }
-            auto it = fmap.find(key);
-            if (it == fmap.end()) {
-                it = fmap.emplace(key, (int64_t)fmap.size()).first;
+            bool fresh;
+            const int64_t fi = fmap.find_or_insert(key, &fresh);
+            if (fresh) {
                 fcount.push_back(0);
-                ftype.push_back(lvf.size() == 3 ? 1 : 0);
+                ftype.push_back(nfv == 3 ? 1 : 0);
             }
-            fcount[it->second] += 1;
-            const Match& M = match_of(s, P, lvf.size() == 3 ? 2 : 1, (int)f, canon, C.face_modes[f]);
+            fcount[fi] += 1;
+            elem_face[(size_t)e * 6 + f] = fi;
+            const Match& M = match_fast(s, nfv == 3 ? 2 : 1, (int)f, canon, nfv, C.face_modes[f]);
             if (!M.ok) {
                 set_error("hp_c0_create: face trace is not a signed permutation (triangle faces need their "
                           "collapsed vertex at the largest global id)");
@@ -350,7 +424,7 @@ hp_status build_c0(const hp_mesh m, const std::vector<int64_t>& vert, std::vecto
             }
             for (size_t i = 0; i < M.mode.size(); ++i) {
                 lclass[base + M.mode[i]] = 2;
-                lent[base + M.mode[i]] = it->second;
+                lent[base + M.mode[i]] = fi;
                 lcan[base + M.mode[i]] = M.canon[i];
                 sign[base + M.mode[i]] = (int8_t)M.sign[i];
             }
@@ -361,7 +435,7 @@ hp_status build_c0(const hp_mesh m, const std::vector<int64_t>& vert, std::vecto
     for (int c : fcount)
         if (c > 2) { set_error("hp_c0_create: a face is shared by more than two elements"); return HP_ERR_GEOM; }
     // global layout: vertices, edges, faces (each with its own size), interiors
-    const int64_t nv = (int64_t)vmap.size(), nedge = (int64_t)emap.size(), nface = (int64_t)fmap.size();
+    const int64_t nv = vmap.size(), nedge = emap.size(), nface = fmap.size();
     const int per_edge = P - 1, per_quad = (P - 1) * (P - 1), per_tri = (P - 1) * (P - 2) / 2;
     std::vector<int64_t> face_base(nface + 1, 0);
     for (int64_t f = 0; f < nface; ++f) face_base[f + 1] = face_base[f] + (ftype[f] ? per_tri : per_quad);
@@ -380,17 +454,11 @@ hp_status build_c0(const hp_mesh m, const std::vector<int64_t>& vert, std::vecto
     for (int64_t e = 0; e < ne; ++e) {
         const int s = m->shape[e];
         const Topo& T = topo(s);
-        const Classes& C = classes_of(s, P);
+        const Classes& C = *cls[s];
         const int64_t base = m->coeff_off[e];
-        const int64_t* g = &vert[e * 8];
         for (size_t f = 0; f < T.faces.size(); ++f) {
             const auto& lvf = T.faces[f];
-            std::array<int64_t, 4> key = {-1, -1, -1, -1};
-            std::vector<int64_t> ids;
-            for (int v : lvf) ids.push_back(g[v]);
-            std::sort(ids.begin(), ids.end());
-            for (size_t i = 0; i < ids.size(); ++i) key[i] = ids[i];
-            if (fcount[fmap[key]] != 1) continue;
+            if (fcount[elem_face[(size_t)e * 6 + f]] != 1) continue;
             for (int mm : C.face_modes[f]) boundary[gid[base + mm]] = 1;
             for (int v : lvf) boundary[gid[base + C.vertex_mode[v][0]]] = 1;
             for (size_t ed = 0; ed < T.edges.size(); ++ed) {
