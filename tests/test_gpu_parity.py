@@ -3,8 +3,9 @@ element by element, on seeded inputs.
 
 Tolerances (relative, infinity norm over the whole output vector):
   FP64: 1e-12 (the operators' required agreement with the FP64 oracle).
-  FP32: see FP32_TOL below (derived in the design doc from unit roundoff and the
-        size of the differentiation matrices).
+  FP32: fp32_tol(P) below, 6e-8 * 40 * Q: the FP32 unit roundoff times the
+        number of rounded terms per output (about six passes of Q each) and
+        the growth of max|D| with Q.
 """
 import numpy as np
 import pytest
