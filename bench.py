@@ -37,6 +37,9 @@ ORDERS = list(range(1, 9))
 CELLS = 16
 FP64_PEAK_TFLOPS = 1.25     # GB300 FP64 (vector and tensor) nominal rate, profiling recipe table
 SHAPES = ("hex", "prism", "pyr", "tet")
+# modes per element of each shape at order P (the modified C0 basis, Sec. 2.3)
+N_MODES = (lambda P: (P + 1) ** 3, lambda P: (P + 1) ** 2 * (P + 2) // 2,
+           lambda P: (P + 1) * (P + 2) * (2 * P + 3) // 6, lambda P: (P + 1) * (P + 2) * (P + 3) // 6)
 # DRAM bytes (read + write) of one launch, measured by ncu on this workload
 # for the kernel named; a kernel whose code changed after the measurement is
 # left out (its traffic reads null)
@@ -78,6 +81,9 @@ def parse():
     p.add_argument("--block-table", action="store_true",
                    help="GDOF/s of FP32 sum factorisation and the TF32 / BF16 tensor-core operator on large "
                         "single-shape blocks instead")
+    p.add_argument("--collocation-study", action="store_true",
+                   help="GDOF/s of the collocated and the non-collocated FP64 sum-factorised Helmholtz on "
+                        "regular (affine) single-shape blocks, P = 1..8, instead")
     p.add_argument("--profile-case", default=None, choices=sorted(PROFILE_CASES),
                    help="run one small case for a profiler capture instead (tc_tet8 / tc16_tet8: TF32 / BF16 "
                         "tensor-core Helmholtz, 19 456 curved tets, P = 8; tc16_hex4: BF16, 65 536 curved hexes, P = 4; sf32_hex4 / sf32_tet4: FP32 sum "
@@ -706,6 +712,50 @@ def run_block_table(local, reps=10):
             print(json.dumps({"block_table": line}), flush=True)
 
 
+def run_collocation_study(local, reps=10):
+    """The paper's collocation study (Sec. 5) on this GPU: FP64 Helmholtz
+    GDOF/s of the collocated sum factorisation (derivatives by collocation at
+    the points) and of the non-collocated form (derivatives by sum
+    factorisation with the derivative tables), on regular (affine) single-shape
+    blocks of about six million DOFs, P = 1..8 (L2 flushed before every apply;
+    median of `reps`), one JSON line per (shape, P)."""
+    import torch
+    from paper_2604_04644_gb300 import hp, inputs
+    torch.cuda.set_device(local)
+    dev = "cuda:%d" % local
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    for shape in range(4):
+        for P in range(1, 9):
+            n = min(200000, max(4096, int(6e6 / N_MODES[shape](P))))
+            mesh = inputs.replicated_mesh(shape, P, n, curved=False)
+            h = hp.hp_mesh_create(mesh, local)
+            co, po, nc, nph = hp.hp_mesh_layout(h, mesh["n_elem"])
+            x = torch.tensor(inputs.random_coefficients(5, co), device=dev, dtype=torch.float64)
+            y = torch.zeros(nc, device=dev, dtype=torch.float64)
+            line = {"shape": SHAPES[shape], "P": P, "elements": int(mesh["n_elem"]), "dofs": int(nc)}
+            op = hp.hp_op_create(h, hp.HP_HELMHOLTZ, hp.HP_STRAT_SUMFAC, hp.HP_FP64)
+            for name, coll in (("collocated", True), ("noncollocated", False)):
+                hp.hp_op_set_collocated(op, coll)
+                for _ in range(3):
+                    hp.hp_op_apply(op, 1.0, x, y)
+                ts = []
+                for _ in range(reps):
+                    flush.zero_()
+                    a = torch.cuda.Event(enable_timing=True)
+                    b = torch.cuda.Event(enable_timing=True)
+                    a.record()
+                    hp.hp_op_apply(op, 1.0, x, y)
+                    b.record()
+                    b.synchronize()
+                    ts.append(a.elapsed_time(b))
+                hp.hp_op_sync(op)
+                line[name] = round(nc / (statistics.median(ts) * 1e-3) / 1e9, 3)
+            line["collocated_over_noncollocated"] = round(line["collocated"] / line["noncollocated"], 3)
+            hp.hp_op_destroy(op)
+            hp.hp_mesh_destroy(h)
+            print(json.dumps({"collocation_study": line}), flush=True)
+
+
 def run_profile_case(name, local):
     """One block of curved elements, three Helmholtz applies (the capture takes one)."""
     import torch
@@ -736,6 +786,10 @@ def main():
     if args.block_table:
         if rank == 0:
             run_block_table(local)
+        return
+    if args.collocation_study:
+        if rank == 0:
+            run_collocation_study(local)
         return
     if args.solve:
         if rank == 0:

@@ -199,6 +199,20 @@ hp_status hp_op_tiles(hp_op op, int* tiles, int64_t n_blocks, int set);
  * blocks of at most 256 modes). */
 hp_status hp_op_strategies(hp_op op, int* strategies, int64_t n_blocks, int set);
 
+/* Form of the sum-factorised Laplacian and Helmholtz blocks of an HP_FP64
+ * operator (the two forms of the paper's collocation study, Sec. 5 "Maximising
+ * collocation-based operations"; Sec. 3.3 for the collocated algorithm).
+ * collocated = 1 (the default): BwdTrans to the points, the derivatives by
+ * collocation differentiation there, and their transposes (Sec. 3.3).
+ * collocated = 0: the derivatives d phi / d eta_d by sum-factorisation passes
+ * with the 1-D derivative tables, and the transposed inner products the same
+ * way (the non-collocated approach).  Both compute (lambda M + L) uhat; they
+ * agree up to rounding.  Blocks with other strategies and other operator
+ * kinds are unaffected.  HP_ERR_ARG unless collocated is 0 or 1;
+ * HP_ERR_UNSUPPORTED for collocated = 0 on an operator that is not HP_FP64.
+ * Drops the op's captured graph when the form changes. */
+hp_status hp_op_set_collocated(hp_op op, int collocated);
+
 /* ---------------------------------------------------------------- cost model
  * Not in the paper (which picks a strategy by a fixed rule per operator):
  * a small MLP, trained by the library's own kernels on timings the library

@@ -441,6 +441,8 @@ cudaError_t launch_block(hp_op op, size_t bi, int tile, double lambda, const voi
         a.blob_bytes = blob.bytes64;
         a.err = op->d_err;
         fill_const_tables(b, a);
+        if (!op->collocated && (op->kind == HP_LAPLACIAN || op->kind == HP_HELMHOLTZ))
+            return sf_nc_launch(b.shape, b.P, !b.curved, a, blob.d_nc64, s);
         return sf_launch_f64(b.shape, b.P, !b.curved, tile, a, s);
     }
     SFArgs<float> a{};
@@ -609,6 +611,9 @@ hp_status hp_mesh_create(const hp_mesh_desc* d, int device, hp_mesh* out) {
             db.d32 = p32;
             db.bytes64 = (int)b64.size();
             db.bytes32 = (int)b32.size();
+            std::vector<double> dtab(t.Tbd);
+            dtab.insert(dtab.end(), t.Tcd.begin(), t.Tcd.end());
+            if ((st = upload(&db.d_nc64, dtab.data(), dtab.size()))) { cudaFree(p64); cudaFree(p32); break; }
             m->blobs[key] = db;
         }
     }
@@ -808,6 +813,17 @@ hp_status hp_op_tiles(hp_op op, int* tiles, int64_t n_blocks, int set) {
         }
     }
     if (set && op->graph) { cudaGraphExecDestroy(op->graph); op->graph = nullptr; }
+    return HP_OK;
+}
+
+hp_status hp_op_set_collocated(hp_op op, int collocated) {
+    if (!op || (collocated != 0 && collocated != 1)) { set_error("hp_op_set_collocated: bad argument"); return HP_ERR_ARG; }
+    if (!collocated && op->dtype != HP_FP64) {
+        set_error("hp_op_set_collocated: the non-collocated form is FP64 only");
+        return HP_ERR_UNSUPPORTED;
+    }
+    if (op->collocated != collocated && op->graph) { cudaGraphExecDestroy(op->graph); op->graph = nullptr; }
+    op->collocated = collocated;
     return HP_OK;
 }
 
@@ -1148,6 +1164,7 @@ void hp_mesh_destroy(hp_mesh m) {
         for (auto& kv : m->blobs) {
             cudaFree(kv.second.d64);
             cudaFree(kv.second.d32);
+            cudaFree(kv.second.d_nc64);
             cudaFree(kv.second.A4_64);
             cudaFree(kv.second.A4T_64);
             cudaFree(kv.second.A4_32);

@@ -28,6 +28,7 @@ struct RefTables {
     std::vector<double> Tp, Td;            // [a][i]        n*Q, eta1 table in parity form and its derivative
     std::vector<double> Tb;                // [t][b][j]     (P+1)*n*Q
     std::vector<double> Tc;                // [s][c][k]     (P+1)*n*Q
+    std::vector<double> Tbd, Tcd;          // d/d eta_2 of Tb, d/d eta_3 of Tc at the points (same layout)
     std::vector<double> D[3];              // [i][m]        Q*Q, d/d eta of Lagrange basis
     std::vector<uint8_t> famb, famc;       // n, n*n
     std::vector<int16_t> slot2mode;        // n^3, -1 = empty slot
@@ -82,6 +83,8 @@ struct DeviceBlobs {
     int64_t tc_chunk16 = 0;
     int tc_KP = 0, tc_NPpad = 0, tc_nch = 0, tc_fwd = 0, tc_bwd = 0;
     int64_t tc_chunk = 0;
+    // derivative tables [Tbd | Tcd] in FP64, for the non-collocated sum-factorisation kernel
+    double* d_nc64 = nullptr;
 };
 
 }  // namespace hp
@@ -107,6 +110,7 @@ struct hp_op_s {
     unsigned int* d_err = nullptr;
     std::vector<int> tile;                      // tile variant per block
     std::vector<int> strat;                     // hp_strategy per block (SUMFAC, ELEMAT, HYBRID)
+    int collocated = 1;                         // 0: FP64 sum-factorised Laplacian/Helmholtz in the non-collocated form
     // CUDA graph of one apply (blocks as independent nodes), for fixed (lambda, in, out)
     cudaGraphExec_t graph = nullptr;
     const void* g_in = nullptr;
@@ -207,6 +211,9 @@ cudaError_t emat_launch_f32(bool hybrid, bool affine, const EMArgs<float>& a, cu
 cudaError_t sf_launch_f64(int shape, int P, bool affine, int tile, const SFArgs<double>& a, cudaStream_t s);
 cudaError_t sf_launch_f32(int shape, int P, bool affine, int tile, const SFArgs<float>& a, cudaStream_t s);
 int sf_epb_host(int P, int tile, bool f64);
+// non-collocated FP64 sum factorisation (hp_sf_nc.cu): the derivatives by
+// sum-factorisation passes with the derivative tables dtab = [Tbd | Tcd]
+cudaError_t sf_nc_launch(int shape, int P, bool affine, const SFArgs<double>& a, const double* dtab, cudaStream_t s);
 constexpr int kTiles = 3;
 
 }  // namespace hp

@@ -219,6 +219,20 @@ RefTables build(int shape, int P) {
                 t.Tb[(s * n + m) * Q + q] = family(P, s, m, t.z[1][q]);
                 t.Tc[(s * n + m) * Q + q] = family(P, s, m, t.z[2][q]);
             }
+    // their derivatives at the points: every family member has degree <= P < Q
+    // in its variable, so the collocation derivative of its values is exact
+    t.Tbd.assign(t.Tb.size(), 0.0);
+    t.Tcd.assign(t.Tc.size(), 0.0);
+    for (int r = 0; r < (P + 1) * n; ++r)
+        for (int q = 0; q < Q; ++q) {
+            double db = 0.0, dc = 0.0;
+            for (int m = 0; m < Q; ++m) {
+                db += t.D[1][q * Q + m] * t.Tb[r * Q + m];
+                dc += t.D[2][q * Q + m] * t.Tc[r * Q + m];
+            }
+            t.Tbd[r * Q + q] = db;
+            t.Tcd[r * Q + q] = dc;
+        }
     // families and slot validity
     t.famb.assign(n, 0);
     t.famc.assign(n * n, 0);

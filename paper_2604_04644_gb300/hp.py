@@ -30,7 +30,7 @@ HP_FP64, HP_FP32, HP_TF32, HP_BF16 = range(4)
 
 EXPORTED = ["hp_mesh_create", "hp_mesh_layout", "hp_geom_factors", "hp_geom_copy", "hp_op_create",
             "hp_op_apply", "hp_op_apply_graph", "hp_op_tune", "hp_op_tiles", "hp_op_strategies",
-            "hp_op_block_features", "hp_op_schedule", "hp_op_schedule_exhaustive", "hp_op_schedule_graph",
+            "hp_op_set_collocated", "hp_op_block_features", "hp_op_schedule", "hp_op_schedule_exhaustive", "hp_op_schedule_graph",
             "hp_op_sync", "hp_op_work",
             "hp_op_block_work", "hp_op_apply_block",
             "hp_op_destroy", "hp_mesh_destroy", "hp_status_str", "hp_last_error",
@@ -63,6 +63,7 @@ _lib.hp_op_apply_graph.argtypes = [_vp, ctypes.c_double, _vp, _vp, _vp]
 _lib.hp_op_tune.argtypes = [_vp, ctypes.c_double, _vp, _vp, _vp]
 _lib.hp_op_tiles.argtypes = [_vp, _vp, ctypes.c_int64, ctypes.c_int]
 _lib.hp_op_strategies.argtypes = [_vp, _vp, ctypes.c_int64, ctypes.c_int]
+_lib.hp_op_set_collocated.argtypes = [_vp, ctypes.c_int]
 _lib.hp_op_block_features.argtypes = [_vp, _vp, ctypes.c_int64]
 _lib.hp_op_schedule.argtypes = [_vp, _vp, _vp]
 _lib.hp_op_schedule_exhaustive.argtypes = [_vp, ctypes.c_double, _vp, _vp, _vp, _vp]
@@ -89,7 +90,7 @@ _lib.hp_status_str.restype = ctypes.c_char_p
 _lib.hp_last_error.restype = ctypes.c_char_p
 for _f in ("hp_mesh_create", "hp_mesh_layout", "hp_geom_factors", "hp_geom_copy", "hp_op_create",
            "hp_op_apply", "hp_op_apply_graph", "hp_op_tune", "hp_op_tiles", "hp_op_sync", "hp_op_work",
-           "hp_op_block_work", "hp_op_apply_block", "hp_op_strategies", "hp_op_block_features", "hp_op_schedule", "hp_op_schedule_exhaustive",
+           "hp_op_block_work", "hp_op_apply_block", "hp_op_strategies", "hp_op_set_collocated", "hp_op_block_features", "hp_op_schedule", "hp_op_schedule_exhaustive",
            "hp_op_schedule_graph", "hp_mlp_create", "hp_mlp_info", "hp_mlp_params", "hp_mlp_forward", "hp_mlp_grad", "hp_mlp_adam_step"):
     getattr(_lib, _f).restype = ctypes.c_int
 
@@ -181,6 +182,12 @@ def hp_op_tiles(op, n_blocks, tiles=None):
     arr = np.zeros(n_blocks, dtype=np.int32) if tiles is None else np.ascontiguousarray(tiles, dtype=np.int32)
     _check(_lib.hp_op_tiles(op, arr.ctypes.data, int(n_blocks), 0 if tiles is None else 1), "hp_op_tiles")
     return arr
+
+
+def hp_op_set_collocated(op, collocated):
+    """Collocated (True, the default) or non-collocated (False, FP64 only) form of
+    the op's sum-factorised Laplacian / Helmholtz blocks."""
+    _check(_lib.hp_op_set_collocated(op, 1 if collocated else 0), "hp_op_set_collocated")
 
 
 def hp_op_sync(op, stream=None):
