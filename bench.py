@@ -84,6 +84,9 @@ def parse():
     p.add_argument("--collocation-study", action="store_true",
                    help="GDOF/s of the collocated and the non-collocated FP64 sum-factorised Helmholtz on "
                         "regular (affine) single-shape blocks, P = 1..8, instead")
+    p.add_argument("--matrix-study", action="store_true",
+                   help="GDOF/s of the stored-matrix strategy (per-element dense H^e) against sum factorisation, "
+                        "FP64 and FP32, curved single-shape blocks, P = 1..5, instead")
     p.add_argument("--profile-case", default=None, choices=sorted(PROFILE_CASES),
                    help="run one small case for a profiler capture instead (tc_tet8 / tc16_tet8: TF32 / BF16 "
                         "tensor-core Helmholtz, 19 456 curved tets, P = 8; tc16_hex4: BF16, 65 536 curved hexes, P = 4; sf32_hex4 / sf32_tet4: FP32 sum "
@@ -756,6 +759,72 @@ def run_collocation_study(local, reps=10):
             print(json.dumps({"collocation_study": line}), flush=True)
 
 
+def run_matrix_study(local, reps=10):
+    """Matrix-based (stored per-element dense H^e, HP_STRAT_MATRIX) against
+    matrix-free sum factorisation: Helmholtz GDOF/s in FP64 and FP32 on curved
+    single-shape blocks of about four million DOFs, P = 1..5 (blocks of at most
+    256 modes), with the build time, the stored bytes and the stored-matrix
+    apply's HBM rate against the measured copy bandwidth (L2 flushed before
+    every apply; median of `reps`). One JSON line per (shape, P)."""
+    import torch
+    from paper_2604_04644_gb300 import hp, inputs
+    torch.cuda.set_device(local)
+    dev = "cuda:%d" % local
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    try:
+        hbm_peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
+    except (OSError, KeyError, ValueError):
+        hbm_peak = 6800.0
+    def timed(op, x, y):
+        for _ in range(3):
+            hp.hp_op_apply(op, 1.0, x, y)
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            hp.hp_op_apply(op, 1.0, x, y)
+            b.record()
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        hp.hp_op_sync(op)
+        return statistics.median(ts) * 1e-3
+    for shape in range(4):
+        for P in range(1, 6):
+            NP = N_MODES[shape](P)
+            if NP > 256:
+                continue
+            n = min(200000, max(4096, int(4e6 / NP)))
+            mesh = inputs.replicated_mesh(shape, P, n, curved=True)
+            h = hp.hp_mesh_create(mesh, local)
+            co, po, nc, nph = hp.hp_mesh_layout(h, mesh["n_elem"])
+            ne = int(mesh["n_elem"])
+            line = {"shape": SHAPES[shape], "P": P, "modes": NP, "elements": ne, "dofs": int(nc)}
+            xs = inputs.random_coefficients(5, co)
+            for dname, dt, tdt, vs in (("f64", hp.HP_FP64, torch.float64, 8), ("f32", hp.HP_FP32, torch.float32, 4)):
+                x = torch.tensor(xs, device=dev, dtype=tdt)
+                y = torch.zeros(nc, device=dev, dtype=tdt)
+                op = hp.hp_op_create(h, hp.HP_HELMHOLTZ, hp.HP_STRAT_SUMFAC, dt)
+                line["sumfac_" + dname] = round(nc / timed(op, x, y) / 1e9, 3)
+                hp.hp_op_destroy(op)
+                op = hp.hp_op_create(h, hp.HP_HELMHOLTZ, hp.HP_STRAT_MATRIX, dt)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                hp.hp_op_apply(op, 1.0, x, y)           # builds the stored matrices
+                hp.hp_op_sync(op)
+                line["build_s_" + dname] = round(time.perf_counter() - t0, 3)
+                t = timed(op, x, y)
+                line["matrix_" + dname] = round(nc / t / 1e9, 3)
+                algo = ne * (NP * NP * vs + 2 * NP * vs + 8)          # stored H^e, in, out, offsets
+                line["matrix_gbs_" + dname] = round(algo / t / 1e9, 1)
+                line["matrix_hbm_frac_" + dname] = round(algo / t / 1e9 / hbm_peak, 3)
+                line["stored_gb_" + dname] = round(ne * NP * NP * vs / 1e9, 3)
+                hp.hp_op_destroy(op)
+            hp.hp_mesh_destroy(h)
+            print(json.dumps({"matrix_study": line}), flush=True)
+
+
 def run_profile_case(name, local):
     """One block of curved elements, three Helmholtz applies (the capture takes one)."""
     import torch
@@ -790,6 +859,10 @@ def main():
     if args.collocation_study:
         if rank == 0:
             run_collocation_study(local)
+        return
+    if args.matrix_study:
+        if rank == 0:
+            run_matrix_study(local)
         return
     if args.solve:
         if rank == 0:

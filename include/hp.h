@@ -83,7 +83,10 @@ typedef enum {
     HP_STRAT_SUMFAC = 0,   /* fused sum-factorised collocated kernel (Alg. collocated Helmholtz)  */
     HP_STRAT_ELEMAT = 1,   /* reference-element dense matrices, non-collocated (StdMat, Sec. 3.3.1) */
     HP_STRAT_HYBRID = 2,   /* dense B / B^T with collocated derivatives                           */
-    HP_STRAT_AUTO = 3      /* the library chooses per block                                       */
+    HP_STRAT_AUTO = 3,     /* the library chooses per block                                       */
+    HP_STRAT_MATRIX = 4    /* stored per-element dense H^e (matrix-based, Sec. 3.3 implementation
+                              strategies): mass, Laplacian, Helmholtz; HP_FP64 / HP_FP32; blocks of
+                              at most 256 modes (larger blocks run HP_STRAT_SUMFAC)               */
 } hp_strategy;
 
 /* Compute type.  HP_FP64: IEEE double throughout (the oracle-parity form).

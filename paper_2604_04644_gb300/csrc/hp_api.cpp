@@ -377,9 +377,80 @@ void fill_const_tables(const Block& b, SFArgs<T>& a) {
     for (size_t i = 0; i < t.Tp.size(); ++i) a.cTa[i] = (T)t.Tp[i];
 }
 
+// the FP64 sum-factorised operator `kind` over block b (tile 0)
+cudaError_t launch_sf64(hp_mesh m, const Block& b, int kind, double lambda, const double* in, double* out,
+                        unsigned int* err, cudaStream_t s) {
+    const DeviceBlobs& blob = m->blobs.at(b.shape * 16 + b.P);
+    SFArgs<double> a{};
+    a.op = kind;
+    a.n_elem = b.n_elem;
+    a.lambda = lambda;
+    a.coeff_off = b.d_coeff_off;
+    a.phys_off = b.d_phys_off;
+    a.in = in;
+    a.out = out;
+    a.n_phys_total = m->phys_off.back();
+    a.geom = b.d_geom;
+    a.dgeom = b.d_dgeom;
+    a.blob = static_cast<const unsigned char*>(blob.d64);
+    a.blob_bytes = blob.bytes64;
+    a.err = err;
+    fill_const_tables(b, a);
+    return sf_launch_f64(b.shape, b.P, !b.curved, 0, a, s);
+}
+
+bool mat_fits(const Block& b) { return n_modes(b.shape, b.P) <= kMatMaxModes; }
+
+// Stored matrices of matrix-based block bi, built (or rebuilt when lambda
+// changed, Helmholtz) column by column: column n of every H^e of the block is
+// the FP64 sum-factorised operator applied to the block's n-th unit
+// coefficient vectors.  Synchronises s when it builds.
+cudaError_t ensure_matrix(hp_op op, size_t bi, double lambda, cudaStream_t s) {
+    if (op->mat.size() != op->strat.size()) {
+        op->mat.assign(op->strat.size(), nullptr);
+        op->mat_lambda.assign(op->strat.size(), 0.0);
+    }
+    if (op->mat[bi] && (op->kind != HP_HELMHOLTZ || op->mat_lambda[bi] == lambda)) return cudaSuccess;
+    hp_mesh m = op->mesh;
+    const Block& b = m->blocks[bi];
+    const int NP = n_modes(b.shape, b.P);
+    const bool f64 = op->dtype == HP_FP64;
+    const int64_t ne = b.n_elem;
+    cudaError_t e = cudaSuccess;
+    if (!op->mat[bi]) {
+        e = cudaMalloc(&op->mat[bi], (size_t)ne * NP * NP * (f64 ? 8 : 4));
+        if (e != cudaSuccess) { op->mat[bi] = nullptr; return e; }
+    }
+    const int64_t ncoef = m->coeff_off.back();
+    double* x = nullptr;
+    double* y = nullptr;
+    e = cudaMalloc(&x, sizeof(double) * ncoef);
+    if (e == cudaSuccess) e = cudaMalloc(&y, sizeof(double) * ncoef);
+    for (int col = 0; col < NP && e == cudaSuccess; ++col) {
+        e = mat_unit(x, b.d_coeff_off, ne, NP, col, s);
+        if (e == cudaSuccess) e = launch_sf64(m, b, op->kind, lambda, x, y, op->d_err, s);
+        if (e == cudaSuccess) e = mat_collect(y, b.d_coeff_off, ne, NP, col, op->mat[bi], f64, s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(x);
+    cudaFree(y);
+    if (e != cudaSuccess) {
+        cudaFree(op->mat[bi]);
+        op->mat[bi] = nullptr;
+        return e;
+    }
+    op->mat_lambda[bi] = lambda;
+    return cudaSuccess;
+}
+
 cudaError_t launch_block(hp_op op, size_t bi, int tile, double lambda, const void* in, void* out, cudaStream_t s) {
     hp_mesh m = op->mesh;
     const Block& b = m->blocks[bi];
+    if (op->strat[bi] == HP_STRAT_MATRIX) {
+        cudaError_t e = ensure_matrix(op, bi, lambda, s);
+        if (e != cudaSuccess) return e;
+        return mat_apply(op->mat[bi], b.d_coeff_off, b.n_elem, n_modes(b.shape, b.P), in, out, op->dtype == HP_FP64, s);
+    }
     const DeviceBlobs& blob = m->blobs.at(b.shape * 16 + b.P);
     const int64_t nphys = m->phys_off.back();
     if ((op->dtype == HP_TF32 || op->dtype == HP_BF16) && op->strat[bi] == HP_STRAT_ELEMAT) {
@@ -712,7 +783,7 @@ hp_status hp_op_create(hp_mesh m, hp_opkind kind, hp_strategy strategy, hp_dtype
     if (!m || !out) { set_error("hp_op_create: null argument"); return HP_ERR_ARG; }
     *out = nullptr;
     if ((int)kind < 0 || kind > HP_IPRODUCT_WRT_DERIV_BASE) { set_error("hp_op_create: bad kind"); return HP_ERR_ARG; }
-    if ((int)strategy < 0 || strategy > HP_STRAT_AUTO) { set_error("hp_op_create: bad strategy"); return HP_ERR_ARG; }
+    if ((int)strategy < 0 || strategy > HP_STRAT_MATRIX) { set_error("hp_op_create: bad strategy"); return HP_ERR_ARG; }
     if ((int)dtype < 0 || dtype > HP_BF16) { set_error("hp_op_create: bad dtype"); return HP_ERR_ARG; }
     const bool tcore = dtype == HP_TF32 || dtype == HP_BF16;
     if (strategy == HP_STRAT_AUTO) strategy = tcore ? HP_STRAT_ELEMAT : HP_STRAT_SUMFAC;
@@ -725,12 +796,16 @@ hp_status hp_op_create(hp_mesh m, hp_opkind kind, hp_strategy strategy, hp_dtype
         set_error("hp_op_create: derivative building blocks exist only with HP_STRAT_SUMFAC");
         return HP_ERR_UNSUPPORTED;
     }
+    if (strategy == HP_STRAT_MATRIX && kind != HP_MASS && kind != HP_LAPLACIAN && kind != HP_HELMHOLTZ) {
+        set_error("hp_op_create: HP_STRAT_MATRIX stores mass, Laplacian or Helmholtz matrices");
+        return HP_ERR_UNSUPPORTED;
+    }
     DeviceGuard guard(m->device);
     hp_status st = ensure_geom(m, needs_deriv_geom(kind), dtype != HP_FP64, 0);
     if (st) return st;
     if (tcore) {
         if ((st = ensure_tc(m, dtype == HP_BF16 ? 2 : 4))) return st;
-    } else if (strategy != HP_STRAT_SUMFAC && (st = ensure_dense(m))) {
+    } else if ((strategy == HP_STRAT_ELEMAT || strategy == HP_STRAT_HYBRID) && (st = ensure_dense(m))) {
         return st;
     }
     auto op = new hp_op_s();
@@ -743,6 +818,11 @@ hp_status hp_op_create(hp_mesh m, hp_opkind kind, hp_strategy strategy, hp_dtype
     if (tcore)   // blocks beyond the tensor-memory budget run FP32 sum factorisation
         for (size_t i = 0; i < m->blocks.size(); ++i)
             if (!tc_fits(m->blocks[i])) op->strat[i] = HP_STRAT_SUMFAC;
+    if (strategy == HP_STRAT_MATRIX)   // blocks beyond the stored-matrix size run sum factorisation
+        for (size_t i = 0; i < m->blocks.size(); ++i)
+            if (!mat_fits(m->blocks[i])) op->strat[i] = HP_STRAT_SUMFAC;
+    op->mat.assign(m->blocks.size(), nullptr);
+    op->mat_lambda.assign(m->blocks.size(), 0.0);
     st = upload<unsigned int>(&op->d_err, nullptr, 1);
     if (!st) cudaMemset(op->d_err, 0, sizeof(unsigned int));
     if (st) { delete op; return st; }
@@ -902,7 +982,16 @@ hp_status hp_op_strategies(hp_op op, int* strat, int64_t n_blocks, int set) {
     }
     bool dense = false;
     for (int64_t i = 0; i < n_blocks; ++i) {
-        if (strat[i] < HP_STRAT_SUMFAC || strat[i] > HP_STRAT_HYBRID) { set_error("hp_op_strategies: bad strategy"); return HP_ERR_ARG; }
+        if (strat[i] < HP_STRAT_SUMFAC || strat[i] > HP_STRAT_MATRIX || strat[i] == HP_STRAT_AUTO) {
+            set_error("hp_op_strategies: bad strategy");
+            return HP_ERR_ARG;
+        }
+        if (strat[i] == HP_STRAT_MATRIX &&
+            ((op->kind != HP_MASS && op->kind != HP_LAPLACIAN && op->kind != HP_HELMHOLTZ) ||
+             op->dtype == HP_TF32 || op->dtype == HP_BF16 || !mat_fits(op->mesh->blocks[i]))) {
+            set_error("hp_op_strategies: HP_STRAT_MATRIX is for FP64 / FP32 mass, Laplacian or Helmholtz blocks of at most 256 modes");
+            return HP_ERR_UNSUPPORTED;
+        }
         if (strat[i] != HP_STRAT_SUMFAC && needs_deriv_geom(op->kind)) {
             set_error("hp_op_strategies: derivative building blocks exist only with HP_STRAT_SUMFAC");
             return HP_ERR_UNSUPPORTED;
@@ -912,13 +1001,20 @@ hp_status hp_op_strategies(hp_op op, int* strat, int64_t n_blocks, int set) {
             set_error("hp_op_strategies: HP_TF32 / HP_BF16 blocks are tensor-core elemental-matrix (N_P <= 256) or FP32 sum factorisation");
             return HP_ERR_UNSUPPORTED;
         }
-        dense |= strat[i] != HP_STRAT_SUMFAC && op->dtype != HP_TF32 && op->dtype != HP_BF16;
+        dense |= (strat[i] == HP_STRAT_ELEMAT || strat[i] == HP_STRAT_HYBRID) && op->dtype != HP_TF32 &&
+                 op->dtype != HP_BF16;
     }
     if (dense) {
         hp_status st = ensure_dense(op->mesh);
         if (st) return st;
     }
-    for (int64_t i = 0; i < n_blocks; ++i) op->strat[i] = strat[i];
+    for (int64_t i = 0; i < n_blocks; ++i) {
+        op->strat[i] = strat[i];
+        if (strat[i] != HP_STRAT_MATRIX && i < (int64_t)op->mat.size() && op->mat[i]) {   // release its matrices
+            cudaFree(op->mat[i]);
+            op->mat[i] = nullptr;
+        }
+    }
     if (op->graph) { cudaGraphExecDestroy(op->graph); op->graph = nullptr; }
     return HP_OK;
 }
@@ -1116,6 +1212,7 @@ hp_status hp_op_block_work(hp_op op, int64_t block, int64_t* n_elem, int64_t* ou
         ne_tot += b.n_elem;
         const int st = op->strat[bi];
         const double fd = st == HP_STRAT_SUMFAC ? elem_flops(b.shape, b.P, op->kind)
+                        : st == HP_STRAT_MATRIX ? 2.0 * np * np
                                                 : elem_flops_dense(b.shape, b.P, op->kind, st == HP_STRAT_HYBRID);
         fl += ne * fd;
         fx += ne * (st == HP_STRAT_SUMFAC ? elem_flops_exec(b.shape, b.P, op->kind, op->dtype == HP_FP64) : fd);
@@ -1132,6 +1229,7 @@ hp_status hp_op_block_work(hp_op op, int64_t block, int64_t* n_elem, int64_t* ou
             case HP_IPRODUCT_WRT_DERIV_BASE: geo = b.curved ? 10 * NQ : 10; break;
             default: geo = 0;
         }
+        if (st == HP_STRAT_MATRIX) geo = np * np;   // the stored matrix takes the place of the factors
         by += ne * ((in_v + out_v + geo) * vs + 8.0);
     }
     if (n_elem) *n_elem = ne_tot;
@@ -1152,6 +1250,7 @@ void hp_op_destroy(hp_op op) {
     DeviceGuard guard(op->mesh->device);
     if (op->graph) cudaGraphExecDestroy(op->graph);
     for (cudaStream_t t : op->pool) cudaStreamDestroy(t);
+    for (void* p : op->mat) cudaFree(p);
     cudaFree(op->d_err);
     delete op;
 }

@@ -111,6 +111,10 @@ struct hp_op_s {
     std::vector<int> tile;                      // tile variant per block
     std::vector<int> strat;                     // hp_strategy per block (SUMFAC, ELEMAT, HYBRID)
     int collocated = 1;                         // 0: FP64 sum-factorised Laplacian/Helmholtz in the non-collocated form
+    // matrix-based blocks: stored H^e as Ht[n][e][m] (FP64 or FP32, the op's I/O type), built on
+    // the first apply, and again when lambda changes (Helmholtz)
+    std::vector<void*> mat;
+    std::vector<double> mat_lambda;
     // CUDA graph of one apply (blocks as independent nodes), for fixed (lambda, in, out)
     cudaGraphExec_t graph = nullptr;
     const void* g_in = nullptr;
@@ -214,6 +218,13 @@ int sf_epb_host(int P, int tile, bool f64);
 // non-collocated FP64 sum factorisation (hp_sf_nc.cu): the derivatives by
 // sum-factorisation passes with the derivative tables dtab = [Tbd | Tcd]
 cudaError_t sf_nc_launch(int shape, int P, bool affine, const SFArgs<double>& a, const double* dtab, cudaStream_t s);
+// matrix-based strategy (hp_mat.cu)
+constexpr int kMatMaxModes = 256;
+cudaError_t mat_unit(double* x, const int64_t* coeff_off, int64_t ne, int NP, int m, cudaStream_t s);
+cudaError_t mat_collect(const double* y, const int64_t* coeff_off, int64_t ne, int NP, int m, void* Ht, bool f64,
+                        cudaStream_t s);
+cudaError_t mat_apply(const void* Ht, const int64_t* coeff_off, int64_t ne, int NP, const void* in, void* out, bool f64,
+                      cudaStream_t s);
 constexpr int kTiles = 3;
 
 }  // namespace hp

@@ -26,6 +26,7 @@ HP_HEX, HP_PRISM, HP_PYR, HP_TET = range(4)
 HP_MASS, HP_LAPLACIAN, HP_HELMHOLTZ, HP_BWDTRANS, HP_IPRODUCT_WRT_BASE, HP_PHYSDERIV, \
     HP_IPRODUCT_WRT_DERIV_BASE = range(7)
 HP_STRAT_SUMFAC, HP_STRAT_ELEMAT, HP_STRAT_HYBRID, HP_STRAT_AUTO = range(4)
+HP_STRAT_MATRIX = 4
 HP_FP64, HP_FP32, HP_TF32, HP_BF16 = range(4)
 
 EXPORTED = ["hp_mesh_create", "hp_mesh_layout", "hp_geom_factors", "hp_geom_copy", "hp_op_create",
