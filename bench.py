@@ -483,23 +483,28 @@ def padaptive(device, reps=10):
     forms = {}
     # scheduled forms: "exhaustive" times every block alone; "graph" searches on
     # the time of the whole concurrent graph (coordinate descent over blocks)
-    for name, strat, dt, sched in (("fp32_sumfac", hp.HP_STRAT_SUMFAC, hp.HP_FP32, None),
+    for name, strat, dt, sched in (("fp64_graph_scheduled", hp.HP_STRAT_SUMFAC, hp.HP_FP64, "graph"),
+                                   ("fp32_sumfac", hp.HP_STRAT_SUMFAC, hp.HP_FP32, None),
+                                   ("fp32_graph_scheduled", hp.HP_STRAT_SUMFAC, hp.HP_FP32, "graph"),
                                    ("tf32_tensor_core", hp.HP_STRAT_ELEMAT, hp.HP_TF32, None),
                                    ("tf32_scheduled", hp.HP_STRAT_ELEMAT, hp.HP_TF32, "exhaustive"),
                                    ("tf32_graph_scheduled", hp.HP_STRAT_ELEMAT, hp.HP_TF32, "graph"),
                                    ("bf16_tensor_core", hp.HP_STRAT_ELEMAT, hp.HP_BF16, None),
                                    ("bf16_graph_scheduled", hp.HP_STRAT_ELEMAT, hp.HP_BF16, "graph")):
         op = hp.hp_op_create(h, hp.HP_HELMHOLTZ, strat, dt)
+        xi, yo = (x, y) if dt == hp.HP_FP64 else (x32, y32)
         if sched == "exhaustive":
-            hp.hp_op_schedule_exhaustive(op, 1.0, x32, y32, nblocks, stream)
+            hp.hp_op_schedule_exhaustive(op, 1.0, xi, yo, nblocks, stream)
         elif sched == "graph":
-            hp.hp_op_schedule_graph(op, 1.0, x32, y32, 5, 2, stream)
-        ms = timed(lambda: hp.hp_op_apply_graph(op, 1.0, x32, y32, stream))
+            hp.hp_op_schedule_graph(op, 1.0, xi, yo, 5, 2 if dt in (hp.HP_TF32, hp.HP_BF16) else 1, stream)
+        ms = timed(lambda: hp.hp_op_apply_graph(op, 1.0, xi, yo, stream))
         st = hp.hp_op_strategies(op, nblocks)
-        err = float((y32.double() - y64).abs().max() / y64.abs().max())
+        err = float((yo.double() - y64).abs().max() / y64.abs().max())
         forms[name] = {"ms": round(ms, 4), "gdofs": round(dofs / (ms * 1e-3) / 1e9, 4),
                        "rel_err_vs_fp64": float("%.3g" % err),
-                       "blocks_on_tensor_core": int((st == hp.HP_STRAT_ELEMAT).sum()) if dt in (hp.HP_TF32, hp.HP_BF16) else 0}
+                       "blocks_on_tensor_core": int((st == hp.HP_STRAT_ELEMAT).sum()) if dt in (hp.HP_TF32, hp.HP_BF16) else 0,
+                       "strategy_histogram": {k: int((st == v).sum()) for k, v in
+                                              (("sumfac", 0), ("elemat", 1), ("hybrid", 2), ("matrix", 4)) if (st == v).any()}}
         hp.hp_op_destroy(op)
     hp.hp_mesh_destroy(h)
     g = lambda ms: round(dofs / (ms * 1e-3) / 1e9, 4)

@@ -275,14 +275,20 @@ hp_status hp_op_schedule(hp_op op, hp_mlp mlp, void* stream);
 
 /* Exhaustive schedule: time every strategy of every block on the given arrays
  * (contents overwritten) and keep the fastest; times_ms[3*block + strategy]
- * (may be NULL) receives the timings (1e30 for strategies not available). */
+ * (may be NULL) receives the timings (1e30 for strategies not available).
+ * The strategies are HP_STRAT_SUMFAC, HP_STRAT_ELEMAT and HP_STRAT_HYBRID (the
+ * three the cost model predicts); hp_op_schedule_graph also tries stored matrices. */
 hp_status hp_op_schedule_exhaustive(hp_op op, double lambda, const void* in, void* out, float* times_ms,
                                     void* stream);
 
 /* Graph-aware schedule (not in the paper): coordinate descent on the time of
  * the whole concurrent graph launch of hp_op_apply_graph.  Starting from the
  * current strategies, each block in turn tries every other strategy built for
- * it and keeps one only if the graph's median time over `reps` timed launches
+ * it (HP_FP64 / HP_FP32 mass, Laplacian and Helmholtz: sum factorisation,
+ * elemental matrix, hybrid and, for blocks of at most 256 modes whose matrices
+ * fit in half of the free device memory, stored matrices; HP_TF32 / HP_BF16:
+ * FP32 sum factorisation and the tensor-core elemental matrix) and keeps one
+ * only if the graph's median time over `reps` timed launches
  * (after a warm-up) drops by more than 1 %; `passes` sweeps over the blocks.
  * Per-block times taken alone (hp_op_schedule_exhaustive) miss the overlap of
  * the blocks that run concurrently in the graph.  in/out as for

@@ -288,15 +288,21 @@ hp_status ensure_tc(hp_mesh m, int es) {
 }
 
 bool tc_fits(const Block& b) { return n_modes(b.shape, b.P) <= kTcMaxModes; }
+bool mat_fits(const Block& b) { return n_modes(b.shape, b.P) <= kMatMaxModes; }
 
-// strategy k (HP_STRAT_SUMFAC / ELEMAT / HYBRID) is built for block i of op:
-// derivative building blocks are sum-factorised only; a TF32 operator has FP32
-// sum factorisation and the tensor-core elemental matrix (N_P <= 256)
+// strategy k (HP_STRAT_SUMFAC / ELEMAT / HYBRID / MATRIX) is built for block i
+// of op: derivative building blocks are sum-factorised only; a TF32 / BF16
+// operator has FP32 sum factorisation and the tensor-core elemental matrix
+// (N_P <= 256); stored matrices are mass, Laplacian or Helmholtz in FP64 /
+// FP32 (N_P <= 256)
 bool strategy_available(const hp_op_s* op, size_t i, int k) {
     if (k == HP_STRAT_SUMFAC) return true;
     if (needs_deriv_geom(op->kind)) return false;
     if (op->dtype == HP_TF32 || op->dtype == HP_BF16) return k == HP_STRAT_ELEMAT && tc_fits(op->mesh->blocks[i]);
-    return true;
+    if (k == HP_STRAT_MATRIX)
+        return (op->kind == HP_MASS || op->kind == HP_LAPLACIAN || op->kind == HP_HELMHOLTZ) &&
+               mat_fits(op->mesh->blocks[i]);
+    return k == HP_STRAT_ELEMAT || k == HP_STRAT_HYBRID;
 }
 
 // flops of the elemental-matrix (hybrid = false) or hybrid strategy per element
@@ -399,8 +405,6 @@ cudaError_t launch_sf64(hp_mesh m, const Block& b, int kind, double lambda, cons
     return sf_launch_f64(b.shape, b.P, !b.curved, 0, a, s);
 }
 
-bool mat_fits(const Block& b) { return n_modes(b.shape, b.P) <= kMatMaxModes; }
-
 // Stored matrices of matrix-based block bi, built (or rebuilt when lambda
 // changed, Helmholtz) column by column: column n of every H^e of the block is
 // the FP64 sum-factorised operator applied to the block's n-th unit
@@ -419,13 +423,18 @@ cudaError_t ensure_matrix(hp_op op, size_t bi, double lambda, cudaStream_t s) {
     cudaError_t e = cudaSuccess;
     if (!op->mat[bi]) {
         e = cudaMalloc(&op->mat[bi], (size_t)ne * NP * NP * (f64 ? 8 : 4));
-        if (e != cudaSuccess) { op->mat[bi] = nullptr; return e; }
+        if (e != cudaSuccess) {
+            cudaGetLastError();   // an allocation failure is reported here, not by the next launch
+            op->mat[bi] = nullptr;
+            return e;
+        }
     }
     const int64_t ncoef = m->coeff_off.back();
     double* x = nullptr;
     double* y = nullptr;
     e = cudaMalloc(&x, sizeof(double) * ncoef);
     if (e == cudaSuccess) e = cudaMalloc(&y, sizeof(double) * ncoef);
+    if (e == cudaErrorMemoryAllocation) cudaGetLastError();
     for (int col = 0; col < NP && e == cudaSuccess; ++col) {
         e = mat_unit(x, b.d_coeff_off, ne, NP, col, s);
         if (e == cudaSuccess) e = launch_sf64(m, b, op->kind, lambda, x, y, op->d_err, s);
@@ -1115,6 +1124,19 @@ hp_status hp_op_schedule_exhaustive(hp_op op, double lambda, const void* in, voi
     return hp_op_strategies(op, choice.data(), nb, 1);
 }
 
+// the stored matrices of block i (and the build's two FP64 coefficient
+// vectors) fit in half of the device's free memory
+static bool matrix_room(hp_op op, size_t i) {
+    if (i < op->mat.size() && op->mat[i]) return true;
+    const Block& b = op->mesh->blocks[i];
+    const double NP = n_modes(b.shape, b.P);
+    const double need = (double)b.n_elem * NP * NP * (op->dtype == HP_FP64 ? 8.0 : 4.0) +
+                        16.0 * (double)op->mesh->coeff_off.back();
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) { cudaGetLastError(); return false; }
+    return need < 0.5 * (double)free_b;
+}
+
 hp_status hp_op_schedule_graph(hp_op op, double lambda, const void* in, void* out, int reps, int passes, float* ms,
                                void* stream) {
     if (!op || !in || !out || in == out) { set_error("hp_op_schedule_graph: null or aliasing arrays"); return HP_ERR_ARG; }
@@ -1155,8 +1177,10 @@ hp_status hp_op_schedule_graph(hp_op op, double lambda, const void* in, void* ou
         bool changed = false;
         for (size_t i = 0; i < op->strat.size() && !st; ++i) {
             const int cur = op->strat[i];
-            for (int k = 0; k < 3 && !st; ++k) {
+            for (int k : {HP_STRAT_SUMFAC, HP_STRAT_ELEMAT, HP_STRAT_HYBRID, HP_STRAT_MATRIX}) {
+                if (st) break;
                 if (k == op->strat[i] || !strategy_available(op, i, k)) continue;
+                if (k == HP_STRAT_MATRIX && !matrix_room(op, i)) continue;
                 const int prev = op->strat[i];
                 op->strat[i] = k;
                 float t = 0.f;
@@ -1169,6 +1193,8 @@ hp_status hp_op_schedule_graph(hp_op op, double lambda, const void* in, void* ou
         if (!changed) break;
     }
     if (op->graph) { cudaGraphExecDestroy(op->graph); op->graph = nullptr; }   // built for a trial
+    for (size_t i = 0; i < op->mat.size(); ++i)   // matrices of trials that were not kept
+        if (op->strat[i] != HP_STRAT_MATRIX && op->mat[i]) { cudaFree(op->mat[i]); op->mat[i] = nullptr; }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     if (st) return st;

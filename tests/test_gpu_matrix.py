@@ -206,3 +206,35 @@ def test_matrix_large_block_sampled(hp):
     idx = np.concatenate([np.arange(co[e], co[e + 1]) for e in sample])
     assert rel_err(ys[0][idx], ref[idx]) <= FP64_TOL
     assert abs(x @ ys[1] - z @ ys[0]) <= 1e-12 * abs(x @ ys[0])
+
+
+def test_graph_schedule_may_store_matrices(hp):
+    """FP64 graph-aware schedule of a p-adaptive mesh (P = 1..6): every block
+    keeps a strategy built for it (stored matrices only up to 256 modes), and
+    the scheduled graph matches the oracle at the FP64 bar, at a lambda other
+    than the one scheduled with (stored Helmholtz matrices are rebuilt)."""
+    from oracle.basis import n_modes
+    mesh = inputs.slab_mesh(2, 2, 4, (1, 6), order_seed=5, curved_rule="x_half")
+    keys = block_keys(mesh)
+    nb = len(keys)
+    co, po = oracle_ops.layout(mesh)
+    uh = inputs.random_coefficients(46, co)
+    h = hp.hp_mesh_create(mesh, 0)
+    try:
+        op = hp.hp_op_create(h, KINDS["helmholtz"], hp.HP_STRAT_SUMFAC, hp.HP_FP64)
+        x = torch.tensor(uh, device="cuda:0", dtype=torch.float64)
+        y = torch.zeros(len(uh), device="cuda:0", dtype=torch.float64)
+        ms = hp.hp_op_schedule_graph(op, 1.0, x, y, 3, 1)
+        assert ms > 0
+        st = hp.hp_op_strategies(op, nb)
+        assert np.isin(st, [hp.HP_STRAT_SUMFAC, hp.HP_STRAT_ELEMAT, hp.HP_STRAT_HYBRID, hp.HP_STRAT_MATRIX]).all()
+        for (s, P, c), k in zip(keys, st):
+            if k == hp.HP_STRAT_MATRIX:
+                assert n_modes(s, P) <= 256
+        y.fill_(float("nan"))
+        hp.hp_op_apply_graph(op, 1.3, x, y)
+        hp.hp_op_sync(op)
+        hp.hp_op_destroy(op)
+    finally:
+        hp.hp_mesh_destroy(h)
+    assert rel_err(y.cpu().numpy(), oracle_ops.apply("helmholtz", mesh, uh, 1.3)) <= FP64_TOL
