@@ -171,7 +171,12 @@ hp_status hp_op_create(hp_mesh mesh, hp_opkind kind, hp_strategy strategy, hp_dt
  * `in`/`out`: device arrays sized by hp_mesh_layout for the op's spaces
  * (see hp_opkind); they must not overlap.  lambda is used by HP_HELMHOLTZ.
  * Errors detected before launch: HP_ERR_ARG; launch failure: HP_ERR_CUDA.
- * Device-side errors latch in the op and are returned by hp_op_sync. */
+ * Device-side errors latch in the op and are returned by hp_op_sync.
+ * HP_STRAT_MATRIX blocks build their stored matrices on the first apply (N_P
+ * sum-factorised applies of the block, then a synchronisation of `stream`),
+ * and again on a Helmholtz apply with a different lambda; device memory for
+ * them is allocated there (HP_ERR_CUDA if it is not available).  Later applies
+ * are asynchronous. */
 hp_status hp_op_apply(hp_op op, double lambda, const void* in, void* out, void* stream);
 
 /* Batched apply for meshes with many blocks (p-adaptive / mixed meshes): the

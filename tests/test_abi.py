@@ -53,3 +53,21 @@ def test_null_arguments_are_rejected_without_gpu(lib):
     lib.hp_op_apply.restype = ctypes.c_int
     lib.hp_op_apply.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     assert lib.hp_op_apply(None, 1.0, None, None, None) == 1
+    lib.hp_op_set_collocated.restype = ctypes.c_int
+    lib.hp_op_set_collocated.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    assert lib.hp_op_set_collocated(None, 0) == 1
+    lib.hp_op_strategies.restype = ctypes.c_int
+    lib.hp_op_strategies.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int]
+    assert lib.hp_op_strategies(None, None, 0, 0) == 1
+
+
+def test_binding_constants_match_header():
+    """Every enumerator the header gives an explicit value has the same value in
+    the binding (strategies, shapes, dtypes, statuses, operator kinds)."""
+    from paper_2604_04644_gb300 import hp
+    txt = open(os.path.join(ROOT, "include", "hp.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    values = dict((k, int(v)) for k, v in re.findall(r"\b(HP_[A-Z0-9_]+)\s*=\s*(\d+)", txt))
+    assert values["HP_STRAT_MATRIX"] == 4 and values["HP_STRAT_AUTO"] == 3
+    for name, v in values.items():
+        assert getattr(hp, name) == v, name
