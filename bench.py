@@ -612,10 +612,12 @@ def run_costmodel(local):
                                                           "orders": "U{3..9}", "curved": "x >= 0.5"}}), flush=True)
 
 
-def run_solve(local, cells, order=4, lam=1.0, tol=1e-10):
+def run_solve(local, cells, order=4, lam=1.0, tol=1e-10, scheduled=False):
     """Time to solution of the C0-assembled Helmholtz problem on the conforming
     four-slab mesh (cells^3 cells + pyramid-to-tet transition layer, curved),
-    P = order, f = (3 pi^2 + lambda) sin(pi x) sin(pi y) sin(pi z)."""
+    P = order, f = (3 pi^2 + lambda) sin(pi x) sin(pi y) sin(pi z).  With
+    `scheduled`, also the FP64, FP32-inner and BF16-inner solves with the
+    operators' strategies chosen by the graph-aware schedule."""
     import torch
     from paper_2604_04644_gb300 import hp, inputs
     torch.cuda.set_device(local)
@@ -665,8 +667,38 @@ def run_solve(local, cells, order=4, lam=1.0, tol=1e-10):
         if rc:
             out[name]["error"] = hp.hp_last_error()
         sols[name] = xs
+    # the same solves with the operators' per-block strategies chosen by the
+    # graph-aware schedule (stored matrices included); the first solve of each
+    # kind schedules (its time is reported as setup), the second is timed
+    sched_setup = {}
+    sched_forms = (("fp64_pcg_scheduled", dict(mixed=False)),
+                   ("mixed_fp32_pcg_fp64_ir_scheduled", dict(mixed=True, inner_tol=1e-4)),
+                   ("mixed_bf16_tensor_core_pcg_fp64_ir_scheduled", dict(mixed=3, inner_tol=1e-2)))
+    for name, kw in sched_forms if scheduled else ():
+        torch.cuda.synchronize(dev)
+        t0 = time.time()
+        hp.hp_solve(c0, lam, b, xw, tol=1e-2, max_refinements=1, schedule=True,
+                    **dict(kw, inner_tol=1e-1) if kw["mixed"] else kw)
+        torch.cuda.synchronize(dev)
+        sched_setup[name] = round(time.time() - t0, 2)
+        xs = torch.zeros(ng, device=dev, dtype=torch.float64)
+        torch.cuda.synchronize(dev)
+        t0 = time.time()
+        rc, st = hp.hp_solve(c0, lam, b, xs, tol=tol, schedule=True, **kw)
+        torch.cuda.synchronize(dev)
+        dt = time.time() - t0
+        out[name] = dict(st, seconds=round(dt, 4), status=hp.hp_status_str(rc))
+        if rc:
+            out[name]["error"] = hp.hp_last_error()
+        sols[name] = xs
+    if scheduled:
+        out["setup_s"]["schedule_first_solve"] = sched_setup
     for name, tag in (("mixed_fp32_pcg_fp64_ir", "mixed"), ("mixed_tf32_tensor_core_pcg_fp64_ir", "tf32_tc"),
-                      ("mixed_bf16_tensor_core_pcg_fp64_ir", "bf16_tc")):
+                      ("mixed_bf16_tensor_core_pcg_fp64_ir", "bf16_tc"), ("fp64_pcg_scheduled", "fp64_scheduled"),
+                      ("mixed_fp32_pcg_fp64_ir_scheduled", "mixed_scheduled"),
+                      ("mixed_bf16_tensor_core_pcg_fp64_ir_scheduled", "bf16_tc_scheduled")):
+        if name not in sols:
+            continue
         d = sols["fp64_pcg"] - sols[name]
         out["rel_diff_%s_vs_fp64" % tag] = float(d.norm() / sols["fp64_pcg"].norm())
         out["speedup_%s_vs_fp64" % tag] = round(out["fp64_pcg"]["seconds"] / out[name]["seconds"], 3)
@@ -871,7 +903,7 @@ def main():
         return
     if args.solve:
         if rank == 0:
-            print(json.dumps({"solve": run_solve(local, args.cells or 64)}), flush=True)
+            print(json.dumps({"solve": run_solve(local, args.cells or 64, scheduled=True)}), flush=True)
         return
     if args.costmodel:
         if rank == 0:

@@ -349,6 +349,12 @@ typedef struct {
     double inner_tol;      /* mixed: relative tolerance of each FP32 solve                      */
     int inner_max_iter;    /* mixed: iteration limit of each FP32 solve                         */
     int max_refinements;   /* mixed: refinement steps                                           */
+    int schedule;          /* 1: before the first solve, choose each block's strategy for the   *
+                            * FP64 operator and the inner operator with hp_op_schedule_graph    *
+                            * (sum factorisation, elemental matrix, hybrid, stored matrices;    *
+                            * tensor-core inner operators: FP32 sum factorisation or the        *
+                            * tensor-core elemental matrix), kept for later solves with         *
+                            * schedule = 1; 0: the operators' default strategies               */
 } hp_solve_opts;
 
 typedef struct {

@@ -33,6 +33,7 @@ struct hp_c0_s {
     // solver state (created on first solve)
     hp_op op64 = nullptr, op32 = nullptr;
     int op32_mode = 0;                 // 1: FP32 sum factorisation, 2 / 3: TF32 / BF16 tensor-core elemental matrices
+    int op64_sched = 0, op32_sched = 0;   // strategies chosen by the graph-aware schedule
     double diag_lambda = -1.0;
     double* d_diag = nullptr;          // assembled Jacobi diagonal (global)
     double* d_loc64[2] = {nullptr, nullptr};
@@ -409,12 +410,18 @@ hp_status alloc(T** p, int64_t n) {
     return e == cudaSuccess ? HP_OK : cuda_fail(e, "hp_solve workspace");
 }
 
-hp_status prepare(hp_c0 c, double lambda, int mixed, cudaStream_t s) {
+hp_status prepare(hp_c0 c, double lambda, int mixed, int schedule, cudaStream_t s) {
     hp_status st;
+    if (!schedule && c->op64_sched) {   // back to the default strategies
+        hp_op_destroy(c->op64);
+        c->op64 = nullptr;
+        c->op64_sched = 0;
+    }
     if (!c->op64 && (st = hp_op_create(c->mesh, HP_HELMHOLTZ, HP_STRAT_SUMFAC, HP_FP64, &c->op64))) return st;
-    if (mixed && c->op32 && c->op32_mode != mixed) {
+    if (mixed && c->op32 && (c->op32_mode != mixed || (!schedule && c->op32_sched))) {
         hp_op_destroy(c->op32);
         c->op32 = nullptr;
+        c->op32_sched = 0;
     }
     if (mixed && !c->op32) {
         st = mixed == 3 ? hp_op_create(c->mesh, HP_HELMHOLTZ, HP_STRAT_ELEMAT, HP_BF16, &c->op32)
@@ -461,6 +468,19 @@ hp_status prepare(hp_c0 c, double lambda, int mixed, cudaStream_t s) {
         cudaError_t e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return cuda_fail(e, "element diagonal");
         c->diag_lambda = lambda;
+    }
+    // graph-aware strategy choice, timed on the local work vectors (zeroed)
+    if (schedule && !c->op64_sched) {
+        cudaError_t e = cudaMemsetAsync(c->d_loc64[0], 0, sizeof(double) * c->n_local, s);
+        if (e != cudaSuccess) return cuda_fail(e, "hp_solve schedule");
+        if ((st = hp_op_schedule_graph(c->op64, lambda, c->d_loc64[0], c->d_loc64[1], 5, 1, nullptr, s))) return st;
+        c->op64_sched = 1;
+    }
+    if (schedule && mixed && !c->op32_sched) {
+        cudaError_t e = cudaMemsetAsync(c->d_loc32[0], 0, sizeof(float) * c->n_local, s);
+        if (e != cudaSuccess) return cuda_fail(e, "hp_solve schedule");
+        if ((st = hp_op_schedule_graph(c->op32, lambda, c->d_loc32[0], c->d_loc32[1], 5, 1, nullptr, s))) return st;
+        c->op32_sched = 1;
     }
     return HP_OK;
 }
@@ -718,7 +738,7 @@ hp_status hp_c0_diagonal(hp_c0 c, double lambda, double* diag, int local, void* 
     if (!c || !diag) { set_error("hp_c0_diagonal: null argument"); return HP_ERR_ARG; }
     cudaSetDevice(c->mesh->device);
     cudaStream_t s = (cudaStream_t)stream;
-    hp_status st = prepare(c, lambda, false, s);
+    hp_status st = prepare(c, lambda, 0, c->op64_sched, s);   // keeps the operators' strategies
     if (st) return st;
     cudaError_t e;
     if (local) {
@@ -735,14 +755,15 @@ hp_status hp_c0_diagonal(hp_c0 c, double lambda, double* diag, int local, void* 
 hp_status hp_solve(hp_c0 c, double lambda, const double* rhs, double* x, const hp_solve_opts* opts,
                    hp_solve_stats* stats, void* stream) {
     if (!c || !rhs || !x || !opts) { set_error("hp_solve: null argument"); return HP_ERR_ARG; }
-    if (!(opts->tol > 0) || opts->max_iter < 1 || opts->mixed < 0 || opts->mixed > 3 ||
+    if (!(opts->tol > 0) || opts->max_iter < 1 || opts->mixed < 0 || opts->mixed > 3 || opts->schedule < 0 ||
+        opts->schedule > 1 ||
         (opts->mixed && (!(opts->inner_tol > 0) || opts->inner_max_iter < 1 || opts->max_refinements < 1))) {
         set_error("hp_solve: bad options");
         return HP_ERR_ARG;
     }
     cudaSetDevice(c->mesh->device);
     cudaStream_t s = (cudaStream_t)stream;
-    hp_status st = prepare(c, lambda, opts->mixed, s);
+    hp_status st = prepare(c, lambda, opts->mixed, opts->schedule, s);
     if (st) return st;
     const int64_t n = c->n_global;
     hp_solve_stats S{};

@@ -314,7 +314,8 @@ def hp_mlp_grad_noalloc(params, n_in, n_hidden, n_out, x, t, batch, grad, loss=N
 
 class hp_solve_opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("mixed", ctypes.c_int),
-                ("inner_tol", ctypes.c_double), ("inner_max_iter", ctypes.c_int), ("max_refinements", ctypes.c_int)]
+                ("inner_tol", ctypes.c_double), ("inner_max_iter", ctypes.c_int), ("max_refinements", ctypes.c_int),
+                ("schedule", ctypes.c_int)]
 
 
 class hp_solve_stats(ctypes.Structure):
@@ -399,12 +400,14 @@ def hp_c0_assemble(c0, loc, glob, mask_boundary=True, stream=None):
 
 
 def hp_solve(c0, lam, rhs, x, tol=1e-10, max_iter=20000, mixed=False, inner_tol=1e-5, inner_max_iter=20000,
-             max_refinements=20, stream=None):
+             max_refinements=20, schedule=False, stream=None):
     """Returns (status, stats); raises for errors other than HP_ERR_NOT_CONVERGED.
     mixed: 0 / False FP64 PCG, 1 / True FP32 inner PCG with FP64 refinement,
-    2 / 3 the same with the TF32 / BF16 tensor-core inner operator."""
+    2 / 3 the same with the TF32 / BF16 tensor-core inner operator.
+    schedule: choose the operators' per-block strategies by the graph-aware
+    schedule (stored matrices included) before the first solve."""
     o = hp_solve_opts(float(tol), int(max_iter), int(mixed), float(inner_tol), int(inner_max_iter),
-                      int(max_refinements))
+                      int(max_refinements), 1 if schedule else 0)
     st = hp_solve_stats()
     rc = _lib.hp_solve(c0, float(lam), _ptr(rhs), _ptr(x), ctypes.byref(o), ctypes.byref(st), _stream(stream))
     if rc not in (HP_OK, HP_ERR_NOT_CONVERGED):
