@@ -16,7 +16,16 @@ per shape/order GDOF/s, the 192 000-element p-adaptive batched apply (FP64 and
 the reduced-precision graph forms), a strategy table, the FP32 / TF32 / BF16
 forms of the bench mesh with their error against FP64, and the time to solution
 of the assembled Helmholtz problem on ~1M elements (FP64 PCG against the
-mixed-precision forms, --no-solve skips it).
+mixed-precision forms, --no-solve skips it).  The p-adaptive forms include the
+FP64 and FP32 graph-scheduled applies, whose per-block strategy may be the
+stored element matrix.
+
+Other modes (instead of the timed step): --solve (time to solution alone, with
+the graph-scheduled solves), --block-table (FP32 / TF32 / BF16 per large
+block), --collocation-study (collocated vs non-collocated FP64 sum
+factorisation on regular blocks, the paper's collocation study),
+--matrix-study (stored H^e vs sum factorisation), --costmodel,
+--profile-case NAME (one small case for a profiler capture).
 """
 import argparse
 import json
