@@ -415,6 +415,12 @@ cudaError_t ensure_matrix(hp_op op, size_t bi, double lambda, cudaStream_t s) {
         op->mat_lambda.assign(op->strat.size(), 0.0);
     }
     if (op->mat[bi] && (op->kind != HP_HELMHOLTZ || op->mat_lambda[bi] == lambda)) return cudaSuccess;
+    // a captured graph reads the stored matrices in place: rebuilding them for
+    // another lambda makes it stale (hp_op_apply_graph captures afresh)
+    if (op->mat[bi] && op->graph) {
+        cudaGraphExecDestroy(op->graph);
+        op->graph = nullptr;
+    }
     hp_mesh m = op->mesh;
     const Block& b = m->blocks[bi];
     const int NP = n_modes(b.shape, b.P);
