@@ -218,7 +218,8 @@ hp_status hp_op_strategies(hp_op op, int* strategies, int64_t n_blocks, int set)
  * agree up to rounding.  Blocks with other strategies and other operator
  * kinds are unaffected.  HP_ERR_ARG unless collocated is 0 or 1;
  * HP_ERR_UNSUPPORTED for collocated = 0 on an operator that is not HP_FP64.
- * Drops the op's captured graph when the form changes. */
+ * Drops the op's captured graph when the form changes.  hp_op_work and
+ * hp_op_block_work keep reporting the collocated form's operation counts. */
 hp_status hp_op_set_collocated(hp_op op, int collocated);
 
 /* ---------------------------------------------------------------- cost model
