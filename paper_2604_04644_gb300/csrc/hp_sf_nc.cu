@@ -10,9 +10,10 @@
 // the same pointwise metric as the collocated kernel, and the transposed
 // passes
 //   out = C^T [B^T (A^T t + A'^T w_1) + B'^T (A^T w_2)] + C'^T [B^T (A^T w_3)].
-// The eta3 and eta2 passes are shared where the products allow (two eta3
-// passes, three eta2 passes, four eta1 passes forward; the mirror image
-// backward), which is the usual way to organise the non-collocated form.
+// The eta3 and eta2 contractions are shared where the products allow: two
+// eta3 contractions (C, C') in one pass, three eta2 contractions (B f, B' f,
+// B f') in one pass and four eta1 contractions in three passes forward; the
+// mirror image backward.
 // Collocated and non-collocated results agree up to rounding: each 1-D factor
 // has degree <= P < Q, so collocation differentiation of its values is exact.
 //
