@@ -2,11 +2,41 @@
 // chain-rule factor d eta / d xi, and the bulk-copy (TMA) staging of the
 // reference tables into shared memory with bounded mbarrier waits.
 #pragma once
+#include <atomic>
 #include <cstdint>
 
 #include "hp_internal.h"
 
 namespace hp {
+
+// Launch set-up of a persistent kernel on the current device: raises its
+// dynamic shared-memory limit to `smem` there and returns in *cap its grid
+// cap (SMs x resident CTAs).  The result is cached per device ordinal in
+// `caps` (one zero-initialised array per kernel), so a second device gets its
+// own attribute call; two threads that race only repeat the same idempotent
+// calls.
+constexpr int kMaxDevices = 64;
+template <typename K>
+cudaError_t persistent_grid_cap(K kern, int threads, int smem, std::atomic<int>* caps, int* cap) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    int c = caps[dev].load(std::memory_order_acquire);
+    if (c == 0) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        int sms = 0, per = 0;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, threads, smem);
+        if (e != cudaSuccess) return e;
+        c = sms * (per > 0 ? per : 1);
+        caps[dev].store(c, std::memory_order_release);
+    }
+    *cap = c;
+    return cudaSuccess;
+}
 
 // xi(eta) of the collapsed coordinates (paper Sec. 2.3, Duffy transformation;
 // repeated for the 3-D shapes): prism collapses xi1 by xi3, pyramid xi1 and

@@ -331,18 +331,11 @@ template <int SHAPE, int P, bool AFFINE>
 cudaError_t nc_launch_one(const SFArgs<double>& a, const double* dtab, cudaStream_t s) {
     constexpr int smem = nc_smem_bytes<SHAPE, P>();
     static_assert(smem <= 227 * 1024, "non-collocated kernel: shared memory above the per-CTA limit");
-    static int grid_cap = 0;
+    static std::atomic<int> caps[kMaxDevices];
     auto kern = sf_nc_kernel<SHAPE, P, AFFINE>;
-    if (grid_cap == 0) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        int dev = 0, sms = 0, per = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, NCCfg<P>::NT, smem);
-        if (e != cudaSuccess) return e;
-        grid_cap = sms * (per > 0 ? per : 1);
-    }
+    int grid_cap = 0;
+    cudaError_t e = persistent_grid_cap(kern, NCCfg<P>::NT, smem, caps, &grid_cap);
+    if (e != cudaSuccess) return e;
     const int64_t groups = (a.n_elem + NCCfg<P>::EPB - 1) / NCCfg<P>::EPB;
     const int grid = (int)(groups < grid_cap ? groups : grid_cap);
     if (grid <= 0) return cudaSuccess;

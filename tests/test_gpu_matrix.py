@@ -263,3 +263,30 @@ def test_matrix_graph_after_lambda_change(hp):
         hp.hp_mesh_destroy(h)
     assert rel_err(y1.cpu().numpy(), oracle_ops.apply("helmholtz", mesh, x, 1.0)) <= FP64_TOL
     assert rel_err(y2.cpu().numpy(), oracle_ops.apply("helmholtz", mesh, x, 4.0)) <= FP64_TOL
+
+
+def test_matrix_graph_after_block_apply_at_other_lambda(hp):
+    """A graph captured at lambda_1, then hp_op_apply_block of every block at
+    lambda_2 (each rebuilds that block's stored Helmholtz matrices in place),
+    then the graph at lambda_1 again: both outputs match the oracle."""
+    mesh = inputs.slab_mesh(2, 2, 4, 2, curved_rule="x_half")
+    co, po = oracle_ops.layout(mesh)
+    x = inputs.random_coefficients(53, co)
+    nb = len(set(zip(mesh["shape"].tolist(), mesh["P"].tolist(), mesh["curved"].tolist())))
+    h = hp.hp_mesh_create(mesh, 0)
+    try:
+        op = hp.hp_op_create(h, KINDS["helmholtz"], hp.HP_STRAT_MATRIX, hp.HP_FP64)
+        xt = torch.tensor(x, device="cuda:0", dtype=torch.float64)
+        y1 = torch.full((len(x),), float("nan"), device="cuda:0", dtype=torch.float64)
+        y2 = torch.full((len(x),), float("nan"), device="cuda:0", dtype=torch.float64)
+        hp.hp_op_apply_graph(op, 1.0, xt, y1)
+        for b in range(nb):
+            hp.hp_op_apply_block(op, b, 2.5, xt, y2)
+        y1.fill_(float("nan"))
+        hp.hp_op_apply_graph(op, 1.0, xt, y1)
+        hp.hp_op_sync(op)
+        hp.hp_op_destroy(op)
+    finally:
+        hp.hp_mesh_destroy(h)
+    assert rel_err(y1.cpu().numpy(), oracle_ops.apply("helmholtz", mesh, x, 1.0)) <= FP64_TOL
+    assert rel_err(y2.cpu().numpy(), oracle_ops.apply("helmholtz", mesh, x, 2.5)) <= FP64_TOL
