@@ -176,7 +176,11 @@ hp_status hp_op_create(hp_mesh mesh, hp_opkind kind, hp_strategy strategy, hp_dt
  * sum-factorised applies of the block, then a synchronisation of `stream`),
  * and again on a Helmholtz apply with a different lambda; device memory for
  * them is allocated there (HP_ERR_CUDA if it is not available).  Later applies
- * are asynchronous. */
+ * are asynchronous.  A rebuild for a new lambda overwrites the matrices in
+ * place: it first waits for all work already queued on the device (applies
+ * and graph replays of this op on any stream finish before it), and it drops
+ * the op's captured graph.  The caller must not queue applies of the same op
+ * on other streams while such a call runs. */
 hp_status hp_op_apply(hp_op op, double lambda, const void* in, void* out, void* stream);
 
 /* Batched apply for meshes with many blocks (p-adaptive / mixed meshes): the
@@ -200,11 +204,16 @@ hp_status hp_op_tune(hp_op op, double lambda, const void* in, void* out, void* s
 hp_status hp_op_tiles(hp_op op, int* tiles, int64_t n_blocks, int set);
 
 /* Read (set = 0) or write (set = 1) the implementation strategy of each block
- * (HP_STRAT_SUMFAC, HP_STRAT_ELEMAT or HP_STRAT_HYBRID).  Writing builds the
- * dense reference matrices if a block needs them.  HP_ERR_UNSUPPORTED for a
- * dense strategy on a derivative building block, and for an HP_TF32 operator
- * for anything but HP_STRAT_SUMFAC (FP32) or HP_STRAT_ELEMAT (tensor core,
- * blocks of at most 256 modes). */
+ * (HP_STRAT_SUMFAC, HP_STRAT_ELEMAT, HP_STRAT_HYBRID or HP_STRAT_MATRIX).
+ * Writing builds the dense reference matrices if a block needs them.
+ * HP_STRAT_MATRIX is accepted for HP_FP64 / HP_FP32 mass, Laplacian and
+ * Helmholtz operators on blocks of at most 256 modes (its matrices are built
+ * by the next apply); a block that leaves HP_STRAT_MATRIX frees its stored
+ * matrices at once.  HP_ERR_UNSUPPORTED for a dense strategy on a derivative
+ * building block, for HP_STRAT_MATRIX outside those limits, and for an
+ * HP_TF32 / HP_BF16 operator for anything but HP_STRAT_SUMFAC (FP32) or
+ * HP_STRAT_ELEMAT (tensor core, blocks of at most 256 modes).  Writing drops
+ * the op's captured graph. */
 hp_status hp_op_strategies(hp_op op, int* strategies, int64_t n_blocks, int set);
 
 /* Form of the sum-factorised Laplacian and Helmholtz blocks of an HP_FP64
@@ -276,14 +285,32 @@ hp_status hp_mlp_grad_noalloc(const float* params, int n_in, int n_hidden, int n
 
 /* Pick each block's strategy as the argmin of the network's 3 outputs (the
  * predicted log times of SUMFAC, ELEMAT, HYBRID) on the block's features.
- * Derivative building blocks stay SUMFAC. */
+ * Derivative building blocks stay SUMFAC.  Same as hp_op_schedule_mlp with
+ * graph_launch = 0. */
 hp_status hp_op_schedule(hp_op op, hp_mlp mlp, void* stream);
 
+/* Pick each block's strategy as the argmin, over the strategies built for the
+ * block, of the network's predicted log times.  The network maps 5 or 6
+ * features to 3 or 4 outputs: the features of hp_op_block_features, then (6
+ * inputs) graph_launch: 1 when the blocks will run as the concurrent graph of
+ * hp_op_apply_graph, 0 when one after another (hp_op_apply); the outputs are
+ * the predicted log times of SUMFAC, ELEMAT, HYBRID and (4 outputs) MATRIX.
+ * For an HP_TF32 / HP_BF16 operator output 0 is its FP32 sum factorisation
+ * and output 1 its tensor-core elemental matrix; the other strategies are not
+ * built for it and never chosen.  Derivative building blocks stay SUMFAC.
+ * Drops the op's captured graph.  Errors: HP_ERR_ARG (null arguments,
+ * graph_launch not 0 or 1, network of another shape), HP_ERR_CUDA. */
+hp_status hp_op_schedule_mlp(hp_op op, hp_mlp mlp, int graph_launch, void* stream);
+
 /* Exhaustive schedule: time every strategy of every block on the given arrays
- * (contents overwritten) and keep the fastest; times_ms[3*block + strategy]
- * (may be NULL) receives the timings (1e30 for strategies not available).
- * The strategies are HP_STRAT_SUMFAC, HP_STRAT_ELEMAT and HP_STRAT_HYBRID (the
- * three the cost model predicts); hp_op_schedule_graph also tries stored matrices. */
+ * (contents overwritten; each block launched alone, one warm-up launch, which
+ * also builds stored matrices, and two timed) and keep the fastest;
+ * times_ms[4*block + k] (may be NULL) receives the timings for k = 0..3 =
+ * HP_STRAT_SUMFAC, HP_STRAT_ELEMAT, HP_STRAT_HYBRID, HP_STRAT_MATRIX (1e30 for
+ * strategies not built for the block, and for stored matrices that would not
+ * fit in half of the free device memory).  Stored matrices of trials that are
+ * not kept are freed.  Synchronises `stream`.  hp_op_schedule_graph searches
+ * on the time of the whole concurrent graph instead. */
 hp_status hp_op_schedule_exhaustive(hp_op op, double lambda, const void* in, void* out, float* times_ms,
                                     void* stream);
 
@@ -375,9 +402,97 @@ hp_status hp_solve(hp_c0 c0, double lambda, const double* rhs, double* x, const 
                    hp_solve_stats* stats, void* stream);
 void hp_c0_destroy(hp_c0 c0);
 
+/* ---------------------------------------------------------------- multi-GPU layout (host only)
+ * The element-local operators of Sec. 2 need no exchange: a partition of the
+ * elements is a partition of the work.  The assembled problem couples
+ * elements through shared global DOFs: each CG iteration needs one sum over
+ * the interface DOFs that partitions share and two dot products.  These calls
+ * build that layout on the host, with no GPU; the data moves between ranks by
+ * the caller's transport (e.g. torch.distributed). */
+
+/* Partition the elements of `desc` into nparts parts (part[n_elem] in
+ * 0..nparts-1) balanced by predicted cost: cost[n_elem] (NULL: each element's
+ * floating-point operations in the collocated sum-factorised Helmholtz
+ * operator, which sets the time of the FP64 path).  method 0: ranges of the block order (blocks of
+ * equal shape, order and curvature in order of first appearance, user order
+ * inside a block), cut where the cost prefix crosses k/nparts of the total, so
+ * each part keeps few, large blocks (element-local operators); method 1:
+ * recursive coordinate bisection of the element centroids, each split along
+ * the axis of largest extent at the cost fraction of its halves (compact
+ * parts, small interfaces: the assembled solve).  Deterministic.  Errors:
+ * HP_ERR_ARG (null arrays, nparts outside 1..65536, bad method, negative or
+ * non-finite cost, vertex id out of range, bad shape or order). */
+hp_status hp_partition(const hp_mesh_desc* desc, const double* cost, int nparts, int method, int32_t* part);
+
+/* Halo plan of one rank for the assembled solve, from the one-rank C0 map
+ * (gid, sign over the one-rank coefficient layout coeff_offset[n_elem+1], as
+ * hp_c0_maps / hp_c0_map_host give) and an element partition.  The rank's
+ * local coefficients are those of its elements in user order; it holds
+ * copies of its "touched" global DOFs (ascending gid), of which it owns those
+ * whose lowest holding rank it is.  One halo sum = reduce (each rank sends
+ * the signed local copies of DOFs owned elsewhere to their owner; the owner
+ * adds every copy, its own and the received ones, in the one-rank local order
+ * starting from 0, so the assembled value has the same bits as
+ * hp_c0_assemble's for any partition) then broadcast (the owner sends each
+ * owned value to every other holder).  Messages between two ranks are in
+ * ascending gid order.  Errors: HP_ERR_ARG (bad sizes, ids, signs or parts),
+ * HP_ERR_OOM. */
+typedef struct hp_halo_s* hp_halo;
+hp_status hp_halo_create(const int64_t* gid, const int8_t* sign, const int64_t* coeff_offset, int64_t n_elem,
+                         int64_t n_global, const int32_t* part, int nparts, int rank, hp_halo* out);
+/* Sizes: local coefficients, touched and owned global DOFs (any pointer may be NULL). */
+hp_status hp_halo_info(hp_halo h, int64_t* n_local, int64_t* n_touched, int64_t* n_owned);
+/* Message sizes (values) per peer rank, arrays of nparts (any may be NULL):
+ * reduce sent / received, broadcast sent / received. */
+hp_status hp_halo_counts(hp_halo h, int64_t* reduce_send, int64_t* reduce_recv, int64_t* bcast_send,
+                         int64_t* bcast_recv);
+/* Maps (any may be NULL): local_index[n_local] = index of each local
+ * coefficient in the one-rank layout; touched_gid[n_touched]; owned_gid[n_owned]. */
+hp_status hp_halo_maps(hp_halo h, int64_t* local_index, int64_t* touched_gid, int64_t* owned_gid);
+/* local[n_local] = sign * touched[...] (the rank's part of u_local = A u_global). */
+hp_status hp_halo_gather(hp_halo h, const double* touched, double* local);
+/* Reduce step, sender side: send[...] = signed local copies for each peer,
+ * peer q's message at the offset given by the prefix of reduce_send counts. */
+hp_status hp_halo_reduce_pack(hp_halo h, const double* local, double* send);
+/* Reduce step, owner side: owned[n_owned] = sum of the copies of each owned
+ * DOF (own signed local values and recv, the peers' messages back to back in
+ * rank order), in the one-rank order. */
+hp_status hp_halo_reduce_sum(hp_halo h, const double* local, const double* recv, double* owned);
+/* Broadcast step: send[...] = owned values for each peer (prefix of
+ * bcast_send counts); unpack writes touched[n_touched] from the rank's owned
+ * values and recv (the peers' messages back to back in rank order). */
+hp_status hp_halo_bcast_pack(hp_halo h, const double* owned, double* send);
+hp_status hp_halo_bcast_unpack(hp_halo h, const double* owned, const double* recv, double* touched);
+void hp_halo_destroy(hp_halo h);
+
+/* Exact dot products (not in the paper; what makes a multi-rank CG take the
+ * same iterates as a one-rank CG).  hp_xdot_acc adds sum_i x[i] y[i] exactly
+ * into acc[hp_xacc_limbs()] (zero it first): each product as its rounded
+ * value and its FMA rounding error, in a fixed-point accumulator of 32-bit
+ * limbs (int64 each) from 2^-1074 up, carries normalised on return.  Ranks
+ * combine accumulators by an integer sum of the limbs (an all-reduce); the
+ * sum is exact and associative, so the result does not depend on the
+ * partition or the order of terms.  hp_xacc_round rounds an accumulator (or
+ * such a sum of at most 2^30 of them) to the nearest double, ties to even.
+ * Products whose error term underflows (|x y| < 2^-969) carry that one
+ * rounding, identically on every partition.  Errors: HP_ERR_ARG. */
+hp_status hp_xdot_acc(const double* x, const double* y, int64_t n, int64_t* acc);
+hp_status hp_xacc_round(const int64_t* acc, double* out);
+int hp_xacc_limbs(void);
+
 /* Synchronise `stream` and report any error latched by the op's kernels
  * (HP_ERR_TIMEOUT, HP_ERR_DEVICE_BOUNDS) or by CUDA. */
 hp_status hp_op_sync(hp_op op, void* stream);
+
+/* Measured FP64 fused multiply-add rate of GPU `device` (not in the paper: the
+ * denominator of the FP64 roofline).  Launches a kernel in which every thread
+ * of a full-occupancy grid runs 8 independent FMA recurrences for `iters`
+ * steps (1..2^24; 20 000 takes a few tens of milliseconds on a GB300), on
+ * `stream`, once to warm up and three times timed with CUDA events; *tflops
+ * receives 2 x FMAs / fastest time, *ms (may be NULL) that time.  Allocates a
+ * small device buffer for the results and synchronises `stream`.
+ * Errors: HP_ERR_ARG, HP_ERR_CUDA. */
+hp_status hp_peak_fp64(int device, int iters, double* tflops, double* ms, void* stream);
 
 /* Algorithmic work of one hp_op_apply: output DOFs (sum of N_P, or of Q^3 for
  * physical-space outputs), flops of the sum-factorised collocated algorithm

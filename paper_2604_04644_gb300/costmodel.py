@@ -2,19 +2,30 @@
 
 The paper chooses an implementation strategy by a fixed rule (StdMat for the
 mass operator, sum factorisation for Helmholtz, Sec. 4).  Here a small MLP
-(5 block features -> 64 -> 64 -> 3 predicted log10 run times of
-{sum-factorised, elemental matrix, hybrid}) is trained on timings that the
-library generates itself, by the library's own forward/backward/Adam kernels
-(hp_mlp_*), and then schedules each block of an operator (hp_op_schedule).
-Exhaustive measurement (hp_op_schedule_exhaustive) is the fallback and the
-judge of its mispredictions.
+predicts, for every block of an operator, the log10 run time of each
+strategy the library builds, and the schedule takes the argmin
+(hp_op_schedule_mlp).  The network is trained on timings the library
+generates itself, by the library's own forward/backward/Adam kernels
+(hp_mlp_*).  Exhaustive measurement is the fallback and the judge of its
+mispredictions: per block alone (hp_op_schedule_exhaustive) or on the time of
+the whole concurrent graph (hp_op_schedule_graph).
 
-Features (hp_op_block_features): shape/3, P/10, curved, log10(elements)/6,
-dtype/2.  One network per operator kind.  For a TF32 operator the three
-outputs are FP32 sum factorisation, the tensor-core elemental matrix, and
-hybrid (not built for TF32: its target is a 10x penalty on the sum-factorised
-time, as is the tensor-core entry of blocks over 256 modes; both schedulers
-skip strategies that are not built).
+Inputs (6): the block features of hp_op_block_features (shape/3, P/10,
+curved, log10(elements)/6, dtype/2) and the launch mode: 0 when the blocks
+run one after another (hp_op_apply), 1 when they run as the concurrent graph
+of hp_op_apply_graph.
+Outputs (4): log10 ms of sum factorisation, elemental matrix, hybrid and
+stored per-element matrices.  For a TF32 / BF16 operator output 0 is its FP32
+sum factorisation and output 1 its tensor-core elemental matrix.  A strategy
+that is not built for a block gets the target 10x its sum-factorised time;
+the schedulers never choose it.
+
+Targets of the two launch modes.  Alone (mode 0): the block's own kernel
+time.  Concurrent (mode 1): in the graph, blocks that do not fill the GPU
+overlap with others, so a block costs its share of the GPU's throughput
+rather than its latency: its per-element time on a block large enough to
+fill the GPU (`n_sat` elements, the largest timed size) times its element
+count.  One grid of single-block timings gives both.
 """
 import statistics
 
@@ -22,19 +33,41 @@ import numpy as np
 
 from . import hp, inputs
 
-STRATS = (hp.HP_STRAT_SUMFAC, hp.HP_STRAT_ELEMAT, hp.HP_STRAT_HYBRID)
-STRAT_NAMES = ("sumfac", "elemat", "hybrid")
+STRATS = (hp.HP_STRAT_SUMFAC, hp.HP_STRAT_ELEMAT, hp.HP_STRAT_HYBRID, hp.HP_STRAT_MATRIX)
+STRAT_NAMES = ("sumfac", "elemat", "hybrid", "matrix")
+N_IN, N_OUT = 6, 4
+_TC = (hp.HP_TF32, hp.HP_BF16)
 
 
-def _time(op, x, y, lam, stream, flush, reps):
+def n_modes(shape, P):
+    """Modes per element of the modified C0 basis (Sec. 2.3): hex (P+1)^3,
+    prism (P+1)^2 (P+2)/2, pyramid (P+1)(P+2)(2P+3)/6, tet (P+1)(P+2)(P+3)/6."""
+    return ((P + 1) ** 3, (P + 1) ** 2 * (P + 2) // 2, (P + 1) * (P + 2) * (2 * P + 3) // 6,
+            (P + 1) * (P + 2) * (P + 3) // 6)[shape]
+
+
+def _built(dtype, kind, shape, P, k):
+    """Strategy column k is built for a block of (shape, P) of this operator."""
+    npm = n_modes(shape, P)
+    if dtype in _TC:
+        return k == 0 or (k == 1 and npm <= 256)
+    if k == 3:
+        return kind in (hp.HP_MASS, hp.HP_LAPLACIAN, hp.HP_HELMHOLTZ) and npm <= 256
+    return True
+
+
+def _time_apply(op, x, y, lam, stream, flush, reps, graph=False):
+    """Median device time (ms) of hp_op_apply (or hp_op_apply_graph), L2
+    flushed before every launch, outside the events; one untimed warm-up."""
     import torch
+    fn = hp.hp_op_apply_graph if graph else hp.hp_op_apply
     ts = []
     for r in range(reps + 1):
         flush.zero_()
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        hp.hp_op_apply(op, lam, x, y, stream)
+        fn(op, lam, x, y, stream)
         b.record(stream)
         b.synchronize()
         if r:
@@ -44,86 +77,88 @@ def _time(op, x, y, lam, stream, flush, reps):
 
 
 def generate_timings(device=0, kind=hp.HP_HELMHOLTZ, shapes=(0, 1, 2, 3), orders=range(1, 11), curved=(0, 1),
-                     sizes=(100, 1000, 10000, 100000, 1000000), dtypes=(hp.HP_FP64, hp.HP_FP32, hp.HP_TF32),
-                     budget_ms=40.0, reps=2, measured_max=100000, log=None):
-    """Time every strategy on single-block meshes of the grid.  A strategy whose
-    time, extrapolated linearly from the next smaller size, would exceed
-    `budget_ms` is not run, nor is any size above `measured_max` elements (at
-    10^5 elements every block already fills the GPU many times over, so time is
-    linear in the element count); their extrapolated times are used (flagged in
-    `meta`).  Returns (X [N,5] float32 features, T [N,3] float32 log10(ms),
-    meta list)."""
+                     sizes=(128, 1024, 8192, 65536), dtypes=(hp.HP_FP64, hp.HP_FP32, hp.HP_BF16),
+                     budget_ms=40.0, reps=2, log=None):
+    """Time every built strategy on single-block meshes of the grid (each
+    block launched alone).  A strategy whose time, extrapolated linearly from
+    the next smaller size, would exceed `budget_ms` is not run; the
+    extrapolated time is used and flagged.  Returns a list of records
+    dict(shape, P, curved, n, dtype, ms[4] (None: not built), extrapolated[4])."""
     import torch
     dev = "cuda:%d" % device
     stream = torch.cuda.current_stream(device)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
-    X, T, meta = [], [], []
+    recs = []
     for shape in shapes:
         for P in orders:
             for cv in curved:
                 prev = {}
                 for n in sizes:
-                    measured = n <= measured_max
-                    if measured:
-                        mesh = inputs.replicated_mesh(shape, P, n, curved=bool(cv))
-                        h = hp.hp_mesh_create(mesh, device)
-                        co, po, nc, nph = hp.hp_mesh_layout(h, n)
-                        uh = inputs.random_coefficients(11, co)
+                    mesh = inputs.replicated_mesh(shape, P, n, curved=bool(cv))
+                    h = hp.hp_mesh_create(mesh, device)
+                    co, po, nc, nph = hp.hp_mesh_layout(h, n)
+                    uh = inputs.random_coefficients(11, co)
                     for dt in dtypes:
-                        feats = np.array([shape / 3.0, P / 10.0, float(cv), np.log10(n) / 6.0,
-                                          (0 if dt == hp.HP_FP64 else dt) / 2.0], dtype=np.float32)
-                        op = None
-                        if measured:
-                            tdt = torch.float64 if dt == hp.HP_FP64 else torch.float32
-                            op = hp.hp_op_create(h, kind, hp.HP_STRAT_ELEMAT if dt == hp.HP_TF32 else hp.HP_STRAT_SUMFAC,
-                                                 dt)
-                            x = torch.tensor(uh, device=dev, dtype=tdt)
-                            y = torch.empty(nc, device=dev, dtype=tdt)
-                            feats = hp.hp_op_block_features(op, 1)[0]
-                            built = hp.hp_op_strategies(op, 1)[0]      # TF32: ELEMAT where the tensor core takes it
-                        times, extrap, avail = [], [], []
+                        tdt = torch.float64 if dt == hp.HP_FP64 else torch.float32
+                        op = hp.hp_op_create(h, kind, hp.HP_STRAT_ELEMAT if dt in _TC else hp.HP_STRAT_SUMFAC, dt)
+                        x = torch.tensor(uh, device=dev, dtype=tdt)
+                        y = torch.empty(nc, device=dev, dtype=tdt)
+                        ms, ex = [None] * 4, [False] * 4
                         for k, st in enumerate(STRATS):
-                            key = (dt, k)
-                            ok = not (dt == hp.HP_TF32 and (k == 2 or (k == 1 and prev.get((dt, "tc")) is False)))
-                            if measured and dt == hp.HP_TF32 and k == 1:
-                                ok = built == hp.HP_STRAT_ELEMAT
-                                prev[(dt, "tc")] = ok
-                            if not ok:
-                                times.append(None)
-                                extrap.append(False)
-                                avail.append(False)
+                            if not _built(dt, kind, shape, P, k):
                                 continue
+                            key = (dt, k)
                             est = prev[key][1] * n / prev[key][0] if key in prev else 0.0
-                            if est > budget_ms or not measured:
-                                t = est
-                                extrap.append(True)
+                            if est > budget_ms:
+                                t, ex[k] = est, True
                             else:
                                 hp.hp_op_strategies(op, 1, [st])
-                                t = _time(op, x, y, 1.0, stream, flush, reps)
-                                extrap.append(False)
+                                t = _time_apply(op, x, y, 1.0, stream, flush, reps)
                             prev[key] = (n, t)
-                            times.append(t)
-                            avail.append(True)
-                        if op is not None:
-                            hp.hp_op_destroy(op)
-                        # strategies that are not built: 10x the sum-factorised time
-                        times = [t if a else 10.0 * times[0] for t, a in zip(times, avail)]
-                        X.append(feats)
-                        T.append(np.log10(np.maximum(times, 1e-4)))
-                        meta.append(dict(shape=shape, P=P, curved=cv, n=n, dtype=dt, ms=times, extrapolated=extrap,
-                                         built=avail))
+                            ms[k] = t
+                        hp.hp_op_destroy(op)
+                        recs.append(dict(shape=shape, P=P, curved=cv, n=n, dtype=dt, ms=ms, extrapolated=ex))
                         if log:
-                            log(meta[-1])
-                    if measured:
-                        hp.hp_mesh_destroy(h)
-    return np.array(X, dtype=np.float32), np.array(T, dtype=np.float32), meta
+                            log(recs[-1])
+                    hp.hp_mesh_destroy(h)
+    return recs
+
+
+def training_set(recs):
+    """(X [N, 6], T [N, 4] log10 ms) with one sample per record and launch
+    mode.  Mode 1 targets: per-element time at the largest timed size of the
+    same (shape, P, curved, dtype) times the element count (for blocks at
+    least that large, their own time)."""
+    big = {}
+    for r in recs:
+        key = (r["shape"], r["P"], r["curved"], r["dtype"])
+        if key not in big or r["n"] > big[key]["n"]:
+            big[key] = r
+    X, T = [], []
+    for r in recs:
+        f = [r["shape"] / 3.0, r["P"] / 10.0, float(r["curved"]), np.log10(r["n"]) / 6.0,
+             (0 if r["dtype"] == hp.HP_FP64 else r["dtype"]) / 2.0]
+        b = big[(r["shape"], r["P"], r["curved"], r["dtype"])]
+        for mode in (0, 1):
+            ms = []
+            for k in range(N_OUT):
+                if r["ms"][k] is None:
+                    ms.append(None)
+                elif mode == 0 or r["n"] >= b["n"]:
+                    ms.append(r["ms"][k])
+                else:
+                    ms.append(b["ms"][k] * r["n"] / b["n"])
+            ms = [t if t is not None else 10.0 * ms[0] for t in ms]
+            X.append(f + [float(mode)])
+            T.append(np.log10(np.maximum(ms, 1e-4)))
+    return np.array(X, dtype=np.float32), np.array(T, dtype=np.float32)
 
 
 def train(X, T, device=0, hidden=64, steps=4000, lr=3e-3, seed=7, decay_at=(0.6, 0.85)):
     """Full-batch Adam on the GPU with the library's kernels; returns (mlp, loss history)."""
     import torch
     dev = "cuda:%d" % device
-    mlp = hp.hp_mlp_create(5, hidden, 3, seed, device)
+    mlp = hp.hp_mlp_create(X.shape[1], hidden, T.shape[1], seed, device)
     xt = torch.tensor(X, device=dev, dtype=torch.float32).contiguous()
     tt = torch.tensor(T, device=dev, dtype=torch.float32).contiguous()
     loss = torch.zeros(1, device=dev, dtype=torch.float32)
@@ -139,17 +174,30 @@ def train(X, T, device=0, hidden=64, steps=4000, lr=3e-3, seed=7, decay_at=(0.6,
 def predict(mlp, X, device=0):
     import torch
     dev = "cuda:%d" % device
+    n_out = hp.hp_mlp_info(mlp)[2]
     xt = torch.tensor(X, device=dev, dtype=torch.float32).contiguous()
-    y = torch.empty((len(X), 3), device=dev, dtype=torch.float32)
+    y = torch.empty((len(X), n_out), device=dev, dtype=torch.float32)
     hp.hp_mlp_forward(mlp, xt, len(X), y)
     torch.cuda.synchronize(device)
     return y.cpu().numpy()
 
 
-def evaluate_schedules(mlp, mesh, kind, dtype=hp.HP_FP64, device=0, reps=5):
-    """Apply time of one operator on `mesh` under three schedules: the paper's
-    rule (elemental matrix for mass, sum factorisation otherwise), the MLP
-    schedule, and the exhaustive-search schedule."""
+def rule_strategy(kind, dtype):
+    """The paper's fixed rule (Sec. 4): the elemental matrix (StdMat) for the
+    mass operator, sum factorisation otherwise.  The paper has no tensor-core
+    form; for TF32 / BF16 the baseline is the tensor core wherever it is built."""
+    if dtype in _TC:
+        return hp.HP_STRAT_ELEMAT
+    return hp.HP_STRAT_ELEMAT if kind == hp.HP_MASS else hp.HP_STRAT_SUMFAC
+
+
+def evaluate_schedules(mlp, mesh, kind, dtype=hp.HP_FP64, device=0, reps=7, graph=True, search=True):
+    """Apply time (ms, median, L2 flushed) of one operator on `mesh`, launched
+    as the concurrent graph (graph=True) or block after block, under: the
+    paper's rule; the MLP schedule for that launch mode; each block's fastest
+    strategy timed alone (hp_op_schedule_exhaustive); and, for graph launches,
+    the search on the whole graph's time (hp_op_schedule_graph, from the
+    rule's strategies) when `search`."""
     import torch
     dev = "cuda:%d" % device
     stream = torch.cuda.current_stream(device)
@@ -159,30 +207,42 @@ def evaluate_schedules(mlp, mesh, kind, dtype=hp.HP_FP64, device=0, reps=5):
     tdt = torch.float64 if dtype == hp.HP_FP64 else torch.float32
     x = torch.tensor(inputs.random_coefficients(21, co), device=dev, dtype=tdt)
     y = torch.empty(nc, device=dev, dtype=tdt)
-    op = hp.hp_op_create(h, kind, hp.HP_STRAT_ELEMAT if dtype == hp.HP_TF32 else hp.HP_STRAT_SUMFAC, dtype)
+    op = hp.hp_op_create(h, kind, hp.HP_STRAT_ELEMAT if dtype in _TC else hp.HP_STRAT_SUMFAC, dtype)
     nb = len(set(zip(mesh["shape"].tolist(), mesh["P"].tolist(), mesh["curved"].tolist())))
-    out = {"blocks": nb}
-    if dtype == hp.HP_TF32:
-        # no rule in the paper for the tensor cores: the baseline is "tensor core wherever it is built"
-        out["rule"] = "tensor core where built (N_P <= 256), FP32 sum factorisation elsewhere"
-    else:
-        rule = hp.HP_STRAT_ELEMAT if kind == hp.HP_MASS else hp.HP_STRAT_SUMFAC
-        hp.hp_op_strategies(op, nb, [rule] * nb)
-        out["rule"] = "elemental matrix for mass, sum factorisation otherwise"
-    out["rule_ms"] = _time(op, x, y, 1.0, stream, flush, reps)
-    hp.hp_op_schedule(op, mlp)
+    default = hp.hp_op_strategies(op, nb)
+    rule = rule_strategy(kind, dtype)
+    rule_choice = np.where(default == hp.HP_STRAT_SUMFAC, hp.HP_STRAT_SUMFAC, rule) if dtype in _TC \
+        else np.full(nb, rule, dtype=np.int32)
+    out = {"blocks": nb, "launch": "graph" if graph else "per_block"}
+
+    def timed():
+        return _time_apply(op, x, y, 1.0, stream, flush, reps, graph=graph)
+
+    def hist(st):
+        return {n: int((st == v).sum()) for n, v in zip(STRAT_NAMES, STRATS) if (st == v).any()}
+
+    hp.hp_op_strategies(op, nb, rule_choice)
+    out["rule_ms"] = timed()
+    hp.hp_op_schedule_mlp(op, mlp, 1 if graph else 0)
     mlp_choice = hp.hp_op_strategies(op, nb)
-    out["mlp_ms"] = _time(op, x, y, 1.0, stream, flush, reps)
+    out["mlp_ms"] = timed()
+    out["choices_mlp"] = hist(mlp_choice)
     times = hp.hp_op_schedule_exhaustive(op, 1.0, x, y, nb)
-    best = hp.hp_op_strategies(op, nb)
-    out["exhaustive_ms"] = _time(op, x, y, 1.0, stream, flush, reps)
-    sumfac_only = np.array([t[0] for t in times]).sum()
-    times = np.where(times >= 1e29, np.inf, times)        # strategies that are not built
-    out["mispredicted_blocks"] = int((mlp_choice != best).sum())
-    out["mispredicted_cost_ms"] = float(sum(times[i][mlp_choice[i]] - times[i][best[i]] for i in range(nb)))
-    out["choices_mlp"] = np.bincount(mlp_choice, minlength=3).tolist()
-    out["choices_exhaustive"] = np.bincount(best, minlength=3).tolist()
-    out["sum_of_block_times_sumfac_ms"] = float(sumfac_only)
+    alone = hp.hp_op_strategies(op, nb)
+    out["exhaustive_alone_ms"] = timed()
+    out["choices_exhaustive_alone"] = hist(alone)
+    out["mispredicted_vs_alone"] = int((mlp_choice != alone).sum())
+    if graph and search:
+        hp.hp_op_strategies(op, nb, rule_choice)
+        hp.hp_op_schedule_graph(op, 1.0, x, y, 5, 2)
+        gs = hp.hp_op_strategies(op, nb)
+        out["graph_search_ms"] = timed()
+        out["choices_graph_search"] = hist(gs)
+        out["mispredicted_vs_graph_search"] = int((mlp_choice != gs).sum())
+    best = min(v for k, v in out.items() if k.endswith("_ms") and k != "mlp_ms")
+    out["mlp_over_best_searched"] = round(out["mlp_ms"] / min(best, out["exhaustive_alone_ms"]), 4)
+    out["rule_over_mlp"] = round(out["rule_ms"] / out["mlp_ms"], 4)
+    out["sum_of_block_times_alone_ms"] = float(np.where(times < 1e29, times, np.inf).min(axis=1).sum())
     hp.hp_op_destroy(op)
     hp.hp_mesh_destroy(h)
     return out

@@ -375,6 +375,12 @@ double elem_flops_exec(int shape, int P, hp_opkind k, bool fp64) {
     }
 }
 
+}  // namespace
+
+double elem_flops_helmholtz(int shape, int P) { return elem_flops(shape, P, HP_HELMHOLTZ); }
+
+namespace {
+
 template <typename T>
 void fill_const_tables(const Block& b, SFArgs<T>& a) {
     const RefTables& t = ref_tables(b.shape, b.P);
@@ -420,6 +426,13 @@ cudaError_t ensure_matrix(hp_op op, size_t bi, double lambda, cudaStream_t s) {
     if (op->mat[bi] && op->graph) {
         cudaGraphExecDestroy(op->graph);
         op->graph = nullptr;
+    }
+    // the matrices are overwritten in place: applies or graph replays already
+    // queued on other streams may still read them, so every earlier piece of
+    // work on the device completes first
+    if (op->mat[bi]) {
+        cudaError_t se = cudaDeviceSynchronize();
+        if (se != cudaSuccess) return se;
     }
     hp_mesh m = op->mesh;
     const Block& b = m->blocks[bi];
@@ -1048,15 +1061,25 @@ hp_status hp_op_block_features(hp_op op, float* features, int64_t n_blocks) {
     return HP_OK;
 }
 
-hp_status hp_op_schedule(hp_op op, hp_mlp mlp, void* stream) {
-    if (!op || !mlp) { set_error("hp_op_schedule: null argument"); return HP_ERR_ARG; }
+static bool matrix_room(hp_op op, size_t i);
+
+hp_status hp_op_schedule_mlp(hp_op op, hp_mlp mlp, int graph_launch, void* stream) {
+    if (!op || !mlp) { set_error("hp_op_schedule_mlp: null argument"); return HP_ERR_ARG; }
+    if (graph_launch != 0 && graph_launch != 1) { set_error("hp_op_schedule_mlp: graph_launch must be 0 or 1"); return HP_ERR_ARG; }
     int n_in = 0, n_out = 0;
     hp_mlp_info(mlp, &n_in, nullptr, &n_out, nullptr);
-    if (n_in != 5 || n_out != 3) { set_error("hp_op_schedule: the network must map 5 features to 3 log-times"); return HP_ERR_ARG; }
+    if ((n_in != 5 && n_in != 6) || (n_out != 3 && n_out != 4)) {
+        set_error("hp_op_schedule_mlp: the network must map 5 or 6 features to 3 or 4 log-times");
+        return HP_ERR_ARG;
+    }
     DeviceGuard guard(op->mesh->device);
     const int64_t nb = (int64_t)op->strat.size();
-    std::vector<float> f(5 * nb), y(3 * nb);
-    hp_op_block_features(op, f.data(), nb);
+    std::vector<float> f5(5 * nb), f((size_t)n_in * nb), y((size_t)n_out * nb);
+    hp_op_block_features(op, f5.data(), nb);
+    for (int64_t i = 0; i < nb; ++i) {
+        for (int j = 0; j < 5; ++j) f[(size_t)n_in * i + j] = f5[5 * i + j];
+        if (n_in == 6) f[(size_t)n_in * i + 5] = (float)graph_launch;
+    }
     float *dx = nullptr, *dy = nullptr;
     hp_status st = upload(&dx, f.data(), f.size());
     if (!st) st = upload<float>(&dy, nullptr, y.size());
@@ -1064,7 +1087,7 @@ hp_status hp_op_schedule(hp_op op, hp_mlp mlp, void* stream) {
     if (!st) {
         cudaError_t e = cudaMemcpyAsync(y.data(), dy, sizeof(float) * y.size(), cudaMemcpyDeviceToHost, (cudaStream_t)stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
-        if (e != cudaSuccess) st = cuda_fail(e, "hp_op_schedule");
+        if (e != cudaSuccess) st = cuda_fail(e, "hp_op_schedule_mlp");
     }
     cudaFree(dx);
     cudaFree(dy);
@@ -1072,12 +1095,17 @@ hp_status hp_op_schedule(hp_op op, hp_mlp mlp, void* stream) {
     std::vector<int> choice(nb);
     for (int64_t i = 0; i < nb; ++i) {
         int best = 0;
-        for (int k = 1; k < 3; ++k)
-            if (strategy_available(op, (size_t)i, k) && y[3 * i + k] < y[3 * i + best]) best = k;
-        choice[i] = best;
+        for (int k = 1; k < n_out; ++k) {
+            const int strat = k == 3 ? HP_STRAT_MATRIX : k;
+            if (strategy_available(op, (size_t)i, strat) && y[(size_t)n_out * i + k] < y[(size_t)n_out * i + best])
+                best = k;
+        }
+        choice[i] = best == 3 ? HP_STRAT_MATRIX : best;
     }
     return hp_op_strategies(op, choice.data(), nb, 1);
 }
+
+hp_status hp_op_schedule(hp_op op, hp_mlp mlp, void* stream) { return hp_op_schedule_mlp(op, mlp, 0, stream); }
 
 hp_status hp_op_schedule_exhaustive(hp_op op, double lambda, const void* in, void* out, float* times_ms,
                                     void* stream) {
@@ -1089,19 +1117,25 @@ hp_status hp_op_schedule_exhaustive(hp_op op, double lambda, const void* in, voi
         hp_status st = ensure_dense(op->mesh);
         if (st) return st;
     }
+    if (op->graph) { cudaGraphExecDestroy(op->graph); op->graph = nullptr; }
     cudaStream_t s = (cudaStream_t)stream;
     cudaEvent_t a, b;
     cudaEventCreate(&a);
     cudaEventCreate(&b);
     std::vector<int> saved = op->strat;
     std::vector<int> choice(nb, 0);
+    // candidates in the order of the output columns: sum factorisation,
+    // elemental matrix, hybrid, stored matrices (where they fit in memory)
+    const int cand[4] = {HP_STRAT_SUMFAC, HP_STRAT_ELEMAT, HP_STRAT_HYBRID, HP_STRAT_MATRIX};
     for (int64_t i = 0; i < nb; ++i) {
         float best = 1e30f;
-        for (int k = 0; k < 3; ++k) {
+        for (int k = 0; k < 4; ++k) {
             float tot = 1e30f;
-            if (strategy_available(op, (size_t)i, k)) {
-                op->strat[i] = k;
+            const int sk = cand[k];
+            if (strategy_available(op, (size_t)i, sk) && (sk != HP_STRAT_MATRIX || matrix_room(op, (size_t)i))) {
+                op->strat[i] = sk;
                 tot = 0.f;
+                // the first launch warms up (and builds stored matrices), two are timed
                 for (int r = 0; r < 3; ++r) {
                     cudaEventRecord(a, s);
                     cudaError_t e = launch_block(op, i, op->tile[i], lambda, in, out, s);
@@ -1117,11 +1151,15 @@ hp_status hp_op_schedule_exhaustive(hp_op op, double lambda, const void* in, voi
                     cudaEventElapsedTime(&ms, a, b);
                     if (r) tot += 0.5f * ms;
                 }
-                if (tot < best) { best = tot; choice[i] = k; }
+                if (tot < best) { best = tot; choice[i] = sk; }
             }
-            if (times_ms) times_ms[3 * i + k] = tot;
+            if (times_ms) times_ms[4 * i + k] = tot;
         }
         op->strat[i] = saved[i];
+        if (choice[i] != HP_STRAT_MATRIX && saved[i] != HP_STRAT_MATRIX && i < (int64_t)op->mat.size() && op->mat[i]) {
+            cudaFree(op->mat[i]);   // built for a trial that was not kept
+            op->mat[i] = nullptr;
+        }
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
@@ -1262,7 +1300,12 @@ hp_status hp_op_block_work(hp_op op, int64_t block, int64_t* n_elem, int64_t* ou
             default: geo = 0;
         }
         if (st == HP_STRAT_MATRIX) geo = np * np;   // the stored matrix takes the place of the factors
-        by += ne * ((in_v + out_v + geo) * vs + 8.0);
+        double geo_bytes = geo * vs;
+        if ((op->dtype == HP_TF32 || op->dtype == HP_BF16) && st == HP_STRAT_ELEMAT)
+            // tensor-core form: FP16 factors at every point (affine ones expanded),
+            // w|J| only for mass, and the element's two FP32 scales
+            geo_bytes = (op->kind == HP_MASS ? 1.0 : 7.0) * NQ * 2.0 + 8.0;
+        by += ne * ((in_v + out_v) * vs + geo_bytes + 8.0);
     }
     if (n_elem) *n_elem = ne_tot;
     if (out_dofs) *out_dofs = dofs;

@@ -38,7 +38,8 @@ __host__ __device__ constexpr int nvalid_c(int shape, int P) {
 }
 
 struct BlobLayout {
-    int Ta, Td, Tb, Tc, D, z, w, total_vals;              // offsets in values (Ta: parity form)
+    int Ta, Td, Tb, Tc, D, z, w, rz, total_vals;          // offsets in values (Ta: parity form;
+                                                          // rz[d][i] = 1 / (1 - z_d[i]), 0 at z = 1)
     int famb, famc, slot2mode, mode_slots;                // offsets in bytes
     int pairs, valid, poff, porder, total_bytes;          // valid (a,b) pairs and slots (int32), pair
                                                           // offset per a (int16), pairs by length (uint8)
@@ -57,6 +58,7 @@ __host__ __device__ constexpr BlobLayout blob_layout_c(int shape, int P, int vs)
     L.D = o; o += 3 * Q * Q;
     L.z = o; o += 3 * Q;
     L.w = o; o += 3 * Q;
+    L.rz = o; o += 3 * Q;
     L.total_vals = o;
     int b = align16c(o * vs);
     L.famb = b; b += n;

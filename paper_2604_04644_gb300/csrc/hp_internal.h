@@ -37,6 +37,8 @@ struct RefTables {
 
 const RefTables& ref_tables(int shape, int P);
 int n_modes(int shape, int P);
+// flops of the collocated sum-factorised Helmholtz operator per element (FMA = 2)
+double elem_flops_helmholtz(int shape, int P);
 
 // All modes of (shape, P) at one reference point xi (not at a collapse point).
 void eval_modes(int shape, int P, const double xi[3], double* out);

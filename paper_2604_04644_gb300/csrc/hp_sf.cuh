@@ -89,6 +89,7 @@ __global__ void __launch_bounds__(256, (sf_min_blocks<SHAPE, P, T, TILE>())) sf_
     const T* D2 = D0 + 2 * QQ;
     const T* zt = reinterpret_cast<const T*>(tab) + L.z;
     const T* wt = reinterpret_cast<const T*>(tab) + L.w;
+    const T* rzt = reinterpret_cast<const T*>(tab) + L.rz;
     const uint8_t* famb = tab + L.famb;
     const uint8_t* famc = tab + L.famc;
     const int16_t* slot2mode = reinterpret_cast<const int16_t*>(tab + L.slot2mode);
@@ -426,6 +427,43 @@ __global__ void __launch_bounds__(256, (sf_min_blocks<SHAPE, P, T, TILE>())) sf_
             const int64_t eg = e0 + e;
             T G[6], wJ, Gx[3][3];
             const bool need_gx = (op == HP_PHYSDERIV || op == HP_IPRODUCT_WRT_DERIV_BASE);
+            if (AFFINE && (op == HP_LAPLACIAN || op == HP_HELMHOLTZ)) {
+                // affine element: w = wl T K T^T v with K = |J| (d xi/d x)(d xi/d x)^T
+                // per element and T = d eta / d xi at the reference point, whose
+                // collapse factors come from the reciprocal tables 1/(1 - z) (no
+                // division and no per-point G: the product is applied factor by
+                // factor); the same G_dd' = wl (T K T^T)_dd' as the curved path
+                const T* rec = args.geom + eg * 16;
+                const int i = r / QQ, jk = r - i * QQ, j = jk / Q, k = jk - j * Q;
+                const T wl = wt[i] * wt[Q + j] * wt[2 * Q + k];
+                T* u = S1 + e * 4 * NQ + r;
+                const T uval = u[0], v0 = u[NQ], v1 = u[2 * NQ], v2 = u[3 * NQ];
+                T g0 = v0, g1 = v1, g2 = v2;                 // g = T^T v
+                T t00 = T(1), t01 = T(0), t02 = T(0), t11 = T(1), t12 = T(0);
+                if constexpr (SHAPE != HP_HEX) {
+                    const T r3 = rzt[2 * Q + k];
+                    const T a1 = T(1) + zt[i];
+                    if constexpr (SHAPE == HP_TET) {
+                        const T r23 = T(2) * rzt[Q + j] * r3;
+                        t00 = T(2) * r23; t01 = a1 * r23; t02 = t01;
+                        t11 = T(2) * r3; t12 = (T(1) + zt[Q + j]) * r3;
+                    } else {
+                        t00 = T(2) * r3; t02 = a1 * r3;
+                        if constexpr (SHAPE == HP_PYR) { t11 = T(2) * r3; t12 = (T(1) + zt[Q + j]) * r3; }
+                    }
+                    g0 = t00 * v0;
+                    g1 = t01 * v0 + t11 * v1;
+                    g2 = t02 * v0 + t12 * v1 + v2;
+                }
+                const T h0 = wl * (rec[0] * g0 + rec[1] * g1 + rec[2] * g2);
+                const T h1 = wl * (rec[1] * g0 + rec[3] * g1 + rec[4] * g2);
+                const T h2 = wl * (rec[2] * g0 + rec[4] * g1 + rec[5] * g2);
+                u[NQ] = t00 * h0 + t01 * h1 + t02 * h2;     // w = T h
+                u[2 * NQ] = t11 * h1 + t12 * h2;
+                u[3 * NQ] = h2;
+                S2[e * NQ + r] = (op == HP_HELMHOLTZ) ? args.lambda * wl * rec[6] * uval : T(0);
+                continue;
+            }
             if (AFFINE) {
                 const T* rec = args.geom + eg * 16;
                 int i = r / QQ, jk = r - i * QQ, j = jk / Q, k = jk - j * Q;
@@ -433,16 +471,6 @@ __global__ void __launch_bounds__(256, (sf_min_blocks<SHAPE, P, T, TILE>())) sf_
                 deta_dxi<SHAPE, T>(zt[i], zt[Q + j], zt[2 * Q + k], Tm);
                 T wl = wt[i] * wt[Q + j] * wt[2 * Q + k];
                 wJ = wl * rec[6];
-                if (op == HP_LAPLACIAN || op == HP_HELMHOLTZ) {
-                    T K[3][3] = {{rec[0], rec[1], rec[2]}, {rec[1], rec[3], rec[4]}, {rec[2], rec[4], rec[5]}};
-                    T M[3][3];
-#pragma unroll
-                    for (int d = 0; d < 3; ++d)
-#pragma unroll
-                        for (int b = 0; b < 3; ++b) M[d][b] = Tm[d][0] * K[0][b] + Tm[d][1] * K[1][b] + Tm[d][2] * K[2][b];
-                    auto gg = [&](int d, int d2) { return wl * (M[d][0] * Tm[d2][0] + M[d][1] * Tm[d2][1] + M[d][2] * Tm[d2][2]); };
-                    G[0] = gg(0, 0); G[1] = gg(0, 1); G[2] = gg(0, 2); G[3] = gg(1, 1); G[4] = gg(1, 2); G[5] = gg(2, 2);
-                }
                 if (need_gx) {
 #pragma unroll
                     for (int d = 0; d < 3; ++d)
@@ -720,18 +748,11 @@ template <int SHAPE, int P, typename T, bool AFFINE, int TILE>
 cudaError_t sf_launch_one(const SFArgs<T>& a, cudaStream_t s) {
     using C = SFCfg<P, T, TILE>;
     constexpr int smem = sf_smem_bytes<SHAPE, P, T, TILE>();
-    static int grid_cap = 0;
+    static std::atomic<int> caps[kMaxDevices];
     auto kern = sf_kernel<SHAPE, P, T, AFFINE, TILE>;
-    if (grid_cap == 0) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        int dev = 0, sms = 0, per = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, C::NT, smem);
-        if (e != cudaSuccess) return e;
-        grid_cap = sms * (per > 0 ? per : 1);
-    }
+    int grid_cap = 0;
+    cudaError_t e = persistent_grid_cap(kern, C::NT, smem, caps, &grid_cap);
+    if (e != cudaSuccess) return e;
     int64_t groups = (a.n_elem + C::EPB - 1) / C::EPB;
     int grid = (int)(groups < grid_cap ? groups : grid_cap);
     if (grid <= 0) return cudaSuccess;

@@ -395,6 +395,11 @@ std::vector<unsigned char> make_blob(const RefTables& t, size_t vs) {
         put(L.D + d * t.Q * t.Q, tmp);
         put(L.z + d * t.Q, t.z[d]);
         put(L.w + d * t.Q, t.w[d]);
+        // reciprocals of the collapse factors 1 - z (the Duffy chain rule of
+        // affine elements); the GLL end point z = 1 never collapses: 0
+        std::vector<double> rz(t.Q);
+        for (int i = 0; i < t.Q; ++i) rz[i] = t.z[d][i] < 1.0 ? 1.0 / (1.0 - t.z[d][i]) : 0.0;
+        put(L.rz + d * t.Q, rz);
     }
     std::memcpy(&out[L.famb], t.famb.data(), t.famb.size());
     std::memcpy(&out[L.famc], t.famc.data(), t.famc.size());

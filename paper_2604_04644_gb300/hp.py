@@ -31,13 +31,16 @@ HP_FP64, HP_FP32, HP_TF32, HP_BF16 = range(4)
 
 EXPORTED = ["hp_mesh_create", "hp_mesh_layout", "hp_geom_factors", "hp_geom_copy", "hp_op_create",
             "hp_op_apply", "hp_op_apply_graph", "hp_op_tune", "hp_op_tiles", "hp_op_strategies",
-            "hp_op_set_collocated", "hp_op_block_features", "hp_op_schedule", "hp_op_schedule_exhaustive", "hp_op_schedule_graph",
-            "hp_op_sync", "hp_op_work",
-            "hp_op_block_work", "hp_op_apply_block",
+            "hp_op_set_collocated", "hp_op_block_features", "hp_op_schedule", "hp_op_schedule_mlp", "hp_op_schedule_exhaustive",
+            "hp_op_schedule_graph", "hp_op_sync", "hp_op_work",
+            "hp_op_block_work", "hp_op_apply_block", "hp_peak_fp64",
             "hp_op_destroy", "hp_mesh_destroy", "hp_status_str", "hp_last_error",
             "hp_mlp_create", "hp_mlp_info", "hp_mlp_params", "hp_mlp_forward", "hp_mlp_grad", "hp_mlp_adam_step",
             "hp_mlp_destroy", "hp_mlp_grad_noalloc", "hp_mesh_points", "hp_c0_create", "hp_c0_info",
-            "hp_c0_map_host", "hp_c0_maps", "hp_c0_gather", "hp_c0_assemble", "hp_solve", "hp_c0_destroy", "hp_c0_diagonal"]
+            "hp_c0_map_host", "hp_c0_maps", "hp_c0_gather", "hp_c0_assemble", "hp_solve", "hp_c0_destroy", "hp_c0_diagonal",
+            "hp_partition", "hp_halo_create", "hp_halo_info", "hp_halo_counts", "hp_halo_maps", "hp_halo_gather",
+            "hp_halo_reduce_pack", "hp_halo_reduce_sum", "hp_halo_bcast_pack", "hp_halo_bcast_unpack",
+            "hp_halo_destroy", "hp_xdot_acc", "hp_xacc_round", "hp_xacc_limbs"]
 
 
 class HpError(RuntimeError):
@@ -67,6 +70,8 @@ _lib.hp_op_strategies.argtypes = [_vp, _vp, ctypes.c_int64, ctypes.c_int]
 _lib.hp_op_set_collocated.argtypes = [_vp, ctypes.c_int]
 _lib.hp_op_block_features.argtypes = [_vp, _vp, ctypes.c_int64]
 _lib.hp_op_schedule.argtypes = [_vp, _vp, _vp]
+_lib.hp_op_schedule_mlp.argtypes = [_vp, _vp, ctypes.c_int, _vp]
+_lib.hp_op_schedule_mlp.restype = ctypes.c_int
 _lib.hp_op_schedule_exhaustive.argtypes = [_vp, ctypes.c_double, _vp, _vp, _vp, _vp]
 _lib.hp_op_schedule_graph.argtypes = [_vp, ctypes.c_double, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp]
 _lib.hp_mlp_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_int,
@@ -84,6 +89,8 @@ _lib.hp_op_sync.argtypes = [_vp, _vp]
 _lib.hp_op_work.argtypes = [_vp, _i64p, _dp, _dp]
 _lib.hp_op_block_work.argtypes = [_vp, ctypes.c_int64, _i64p, _i64p, _dp, _dp, _dp]
 _lib.hp_op_apply_block.argtypes = [_vp, ctypes.c_int64, ctypes.c_double, _vp, _vp, _vp]
+_lib.hp_peak_fp64.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, _vp]
+_lib.hp_peak_fp64.restype = ctypes.c_int
 _lib.hp_op_destroy.argtypes = [_vp]
 _lib.hp_mesh_destroy.argtypes = [_vp]
 _lib.hp_status_str.argtypes = [ctypes.c_int]
@@ -218,6 +225,14 @@ def hp_op_apply_block(op, block, lam, x, y, stream=None):
     _check(_lib.hp_op_apply_block(op, int(block), float(lam), _ptr(x), _ptr(y), _stream(stream)), "hp_op_apply_block")
 
 
+def hp_peak_fp64(device=0, iters=20000, stream=None):
+    """(TFLOP/s, ms) of the library's FP64 FMA-loop kernel on `device`."""
+    t, ms = ctypes.c_double(), ctypes.c_double()
+    _check(_lib.hp_peak_fp64(int(device), int(iters), ctypes.byref(t), ctypes.byref(ms), _stream(stream)),
+           "hp_peak_fp64")
+    return t.value, ms.value
+
+
 def hp_op_destroy(op):
     _lib.hp_op_destroy(op)
 
@@ -252,8 +267,14 @@ def hp_op_schedule(op, mlp, stream=None):
     _check(_lib.hp_op_schedule(op, mlp, _stream(stream)), "hp_op_schedule")
 
 
+def hp_op_schedule_mlp(op, mlp, graph_launch=0, stream=None):
+    _check(_lib.hp_op_schedule_mlp(op, mlp, int(graph_launch), _stream(stream)), "hp_op_schedule_mlp")
+
+
 def hp_op_schedule_exhaustive(op, lam, x, y, n_blocks, stream=None):
-    t = np.zeros((n_blocks, 3), dtype=np.float32)
+    """Per-block times [n_blocks, 4] (ms; columns SUMFAC, ELEMAT, HYBRID, MATRIX;
+    1e30 where not built) after choosing the fastest per block."""
+    t = np.zeros((n_blocks, 4), dtype=np.float32)
     _check(_lib.hp_op_schedule_exhaustive(op, float(lam), _ptr(x), _ptr(y), t.ctypes.data, _stream(stream)),
            "hp_op_schedule_exhaustive")
     return t
@@ -422,3 +443,164 @@ def hp_c0_destroy(c0):
 
 def hp_c0_diagonal(c0, lam, diag, local=False, stream=None):
     _check(_lib.hp_c0_diagonal(c0, float(lam), _ptr(diag), 1 if local else 0, _stream(stream)), "hp_c0_diagonal")
+
+
+# ---------------------------------------------------------------- multi-GPU layout (host only)
+_lib.hp_partition.argtypes = [ctypes.POINTER(hp_mesh_desc), _vp, ctypes.c_int, ctypes.c_int, _vp]
+_lib.hp_halo_create.argtypes = [_vp, _vp, _vp, ctypes.c_int64, ctypes.c_int64, _vp, ctypes.c_int, ctypes.c_int,
+                                ctypes.POINTER(_vp)]
+_lib.hp_halo_info.argtypes = [_vp, _i64p, _i64p, _i64p]
+_lib.hp_halo_counts.argtypes = [_vp, _vp, _vp, _vp, _vp]
+_lib.hp_halo_maps.argtypes = [_vp, _vp, _vp, _vp]
+_lib.hp_halo_gather.argtypes = [_vp, _vp, _vp]
+_lib.hp_halo_reduce_pack.argtypes = [_vp, _vp, _vp]
+_lib.hp_halo_reduce_sum.argtypes = [_vp, _vp, _vp, _vp]
+_lib.hp_halo_bcast_pack.argtypes = [_vp, _vp, _vp]
+_lib.hp_halo_bcast_unpack.argtypes = [_vp, _vp, _vp, _vp]
+_lib.hp_halo_destroy.argtypes = [_vp]
+_lib.hp_xdot_acc.argtypes = [_vp, _vp, ctypes.c_int64, _vp]
+_lib.hp_xacc_round.argtypes = [_vp, _dp]
+for _f in ("hp_partition", "hp_halo_create", "hp_halo_info", "hp_halo_counts", "hp_halo_maps", "hp_halo_gather",
+           "hp_halo_reduce_pack", "hp_halo_reduce_sum", "hp_halo_bcast_pack", "hp_halo_bcast_unpack", "hp_xdot_acc",
+           "hp_xacc_round", "hp_xacc_limbs"):
+    getattr(_lib, _f).restype = ctypes.c_int
+HP_XACC_LIMBS = _lib.hp_xacc_limbs()
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def hp_partition(mesh, nparts, method=0, cost=None):
+    """Element partition (int32 part ids) balanced by cost (default: the
+    collocated Helmholtz flops of each element); method 0: ranges of the
+    block order, 1: recursive coordinate bisection."""
+    d, keep = _desc(mesh)
+    part = np.zeros(int(mesh["n_elem"]), dtype=np.int32)
+    c = None if cost is None else _f64(cost)
+    _check(_lib.hp_partition(ctypes.byref(d), None if c is None else c.ctypes.data, int(nparts), int(method),
+                             part.ctypes.data), "hp_partition")
+    return part
+
+
+class Halo:
+    """One rank's halo plan (hp_halo_*): sizes, per-peer message counts, maps
+    and the host pack / sum / unpack steps on numpy float64 arrays."""
+
+    def __init__(self, gid, sign, coeff_offset, n_global, part, nparts, rank):
+        gid = np.ascontiguousarray(gid, dtype=np.int64)
+        sign = np.ascontiguousarray(sign, dtype=np.int8)
+        co = np.ascontiguousarray(coeff_offset, dtype=np.int64)
+        part = np.ascontiguousarray(part, dtype=np.int32)
+        h = _vp()
+        _check(_lib.hp_halo_create(gid.ctypes.data, sign.ctypes.data, co.ctypes.data, len(co) - 1, int(n_global),
+                                   part.ctypes.data, int(nparts), int(rank), ctypes.byref(h)), "hp_halo_create")
+        self.h, self.nparts, self.rank = h.value, int(nparts), int(rank)
+        a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(_lib.hp_halo_info(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "hp_halo_info")
+        self.n_local, self.n_touched, self.n_owned = a.value, b.value, c.value
+        self.counts = [np.zeros(self.nparts, dtype=np.int64) for _ in range(4)]
+        _check(_lib.hp_halo_counts(self.h, *[x.ctypes.data for x in self.counts]), "hp_halo_counts")
+        self.reduce_send, self.reduce_recv, self.bcast_send, self.bcast_recv = self.counts
+        self.local_index = np.zeros(self.n_local, dtype=np.int64)
+        self.touched_gid = np.zeros(self.n_touched, dtype=np.int64)
+        self.owned_gid = np.zeros(self.n_owned, dtype=np.int64)
+        _check(_lib.hp_halo_maps(self.h, self.local_index.ctypes.data, self.touched_gid.ctypes.data,
+                                 self.owned_gid.ctypes.data), "hp_halo_maps")
+
+    def gather(self, touched):
+        touched = _f64(touched)
+        out = np.zeros(self.n_local)
+        _check(_lib.hp_halo_gather(self.h, touched.ctypes.data, out.ctypes.data), "hp_halo_gather")
+        return out
+
+    def reduce_pack(self, local):
+        local = _f64(local)
+        out = np.zeros(int(self.reduce_send.sum()))
+        _check(_lib.hp_halo_reduce_pack(self.h, local.ctypes.data, out.ctypes.data), "hp_halo_reduce_pack")
+        return out
+
+    def reduce_sum(self, local, recv):
+        local, recv = _f64(local), _f64(recv)
+        out = np.zeros(self.n_owned)
+        _check(_lib.hp_halo_reduce_sum(self.h, local.ctypes.data, recv.ctypes.data, out.ctypes.data),
+               "hp_halo_reduce_sum")
+        return out
+
+    def bcast_pack(self, owned):
+        owned = _f64(owned)
+        out = np.zeros(int(self.bcast_send.sum()))
+        _check(_lib.hp_halo_bcast_pack(self.h, owned.ctypes.data, out.ctypes.data), "hp_halo_bcast_pack")
+        return out
+
+    def bcast_unpack(self, owned, recv):
+        owned, recv = _f64(owned), _f64(recv)
+        out = np.zeros(self.n_touched)
+        _check(_lib.hp_halo_bcast_unpack(self.h, owned.ctypes.data, recv.ctypes.data, out.ctypes.data),
+               "hp_halo_bcast_unpack")
+        return out
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            _lib.hp_halo_destroy(self.h)
+            self.h = None
+
+
+def hp_xdot_acc(x, y, acc=None):
+    """Add sum x_i y_i exactly into an int64 accumulator (new if None); returns it."""
+    x, y = _f64(x), _f64(y)
+    if acc is None:
+        acc = np.zeros(HP_XACC_LIMBS, dtype=np.int64)
+    _check(_lib.hp_xdot_acc(x.ctypes.data, y.ctypes.data, len(x), acc.ctypes.data), "hp_xdot_acc")
+    return acc
+
+
+def hp_xacc_round(acc):
+    acc = np.ascontiguousarray(acc, dtype=np.int64)
+    out = ctypes.c_double()
+    _check(_lib.hp_xacc_round(acc.ctypes.data, ctypes.byref(out)), "hp_xacc_round")
+    return out.value
+
+
+def hp_xacc_limbs():
+    return HP_XACC_LIMBS
+
+
+def hp_halo_create(gid, sign, coeff_offset, n_global, part, nparts, rank):
+    return Halo(gid, sign, coeff_offset, n_global, part, nparts, rank)
+
+
+def hp_halo_info(halo):
+    return halo.n_local, halo.n_touched, halo.n_owned
+
+
+def hp_halo_counts(halo):
+    return halo.reduce_send, halo.reduce_recv, halo.bcast_send, halo.bcast_recv
+
+
+def hp_halo_maps(halo):
+    return halo.local_index, halo.touched_gid, halo.owned_gid
+
+
+def hp_halo_gather(halo, touched):
+    return halo.gather(touched)
+
+
+def hp_halo_reduce_pack(halo, local):
+    return halo.reduce_pack(local)
+
+
+def hp_halo_reduce_sum(halo, local, recv):
+    return halo.reduce_sum(local, recv)
+
+
+def hp_halo_bcast_pack(halo, owned):
+    return halo.bcast_pack(owned)
+
+
+def hp_halo_bcast_unpack(halo, owned, recv):
+    return halo.bcast_unpack(owned, recv)
+
+
+def hp_halo_destroy(halo):
+    halo.__del__()

@@ -12,7 +12,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def declared_functions():
     txt = open(os.path.join(ROOT, "include", "hp.h")).read()
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-    return sorted(set(re.findall(r"^\s*(?:hp_status|void|const char\s*\*)\s*(hp_\w+)\s*\(", txt, flags=re.M)))
+    return sorted(set(re.findall(r"^\s*(?:hp_status|void|int|const char\s*\*)\s*(hp_\w+)\s*\(", txt, flags=re.M)))
 
 
 @pytest.fixture(scope="module")

@@ -92,7 +92,10 @@ def test_schedule_by_network_and_exhaustive(hp):
         assert np.abs(y.cpu().numpy() - ref).max() <= 1e-12 * np.abs(ref).max()
         times = hp.hp_op_schedule_exhaustive(op, 1.0, x, y, nb)
         best = hp.hp_op_strategies(op, nb)
-        assert (best == times.argmin(axis=1)).all()
+        # columns: sum factorisation, elemental matrix, hybrid, stored matrices
+        assert (best == np.array([hp.HP_STRAT_SUMFAC, hp.HP_STRAT_ELEMAT, hp.HP_STRAT_HYBRID,
+                                  hp.HP_STRAT_MATRIX])[times.argmin(axis=1)]).all()
+        assert (times < 1e29).all()      # every strategy is built for these FP64 blocks (N_P <= 256)
         y2 = torch.full_like(y, np.nan)
         hp.hp_op_apply(op, 1.0, x, y2)
         hp.hp_op_sync(op)
@@ -141,7 +144,7 @@ def test_tf32_schedules_only_built_strategies(hp):
         x = torch.tensor(inputs.random_coefficients(5, co), device="cuda:0", dtype=torch.float32)
         y = torch.zeros(nc, device="cuda:0", dtype=torch.float32)
         times = hp.hp_op_schedule_exhaustive(op, 1.0, x, y, nb)
-        assert (times[:, 2] >= 1e29).all() and (times[~fits, 1] >= 1e29).all()
+        assert (times[:, 2] >= 1e29).all() and (times[:, 3] >= 1e29).all() and (times[~fits, 1] >= 1e29).all()
         best = hp.hp_op_strategies(op, nb)
         assert (best == times.argmin(axis=1)).all() and (best != hp.HP_STRAT_HYBRID).all()
         hp.hp_op_destroy(op)
@@ -198,3 +201,34 @@ def test_graph_schedule_keeps_valid_strategies_and_results(hp):
             hp.hp_op_destroy(op)
     finally:
         hp.hp_mesh_destroy(h)
+
+
+def test_trained_network_beats_rule_on_held_out_mesh(hp):
+    """The cost model end to end: timings generated by the library (FP64
+    Helmholtz, four shapes, P = 1..6, affine and curved, 256 / 2 048 / 16 384
+    elements, all four strategies), a 6 -> 64 -> 64 -> 4 network trained on
+    them with the library's Adam kernels, and its schedule of a held-out mixed
+    p-adaptive mesh (8x8x16 cells, P ~ U{1..6}, affine x < 0.5, curved
+    otherwise) launched as the concurrent graph.  The schedule must be no
+    slower than the paper's fixed rule (sum factorisation for Helmholtz,
+    Sec. 4) and within 25 % of the best searched schedule (each block's fastest
+    strategy timed alone, and the search on the whole graph's time); the
+    stored-matrix strategy it can now choose makes it strictly faster than
+    the rule (low-order blocks)."""
+    from paper_2604_04644_gb300 import costmodel
+    recs = costmodel.generate_timings(0, hp.HP_HELMHOLTZ, orders=range(1, 7), sizes=(256, 2048, 16384),
+                                      dtypes=(hp.HP_FP64,), budget_ms=20.0, reps=2)
+    X, T = costmodel.training_set(recs)
+    assert X.shape[1] == 6 and T.shape[1] == 4 and len(X) == 2 * len(recs)
+    mlp, hist = costmodel.train(X, T, 0, steps=3000)
+    try:
+        assert hist[-1][1] < 0.1 * hist[0][1]
+        held = inputs.slab_mesh(8, 8, 16, (1, 6), order_seed=9, curved_rule="x_half")
+        ev = costmodel.evaluate_schedules(mlp, held, hp.HP_HELMHOLTZ, hp.HP_FP64, graph=True, search=True)
+    finally:
+        hp.hp_mlp_destroy(mlp)
+    print(ev)
+    assert ev["mlp_ms"] <= 1.02 * ev["rule_ms"], ev
+    assert ev["mlp_ms"] < ev["rule_ms"], ev
+    assert ev["mlp_ms"] <= 1.25 * min(ev["graph_search_ms"], ev["exhaustive_alone_ms"]), ev
+    assert ev["choices_mlp"].get("matrix", 0) > 0, ev
