@@ -75,7 +75,7 @@ def element_rhs(mesh, f):
         X = mesh["xyz"][mesh["vert"][e][:NV[s]]]
         chi = element_map(s, X, bool(mesh["curved"][e]), mesh["deformation"])
         x = chi(*ref["xi"])
-        g = block_metrics(s, P, Q, X[None], bool(mesh["curved"][e]), mesh["deformation"])
+        g = block_metrics(s, P, Q, X[None], bool(mesh["curved"][e]), mesh["deformation"], mesh.get("geometry", 0))
         b[co[e]:co[e + 1]] = ref["B"].T @ (g["wJ"][0] * f(x[0], x[1], x[2]))
     return b
 
@@ -89,7 +89,7 @@ def solve(mesh, lam, f, Z=None):
     for e in range(mesh["n_elem"]):
         s, P, Q = int(mesh["shape"][e]), int(mesh["P"][e]), int(mesh["Q"][e])
         X = mesh["xyz"][mesh["vert"][e][:NV[s]]][None]
-        M, L = element_matrices(s, P, Q, X, bool(mesh["curved"][e]), mesh["deformation"])
+        M, L = element_matrices(s, P, Q, X, bool(mesh["curved"][e]), mesh["deformation"], mesh.get("geometry", 0))
         H[co[e]:co[e + 1], co[e]:co[e + 1]] = lam * M[0] + L[0]
     b = element_rhs(mesh, f)
     A = Z.T @ H @ Z

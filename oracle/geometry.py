@@ -5,7 +5,9 @@ Each element is the affine image of its reference element, fixed by vertex 0
 and the three vertices adjacent to it along xi_1, xi_2, xi_3:
   A_e(xi) = X_0 + sum_d (xi_d + 1)/2 (X_{v_d} - X_0);
 curved elements are further mapped by the smooth deformation
-  Phi(x)_i = x_i + 0.05 sin(pi x_j) sin(pi x_k),  (i,j,k) cyclic,
+  Phi(x)_i = x_i + 0.05 sin(pi x_j) sin(pi x_k),  (i,j,k) cyclic   (kind 1),
+or, for tests that need a polynomial map, the quadratic
+  Phi(x)_i = x_i + 0.1 x_j x_k,  (i,j,k) cyclic                     (kind 2),
 so x = Phi(A_e(xi)).  The Jacobian J[i][d] = d x_i / d xi_d is taken by
 complex-step differentiation of that composition (exact to rounding).
 """
@@ -19,6 +21,8 @@ AXIS_VERTS = {0: (1, 3, 4), 1: (1, 3, 4), 2: (1, 3, 4), 3: (1, 2, 3)}
 def deform(x1, x2, x3, kind=1):
     if kind == 0:
         return x1, x2, x3
+    if kind == 2:
+        return x1 + 0.1 * x2 * x3, x2 + 0.1 * x3 * x1, x3 + 0.1 * x1 * x2
     s = lambda t: np.sin(np.pi * t)
     return (x1 + 0.05 * s(x2) * s(x3),
             x2 + 0.05 * s(x3) * s(x1),

@@ -85,9 +85,56 @@ def block_jacobian(shape, X, curved, kind, xi):
     return np.stack(g, axis=-1).transpose(1, 2, 0, 3)
 
 
-def block_metrics(shape, P, Q, X, curved, kind):
+def block_points(shape, X, curved, kind, xi):
+    """x[i, e, l] = chi^e(xi_l) for vertex arrays X (Ne, nv, 3)."""
+    v = AXIS_VERTS[shape]
+    X0 = X[:, 0, :]
+    E = np.stack([X[:, v[d], :] - X0 for d in range(3)], axis=-1)
+    t = [(xi[d] + 1.0) / 2.0 for d in range(3)]
+    y = np.stack([X0[:, i:i + 1] + E[:, i, 0:1] * t[0][None, :] + E[:, i, 1:2] * t[1][None, :]
+                  + E[:, i, 2:3] * t[2][None, :] for i in range(3)])
+    if curved:
+        y = np.stack(deform(y[0], y[1], y[2], kind))
+    return y
+
+
+def isoparametric_coefficients(shape, P, Q, X, curved, kind):
+    """Modal coefficients xh[i, e, m] of the iso-parametric map: each
+    coordinate of the element map projected onto the element's own degree-P
+    expansion (the paper's benchmarks use curved elements whose geometry has
+    the degree of the solution, Sec. 4; no construction is given).  Reading:
+    the L2 projection on the reference element with the element's quadrature,
+    xh = (B^T W B)^{-1} B^T W x(xi_l), W the reference weights."""
     ref = reference(shape, P, Q)
-    J = block_jacobian(shape, X, curved, kind, ref["xi"])
+    x = block_points(shape, X, curved, kind, ref["xi"])             # (3, Ne, NQ)
+    return np.einsum("iel,ml->iem", x, projection_matrix(shape, P, Q))
+
+
+def projection_matrix(shape, P, Q):
+    """R (NP, NQ): point values -> modal coefficients of their L2 projection
+    on the reference element, R = (B^T W B)^{-1} B^T W."""
+    ref = reference(shape, P, Q)
+    B, W = ref["B"], ref["W"]
+    return np.linalg.solve(B.T @ (W[:, None] * B), B.T * W[None, :])
+
+
+def isoparametric_jacobian(shape, P, Q, X, curved, kind):
+    """J[e, l, i, d] = d x_i / d xi_d of the iso-parametric map at the points:
+    sum_m xh[i, e, m] (d phi_m / d xi_d)(xi_l)."""
+    ref = reference(shape, P, Q)
+    xh = isoparametric_coefficients(shape, P, Q, X, curved, kind)
+    return np.einsum("iem,dlm->elid", xh, np.stack(ref["Dxi"]))
+
+
+def block_metrics(shape, P, Q, X, curved, kind, geometry=0):
+    """J, det J, J^{-1} and w|J| at the points; geometry 1 takes J from the
+    iso-parametric map of curved elements (affine maps are in the span of
+    every expansion, so their iso-parametric map is the map itself)."""
+    ref = reference(shape, P, Q)
+    if geometry == 1 and curved:
+        J = isoparametric_jacobian(shape, P, Q, X, curved, kind)
+    else:
+        J = block_jacobian(shape, X, curved, kind, ref["xi"])
     detJ = np.linalg.det(J)
     Jinv = np.linalg.inv(J)                               # [e, l, d, i] = d xi_d / d x_i
     wJ = ref["W"][None, :] * detJ
@@ -109,9 +156,9 @@ def _iprod_grad(ref, g, f):
     return sum(t[d] @ ref["Dxi"][d] for d in range(3))
 
 
-def apply_block(op, shape, P, Q, X, curved, kind, data, lam=1.0):
+def apply_block(op, shape, P, Q, X, curved, kind, data, lam=1.0, geometry=0):
     ref = reference(shape, P, Q)
-    g = block_metrics(shape, P, Q, X, curved, kind)
+    g = block_metrics(shape, P, Q, X, curved, kind, geometry)
     B = ref["B"]
     if op == "bwd_trans":
         return data @ B.T
@@ -170,10 +217,10 @@ def helmholtz_collocated_block(ref, g, uh, lam):
     return up @ ref["B"]
 
 
-def element_matrices(shape, P, Q, X, curved, kind):
+def element_matrices(shape, P, Q, X, curved, kind, geometry=0):
     """Explicit (M, L) of each element of the block: (Ne, NP, NP) each."""
     ref = reference(shape, P, Q)
-    g = block_metrics(shape, P, Q, X, curved, kind)
+    g = block_metrics(shape, P, Q, X, curved, kind, geometry)
     B = ref["B"]
     M = np.einsum("lm,el,ln->emn", B, g["wJ"], B)
     Gx = np.einsum("eldi,dlm->eilm", g["Jinv"], np.stack(ref["Dxi"]))    # d phi_m / d x_i at l
@@ -181,11 +228,11 @@ def element_matrices(shape, P, Q, X, curved, kind):
     return M, L
 
 
-def geometric_factors_block(shape, P, Q, X, curved, kind):
+def geometric_factors_block(shape, P, Q, X, curved, kind, geometry=0):
     """Per point: G_dd' = w|J| sum_i (d eta_d/dx_i)(d eta_d'/dx_i) (6: 11,12,13,22,23,33),
     w|J|, and d eta_d / d x_i (9, row-major d then i)."""
     ref = reference(shape, P, Q)
-    g = block_metrics(shape, P, Q, X, curved, kind)
+    g = block_metrics(shape, P, Q, X, curved, kind, geometry)
     Gx = _deta_dx(ref, g)
     G = np.einsum("el,eldi,elki->eldk", g["wJ"], Gx, Gx)
     six = np.stack([G[:, :, 0, 0], G[:, :, 0, 1], G[:, :, 0, 2], G[:, :, 1, 1], G[:, :, 1, 2], G[:, :, 2, 2],
@@ -251,7 +298,7 @@ def apply(op, mesh, data, lam=1.0, elems=None):
             x = np.stack([data[c * n_in_vec + idx_in] for c in range(3)])
         else:
             x = data[idx_in]
-        y = apply_block(op, shape, P, Q, X, bool(cv), kind, x, lam)
+        y = apply_block(op, shape, P, Q, X, bool(cv), kind, x, lam, mesh.get("geometry", 0))
         idx_out = oo[el][:, None] + np.arange(no)[None, :]
         if ok == "phys3":
             for c in range(3):
@@ -269,7 +316,8 @@ def geometric_factors(mesh, elems=None):
     kind = mesh["deformation"]
     for (shape, P, Q, cv), el in _blocks(mesh, elems).items():
         el = np.array(el)
-        s7, s9 = geometric_factors_block(shape, P, Q, _verts(mesh, shape, el), bool(cv), kind)
+        s7, s9 = geometric_factors_block(shape, P, Q, _verts(mesh, shape, el), bool(cv), kind,
+                                         mesh.get("geometry", 0))
         for t, e in enumerate(el):
             six[e] = s7[t]
             nine[e] = s9[t]

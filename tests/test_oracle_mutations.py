@@ -69,3 +69,20 @@ def test_wrong_lagrange_derivative_is_caught(monkeypatch):
     orig = ops.lagrange_derivative_matrix
     monkeypatch.setattr(ops, "lagrange_derivative_matrix", lambda x: orig(x).T)
     _fails(T_ops.test_collocated_equals_plain, 3, True, 3)
+
+
+def test_unweighted_geometry_projection_is_caught(monkeypatch):
+    from tests import test_oracle_isoparametric as T_iso
+
+    def bad(shape, P, Q):
+        B = ops.reference(shape, P, Q)["B"]
+        return np.linalg.solve(B.T @ B, B.T)          # least squares at the points, W dropped
+    monkeypatch.setattr(ops, "projection_matrix", bad)
+    _fails(T_iso.test_hex_projection_annihilates_the_next_legendre_polynomial, 4)
+
+
+def test_transposed_iso_jacobian_is_caught(monkeypatch):
+    from tests import test_oracle_isoparametric as T_iso
+    orig = ops.isoparametric_jacobian
+    monkeypatch.setattr(ops, "isoparametric_jacobian", lambda *a: np.swapaxes(orig(*a), -1, -2))
+    _fails(T_iso.test_quadratic_map_is_reproduced_from_degree_two, 3)
