@@ -98,32 +98,39 @@ def block_points(shape, X, curved, kind, xi):
     return y
 
 
-def isoparametric_coefficients(shape, P, Q, X, curved, kind):
-    """Modal coefficients xh[i, e, m] of the iso-parametric map: each
-    coordinate of the element map projected onto the element's own degree-P
-    expansion (the paper's benchmarks use curved elements whose geometry has
-    the degree of the solution, Sec. 4; no construction is given).  Reading:
-    the L2 projection on the reference element with the element's quadrature,
-    xh = (B^T W B)^{-1} B^T W x(xi_l), W the reference weights."""
-    ref = reference(shape, P, Q)
-    x = block_points(shape, X, curved, kind, ref["xi"])             # (3, Ne, NQ)
-    return np.einsum("iel,ml->iem", x, projection_matrix(shape, P, Q))
-
-
-def projection_matrix(shape, P, Q):
-    """R (NP, NQ): point values -> modal coefficients of their L2 projection
-    on the reference element, R = (B^T W B)^{-1} B^T W."""
+def projection_operator(shape, P, Q):
+    """Pi (NQ, NQ): point values -> values at the same points of their L2
+    projection onto the element's expansion on the reference element,
+    Pi = B (B^T W B)^{-1} B^T W, taken through the Householder QR
+    W^{1/2} B = Qo R as Pi = W^{-1/2} Qo Qo^T W^{1/2}: the orthonormal Qo keeps
+    it well conditioned, where the normal equations of the modal basis (or
+    R^{-1}) lose many digits at high order."""
     ref = reference(shape, P, Q)
     B, W = ref["B"], ref["W"]
-    return np.linalg.solve(B.T @ (W[:, None] * B), B.T * W[None, :])
+    sw = np.sqrt(W)
+    Qo, _ = np.linalg.qr(sw[:, None] * B)
+    return (Qo / sw[:, None]) @ (Qo.T * sw[None, :])
 
 
 def isoparametric_jacobian(shape, P, Q, X, curved, kind):
     """J[e, l, i, d] = d x_i / d xi_d of the iso-parametric map at the points:
-    sum_m xh[i, e, m] (d phi_m / d xi_d)(xi_l)."""
+    each coordinate of the element map (its values at the points) projected
+    onto the element's own degree-P expansion (the paper's benchmarks use
+    curved elements whose geometry has the degree of the solution, Sec. 4; no
+    construction is given; reading: the L2 projection on the reference
+    element with the element's quadrature, Pi of projection_operator), then
+    differentiated at the points.  The projection is a polynomial of degree
+    <= P < Q in each collapsed coordinate eta_d, so the Lagrange collocation
+    derivative along each eta line is exact; d x / d xi = (d x / d eta)(d eta / d xi)."""
     ref = reference(shape, P, Q)
-    xh = isoparametric_coefficients(shape, P, Q, X, curved, kind)
-    return np.einsum("iem,dlm->elid", xh, np.stack(ref["Dxi"]))
+    x = block_points(shape, X, curved, kind, ref["xi"])             # (3, Ne, NQ)
+    xp = np.einsum("cel,ml->cem", x, projection_operator(shape, P, Q))
+    U = xp.reshape(3, -1, Q, Q, Q)
+    D1, D2, D3 = ref["D1"]
+    v = np.stack([np.einsum("am,cemjk->ceajk", D1, U), np.einsum("bm,ceimk->ceibk", D2, U),
+                  np.einsum("km,ceijm->ceijk", D3, U)])               # (d, c, e, Q, Q, Q)
+    Jeta = v.reshape(3, 3, X.shape[0], -1).transpose(2, 3, 1, 0)     # [e, l, c, d] = d x_c / d eta_d
+    return np.einsum("elcd,lda->elca", Jeta, ref["T"])
 
 
 def block_metrics(shape, P, Q, X, curved, kind, geometry=0):
@@ -156,10 +163,13 @@ def _iprod_grad(ref, g, f):
     return sum(t[d] @ ref["Dxi"][d] for d in range(3))
 
 
-def apply_block(op, shape, P, Q, X, curved, kind, data, lam=1.0, geometry=0):
+def apply_block(op, shape, P, Q, X, curved, kind, data, lam=1.0, geometry=0, adv=None):
     ref = reference(shape, P, Q)
     g = block_metrics(shape, P, Q, X, curved, kind, geometry)
     B = ref["B"]
+    if op == "adr":
+        return (lam * ((g["wJ"] * (data @ B.T)) @ B) + _iprod_grad(ref, g, _grad_x(ref, g, data))
+                + advection_block(ref, g, data, adv))
     if op == "bwd_trans":
         return data @ B.T
     if op == "iproduct_wrt_base":
@@ -177,6 +187,24 @@ def apply_block(op, shape, P, Q, X, curved, kind, data, lam=1.0, geometry=0):
     if op == "helmholtz_collocated":
         return helmholtz_collocated_block(ref, g, data, lam)
     raise ValueError(op)
+
+
+def advection_block(ref, g, uh, adv):
+    """The advection part of the linear advection-diffusion-reaction operator
+    (Sec. 2.2: the B^T {pointwise} B decomposition applies to any operator
+    tested against the basis or its derivatives, the paper names this one):
+    out_m = sum_l w_l |J_l| phi_m(l) (a . grad_x u)(l), a constant velocity."""
+    a = np.zeros(3) if adv is None else np.asarray(adv, dtype=np.float64)
+    gx = _grad_x(ref, g, uh)                                           # (3, Ne, NQ)
+    return (g["wJ"] * np.einsum("i,iel->el", a, gx)) @ ref["B"]
+
+
+def element_advection_matrices(shape, P, Q, X, curved, kind, adv, geometry=0):
+    """Explicit C[e][m][n] = sum_l w|J| phi_m (a . grad_x phi_n) of each element."""
+    ref = reference(shape, P, Q)
+    g = block_metrics(shape, P, Q, X, curved, kind, geometry)
+    Gx = np.einsum("eldi,dlm->eilm", g["Jinv"], np.stack(ref["Dxi"]))    # d phi_m / d x_i at l
+    return np.einsum("lm,el,i,eiln->emn", ref["B"], g["wJ"], np.asarray(adv, dtype=np.float64), Gx)
 
 
 def _eta_derivs(ref, u):
@@ -271,15 +299,17 @@ def _verts(mesh, shape, elems):
 
 IN_KIND = {"bwd_trans": "coeff", "iproduct_wrt_base": "phys", "mass": "coeff", "laplacian": "coeff",
            "helmholtz": "coeff", "phys_deriv": "phys", "iproduct_wrt_deriv": "phys3",
-           "helmholtz_collocated": "coeff"}
+           "helmholtz_collocated": "coeff", "adr": "coeff"}
 OUT_KIND = {"bwd_trans": "phys", "iproduct_wrt_base": "coeff", "mass": "coeff", "laplacian": "coeff",
             "helmholtz": "coeff", "phys_deriv": "phys3", "iproduct_wrt_deriv": "coeff",
-            "helmholtz_collocated": "coeff"}
+            "helmholtz_collocated": "coeff", "adr": "coeff"}
 
 
-def apply(op, mesh, data, lam=1.0, elems=None):
+def apply(op, mesh, data, lam=1.0, elems=None, adv=None):
     """Apply ``op`` to the ragged vector ``data``; with ``elems``, only those
-    elements' outputs are computed (others left zero)."""
+    elements' outputs are computed (others left zero).  ``adv``: the constant
+    velocity of the advection-diffusion-reaction operator ("adr":
+    -div grad u + a . grad u + lam u, tested against the basis)."""
     coeff, phys = layout(mesh)
     offs = {"coeff": coeff, "phys": phys, "phys3": phys}
     ik, ok = IN_KIND[op], OUT_KIND[op]
@@ -298,7 +328,7 @@ def apply(op, mesh, data, lam=1.0, elems=None):
             x = np.stack([data[c * n_in_vec + idx_in] for c in range(3)])
         else:
             x = data[idx_in]
-        y = apply_block(op, shape, P, Q, X, bool(cv), kind, x, lam, mesh.get("geometry", 0))
+        y = apply_block(op, shape, P, Q, X, bool(cv), kind, x, lam, mesh.get("geometry", 0), adv)
         idx_out = oo[el][:, None] + np.arange(no)[None, :]
         if ok == "phys3":
             for c in range(3):

@@ -76,8 +76,9 @@ def test_unweighted_geometry_projection_is_caught(monkeypatch):
 
     def bad(shape, P, Q):
         B = ops.reference(shape, P, Q)["B"]
-        return np.linalg.solve(B.T @ B, B.T)          # least squares at the points, W dropped
-    monkeypatch.setattr(ops, "projection_matrix", bad)
+        Qo, _ = np.linalg.qr(B)                        # least squares at the points, W dropped
+        return Qo @ Qo.T
+    monkeypatch.setattr(ops, "projection_operator", bad)
     _fails(T_iso.test_hex_projection_annihilates_the_next_legendre_polynomial, 4)
 
 
@@ -86,3 +87,22 @@ def test_transposed_iso_jacobian_is_caught(monkeypatch):
     orig = ops.isoparametric_jacobian
     monkeypatch.setattr(ops, "isoparametric_jacobian", lambda *a: np.swapaxes(orig(*a), -1, -2))
     _fails(T_iso.test_quadratic_map_is_reproduced_from_degree_two, 3)
+
+
+def test_advection_without_jacobian_weight_is_caught(monkeypatch):
+    from tests import test_oracle_adr as T_adr
+    orig = ops.block_metrics
+
+    def bad(*a):
+        g = orig(*a)
+        g["wJ"] = g["wJ"] / g["detJ"]
+        return g
+    monkeypatch.setattr(ops, "block_metrics", bad)
+    _fails(T_adr.test_linear_function_against_one_gives_velocity_times_volume, 3)
+
+
+def test_advection_with_transposed_roles_is_caught(monkeypatch):
+    from tests import test_oracle_adr as T_adr
+    orig = ops.element_advection_matrices
+    monkeypatch.setattr(ops, "element_advection_matrices", lambda *a, **k: orig(*a, **k).transpose(0, 2, 1))
+    _fails(T_adr.test_constants_are_annihilated, 1, True)
