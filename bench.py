@@ -80,6 +80,7 @@ def parse():
     p.add_argument("--steps", type=int, default=50)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--oracle-sample", type=float, default=None, help=argparse.SUPPRESS)
     p.add_argument("--dtype", default="f64", choices=["f64", "f32"])
     p.add_argument("--no-table", action="store_true", help="skip the per-shape/order table")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
@@ -570,6 +571,13 @@ def padaptive(device, reps=10):
 
     t_stream = timed(lambda: hp.hp_op_apply(op, 1.0, x, y, stream))
     t_graph = timed(lambda: hp.hp_op_apply_graph(op, 1.0, x, y, stream))
+    y_blocks = y.clone()
+    # one persistent launch over a device work list (all blocks), plain and graph-captured
+    hp.hp_op_set_batching(op, 1)
+    t_wl = timed(lambda: hp.hp_op_apply(op, 1.0, x, y, stream))
+    t_wl_graph = timed(lambda: hp.hp_op_apply_graph(op, 1.0, x, y, stream))
+    wl_bitwise = bool(torch.equal(y, y_blocks))
+    hp.hp_op_set_batching(op, 0)
     hp.hp_op_tune(op, 1.0, x, y, stream)
     tiles = hp.hp_op_tiles(op, nblocks)
     t_tuned = timed(lambda: hp.hp_op_apply_graph(op, 1.0, x, y, stream))
@@ -614,21 +622,20 @@ def padaptive(device, reps=10):
             "dofs": int(dofs), "blocks": nblocks, "dtype": "f64",
             "per_block_launches": {"ms": round(t_stream, 4), "gdofs": g(t_stream)},
             "graph": {"ms": round(t_graph, 4), "gdofs": g(t_graph)},
+            "persistent_worklist": {"ms": round(t_wl, 4), "gdofs": g(t_wl), "bitwise_equal_to_per_block": wl_bitwise},
+            "persistent_worklist_graph": {"ms": round(t_wl_graph, 4), "gdofs": g(t_wl_graph)},
             "graph_autotuned": {"ms": round(t_tuned, 4), "gdofs": g(t_tuned),
                                 "tiles_histogram": np.bincount(tiles, minlength=3).tolist()},
             "tflops_graph_autotuned": round(flops / (t_tuned * 1e-3) / 1e12, 4)}
 
 
-def cpu_baseline(target_s=12.0):
-    """The oracle (plain FP64 numpy definition) on a bounded sample of the
-    workload: Helmholtz on a random subset of elements at each order."""
+def _oracle_sample(target_s):
+    """Time the oracle (plain FP64 numpy definition) on a bounded sample of the
+    workload: Helmholtz on a random subset of elements at each order, each
+    subset grown until it takes about target_s / 32 s.  Returns (output DOFs,
+    seconds, sample description)."""
     from oracle import operators as oracle_ops
     from paper_2604_04644_gb300 import inputs
-    try:
-        from threadpoolctl import threadpool_info
-        cores = max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
-    except Exception:
-        cores = os.cpu_count()
     rng = np.random.default_rng(0)
     dofs = 0
     t_total = 0.0
@@ -651,9 +658,36 @@ def cpu_baseline(target_s=12.0):
         dofs += int(sum(co[e + 1] - co[e] for e in el))
         t_total += dt
         sample_desc.append("P%d:%d" % (P, len(el)))
-    return {"value": dofs / t_total / 1e9, "unit": "GDOF/s", "cores": int(cores), "kind": "oracle",
-            "sample": "Helmholtz on random element subsets of the 16^3 mixed curved mesh (" +
-                      ",".join(sample_desc) + "), %.1f s of CPU work" % t_total}
+    return dofs, t_total, sample_desc
+
+
+def cpu_baseline(target_s=12.0, one_thread=True):
+    """The oracle on the host cores, all of them (numpy's thread pool) and, in
+    a child process whose BLAS / OpenMP pools are limited to one thread, one
+    core; GDOF/s on a bounded sample of the workload (see _oracle_sample)."""
+    nproc = os.cpu_count()
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
+    except Exception:
+        cores = nproc
+    dofs, t_total, desc = _oracle_sample(target_s)
+    out = {"value": dofs / t_total / 1e9, "unit": "GDOF/s", "cores": int(cores), "nproc": int(nproc or 0),
+           "kind": "oracle",
+           "sample": "Helmholtz on random element subsets of the 16^3 mixed curved mesh (" + ",".join(desc) +
+                     "), %.1f s of CPU work" % t_total}
+    if one_thread:
+        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+                   NUMEXPR_NUM_THREADS="1")
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", str(target_s)], env=env,
+                           capture_output=True, text=True, timeout=600)
+        try:
+            d1, t1, desc1 = json.loads(r.stdout.strip().splitlines()[-1])
+            out["one_thread"] = {"value": d1 / t1 / 1e9, "cores": 1, "seconds": round(t1, 2),
+                                 "sample": ",".join(desc1)}
+        except Exception:
+            out["one_thread"] = {"error": (r.stderr or r.stdout)[-300:]}
+    return out
 
 
 def run_reference(args, world, rank):
@@ -665,7 +699,7 @@ def run_reference(args, world, rank):
     t0 = time.time()
     cb = None
     for _ in range(max(args.steps, 1)):
-        cb = cpu_baseline(target_s=max(4.0, 60.0 / max(args.steps, 1)))
+        cb = cpu_baseline(target_s=max(4.0, 60.0 / max(args.steps, 1)), one_thread=False)
         vals.append(cb["value"])
     v = statistics.median(vals)
     line = {"metric": METRIC, "value": v, "unit": "GDOF/s", "n_gpus": args.gpus, "steps": args.steps,
@@ -1018,6 +1052,9 @@ def run_profile_case(name, local):
 
 def main():
     args = parse()
+    if args.oracle_sample is not None:     # the one-thread leg of cpu_baseline (a child process)
+        print(json.dumps(_oracle_sample(args.oracle_sample)), flush=True)
+        return
     world, rank, local = dist_init(args)
     if args.profile_case:
         if rank == 0:
@@ -1140,7 +1177,7 @@ def main():
     # FP64 PCG against the mixed-precision forms, on one GPU only
     solve = None
     if rank == 0 and world == 1 and not args.no_extra and not args.no_solve:
-        solve = run_solve(local, 64)
+        solve = run_solve(local, 64, scheduled=True)
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 4), "unit": "GDOF/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),

@@ -76,7 +76,12 @@ typedef enum {
     HP_BWDTRANS = 3,                /* coeff -> phys  : u = B uhat                               */
     HP_IPRODUCT_WRT_BASE = 4,       /* phys  -> coeff : B^T W f                                  */
     HP_PHYSDERIV = 5,               /* phys  -> 3 phys: du/dx_i of the Lagrange interpolant      */
-    HP_IPRODUCT_WRT_DERIV_BASE = 6  /* 3 phys -> coeff: sum_i (d phi/d x_i, f_i)                 */
+    HP_IPRODUCT_WRT_DERIV_BASE = 6, /* 3 phys -> coeff: sum_i (d phi/d x_i, f_i)                 */
+    HP_ADVECTION_DIFFUSION_REACTION = 7  /* coeff -> coeff: (grad phi_m, grad u) + (phi_m, a . grad u)
+                                            + lambda (phi_m, u), a constant velocity set by
+                                            hp_op_set_advection (Sec. 2.2 names this operator among those
+                                            the B^T {pointwise} B decomposition covers); the Helmholtz
+                                            passes with the advection term added at the points */
 } hp_opkind;
 
 typedef enum {
@@ -110,7 +115,14 @@ typedef enum { HP_FP64 = 0, HP_FP32 = 1, HP_TF32 = 2, HP_BF16 = 3 } hp_dtype;
  *                        tet (-1,-1,-1)(1,-1,-1)(-1,1,-1)(-1,-1,1)
  *   xyz[3*n_vert]        vertex coordinates, x y z per vertex
  *   curved[n_elem]       0: the element map is the affine vertex map; 1: apply `deformation`
- *   deformation          0 none; 1: x_i += 0.05 sin(pi x_j) sin(pi x_k), (i,j,k) cyclic
+ *   deformation          0 none; 1: x_i += 0.05 sin(pi x_j) sin(pi x_k), (i,j,k) cyclic;
+ *                        2: x_i += 0.1 x_j x_k (a quadratic map, for tests of the geometry)
+ *   geometry             0: curved elements use the map itself (analytic Jacobian);
+ *                        1: iso-parametric: each coordinate of a curved element's map is
+ *                        projected onto the element's own degree-P expansion (L2 projection on
+ *                        the reference element with its quadrature rule) and the Jacobian is
+ *                        that of the expansion (the iso-parametric curved elements of the
+ *                        paper's benchmarks, Sec. 4).  Affine elements are exact either way.
  * Every element must be an affine image of its reference element (all vertices
  * are checked); curved elements are that affine map followed by the deformation. */
 typedef struct {
@@ -123,6 +135,7 @@ typedef struct {
     int64_t n_vert;
     const uint8_t* curved;
     int32_t deformation;
+    int32_t geometry;
 } hp_mesh_desc;
 
 /* Create a mesh on CUDA device `device`: validates and copies the description,
@@ -144,6 +157,11 @@ hp_status hp_mesh_layout(hp_mesh mesh, int64_t* coeff_offset, int64_t* phys_offs
  * (d eta_d'/d x_i) (d <= d') and w|J|; for affine elements per element
  * |J| (d xi/d x)(d xi/d x)^T, |J| and d xi/d x.  Idempotent: the first call
  * computes, later calls return HP_OK at once.  Synchronises `stream`.
+ * With geometry = 1 the curved elements' factors come from the iso-parametric
+ * map (one kernel per block: the map at the points, its projection, the
+ * derivatives of the expansion), computed in FP64 on the device; the FP32 and
+ * tensor-core copies and every operator then use them.  hp_mesh_points still
+ * gives the points of the map itself.
  * Errors: HP_ERR_GEOM if some |J| <= 0 at a quadrature point (message names
  * the first such element), HP_ERR_CUDA. */
 hp_status hp_geom_factors(hp_mesh mesh, void* stream);
@@ -157,7 +175,8 @@ hp_status hp_geom_copy(hp_mesh mesh, double* out7, double* out9);
 
 /* Create an operator of kind `kind` over all blocks of `mesh`, computing in
  * `dtype` with `strategy`.  HP_FP64 and HP_FP32 apply to every kind with
- * HP_STRAT_SUMFAC; arrays passed to hp_op_apply are double (HP_FP64) or
+ * HP_STRAT_SUMFAC (the only strategy of the derivative building blocks and of
+ * HP_ADVECTION_DIFFUSION_REACTION); arrays passed to hp_op_apply are double (HP_FP64) or
  * float (HP_FP32, HP_TF32, HP_BF16).  HP_TF32 and HP_BF16 take HP_STRAT_ELEMAT (or AUTO) and the
  * kinds HP_MASS, HP_LAPLACIAN, HP_HELMHOLTZ: blocks with at most 256 modes per
  * element run the tensor-core elemental-matrix kernel, larger ones FP32 sum
@@ -191,6 +210,23 @@ hp_status hp_op_apply(hp_op op, double lambda, const void* in, void* out, void* 
  * replayed by later calls with the same arguments; other arguments rebuild it.
  * Do not call it while `stream` is being captured.  Errors as hp_op_apply. */
 hp_status hp_op_apply_graph(hp_op op, double lambda, const void* in, void* out, void* stream);
+
+/* How hp_op_apply and hp_op_apply_graph launch the blocks (a p-adaptive mesh
+ * has many blocks, each too small to fill the GPU).  mode 0 (the default):
+ * one kernel per block (hp_op_apply: one after another; hp_op_apply_graph: a
+ * CUDA graph with the blocks as concurrent nodes).  mode 1: one persistent
+ * launch over a device work list.  The blocks' element groups are cut into
+ * work items of about a quarter of a CTA's fair share of the FP64 operation
+ * count, ordered by decreasing cost.  Each CTA takes the next item from a
+ * device counter, stages that block's reference tables and runs its
+ * sum-factorisation body; hp_op_apply_graph captures the counter reset and
+ * that one launch.  Results are bitwise those of mode 0 (the same body per
+ * element).  Mode 1 needs an HP_FP64 operator in the collocated form whose
+ * blocks all use HP_STRAT_SUMFAC with P <= 8 (HP_ERR_UNSUPPORTED otherwise);
+ * writing other strategies, the non-collocated form or running a schedule
+ * search returns the op to mode 0.  Drops the op's captured graph.
+ * Errors: HP_ERR_ARG, HP_ERR_UNSUPPORTED, HP_ERR_CUDA / HP_ERR_OOM. */
+hp_status hp_op_set_batching(hp_op op, int mode);
 
 /* Autotune: time each block's kernel with each tile variant (elements per CTA
  * chosen from shared-memory budgets of 56, 20 and 110 KB) on the given arrays
@@ -230,6 +266,29 @@ hp_status hp_op_strategies(hp_op op, int* strategies, int64_t n_blocks, int set)
  * Drops the op's captured graph when the form changes.  hp_op_work and
  * hp_op_block_work keep reporting the collocated form's operation counts. */
 hp_status hp_op_set_collocated(hp_op op, int collocated);
+
+/* Advection velocity a (host array of 3 doubles, x y z) of an
+ * HP_ADVECTION_DIFFUSION_REACTION operator (0 at creation): its applies then
+ * compute (grad phi_m, grad u) + (phi_m, a . grad u) + lambda (phi_m, u).  At
+ * each point the velocity enters in collapsed coordinates, c_d = sum_i a_i
+ * d eta_d / d x_i (curved elements: the stored d eta / d x; affine ones:
+ * d eta / d xi times the element's d xi / d x).  Drops the op's captured graph.
+ * Errors: HP_ERR_ARG (null arguments, another operator kind). */
+hp_status hp_op_set_advection(hp_op op, const double* velocity);
+
+/* Summation order of the tensor-core operators' split tiles (HP_TF32 /
+ * HP_BF16; not in the paper).  A block with fewer 128-element tiles than the
+ * GPU has CTA slots splits each tile's point chunks over several CTAs, whose
+ * partial outputs are added.  deterministic = 0 (the default): FP32 atomics
+ * into the zeroed output, so results differ run to run at FP32 rounding
+ * (far below the form's own error); 1: each part writes its partial output
+ * to a scratch buffer of the op (parts x elements x modes floats per split
+ * block, allocated by the first apply that needs it) and one more kernel
+ * adds the parts in part order, so results are bitwise reproducible.  Other
+ * dtypes are always reproducible and ignore the flag.  hp_solve sets it on
+ * its inner tensor-core operator.  Drops the op's captured graph when the
+ * setting changes.  Errors: HP_ERR_ARG. */
+hp_status hp_op_set_deterministic(hp_op op, int deterministic);
 
 /* ---------------------------------------------------------------- cost model
  * Not in the paper (which picks a strategy by a fixed rule per operator):

@@ -100,7 +100,14 @@ hp_status check_device_error(hp_mesh m, unsigned int* d_err, int* d_bad, const c
     return HP_ERR_DEVICE_BOUNDS;
 }
 
+hp_status ensure_dense(hp_mesh m);
+hp_status ensure_iso(hp_mesh m);
+
 hp_status compute_geom(hp_mesh m, bool want_deriv, cudaStream_t s) {
+    if (m->geometry == 1) {
+        hp_status sti = ensure_iso(m);
+        if (sti) return sti;
+    }
     int* d_bad = nullptr;
     hp_status st = upload<int>(&d_bad, nullptr, 1);
     if (st) return st;
@@ -116,7 +123,9 @@ hp_status compute_geom(hp_mesh m, bool want_deriv, cudaStream_t s) {
             if (st) { cudaFree(d_bad); return st; }
         }
         const DeviceBlobs& blob = m->blobs.at(b.shape * 16 + b.P);
-        cudaError_t e = launch_geom(b, blob, m->deformation, want_deriv && b.curved, m->d_err, d_bad, s);
+        cudaError_t e = (b.curved && m->geometry == 1)
+                            ? launch_geom_iso(b, blob, m->deformation, want_deriv, m->d_err, d_bad, s)
+                            : launch_geom(b, blob, m->deformation, want_deriv && b.curved, m->d_err, d_bad, s);
         if (e != cudaSuccess) { cudaFree(d_bad); return cuda_fail(e, "geometry kernel"); }
         cudaError_t se = cudaStreamSynchronize(s);
         if (se != cudaSuccess) { cudaFree(d_bad); return cuda_fail(se, "geometry kernel"); }
@@ -166,9 +175,15 @@ hp_status ensure_geom(hp_mesh m, bool deriv, bool f32, cudaStream_t s) {
     return HP_OK;
 }
 
-bool coeff_in(hp_opkind k) { return k == HP_MASS || k == HP_LAPLACIAN || k == HP_HELMHOLTZ || k == HP_BWDTRANS; }
+bool coeff_in(hp_opkind k) {
+    return k == HP_MASS || k == HP_LAPLACIAN || k == HP_HELMHOLTZ || k == HP_BWDTRANS ||
+           k == HP_ADVECTION_DIFFUSION_REACTION;
+}
 bool coeff_out(hp_opkind k) { return k != HP_BWDTRANS && k != HP_PHYSDERIV; }
-bool needs_deriv_geom(hp_opkind k) { return k == HP_PHYSDERIV || k == HP_IPRODUCT_WRT_DERIV_BASE; }
+// kinds that read d eta / d x at the points (and are sum-factorised only)
+bool needs_deriv_geom(hp_opkind k) {
+    return k == HP_PHYSDERIV || k == HP_IPRODUCT_WRT_DERIV_BASE || k == HP_ADVECTION_DIFFUSION_REACTION;
+}
 
 hp_status ensure_dense(hp_mesh m) {
     for (auto& kv : m->blobs) {
@@ -187,6 +202,81 @@ hp_status ensure_dense(hp_mesh m) {
         if ((st = upload(&db.A4T_64, AT.data(), AT.size()))) return st;
         if ((st = upload(&db.A4_32, A32.data(), A32.size()))) return st;
         if ((st = upload(&db.A4T_32, AT32.data(), AT32.size()))) return st;
+    }
+    return HP_OK;
+}
+
+// Projection tables of the iso-parametric geometry for every (shape, P) of the
+// mesh's curved blocks.  The L2 projection on the reference element of point
+// values x onto the element's expansion is W^{-1/2} Qo Qo^T W^{1/2} x, with
+// W^{1/2} B = Qo R a Householder QR (B the modes at the points, W the
+// reference weights) and Qo formed explicitly from the reflectors: the
+// orthonormal columns keep it well conditioned, where the normal equations
+// B^T W B (or R^{-1}) of the modal basis lose digits at high order.
+// Stored (FP64): iso_RT [point][mode] = Qo W^{1/2} (coefficients c = S x of
+// the projection in the orthonormal functions, S = RT^T) and iso_VT
+// [mode][point] = (W^{-1/2} Qo)^T (their values at the points).
+hp_status ensure_iso(hp_mesh m) {
+    for (auto& kv : m->blobs) {
+        DeviceBlobs& db = kv.second;
+        const int shape = kv.first / 16, P = kv.first % 16;
+        bool used = false;
+        for (const Block& b : m->blocks) used |= b.curved && b.shape == shape && b.P == P;
+        if (!used || db.iso_RT) continue;
+        const RefTables& t = ref_tables(shape, P);
+        const int Q = t.Q, NQ = Q * Q * Q, NP = n_modes(shape, P);
+        std::vector<double> A4 = dense_matrices(shape, P);             // [4][NQ][NP], q = 0: B
+        std::vector<double> sw(NQ);
+        for (int i = 0; i < Q; ++i)
+            for (int j = 0; j < Q; ++j)
+                for (int k = 0; k < Q; ++k) sw[(i * Q + j) * Q + k] = std::sqrt(t.w[0][i] * t.w[1][j] * t.w[2][k]);
+        // Householder QR of A = W^{1/2} B, column-major; reflector j in V[j][.] (rows >= j)
+        std::vector<double> A((size_t)NP * NQ), V((size_t)NP * NQ, 0.0), vv(NP, 0.0);
+        for (int l = 0; l < NQ; ++l)
+            for (int c = 0; c < NP; ++c) A[(size_t)c * NQ + l] = sw[l] * A4[(size_t)l * NP + c];
+        for (int j = 0; j < NP; ++j) {
+            double* x = &A[(size_t)j * NQ];
+            double* v = &V[(size_t)j * NQ];
+            double nrm = 0.0;
+            for (int r = j; r < NQ; ++r) nrm += x[r] * x[r];
+            nrm = std::sqrt(nrm);
+            if (!(nrm > 0.0)) { set_error("iso-parametric geometry: rank-deficient mode table"); return HP_ERR_GEOM; }
+            const double alpha = x[j] > 0.0 ? -nrm : nrm;
+            for (int r = j; r < NQ; ++r) v[r] = x[r];
+            v[j] -= alpha;
+            for (int r = j; r < NQ; ++r) vv[j] += v[r] * v[r];
+            x[j] = alpha;
+            for (int r = j + 1; r < NQ; ++r) x[r] = 0.0;
+            for (int c = j + 1; c < NP; ++c) {
+                double* y = &A[(size_t)c * NQ];
+                double sdot = 0.0;
+                for (int r = j; r < NQ; ++r) sdot += v[r] * y[r];
+                const double f = 2.0 * sdot / vv[j];
+                for (int r = j; r < NQ; ++r) y[r] -= f * v[r];
+            }
+        }
+        // Qo = H_0 H_1 ... H_{NP-1} [I; 0], column-major (backward accumulation)
+        std::vector<double> Qo((size_t)NP * NQ, 0.0);
+        for (int c = 0; c < NP; ++c) Qo[(size_t)c * NQ + c] = 1.0;
+        for (int j = NP - 1; j >= 0; --j) {
+            const double* v = &V[(size_t)j * NQ];
+            for (int c = j; c < NP; ++c) {
+                double* y = &Qo[(size_t)c * NQ];
+                double sdot = 0.0;
+                for (int r = j; r < NQ; ++r) sdot += v[r] * y[r];
+                const double f = 2.0 * sdot / vv[j];
+                for (int r = j; r < NQ; ++r) y[r] -= f * v[r];
+            }
+        }
+        std::vector<double> RT((size_t)NQ * NP), VT((size_t)NP * NQ);
+        for (int l = 0; l < NQ; ++l)
+            for (int c = 0; c < NP; ++c) {
+                RT[(size_t)l * NP + c] = Qo[(size_t)c * NQ + l] * sw[l];
+                VT[(size_t)c * NQ + l] = Qo[(size_t)c * NQ + l] / sw[l];
+            }
+        hp_status st;
+        if ((st = upload(&db.iso_RT, RT.data(), RT.size()))) return st;
+        if ((st = upload(&db.iso_VT, VT.data(), VT.size()))) return st;
     }
     return HP_OK;
 }
@@ -340,6 +430,7 @@ double elem_flops(int shape, int P, hp_opkind k) {
         case HP_MASS: return 2 * bwd + NQ;
         case HP_LAPLACIAN: return 2 * bwd + 2 * deriv + 15 * NQ;
         case HP_HELMHOLTZ: return 2 * bwd + 2 * deriv + 18 * NQ;
+        case HP_ADVECTION_DIFFUSION_REACTION: return 2 * bwd + 2 * deriv + 40 * NQ;   // + velocity in eta, c . v
         case HP_PHYSDERIV: return deriv + 15 * NQ;
         default: return bwd + deriv + 18 * NQ;
     }
@@ -369,7 +460,7 @@ double elem_flops_exec(int shape, int P, hp_opkind k, bool fp64) {
             const double d = 4.0 * Q * NQ;                           // eta2, eta3 derivatives
             const double dt = Qh * QQ * (8.0 * Q + 4.0);              // paired transposed pass + sweeps
             const double r1 = 4.0 * Qh * n * QQ;                      // eta1 restriction of (y, w1)
-            const double metric = (k == HP_HELMHOLTZ ? 18.0 : 15.0) * NQ;
+            const double metric = (k == HP_HELMHOLTZ ? 18.0 : k == HP_ADVECTION_DIFFUSION_REACTION ? 40.0 : 15.0) * NQ;
             return b3 + b2 + u1 + v1 + d + metric + dt + r1 + r2 + r3;
         }
     }
@@ -471,6 +562,42 @@ cudaError_t ensure_matrix(hp_op op, size_t bi, double lambda, cudaStream_t s) {
     return cudaSuccess;
 }
 
+// descriptors of every block of an FP64 sum-factorised op for the work-list kernel
+std::vector<SFDesc> worklist_descs(hp_op op, double lambda, const void* in, void* out) {
+    hp_mesh m = op->mesh;
+    std::vector<SFDesc> d(m->blocks.size());
+    for (size_t i = 0; i < m->blocks.size(); ++i) {
+        const Block& b = m->blocks[i];
+        const DeviceBlobs& blob = m->blobs.at(b.shape * 16 + b.P);
+        SFDesc& a = d[i];
+        a.op = op->kind;
+        a.n_elem = b.n_elem;
+        a.lambda = lambda;
+        for (int k = 0; k < 3; ++k) a.adv[k] = op->adv[k];
+        a.coeff_off = b.d_coeff_off;
+        a.phys_off = b.d_phys_off;
+        a.in = static_cast<const double*>(in);
+        a.out = static_cast<double*>(out);
+        a.n_phys_total = m->phys_off.back();
+        a.geom = b.d_geom;
+        a.dgeom = b.d_dgeom;
+        a.blob = static_cast<const unsigned char*>(blob.d64);
+        a.blob_bytes = blob.bytes64;
+        a.err = op->d_err;
+    }
+    return d;
+}
+
+// one persistent launch over all blocks; the descriptors are copied from
+// pageable host memory (the copy has consumed the host buffer when it returns)
+cudaError_t launch_worklist(hp_op op, double lambda, const void* in, void* out, cudaStream_t s) {
+    std::vector<SFDesc> d = worklist_descs(op, lambda, in, out);
+    cudaError_t e = cudaMemcpyAsync(op->d_desc, d.data(), sizeof(SFDesc) * d.size(), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    return sf_worklist_launch(static_cast<const SFDesc*>(op->d_desc), static_cast<const WorkItem*>(op->d_items),
+                              op->n_items, op->d_next, op->wl_smem, op->wl_grid, op->d_err, s);
+}
+
 cudaError_t launch_block(hp_op op, size_t bi, int tile, double lambda, const void* in, void* out, cudaStream_t s) {
     hp_mesh m = op->mesh;
     const Block& b = m->blocks[bi];
@@ -501,6 +628,25 @@ cudaError_t launch_block(hp_op op, size_t bi, int tile, double lambda, const voi
         // backward MMAs); TF32: forward slices and backward tiles separately
         a.stage_bytes = bf ? a.fwd_bytes : (std::max(4 * tc_chunk_points() * 128, a.bwd_bytes) + 1023) & ~1023;
         a.err = op->d_err;
+        a.part_out = nullptr;
+        if (op->deterministic) {   // split tiles: partial outputs in a scratch of the op, summed in part order
+            const int ns = tc_emat_nsplit(a);
+            if (ns < 1) return cudaErrorInvalidValue;
+            const int64_t need = ns > 1 ? (int64_t)ns * b.n_elem * a.NP : 0;
+            if (op->part_buf.size() != op->strat.size()) {
+                op->part_buf.assign(op->strat.size(), nullptr);
+                op->part_cap.assign(op->strat.size(), 0);
+            }
+            if (need > op->part_cap[bi]) {
+                cudaFree(op->part_buf[bi]);
+                op->part_buf[bi] = nullptr;
+                op->part_cap[bi] = 0;
+                cudaError_t e = cudaMalloc(&op->part_buf[bi], sizeof(float) * (size_t)need);
+                if (e != cudaSuccess) { cudaGetLastError(); op->part_buf[bi] = nullptr; return e; }
+                op->part_cap[bi] = need;
+            }
+            a.part_out = need > 0 ? op->part_buf[bi] : nullptr;
+        }
         return tc_emat_launch(a, s);
     }
     if (op->strat[bi] != HP_STRAT_SUMFAC) {
@@ -539,6 +685,7 @@ cudaError_t launch_block(hp_op op, size_t bi, int tile, double lambda, const voi
         a.blob = static_cast<const unsigned char*>(blob.d64);
         a.blob_bytes = blob.bytes64;
         a.err = op->d_err;
+        for (int i = 0; i < 3; ++i) a.adv[i] = op->adv[i];
         fill_const_tables(b, a);
         if (!op->collocated && (op->kind == HP_LAPLACIAN || op->kind == HP_HELMHOLTZ))
             return sf_nc_launch(b.shape, b.P, !b.curved, a, blob.d_nc64, s);
@@ -558,6 +705,7 @@ cudaError_t launch_block(hp_op op, size_t bi, int tile, double lambda, const voi
     a.blob = static_cast<const unsigned char*>(blob.d32);
     a.blob_bytes = blob.bytes32;
     a.err = op->d_err;
+    for (int i = 0; i < 3; ++i) a.adv[i] = (float)op->adv[i];
     fill_const_tables(b, a);
     return sf_launch_f32(b.shape, b.P, !b.curved, tile, a, s);
 }
@@ -593,7 +741,8 @@ hp_status hp_mesh_create(const hp_mesh_desc* d, int device, hp_mesh* out) {
         set_error("hp_mesh_create: bad descriptor (null array or empty mesh)");
         return HP_ERR_ARG;
     }
-    if (d->deformation < 0 || d->deformation > 1) { set_error("hp_mesh_create: unknown deformation"); return HP_ERR_ARG; }
+    if (d->deformation < 0 || d->deformation > 2) { set_error("hp_mesh_create: unknown deformation"); return HP_ERR_ARG; }
+    if (d->geometry < 0 || d->geometry > 1) { set_error("hp_mesh_create: geometry must be 0 or 1"); return HP_ERR_ARG; }
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
         set_error("hp_mesh_create: no such CUDA device");
@@ -604,6 +753,7 @@ hp_status hp_mesh_create(const hp_mesh_desc* d, int device, hp_mesh* out) {
     m->device = device;
     m->n_elem = d->n_elem;
     m->deformation = d->deformation;
+    m->geometry = d->geometry;
     m->shape.assign(d->shape, d->shape + d->n_elem);
     m->P.assign(d->P, d->P + d->n_elem);
     m->Q.assign(d->Q, d->Q + d->n_elem);
@@ -810,7 +960,7 @@ hp_status hp_geom_copy(hp_mesh m, double* out7, double* out9) {
 hp_status hp_op_create(hp_mesh m, hp_opkind kind, hp_strategy strategy, hp_dtype dtype, hp_op* out) {
     if (!m || !out) { set_error("hp_op_create: null argument"); return HP_ERR_ARG; }
     *out = nullptr;
-    if ((int)kind < 0 || kind > HP_IPRODUCT_WRT_DERIV_BASE) { set_error("hp_op_create: bad kind"); return HP_ERR_ARG; }
+    if ((int)kind < 0 || kind > HP_ADVECTION_DIFFUSION_REACTION) { set_error("hp_op_create: bad kind"); return HP_ERR_ARG; }
     if ((int)strategy < 0 || strategy > HP_STRAT_MATRIX) { set_error("hp_op_create: bad strategy"); return HP_ERR_ARG; }
     if ((int)dtype < 0 || dtype > HP_BF16) { set_error("hp_op_create: bad dtype"); return HP_ERR_ARG; }
     const bool tcore = dtype == HP_TF32 || dtype == HP_BF16;
@@ -820,8 +970,9 @@ hp_status hp_op_create(hp_mesh m, hp_opkind kind, hp_strategy strategy, hp_dtype
         set_error("hp_op_create: HP_TF32 / HP_BF16 are the tensor-core elemental-matrix form of mass, Laplacian and Helmholtz");
         return HP_ERR_UNSUPPORTED;
     }
-    if (strategy != HP_STRAT_SUMFAC && (kind == HP_PHYSDERIV || kind == HP_IPRODUCT_WRT_DERIV_BASE)) {
-        set_error("hp_op_create: derivative building blocks exist only with HP_STRAT_SUMFAC");
+    if (strategy != HP_STRAT_SUMFAC && needs_deriv_geom(kind)) {
+        set_error("hp_op_create: derivative building blocks and the advection-diffusion-reaction operator exist only "
+                  "with HP_STRAT_SUMFAC");
         return HP_ERR_UNSUPPORTED;
     }
     if (strategy == HP_STRAT_MATRIX && kind != HP_MASS && kind != HP_LAPLACIAN && kind != HP_HELMHOLTZ) {
@@ -862,10 +1013,94 @@ hp_status hp_op_apply(hp_op op, double lambda, const void* in, void* out, void* 
     if (!op || !in || !out) { set_error("hp_op_apply: null argument"); return HP_ERR_ARG; }
     if (in == out) { set_error("hp_op_apply: in and out must not alias"); return HP_ERR_ARG; }
     DeviceGuard guard(op->mesh->device);
+    if (op->batching == 1) {
+        cudaError_t e = launch_worklist(op, lambda, in, out, (cudaStream_t)stream);
+        return e == cudaSuccess ? HP_OK : cuda_fail(e, "hp_op_apply work-list launch");
+    }
     for (size_t i = 0; i < op->mesh->blocks.size(); ++i) {
         cudaError_t e = launch_block(op, i, op->tile[i], lambda, in, out, (cudaStream_t)stream);
         if (e != cudaSuccess) return cuda_fail(e, "hp_op_apply launch");
     }
+    return HP_OK;
+}
+
+hp_status hp_op_set_batching(hp_op op, int mode) {
+    if (!op || (mode != 0 && mode != 1)) { set_error("hp_op_set_batching: bad argument"); return HP_ERR_ARG; }
+    DeviceGuard guard(op->mesh->device);
+    if (op->graph) { cudaGraphExecDestroy(op->graph); op->graph = nullptr; }
+    if (mode == 0) { op->batching = 0; return HP_OK; }
+    const hp_mesh m = op->mesh;
+    if (op->dtype != HP_FP64 || !op->collocated) {
+        set_error("hp_op_set_batching: the work-list launch is for FP64 collocated sum factorisation");
+        return HP_ERR_UNSUPPORTED;
+    }
+    for (size_t i = 0; i < m->blocks.size(); ++i)
+        if (op->strat[i] != HP_STRAT_SUMFAC || m->blocks[i].P > kWorklistMaxP) {
+            set_error("hp_op_set_batching: every block must be sum-factorised with P <= 8");
+            return HP_ERR_UNSUPPORTED;
+        }
+    int smem = 0;
+    for (const Block& b : m->blocks) smem = std::max(smem, sf_worklist_smem(b.shape, b.P));
+    int grid = 0;
+    cudaError_t e = sf_worklist_grid(smem, &grid);
+    if (e != cudaSuccess) return cuda_fail(e, "hp_op_set_batching");
+    // work items: each block's element groups cut into chunks of about a
+    // quarter of a CTA's fair share of the total cost (FP64 operations), the
+    // chunks ordered by decreasing cost so that the last items are small
+    std::vector<WorkItem> items;
+    std::vector<double> cost;
+    double total = 0.0;
+    std::vector<double> gcost(m->blocks.size());
+    std::vector<int64_t> ng(m->blocks.size());
+    for (size_t i = 0; i < m->blocks.size(); ++i) {
+        const Block& b = m->blocks[i];
+        const int epb = sf_worklist_epb(b.P);
+        ng[i] = (b.n_elem + epb - 1) / epb;
+        gcost[i] = epb * elem_flops_exec(b.shape, b.P, op->kind, true);
+        total += gcost[i] * ng[i];
+    }
+    const double target = total / (4.0 * grid);
+    for (size_t i = 0; i < m->blocks.size(); ++i) {
+        const Block& b = m->blocks[i];
+        const int64_t per = std::max<int64_t>(1, (int64_t)(target / std::max(gcost[i], 1.0)));
+        for (int64_t g = 0; g < ng[i]; g += per) {
+            WorkItem w;
+            w.block = (int32_t)i;
+            w.key = b.shape * 32 + b.P * 2 + (b.curved ? 0 : 1);
+            w.g0 = g;
+            w.g1 = std::min(ng[i], g + per);
+            items.push_back(w);
+            cost.push_back(gcost[i] * (double)(w.g1 - w.g0));
+        }
+    }
+    std::vector<size_t> ord(items.size());
+    for (size_t k = 0; k < ord.size(); ++k) ord[k] = k;
+    std::stable_sort(ord.begin(), ord.end(), [&](size_t x, size_t y) { return cost[x] > cost[y]; });
+    std::vector<WorkItem> sorted(items.size());
+    for (size_t k = 0; k < ord.size(); ++k) sorted[k] = items[ord[k]];
+    cudaFree(op->d_items);
+    cudaFree(op->d_desc);
+    cudaFree(op->d_desc_graph);
+    cudaFree(op->d_next);
+    op->d_items = op->d_desc = op->d_desc_graph = nullptr;
+    op->d_next = nullptr;
+    hp_status st;
+    WorkItem* di = nullptr;
+    SFDesc *dd = nullptr, *dg = nullptr;
+    if ((st = upload(&di, sorted.data(), sorted.size())) || (st = upload<SFDesc>(&dd, nullptr, m->blocks.size())) ||
+        (st = upload<SFDesc>(&dg, nullptr, m->blocks.size())) || (st = upload<int>(&op->d_next, nullptr, 1))) {
+        cudaFree(di);
+        cudaFree(dd);
+        cudaFree(dg);
+        return st;
+    }
+    op->d_items = di;
+    op->d_desc = dd;
+    op->d_desc_graph = dg;
+    op->n_items = (int)sorted.size();
+    op->wl_smem = smem;
+    op->wl_grid = grid;
+    op->batching = 1;
     return HP_OK;
 }
 
@@ -932,6 +1167,28 @@ hp_status hp_op_set_collocated(hp_op op, int collocated) {
     }
     if (op->collocated != collocated && op->graph) { cudaGraphExecDestroy(op->graph); op->graph = nullptr; }
     op->collocated = collocated;
+    if (!collocated) op->batching = 0;   // the work-list launch runs the collocated form
+    return HP_OK;
+}
+
+hp_status hp_op_set_advection(hp_op op, const double* velocity) {
+    if (!op || !velocity) { set_error("hp_op_set_advection: null argument"); return HP_ERR_ARG; }
+    if (op->kind != HP_ADVECTION_DIFFUSION_REACTION) {
+        set_error("hp_op_set_advection: the operator is not HP_ADVECTION_DIFFUSION_REACTION");
+        return HP_ERR_ARG;
+    }
+    for (int i = 0; i < 3; ++i) op->adv[i] = velocity[i];
+    if (op->graph) { cudaGraphExecDestroy(op->graph); op->graph = nullptr; }
+    return HP_OK;
+}
+
+hp_status hp_op_set_deterministic(hp_op op, int deterministic) {
+    if (!op || (deterministic != 0 && deterministic != 1)) {
+        set_error("hp_op_set_deterministic: bad argument");
+        return HP_ERR_ARG;
+    }
+    if (op->deterministic != deterministic && op->graph) { cudaGraphExecDestroy(op->graph); op->graph = nullptr; }
+    op->deterministic = deterministic;
     return HP_OK;
 }
 
@@ -940,6 +1197,34 @@ hp_status hp_op_apply_graph(hp_op op, double lambda, const void* in, void* out, 
     if (in == out) { set_error("hp_op_apply_graph: in and out must not alias"); return HP_ERR_ARG; }
     DeviceGuard guard(op->mesh->device);
     cudaStream_t s = (cudaStream_t)stream;
+    if (op->batching == 1 && (!op->graph || op->g_in != in || op->g_out != out || op->g_lambda != lambda)) {
+        // one persistent launch: the graph holds the counter reset and the kernel;
+        // its descriptors are uploaded once, before the capture
+        if (op->graph) { cudaGraphExecDestroy(op->graph); op->graph = nullptr; }
+        cudaError_t e = launch_worklist(op, lambda, in, out, s);   // warm-up (kernel attributes)
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        std::vector<SFDesc> d = worklist_descs(op, lambda, in, out);
+        if (e == cudaSuccess) e = cudaMemcpy(op->d_desc_graph, d.data(), sizeof(SFDesc) * d.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(e, "hp_op_apply_graph work-list warm-up");
+        cudaStream_t cap;
+        e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
+        cudaGraph_t g = nullptr;
+        e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            e = sf_worklist_launch(static_cast<const SFDesc*>(op->d_desc_graph), static_cast<const WorkItem*>(op->d_items),
+                                   op->n_items, op->d_next, op->wl_smem, op->wl_grid, op->d_err, cap);
+            cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+            if (e == cudaSuccess) e = e2;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&op->graph, g, 0);
+        if (g) cudaGraphDestroy(g);
+        cudaStreamDestroy(cap);
+        if (e != cudaSuccess) { op->graph = nullptr; return cuda_fail(e, "hp_op_apply_graph work-list capture"); }
+        op->g_in = in;
+        op->g_out = out;
+        op->g_lambda = lambda;
+    }
     if (!op->graph || op->g_in != in || op->g_out != out || op->g_lambda != lambda) {
         if (op->graph) { cudaGraphExecDestroy(op->graph); op->graph = nullptr; }
         const size_t nb = op->mesh->blocks.size();
@@ -1036,6 +1321,8 @@ hp_status hp_op_strategies(hp_op op, int* strat, int64_t n_blocks, int set) {
         hp_status st = ensure_dense(op->mesh);
         if (st) return st;
     }
+    for (int64_t i = 0; i < n_blocks; ++i)
+        if (strat[i] != HP_STRAT_SUMFAC) op->batching = 0;   // the work-list launch is sum factorisation only
     for (int64_t i = 0; i < n_blocks; ++i) {
         op->strat[i] = strat[i];
         if (strat[i] != HP_STRAT_MATRIX && i < (int64_t)op->mat.size() && op->mat[i]) {   // release its matrices
@@ -1112,6 +1399,7 @@ hp_status hp_op_schedule_exhaustive(hp_op op, double lambda, const void* in, voi
     if (!op || !in || !out) { set_error("hp_op_schedule_exhaustive: null argument"); return HP_ERR_ARG; }
     if (in == out) { set_error("hp_op_schedule_exhaustive: in and out must not alias"); return HP_ERR_ARG; }
     DeviceGuard guard(op->mesh->device);
+    op->batching = 0;
     const int64_t nb = (int64_t)op->strat.size();
     if (!needs_deriv_geom(op->kind) && op->dtype != HP_TF32 && op->dtype != HP_BF16) {
         hp_status st = ensure_dense(op->mesh);
@@ -1186,6 +1474,7 @@ hp_status hp_op_schedule_graph(hp_op op, double lambda, const void* in, void* ou
     if (!op || !in || !out || in == out) { set_error("hp_op_schedule_graph: null or aliasing arrays"); return HP_ERR_ARG; }
     if (reps < 1 || reps > 64 || passes < 1 || passes > 8) { set_error("hp_op_schedule_graph: reps or passes out of range"); return HP_ERR_ARG; }
     DeviceGuard guard(op->mesh->device);
+    op->batching = 0;   // the search times per-block graphs
     if (!needs_deriv_geom(op->kind) && op->dtype != HP_TF32 && op->dtype != HP_BF16) {
         hp_status st = ensure_dense(op->mesh);
         if (st) return st;
@@ -1297,6 +1586,7 @@ hp_status hp_op_block_work(hp_op op, int64_t block, int64_t* n_elem, int64_t* ou
             case HP_IPRODUCT_WRT_BASE: geo = b.curved ? NQ : 1; break;
             case HP_PHYSDERIV: geo = b.curved ? 9 * NQ : 9; break;
             case HP_IPRODUCT_WRT_DERIV_BASE: geo = b.curved ? 10 * NQ : 10; break;
+            case HP_ADVECTION_DIFFUSION_REACTION: geo = b.curved ? 16 * NQ : 16; break;
             default: geo = 0;
         }
         if (st == HP_STRAT_MATRIX) geo = np * np;   // the stored matrix takes the place of the factors
@@ -1326,6 +1616,11 @@ void hp_op_destroy(hp_op op) {
     if (op->graph) cudaGraphExecDestroy(op->graph);
     for (cudaStream_t t : op->pool) cudaStreamDestroy(t);
     for (void* p : op->mat) cudaFree(p);
+    for (float* p : op->part_buf) cudaFree(p);
+    cudaFree(op->d_desc);
+    cudaFree(op->d_desc_graph);
+    cudaFree(op->d_items);
+    cudaFree(op->d_next);
     cudaFree(op->d_err);
     delete op;
 }
@@ -1339,6 +1634,8 @@ void hp_mesh_destroy(hp_mesh m) {
             cudaFree(kv.second.d64);
             cudaFree(kv.second.d32);
             cudaFree(kv.second.d_nc64);
+            cudaFree(kv.second.iso_RT);
+            cudaFree(kv.second.iso_VT);
             cudaFree(kv.second.A4_64);
             cudaFree(kv.second.A4T_64);
             cudaFree(kv.second.A4_32);

@@ -157,4 +157,23 @@ __device__ __forceinline__ bool stage_tables(void* dst, const void* src, uint32_
     return __syncthreads_and(ok ? 1 : 0) != 0;
 }
 
+// The same with a barrier the caller initialised once (count 1) and reuses:
+// each staging waits on `phase`, which then flips for the next one.  Every
+// thread must have finished with the previous tables (a CTA barrier) before
+// the call.
+__device__ __forceinline__ bool stage_tables_phase(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
+                                                   uint32_t& phase, unsigned int* err) {
+    if (threadIdx.x == 0) {
+        mbar_expect_tx(bar, bytes);
+        bulk_g2s(dst, src, bytes, bar);
+    }
+    bool ok = mbar_wait_bounded(bar, phase, kWaitLimitNs);
+    if (!ok) {
+        if (threadIdx.x == 0) atomicOr(err, DERR_TIMEOUT);
+        mbar_wait_bounded(bar, phase, kWaitLimitNs);
+    }
+    phase ^= 1u;
+    return __syncthreads_and(ok ? 1 : 0) != 0;
+}
+
 }  // namespace hp

@@ -87,6 +87,10 @@ struct DeviceBlobs {
     int64_t tc_chunk = 0;
     // derivative tables [Tbd | Tcd] in FP64, for the non-collocated sum-factorisation kernel
     double* d_nc64 = nullptr;
+    // iso-parametric geometry (FP64): point values -> coefficients of the projection in
+    // reference-orthonormal functions, S^T [point][mode], and their values VT [mode][point]
+    double* iso_RT = nullptr;
+    double* iso_VT = nullptr;
 };
 
 }  // namespace hp
@@ -95,6 +99,7 @@ struct hp_mesh_s {
     int device = 0;
     int64_t n_elem = 0;
     int deformation = 0;
+    int geometry = 0;                           // 0 analytic map, 1 iso-parametric (curved elements)
     std::vector<uint8_t> shape, P, Q, curved;
     std::vector<int64_t> coeff_off, phys_off;   // n_elem + 1
     std::vector<int64_t> vert;                  // n_elem * 8 global vertex ids (for the C0 map)
@@ -113,6 +118,17 @@ struct hp_op_s {
     std::vector<int> tile;                      // tile variant per block
     std::vector<int> strat;                     // hp_strategy per block (SUMFAC, ELEMAT, HYBRID)
     int collocated = 1;                         // 0: FP64 sum-factorised Laplacian/Helmholtz in the non-collocated form
+    int deterministic = 0;                      // 1: tensor-core split tiles summed in a fixed order
+    double adv[3] = {0.0, 0.0, 0.0};            // advection velocity of an advection-diffusion-reaction op
+    // batching 1: every block in one persistent work-list launch (FP64 sum factorisation)
+    int batching = 0;
+    void* d_desc = nullptr;                     // SFDesc per block (plain applies)
+    void* d_desc_graph = nullptr;               // the same for the captured graph
+    void* d_items = nullptr;                    // WorkItem list, by decreasing cost
+    int* d_next = nullptr;                      // work-list counter
+    int n_items = 0, wl_smem = 0, wl_grid = 0;
+    std::vector<float*> part_buf;               // their partial outputs, per block (grown on demand)
+    std::vector<int64_t> part_cap;
     // matrix-based blocks: stored H^e as Ht[n][e][m] (FP64 or FP32, the op's I/O type), built on
     // the first apply, and again when lambda changes (Helmholtz)
     std::vector<void*> mat;
@@ -138,6 +154,9 @@ constexpr unsigned int DERR_GEOM = 4u;
 // launch of the geometry kernel over one block (hp_geom.cu)
 cudaError_t launch_geom(const Block& b, const DeviceBlobs& blob, int deformation, bool want_deriv,
                         unsigned int* d_err, int* d_bad_elem, cudaStream_t s);
+// iso-parametric geometric factors of a curved block (needs blob.iso_RT and blob.iso_VT)
+cudaError_t launch_geom_iso(const Block& b, const DeviceBlobs& blob, int deformation, bool want_deriv,
+                            unsigned int* d_err, int* d_bad_elem, cudaStream_t s);
 cudaError_t launch_to_f32(const double* src, float* dst, int64_t n, cudaStream_t s);
 // physical coordinates of the quadrature points of a block, xyz[c*n_phys_total + phys_off + l]
 cudaError_t launch_points(const Block& b, const DeviceBlobs& blob, int deformation, double* xyz,
@@ -154,6 +173,7 @@ struct SFArgs {
     int op;                      // hp_opkind
     int64_t n_elem;
     T lambda;
+    T adv[3];                    // advection velocity (HP_ADVECTION_DIFFUSION_REACTION)
     const int64_t* coeff_off;    // per block element
     const int64_t* phys_off;
     const T* in;
@@ -203,8 +223,12 @@ struct TCArgs {
     int fwd_bytes, bwd_bytes, stage_bytes;
     int es;                            // operand bytes: 4 TF32, 2 BF16
     int nsplit, stages, ubufs;         // set by the launcher
+    float* part_out;                   // nullptr: split tiles add with atomics; else [nsplit][n_elem][NP]
+                                       // partial outputs summed in part order (deterministic)
     unsigned int* err;
 };
+// parts per tile the launcher will use (0 on error): part_out needs nsplit * n_elem * NP floats
+int tc_emat_nsplit(const TCArgs& a);
 constexpr int kTcMaxModes = 256;
 int tc_chunk_points();
 int64_t tc_geom_halves(int64_t n_elem, int nch);
@@ -212,6 +236,36 @@ cudaError_t tc_geom_layout16(int shape, bool curved, const double* g, int NQp, c
                              uint16_t* out, float* isc, int64_t n_elem, int nch, cudaStream_t s);
 cudaError_t tc_emat_launch(const TCArgs& a, cudaStream_t s);
 cudaError_t emat_launch_f32(bool hybrid, bool affine, const EMArgs<float>& a, cudaStream_t s);
+
+// persistent work-list form of the FP64 sum-factorised operators (hp_sf_worklist.cu):
+// one launch in which CTAs take work items (a block and a range of its element
+// groups) from a device counter and run that block's (shape, P, affine) body
+struct SFDesc {                  // the fields of SFArgs<double> the FP64 bodies read
+    int op;
+    int64_t n_elem;
+    double lambda;
+    double adv[3];
+    const int64_t* coeff_off;
+    const int64_t* phys_off;
+    const double* in;
+    double* out;
+    int64_t n_phys_total;
+    const double* geom;
+    const double* dgeom;
+    const unsigned char* blob;
+    int blob_bytes;
+    unsigned int* err;
+};
+struct WorkItem {
+    int32_t block, key;          // key = shape * 32 + P * 2 + affine
+    int64_t g0, g1;              // element groups [g0, g1) of the block
+};
+constexpr int kWorklistMaxP = 8;
+int sf_worklist_epb(int P);                       // elements per group (tile 0)
+int sf_worklist_smem(int shape, int P);           // dynamic shared memory of that body
+cudaError_t sf_worklist_grid(int smem, int* grid);   // CTAs resident on the device at that smem
+cudaError_t sf_worklist_launch(const SFDesc* desc, const WorkItem* items, int n_items, int* next, int smem, int grid,
+                               unsigned int* err, cudaStream_t s);
 
 // per-shape launchers (hp_sf_<shape>.cu)
 cudaError_t sf_launch_f64(int shape, int P, bool affine, int tile, const SFArgs<double>& a, cudaStream_t s);

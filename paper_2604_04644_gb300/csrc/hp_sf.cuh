@@ -60,8 +60,15 @@ __host__ __device__ constexpr int sf_min_blocks() {
     return b < 1 ? 1 : (b > 4 ? 4 : b);
 }
 
-template <int SHAPE, int P, typename T, bool AFFINE, int TILE>
-__global__ void __launch_bounds__(256, (sf_min_blocks<SHAPE, P, T, TILE>())) sf_kernel(const __grid_constant__ SFArgs<T> args) {
+// One CTA's share of a block of (SHAPE, P): stage the block's reference
+// tables into shared memory (one bulk copy on the CTA's barrier at smem[0],
+// initialised by the caller, waiting on `phase`, which then flips), then
+// process the element groups g_first, g_first + g_step, ... below g_end.
+// Returns false (error word set) if the copy did not land in time.  A is
+// SFArgs<T> or any struct with the same fields the instantiation reads.
+template <int SHAPE, int P, typename T, bool AFFINE, int TILE, typename A>
+__device__ __forceinline__ bool sf_groups(const A& args, unsigned char* smem, int64_t g_first, int64_t g_step,
+                                          int64_t g_end, uint32_t& phase) {
     using C = SFCfg<P, T, TILE>;
     constexpr int n = C::n, Q = C::Q, QQ = C::QQ, NQ = C::NQ, N3 = C::N3, EPB = C::EPB, NT = C::NT;
     constexpr int NN = n * n, Qh = (Q + 1) / 2;   // Qh: even-odd pairs (i, Q-1-i) along eta1
@@ -75,10 +82,9 @@ __global__ void __launch_bounds__(256, (sf_min_blocks<SHAPE, P, T, TILE>())) sf_
     constexpr int kU = 4;      // FP32: loop iterations per thread whose global loads are issued together
     constexpr int kUG = 8;     // the same for the coefficient gather (one batch for most blocks)
 
-    extern __shared__ __align__(16) unsigned char smem[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
     unsigned char* tab = smem + 16;
-    if (!stage_tables(tab, args.blob, L.total_bytes, bar, args.err)) return;
+    if (!stage_tables_phase(tab, args.blob, L.total_bytes, bar, phase, args.err)) return false;
 
     const T* Ta = reinterpret_cast<const T*>(tab) + L.Ta;   // parity form {1/2, -z/2, psi_2..}
     const T* Td = reinterpret_cast<const T*>(tab) + L.Td;   // its eta1 derivative
@@ -105,13 +111,13 @@ __global__ void __launch_bounds__(256, (sf_min_blocks<SHAPE, P, T, TILE>())) sf_
 
     const int tid = threadIdx.x;
     const int op = args.op;
-    const bool coeff_in = (op == HP_MASS || op == HP_LAPLACIAN || op == HP_HELMHOLTZ || op == HP_BWDTRANS);
-    const bool deriv = (op == HP_LAPLACIAN || op == HP_HELMHOLTZ || op == HP_PHYSDERIV);
-    const bool sumderiv = (op == HP_LAPLACIAN || op == HP_HELMHOLTZ || op == HP_IPRODUCT_WRT_DERIV_BASE);
+    const bool adr = op == HP_ADVECTION_DIFFUSION_REACTION;
+    const bool coeff_in = (op == HP_MASS || op == HP_LAPLACIAN || op == HP_HELMHOLTZ || op == HP_BWDTRANS || adr);
+    const bool deriv = (op == HP_LAPLACIAN || op == HP_HELMHOLTZ || op == HP_PHYSDERIV || adr);
+    const bool sumderiv = (op == HP_LAPLACIAN || op == HP_HELMHOLTZ || op == HP_IPRODUCT_WRT_DERIV_BASE || adr);
     const bool merged = !LINES && deriv && coeff_in;   // v1 comes out of the eta1 pass
-    const int64_t ngroups = (args.n_elem + EPB - 1) / EPB;
 
-    for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x) {
+    for (int64_t g = g_first; g < g_end; g += g_step) {
         const int64_t e0 = g * EPB;
         const int ne = (int)min((int64_t)EPB, args.n_elem - e0);
 
@@ -426,8 +432,8 @@ __global__ void __launch_bounds__(256, (sf_min_blocks<SHAPE, P, T, TILE>())) sf_
             }
             const int64_t eg = e0 + e;
             T G[6], wJ, Gx[3][3];
-            const bool need_gx = (op == HP_PHYSDERIV || op == HP_IPRODUCT_WRT_DERIV_BASE);
-            if (AFFINE && (op == HP_LAPLACIAN || op == HP_HELMHOLTZ)) {
+            const bool need_gx = (op == HP_PHYSDERIV || op == HP_IPRODUCT_WRT_DERIV_BASE || adr);
+            if (AFFINE && (op == HP_LAPLACIAN || op == HP_HELMHOLTZ || adr)) {
                 // affine element: w = wl T K T^T v with K = |J| (d xi/d x)(d xi/d x)^T
                 // per element and T = d eta / d xi at the reference point, whose
                 // collapse factors come from the reciprocal tables 1/(1 - z) (no
@@ -461,7 +467,16 @@ __global__ void __launch_bounds__(256, (sf_min_blocks<SHAPE, P, T, TILE>())) sf_
                 u[NQ] = t00 * h0 + t01 * h1 + t02 * h2;     // w = T h
                 u[2 * NQ] = t11 * h1 + t12 * h2;
                 u[3 * NQ] = h2;
-                S2[e * NQ + r] = (op == HP_HELMHOLTZ) ? args.lambda * wl * rec[6] * uval : T(0);
+                T mass = (op == HP_HELMHOLTZ || adr) ? args.lambda * uval : T(0);
+                if (adr) {
+                    // advection a . grad u = c . v with c = T (d xi / d x) a, the
+                    // velocity in eta coordinates (rec[7 + 3 a + i] = d xi_a / d x_i)
+                    const T b0 = rec[7] * args.adv[0] + rec[8] * args.adv[1] + rec[9] * args.adv[2];
+                    const T b1 = rec[10] * args.adv[0] + rec[11] * args.adv[1] + rec[12] * args.adv[2];
+                    const T b2 = rec[13] * args.adv[0] + rec[14] * args.adv[1] + rec[15] * args.adv[2];
+                    mass += (t00 * b0 + t01 * b1 + t02 * b2) * v0 + (t11 * b1 + t12 * b2) * v1 + b2 * v2;
+                }
+                S2[e * NQ + r] = wl * rec[6] * mass;
                 continue;
             }
             if (AFFINE) {
@@ -481,7 +496,7 @@ __global__ void __launch_bounds__(256, (sf_min_blocks<SHAPE, P, T, TILE>())) sf_
             } else {
                 const T* gp = args.geom + eg * 7 * (int64_t)NQp + r;
                 wJ = gp[6 * NQp];
-                if (op == HP_LAPLACIAN || op == HP_HELMHOLTZ) {
+                if (op == HP_LAPLACIAN || op == HP_HELMHOLTZ || adr) {
 #pragma unroll
                     for (int f = 0; f < 6; ++f) G[f] = gp[f * NQp];
                 }
@@ -497,12 +512,19 @@ __global__ void __launch_bounds__(256, (sf_min_blocks<SHAPE, P, T, TILE>())) sf_
             T uval = u[0];
             if (op == HP_MASS || op == HP_IPRODUCT_WRT_BASE) {
                 S2[e * NQ + r] = wJ * uval;
-            } else if (op == HP_LAPLACIAN || op == HP_HELMHOLTZ) {
+            } else if (op == HP_LAPLACIAN || op == HP_HELMHOLTZ || adr) {
                 T v1 = u[NQ], v2 = u[2 * NQ], v3 = u[3 * NQ];
                 u[NQ] = G[0] * v1 + G[1] * v2 + G[2] * v3;
                 u[2 * NQ] = G[1] * v1 + G[3] * v2 + G[4] * v3;
                 u[3 * NQ] = G[2] * v1 + G[4] * v2 + G[5] * v3;
-                S2[e * NQ + r] = (op == HP_HELMHOLTZ) ? args.lambda * wJ * uval : T(0);
+                T mass = (op == HP_HELMHOLTZ || adr) ? args.lambda * uval : T(0);
+                if (adr) {   // a . grad u = sum_d c_d du / d eta_d, c_d = sum_i a_i d eta_d / d x_i
+                    const T c1 = Gx[0][0] * args.adv[0] + Gx[0][1] * args.adv[1] + Gx[0][2] * args.adv[2];
+                    const T c2 = Gx[1][0] * args.adv[0] + Gx[1][1] * args.adv[1] + Gx[1][2] * args.adv[2];
+                    const T c3 = Gx[2][0] * args.adv[0] + Gx[2][1] * args.adv[1] + Gx[2][2] * args.adv[2];
+                    mass += c1 * v1 + c2 * v2 + c3 * v3;
+                }
+                S2[e * NQ + r] = wJ * mass;
             } else if (op == HP_PHYSDERIV) {
                 T v1 = u[NQ], v2 = u[2 * NQ], v3 = u[3 * NQ];
                 const int64_t o = args.phys_off[eg] + r;
@@ -742,6 +764,18 @@ __global__ void __launch_bounds__(256, (sf_min_blocks<SHAPE, P, T, TILE>())) sf_
         }
         __syncthreads();
     }
+    return true;
+}
+
+// One launch per block: a persistent grid of CTAs over the block's element groups.
+template <int SHAPE, int P, typename T, bool AFFINE, int TILE>
+__global__ void __launch_bounds__(256, (sf_min_blocks<SHAPE, P, T, TILE>())) sf_kernel(const __grid_constant__ SFArgs<T> args) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    if (threadIdx.x == 0) mbar_init(reinterpret_cast<uint64_t*>(smem), 1);
+    __syncthreads();
+    uint32_t phase = 0;
+    const int64_t ngroups = (args.n_elem + SFCfg<P, T, TILE>::EPB - 1) / SFCfg<P, T, TILE>::EPB;
+    sf_groups<SHAPE, P, T, AFFINE, TILE>(args, smem, blockIdx.x, gridDim.x, ngroups, phase);
 }
 
 template <int SHAPE, int P, typename T, bool AFFINE, int TILE>

@@ -428,6 +428,8 @@ hp_status prepare(hp_c0 c, double lambda, int mixed, int schedule, cudaStream_t 
            : mixed == 2 ? hp_op_create(c->mesh, HP_HELMHOLTZ, HP_STRAT_ELEMAT, HP_TF32, &c->op32)
                         : hp_op_create(c->mesh, HP_HELMHOLTZ, HP_STRAT_SUMFAC, HP_FP32, &c->op32);
         if (st) return st;
+        // split tensor-core tiles summed in a fixed order: the solve is reproducible
+        if ((st = hp_op_set_deterministic(c->op32, 1))) return st;
         c->op32_mode = mixed;
     }
     if (!c->d_red) {

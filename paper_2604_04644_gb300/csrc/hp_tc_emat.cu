@@ -579,8 +579,10 @@ __global__ void __launch_bounds__(Epi<EW>::kThreads, Epi<EW>::kCtas) tc_emat_ker
                     for (int m = lane; m < CB; m += 32) {
                         if (cb + m >= a.NP) break;
                         const float val = stage[row * CB + (((m >> 2) ^ (row & 7)) << 2) + (m & 3)];
-                        if (a.nsplit > 1) atomicAdd(a.out + off + cb + m, val);
-                        else a.out[off + cb + m] = val;
+                        if (a.nsplit == 1) a.out[off + cb + m] = val;
+                        else if (a.part_out)   // fixed-order sum later: this part's own slot
+                            a.part_out[((w % a.nsplit) * a.n_elem + tile * 128 + row) * (int64_t)a.NP + cb + m] = val;
+                        else atomicAdd(a.out + off + cb + m, val);
                     }
                 }
                 if (!(ok = epi_sync())) break;
@@ -595,6 +597,17 @@ __global__ void __launch_bounds__(Epi<EW>::kThreads, Epi<EW>::kCtas) tc_emat_ker
     __syncthreads();
     tc::fence_after();
     if (warp == 0) tc::tmem_dealloc(tbase, E::kTmemCols);
+}
+
+// deterministic split-tile sum: out = part 0 + part 1 + ... in part order
+__global__ void sum_parts_kernel(float* out, const int64_t* coeff_off, const float* part_out, int64_t n_elem, int NP,
+                                 int nsplit) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n_elem * NP) return;
+    const int64_t e = i / NP;
+    float acc = part_out[i];
+    for (int p = 1; p < nsplit; ++p) acc += part_out[(int64_t)p * n_elem * NP + i];
+    out[coeff_off[e] + (i - e * NP)] = acc;
 }
 
 // zero the block's output coefficients (the parts of a tile add into them)
@@ -761,6 +774,21 @@ cudaError_t tc_geom_layout16(int shape, bool curved, const double* g, int NQp, c
     }
 }
 
+// point-chunk parts per tile: split until the grid covers the CTA slots (at
+// least 4 chunks per part); 0 on error
+int tc_emat_nsplit(const TCArgs& a) {
+    const int64_t ntiles = (a.n_elem + 127) / 128;
+    if (ntiles <= 0) return 1;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 0;
+    const TcPlan pl = tc_plan(a.KP, a.NPpad, a.stage_bytes, a.es, ntiles >= 2 * (int64_t)sms);
+    if (pl.stages == 0) return 0;
+    const int64_t ns = ((int64_t)sms * pl.ctas + ntiles - 1) / ntiles;
+    const int64_t cap = a.nch / 4 > 1 ? a.nch / 4 : 1;
+    return (int)(ns < cap ? ns : cap);
+}
+
 cudaError_t tc_emat_launch(const TCArgs& a, cudaStream_t s) {
     const int64_t ntiles = (a.n_elem + 127) / 128;
     if (ntiles <= 0) return cudaSuccess;
@@ -777,19 +805,22 @@ cudaError_t tc_emat_launch(const TCArgs& a, cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, pl.smem);
     if (e != cudaSuccess) return e;
     const int slots = sms * pl.ctas;
-    // split the point chunks of a tile over CTAs until the grid covers the
-    // CTA slots (at least 4 chunks per part)
-    int64_t ns = (slots + ntiles - 1) / ntiles;
-    const int64_t cap = a.nch / 4 > 1 ? a.nch / 4 : 1;
-    b.nsplit = (int)(ns < cap ? ns : cap);
-    if (b.nsplit > 1) {
-        const int64_t n = a.n_elem * a.NP;
+    b.nsplit = tc_emat_nsplit(a);
+    if (b.nsplit < 1) return cudaErrorInvalidValue;
+    const int64_t n = a.n_elem * a.NP;
+    if (b.nsplit == 1) b.part_out = nullptr;
+    if (b.nsplit > 1 && !b.part_out)   // atomics: the parts add into a zeroed output
         zero_coeffs_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a.out, a.coeff_off, a.n_elem, a.NP);
-    }
     const int64_t nwork = ntiles * b.nsplit;
     const int grid = (int)(nwork < slots ? nwork : slots);
     kern<<<grid, threads, pl.smem, s>>>(b);
-    return cudaGetLastError();
+    e = cudaGetLastError();
+    if (e == cudaSuccess && b.part_out) {
+        sum_parts_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a.out, a.coeff_off, b.part_out, a.n_elem, a.NP,
+                                                                    b.nsplit);
+        e = cudaGetLastError();
+    }
+    return e;
 }
 
 }  // namespace hp

@@ -24,14 +24,14 @@ HP_OK, HP_ERR_ARG, HP_ERR_OOM, HP_ERR_CUDA, HP_ERR_GEOM, HP_ERR_UNSUPPORTED, HP_
     HP_ERR_DEVICE_BOUNDS, HP_ERR_NOT_CONVERGED = range(9)
 HP_HEX, HP_PRISM, HP_PYR, HP_TET = range(4)
 HP_MASS, HP_LAPLACIAN, HP_HELMHOLTZ, HP_BWDTRANS, HP_IPRODUCT_WRT_BASE, HP_PHYSDERIV, \
-    HP_IPRODUCT_WRT_DERIV_BASE = range(7)
+    HP_IPRODUCT_WRT_DERIV_BASE, HP_ADVECTION_DIFFUSION_REACTION = range(8)
 HP_STRAT_SUMFAC, HP_STRAT_ELEMAT, HP_STRAT_HYBRID, HP_STRAT_AUTO = range(4)
 HP_STRAT_MATRIX = 4
 HP_FP64, HP_FP32, HP_TF32, HP_BF16 = range(4)
 
 EXPORTED = ["hp_mesh_create", "hp_mesh_layout", "hp_geom_factors", "hp_geom_copy", "hp_op_create",
             "hp_op_apply", "hp_op_apply_graph", "hp_op_tune", "hp_op_tiles", "hp_op_strategies",
-            "hp_op_set_collocated", "hp_op_block_features", "hp_op_schedule", "hp_op_schedule_mlp", "hp_op_schedule_exhaustive",
+            "hp_op_set_collocated", "hp_op_set_deterministic", "hp_op_set_advection", "hp_op_set_batching", "hp_op_block_features", "hp_op_schedule", "hp_op_schedule_mlp", "hp_op_schedule_exhaustive",
             "hp_op_schedule_graph", "hp_op_sync", "hp_op_work",
             "hp_op_block_work", "hp_op_apply_block", "hp_peak_fp64",
             "hp_op_destroy", "hp_mesh_destroy", "hp_status_str", "hp_last_error",
@@ -53,7 +53,8 @@ class HpError(RuntimeError):
 class hp_mesh_desc(ctypes.Structure):
     _fields_ = [("n_elem", ctypes.c_int64), ("shape", ctypes.c_void_p), ("P", ctypes.c_void_p),
                 ("Q", ctypes.c_void_p), ("vert", ctypes.c_void_p), ("xyz", ctypes.c_void_p),
-                ("n_vert", ctypes.c_int64), ("curved", ctypes.c_void_p), ("deformation", ctypes.c_int32)]
+                ("n_vert", ctypes.c_int64), ("curved", ctypes.c_void_p), ("deformation", ctypes.c_int32),
+                ("geometry", ctypes.c_int32)]
 
 
 _vp, _i64p, _dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)
@@ -68,6 +69,12 @@ _lib.hp_op_tune.argtypes = [_vp, ctypes.c_double, _vp, _vp, _vp]
 _lib.hp_op_tiles.argtypes = [_vp, _vp, ctypes.c_int64, ctypes.c_int]
 _lib.hp_op_strategies.argtypes = [_vp, _vp, ctypes.c_int64, ctypes.c_int]
 _lib.hp_op_set_collocated.argtypes = [_vp, ctypes.c_int]
+_lib.hp_op_set_deterministic.argtypes = [_vp, ctypes.c_int]
+_lib.hp_op_set_advection.argtypes = [_vp, _vp]
+_lib.hp_op_set_batching.argtypes = [_vp, ctypes.c_int]
+_lib.hp_op_set_batching.restype = ctypes.c_int
+_lib.hp_op_set_advection.restype = ctypes.c_int
+_lib.hp_op_set_deterministic.restype = ctypes.c_int
 _lib.hp_op_block_features.argtypes = [_vp, _vp, ctypes.c_int64]
 _lib.hp_op_schedule.argtypes = [_vp, _vp, _vp]
 _lib.hp_op_schedule_mlp.argtypes = [_vp, _vp, ctypes.c_int, _vp]
@@ -98,7 +105,7 @@ _lib.hp_status_str.restype = ctypes.c_char_p
 _lib.hp_last_error.restype = ctypes.c_char_p
 for _f in ("hp_mesh_create", "hp_mesh_layout", "hp_geom_factors", "hp_geom_copy", "hp_op_create",
            "hp_op_apply", "hp_op_apply_graph", "hp_op_tune", "hp_op_tiles", "hp_op_sync", "hp_op_work",
-           "hp_op_block_work", "hp_op_apply_block", "hp_op_strategies", "hp_op_set_collocated", "hp_op_block_features", "hp_op_schedule", "hp_op_schedule_exhaustive",
+           "hp_op_block_work", "hp_op_apply_block", "hp_op_strategies", "hp_op_set_collocated", "hp_op_set_deterministic", "hp_op_set_advection", "hp_op_set_batching", "hp_op_block_features", "hp_op_schedule", "hp_op_schedule_exhaustive",
            "hp_op_schedule_graph", "hp_mlp_create", "hp_mlp_info", "hp_mlp_params", "hp_mlp_forward", "hp_mlp_grad", "hp_mlp_adam_step"):
     getattr(_lib, _f).restype = ctypes.c_int
 
@@ -141,7 +148,8 @@ def hp_mesh_create(mesh, device=0):
     )
     d = hp_mesh_desc(int(mesh["n_elem"]), keep["shape"].ctypes.data, keep["P"].ctypes.data,
                      keep["Q"].ctypes.data, keep["vert"].ctypes.data, keep["xyz"].ctypes.data,
-                     int(keep["xyz"].shape[0]), keep["curved"].ctypes.data, int(mesh["deformation"]))
+                     int(keep["xyz"].shape[0]), keep["curved"].ctypes.data, int(mesh["deformation"]),
+                     int(mesh.get("geometry", 0)))
     h = _vp()
     _check(_lib.hp_mesh_create(ctypes.byref(d), int(device), ctypes.byref(h)), "hp_mesh_create")
     return h.value
@@ -190,6 +198,25 @@ def hp_op_tiles(op, n_blocks, tiles=None):
     arr = np.zeros(n_blocks, dtype=np.int32) if tiles is None else np.ascontiguousarray(tiles, dtype=np.int32)
     _check(_lib.hp_op_tiles(op, arr.ctypes.data, int(n_blocks), 0 if tiles is None else 1), "hp_op_tiles")
     return arr
+
+
+def hp_op_set_advection(op, velocity):
+    """Constant advection velocity (3 floats) of an HP_ADVECTION_DIFFUSION_REACTION op."""
+    v = np.ascontiguousarray(velocity, dtype=np.float64)
+    if v.shape != (3,):
+        raise ValueError("velocity must have 3 components")
+    _check(_lib.hp_op_set_advection(op, v.ctypes.data), "hp_op_set_advection")
+
+
+def hp_op_set_batching(op, mode):
+    """0: one kernel per block (graph of concurrent nodes); 1: one persistent work-list launch."""
+    _check(_lib.hp_op_set_batching(op, int(mode)), "hp_op_set_batching")
+
+
+def hp_op_set_deterministic(op, deterministic):
+    """Fixed-order (True) or atomic (False, the default) sum of the tensor-core
+    operators' split tiles."""
+    _check(_lib.hp_op_set_deterministic(op, 1 if deterministic else 0), "hp_op_set_deterministic")
 
 
 def hp_op_set_collocated(op, collocated):
@@ -370,7 +397,8 @@ def _desc(mesh):
                 curved=np.ascontiguousarray(mesh["curved"], dtype=np.uint8))
     d = hp_mesh_desc(int(mesh["n_elem"]), keep["shape"].ctypes.data, keep["P"].ctypes.data,
                      keep["Q"].ctypes.data, keep["vert"].ctypes.data, keep["xyz"].ctypes.data,
-                     int(keep["xyz"].shape[0]), keep["curved"].ctypes.data, int(mesh["deformation"]))
+                     int(keep["xyz"].shape[0]), keep["curved"].ctypes.data, int(mesh["deformation"]),
+                     int(mesh.get("geometry", 0)))
     return d, keep
 
 

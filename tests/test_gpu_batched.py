@@ -87,3 +87,45 @@ def test_tiles_argument_checks(hp, padaptive):
         hp.hp_op_destroy(op)
     finally:
         hp.hp_mesh_destroy(h)
+
+
+@pytest.mark.parametrize("kind", ["helmholtz", "laplacian", "mass"])
+def test_persistent_worklist_is_bitwise_the_per_block_launch(hp, padaptive, kind):
+    """hp_op_set_batching(op, 1): one persistent work-list launch over all the
+    p-adaptive mesh's blocks (plain and graph-captured) gives the bits of the
+    per-block launches (the same body per element), and matches the oracle;
+    switching a block to another strategy returns the op to per-block launches."""
+    kinds = {"helmholtz": hp.HP_HELMHOLTZ, "laplacian": hp.HP_LAPLACIAN, "mass": hp.HP_MASS}
+    mesh = padaptive
+    nb = n_blocks(mesh)
+    h = hp.hp_mesh_create(mesh, 0)
+    try:
+        co, po, nc, nph = hp.hp_mesh_layout(h, mesh["n_elem"])
+        uh = inputs.random_coefficients(37, co)
+        op = hp.hp_op_create(h, kinds[kind])
+        x = torch.tensor(uh, device="cuda:0")
+        y0 = torch.full((nc,), np.nan, device="cuda:0", dtype=torch.float64)
+        hp.hp_op_apply(op, 1.4, x, y0)
+        hp.hp_op_set_batching(op, 1)
+        y1 = torch.full_like(y0, np.nan)
+        hp.hp_op_apply(op, 1.4, x, y1)
+        y2 = torch.full_like(y0, np.nan)
+        for _ in range(3):
+            hp.hp_op_apply_graph(op, 1.4, x, y2)
+        hp.hp_op_sync(op)
+        assert torch.equal(y0, y1) and torch.equal(y0, y2)
+        ref = oracle_ops.apply(kind, mesh, uh, 1.4)
+        assert np.abs(y1.cpu().numpy() - ref).max() <= 1e-12 * np.abs(ref).max()
+        hp.hp_op_strategies(op, nb, np.full(nb, hp.HP_STRAT_HYBRID))
+        y3 = torch.full_like(y0, np.nan)
+        hp.hp_op_apply(op, 1.4, x, y3)           # per-block launches again (hybrid blocks)
+        hp.hp_op_sync(op)
+        assert np.abs(y3.cpu().numpy() - ref).max() <= 1e-12 * np.abs(ref).max()
+        hp.hp_op_destroy(op)
+        op32 = hp.hp_op_create(h, hp.HP_HELMHOLTZ, hp.HP_STRAT_SUMFAC, hp.HP_FP32)
+        with pytest.raises(hp.HpError) as ei:
+            hp.hp_op_set_batching(op32, 1)
+        assert ei.value.status == hp.HP_ERR_UNSUPPORTED
+        hp.hp_op_destroy(op32)
+    finally:
+        hp.hp_mesh_destroy(h)

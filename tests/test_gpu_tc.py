@@ -92,6 +92,13 @@ def test_tensor_core_matches_oracle(hp, P, opname, prec):
     for s, err in errs.items():
         tol = (TF32_TOL if prec == "tf32" else BF16_TOL) if n_modes(s, P) <= MAX_TC_MODES else fp32_tol(P)
         assert err <= tol, (s, err, tol)
+    # per output: the first-order rounding bound of the form each block runs
+    from tests import roundoff
+    tc = roundoff.tc_bound(mesh, x32, 1.3, opname, TF32_U if prec == "tf32" else BF16_U)
+    sf = roundoff.sf32_bound(mesh, x32, 1.3, opname)
+    fits = np.repeat([n_modes(int(s), P) <= MAX_TC_MODES for s in mesh["shape"]], np.diff(co))
+    bound = np.where(fits, tc, sf)
+    assert (np.abs(y - ref) <= bound).all(), np.max(np.abs(y - ref) / bound)
 
 
 def test_tf32_strategy_per_block(hp):
@@ -185,3 +192,39 @@ def test_tensor_core_small_elements(hp, prec, opname, lam):
     y, _ = run_tc(hp, mesh, opname, x, lam, hp.HP_TF32 if prec == "tf32" else hp.HP_BF16)
     assert not np.isnan(y).any()
     assert rel_err(y, ref) <= (TF32_TOL if prec == "tf32" else BF16_TOL)
+
+
+@pytest.mark.parametrize("dt", ["tf32", "bf16"])
+def test_deterministic_split_tiles_are_bitwise_reproducible(hp, dt):
+    """Small blocks split their tiles' point chunks over CTAs.  With
+    hp_op_set_deterministic the parts are summed in part order: repeated
+    applies (plain and graph) give the same bits, and the result matches the
+    atomic form to FP32 rounding and the oracle within the form's bound."""
+    mesh = inputs.slab_mesh(2, 2, 4, (2, 4), order_seed=3, curved_rule="x_half")
+    co, po = oracle_ops.layout(mesh)
+    uh = inputs.random_coefficients(71, co)
+    dtype = {"tf32": hp.HP_TF32, "bf16": hp.HP_BF16}[dt]
+    h = hp.hp_mesh_create(mesh, 0)
+    try:
+        op = hp.hp_op_create(h, hp.HP_HELMHOLTZ, hp.HP_STRAT_ELEMAT, dtype)
+        x = torch.tensor(uh, device="cuda:0", dtype=torch.float32)
+        ys = []
+        hp.hp_op_set_deterministic(op, True)
+        for graph in (False, False, True, True):
+            y = torch.full((len(uh),), float("nan"), device="cuda:0", dtype=torch.float32)
+            (hp.hp_op_apply_graph if graph else hp.hp_op_apply)(op, 1.0, x, y)
+            hp.hp_op_sync(op)
+            ys.append(y.cpu().numpy())
+        hp.hp_op_set_deterministic(op, False)
+        ya = torch.zeros(len(uh), device="cuda:0", dtype=torch.float32)
+        hp.hp_op_apply(op, 1.0, x, ya)
+        hp.hp_op_sync(op)
+        hp.hp_op_destroy(op)
+    finally:
+        hp.hp_mesh_destroy(h)
+    for y in ys[1:]:
+        assert np.array_equal(y.view(np.int32), ys[0].view(np.int32))
+    ref = oracle_ops.apply("helmholtz", mesh, uh.astype(np.float32).astype(np.float64), 1.0)
+    tol = TF32_TOL if dt == "tf32" else BF16_TOL
+    assert rel_err(ys[0].astype(np.float64), ref) <= tol
+    assert np.abs(ys[0] - ya.cpu().numpy()).max() <= 1e-5 * np.abs(ref).max()
