@@ -66,6 +66,9 @@ PROFILE_CASES = {
     "tc16_hex4": (0, 4, 65536, "ELEMAT", "BF16"),
     "sf32_hex4": (0, 4, 65536, "SUMFAC", "FP32"),
     "sf32_tet4": (3, 4, 65536, "SUMFAC", "FP32"),
+    # shape -1: the bench mesh itself (16^3 mixed curved cells) at order P
+    "mesh16_bf16_P8": (-1, 8, 0, "ELEMAT", "BF16"),
+    "mesh16_bf16_P4": (-1, 4, 0, "ELEMAT", "BF16"),
 }
 
 
@@ -1031,12 +1034,16 @@ def run_matrix_study(local, reps=10):
 
 
 def run_profile_case(name, local):
-    """One block of curved elements, three Helmholtz applies (the capture takes one)."""
+    """One block of curved elements (or the bench mesh at one order), three
+    Helmholtz applies (the capture takes one)."""
     import torch
     from paper_2604_04644_gb300 import hp, inputs
     torch.cuda.set_device(local)
     shape, P, n, strat, dt = PROFILE_CASES[name]
-    mesh = inputs.replicated_mesh(shape, P, n, curved=True)
+    if shape < 0:
+        mesh = inputs.slab_mesh(CELLS, CELLS, CELLS, P, curved=True)
+    else:
+        mesh = inputs.replicated_mesh(shape, P, n, curved=True)
     h = hp.hp_mesh_create(mesh, local)
     co, po, nc, nph = hp.hp_mesh_layout(h, mesh["n_elem"])
     x = torch.tensor(inputs.random_coefficients(5, co), device="cuda:%d" % local, dtype=torch.float32)

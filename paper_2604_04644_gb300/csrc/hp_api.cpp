@@ -69,6 +69,8 @@ void free_block(Block& b) {
     cudaFree(b.d_dgeom32);
     cudaFree(b.d_geom_tc);
     cudaFree(b.d_gscale_tc);
+    cudaFree(b.d_geom_pts);
+    b.d_geom_pts = nullptr;
     b.d_geom_tc = nullptr;
     b.d_gscale_tc = nullptr;
     b.d_coeff_off = b.d_phys_off = nullptr;
@@ -171,6 +173,27 @@ hp_status ensure_geom(hp_mesh m, bool deriv, bool f32, cudaStream_t s) {
         cudaError_t e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return cuda_fail(e, "fp32 geometry");
         m->geom32_ready = true;
+    }
+    return HP_OK;
+}
+
+// Affine blocks of FP64 collocated Laplacian / Helmholtz operators read
+// per-point factors expanded from their records (like curved blocks): on
+// GB300 the FP64 pipe is the limit and HBM has bandwidth to spare, so
+// loading G costs less than rebuilding T K T^T at every point.
+bool affine_expanded(const hp_op_s* op, const Block& b) {
+    return !b.curved && b.d_geom_pts && op->dtype == HP_FP64 && op->collocated &&
+           (op->kind == HP_LAPLACIAN || op->kind == HP_HELMHOLTZ);
+}
+
+hp_status ensure_affine_points(hp_mesh m, cudaStream_t s) {
+    for (Block& b : m->blocks) {
+        if (b.curved || b.d_geom_pts || b.n_elem == 0) continue;
+        hp_status st = upload<double>(&b.d_geom_pts, nullptr, (size_t)b.n_elem * 7 * nqp(b.Q));
+        if (st) return st;
+        cudaError_t e = launch_affine_points(b, m->blobs.at(b.shape * 16 + b.P), b.d_geom_pts, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(e, "affine point factors");
     }
     return HP_OK;
 }
@@ -579,7 +602,7 @@ std::vector<SFDesc> worklist_descs(hp_op op, double lambda, const void* in, void
         a.in = static_cast<const double*>(in);
         a.out = static_cast<double*>(out);
         a.n_phys_total = m->phys_off.back();
-        a.geom = b.d_geom;
+        a.geom = affine_expanded(op, b) ? b.d_geom_pts : b.d_geom;
         a.dgeom = b.d_dgeom;
         a.blob = static_cast<const unsigned char*>(blob.d64);
         a.blob_bytes = blob.bytes64;
@@ -680,7 +703,8 @@ cudaError_t launch_block(hp_op op, size_t bi, int tile, double lambda, const voi
         a.in = static_cast<const double*>(in);
         a.out = static_cast<double*>(out);
         a.n_phys_total = nphys;
-        a.geom = b.d_geom;
+        const bool expanded = affine_expanded(op, b);
+        a.geom = expanded ? b.d_geom_pts : b.d_geom;
         a.dgeom = b.d_dgeom;
         a.blob = static_cast<const unsigned char*>(blob.d64);
         a.blob_bytes = blob.bytes64;
@@ -689,7 +713,7 @@ cudaError_t launch_block(hp_op op, size_t bi, int tile, double lambda, const voi
         fill_const_tables(b, a);
         if (!op->collocated && (op->kind == HP_LAPLACIAN || op->kind == HP_HELMHOLTZ))
             return sf_nc_launch(b.shape, b.P, !b.curved, a, blob.d_nc64, s);
-        return sf_launch_f64(b.shape, b.P, !b.curved, tile, a, s);
+        return sf_launch_f64(b.shape, b.P, !b.curved && !expanded, tile, a, s);
     }
     SFArgs<float> a{};
     a.op = op->kind;
@@ -982,6 +1006,7 @@ hp_status hp_op_create(hp_mesh m, hp_opkind kind, hp_strategy strategy, hp_dtype
     DeviceGuard guard(m->device);
     hp_status st = ensure_geom(m, needs_deriv_geom(kind), dtype != HP_FP64, 0);
     if (st) return st;
+    if (dtype == HP_FP64 && (kind == HP_LAPLACIAN || kind == HP_HELMHOLTZ) && (st = ensure_affine_points(m, 0))) return st;
     if (tcore) {
         if ((st = ensure_tc(m, dtype == HP_BF16 ? 2 : 4))) return st;
     } else if ((strategy == HP_STRAT_ELEMAT || strategy == HP_STRAT_HYBRID) && (st = ensure_dense(m))) {
@@ -1066,7 +1091,7 @@ hp_status hp_op_set_batching(hp_op op, int mode) {
         for (int64_t g = 0; g < ng[i]; g += per) {
             WorkItem w;
             w.block = (int32_t)i;
-            w.key = b.shape * 32 + b.P * 2 + (b.curved ? 0 : 1);
+            w.key = b.shape * 32 + b.P * 2 + ((b.curved || affine_expanded(op, b)) ? 0 : 1);
             w.g0 = g;
             w.g1 = std::min(ng[i], g + per);
             items.push_back(w);
@@ -1581,7 +1606,7 @@ hp_status hp_op_block_work(hp_op op, int64_t block, int64_t* n_elem, int64_t* ou
         double geo = 0;
         switch (op->kind) {
             case HP_LAPLACIAN:
-            case HP_HELMHOLTZ: geo = b.curved ? 7 * NQ : 7; break;
+            case HP_HELMHOLTZ: geo = (b.curved || (st == HP_STRAT_SUMFAC && affine_expanded(op, b))) ? 7 * NQ : 7; break;
             case HP_MASS:
             case HP_IPRODUCT_WRT_BASE: geo = b.curved ? NQ : 1; break;
             case HP_PHYSDERIV: geo = b.curved ? 9 * NQ : 9; break;

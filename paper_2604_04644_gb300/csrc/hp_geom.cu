@@ -248,6 +248,39 @@ __global__ void geom_affine_kernel(int64_t n_elem, const double* __restrict__ fr
         for (int c = 0; c < 3; ++c) o[7 + 3 * a + c] = Ji[a][c];
 }
 
+// Per-point factors of affine elements, expanded once from their records
+// (K = |J| J^{-1} J^{-T}, |J|): G_dd' = wl (T K T^T)_dd' and wl |J|, the
+// layout of the curved factors [elem][7][NQp].  The FP64 operators read
+// these instead of rebuilding T K T^T at every point of every apply.
+template <int SHAPE>
+__global__ void affine_points_kernel(int Q, int NQp, int64_t n_elem, const double* __restrict__ rec,
+                                     const double* __restrict__ z, const double* __restrict__ w,
+                                     double* __restrict__ out) {
+    const int NQ = Q * Q * Q;
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= n_elem * NQ) return;
+    const int64_t e = idx / NQ;
+    const int l = (int)(idx % NQ);
+    const int i = l / (Q * Q), j = (l / Q) % Q, k = l % Q;
+    double T[3][3];
+    deta_dxi<SHAPE, double>(z[i], z[Q + j], z[2 * Q + k], T);
+    const double* r = rec + e * 16;
+    const double K[3][3] = {{r[0], r[1], r[2]}, {r[1], r[3], r[4]}, {r[2], r[4], r[5]}};
+    const double wl = w[i] * w[Q + j] * w[2 * Q + k];
+    double M[3][3];
+    for (int d = 0; d < 3; ++d)
+        for (int b = 0; b < 3; ++b) M[d][b] = T[d][0] * K[0][b] + T[d][1] * K[1][b] + T[d][2] * K[2][b];
+    auto g = [&](int d, int d2) { return wl * (M[d][0] * T[d2][0] + M[d][1] * T[d2][1] + M[d][2] * T[d2][2]); };
+    double* o = out + e * 7 * (int64_t)NQp + l;
+    o[0 * NQp] = g(0, 0);
+    o[1 * NQp] = g(0, 1);
+    o[2 * NQp] = g(0, 2);
+    o[3 * NQp] = g(1, 1);
+    o[4 * NQp] = g(1, 2);
+    o[5 * NQp] = g(2, 2);
+    o[6 * NQp] = wl * r[6];
+}
+
 template <int SHAPE>
 __global__ void points_kernel(int Q, int64_t n_elem, const double* __restrict__ frame, const int64_t* __restrict__ phys_off,
                               const double* __restrict__ z, int kind, int curved, double* __restrict__ xyz, int64_t n_phys) {
@@ -336,6 +369,22 @@ cudaError_t launch_geom_iso(const Block& b, const DeviceBlobs& blob, int deforma
         case HP_PYR: return run(geom_iso_kernel<HP_PYR>);
         default: return run(geom_iso_kernel<HP_TET>);
     }
+}
+
+cudaError_t launch_affine_points(const Block& b, const DeviceBlobs& blob, double* out, cudaStream_t s) {
+    if (b.n_elem == 0) return cudaSuccess;
+    const BlobLayout L = blob_layout_c(b.shape, b.P, 8);
+    const double* vals = reinterpret_cast<const double*>(blob.d64);
+    const int NQ = b.Q * b.Q * b.Q, nt = 128;
+    const unsigned nb = (unsigned)((b.n_elem * NQ + nt - 1) / nt);
+    const int NQp = nqp(b.Q);
+    switch (b.shape) {
+        case HP_HEX: affine_points_kernel<HP_HEX><<<nb, nt, 0, s>>>(b.Q, NQp, b.n_elem, b.d_geom, vals + L.z, vals + L.w, out); break;
+        case HP_PRISM: affine_points_kernel<HP_PRISM><<<nb, nt, 0, s>>>(b.Q, NQp, b.n_elem, b.d_geom, vals + L.z, vals + L.w, out); break;
+        case HP_PYR: affine_points_kernel<HP_PYR><<<nb, nt, 0, s>>>(b.Q, NQp, b.n_elem, b.d_geom, vals + L.z, vals + L.w, out); break;
+        default: affine_points_kernel<HP_TET><<<nb, nt, 0, s>>>(b.Q, NQp, b.n_elem, b.d_geom, vals + L.z, vals + L.w, out);
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_points(const Block& b, const DeviceBlobs& blob, int deformation, double* xyz,

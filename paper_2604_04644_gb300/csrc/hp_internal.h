@@ -63,6 +63,8 @@ struct Block {
     double* d_dgeom = nullptr;            // curved only: [n_elem][9][NQp] d eta_d / d x_i
     float* d_geom32 = nullptr;            // FP32 copies (created on demand)
     float* d_dgeom32 = nullptr;
+    double* d_geom_pts = nullptr;         // affine only: per-point factors [n_elem][7][NQp] (FP64 Laplacian /
+                                          // Helmholtz read these like curved factors)
     uint16_t* d_geom_tc = nullptr;        // tensor-core operator: tile-major FP16 factors (curved and affine)
     float* d_gscale_tc = nullptr;         // and their per-element scales (Laplacian factors, w|J|)
     int64_t coeff_total = 0, phys_total = 0;   // per-block totals (work accounting)
@@ -154,6 +156,8 @@ constexpr unsigned int DERR_GEOM = 4u;
 // launch of the geometry kernel over one block (hp_geom.cu)
 cudaError_t launch_geom(const Block& b, const DeviceBlobs& blob, int deformation, bool want_deriv,
                         unsigned int* d_err, int* d_bad_elem, cudaStream_t s);
+// per-point factors of an affine block, expanded from its records (FP64, curved layout)
+cudaError_t launch_affine_points(const Block& b, const DeviceBlobs& blob, double* out, cudaStream_t s);
 // iso-parametric geometric factors of a curved block (needs blob.iso_RT and blob.iso_VT)
 cudaError_t launch_geom_iso(const Block& b, const DeviceBlobs& blob, int deformation, bool want_deriv,
                             unsigned int* d_err, int* d_bad_elem, cudaStream_t s);

@@ -23,7 +23,7 @@ __device__ __noinline__ bool wl_body(const SFDesc& a, unsigned char* smem, int64
     return ok;
 }
 
-__global__ void __launch_bounds__(256) sf_worklist_kernel(const SFDesc* __restrict__ desc,
+__global__ void __launch_bounds__(256, 3) sf_worklist_kernel(const SFDesc* __restrict__ desc,
                                                           const WorkItem* __restrict__ items, int n_items,
                                                           int* __restrict__ next, unsigned int* err) {
     extern __shared__ __align__(16) unsigned char smem[];
