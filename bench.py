@@ -55,7 +55,9 @@ N_MODES = (lambda P: (P + 1) ** 3, lambda P: (P + 1) ** 2 * (P + 2) // 2,
 # DRAM bytes (read + write) of one launch, measured by ncu on this workload
 # for the kernel named; a kernel whose code changed after the measurement is
 # left out (its traffic reads null)
-MEASURED_TRAFFIC = {"sf_kernel<pyr,P8,f64>": 372166400}
+MEASURED_TRAFFIC = {"sf_kernel<pyr,P8,f64>": 371767040,           # profiles/sf_kernel_pyr_P8_fp64.md
+                    "tc_emat_kernel<tet,P8,bf16>": 99799040,      # profiles/tc_emat_kernel_tet_P8_bf16_mixed16.md
+                    "sf_kernel<pyr,P8,f32>": 185675520}          # profiles/sf_kernel_pyr_P8_fp32_mixed16.md
 
 
 # small, fixed cases for ncu captures (a few hundred MB on the device):
