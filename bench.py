@@ -882,13 +882,14 @@ def run_solve(local, cells, order=4, lam=1.0, tol=1e-10, scheduled=False):
 
 # large single-shape blocks of the per-block precision table: (shape, P, elements)
 BLOCK_TABLE = [(3, 2, 65536), (3, 4, 65536), (3, 6, 32768), (3, 8, 32768), (2, 4, 65536), (2, 6, 32768),
-               (1, 4, 65536), (0, 4, 65536), (0, 5, 32768)]
+               (1, 4, 65536), (0, 4, 65536), (0, 5, 32768), (0, 6, 16384), (0, 7, 16384)]
 
 
 def run_block_table(local, reps=10):
-    """Helmholtz GDOF/s of FP32 sum factorisation and the TF32 / BF16 tensor-core
-    operator on large single-shape blocks, curved and affine (L2 flushed before
-    every apply; median of `reps`), one JSON line per block."""
+    """Helmholtz GDOF/s of FP32 sum factorisation and of the TF32 / BF16
+    tensor-core elemental matrix and hybrid on large single-shape blocks,
+    curved and affine (L2 flushed before every apply; median of `reps`), one
+    JSON line per block; null where the form is not built for the block."""
     import torch
     from paper_2604_04644_gb300 import hp, inputs
     torch.cuda.set_device(local)
@@ -904,8 +905,14 @@ def run_block_table(local, reps=10):
             line = {"shape": SHAPES[shape], "P": P, "curved": curved, "elements": n}
             for name, strat, dt in (("fp32_sumfac", hp.HP_STRAT_SUMFAC, hp.HP_FP32),
                                     ("tf32_tensor_core", hp.HP_STRAT_ELEMAT, hp.HP_TF32),
-                                    ("bf16_tensor_core", hp.HP_STRAT_ELEMAT, hp.HP_BF16)):
+                                    ("bf16_tensor_core", hp.HP_STRAT_ELEMAT, hp.HP_BF16),
+                                    ("tf32_tc_hybrid", hp.HP_STRAT_HYBRID, hp.HP_TF32),
+                                    ("bf16_tc_hybrid", hp.HP_STRAT_HYBRID, hp.HP_BF16)):
                 op = hp.hp_op_create(h, hp.HP_HELMHOLTZ, strat, dt)
+                if int(hp.hp_op_strategies(op, 1)[0]) != strat:    # not built for this block
+                    hp.hp_op_destroy(op)
+                    line[name] = None
+                    continue
                 for _ in range(3):
                     hp.hp_op_apply(op, 1.0, x, y)
                 ts = []

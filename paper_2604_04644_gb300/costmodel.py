@@ -16,7 +16,8 @@ run one after another (hp_op_apply), 1 when they run as the concurrent graph
 of hp_op_apply_graph.
 Outputs (4): log10 ms of sum factorisation, elemental matrix, hybrid and
 stored per-element matrices.  For a TF32 / BF16 operator output 0 is its FP32
-sum factorisation and output 1 its tensor-core elemental matrix.  A strategy
+sum factorisation, output 1 its tensor-core elemental matrix and output 2 its
+tensor-core hybrid.  A strategy
 that is not built for a block gets the target 10x its sum-factorised time;
 the schedulers never choose it.
 
@@ -50,7 +51,7 @@ def _built(dtype, kind, shape, P, k):
     """Strategy column k is built for a block of (shape, P) of this operator."""
     npm = n_modes(shape, P)
     if dtype in _TC:
-        return k == 0 or (k == 1 and npm <= 256)
+        return k == 0 or (k == 1 and npm <= 256) or (k == 2 and npm <= (512 if dtype == hp.HP_BF16 else 384))
     if k == 3:
         return kind in (hp.HP_MASS, hp.HP_LAPLACIAN, hp.HP_HELMHOLTZ) and npm <= 256
     return True

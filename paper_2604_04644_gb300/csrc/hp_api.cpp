@@ -337,7 +337,7 @@ hp_status ensure_tc(hp_mesh m, int es) {
         DeviceBlobs& db = kv.second;
         const int shape = kv.first / 16, P = kv.first % 16;
         const int Q = P + 2, NQ = Q * Q * Q, NP = n_modes(shape, P), NPT = tc_chunk_points();
-        if (NP > kTcMaxModes) continue;
+        if (NP > (es == 2 ? kTcHybMaxModes : kTcHybMaxModesTF32)) continue;   // the hybrid's limit (>= the elemental matrix's)
         const int KR = 128 / es, vrow = NPT * es;
         const int KP = (NP + KR - 1) / KR * KR, NPpad = (NP + 15) & ~15, nch = (NQ + NPT - 1) / NPT;
         const int slice = 4 * NPT * 128;                       // 64 rows x 128 bytes
@@ -401,17 +401,23 @@ hp_status ensure_tc(hp_mesh m, int es) {
 }
 
 bool tc_fits(const Block& b) { return n_modes(b.shape, b.P) <= kTcMaxModes; }
+bool tc_hyb_fits(const Block& b, hp_dtype dt) {
+    return n_modes(b.shape, b.P) <= (dt == HP_BF16 ? kTcHybMaxModes : kTcHybMaxModesTF32);
+}
+bool tc_strategy_fits(const Block& b, hp_dtype dt, int k) {
+    return (k == HP_STRAT_ELEMAT && tc_fits(b)) || (k == HP_STRAT_HYBRID && tc_hyb_fits(b, dt));
+}
 bool mat_fits(const Block& b) { return n_modes(b.shape, b.P) <= kMatMaxModes; }
 
 // strategy k (HP_STRAT_SUMFAC / ELEMAT / HYBRID / MATRIX) is built for block i
 // of op: derivative building blocks are sum-factorised only; a TF32 / BF16
-// operator has FP32 sum factorisation and the tensor-core elemental matrix
-// (N_P <= 256); stored matrices are mass, Laplacian or Helmholtz in FP64 /
-// FP32 (N_P <= 256)
+// operator has FP32 sum factorisation, the tensor-core elemental matrix
+// (N_P <= 256) and the tensor-core hybrid (N_P <= 512 BF16, 384 TF32); stored
+// matrices are mass, Laplacian or Helmholtz in FP64 / FP32 (N_P <= 256)
 bool strategy_available(const hp_op_s* op, size_t i, int k) {
     if (k == HP_STRAT_SUMFAC) return true;
     if (needs_deriv_geom(op->kind)) return false;
-    if (op->dtype == HP_TF32 || op->dtype == HP_BF16) return k == HP_STRAT_ELEMAT && tc_fits(op->mesh->blocks[i]);
+    if (op->dtype == HP_TF32 || op->dtype == HP_BF16) return tc_strategy_fits(op->mesh->blocks[i], op->dtype, k);
     if (k == HP_STRAT_MATRIX)
         return (op->kind == HP_MASS || op->kind == HP_LAPLACIAN || op->kind == HP_HELMHOLTZ) &&
                mat_fits(op->mesh->blocks[i]);
@@ -671,6 +677,44 @@ cudaError_t launch_block(hp_op op, size_t bi, int tile, double lambda, const voi
             a.part_out = need > 0 ? op->part_buf[bi] : nullptr;
         }
         return tc_emat_launch(a, s);
+    }
+    if ((op->dtype == HP_TF32 || op->dtype == HP_BF16) && op->strat[bi] == HP_STRAT_HYBRID) {
+        // u = B uhat (tensor cores) -> u' = point-space core (FP32 CUDA cores) -> out = B^T u' (tensor cores)
+        if (!op->hyb_u) {
+            const size_t n = sizeof(float) * (size_t)std::max<int64_t>(nphys, 1);
+            cudaError_t e = cudaMalloc(&op->hyb_u, n);
+            if (e == cudaSuccess) e = cudaMalloc(&op->hyb_v, n);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                cudaFree(op->hyb_u);
+                op->hyb_u = op->hyb_v = nullptr;
+                return e;
+            }
+        }
+        const bool bf = op->dtype == HP_BF16;
+        HybArgs h{};
+        h.NQ = b.Q * b.Q * b.Q; h.NP = n_modes(b.shape, b.P);
+        h.KP = bf ? blob.tc_KP16 : blob.tc_KP; h.NPpad = blob.tc_NPpad; h.nch = blob.tc_nch; h.es = bf ? 2 : 4;
+        h.n_elem = b.n_elem; h.coeff_off = b.d_coeff_off; h.phys_off = b.d_phys_off;
+        h.img = bf ? blob.tc_img16 : blob.tc_img;
+        h.chunk_bytes = bf ? blob.tc_chunk16 : blob.tc_chunk;
+        h.fwd_bytes = bf ? blob.tc_fwd16 : blob.tc_fwd;
+        h.bwd_bytes = bf ? blob.tc_bwd16 : blob.tc_bwd;
+        h.err = op->d_err;
+        h.in = static_cast<const float*>(in); h.out = op->hyb_u;
+        cudaError_t e = tc_hyb_launch(h, 0, s);
+        if (e != cudaSuccess) return e;
+        EMArgs<float> c{};
+        c.op = op->kind; c.shape = b.shape; c.P = b.P; c.Q = b.Q; c.NQ = h.NQ;
+        c.NP = h.NP; c.NQp = nqp(b.Q); c.n_elem = b.n_elem; c.lambda = (float)lambda;
+        c.coeff_off = b.d_coeff_off; c.phys_off = b.d_phys_off;
+        c.in = op->hyb_u; c.out = op->hyb_v;
+        c.geom = b.d_geom32; c.blob = static_cast<const unsigned char*>(blob.d32); c.err = op->d_err;
+        c.point_space = 1;
+        e = emat_launch_f32(true, !b.curved, c, s);
+        if (e != cudaSuccess) return e;
+        h.in = op->hyb_v; h.out = static_cast<float*>(out);
+        return tc_hyb_launch(h, 1, s);
     }
     if (op->strat[bi] != HP_STRAT_SUMFAC) {
         const bool hybrid = op->strat[bi] == HP_STRAT_HYBRID;
@@ -989,9 +1033,10 @@ hp_status hp_op_create(hp_mesh m, hp_opkind kind, hp_strategy strategy, hp_dtype
     if ((int)dtype < 0 || dtype > HP_BF16) { set_error("hp_op_create: bad dtype"); return HP_ERR_ARG; }
     const bool tcore = dtype == HP_TF32 || dtype == HP_BF16;
     if (strategy == HP_STRAT_AUTO) strategy = tcore ? HP_STRAT_ELEMAT : HP_STRAT_SUMFAC;
-    if (tcore && (strategy != HP_STRAT_ELEMAT ||
-                             (kind != HP_MASS && kind != HP_LAPLACIAN && kind != HP_HELMHOLTZ))) {
-        set_error("hp_op_create: HP_TF32 / HP_BF16 are the tensor-core elemental-matrix form of mass, Laplacian and Helmholtz");
+    if (tcore && ((strategy != HP_STRAT_ELEMAT && strategy != HP_STRAT_HYBRID) ||
+                  (kind != HP_MASS && kind != HP_LAPLACIAN && kind != HP_HELMHOLTZ))) {
+        set_error("hp_op_create: HP_TF32 / HP_BF16 are the tensor-core elemental-matrix and hybrid forms of mass, "
+                  "Laplacian and Helmholtz");
         return HP_ERR_UNSUPPORTED;
     }
     if (strategy != HP_STRAT_SUMFAC && needs_deriv_geom(kind)) {
@@ -1019,9 +1064,9 @@ hp_status hp_op_create(hp_mesh m, hp_opkind kind, hp_strategy strategy, hp_dtype
     op->dtype = dtype;
     op->tile.assign(m->blocks.size(), 0);
     op->strat.assign(m->blocks.size(), (int)strategy);
-    if (tcore)   // blocks beyond the tensor-memory budget run FP32 sum factorisation
+    if (tcore)   // blocks beyond the form's tensor-memory / shared-memory budget run FP32 sum factorisation
         for (size_t i = 0; i < m->blocks.size(); ++i)
-            if (!tc_fits(m->blocks[i])) op->strat[i] = HP_STRAT_SUMFAC;
+            if (!tc_strategy_fits(m->blocks[i], dtype, strategy)) op->strat[i] = HP_STRAT_SUMFAC;
     if (strategy == HP_STRAT_MATRIX)   // blocks beyond the stored-matrix size run sum factorisation
         for (size_t i = 0; i < m->blocks.size(); ++i)
             if (!mat_fits(m->blocks[i])) op->strat[i] = HP_STRAT_SUMFAC;
@@ -1335,8 +1380,9 @@ hp_status hp_op_strategies(hp_op op, int* strat, int64_t n_blocks, int set) {
             return HP_ERR_UNSUPPORTED;
         }
         if ((op->dtype == HP_TF32 || op->dtype == HP_BF16) && strat[i] != HP_STRAT_SUMFAC &&
-            (strat[i] != HP_STRAT_ELEMAT || !tc_fits(op->mesh->blocks[i]))) {
-            set_error("hp_op_strategies: HP_TF32 / HP_BF16 blocks are tensor-core elemental-matrix (N_P <= 256) or FP32 sum factorisation");
+            !tc_strategy_fits(op->mesh->blocks[i], op->dtype, strat[i])) {
+            set_error("hp_op_strategies: HP_TF32 / HP_BF16 blocks are tensor-core elemental-matrix (N_P <= 256), "
+                      "tensor-core hybrid (N_P <= 512 BF16, 384 TF32) or FP32 sum factorisation");
             return HP_ERR_UNSUPPORTED;
         }
         dense |= (strat[i] == HP_STRAT_ELEMAT || strat[i] == HP_STRAT_HYBRID) && op->dtype != HP_TF32 &&
@@ -1620,6 +1666,10 @@ hp_status hp_op_block_work(hp_op op, int64_t block, int64_t* n_elem, int64_t* ou
             // tensor-core form: FP16 factors at every point (affine ones expanded),
             // w|J| only for mass, and the element's two FP32 scales
             geo_bytes = (op->kind == HP_MASS ? 1.0 : 7.0) * NQ * 2.0 + 8.0;
+        if ((op->dtype == HP_TF32 || op->dtype == HP_BF16) && st == HP_STRAT_HYBRID)
+            // tensor-core hybrid: FP32 factors, and the point vectors u and u'
+            // between its three kernels, each written once and read once
+            geo_bytes += 16.0 * NQ;
         by += ne * ((in_v + out_v) * vs + geo_bytes + 8.0);
     }
     if (n_elem) *n_elem = ne_tot;
@@ -1642,6 +1692,8 @@ void hp_op_destroy(hp_op op) {
     for (cudaStream_t t : op->pool) cudaStreamDestroy(t);
     for (void* p : op->mat) cudaFree(p);
     for (float* p : op->part_buf) cudaFree(p);
+    cudaFree(op->hyb_u);
+    cudaFree(op->hyb_v);
     cudaFree(op->d_desc);
     cudaFree(op->d_desc_graph);
     cudaFree(op->d_items);

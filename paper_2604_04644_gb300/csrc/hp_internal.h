@@ -129,6 +129,10 @@ struct hp_op_s {
     void* d_items = nullptr;                    // WorkItem list, by decreasing cost
     int* d_next = nullptr;                      // work-list counter
     int n_items = 0, wl_smem = 0, wl_grid = 0;
+    // tensor-core hybrid blocks: u = B uhat and u' at every point of the mesh's
+    // point layout (two FP32 vectors; blocks write disjoint ranges)
+    float* hyb_u = nullptr;
+    float* hyb_v = nullptr;
     std::vector<float*> part_buf;               // their partial outputs, per block (grown on demand)
     std::vector<int64_t> part_cap;
     // matrix-based blocks: stored H^e as Ht[n][e][m] (FP64 or FP32, the op's I/O type), built on
@@ -209,6 +213,7 @@ struct EMArgs {
     const T* A4T;                // [NP][4][NQ]
     const unsigned char* blob;   // table blob (for D, z, w)
     unsigned int* err;
+    int point_space;             // hybrid core only: in / out are point values (no B, B^T)
 };
 cudaError_t emat_launch_f64(bool hybrid, bool affine, const EMArgs<double>& a, cudaStream_t s);
 
@@ -233,7 +238,26 @@ struct TCArgs {
 };
 // parts per tile the launcher will use (0 on error): part_out needs nsplit * n_elem * NP floats
 int tc_emat_nsplit(const TCArgs& a);
+// hybrid strategy on the tensor cores (hp_tc_emat.cu): mode 0 u = B uhat
+// (coefficients -> the block's points in the phys layout), mode 1 out = B^T u'
+struct HybArgs {
+    int NQ, NP, KP, NPpad, nch, es;
+    int64_t n_elem;
+    const int64_t* coeff_off;
+    const int64_t* phys_off;
+    const float* in;
+    float* out;
+    const unsigned char* img;          // the elemental-matrix operator's reference image
+    int64_t chunk_bytes;
+    int fwd_bytes, bwd_bytes;
+    unsigned int* err;
+};
+cudaError_t tc_hyb_launch(const HybArgs& a, int mode, cudaStream_t s);
 constexpr int kTcMaxModes = 256;
+// the tensor-core hybrid: BF16 up to 512 modes; TF32 up to 384 (its U tile,
+// 128 x K_P x 4 bytes, must fit in shared memory)
+constexpr int kTcHybMaxModes = 512, kTcHybMaxModesTF32 = 384;
+int tc_hyb_smem(int mode, int es, int KP, int NPpad, int bwd_bytes);
 int tc_chunk_points();
 int64_t tc_geom_halves(int64_t n_elem, int nch);
 cudaError_t tc_geom_layout16(int shape, bool curved, const double* g, int NQp, const double* z, const double* w, int Q,

@@ -33,6 +33,7 @@
 // issues the MMAs.  Every wait is
 // bounded; a timeout latches DERR_TIMEOUT, stops every role, drains the
 // copies and MMAs in flight and frees the tensor memory before the CTA exits.
+#include <algorithm>
 #include <cuda_bf16.h>
 #include <type_traits>
 #include <cuda_fp16.h>
@@ -599,6 +600,167 @@ __global__ void __launch_bounds__(Epi<EW>::kThreads, Epi<EW>::kCtas) tc_emat_ker
     if (warp == 0) tc::tmem_dealloc(tbase, E::kTmemCols);
 }
 
+// Hybrid strategy on the tensor cores: the two dense contractions with the
+// reference basis, u = B uhat (MODE 0, modes -> points) and out = B^T u'
+// (MODE 1, points -> modes), for tiles of 128 elements (the MMA's M, one
+// element per TMEM lane), on component 0 (B) of the elemental-matrix image;
+// the collocated derivatives and the metric between them run on the CUDA
+// cores.  Per point chunk: a bulk copy of component 0's operand (its 16 rows
+// of every 128-byte K slice, packed 2 KB apart in shared memory), the MMAs, a
+// commit; MODE 0 stores the chunk's 16 point values of every element from
+// TMEM, MODE 1 accumulates all chunks into N_P columns (two MMAs of at most
+// 256 columns each past 256 modes).  128 threads, thread 0 issuing; every
+// wait bounded.
+constexpr int kHybSlice = kNPT * 128;       // component 0 of one K slice: 16 rows x 128 bytes
+
+struct HybBars {
+    uint64_t full, mma;
+    uint32_t tmem;
+};
+
+template <int ES, int MODE>
+__global__ void __launch_bounds__(128) tc_hyb_kernel(const __grid_constant__ HybArgs a) {
+    using O = Op<ES>;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* smem = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
+    HybBars* B = reinterpret_cast<HybBars*>(smem);
+    // MODE 0: U [KP / KR][128 x 128 B]; MODE 1: V' [128 x 16 points]; then the chunk's operand
+    unsigned char* sOp = smem + 1024;
+    const size_t op_bytes = MODE == 0 ? (size_t)128 * a.KP * ES : (size_t)O::VBYTES;
+    unsigned char* sSt = sOp + (op_bytes + 1023) / 1024 * 1024;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const uint32_t ncols = MODE == 0 ? 32u : (a.NPpad > 256 ? 512u : 256u);
+    if (tid == 0) {
+        mbar_init(&B->full, 1);
+        mbar_init(&B->mma, 1);
+    }
+    if (warp == 0) { tc::tmem_alloc(&B->tmem, ncols); tc::tmem_relinquish(); }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tbase = B->tmem;
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    uint32_t pf = 0, pm = 0;
+    bool ok = true;
+    auto wait = [&](uint64_t* bar, uint32_t& ph) {
+        const bool w = mbar_wait_bounded(bar, ph, kWaitLimitNs);
+        if (!w) {
+            if (tid == 0) atomicOr(a.err, DERR_TIMEOUT);
+            mbar_wait_bounded(bar, ph, kWaitLimitNs);
+        }
+        ph ^= 1u;
+        ok = (__syncthreads_and(w ? 1 : 0) != 0) && ok;
+    };
+    const int64_t ntiles = (a.n_elem + 127) / 128;
+    const uint32_t nsl = (uint32_t)((a.KP + O::KR - 1) / O::KR);
+    constexpr uint32_t hs16 = kHybSlice >> 4;
+    // MODE 0: A = U (K-major, 128-byte swizzle), B = the packed slices (K-major)
+    const uint64_t dU = tc::smem_desc_sw(smem_addr(sOp), 1024, tc::kSw128);
+    const uint64_t dF = tc::smem_desc_sw(smem_addr(sSt), 1024, tc::kSw128);
+    // MODE 1: A = V' (K = the 16 points); B = BF16: the packed slices read MN-major
+    // (64-mode atoms one packed slice apart, 8-point groups 1 KB apart);
+    // TF32: the component's backward tile R_0[mode][point] (K-major)
+    const uint64_t dV = tc::smem_desc_sw(smem_addr(sOp), 8 * O::VROW, O::VSW);
+    const uint64_t dRt = tc::smem_desc_sw_lbo(smem_addr(sSt), kHybSlice, 1024, tc::kSw128);
+    const uint64_t dRb = tc::smem_desc_sw(smem_addr(sSt), 8 * O::VROW, O::VSW);
+    const uint32_t id_f = tc::instr_desc(O::FMT, 128, kNPT);
+    const uint32_t n0 = a.NPpad > 256 ? 256u : (uint32_t)a.NPpad, n1 = (uint32_t)a.NPpad - n0;
+    // BF16 backward: B operand MN-major (bit 16 of the instruction descriptor)
+    const uint32_t mn = ES == 2 ? (1u << 16) : 0u;
+    const uint32_t id_b0 = tc::instr_desc(O::FMT, 128, n0) | mn, id_b1 = tc::instr_desc(O::FMT, 128, n1 > 0 ? n1 : 16) | mn;
+    // start of modes 256.. in the backward operand (16-byte units)
+    const uint32_t half16 = ES == 2 ? (256 / 64) * hs16 : (256 * O::VROW) >> 4;
+    for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        const int64_t e = tile * 128 + tid;              // this thread's element = TMEM lane
+        const bool valid = e < a.n_elem;
+        if (MODE == 0) {
+            const float* cin = valid ? a.in + a.coeff_off[e] : nullptr;
+            for (int m = 0; m < a.KP; ++m)
+                O::put(sOp + (m / O::KR) * 128 * 128 + O::off128(tid, m % O::KR), (valid && m < a.NP) ? __ldg(cin + m) : 0.f);
+            tc::fence_async_smem();
+            __syncthreads();
+        }
+        for (int k = 0; k < a.nch && ok; ++k) {
+            if (tid == 0) {
+                const unsigned char* src = a.img + (size_t)k * a.chunk_bytes;
+                if (MODE == 1 && ES == 4) {
+                    mbar_expect_tx(&B->full, (uint32_t)a.bwd_bytes);
+                    bulk_g2s(sSt, src + a.fwd_bytes, (uint32_t)a.bwd_bytes, &B->full);
+                } else {
+                    mbar_expect_tx(&B->full, nsl * (uint32_t)kHybSlice);
+                    for (uint32_t sl = 0; sl < nsl; ++sl)
+                        bulk_g2s(sSt + sl * kHybSlice, src + (size_t)sl * kSliceBytes, kHybSlice, &B->full);
+                }
+            }
+            if (MODE == 1) {
+                float x[kNPT];
+#pragma unroll
+                for (int p = 0; p < kNPT; ++p) {
+                    const int l = k * kNPT + p;
+                    x[p] = (valid && l < a.NQ) ? __ldg(a.in + a.phys_off[e] + l) : 0.f;
+                }
+                O::template put_pts<kNPT>(sOp, (uint32_t)tid, 0, x);
+                tc::fence_async_smem();
+                __syncthreads();
+            }
+            wait(&B->full, pf);
+            if (!ok) break;
+            if (tid == 0) {
+                tc::fence_after();
+                if (MODE == 0) {
+                    for (uint32_t sl = 0; sl < nsl; ++sl)
+#pragma unroll
+                        for (uint32_t st = 0; st < 4; ++st)
+                            O::mma(tbase, dU + (sl * 1024 + st * 2), dF + (sl * hs16 + st * 2), id_f, sl > 0 || st > 0);
+                } else if (ES == 2) {
+                    O::mma(tbase, dV, dRt, id_b0, k > 0);
+                    if (n1 > 0) O::mma(tbase + 256, dV, dRt + half16, id_b1, k > 0);
+                } else {
+#pragma unroll
+                    for (uint32_t st = 0; st < O::VROW / 32; ++st) {
+                        O::mma(tbase, dV + st * 2, dRb + st * 2, id_b0, k > 0 || st > 0);
+                        if (n1 > 0) O::mma(tbase + 256, dV + st * 2, dRb + half16 + st * 2, id_b1, k > 0 || st > 0);
+                    }
+                }
+                tc::commit(&B->mma);
+            }
+            wait(&B->mma, pm);
+            if (!ok) break;
+            tc::fence_after();
+            if (MODE == 0) {
+                float v[16];
+                tc::ld_32x16(tbase + lane_base, v);
+                if (valid) {
+                    float* o = a.out + a.phys_off[e] + k * kNPT;
+#pragma unroll
+                    for (int p = 0; p < kNPT; ++p)
+                        if (k * kNPT + p < a.NQ) o[p] = v[p];
+                }
+                tc::fence_before();
+                __syncthreads();
+            }
+        }
+        if (MODE == 1 && ok) {
+            for (int c = 0; c < a.NPpad; c += 16) {
+                float v[16];
+                tc::ld_32x16(tbase + lane_base + (uint32_t)c, v);
+                if (valid) {
+                    float* o = a.out + a.coeff_off[e] + c;
+#pragma unroll
+                    for (int i = 0; i < 16; ++i)
+                        if (c + i < a.NP) o[i] = v[i];
+                }
+            }
+            tc::fence_before();
+            __syncthreads();
+        }
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    if (warp == 0) tc::tmem_dealloc(tbase, ncols);
+}
+
 // deterministic split-tile sum: out = part 0 + part 1 + ... in part order
 __global__ void sum_parts_kernel(float* out, const int64_t* coeff_off, const float* part_out, int64_t n_elem, int NP,
                                  int nsplit) {
@@ -787,6 +949,41 @@ int tc_emat_nsplit(const TCArgs& a) {
     const int64_t ns = ((int64_t)sms * pl.ctas + ntiles - 1) / ntiles;
     const int64_t cap = a.nch / 4 > 1 ? a.nch / 4 : 1;
     return (int)(ns < cap ? ns : cap);
+}
+
+int tc_hyb_smem(int mode, int es, int KP, int NPpad, int bwd_bytes) {
+    const int kr = 128 / es, nsl = (KP + kr - 1) / kr;
+    const int op_bytes = mode == 0 ? 128 * KP * es : 128 * kNPT * es;
+    const int st_bytes = (mode == 1 && es == 4) ? bwd_bytes : nsl * kHybSlice;
+    int smem = 1024 + (op_bytes + 1023) / 1024 * 1024 + st_bytes + 1024;
+    // MODE 1 holds 256 (N_P <= 256) or 512 TMEM columns: shared memory keeps
+    // at most two CTAs, or one, on an SM, so that every allocation succeeds at once
+    if (mode == 1) smem = std::max(smem, NPpad > 256 ? 120 * 1024 : 80 * 1024);
+    return smem;
+}
+
+cudaError_t tc_hyb_launch(const HybArgs& a, int mode, cudaStream_t s) {
+    const int64_t ntiles = (a.n_elem + 127) / 128;
+    if (ntiles <= 0) return cudaSuccess;
+    if (a.NPpad > kTcHybMaxModes || a.NPpad % 16 || (a.es != 2 && a.es != 4) || a.nch < 1) return cudaErrorInvalidValue;
+    const int smem = tc_hyb_smem(mode, a.es, a.KP, a.NPpad, a.bwd_bytes);
+    if (smem > 227 * 1024) return cudaErrorInvalidValue;
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    auto launch = [&](auto kern) -> cudaError_t {
+        cudaError_t e2 = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e2 != cudaSuccess) return e2;
+        int per = 0;
+        e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 128, smem);
+        if (e2 != cudaSuccess) return e2;
+        const int grid = (int)std::min<int64_t>(ntiles, (int64_t)sms * std::max(per, 1));
+        kern<<<grid, 128, smem, s>>>(a);
+        return cudaGetLastError();
+    };
+    if (a.es == 4) return mode == 0 ? launch(tc_hyb_kernel<4, 0>) : launch(tc_hyb_kernel<4, 1>);
+    return mode == 0 ? launch(tc_hyb_kernel<2, 0>) : launch(tc_hyb_kernel<2, 1>);
 }
 
 cudaError_t tc_emat_launch(const TCArgs& a, cudaStream_t s) {

@@ -29,7 +29,14 @@ with |B| |uhat| taken per point as the sum over modes of |phi_m| |uhat_m|
 eta_1 passes use the table {1/2, -z/2} on the sum and the difference of the
 two vertex coefficients (L = 1/2 - z/2, R = 1/2 + z/2), whose absolute chain
 (1/2 + |z|/2)(|u_L| + |u_R|) is at most twice |L| |u_L| + |R| |u_R|.
-Both are slightly enlarged (x 1.1) for second-order terms.
+Tensor-core hybrid (TF32 / BF16), which evaluates the same chain with B and
+B^T as tensor-core products and the collocated core in FP32: four roundings
+to the operand type (the coefficient and the entry of B in u = B uhat, the
+point value u' and the entry of B in B^T u'), and FP32 along the rest of the
+chain (N_P terms forward, Q + 3 + 3 Q in the core, N_Q backward, and the FP32
+factors and collocation tables):
+    bound_m = (4 u + (N_P + N_Q + 4 Q + 10) 2^-24) (the chain of the sum factorisation)_m.
+All three are slightly enlarged (x 1.1) for second-order terms.
 """
 import numpy as np
 
@@ -123,4 +130,15 @@ def sf32_bound(mesh, x, lam, kind):
     for e in range(mesh["n_elem"]):
         P = int(mesh["P"][e])
         out[co[e]:co[e + 1]] = 1.1 * 2 * (3 * (P + 1) + 7 * (P + 2) + 3) * U32 * chain[co[e]:co[e + 1]]
+    return out
+
+
+def hyb_bound(mesh, x, lam, kind, u):
+    co, _ = ops.layout(mesh)
+    out = np.zeros(co[-1])
+    chain = sf_chain(mesh, x, lam, kind)
+    for e in range(mesh["n_elem"]):
+        NP = co[e + 1] - co[e]
+        Q = int(mesh["Q"][e])
+        out[co[e]:co[e + 1]] = 1.1 * (4 * u + (NP + Q ** 3 + 4 * Q + 10) * U32) * chain[co[e]:co[e + 1]]
     return out

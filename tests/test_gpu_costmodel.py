@@ -119,34 +119,38 @@ def test_mlp_argument_checks(hp):
 
 
 def test_tf32_schedules_only_built_strategies(hp):
-    """A TF32 operator has FP32 sum factorisation and the tensor-core elemental
-    matrix (blocks of at most 256 modes): both schedulers choose among those
-    only, whatever the network predicts for the hybrid strategy."""
+    """A TF32 operator has FP32 sum factorisation, the tensor-core elemental
+    matrix (blocks of at most 256 modes) and the tensor-core hybrid (at most
+    384): both schedulers choose among those only, never a stored matrix."""
     from oracle.basis import n_modes
-    mesh = inputs.slab_mesh(2, 2, 4, (2, 7), order_seed=5, curved_rule="x_half")
+    mesh = inputs.slab_mesh(2, 2, 4, (2, 9), order_seed=5, curved_rule="x_half")
     keys = []
     for k in zip(mesh["shape"].tolist(), mesh["P"].tolist(), mesh["curved"].tolist()):
         if k not in keys:
             keys.append(k)
     nb = len(keys)
     fits = np.array([n_modes(s, P) <= 256 for s, P, _ in keys])
+    fits_h = np.array([n_modes(s, P) <= 384 for s, P, _ in keys])
+    assert (fits_h & ~fits).any() and (~fits_h).any()
     h = hp.hp_mesh_create(mesh, 0)
     m = hp.hp_mlp_create(5, 32, 3, seed=1)
     try:
         co, po, nc, nph = hp.hp_mesh_layout(h, mesh["n_elem"])
         op = hp.hp_op_create(h, hp.HP_HELMHOLTZ, hp.HP_STRAT_ELEMAT, hp.HP_TF32)
         p = np.zeros(hp.hp_mlp_info(m)[3], dtype=np.float32)
-        p[-3:] = [2.0, 1.0, 0.5]          # hybrid smallest, then the elemental matrix
+        p[-3:] = [2.0, 0.5, 1.0]          # the elemental matrix smallest, then the hybrid
         hp.hp_mlp_params(m, p)
         hp.hp_op_schedule(op, m)
         st = hp.hp_op_strategies(op, nb)
-        assert (st[fits] == hp.HP_STRAT_ELEMAT).all() and (st[~fits] == hp.HP_STRAT_SUMFAC).all()
+        assert (st[fits] == hp.HP_STRAT_ELEMAT).all()
+        assert (st[fits_h & ~fits] == hp.HP_STRAT_HYBRID).all() and (st[~fits_h] == hp.HP_STRAT_SUMFAC).all()
         x = torch.tensor(inputs.random_coefficients(5, co), device="cuda:0", dtype=torch.float32)
         y = torch.zeros(nc, device="cuda:0", dtype=torch.float32)
         times = hp.hp_op_schedule_exhaustive(op, 1.0, x, y, nb)
-        assert (times[:, 2] >= 1e29).all() and (times[:, 3] >= 1e29).all() and (times[~fits, 1] >= 1e29).all()
+        assert (times[:, 3] >= 1e29).all() and (times[~fits, 1] >= 1e29).all() and (times[~fits_h, 2] >= 1e29).all()
+        assert (times[fits_h, 2] < 1e29).all()
         best = hp.hp_op_strategies(op, nb)
-        assert (best == times.argmin(axis=1)).all() and (best != hp.HP_STRAT_HYBRID).all()
+        assert (best == times.argmin(axis=1)).all() and (best != hp.HP_STRAT_MATRIX).all()
         hp.hp_op_destroy(op)
     finally:
         hp.hp_mlp_destroy(m)
@@ -155,10 +159,11 @@ def test_tf32_schedules_only_built_strategies(hp):
 
 def test_graph_schedule_keeps_valid_strategies_and_results(hp):
     """The graph-aware search chooses only strategies built for each block (TF32:
-    FP32 sum factorisation or the tensor-core elemental matrix, the latter only
-    up to 256 modes), returns a positive graph time, rejects bad arguments, and
-    the scheduled graph still matches the FP64 oracle within each block's bound
-    (TF32_TOL on tensor-core blocks, the FP32 bound elsewhere)."""
+    FP32 sum factorisation, the tensor-core elemental matrix up to 256 modes
+    or the tensor-core hybrid up to 384), returns a positive graph time,
+    rejects bad arguments, and the scheduled graph still matches the FP64
+    oracle within each block's bound (TF32_TOL on tensor-core blocks, the FP32
+    bound elsewhere)."""
     from oracle import operators as oracle_ops
     from oracle.basis import n_modes
     from tests.test_gpu_parity import fp32_tol, rel_err
@@ -170,6 +175,7 @@ def test_graph_schedule_keeps_valid_strategies_and_results(hp):
             keys.append(k)
     nb = len(keys)
     fits = np.array([n_modes(s, P) <= 256 for s, P, _ in keys])
+    fits_h = np.array([n_modes(s, P) <= 384 for s, P, _ in keys])
     h = hp.hp_mesh_create(mesh, 0)
     try:
         co, po, nc, nph = hp.hp_mesh_layout(h, mesh["n_elem"])
@@ -185,8 +191,8 @@ def test_graph_schedule_keeps_valid_strategies_and_results(hp):
             ms = hp.hp_op_schedule_graph(op, 1.0, x, y, 3, 2)
             assert ms > 0
             st = hp.hp_op_strategies(op, nb)
-            assert np.isin(st, [hp.HP_STRAT_SUMFAC, hp.HP_STRAT_ELEMAT]).all()
-            assert (st[~fits] == hp.HP_STRAT_SUMFAC).all()
+            assert np.isin(st, [hp.HP_STRAT_SUMFAC, hp.HP_STRAT_ELEMAT, hp.HP_STRAT_HYBRID]).all()
+            assert (st[~fits] != hp.HP_STRAT_ELEMAT).all() and (st[~fits_h] == hp.HP_STRAT_SUMFAC).all()
             y.zero_()
             hp.hp_op_apply_graph(op, 1.3, x, y)
             hp.hp_op_sync(op)
@@ -195,7 +201,7 @@ def test_graph_schedule_keeps_valid_strategies_and_results(hp):
             for (s, P, c), strat in zip(keys, st):
                 els = np.nonzero((mesh["shape"] == s) & (mesh["P"] == P) & (mesh["curved"] == c))[0]
                 idx = np.concatenate([np.arange(co[e], co[e + 1]) for e in els])
-                tol = TF32_TOL if strat == hp.HP_STRAT_ELEMAT else fp32_tol(P)
+                tol = TF32_TOL if strat in (hp.HP_STRAT_ELEMAT, hp.HP_STRAT_HYBRID) else fp32_tol(P)
                 assert rel_err(out[idx], ref[idx]) <= tol, (s, P, c, strat)
         finally:
             hp.hp_op_destroy(op)

@@ -117,9 +117,12 @@ def test_tf32_strategy_per_block(hp):
                 keys.append(k)
         want = [hp.HP_STRAT_ELEMAT if n_modes(s, 6) <= MAX_TC_MODES else hp.HP_STRAT_SUMFAC for s, _ in keys]
         assert strat.tolist() == want
-        with pytest.raises(hp.HpError) as ei:       # hybrid is not a tensor-core form
-            hp.hp_op_strategies(op, len(keys), np.full(len(keys), hp.HP_STRAT_HYBRID))
+        with pytest.raises(hp.HpError) as ei:       # stored matrices are FP64 / FP32 only
+            hp.hp_op_strategies(op, len(keys), np.full(len(keys), hp.HP_STRAT_MATRIX))
         assert ei.value.status == hp.HP_ERR_UNSUPPORTED
+        # the tensor-core hybrid covers every block here (N_P <= 343 <= 384)
+        hp.hp_op_strategies(op, len(keys), np.full(len(keys), hp.HP_STRAT_HYBRID))
+        assert (hp.hp_op_strategies(op, len(keys)) == hp.HP_STRAT_HYBRID).all()
         hp.hp_op_destroy(op)
         for kind, strategy in ((hp.HP_BWDTRANS, hp.HP_STRAT_ELEMAT), (hp.HP_HELMHOLTZ, hp.HP_STRAT_SUMFAC)):
             with pytest.raises(hp.HpError) as ei:
