@@ -96,12 +96,15 @@ typedef enum {
 
 /* Compute type.  HP_FP64: IEEE double throughout (the oracle-parity form).
  * HP_FP32: single precision (CUDA cores), float arrays.  HP_TF32 / HP_BF16:
- * the elemental-matrix strategy on the tensor cores (tcgen05, Blackwell):
- * coefficients, reference matrices and metric-weighted point values rounded
- * to TF32 (10-bit mantissa) or BF16 (7-bit mantissa), products accumulated in
- * FP32 in tensor memory, metric factors kept in FP16 with one power-of-two
- * scale per element (11 significant bits); float arrays; relative error a
- * few units of 2^-11 (TF32) or 2^-8 (BF16). */
+ * the elemental-matrix and hybrid strategies on the tensor cores (tcgen05,
+ * Blackwell).  Elemental matrix: coefficients, reference matrices and
+ * metric-weighted point values rounded to TF32 (10-bit mantissa) or BF16
+ * (7-bit mantissa), products accumulated in FP32 in tensor memory, metric
+ * factors kept in FP16 with one power-of-two scale per element (11
+ * significant bits).  Hybrid: u = B uhat and B^T u' on the tensor cores
+ * (coefficients, B and u' rounded to TF32 / BF16, FP32 accumulation), the
+ * collocated derivatives and the FP32 metric between them on the CUDA cores.
+ * Float arrays; relative error a few units of 2^-11 (TF32) or 2^-8 (BF16). */
 typedef enum { HP_FP64 = 0, HP_FP32 = 1, HP_TF32 = 2, HP_BF16 = 3 } hp_dtype;
 
 /* Mesh description (all host arrays, copied by hp_mesh_create).
@@ -177,9 +180,10 @@ hp_status hp_geom_copy(hp_mesh mesh, double* out7, double* out9);
  * `dtype` with `strategy`.  HP_FP64 and HP_FP32 apply to every kind with
  * HP_STRAT_SUMFAC (the only strategy of the derivative building blocks and of
  * HP_ADVECTION_DIFFUSION_REACTION); arrays passed to hp_op_apply are double (HP_FP64) or
- * float (HP_FP32, HP_TF32, HP_BF16).  HP_TF32 and HP_BF16 take HP_STRAT_ELEMAT (or AUTO) and the
- * kinds HP_MASS, HP_LAPLACIAN, HP_HELMHOLTZ: blocks with at most 256 modes per
- * element run the tensor-core elemental-matrix kernel, larger ones FP32 sum
+ * float (HP_FP32, HP_TF32, HP_BF16).  HP_TF32 and HP_BF16 take HP_STRAT_ELEMAT (or AUTO)
+ * or HP_STRAT_HYBRID and the kinds HP_MASS, HP_LAPLACIAN, HP_HELMHOLTZ: blocks
+ * with at most 256 modes per element (elemental matrix) or 512 (BF16 hybrid)
+ * / 352 (TF32 hybrid) run the tensor-core form, larger ones FP32 sum
  * factorisation (hp_op_strategies reports which).  Errors: HP_ERR_ARG,
  * HP_ERR_UNSUPPORTED (combination not built), HP_ERR_GEOM / HP_ERR_CUDA from
  * the geometric factors it needs. */
@@ -247,9 +251,10 @@ hp_status hp_op_tiles(hp_op op, int* tiles, int64_t n_blocks, int set);
  * by the next apply); a block that leaves HP_STRAT_MATRIX frees its stored
  * matrices at once.  HP_ERR_UNSUPPORTED for a dense strategy on a derivative
  * building block, for HP_STRAT_MATRIX outside those limits, and for an
- * HP_TF32 / HP_BF16 operator for anything but HP_STRAT_SUMFAC (FP32) or
- * HP_STRAT_ELEMAT (tensor core, blocks of at most 256 modes).  Writing drops
- * the op's captured graph. */
+ * HP_TF32 / HP_BF16 operator for anything but HP_STRAT_SUMFAC (FP32),
+ * HP_STRAT_ELEMAT (tensor core, blocks of at most 256 modes) or
+ * HP_STRAT_HYBRID (tensor core, at most 512 modes in BF16, 352 in TF32).
+ * Writing drops the op's captured graph. */
 hp_status hp_op_strategies(hp_op op, int* strategies, int64_t n_blocks, int set);
 
 /* Form of the sum-factorised Laplacian and Helmholtz blocks of an HP_FP64
@@ -354,9 +359,9 @@ hp_status hp_op_schedule(hp_op op, hp_mlp mlp, void* stream);
  * inputs) graph_launch: 1 when the blocks will run as the concurrent graph of
  * hp_op_apply_graph, 0 when one after another (hp_op_apply); the outputs are
  * the predicted log times of SUMFAC, ELEMAT, HYBRID and (4 outputs) MATRIX.
- * For an HP_TF32 / HP_BF16 operator output 0 is its FP32 sum factorisation
- * and output 1 its tensor-core elemental matrix; the other strategies are not
- * built for it and never chosen.  Derivative building blocks stay SUMFAC.
+ * For an HP_TF32 / HP_BF16 operator output 0 is its FP32 sum factorisation,
+ * output 1 its tensor-core elemental matrix and output 2 its tensor-core
+ * hybrid; stored matrices are not built for it and never chosen.  Derivative building blocks stay SUMFAC.
  * Drops the op's captured graph.  Errors: HP_ERR_ARG (null arguments,
  * graph_launch not 0 or 1, network of another shape), HP_ERR_CUDA. */
 hp_status hp_op_schedule_mlp(hp_op op, hp_mlp mlp, int graph_launch, void* stream);
@@ -379,7 +384,8 @@ hp_status hp_op_schedule_exhaustive(hp_op op, double lambda, const void* in, voi
  * it (HP_FP64 / HP_FP32 mass, Laplacian and Helmholtz: sum factorisation,
  * elemental matrix, hybrid and, for blocks of at most 256 modes whose matrices
  * fit in half of the free device memory, stored matrices; HP_TF32 / HP_BF16:
- * FP32 sum factorisation and the tensor-core elemental matrix) and keeps one
+ * FP32 sum factorisation, the tensor-core elemental matrix and the
+ * tensor-core hybrid) and keeps one
  * only if the graph's median time over `reps` timed launches
  * (after a warm-up) drops by more than 1 %; `passes` sweeps over the blocks.
  * Per-block times taken alone (hp_op_schedule_exhaustive) miss the overlap of

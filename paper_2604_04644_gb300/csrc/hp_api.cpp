@@ -412,7 +412,7 @@ bool mat_fits(const Block& b) { return n_modes(b.shape, b.P) <= kMatMaxModes; }
 // strategy k (HP_STRAT_SUMFAC / ELEMAT / HYBRID / MATRIX) is built for block i
 // of op: derivative building blocks are sum-factorised only; a TF32 / BF16
 // operator has FP32 sum factorisation, the tensor-core elemental matrix
-// (N_P <= 256) and the tensor-core hybrid (N_P <= 512 BF16, 384 TF32); stored
+// (N_P <= 256) and the tensor-core hybrid (N_P <= 512 BF16, 352 TF32); stored
 // matrices are mass, Laplacian or Helmholtz in FP64 / FP32 (N_P <= 256)
 bool strategy_available(const hp_op_s* op, size_t i, int k) {
     if (k == HP_STRAT_SUMFAC) return true;
@@ -704,14 +704,16 @@ cudaError_t launch_block(hp_op op, size_t bi, int tile, double lambda, const voi
         h.in = static_cast<const float*>(in); h.out = op->hyb_u;
         cudaError_t e = tc_hyb_launch(h, 0, s);
         if (e != cudaSuccess) return e;
-        EMArgs<float> c{};
-        c.op = op->kind; c.shape = b.shape; c.P = b.P; c.Q = b.Q; c.NQ = h.NQ;
-        c.NP = h.NP; c.NQp = nqp(b.Q); c.n_elem = b.n_elem; c.lambda = (float)lambda;
+        SFArgs<float> c{};
+        c.op = op->kind; c.n_elem = b.n_elem; c.lambda = (float)lambda;
         c.coeff_off = b.d_coeff_off; c.phys_off = b.d_phys_off;
-        c.in = op->hyb_u; c.out = op->hyb_v;
-        c.geom = b.d_geom32; c.blob = static_cast<const unsigned char*>(blob.d32); c.err = op->d_err;
-        c.point_space = 1;
-        e = emat_launch_f32(true, !b.curved, c, s);
+        c.in = op->hyb_u; c.out = op->hyb_v; c.n_phys_total = nphys;
+        c.geom = b.d_geom32; c.dgeom = b.d_dgeom32;
+        c.blob = static_cast<const unsigned char*>(blob.d32); c.blob_bytes = blob.bytes32;
+        c.err = op->d_err;
+        c.point_io = 1;
+        fill_const_tables(b, c);
+        e = sf_launch_f32(b.shape, b.P, !b.curved, tile, c, s);
         if (e != cudaSuccess) return e;
         h.in = op->hyb_v; h.out = static_cast<float*>(out);
         return tc_hyb_launch(h, 1, s);
@@ -1382,7 +1384,7 @@ hp_status hp_op_strategies(hp_op op, int* strat, int64_t n_blocks, int set) {
         if ((op->dtype == HP_TF32 || op->dtype == HP_BF16) && strat[i] != HP_STRAT_SUMFAC &&
             !tc_strategy_fits(op->mesh->blocks[i], op->dtype, strat[i])) {
             set_error("hp_op_strategies: HP_TF32 / HP_BF16 blocks are tensor-core elemental-matrix (N_P <= 256), "
-                      "tensor-core hybrid (N_P <= 512 BF16, 384 TF32) or FP32 sum factorisation");
+                      "tensor-core hybrid (N_P <= 512 BF16, 352 TF32) or FP32 sum factorisation");
             return HP_ERR_UNSUPPORTED;
         }
         dense |= (strat[i] == HP_STRAT_ELEMAT || strat[i] == HP_STRAT_HYBRID) && op->dtype != HP_TF32 &&

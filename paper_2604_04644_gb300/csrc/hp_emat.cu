@@ -16,9 +16,7 @@
 // Hybrid (not in the paper): the restriction/expansion B, B^T as dense
 // products and the derivatives collocated (D_d at the points), i.e. the
 // collocated algorithm of Sec. 3.3 with the two sum-factorised passes replaced
-// by dense reference-matrix products.  With point_space set the kernel is the
-// point-space core alone (u -> u' = sum_d D_d^T G D_d u + lambda w|J| u, or
-// w|J| u for mass) between the tensor-core B and B^T of the TF32 / BF16 hybrid.
+// by dense reference-matrix products.
 #include "hp_device.cuh"
 
 namespace hp {
@@ -184,7 +182,7 @@ __global__ void __launch_bounds__(kNT) hyb_kernel(const EMArgs<T> a, int E) {
     for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x) {
         const int64_t e0 = g * E;
         const int ne = (int)min((int64_t)E, a.n_elem - e0);
-        if (op == HP_IPRODUCT_WRT_BASE || a.point_space) {
+        if (op == HP_IPRODUCT_WRT_BASE) {
             for (int idx = tid; idx < E * NQ; idx += kNT) {
                 int e = idx / NQ, l = idx - e * NQ;
                 S1[e * 4 * NQ + l] = e < ne ? a.in[a.phys_off[e0 + e] + l] : T(0);
@@ -266,14 +264,6 @@ __global__ void __launch_bounds__(kNT) hyb_kernel(const EMArgs<T> a, int E) {
                 S2[e * NQ + r] = s;
             }
             __syncthreads();
-        }
-        if (a.point_space) {
-            for (int idx = tid; idx < E * NQ; idx += kNT) {
-                int e = idx / NQ, l = idx - e * NQ;
-                if (e < ne) a.out[a.phys_off[e0 + e] + l] = S2[e * NQ + l];
-            }
-            __syncthreads();
-            continue;
         }
         // out[m] = sum_l B[l][m] u'[l]   (B rows coalesced over m)
         for (int idx = tid; idx < E * NP; idx += kNT) {

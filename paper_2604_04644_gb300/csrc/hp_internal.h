@@ -192,6 +192,10 @@ struct SFArgs {
     const unsigned char* blob;   // table blob (16-byte aligned)
     int blob_bytes;
     unsigned int* err;
+    // FP32 only: 1 = the point-space core of mass / Laplacian / Helmholtz (in and
+    // out are point values in the phys layout; no B, no B^T), the middle kernel
+    // of the tensor-core hybrid
+    int point_io;
     // differentiation matrices D_d[i][m] and the eta1 table A[a][i] of the block,
     // read by the kernels as constant-bank operands (Q <= 12, n <= 11)
     T cD[3][144];
@@ -213,7 +217,6 @@ struct EMArgs {
     const T* A4T;                // [NP][4][NQ]
     const unsigned char* blob;   // table blob (for D, z, w)
     unsigned int* err;
-    int point_space;             // hybrid core only: in / out are point values (no B, B^T)
 };
 cudaError_t emat_launch_f64(bool hybrid, bool affine, const EMArgs<double>& a, cudaStream_t s);
 
@@ -250,14 +253,15 @@ struct HybArgs {
     const unsigned char* img;          // the elemental-matrix operator's reference image
     int64_t chunk_bytes;
     int fwd_bytes, bwd_bytes;
+    int stages, stage_bytes;           // set by the launcher
     unsigned int* err;
 };
 cudaError_t tc_hyb_launch(const HybArgs& a, int mode, cudaStream_t s);
 constexpr int kTcMaxModes = 256;
-// the tensor-core hybrid: BF16 up to 512 modes; TF32 up to 384 (its U tile,
-// 128 x K_P x 4 bytes, must fit in shared memory)
-constexpr int kTcHybMaxModes = 512, kTcHybMaxModesTF32 = 384;
-int tc_hyb_smem(int mode, int es, int KP, int NPpad, int bwd_bytes);
+// the tensor-core hybrid: BF16 up to 512 modes; TF32 up to 352 (its U tile,
+// 128 x K_P x 4 bytes, and two ring stages must fit in shared memory)
+constexpr int kTcHybMaxModes = 512, kTcHybMaxModesTF32 = 352;
+int tc_hyb_smem(int mode, int es, int KP, int NPpad, int bwd_bytes, int* stages_out, int* stage_bytes_out);
 int tc_chunk_points();
 int64_t tc_geom_halves(int64_t n_elem, int nch);
 cudaError_t tc_geom_layout16(int shape, bool curved, const double* g, int NQp, const double* z, const double* w, int Q,

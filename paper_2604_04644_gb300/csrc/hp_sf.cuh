@@ -116,12 +116,14 @@ __device__ __forceinline__ bool sf_groups(const A& args, unsigned char* smem, in
     const bool deriv = (op == HP_LAPLACIAN || op == HP_HELMHOLTZ || op == HP_PHYSDERIV || adr);
     const bool sumderiv = (op == HP_LAPLACIAN || op == HP_HELMHOLTZ || op == HP_IPRODUCT_WRT_DERIV_BASE || adr);
     const bool merged = !LINES && deriv && coeff_in;   // v1 comes out of the eta1 pass
+    bool point_io = false;                             // FP32: point values in and out (no B, B^T)
+    if constexpr (LINES) point_io = args.point_io != 0;
 
     for (int64_t g = g_first; g < g_end; g += g_step) {
         const int64_t e0 = g * EPB;
         const int ne = (int)min((int64_t)EPB, args.n_elem - e0);
 
-        if (coeff_in) {
+        if (coeff_in && !point_io) {
             // gather modal coefficients into the slot tensor
             // (slots a = 0, 1 take the sum and the difference of the two coefficients,
             // the inputs of the parity-form eta1 table)
@@ -628,6 +630,14 @@ __device__ __forceinline__ bool sf_groups(const A& args, unsigned char* smem, in
 
         }
 
+        if (point_io) {
+            for (int idx = tid; idx < EPB * NQ; idx += NT) {
+                const int e = idx / NQ, r = idx - e * NQ;
+                if (e < ne) args.out[args.phys_off[e0 + e] + r] = S2[e * NQ + r];
+            }
+            __syncthreads();
+            continue;
+        }
         if constexpr (LINES) {
         // restriction B^T: eta1 pass g'[a][j][k] = sum_i Ta[a][i] u'[i][j][k], one (j,k) line per thread
         for (int idx = tid; idx < EPB * QQ; idx += NT) {

@@ -605,16 +605,22 @@ __global__ void __launch_bounds__(Epi<EW>::kThreads, Epi<EW>::kCtas) tc_emat_ker
 // (MODE 1, points -> modes), for tiles of 128 elements (the MMA's M, one
 // element per TMEM lane), on component 0 (B) of the elemental-matrix image;
 // the collocated derivatives and the metric between them run on the CUDA
-// cores.  Per point chunk: a bulk copy of component 0's operand (its 16 rows
-// of every 128-byte K slice, packed 2 KB apart in shared memory), the MMAs, a
-// commit; MODE 0 stores the chunk's 16 point values of every element from
-// TMEM, MODE 1 accumulates all chunks into N_P columns (two MMAs of at most
-// 256 columns each past 256 modes).  128 threads, thread 0 issuing; every
-// wait bounded.
+// cores.  The point chunks of a tile are software pipelined: component 0's
+// operand of chunk k (its 16 rows of every 128-byte K slice, packed 2 KB
+// apart) is bulk-copied into stage k mod S of a ring S (2 or 3) deep, issued
+// as soon as the MMA that read the stage's previous chunk has completed; the
+// MMA of chunk k runs while MODE 0 stores chunk k-1's 16 point values per
+// element from the other of two TMEM buffers, and while MODE 1 loads chunk
+// k+1's point values into registers for the other of two V' tiles.  MODE 1
+// accumulates all chunks into N_P columns (two MMAs of at most 256 columns
+// each past 256 modes).  128 threads, thread 0 issuing; every wait bounded,
+// and copies or MMAs still in flight after a timeout are waited for (bounded)
+// before the CTA frees its tensor memory.
 constexpr int kHybSlice = kNPT * 128;       // component 0 of one K slice: 16 rows x 128 bytes
+constexpr int kHybMaxStages = 3;
 
 struct HybBars {
-    uint64_t full, mma;
+    uint64_t full[kHybMaxStages], mma[2];
     uint32_t tmem;
 };
 
@@ -624,15 +630,18 @@ __global__ void __launch_bounds__(128) tc_hyb_kernel(const __grid_constant__ Hyb
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
     HybBars* B = reinterpret_cast<HybBars*>(smem);
-    // MODE 0: U [KP / KR][128 x 128 B]; MODE 1: V' [128 x 16 points]; then the chunk's operand
+    // MODE 0: U [KP / KR][128 x 128 B]; MODE 1: V' [2][128 x 16 points]; then the ring
     unsigned char* sOp = smem + 1024;
-    const size_t op_bytes = MODE == 0 ? (size_t)128 * a.KP * ES : (size_t)O::VBYTES;
+    const size_t op_bytes = MODE == 0 ? (size_t)128 * a.KP * ES : (size_t)2 * O::VBYTES;
     unsigned char* sSt = sOp + (op_bytes + 1023) / 1024 * 1024;
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const int S = a.stages;
+    const uint32_t stb = (uint32_t)a.stage_bytes;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t ncols = MODE == 0 ? 32u : (a.NPpad > 256 ? 512u : 256u);
     if (tid == 0) {
-        mbar_init(&B->full, 1);
-        mbar_init(&B->mma, 1);
+        for (int s = 0; s < S; ++s) mbar_init(&B->full[s], 1);
+        mbar_init(&B->mma[0], 1);
+        mbar_init(&B->mma[1], 1);
     }
     if (warp == 0) { tc::tmem_alloc(&B->tmem, ncols); tc::tmem_relinquish(); }
     tc::fence_before();
@@ -640,20 +649,44 @@ __global__ void __launch_bounds__(128) tc_hyb_kernel(const __grid_constant__ Hyb
     tc::fence_after();
     const uint32_t tbase = B->tmem;
     const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-    uint32_t pf = 0, pm = 0;
+    // barrier bookkeeping, identical in every thread: next phase, and whether a
+    // copy (full) or an MMA group (mma) was issued and not yet waited for
+    uint32_t ph_full[kHybMaxStages] = {0, 0, 0}, ph_mma[2] = {0, 0};
+    bool fl[kHybMaxStages] = {false, false, false}, ml[2] = {false, false};
     bool ok = true;
-    auto wait = [&](uint64_t* bar, uint32_t& ph) {
-        const bool w = mbar_wait_bounded(bar, ph, kWaitLimitNs);
-        if (!w) {
-            if (tid == 0) atomicOr(a.err, DERR_TIMEOUT);
-            mbar_wait_bounded(bar, ph, kWaitLimitNs);
-        }
-        ph ^= 1u;
+    auto wait_full = [&](int s) {
+        const bool w = mbar_wait_bounded(&B->full[s], ph_full[s], kWaitLimitNs);
+        if (w) { ph_full[s] ^= 1u; fl[s] = false; }
+        else if (tid == 0) atomicOr(a.err, DERR_TIMEOUT);
         ok = (__syncthreads_and(w ? 1 : 0) != 0) && ok;
     };
-    const int64_t ntiles = (a.n_elem + 127) / 128;
+    auto wait_mma = [&](int b) {
+        const bool w = mbar_wait_bounded(&B->mma[b], ph_mma[b], kWaitLimitNs);
+        if (w) { ph_mma[b] ^= 1u; ml[b] = false; }
+        else if (tid == 0) atomicOr(a.err, DERR_TIMEOUT);
+        ok = (__syncthreads_and(w ? 1 : 0) != 0) && ok;
+    };
     const uint32_t nsl = (uint32_t)((a.KP + O::KR - 1) / O::KR);
+    // copy of chunk k's operand into stage k mod S (thread 0 issues; all threads book it)
+    auto issue = [&](int k) {
+        const int s = k % S;
+        if (tid == 0) {
+            const unsigned char* src = a.img + (size_t)k * a.chunk_bytes;
+            unsigned char* dst = sSt + (size_t)s * stb;
+            if (MODE == 1 && ES == 4) {     // TF32 backward: component 0's tile R_0[mode][point]
+                mbar_expect_tx(&B->full[s], (uint32_t)a.bwd_bytes);
+                bulk_g2s(dst, src + a.fwd_bytes, (uint32_t)a.bwd_bytes, &B->full[s]);
+            } else {
+                mbar_expect_tx(&B->full[s], nsl * (uint32_t)kHybSlice);
+                for (uint32_t sl = 0; sl < nsl; ++sl)
+                    bulk_g2s(dst + sl * kHybSlice, src + (size_t)sl * kSliceBytes, kHybSlice, &B->full[s]);
+            }
+        }
+        fl[s] = true;
+    };
+    const int64_t ntiles = (a.n_elem + 127) / 128;
     constexpr uint32_t hs16 = kHybSlice >> 4;
+    const uint32_t st16 = stb >> 4;
     // MODE 0: A = U (K-major, 128-byte swizzle), B = the packed slices (K-major)
     const uint64_t dU = tc::smem_desc_sw(smem_addr(sOp), 1024, tc::kSw128);
     const uint64_t dF = tc::smem_desc_sw(smem_addr(sSt), 1024, tc::kSw128);
@@ -663,6 +696,7 @@ __global__ void __launch_bounds__(128) tc_hyb_kernel(const __grid_constant__ Hyb
     const uint64_t dV = tc::smem_desc_sw(smem_addr(sOp), 8 * O::VROW, O::VSW);
     const uint64_t dRt = tc::smem_desc_sw_lbo(smem_addr(sSt), kHybSlice, 1024, tc::kSw128);
     const uint64_t dRb = tc::smem_desc_sw(smem_addr(sSt), 8 * O::VROW, O::VSW);
+    constexpr uint32_t v16 = O::VBYTES >> 4;
     const uint32_t id_f = tc::instr_desc(O::FMT, 128, kNPT);
     const uint32_t n0 = a.NPpad > 256 ? 256u : (uint32_t)a.NPpad, n1 = (uint32_t)a.NPpad - n0;
     // BF16 backward: B operand MN-major (bit 16 of the instruction descriptor)
@@ -670,77 +704,129 @@ __global__ void __launch_bounds__(128) tc_hyb_kernel(const __grid_constant__ Hyb
     const uint32_t id_b0 = tc::instr_desc(O::FMT, 128, n0) | mn, id_b1 = tc::instr_desc(O::FMT, 128, n1 > 0 ? n1 : 16) | mn;
     // start of modes 256.. in the backward operand (16-byte units)
     const uint32_t half16 = ES == 2 ? (256 / 64) * hs16 : (256 * O::VROW) >> 4;
+    const int nch = a.nch, npre = nch < S ? nch : S;
+    bool pre = false;               // the tile's first chunks were issued at the end of the previous tile
+    float x[kNPT];                  // MODE 1: the next chunk's point values of this thread's element
+    auto load_pts = [&](int64_t tl, int k) {
+        const int64_t e = tl * 128 + tid;
+        const bool v = e < a.n_elem;
+        const float* src = v ? a.in + __ldg(a.phys_off + e) : nullptr;
+#pragma unroll
+        for (int p = 0; p < kNPT; ++p) {
+            const int l = k * kNPT + p;
+            x[p] = (v && l < a.NQ) ? __ldg(src + l) : 0.f;
+        }
+    };
     for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
         const int64_t e = tile * 128 + tid;              // this thread's element = TMEM lane
         const bool valid = e < a.n_elem;
+        const int64_t next = tile + gridDim.x;
         if (MODE == 0) {
-            const float* cin = valid ? a.in + a.coeff_off[e] : nullptr;
-            for (int m = 0; m < a.KP; ++m)
-                O::put(sOp + (m / O::KR) * 128 * 128 + O::off128(tid, m % O::KR), (valid && m < a.NP) ? __ldg(cin + m) : 0.f);
+            // U: the tile's coefficient rows, read coalesced (a warp takes 32 rows,
+            // its lanes consecutive modes), rounded to the operand type, zero padded to KP
+            const int per_warp = 32 * a.KP;
+            for (int base = lane; base < per_warp; base += 32 * 8) {
+                float v[8];
+                int row[8], col[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int idx = base + 32 * u;
+                    v[u] = 0.f;
+                    row[u] = -1;
+                    col[u] = 0;
+                    if (idx < per_warp) {
+                        const int rr = idx / a.KP, m = idx - rr * a.KP;
+                        const int64_t er = tile * 128 + warp * 32 + rr;
+                        row[u] = warp * 32 + rr;
+                        col[u] = m;
+                        if (er < a.n_elem && m < a.NP) v[u] = __ldg(a.in + __ldg(a.coeff_off + er) + m);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (row[u] >= 0)
+                        O::put(sOp + (col[u] / O::KR) * 128 * 128 + O::off128((uint32_t)row[u], (uint32_t)(col[u] % O::KR)), v[u]);
+            }
             tc::fence_async_smem();
             __syncthreads();
+        } else if (!pre) {
+            load_pts(tile, 0);
         }
-        for (int k = 0; k < a.nch && ok; ++k) {
-            if (tid == 0) {
-                const unsigned char* src = a.img + (size_t)k * a.chunk_bytes;
-                if (MODE == 1 && ES == 4) {
-                    mbar_expect_tx(&B->full, (uint32_t)a.bwd_bytes);
-                    bulk_g2s(sSt, src + a.fwd_bytes, (uint32_t)a.bwd_bytes, &B->full);
-                } else {
-                    mbar_expect_tx(&B->full, nsl * (uint32_t)kHybSlice);
-                    for (uint32_t sl = 0; sl < nsl; ++sl)
-                        bulk_g2s(sSt + sl * kHybSlice, src + (size_t)sl * kSliceBytes, kHybSlice, &B->full);
-                }
-            }
-            if (MODE == 1) {
-                float x[kNPT];
+        if (!pre)
+            for (int k = 0; k < npre; ++k) issue(k);
+        const int64_t po = valid ? __ldg(a.phys_off + e) : 0;
+        auto store_chunk = [&](int j) {       // MODE 0: chunk j's point values from TMEM buffer j & 1
+            float v[16];
+            tc::ld_32x16(tbase + lane_base + (uint32_t)((j & 1) * kNPT), v);
+            if (valid) {
+                float* o = a.out + po + j * kNPT;
 #pragma unroll
-                for (int p = 0; p < kNPT; ++p) {
-                    const int l = k * kNPT + p;
-                    x[p] = (valid && l < a.NQ) ? __ldg(a.in + a.phys_off[e] + l) : 0.f;
-                }
-                O::template put_pts<kNPT>(sOp, (uint32_t)tid, 0, x);
-                tc::fence_async_smem();
-                __syncthreads();
+                for (int p = 0; p < kNPT; ++p)
+                    if (j * kNPT + p < a.NQ) o[p] = v[p];
             }
-            wait(&B->full, pf);
+        };
+        for (int k = 0; k < nch && ok; ++k) {
+            const int s = k % S;
+            if (MODE == 1) {
+                O::template put_pts<kNPT>(sOp + (size_t)(k & 1) * O::VBYTES, (uint32_t)tid, 0, x);
+                tc::fence_async_smem();
+                if (k + 1 < nch) load_pts(tile, k + 1);
+            }
+            wait_full(s);
             if (!ok) break;
             if (tid == 0) {
                 tc::fence_after();
+                const uint64_t dFs = dF + (uint32_t)s * st16;
                 if (MODE == 0) {
+                    const uint32_t d = tbase + (uint32_t)((k & 1) * kNPT);
                     for (uint32_t sl = 0; sl < nsl; ++sl)
 #pragma unroll
                         for (uint32_t st = 0; st < 4; ++st)
-                            O::mma(tbase, dU + (sl * 1024 + st * 2), dF + (sl * hs16 + st * 2), id_f, sl > 0 || st > 0);
-                } else if (ES == 2) {
-                    O::mma(tbase, dV, dRt, id_b0, k > 0);
-                    if (n1 > 0) O::mma(tbase + 256, dV, dRt + half16, id_b1, k > 0);
+                            O::mma(d, dU + (sl * 1024 + st * 2), dFs + (sl * hs16 + st * 2), id_f, sl > 0 || st > 0);
                 } else {
+                    const uint64_t dVk = dV + (uint32_t)(k & 1) * v16;
+                    if (ES == 2) {
+                        const uint64_t dRs = dRt + (uint32_t)s * st16;
+                        O::mma(tbase, dVk, dRs, id_b0, k > 0);
+                        if (n1 > 0) O::mma(tbase + 256, dVk, dRs + half16, id_b1, k > 0);
+                    } else {
+                        const uint64_t dRs = dRb + (uint32_t)s * st16;
 #pragma unroll
-                    for (uint32_t st = 0; st < O::VROW / 32; ++st) {
-                        O::mma(tbase, dV + st * 2, dRb + st * 2, id_b0, k > 0 || st > 0);
-                        if (n1 > 0) O::mma(tbase + 256, dV + st * 2, dRb + half16 + st * 2, id_b1, k > 0 || st > 0);
+                        for (uint32_t st = 0; st < O::VROW / 32; ++st) {
+                            O::mma(tbase, dVk + st * 2, dRs + st * 2, id_b0, k > 0 || st > 0);
+                            if (n1 > 0) O::mma(tbase + 256, dVk + st * 2, dRs + half16 + st * 2, id_b1, k > 0 || st > 0);
+                        }
                     }
                 }
-                tc::commit(&B->mma);
+                tc::commit(&B->mma[k & 1]);
             }
-            wait(&B->mma, pm);
-            if (!ok) break;
-            tc::fence_after();
-            if (MODE == 0) {
-                float v[16];
-                tc::ld_32x16(tbase + lane_base, v);
-                if (valid) {
-                    float* o = a.out + a.phys_off[e] + k * kNPT;
-#pragma unroll
-                    for (int p = 0; p < kNPT; ++p)
-                        if (k * kNPT + p < a.NQ) o[p] = v[p];
+            ml[k & 1] = true;
+            if (k >= 1) {
+                // MMA k-1 done: its stage takes chunk k-1+S; MODE 0 stores its points
+                wait_mma((k - 1) & 1);
+                if (!ok) break;
+                if (k - 1 + S < nch) issue(k - 1 + S);
+                if (MODE == 0) {
+                    tc::fence_after();
+                    store_chunk(k - 1);
+                    tc::fence_before();
+                    __syncthreads();
                 }
-                tc::fence_before();
-                __syncthreads();
             }
         }
-        if (MODE == 1 && ok) {
+        if (!ok) break;
+        wait_mma((nch - 1) & 1);
+        if (!ok) break;
+        // every stage is free: the next tile's first chunks go in flight now
+        pre = next < ntiles;
+        if (pre) {
+            for (int k = 0; k < npre; ++k) issue(k);
+            if (MODE == 1) load_pts(next, 0);
+        }
+        tc::fence_after();
+        if (MODE == 0) {
+            store_chunk(nch - 1);
+        } else {
             for (int c = 0; c < a.NPpad; c += 16) {
                 float v[16];
                 tc::ld_32x16(tbase + lane_base + (uint32_t)c, v);
@@ -751,9 +837,15 @@ __global__ void __launch_bounds__(128) tc_hyb_kernel(const __grid_constant__ Hyb
                         if (c + i < a.NP) o[i] = v[i];
                 }
             }
-            tc::fence_before();
-            __syncthreads();
         }
+        tc::fence_before();
+        __syncthreads();
+    }
+    if (!ok) {      // nothing may still write shared or tensor memory when the CTA leaves
+        for (int s = 0; s < S; ++s)
+            if (fl[s]) mbar_wait_bounded(&B->full[s], ph_full[s], kWaitLimitNs);
+        for (int b = 0; b < 2; ++b)
+            if (ml[b]) mbar_wait_bounded(&B->mma[b], ph_mma[b], kWaitLimitNs);
     }
     tc::fence_before();
     __syncthreads();
@@ -951,34 +1043,45 @@ int tc_emat_nsplit(const TCArgs& a) {
     return (int)(ns < cap ? ns : cap);
 }
 
-int tc_hyb_smem(int mode, int es, int KP, int NPpad, int bwd_bytes) {
+// shared memory of a hybrid launch with `stages` ring stages (0: the plan's
+// choice, 3 if it fits, else 2); *stages_out, *stage_bytes_out receive the plan
+int tc_hyb_smem(int mode, int es, int KP, int NPpad, int bwd_bytes, int* stages_out, int* stage_bytes_out) {
     const int kr = 128 / es, nsl = (KP + kr - 1) / kr;
-    const int op_bytes = mode == 0 ? 128 * KP * es : 128 * kNPT * es;
-    const int st_bytes = (mode == 1 && es == 4) ? bwd_bytes : nsl * kHybSlice;
-    int smem = 1024 + (op_bytes + 1023) / 1024 * 1024 + st_bytes + 1024;
+    const int op_bytes = mode == 0 ? 128 * KP * es : 2 * 128 * kNPT * es;
+    const int stb = (((mode == 1 && es == 4) ? bwd_bytes : nsl * kHybSlice) + 1023) & ~1023;
+    int st = kHybMaxStages, smem = 0;
+    for (; st >= 2; --st) {
+        smem = 1024 + (op_bytes + 1023) / 1024 * 1024 + st * stb + 1024;
+        if (smem <= 227 * 1024) break;
+    }
     // MODE 1 holds 256 (N_P <= 256) or 512 TMEM columns: shared memory keeps
     // at most two CTAs, or one, on an SM, so that every allocation succeeds at once
     if (mode == 1) smem = std::max(smem, NPpad > 256 ? 120 * 1024 : 80 * 1024);
-    return smem;
+    if (stages_out) *stages_out = st;
+    if (stage_bytes_out) *stage_bytes_out = stb;
+    return st >= 2 ? smem : 0;
 }
 
-cudaError_t tc_hyb_launch(const HybArgs& a, int mode, cudaStream_t s) {
-    const int64_t ntiles = (a.n_elem + 127) / 128;
+cudaError_t tc_hyb_launch(const HybArgs& a0, int mode, cudaStream_t s) {
+    const int64_t ntiles = (a0.n_elem + 127) / 128;
     if (ntiles <= 0) return cudaSuccess;
-    if (a.NPpad > kTcHybMaxModes || a.NPpad % 16 || (a.es != 2 && a.es != 4) || a.nch < 1) return cudaErrorInvalidValue;
-    const int smem = tc_hyb_smem(mode, a.es, a.KP, a.NPpad, a.bwd_bytes);
-    if (smem > 227 * 1024) return cudaErrorInvalidValue;
+    if (a0.NPpad > kTcHybMaxModes || a0.NPpad % 16 || (a0.es != 2 && a0.es != 4) || a0.nch < 1)
+        return cudaErrorInvalidValue;
+    HybArgs a = a0;
+    const int smem = tc_hyb_smem(mode, a.es, a.KP, a.NPpad, a.bwd_bytes, &a.stages, &a.stage_bytes);
+    if (smem <= 0 || smem > 227 * 1024) return cudaErrorInvalidValue;
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
+    // resident CTAs per SM: shared memory (228 KB an SM, 1 KB reserved per CTA),
+    // at most 8, and the tensor memory the CTAs hold (512 columns an SM)
+    const int ncols = mode == 0 ? 32 : (a.NPpad > 256 ? 512 : 256);
+    const int per = std::max(1, std::min({228 * 1024 / (smem + 1024), 8, 512 / ncols}));
     auto launch = [&](auto kern) -> cudaError_t {
         cudaError_t e2 = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e2 != cudaSuccess) return e2;
-        int per = 0;
-        e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 128, smem);
-        if (e2 != cudaSuccess) return e2;
-        const int grid = (int)std::min<int64_t>(ntiles, (int64_t)sms * std::max(per, 1));
+        const int grid = (int)std::min<int64_t>(ntiles, (int64_t)sms * per);
         kern<<<grid, 128, smem, s>>>(a);
         return cudaGetLastError();
     };

@@ -121,7 +121,7 @@ def test_mlp_argument_checks(hp):
 def test_tf32_schedules_only_built_strategies(hp):
     """A TF32 operator has FP32 sum factorisation, the tensor-core elemental
     matrix (blocks of at most 256 modes) and the tensor-core hybrid (at most
-    384): both schedulers choose among those only, never a stored matrix."""
+    352): both schedulers choose among those only, never a stored matrix."""
     from oracle.basis import n_modes
     mesh = inputs.slab_mesh(2, 2, 4, (2, 9), order_seed=5, curved_rule="x_half")
     keys = []
@@ -130,7 +130,7 @@ def test_tf32_schedules_only_built_strategies(hp):
             keys.append(k)
     nb = len(keys)
     fits = np.array([n_modes(s, P) <= 256 for s, P, _ in keys])
-    fits_h = np.array([n_modes(s, P) <= 384 for s, P, _ in keys])
+    fits_h = np.array([n_modes(s, P) <= 352 for s, P, _ in keys])
     assert (fits_h & ~fits).any() and (~fits_h).any()
     h = hp.hp_mesh_create(mesh, 0)
     m = hp.hp_mlp_create(5, 32, 3, seed=1)
@@ -160,7 +160,7 @@ def test_tf32_schedules_only_built_strategies(hp):
 def test_graph_schedule_keeps_valid_strategies_and_results(hp):
     """The graph-aware search chooses only strategies built for each block (TF32:
     FP32 sum factorisation, the tensor-core elemental matrix up to 256 modes
-    or the tensor-core hybrid up to 384), returns a positive graph time,
+    or the tensor-core hybrid up to 352), returns a positive graph time,
     rejects bad arguments, and the scheduled graph still matches the FP64
     oracle within each block's bound (TF32_TOL on tensor-core blocks, the FP32
     bound elsewhere)."""
@@ -175,7 +175,7 @@ def test_graph_schedule_keeps_valid_strategies_and_results(hp):
             keys.append(k)
     nb = len(keys)
     fits = np.array([n_modes(s, P) <= 256 for s, P, _ in keys])
-    fits_h = np.array([n_modes(s, P) <= 384 for s, P, _ in keys])
+    fits_h = np.array([n_modes(s, P) <= 352 for s, P, _ in keys])
     h = hp.hp_mesh_create(mesh, 0)
     try:
         co, po, nc, nph = hp.hp_mesh_layout(h, mesh["n_elem"])

@@ -120,7 +120,7 @@ def test_tf32_strategy_per_block(hp):
         with pytest.raises(hp.HpError) as ei:       # stored matrices are FP64 / FP32 only
             hp.hp_op_strategies(op, len(keys), np.full(len(keys), hp.HP_STRAT_MATRIX))
         assert ei.value.status == hp.HP_ERR_UNSUPPORTED
-        # the tensor-core hybrid covers every block here (N_P <= 343 <= 384)
+        # the tensor-core hybrid covers every block here (N_P <= 343 <= 352)
         hp.hp_op_strategies(op, len(keys), np.full(len(keys), hp.HP_STRAT_HYBRID))
         assert (hp.hp_op_strategies(op, len(keys)) == hp.HP_STRAT_HYBRID).all()
         hp.hp_op_destroy(op)
