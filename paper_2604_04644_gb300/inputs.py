@@ -209,6 +209,55 @@ def replicated_mesh(shape, order, n_elem, *, curved=True, deformation=1):
 
 
 # ---------------------------------------------------------------------------
+# two-dimensional meshes (quadrilaterals and triangles)
+# ---------------------------------------------------------------------------
+QUAD, TRI = 4, 5
+
+
+def square_mesh_2d(nx, ny, order, *, cells="checker", curved=True, deformation=1, order_seed=None,
+                   curved_rule=None):
+    """nx*ny cells of the unit square; a cell is one quadrilateral or two
+    triangles (cut along its (1,0)-(0,1) diagonal): ``cells`` = "checker"
+    (quadrilateral where i + j is even), "quad" or "tri".  Vertex order:
+    quadrilateral (0,0) (1,0) (1,1) (0,1) of the cell; triangles (0,0) (1,0)
+    (0,1) and (1,1) (0,1) (1,0) -- vertex 0 and its neighbours along xi_1 and
+    xi_2 come first, counter-clockwise.  order / order_seed / curved /
+    curved_rule as for slab_mesh (x_half: cell centre x >= 0.5 curved)."""
+    gid = lambda i, j: j * (nx + 1) + i
+    xs, ys = np.meshgrid(np.arange(nx + 1) / nx, np.arange(ny + 1) / ny, indexing="xy")
+    xy = np.stack([xs.ravel(), ys.ravel()], axis=1)
+    shapes, verts, cc = [], [], []
+    for j in range(ny):
+        for i in range(nx):
+            c = ((i + 0.5) / nx, (j + 0.5) / ny)
+            quad = cells == "quad" or (cells == "checker" and (i + j) % 2 == 0)
+            if quad:
+                shapes.append(QUAD)
+                verts.append([gid(i, j), gid(i + 1, j), gid(i + 1, j + 1), gid(i, j + 1)])
+                cc.append(c)
+            else:
+                for t in ([gid(i, j), gid(i + 1, j), gid(i, j + 1), -1],
+                          [gid(i + 1, j + 1), gid(i, j + 1), gid(i + 1, j), -1]):
+                    shapes.append(TRI)
+                    verts.append(t)
+                    cc.append(c)
+    n_elem = len(shapes)
+    if isinstance(order, tuple):
+        rng = np.random.default_rng(order_seed)
+        P_arr = rng.integers(order[0], order[1] + 1, size=n_elem).astype(np.uint8)
+    else:
+        P_arr = np.full(n_elem, int(order), dtype=np.uint8)
+    cc = np.array(cc)
+    if curved_rule == "x_half":
+        curved_arr = (cc[:, 0] >= 0.5).astype(np.uint8)
+    else:
+        curved_arr = np.full(n_elem, 1 if curved else 0, dtype=np.uint8)
+    return dict(n_elem=n_elem, shape=np.array(shapes, dtype=np.uint8), P=P_arr,
+                vert=np.array(verts, dtype=np.int64), xy=np.ascontiguousarray(xy, dtype=np.float64),
+                n_vert=int(xy.shape[0]), curved=curved_arr, deformation=int(deformation))
+
+
+# ---------------------------------------------------------------------------
 # counter-based random numbers (SplitMix64, Steele, Lea & Flood 2014)
 # ---------------------------------------------------------------------------
 _M64 = np.uint64(0xFFFFFFFFFFFFFFFF)
