@@ -581,6 +581,73 @@ hp_status hp_op_block_work(hp_op op, int64_t block, int64_t* n_elem, int64_t* ou
  * the kernels one by one.  Errors as hp_op_apply, HP_ERR_ARG for a bad block. */
 hp_status hp_op_apply_block(hp_op op, int64_t block, double lambda, const void* in, void* out, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Two-dimensional formulation (paper Sec. 2.2): quadrilaterals (HP_QUAD) and
+ * triangles (HP_TRI) with the modified C0 basis on (collapsed) coordinates
+ * -- quadrilateral A_a(xi_1) A_b(xi_2), triangle A_a(eta_1) W_{w(a),b}(eta_2)
+ * on eta_1 = 2 (1 + xi_1)/(1 - xi_2) - 1 -- Q = P + 2 points per direction
+ * (Gauss-Lobatto-Legendre; Gauss-Radau-Jacobi alpha = 1 in the triangle's
+ * eta_2), and the mass, Laplacian and Helmholtz operators by the collocated
+ * algorithm (Eq. helm1 in two dimensions): two sum-factorised passes for B
+ * and B^T, collocation derivatives along the point lines, pointwise metric.
+ * Mode order: by the slot key (a, b), b fastest (a: L or 1 -> 0, R -> 1,
+ * psi_n -> n + 1; b the same on the second factor, or the warped-family
+ * index r when a is a bubble of the triangle).  Points (i, j), j fastest.
+ * ------------------------------------------------------------------------ */
+typedef struct hp_mesh2d_s* hp_mesh2d;
+enum { HP_QUAD = 4, HP_TRI = 5 };
+
+/* Two-dimensional mesh (copied by hp_mesh2d_create):
+ *   shape[n_elem]        HP_QUAD or HP_TRI
+ *   P[n_elem]            polynomial order 1..10 (Q = P + 2)
+ *   vert[n_elem * 4]     vertex ids; vertex 0 and its neighbours along xi_1 and
+ *                        xi_2 are ids 0, 1 and 3 (quadrilateral, a parallelogram:
+ *                        id 2 is not read by the affine map) or 0, 1, 2 (triangle;
+ *                        id 3 ignored)
+ *   xy[2 * n_vert]       vertex coordinates
+ *   curved[n_elem]       1: apply the deformation to the element map
+ *   deformation          0 none, 1 x_i += 0.05 sin(pi x_1) sin(pi x_2) (i = 1, 2;
+ *                        fixes the boundary of the unit square) */
+typedef struct {
+    int64_t n_elem;
+    const uint8_t* shape;
+    const uint8_t* P;
+    const int64_t* vert;
+    const double* xy;
+    int64_t n_vert;
+    const uint8_t* curved;
+    int32_t deformation;
+} hp_mesh2d_desc;
+
+/* Build the mesh on `device`: blocks of equal (shape, P, curved), reference
+ * tables, and the FP64 metric factors G11, G12, G22, w|J| at every point (FP32
+ * copy).  Synchronises the device.  Errors: HP_ERR_ARG (null or empty arrays,
+ * shape, order or vertex id out of range, deformation not 0 / 1),
+ * HP_ERR_GEOM (|J| <= 0 at a point), HP_ERR_CUDA / HP_ERR_OOM. */
+hp_status hp_mesh2d_create(const hp_mesh2d_desc* desc, int device, hp_mesh2d* out);
+
+/* Element offsets (n_elem + 1 each, may be NULL) of the modal vectors (N_P =
+ * (P+1)^2 or (P+1)(P+2)/2 per element) and of the point vectors (Q^2). */
+hp_status hp_mesh2d_layout(hp_mesh2d mesh, int64_t* coeff_offset, int64_t* phys_offset);
+
+/* out = operator(in) for kind HP_MASS, HP_LAPLACIAN or HP_HELMHOLTZ (lambda:
+ * the Helmholtz constant), dtype HP_FP64 (double arrays) or HP_FP32 (float
+ * arrays, FP32 factors and tables); in and out are device modal vectors of
+ * the layout above, caller-owned, not aliased.  Asynchronous on `stream`
+ * (NULL: the legacy default stream).  Errors: HP_ERR_ARG, HP_ERR_UNSUPPORTED
+ * (another kind or dtype), HP_ERR_CUDA. */
+hp_status hp_op2d_apply(hp_mesh2d mesh, hp_opkind kind, hp_dtype dtype, double lambda, const void* in, void* out,
+                        void* stream);
+
+/* Copy the FP64 metric factors to host memory: host_out[4 * phys_offset[e] +
+ * f * Q^2 + l] for factor f = G11, G12, G22, w|J| of element e at point l.
+ * Synchronous.  Errors: HP_ERR_ARG, HP_ERR_CUDA. */
+hp_status hp_mesh2d_factors(hp_mesh2d mesh, double* host_out);
+
+/* Wait for `stream` and report an asynchronous CUDA error.  Errors: HP_ERR_ARG, HP_ERR_CUDA. */
+hp_status hp_mesh2d_sync(hp_mesh2d mesh, void* stream);
+void hp_mesh2d_destroy(hp_mesh2d mesh);
+
 void hp_op_destroy(hp_op op);
 void hp_mesh_destroy(hp_mesh mesh);
 const char* hp_status_str(hp_status s);

@@ -40,7 +40,9 @@ EXPORTED = ["hp_mesh_create", "hp_mesh_layout", "hp_geom_factors", "hp_geom_copy
             "hp_c0_map_host", "hp_c0_maps", "hp_c0_gather", "hp_c0_assemble", "hp_solve", "hp_c0_destroy", "hp_c0_diagonal",
             "hp_partition", "hp_halo_create", "hp_halo_info", "hp_halo_counts", "hp_halo_maps", "hp_halo_gather",
             "hp_halo_reduce_pack", "hp_halo_reduce_sum", "hp_halo_bcast_pack", "hp_halo_bcast_unpack",
-            "hp_halo_destroy", "hp_xdot_acc", "hp_xacc_round", "hp_xacc_limbs"]
+            "hp_halo_destroy", "hp_xdot_acc", "hp_xacc_round", "hp_xacc_limbs",
+            "hp_mesh2d_create", "hp_mesh2d_layout", "hp_op2d_apply", "hp_mesh2d_factors", "hp_mesh2d_sync",
+            "hp_mesh2d_destroy"]
 
 
 class HpError(RuntimeError):
@@ -55,6 +57,12 @@ class hp_mesh_desc(ctypes.Structure):
                 ("Q", ctypes.c_void_p), ("vert", ctypes.c_void_p), ("xyz", ctypes.c_void_p),
                 ("n_vert", ctypes.c_int64), ("curved", ctypes.c_void_p), ("deformation", ctypes.c_int32),
                 ("geometry", ctypes.c_int32)]
+
+
+class hp_mesh2d_desc(ctypes.Structure):
+    _fields_ = [("n_elem", ctypes.c_int64), ("shape", ctypes.c_void_p), ("P", ctypes.c_void_p),
+                ("vert", ctypes.c_void_p), ("xy", ctypes.c_void_p), ("n_vert", ctypes.c_int64),
+                ("curved", ctypes.c_void_p), ("deformation", ctypes.c_int32)]
 
 
 _vp, _i64p, _dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)
@@ -99,6 +107,13 @@ _lib.hp_op_apply_block.argtypes = [_vp, ctypes.c_int64, ctypes.c_double, _vp, _v
 _lib.hp_peak_fp64.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, _vp]
 _lib.hp_peak_fp64.restype = ctypes.c_int
 _lib.hp_op_destroy.argtypes = [_vp]
+_lib.hp_mesh2d_create.argtypes = [ctypes.POINTER(hp_mesh2d_desc), ctypes.c_int, ctypes.POINTER(_vp)]
+_lib.hp_mesh2d_layout.argtypes = [_vp, _vp, _vp]
+_lib.hp_op2d_apply.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, _vp, _vp, _vp]
+_lib.hp_mesh2d_factors.argtypes = [_vp, _vp]
+_lib.hp_mesh2d_sync.argtypes = [_vp, _vp]
+_lib.hp_mesh2d_destroy.argtypes = [_vp]
+_lib.hp_mesh2d_destroy.restype = None
 _lib.hp_mesh_destroy.argtypes = [_vp]
 _lib.hp_status_str.argtypes = [ctypes.c_int]
 _lib.hp_status_str.restype = ctypes.c_char_p
@@ -153,6 +168,50 @@ def hp_mesh_create(mesh, device=0):
     h = _vp()
     _check(_lib.hp_mesh_create(ctypes.byref(d), int(device), ctypes.byref(h)), "hp_mesh_create")
     return h.value
+
+
+HP_QUAD, HP_TRI = 4, 5
+
+
+def hp_mesh2d_create(mesh, device=0):
+    """mesh: dict with the hp_mesh2d_desc arrays (see inputs.square_mesh_2d)."""
+    keep = dict(shape=np.ascontiguousarray(mesh["shape"], dtype=np.uint8),
+                P=np.ascontiguousarray(mesh["P"], dtype=np.uint8),
+                vert=np.ascontiguousarray(mesh["vert"], dtype=np.int64),
+                xy=np.ascontiguousarray(mesh["xy"], dtype=np.float64),
+                curved=np.ascontiguousarray(mesh["curved"], dtype=np.uint8))
+    d = hp_mesh2d_desc(int(mesh["n_elem"]), keep["shape"].ctypes.data, keep["P"].ctypes.data, keep["vert"].ctypes.data,
+                       keep["xy"].ctypes.data, int(keep["xy"].shape[0]), keep["curved"].ctypes.data,
+                       int(mesh["deformation"]))
+    h = _vp()
+    _check(_lib.hp_mesh2d_create(ctypes.byref(d), int(device), ctypes.byref(h)), "hp_mesh2d_create")
+    return h.value
+
+
+def hp_mesh2d_layout(mesh, n_elem):
+    co = np.zeros(n_elem + 1, dtype=np.int64)
+    po = np.zeros(n_elem + 1, dtype=np.int64)
+    _check(_lib.hp_mesh2d_layout(mesh, co.ctypes.data, po.ctypes.data), "hp_mesh2d_layout")
+    return co, po
+
+
+def hp_op2d_apply(mesh, kind, dtype, lam, x, y, stream=None):
+    _check(_lib.hp_op2d_apply(mesh, int(kind), int(dtype), float(lam), _ptr(x), _ptr(y), _stream(stream)),
+           "hp_op2d_apply")
+
+
+def hp_mesh2d_factors(mesh, n_phys):
+    out = np.zeros(4 * int(n_phys), dtype=np.float64)
+    _check(_lib.hp_mesh2d_factors(mesh, out.ctypes.data), "hp_mesh2d_factors")
+    return out
+
+
+def hp_mesh2d_sync(mesh, stream=None):
+    _check(_lib.hp_mesh2d_sync(mesh, _stream(stream)), "hp_mesh2d_sync")
+
+
+def hp_mesh2d_destroy(mesh):
+    _lib.hp_mesh2d_destroy(mesh)
 
 
 def hp_mesh_layout(mesh, n_elem):

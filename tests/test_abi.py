@@ -71,3 +71,23 @@ def test_binding_constants_match_header():
     assert values["HP_STRAT_MATRIX"] == 4 and values["HP_STRAT_AUTO"] == 3
     for name, v in values.items():
         assert getattr(hp, name) == v, name
+
+
+def test_mesh2d_arguments_are_checked_without_gpu(lib):
+    from paper_2604_04644_gb300 import hp, inputs
+    lib.hp_mesh2d_create.restype = ctypes.c_int
+    assert lib.hp_mesh2d_create(None, 0, None) == 1
+    mesh = inputs.square_mesh_2d(2, 1, 3)
+    for key, val in (("shape", 3), ("P", 11)):
+        bad = dict(mesh)
+        bad[key] = mesh[key].copy()
+        bad[key][0] = val
+        with pytest.raises(hp.HpError) as ei:
+            hp.hp_mesh2d_create(bad, 0)
+        assert ei.value.status == hp.HP_ERR_ARG
+    bad = dict(mesh)
+    bad["vert"] = mesh["vert"].copy()
+    bad["vert"][0, 0] = mesh["n_vert"]
+    with pytest.raises(hp.HpError) as ei:
+        hp.hp_mesh2d_create(bad, 0)
+    assert ei.value.status == hp.HP_ERR_ARG
