@@ -99,6 +99,9 @@ def parse():
     p.add_argument("--block-table", action="store_true",
                    help="GDOF/s of FP32 sum factorisation and the TF32 / BF16 tensor-core operator on large "
                         "single-shape blocks instead")
+    p.add_argument("--two-d", action="store_true",
+                   help="GDOF/s of the two-dimensional quadrilateral / triangle Helmholtz operator (FP64, FP32) "
+                        "instead")
     p.add_argument("--collocation-study", action="store_true",
                    help="GDOF/s of the collocated and the non-collocated FP64 sum-factorised Helmholtz on "
                         "regular (affine) single-shape blocks, P = 1..8, instead")
@@ -932,6 +935,53 @@ def run_block_table(local, reps=10):
             print(json.dumps({"block_table": line}), flush=True)
 
 
+# two-dimensional blocks: (cells, P, cells per side of the unit square)
+TWO_D = [("quad", 2, 500), ("quad", 4, 400), ("quad", 8, 250), ("tri", 2, 400), ("tri", 4, 300), ("tri", 8, 200)]
+
+
+def run_two_d(local, reps=10):
+    """The paper's two-dimensional formulation (Sec. 2.2) on this GPU:
+    Helmholtz GDOF/s of the collocated sum factorisation on curved
+    quadrilateral / triangle meshes of the unit square, FP64 and FP32 (L2
+    flushed before every apply; median of `reps`), with the FP64 rate against
+    the measured FP64 FMA peak (flops: the passes the kernel runs, FMA = 2)."""
+    import torch
+    from paper_2604_04644_gb300 import hp, inputs
+    torch.cuda.set_device(local)
+    dev = "cuda:%d" % local
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    for cells, P, nx in TWO_D:
+        mesh = inputs.square_mesh_2d(nx, nx, P, cells=cells, curved=True)
+        h = hp.hp_mesh2d_create(mesh, local)
+        co, po = hp.hp_mesh2d_layout(h, mesh["n_elem"])
+        n, Q = P + 1, P + 2
+        rows = n * n if cells == "quad" else (2 * n + sum(P - f for f in range(1, P)))
+        # FMAs per element: eta_2 / eta_1 passes of B and B^T, two collocation
+        # derivatives and their transposes, the metric (5) and the mass term (2)
+        fma = 2 * (rows * Q + n * Q * Q) + 4 * Q * Q * Q + 7 * Q * Q
+        line = {"shape": cells, "P": P, "elements": int(mesh["n_elem"]), "dofs": int(co[-1])}
+        for name, dt, tdt in (("fp64", hp.HP_FP64, torch.float64), ("fp32", hp.HP_FP32, torch.float32)):
+            x = torch.rand(int(co[-1]), device=dev, dtype=tdt)
+            y = torch.empty_like(x)
+            for _ in range(3):
+                hp.hp_op2d_apply(h, hp.HP_HELMHOLTZ, dt, 1.0, x, y)
+            ts = []
+            for _ in range(reps):
+                flush.zero_()
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record()
+                hp.hp_op2d_apply(h, hp.HP_HELMHOLTZ, dt, 1.0, x, y)
+                b.record()
+                b.synchronize()
+                ts.append(a.elapsed_time(b))
+            ms = statistics.median(ts)
+            line[name + "_gdofs"] = round(co[-1] / (ms * 1e-3) / 1e9, 2)
+            line[name + "_tflops"] = round(2.0 * fma * mesh["n_elem"] / (ms * 1e-3) / 1e12, 3)
+        hp.hp_mesh2d_destroy(h)
+        print(json.dumps({"two_d": line}), flush=True)
+
+
 def run_collocation_study(local, reps=10):
     """The paper's collocation study (Sec. 5) on this GPU: FP64 Helmholtz
     GDOF/s of the collocated sum factorisation (derivatives by collocation at
@@ -1079,6 +1129,10 @@ def main():
     if args.block_table:
         if rank == 0:
             run_block_table(local)
+        return
+    if args.two_d:
+        if rank == 0:
+            run_two_d(local)
         return
     if args.collocation_study:
         if rank == 0:
