@@ -1038,7 +1038,10 @@ int tc_emat_nsplit(const TCArgs& a) {
         return 0;
     const TcPlan pl = tc_plan(a.KP, a.NPpad, a.stage_bytes, a.es, ntiles >= 2 * (int64_t)sms);
     if (pl.stages == 0) return 0;
-    const int64_t ns = ((int64_t)sms * pl.ctas + ntiles - 1) / ntiles;
+    // parts per tile: as many as keep every work item in one wave of the
+    // launch's CTA slots (a ceiling would leave some CTAs a second item, and
+    // the launch twice an item's time), at least four chunks a part
+    const int64_t ns = std::max<int64_t>(1, (int64_t)sms * pl.ctas / ntiles);
     const int64_t cap = a.nch / 4 > 1 ? a.nch / 4 : 1;
     return (int)(ns < cap ? ns : cap);
 }
