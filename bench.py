@@ -1036,7 +1036,8 @@ def run_collocation_study(local, reps=10):
 def run_matrix_study(local, reps=10):
     """Matrix-based (stored per-element dense H^e, HP_STRAT_MATRIX) against
     matrix-free sum factorisation: Helmholtz GDOF/s in FP64 and FP32 on curved
-    single-shape blocks of about four million DOFs, P = 1..5 (blocks of at most
+    single-shape blocks of about four million DOFs and at least 256 MB of FP32
+    stored matrices and vectors, P = 1..5 (blocks of at most
     256 modes), with the build time, the stored bytes and the stored-matrix
     apply's HBM rate against the measured copy bandwidth (L2 flushed before
     every apply; median of `reps`). One JSON line per (shape, P)."""
@@ -1069,7 +1070,9 @@ def run_matrix_study(local, reps=10):
             NP = N_MODES[shape](P)
             if NP > 256:
                 continue
-            n = min(200000, max(4096, int(4e6 / NP)))
+            # about four million DOFs, and at least 256 MB (twice L2) of stored
+            # FP32 matrices, coefficients and offsets, at most four million elements
+            n = min(4000000, max(4096, int(4e6 / NP), int(256e6 / (4 * NP * NP + 8 * NP + 8))))
             mesh = inputs.replicated_mesh(shape, P, n, curved=True)
             h = hp.hp_mesh_create(mesh, local)
             co, po, nc, nph = hp.hp_mesh_layout(h, mesh["n_elem"])
