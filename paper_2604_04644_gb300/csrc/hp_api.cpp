@@ -657,6 +657,10 @@ cudaError_t launch_block(hp_op op, size_t bi, int tile, double lambda, const voi
         // backward MMAs); TF32: forward slices and backward tiles separately
         a.stage_bytes = bf ? a.fwd_bytes : (std::max(4 * tc_chunk_points() * 128, a.bwd_bytes) + 1023) & ~1023;
         a.err = op->d_err;
+        // split for the graph's share: BF16 always; TF32 up to 16 point chunks
+        // (measured on the 16^3 mesh: TF32 at P = 5..7 ran 9-13 % slower
+        // unsplit, where its longer chunks keep more CTAs busy when split)
+        a.concurrent_tiles = (bf || a.nch <= 16) ? op->tc_concurrent_tiles : 0;
         a.part_out = nullptr;
         if (op->deterministic) {   // split tiles: partial outputs in a scratch of the op, summed in part order
             const int ns = tc_emat_nsplit(a);
@@ -1300,6 +1304,17 @@ hp_status hp_op_apply_graph(hp_op op, double lambda, const void* in, void* out, 
     if (!op->graph || op->g_in != in || op->g_out != out || op->g_lambda != lambda) {
         if (op->graph) { cudaGraphExecDestroy(op->graph); op->graph = nullptr; }
         const size_t nb = op->mesh->blocks.size();
+        // the tensor-core blocks run concurrently in the graph: each splits its
+        // tiles for its share of the GPU (the warm-up launches below size the
+        // deterministic scratch with the same split)
+        struct ResetTiles {
+            hp_op o;
+            ~ResetTiles() { o->tc_concurrent_tiles = 0; }
+        } reset_tiles{op};
+        op->tc_concurrent_tiles = 0;
+        if (op->dtype == HP_TF32 || op->dtype == HP_BF16)
+            for (size_t i = 0; i < nb; ++i)
+                if (op->strat[i] == HP_STRAT_ELEMAT) op->tc_concurrent_tiles += (op->mesh->blocks[i].n_elem + 127) / 128;
         // first launches set kernel attributes outside the capture
         for (size_t i = 0; i < nb; ++i) {
             cudaError_t e = launch_block(op, i, op->tile[i], lambda, in, out, s);

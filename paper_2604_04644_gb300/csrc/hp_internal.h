@@ -129,6 +129,9 @@ struct hp_op_s {
     void* d_items = nullptr;                    // WorkItem list, by decreasing cost
     int* d_next = nullptr;                      // work-list counter
     int n_items = 0, wl_smem = 0, wl_grid = 0;
+    // while a graph of all blocks is captured: the tensor-core elemental-matrix
+    // blocks' total tile count, so that each splits its tiles for its share of the GPU
+    int64_t tc_concurrent_tiles = 0;
     // tensor-core hybrid blocks: u = B uhat and u' at every point of the mesh's
     // point layout (two FP32 vectors; blocks write disjoint ranges)
     float* hyb_u = nullptr;
@@ -235,6 +238,7 @@ struct TCArgs {
     int fwd_bytes, bwd_bytes, stage_bytes;
     int es;                            // operand bytes: 4 TF32, 2 BF16
     int nsplit, stages, ubufs;         // set by the launcher
+    int64_t concurrent_tiles;          // tiles of all tensor-core blocks launched together (0: this block alone)
     float* part_out;                   // nullptr: split tiles add with atomics; else [nsplit][n_elem][NP]
                                        // partial outputs summed in part order (deterministic)
     unsigned int* err;

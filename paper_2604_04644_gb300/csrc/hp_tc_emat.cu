@@ -1041,7 +1041,8 @@ int tc_emat_nsplit(const TCArgs& a) {
     // parts per tile: as many as keep every work item in one wave of the
     // launch's CTA slots (a ceiling would leave some CTAs a second item, and
     // the launch twice an item's time), at least four chunks a part
-    const int64_t ns = std::max<int64_t>(1, (int64_t)sms * pl.ctas / ntiles);
+    // (blocks launched together in a graph share the slots by their tiles)
+    const int64_t ns = std::max<int64_t>(1, (int64_t)sms * pl.ctas / std::max<int64_t>(ntiles, a.concurrent_tiles));
     const int64_t cap = a.nch / 4 > 1 ? a.nch / 4 : 1;
     return (int)(ns < cap ? ns : cap);
 }
