@@ -34,9 +34,10 @@ from .geometry import AXIS_VERTS, deform
 
 
 @lru_cache(maxsize=None)
-def reference(shape, P, Q):
-    """Reference-element data at the quadrature points of (shape, P, Q)."""
-    rule = quadrature.shape_rule(shape, Q)
+def reference(shape, P, Q, reduced=0):
+    """Reference-element data at the quadrature points of (shape, P, Q);
+    reduced = 1: Q - 1 points in the collapsed directions."""
+    rule = quadrature.shape_rule(shape, Q, reduced)
     (x1, w1), (x2, w2), (x3, w3) = rule
     e1, e2, e3 = np.meshgrid(x1, x2, x3, indexing="ij")
     eta = np.stack([e1.ravel(), e2.ravel(), e3.ravel()])
@@ -50,7 +51,7 @@ def reference(shape, P, Q):
                  axis=-1).transpose(1, 0, 2)
     D1 = [lagrange_derivative_matrix(x) for x in (x1, x2, x3)]
     return dict(eta=eta, xi=xi, W=W, B=B, Dxi=Dxi, T=T, nodes=(x1, x2, x3), D1=D1,
-                NP=B.shape[1], NQ=B.shape[0], Q=Q)
+                NP=B.shape[1], NQ=B.shape[0], Q=Q, dims=(len(x1), len(x2), len(x3)))
 
 
 def lagrange_derivative_matrix(x):
@@ -133,11 +134,13 @@ def isoparametric_jacobian(shape, P, Q, X, curved, kind):
     return np.einsum("elcd,lda->elca", Jeta, ref["T"])
 
 
-def block_metrics(shape, P, Q, X, curved, kind, geometry=0):
+def block_metrics(shape, P, Q, X, curved, kind, geometry=0, reduced=0):
     """J, det J, J^{-1} and w|J| at the points; geometry 1 takes J from the
     iso-parametric map of curved elements (affine maps are in the span of
     every expansion, so their iso-parametric map is the map itself)."""
-    ref = reference(shape, P, Q)
+    ref = reference(shape, P, Q, reduced)
+    if geometry == 1 and curved and reduced:
+        raise ValueError("the iso-parametric geometry is defined on the full rule")
     if geometry == 1 and curved:
         J = isoparametric_jacobian(shape, P, Q, X, curved, kind)
     else:
@@ -163,9 +166,9 @@ def _iprod_grad(ref, g, f):
     return sum(t[d] @ ref["Dxi"][d] for d in range(3))
 
 
-def apply_block(op, shape, P, Q, X, curved, kind, data, lam=1.0, geometry=0, adv=None):
-    ref = reference(shape, P, Q)
-    g = block_metrics(shape, P, Q, X, curved, kind, geometry)
+def apply_block(op, shape, P, Q, X, curved, kind, data, lam=1.0, geometry=0, adv=None, reduced=0):
+    ref = reference(shape, P, Q, reduced)
+    g = block_metrics(shape, P, Q, X, curved, kind, geometry, reduced)
     B = ref["B"]
     if op == "adr":
         return (lam * ((g["wJ"] * (data @ B.T)) @ B) + _iprod_grad(ref, g, _grad_x(ref, g, data))
@@ -209,8 +212,7 @@ def element_advection_matrices(shape, P, Q, X, curved, kind, adv, geometry=0):
 
 def _eta_derivs(ref, u):
     """d u / d eta_d of the tensor Lagrange interpolant: (3, Ne, NQ)."""
-    Q = ref["Q"]
-    U = u.reshape(-1, Q, Q, Q)
+    U = u.reshape(-1, *ref["dims"])
     D1, D2, D3 = ref["D1"]
     v1 = np.einsum("im,emjk->eijk", D1, U)
     v2 = np.einsum("jm,eimk->eijk", D2, U)
@@ -230,7 +232,6 @@ def phys_deriv_block(ref, g, u):
 
 def helmholtz_collocated_block(ref, g, uh, lam):
     """Eq. (helm1): B^T { sum_i [sum_d D_d^T Lam_di] W [sum_d' Lam_d'i D_d'] + lam W } B."""
-    Q = ref["Q"]
     u = uh @ ref["B"].T
     v = _eta_derivs(ref, u)
     Gx = _deta_dx(ref, g)
@@ -238,17 +239,17 @@ def helmholtz_collocated_block(ref, g, uh, lam):
     # w_d = sum_d' G_dd' v_d'
     w = np.stack([sum(G[:, :, d, e] * v[e] for e in range(3)) for d in range(3)])
     D1, D2, D3 = ref["D1"]
-    W1, W2, W3 = (x.reshape(-1, Q, Q, Q) for x in w)
+    W1, W2, W3 = (x.reshape(-1, *ref["dims"]) for x in w)
     up = (np.einsum("mi,emjk->eijk", D1, W1) + np.einsum("mj,eimk->eijk", D2, W2)
           + np.einsum("mk,eijm->eijk", D3, W3)).reshape(u.shape)
     up = up + lam * g["wJ"] * u
     return up @ ref["B"]
 
 
-def element_matrices(shape, P, Q, X, curved, kind, geometry=0):
+def element_matrices(shape, P, Q, X, curved, kind, geometry=0, reduced=0):
     """Explicit (M, L) of each element of the block: (Ne, NP, NP) each."""
-    ref = reference(shape, P, Q)
-    g = block_metrics(shape, P, Q, X, curved, kind, geometry)
+    ref = reference(shape, P, Q, reduced)
+    g = block_metrics(shape, P, Q, X, curved, kind, geometry, reduced)
     B = ref["B"]
     M = np.einsum("lm,el,ln->emn", B, g["wJ"], B)
     Gx = np.einsum("eldi,dlm->eilm", g["Jinv"], np.stack(ref["Dxi"]))    # d phi_m / d x_i at l
@@ -256,11 +257,11 @@ def element_matrices(shape, P, Q, X, curved, kind, geometry=0):
     return M, L
 
 
-def geometric_factors_block(shape, P, Q, X, curved, kind, geometry=0):
+def geometric_factors_block(shape, P, Q, X, curved, kind, geometry=0, reduced=0):
     """Per point: G_dd' = w|J| sum_i (d eta_d/dx_i)(d eta_d'/dx_i) (6: 11,12,13,22,23,33),
     w|J|, and d eta_d / d x_i (9, row-major d then i)."""
-    ref = reference(shape, P, Q)
-    g = block_metrics(shape, P, Q, X, curved, kind, geometry)
+    ref = reference(shape, P, Q, reduced)
+    g = block_metrics(shape, P, Q, X, curved, kind, geometry, reduced)
     Gx = _deta_dx(ref, g)
     G = np.einsum("el,eldi,elki->eldk", g["wJ"], Gx, Gx)
     six = np.stack([G[:, :, 0, 0], G[:, :, 0, 1], G[:, :, 0, 2], G[:, :, 1, 1], G[:, :, 1, 2], G[:, :, 2, 2],
@@ -272,13 +273,23 @@ def geometric_factors_block(shape, P, Q, X, curved, kind, geometry=0):
 # ---------------------------------------------------------------------------
 # mesh level (ragged vectors in user element order)
 # ---------------------------------------------------------------------------
+def n_points(shape, Q, reduced=0):
+    """Quadrature points of an element: Q^3, or with the reduced rule Q - 1 in
+    the collapsed directions (prism and pyramid eta_3, tetrahedron eta_2 and eta_3)."""
+    Q = int(Q)
+    if not reduced or shape == 0:
+        return Q ** 3
+    return Q * Q * (Q - 1) if shape in (1, 2) else Q * (Q - 1) ** 2
+
+
 def layout(mesh):
     shape = mesh["shape"].astype(int)
     P = mesh["P"].astype(int)
     Q = mesh["Q"].astype(int)
     npm = np.array([basis.n_modes(s, p) for s, p in zip(shape, P)], dtype=np.int64)
     coeff = np.concatenate([[0], np.cumsum(npm)]).astype(np.int64)
-    phys = np.concatenate([[0], np.cumsum(Q.astype(np.int64) ** 3)]).astype(np.int64)
+    phys = np.concatenate([[0], np.cumsum([n_points(s, q, mesh.get("quadrature", 0))
+                                           for s, q in zip(shape, Q)])]).astype(np.int64)
     return coeff, phys
 
 
@@ -328,7 +339,8 @@ def apply(op, mesh, data, lam=1.0, elems=None, adv=None):
             x = np.stack([data[c * n_in_vec + idx_in] for c in range(3)])
         else:
             x = data[idx_in]
-        y = apply_block(op, shape, P, Q, X, bool(cv), kind, x, lam, mesh.get("geometry", 0), adv)
+        y = apply_block(op, shape, P, Q, X, bool(cv), kind, x, lam, mesh.get("geometry", 0), adv,
+                        mesh.get("quadrature", 0))
         idx_out = oo[el][:, None] + np.arange(no)[None, :]
         if ok == "phys3":
             for c in range(3):
@@ -347,7 +359,7 @@ def geometric_factors(mesh, elems=None):
     for (shape, P, Q, cv), el in _blocks(mesh, elems).items():
         el = np.array(el)
         s7, s9 = geometric_factors_block(shape, P, Q, _verts(mesh, shape, el), bool(cv), kind,
-                                         mesh.get("geometry", 0))
+                                         mesh.get("geometry", 0), mesh.get("quadrature", 0))
         for t, e in enumerate(el):
             six[e] = s7[t]
             nine[e] = s9[t]

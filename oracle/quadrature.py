@@ -56,20 +56,24 @@ def grj(Q, alpha):
     return x, interpolatory_weights(x, alpha)
 
 
-def shape_rule(shape, Q):
+def shape_rule(shape, Q, reduced=0):
     """Per-direction (nodes, weights) in the collapsed coordinates eta_1..3.
 
     The Duffy Jacobian is absorbed into the collapsed directions:
     prism (1-eta3)/2, pyramid ((1-eta3)/2)^2, tet ((1-eta2)/2)((1-eta3)/2)^2,
     so GRJ(alpha=1) weights are halved and GRJ(alpha=2) weights quartered.
     The product of the three weights is the weight of the xi-space integral.
+    reduced = 1: Q - 1 points in the collapsed (Gauss-Radau-Jacobi)
+    directions, which still integrate degree 2Q - 4 = 2P exactly against
+    their Jacobi weight.
     """
     g = gll(Q)
     if shape == 0:
         return [g, g, g]
-    r1 = grj(Q, 1)
+    Qc = Q - (1 if reduced else 0)
+    r1 = grj(Qc, 1)
     r1 = (r1[0], r1[1] / 2.0)
-    r2 = grj(Q, 2)
+    r2 = grj(Qc, 2)
     r2 = (r2[0], r2[1] / 4.0)
     if shape == 1:
         return [g, g, r1]
