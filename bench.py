@@ -99,6 +99,9 @@ def parse():
     p.add_argument("--block-table", action="store_true",
                    help="GDOF/s of FP32 sum factorisation and the TF32 / BF16 tensor-core operator on large "
                         "single-shape blocks instead")
+    p.add_argument("--reduced-q", action="store_true",
+                   help="GDOF/s of the BF16 / TF32 tensor-core Helmholtz operator with the full and the reduced "
+                        "quadrature rule on large collapsed-shape blocks instead")
     p.add_argument("--two-d", action="store_true",
                    help="GDOF/s of the two-dimensional quadrilateral / triangle Helmholtz operator (FP64, FP32) "
                         "instead")
@@ -942,6 +945,62 @@ def run_block_table(local, reps=10):
             print(json.dumps({"block_table": line}), flush=True)
 
 
+# collapsed-shape blocks of the reduced-rule study: (shape, P, elements)
+REDUCED_Q = [(3, 2, 65536), (3, 4, 65536), (3, 6, 32768), (3, 8, 32768), (2, 4, 65536), (2, 6, 32768),
+             (1, 4, 65536), (1, 6, 32768)]
+
+
+def run_reduced_q(local, reps=10):
+    """The reduced quadrature rule (Q - 1 points in the collapsed directions)
+    against the full one: Helmholtz GDOF/s of the BF16 and TF32 tensor-core
+    elemental-matrix operator on large curved single-shape blocks (L2 flushed
+    before every apply; median of `reps`), the points per element of each rule
+    and the relative difference of the two FP64 elemental-matrix results (the
+    quadrature error the reduced rule adds on curved elements)."""
+    import torch
+    from paper_2604_04644_gb300 import hp, inputs
+    torch.cuda.set_device(local)
+    dev = "cuda:%d" % local
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    for shape, P, n in REDUCED_Q:
+        line = {"shape": SHAPES[shape], "P": P, "elements": n}
+        ys = {}
+        for rq in (0, 1):
+            mesh = inputs.replicated_mesh(shape, P, n, curved=True)
+            mesh["quadrature"] = rq
+            h = hp.hp_mesh_create(mesh, local)
+            co, po, nc, nph = hp.hp_mesh_layout(h, mesh["n_elem"])
+            line["points_" + ("reduced" if rq else "full")] = int(po[1] - po[0])
+            x = torch.tensor(inputs.random_coefficients(5, co), device=dev, dtype=torch.float64)
+            y = torch.zeros(nc, device=dev, dtype=torch.float64)
+            op = hp.hp_op_create(h, hp.HP_HELMHOLTZ, hp.HP_STRAT_ELEMAT, hp.HP_FP64)
+            hp.hp_op_apply(op, 1.0, x, y)
+            hp.hp_op_sync(op)
+            ys[rq] = y.clone()
+            hp.hp_op_destroy(op)
+            x32, y32 = x.float(), torch.zeros(nc, device=dev, dtype=torch.float32)
+            for name, dt in (("bf16", hp.HP_BF16), ("tf32", hp.HP_TF32)):
+                op = hp.hp_op_create(h, hp.HP_HELMHOLTZ, hp.HP_STRAT_ELEMAT, dt)
+                for _ in range(3):
+                    hp.hp_op_apply(op, 1.0, x32, y32)
+                ts = []
+                for _ in range(reps):
+                    flush.zero_()
+                    a = torch.cuda.Event(enable_timing=True)
+                    b = torch.cuda.Event(enable_timing=True)
+                    a.record()
+                    hp.hp_op_apply(op, 1.0, x32, y32)
+                    b.record()
+                    b.synchronize()
+                    ts.append(a.elapsed_time(b))
+                hp.hp_op_sync(op)
+                line["%s_%s" % (name, "reduced" if rq else "full")] = round(nc / (statistics.median(ts) * 1e-3) / 1e9, 2)
+                hp.hp_op_destroy(op)
+            hp.hp_mesh_destroy(h)
+        line["rel_diff_fp64"] = float("%.3g" % float((ys[1] - ys[0]).abs().max() / ys[0].abs().max()))
+        print(json.dumps({"reduced_q": line}), flush=True)
+
+
 # two-dimensional blocks: (cells, P, cells per side of the unit square)
 TWO_D = [("quad", 2, 500), ("quad", 4, 400), ("quad", 8, 250), ("tri", 2, 400), ("tri", 4, 300), ("tri", 8, 200)]
 
@@ -1143,6 +1202,10 @@ def main():
     if args.two_d:
         if rank == 0:
             run_two_d(local)
+        return
+    if args.reduced_q:
+        if rank == 0:
+            run_reduced_q(local)
         return
     if args.collocation_study:
         if rank == 0:

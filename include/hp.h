@@ -126,6 +126,17 @@ typedef enum { HP_FP64 = 0, HP_FP32 = 1, HP_TF32 = 2, HP_BF16 = 3 } hp_dtype;
  *                        the reference element with its quadrature rule) and the Jacobian is
  *                        that of the expansion (the iso-parametric curved elements of the
  *                        paper's benchmarks, Sec. 4).  Affine elements are exact either way.
+ *   quadrature           0: Q = P + 2 points in every direction; 1 (reduced rule): Q - 1
+ *                        Gauss-Radau-Jacobi points in the collapsed directions (prism and
+ *                        pyramid eta_3, tetrahedron eta_2 and eta_3), which still integrates
+ *                        the mass and Laplacian matrices of affine elements exactly and cuts
+ *                        the points, so the metric factors, of a tetrahedron by (2Q - 1)/Q^2.
+ *                        The point vectors then hold q1 q2 q3 values per element in the same
+ *                        (i, j, k) order.  A reduced-rule mesh has the elemental-matrix
+ *                        operators of mass, Laplacian and Helmholtz (HP_STRAT_ELEMAT in every
+ *                        dtype: FP64 / FP32 CUDA cores, TF32 / BF16 tensor cores); geometry 1,
+ *                        the sum-factorised kernels, the C0 space and hp_mesh_points are for
+ *                        the full rule (HP_ERR_UNSUPPORTED).
  * Every element must be an affine image of its reference element (all vertices
  * are checked); curved elements are that affine map followed by the deformation. */
 typedef struct {
@@ -139,6 +150,7 @@ typedef struct {
     const uint8_t* curved;
     int32_t deformation;
     int32_t geometry;
+    int32_t quadrature;
 } hp_mesh_desc;
 
 /* Create a mesh on CUDA device `device`: validates and copies the description,

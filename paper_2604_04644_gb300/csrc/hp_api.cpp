@@ -78,8 +78,9 @@ void free_block(Block& b) {
     b.d_geom32 = b.d_dgeom32 = nullptr;
 }
 
-int64_t geom_count(const Block& b) { return b.curved ? b.n_elem * 7 * (int64_t)nqp(b.Q) : b.n_elem * 16; }
-int64_t dgeom_count(const Block& b) { return b.curved ? b.n_elem * 9 * (int64_t)nqp(b.Q) : 0; }
+int bnqp(const Block& b) { return (b.nq + 3) & ~3; }   // padded points per element of the block's rule
+int64_t geom_count(const Block& b) { return b.curved ? b.n_elem * 7 * (int64_t)bnqp(b) : b.n_elem * 16; }
+int64_t dgeom_count(const Block& b) { return b.curved ? b.n_elem * 9 * (int64_t)bnqp(b) : 0; }
 
 hp_status check_device_error(hp_mesh m, unsigned int* d_err, int* d_bad, const char* what) {
     unsigned int herr = 0;
@@ -189,7 +190,7 @@ bool affine_expanded(const hp_op_s* op, const Block& b) {
 hp_status ensure_affine_points(hp_mesh m, cudaStream_t s) {
     for (Block& b : m->blocks) {
         if (b.curved || b.d_geom_pts || b.n_elem == 0) continue;
-        hp_status st = upload<double>(&b.d_geom_pts, nullptr, (size_t)b.n_elem * 7 * nqp(b.Q));
+        hp_status st = upload<double>(&b.d_geom_pts, nullptr, (size_t)b.n_elem * 7 * bnqp(b));
         if (st) return st;
         cudaError_t e = launch_affine_points(b, m->blobs.at(b.shape * 16 + b.P), b.d_geom_pts, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -213,8 +214,8 @@ hp_status ensure_dense(hp_mesh m) {
         DeviceBlobs& db = kv.second;
         if (db.A4_64) continue;
         int shape = kv.first / 16, P = kv.first % 16;
-        const int NQ = (P + 2) * (P + 2) * (P + 2), NP = n_modes(shape, P);
-        std::vector<double> A = dense_matrices(shape, P);
+        const int NQ = n_points(shape, P, m->quadrature), NP = n_modes(shape, P);
+        std::vector<double> A = m->quadrature ? dense_matrices_rq(shape, P) : dense_matrices(shape, P);
         std::vector<double> AT(A.size());
         for (int q = 0; q < 4; ++q)
             for (int l = 0; l < NQ; ++l)
@@ -336,7 +337,7 @@ hp_status ensure_tc(hp_mesh m, int es) {
     for (auto& kv : m->blobs) {
         DeviceBlobs& db = kv.second;
         const int shape = kv.first / 16, P = kv.first % 16;
-        const int Q = P + 2, NQ = Q * Q * Q, NP = n_modes(shape, P), NPT = tc_chunk_points();
+        const int NQ = n_points(shape, P, m->quadrature), NP = n_modes(shape, P), NPT = tc_chunk_points();
         if (NP > (es == 2 ? kTcHybMaxModes : kTcHybMaxModesTF32)) continue;   // the hybrid's limit (>= the elemental matrix's)
         const int KR = 128 / es, vrow = NPT * es;
         const int KP = (NP + KR - 1) / KR * KR, NPpad = (NP + 15) & ~15, nch = (NQ + NPT - 1) / NPT;
@@ -344,7 +345,7 @@ hp_status ensure_tc(hp_mesh m, int es) {
         const int fwd = (KP / KR) * slice, bwd = NPpad * vrow;
         const int64_t chunk = fwd + 4 * (int64_t)bwd;
         if ((es == 4 && db.tc_img) || (es == 2 && db.tc_img16)) continue;
-        std::vector<double> A = dense_matrices(shape, P);
+        std::vector<double> A = m->quadrature ? dense_matrices_rq(shape, P) : dense_matrices(shape, P);
         std::vector<unsigned char> img((size_t)(chunk * nch), 0);
         auto put = [&](unsigned char* dst, double x) {
             if (es == 4) {
@@ -392,7 +393,7 @@ hp_status ensure_tc(hp_mesh m, int es) {
         if (st) return st;
         const BlobLayout L = blob_layout_c(b.shape, b.P, 8);
         const double* v64 = static_cast<const double*>(db.d64);
-        cudaError_t e = tc_geom_layout16(b.shape, b.curved != 0, b.d_geom, nqp(b.Q), v64 + L.z, v64 + L.w, b.Q,
+        cudaError_t e = tc_geom_layout16(b.shape, b.curved != 0, b.d_geom, bnqp(b), b.nq, v64 + L.z, v64 + L.w, b.Q,
                                          b.d_geom_tc, b.d_gscale_tc, b.n_elem, db.tc_nch, 0);
         if (e == cudaSuccess) e = cudaStreamSynchronize(0);
         if (e != cudaSuccess) return cuda_fail(e, "tensor-core geometry layout");
@@ -415,6 +416,8 @@ bool mat_fits(const Block& b) { return n_modes(b.shape, b.P) <= kMatMaxModes; }
 // (N_P <= 256) and the tensor-core hybrid (N_P <= 512 BF16, 352 TF32); stored
 // matrices are mass, Laplacian or Helmholtz in FP64 / FP32 (N_P <= 256)
 bool strategy_available(const hp_op_s* op, size_t i, int k) {
+    if (op->mesh->quadrature)   // the reduced rule: elemental matrices only (tensor cores up to 256 modes)
+        return k == HP_STRAT_ELEMAT && (!(op->dtype == HP_TF32 || op->dtype == HP_BF16) || tc_fits(op->mesh->blocks[i]));
     if (k == HP_STRAT_SUMFAC) return true;
     if (needs_deriv_geom(op->kind)) return false;
     if (op->dtype == HP_TF32 || op->dtype == HP_BF16) return tc_strategy_fits(op->mesh->blocks[i], op->dtype, k);
@@ -425,9 +428,9 @@ bool strategy_available(const hp_op_s* op, size_t i, int k) {
 }
 
 // flops of the elemental-matrix (hybrid = false) or hybrid strategy per element
-double elem_flops_dense(int shape, int P, hp_opkind k, bool hybrid) {
+double elem_flops_dense(int shape, int P, hp_opkind k, bool hybrid, int nq = 0) {
     const int Q = P + 2;
-    const double NQ = (double)Q * Q * Q, NP = n_modes(shape, P);
+    const double NQ = nq > 0 ? (double)nq : (double)Q * Q * Q, NP = n_modes(shape, P);
     const double deriv = 3.0 * 2.0 * Q * NQ;
     const double mv = 2.0 * NQ * NP;
     switch (k) {
@@ -640,7 +643,7 @@ cudaError_t launch_block(hp_op op, size_t bi, int tile, double lambda, const voi
     if ((op->dtype == HP_TF32 || op->dtype == HP_BF16) && op->strat[bi] == HP_STRAT_ELEMAT) {
         const bool bf = op->dtype == HP_BF16;
         TCArgs a{};
-        a.op = op->kind; a.Q = b.Q; a.NQ = b.Q * b.Q * b.Q; a.NQp = nqp(b.Q); a.NP = n_modes(b.shape, b.P);
+        a.op = op->kind; a.Q = b.Q; a.NQ = b.nq; a.NQp = bnqp(b); a.NP = n_modes(b.shape, b.P);
         a.KP = bf ? blob.tc_KP16 : blob.tc_KP; a.NPpad = blob.tc_NPpad; a.nch = blob.tc_nch;
         a.es = bf ? 2 : 4;
         a.c0 = op->kind == HP_LAPLACIAN ? 1 : 0;
@@ -697,7 +700,7 @@ cudaError_t launch_block(hp_op op, size_t bi, int tile, double lambda, const voi
         }
         const bool bf = op->dtype == HP_BF16;
         HybArgs h{};
-        h.NQ = b.Q * b.Q * b.Q; h.NP = n_modes(b.shape, b.P);
+        h.NQ = b.nq; h.NP = n_modes(b.shape, b.P);
         h.KP = bf ? blob.tc_KP16 : blob.tc_KP; h.NPpad = blob.tc_NPpad; h.nch = blob.tc_nch; h.es = bf ? 2 : 4;
         h.n_elem = b.n_elem; h.coeff_off = b.d_coeff_off; h.phys_off = b.d_phys_off;
         h.img = bf ? blob.tc_img16 : blob.tc_img;
@@ -726,8 +729,8 @@ cudaError_t launch_block(hp_op op, size_t bi, int tile, double lambda, const voi
         const bool hybrid = op->strat[bi] == HP_STRAT_HYBRID;
         if (op->dtype == HP_FP64) {
             EMArgs<double> a{};
-            a.op = op->kind; a.shape = b.shape; a.P = b.P; a.Q = b.Q; a.NQ = b.Q * b.Q * b.Q;
-            a.NP = n_modes(b.shape, b.P); a.NQp = nqp(b.Q); a.n_elem = b.n_elem; a.lambda = lambda;
+            a.op = op->kind; a.shape = b.shape; a.P = b.P; a.Q = b.Q; a.NQ = b.nq;
+            a.NP = n_modes(b.shape, b.P); a.NQp = bnqp(b); a.n_elem = b.n_elem; a.lambda = lambda;
             a.coeff_off = b.d_coeff_off; a.phys_off = b.d_phys_off;
             a.in = static_cast<const double*>(in); a.out = static_cast<double*>(out);
             a.geom = b.d_geom; a.A4 = blob.A4_64; a.A4T = blob.A4T_64;
@@ -735,8 +738,8 @@ cudaError_t launch_block(hp_op op, size_t bi, int tile, double lambda, const voi
             return emat_launch_f64(hybrid, !b.curved, a, s);
         }
         EMArgs<float> a{};
-        a.op = op->kind; a.shape = b.shape; a.P = b.P; a.Q = b.Q; a.NQ = b.Q * b.Q * b.Q;
-        a.NP = n_modes(b.shape, b.P); a.NQp = nqp(b.Q); a.n_elem = b.n_elem; a.lambda = (float)lambda;
+        a.op = op->kind; a.shape = b.shape; a.P = b.P; a.Q = b.Q; a.NQ = b.nq;
+        a.NP = n_modes(b.shape, b.P); a.NQp = bnqp(b); a.n_elem = b.n_elem; a.lambda = (float)lambda;
         a.coeff_off = b.d_coeff_off; a.phys_off = b.d_phys_off;
         a.in = static_cast<const float*>(in); a.out = static_cast<float*>(out);
         a.geom = b.d_geom32; a.A4 = blob.A4_32; a.A4T = blob.A4T_32;
@@ -817,6 +820,11 @@ hp_status hp_mesh_create(const hp_mesh_desc* d, int device, hp_mesh* out) {
     }
     if (d->deformation < 0 || d->deformation > 2) { set_error("hp_mesh_create: unknown deformation"); return HP_ERR_ARG; }
     if (d->geometry < 0 || d->geometry > 1) { set_error("hp_mesh_create: geometry must be 0 or 1"); return HP_ERR_ARG; }
+    if (d->quadrature < 0 || d->quadrature > 1) { set_error("hp_mesh_create: quadrature must be 0 or 1"); return HP_ERR_ARG; }
+    if (d->quadrature == 1 && d->geometry == 1) {
+        set_error("hp_mesh_create: the iso-parametric geometry is built on the full quadrature rule");
+        return HP_ERR_UNSUPPORTED;
+    }
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
         set_error("hp_mesh_create: no such CUDA device");
@@ -828,6 +836,7 @@ hp_status hp_mesh_create(const hp_mesh_desc* d, int device, hp_mesh* out) {
     m->n_elem = d->n_elem;
     m->deformation = d->deformation;
     m->geometry = d->geometry;
+    m->quadrature = d->quadrature;
     m->shape.assign(d->shape, d->shape + d->n_elem);
     m->P.assign(d->P, d->P + d->n_elem);
     m->Q.assign(d->Q, d->Q + d->n_elem);
@@ -887,7 +896,7 @@ hp_status hp_mesh_create(const hp_mesh_desc* d, int device, hp_mesh* out) {
                 }
             }
         m->coeff_off[e + 1] = m->coeff_off[e] + n_modes(s, P);
-        m->phys_off[e + 1] = m->phys_off[e] + (int64_t)Q * Q * Q;
+        m->phys_off[e + 1] = m->phys_off[e] + (int64_t)n_points(s, P, m->quadrature);
     }
     // blocks of equal (shape, P, curved), in order of first appearance
     std::map<std::tuple<int, int, int>, int> key2blk;
@@ -900,7 +909,15 @@ hp_status hp_mesh_create(const hp_mesh_desc* d, int device, hp_mesh* out) {
             b.P = d->P[e];
             b.Q = d->Q[e];
             b.curved = d->curved[e] ? 1 : 0;
+            b.map_curved = b.curved;
             b.n_elem = 0;
+            {
+                std::vector<double> zz[3], ww[3];
+                rule_points(b.shape, b.P, m->quadrature, zz, ww);
+                for (int dd = 0; dd < 3; ++dd) b.q[dd] = (int)zz[dd].size();
+                b.nq = b.q[0] * b.q[1] * b.q[2];
+            }
+            if (m->quadrature) b.curved = 1;     // the reduced rule keeps per-point factors for every block
             m->blocks.push_back(b);
             it = key2blk.emplace(key, (int)m->blocks.size() - 1).first;
         }
@@ -937,6 +954,15 @@ hp_status hp_mesh_create(const hp_mesh_desc* d, int device, hp_mesh* out) {
             std::vector<double> dtab(t.Tbd);
             dtab.insert(dtab.end(), t.Tcd.begin(), t.Tcd.end());
             if ((st = upload(&db.d_nc64, dtab.data(), dtab.size()))) { cudaFree(p64); cudaFree(p32); break; }
+            if (m->quadrature) {
+                std::vector<double> zz[3], ww[3], zw;
+                rule_points(b.shape, b.P, 1, zz, ww);
+                for (int dd = 0; dd < 3; ++dd) {
+                    zw.insert(zw.end(), zz[dd].begin(), zz[dd].end());
+                    zw.insert(zw.end(), ww[dd].begin(), ww[dd].end());
+                }
+                if ((st = upload(&db.rq_zw, zw.data(), zw.size()))) { cudaFree(p64); cudaFree(p32); cudaFree(db.d_nc64); break; }
+            }
             m->blobs[key] = db;
         }
     }
@@ -976,7 +1002,7 @@ hp_status hp_geom_copy(hp_mesh m, double* out7, double* out9) {
     hp_status st = ensure_geom(m, out9 != nullptr, false, 0);
     if (st) return st;
     for (const Block& b : m->blocks) {
-        const int Q = b.Q, NQ = Q * Q * Q, NQp = nqp(Q);
+        const int Q = b.Q, NQ = b.nq, NQp = bnqp(b);
         std::vector<double> g(geom_count(b)), h(dgeom_count(b));
         cudaError_t e = cudaMemcpy(g.data(), b.d_geom, g.size() * sizeof(double), cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return cuda_fail(e, "hp_geom_copy");
@@ -1038,7 +1064,17 @@ hp_status hp_op_create(hp_mesh m, hp_opkind kind, hp_strategy strategy, hp_dtype
     if ((int)strategy < 0 || strategy > HP_STRAT_MATRIX) { set_error("hp_op_create: bad strategy"); return HP_ERR_ARG; }
     if ((int)dtype < 0 || dtype > HP_BF16) { set_error("hp_op_create: bad dtype"); return HP_ERR_ARG; }
     const bool tcore = dtype == HP_TF32 || dtype == HP_BF16;
-    if (strategy == HP_STRAT_AUTO) strategy = tcore ? HP_STRAT_ELEMAT : HP_STRAT_SUMFAC;
+    if (strategy == HP_STRAT_AUTO) strategy = (tcore || m->quadrature) ? HP_STRAT_ELEMAT : HP_STRAT_SUMFAC;
+    if (m->quadrature) {
+        bool ok = strategy == HP_STRAT_ELEMAT && (kind == HP_MASS || kind == HP_LAPLACIAN || kind == HP_HELMHOLTZ);
+        if (ok && tcore)
+            for (const Block& b : m->blocks) ok = ok && tc_fits(b);
+        if (!ok) {
+            set_error("hp_op_create: a reduced-rule mesh has the elemental-matrix mass, Laplacian and Helmholtz "
+                      "operators (tensor cores: blocks of at most 256 modes)");
+            return HP_ERR_UNSUPPORTED;
+        }
+    }
     if (tcore && ((strategy != HP_STRAT_ELEMAT && strategy != HP_STRAT_HYBRID) ||
                   (kind != HP_MASS && kind != HP_LAPLACIAN && kind != HP_HELMHOLTZ))) {
         set_error("hp_op_create: HP_TF32 / HP_BF16 are the tensor-core elemental-matrix and hybrid forms of mass, "
@@ -1364,6 +1400,7 @@ hp_status hp_op_apply_graph(hp_op op, double lambda, const void* in, void* out, 
 
 hp_status hp_mesh_points(hp_mesh m, double* xyz, void* stream) {
     if (!m || !xyz) { set_error("hp_mesh_points: null argument"); return HP_ERR_ARG; }
+    if (m->quadrature) { set_error("hp_mesh_points: the points of the full rule only"); return HP_ERR_UNSUPPORTED; }
     DeviceGuard guard(m->device);
     for (const Block& b : m->blocks) {
         cudaError_t e = launch_points(b, m->blobs.at(b.shape * 16 + b.P), m->deformation, xyz, m->phys_off.back(),
@@ -1385,6 +1422,10 @@ hp_status hp_op_strategies(hp_op op, int* strat, int64_t n_blocks, int set) {
         if (strat[i] < HP_STRAT_SUMFAC || strat[i] > HP_STRAT_MATRIX || strat[i] == HP_STRAT_AUTO) {
             set_error("hp_op_strategies: bad strategy");
             return HP_ERR_ARG;
+        }
+        if (op->mesh->quadrature && !strategy_available(op, (size_t)i, strat[i])) {
+            set_error("hp_op_strategies: a reduced-rule mesh runs elemental matrices only");
+            return HP_ERR_UNSUPPORTED;
         }
         if (strat[i] == HP_STRAT_MATRIX &&
             ((op->kind != HP_MASS && op->kind != HP_LAPLACIAN && op->kind != HP_HELMHOLTZ) ||
@@ -1653,14 +1694,14 @@ hp_status hp_op_block_work(hp_op op, int64_t block, int64_t* n_elem, int64_t* ou
     for (const Block& b : m->blocks) {
         size_t bi = &b - &m->blocks[0];
         if (block >= 0 && (int64_t)bi != block) continue;
-        const double NQ = (double)b.Q * b.Q * b.Q;
+        const double NQ = (double)b.nq;
         const double np = (double)n_modes(b.shape, b.P);
         const double ne = (double)b.n_elem;
         ne_tot += b.n_elem;
         const int st = op->strat[bi];
         const double fd = st == HP_STRAT_SUMFAC ? elem_flops(b.shape, b.P, op->kind)
                         : st == HP_STRAT_MATRIX ? 2.0 * np * np
-                                                : elem_flops_dense(b.shape, b.P, op->kind, st == HP_STRAT_HYBRID);
+                                                : elem_flops_dense(b.shape, b.P, op->kind, st == HP_STRAT_HYBRID, b.nq);
         fl += ne * fd;
         fx += ne * (st == HP_STRAT_SUMFAC ? elem_flops_exec(b.shape, b.P, op->kind, op->dtype == HP_FP64) : fd);
         double in_v = coeff_in(op->kind) ? np : (op->kind == HP_IPRODUCT_WRT_DERIV_BASE ? 3 * NQ : NQ);
@@ -1726,6 +1767,7 @@ void hp_mesh_destroy(hp_mesh m) {
         for (Block& b : m->blocks) free_block(b);
         for (auto& kv : m->blobs) {
             cudaFree(kv.second.d64);
+            cudaFree(kv.second.rq_zw);
             cudaFree(kv.second.d32);
             cudaFree(kv.second.d_nc64);
             cudaFree(kv.second.iso_RT);

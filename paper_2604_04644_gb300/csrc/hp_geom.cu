@@ -195,18 +195,24 @@ __global__ void __launch_bounds__(256) geom_iso_kernel(int Q, int NP, int NQp, i
     }
 }
 
+// per-direction point counts q1, q2, q3 (Q each for the full rule) and the
+// points / weights of each direction
+struct Rule3 {
+    int q1, q2, q3;
+    const double *z1, *z2, *z3, *w1, *w2, *w3;
+};
+
 template <int SHAPE>
-__global__ void geom_curved_kernel(int Q, int NQp, int64_t n_elem, const double* __restrict__ frame,
-                                   const double* __restrict__ z, const double* __restrict__ w, int kind,
+__global__ void geom_curved_kernel(Rule3 R, int NQp, int64_t n_elem, const double* __restrict__ frame, int kind,
                                    int want_deriv, double* __restrict__ geom, double* __restrict__ dgeom,
                                    unsigned int* err, int* bad_elem) {
-    const int NQ = Q * Q * Q;
+    const int NQ = R.q1 * R.q2 * R.q3;
     int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (idx >= n_elem * NQ) return;
     int64_t e = idx / NQ;
     int l = (int)(idx % NQ);
-    int i = l / (Q * Q), j = (l / Q) % Q, k = l % Q;
-    double e1 = z[i], e2 = z[Q + j], e3 = z[2 * Q + k];
+    int i = l / (R.q2 * R.q3), j = (l / R.q3) % R.q2, k = l % R.q3;
+    double e1 = R.z1[i], e2 = R.z2[j], e3 = R.z3[k];
     double xi[3];
     xi_from_eta<SHAPE>(e1, e2, e3, xi);
     const double* F = frame + e * 12;
@@ -222,7 +228,7 @@ __global__ void geom_curved_kernel(int Q, int NQp, int64_t n_elem, const double*
     deform_jacobian(kind, y, Dp);
     for (int r = 0; r < 3; ++r)
         for (int d = 0; d < 3; ++d) J[r][d] = Dp[r][0] * JA[0][d] + Dp[r][1] * JA[1][d] + Dp[r][2] * JA[2][d];
-    store_factors<SHAPE>(J, e1, e2, e3, w[i] * w[Q + j] * w[2 * Q + k], e, l, NQp, want_deriv, geom, dgeom, err,
+    store_factors<SHAPE>(J, e1, e2, e3, R.w1[i] * R.w2[j] * R.w3[k], e, l, NQp, want_deriv, geom, dgeom, err,
                          bad_elem);
 }
 
@@ -318,27 +324,38 @@ cudaError_t launch_geom(const Block& b, const DeviceBlobs& blob, int deformation
     const double* vals = reinterpret_cast<const double*>(blob.d64);
     const double* z = vals + L.z;
     const double* w = vals + L.w;
-    int NQ = b.Q * b.Q * b.Q;
+    const int Q = b.Q;
+    Rule3 R{Q, Q, Q, z, z + Q, z + 2 * Q, w, w + Q, w + 2 * Q};
+    // every block here keeps per-point factors; the reduced rule's affine blocks
+    // (curved = 1 for the layout, map_curved = 0) take the map without deformation
+    const int kind = b.map_curved ? deformation : 0;
+    if (b.nq != Q * Q * Q) {       // reduced rule: its own points
+        if (!blob.rq_zw) return cudaErrorInvalidValue;
+        const double* p = blob.rq_zw;
+        R = Rule3{b.q[0], b.q[1], b.q[2], p, p + 2 * b.q[0], p + 2 * (b.q[0] + b.q[1]),
+                  p + b.q[0], p + 2 * b.q[0] + b.q[1], p + 2 * (b.q[0] + b.q[1]) + b.q[2]};
+    }
+    const int NQ = R.q1 * R.q2 * R.q3;
     int nt = 128;
     int64_t total = b.n_elem * NQ;
     unsigned nb = (unsigned)((total + nt - 1) / nt);
-    int NQp = nqp(b.Q);
+    const int NQp = (NQ + 3) & ~3;
     switch (b.shape) {
         case HP_HEX:
-            geom_curved_kernel<HP_HEX><<<nb, nt, 0, s>>>(b.Q, NQp, b.n_elem, b.d_frame, z, w, deformation,
-                                                         want_deriv, b.d_geom, b.d_dgeom, d_err, d_bad_elem);
+            geom_curved_kernel<HP_HEX><<<nb, nt, 0, s>>>(R, NQp, b.n_elem, b.d_frame, kind, want_deriv, b.d_geom,
+                                                         b.d_dgeom, d_err, d_bad_elem);
             break;
         case HP_PRISM:
-            geom_curved_kernel<HP_PRISM><<<nb, nt, 0, s>>>(b.Q, NQp, b.n_elem, b.d_frame, z, w, deformation,
-                                                           want_deriv, b.d_geom, b.d_dgeom, d_err, d_bad_elem);
+            geom_curved_kernel<HP_PRISM><<<nb, nt, 0, s>>>(R, NQp, b.n_elem, b.d_frame, kind, want_deriv, b.d_geom,
+                                                           b.d_dgeom, d_err, d_bad_elem);
             break;
         case HP_PYR:
-            geom_curved_kernel<HP_PYR><<<nb, nt, 0, s>>>(b.Q, NQp, b.n_elem, b.d_frame, z, w, deformation,
-                                                         want_deriv, b.d_geom, b.d_dgeom, d_err, d_bad_elem);
+            geom_curved_kernel<HP_PYR><<<nb, nt, 0, s>>>(R, NQp, b.n_elem, b.d_frame, kind, want_deriv, b.d_geom,
+                                                         b.d_dgeom, d_err, d_bad_elem);
             break;
         default:
-            geom_curved_kernel<HP_TET><<<nb, nt, 0, s>>>(b.Q, NQp, b.n_elem, b.d_frame, z, w, deformation,
-                                                         want_deriv, b.d_geom, b.d_dgeom, d_err, d_bad_elem);
+            geom_curved_kernel<HP_TET><<<nb, nt, 0, s>>>(R, NQp, b.n_elem, b.d_frame, kind, want_deriv, b.d_geom,
+                                                         b.d_dgeom, d_err, d_bad_elem);
     }
     return cudaGetLastError();
 }

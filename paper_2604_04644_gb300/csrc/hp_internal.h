@@ -47,6 +47,12 @@ double family_value(int P, int s, int m, double z);
 
 // Dense reference matrices A4[q][l][m] (q = 0: B, q = 1..3: d/d eta_q of B), FP64.
 std::vector<double> dense_matrices(int shape, int P);
+// Points and weights per direction of the full (rq = 0) or reduced (rq = 1:
+// Q - 1 Gauss-Radau-Jacobi points in the collapsed directions) rule.
+void rule_points(int shape, int P, int rq, std::vector<double> z[3], std::vector<double> w[3]);
+// A4 at the points of the reduced rule (layout as dense_matrices, N_Q = q1 q2 q3).
+std::vector<double> dense_matrices_rq(int shape, int P);
+int n_points(int shape, int P, int rq);   // points per element of the rule
 
 // Serialise the tables in value type T (double or float) into bytes.
 std::vector<unsigned char> make_blob(const RefTables& t, size_t value_size);
@@ -55,6 +61,12 @@ std::vector<unsigned char> make_blob(const RefTables& t, size_t value_size);
 struct Block {
     int shape, P, Q, curved;
     int64_t n_elem;
+    // quadrature points per direction and per element (Q, Q, Q and Q^3 for the
+    // full rule; the reduced rule has Q - 1 in the collapsed directions, and
+    // its blocks keep per-point factors: curved = 1, map_curved = the user flag)
+    int q[3] = {0, 0, 0};
+    int nq = 0;
+    int map_curved = 0;
     std::vector<int64_t> elems;           // user element ids (host)
     int64_t* d_coeff_off = nullptr;       // [n_elem] coefficient offset of each element
     int64_t* d_phys_off = nullptr;        // [n_elem] phys offset of each element
@@ -71,6 +83,7 @@ struct Block {
 };
 
 struct DeviceBlobs {
+    double* rq_zw = nullptr;    // reduced rule: z1 w1 z2 w2 z3 w3 (per-direction counts of the blocks)
     void* d64 = nullptr;
     void* d32 = nullptr;
     int bytes64 = 0, bytes32 = 0;
@@ -102,6 +115,7 @@ struct hp_mesh_s {
     int64_t n_elem = 0;
     int deformation = 0;
     int geometry = 0;                           // 0 analytic map, 1 iso-parametric (curved elements)
+    int quadrature = 0;                         // 1: Q - 1 points in the collapsed directions
     std::vector<uint8_t> shape, P, Q, curved;
     std::vector<int64_t> coeff_off, phys_off;   // n_elem + 1
     std::vector<int64_t> vert;                  // n_elem * 8 global vertex ids (for the C0 map)
@@ -268,7 +282,7 @@ constexpr int kTcHybMaxModes = 512, kTcHybMaxModesTF32 = 352;
 int tc_hyb_smem(int mode, int es, int KP, int NPpad, int bwd_bytes, int* stages_out, int* stage_bytes_out);
 int tc_chunk_points();
 int64_t tc_geom_halves(int64_t n_elem, int nch);
-cudaError_t tc_geom_layout16(int shape, bool curved, const double* g, int NQp, const double* z, const double* w, int Q,
+cudaError_t tc_geom_layout16(int shape, bool curved, const double* g, int NQp, int NQ, const double* z, const double* w, int Q,
                              uint16_t* out, float* isc, int64_t n_elem, int nch, cudaStream_t s);
 cudaError_t tc_emat_launch(const TCArgs& a, cudaStream_t s);
 cudaError_t emat_launch_f32(bool hybrid, bool affine, const EMArgs<float>& a, cudaStream_t s);

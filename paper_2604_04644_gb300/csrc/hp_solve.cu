@@ -633,6 +633,10 @@ extern "C" {
 hp_status hp_c0_create(hp_mesh mesh, hp_c0* out) {
     if (!mesh || !out) { set_error("hp_c0_create: null argument"); return HP_ERR_ARG; }
     *out = nullptr;
+    if (mesh->quadrature) {
+        set_error("hp_c0_create: the C0 space and its solves use the sum-factorised operators of the full rule");
+        return HP_ERR_UNSUPPORTED;
+    }
     cudaSetDevice(mesh->device);
     auto c = new hp_c0_s();
     c->mesh = mesh;

@@ -440,4 +440,72 @@ std::vector<unsigned char> make_blob(const RefTables& t, size_t vs) {
     return out;
 }
 
+// Reduced rule (reading of the quadrature option): Q - 1 Gauss-Radau-Jacobi
+// points in the collapsed directions, which integrate degree 2Q - 4 = 2P
+// exactly against their Jacobi weight, the Gauss-Lobatto-Legendre Q points
+// elsewhere.
+void rule_points(int shape, int P, int rq, std::vector<double> z[3], std::vector<double> w[3]) {
+    const int Q = P + 2, Qc = rq ? Q - 1 : Q;
+    std::vector<double> gx, gw, r1x, r1w, r2x, r2w;
+    gll_rule(Q, gx, gw);
+    grj_rule(Qc, 1, r1x, r1w);
+    for (double& v : r1w) v *= 0.5;
+    grj_rule(Qc, 2, r2x, r2w);
+    for (double& v : r2w) v *= 0.25;
+    z[0] = gx; w[0] = gw;
+    z[1] = gx; w[1] = gw;
+    z[2] = gx; w[2] = gw;
+    if (shape == HP_PRISM) { z[2] = r1x; w[2] = r1w; }
+    if (shape == HP_PYR) { z[2] = r2x; w[2] = r2w; }
+    if (shape == HP_TET) { z[1] = r1x; w[1] = r1w; z[2] = r2x; w[2] = r2w; }
+}
+
+int n_points(int shape, int P, int rq) {
+    const int Q = P + 2;
+    if (!rq || shape == HP_HEX) return Q * Q * Q;
+    return shape == HP_TET ? Q * (Q - 1) * (Q - 1) : Q * Q * (Q - 1);
+}
+
+std::vector<double> dense_matrices_rq(int shape, int P) {
+    // B at the reduced rule's points from the 1-D factors, then D_d B with the
+    // Lagrange derivatives of each direction's points (exact: every factor has
+    // degree <= P below the direction's point count)
+    const RefTables& t = ref_tables(shape, P);
+    std::vector<double> z[3], w[3];
+    rule_points(shape, P, 1, z, w);
+    const int n = t.n, NP = t.NP;
+    const int q1 = (int)z[0].size(), q2 = (int)z[1].size(), q3 = (int)z[2].size(), NQ = q1 * q2 * q3;
+    std::vector<double> A(4 * (size_t)NQ * NP, 0.0);
+    for (int m = 0; m < NP; ++m)
+        for (int q = 0; q < 4; ++q) {
+            const int sl = t.mode_slots[m * 4 + q];
+            if (sl < 0) continue;
+            const int a = sl / (n * n), b = (sl / n) % n, c = sl % n;
+            const int tb = t.famb[a], sc = t.famc[a * n + b];
+            for (int i = 0; i < q1; ++i)
+                for (int j = 0; j < q2; ++j)
+                    for (int k = 0; k < q3; ++k)
+                        A[((size_t)((i * q2 + j) * q3 + k)) * NP + m] +=
+                            family(P, 0, a, z[0][i]) * family(P, tb, b, z[1][j]) * family(P, sc, c, z[2][k]);
+        }
+    const int qd[3] = {q1, q2, q3};
+    for (int d = 0; d < 3; ++d) {
+        const std::vector<double> D = lagrange_d(z[d]);
+        const int qq = qd[d];
+        for (int i = 0; i < q1; ++i)
+            for (int j = 0; j < q2; ++j)
+                for (int k = 0; k < q3; ++k) {
+                    const int l = (i * q2 + j) * q3 + k, own = d == 0 ? i : d == 1 ? j : k;
+                    for (int mm = 0; mm < qq; ++mm) {
+                        const int src = d == 0 ? (mm * q2 + j) * q3 + k : d == 1 ? (i * q2 + mm) * q3 + k : (i * q2 + j) * q3 + mm;
+                        const double dv = D[own * qq + mm];
+                        const double* from = &A[(size_t)src * NP];
+                        double* to = &A[((size_t)(d + 1) * NQ + l) * NP];
+                        for (int m = 0; m < NP; ++m) to[m] += dv * from[m];
+                    }
+                }
+    }
+    return A;
+}
+
 }  // namespace hp

@@ -921,9 +921,9 @@ __device__ __forceinline__ void point_factors(const double* g, int NQp, const do
 // G ~ h differ by h^2, which one scale would push into FP16's subnormals on
 // small elements), then the scaled values; isc[2e], isc[2e + 1] undo the scales
 template <int SHAPE, bool CURVED>
-__global__ void tc_geom16_kernel(const double* g, int NQp, const double* z, const double* w, int Q, uint16_t* out,
-                                 float* isc, int64_t n_elem, int nch) {
-    const int NQ = Q * Q * Q, lane = threadIdx.x & 31;
+__global__ void tc_geom16_kernel(const double* g, int NQp, int NQ, const double* z, const double* w, int Q,
+                                 uint16_t* out, float* isc, int64_t n_elem, int nch) {
+    const int lane = threadIdx.x & 31;
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x / 32);
     for (int64_t e = blockIdx.x * (int64_t)(blockDim.x / 32) + threadIdx.x / 32; e < n_elem; e += nw) {
         double mg = 0.0, mm = 0.0;
@@ -955,12 +955,12 @@ __global__ void tc_geom16_kernel(const double* g, int NQp, const double* z, cons
 }
 
 template <int SHAPE>
-cudaError_t geom16_shape(bool curved, const double* g, int NQp, const double* z, const double* w, int Q,
+cudaError_t geom16_shape(bool curved, const double* g, int NQp, int NQ, const double* z, const double* w, int Q,
                          uint16_t* out, float* isc, int64_t n_elem, int nch, cudaStream_t s) {
     const int64_t blocks = (n_elem + 7) / 8;
     const unsigned grid = (unsigned)(blocks < 8192 ? blocks : 8192);
-    if (curved) tc_geom16_kernel<SHAPE, true><<<grid, 256, 0, s>>>(g, NQp, z, w, Q, out, isc, n_elem, nch);
-    else tc_geom16_kernel<SHAPE, false><<<grid, 256, 0, s>>>(g, NQp, z, w, Q, out, isc, n_elem, nch);
+    if (curved) tc_geom16_kernel<SHAPE, true><<<grid, 256, 0, s>>>(g, NQp, NQ, z, w, Q, out, isc, n_elem, nch);
+    else tc_geom16_kernel<SHAPE, false><<<grid, 256, 0, s>>>(g, NQp, NQ, z, w, Q, out, isc, n_elem, nch);
     return cudaGetLastError();
 }
 
@@ -1013,7 +1013,7 @@ int tc_chunk_points() { return kNPT; }
 
 int64_t tc_geom_halves(int64_t n_elem, int nch) { return (n_elem + 127) / 128 * nch * 7 * kNPT * 128; }
 
-cudaError_t tc_geom_layout16(int shape, bool curved, const double* g, int NQp, const double* z, const double* w, int Q,
+cudaError_t tc_geom_layout16(int shape, bool curved, const double* g, int NQp, int NQ, const double* z, const double* w, int Q,
                              uint16_t* out, float* isc, int64_t n_elem, int nch, cudaStream_t s) {
     if (n_elem <= 0) return cudaSuccess;
     const int64_t ntiles = (n_elem + 127) / 128;
@@ -1021,10 +1021,10 @@ cudaError_t tc_geom_layout16(int shape, bool curved, const double* g, int NQp, c
     if (e == cudaSuccess) e = cudaMemsetAsync(isc, 0, (size_t)ntiles * 128 * 2 * sizeof(float), s);
     if (e != cudaSuccess) return e;
     switch (shape) {
-        case HP_HEX: return geom16_shape<HP_HEX>(curved, g, NQp, z, w, Q, out, isc, n_elem, nch, s);
-        case HP_PRISM: return geom16_shape<HP_PRISM>(curved, g, NQp, z, w, Q, out, isc, n_elem, nch, s);
-        case HP_PYR: return geom16_shape<HP_PYR>(curved, g, NQp, z, w, Q, out, isc, n_elem, nch, s);
-        default: return geom16_shape<HP_TET>(curved, g, NQp, z, w, Q, out, isc, n_elem, nch, s);
+        case HP_HEX: return geom16_shape<HP_HEX>(curved, g, NQp, NQ, z, w, Q, out, isc, n_elem, nch, s);
+        case HP_PRISM: return geom16_shape<HP_PRISM>(curved, g, NQp, NQ, z, w, Q, out, isc, n_elem, nch, s);
+        case HP_PYR: return geom16_shape<HP_PYR>(curved, g, NQp, NQ, z, w, Q, out, isc, n_elem, nch, s);
+        default: return geom16_shape<HP_TET>(curved, g, NQp, NQ, z, w, Q, out, isc, n_elem, nch, s);
     }
 }
 

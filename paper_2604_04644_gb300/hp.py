@@ -56,7 +56,7 @@ class hp_mesh_desc(ctypes.Structure):
     _fields_ = [("n_elem", ctypes.c_int64), ("shape", ctypes.c_void_p), ("P", ctypes.c_void_p),
                 ("Q", ctypes.c_void_p), ("vert", ctypes.c_void_p), ("xyz", ctypes.c_void_p),
                 ("n_vert", ctypes.c_int64), ("curved", ctypes.c_void_p), ("deformation", ctypes.c_int32),
-                ("geometry", ctypes.c_int32)]
+                ("geometry", ctypes.c_int32), ("quadrature", ctypes.c_int32)]
 
 
 class hp_mesh2d_desc(ctypes.Structure):
@@ -164,7 +164,7 @@ def hp_mesh_create(mesh, device=0):
     d = hp_mesh_desc(int(mesh["n_elem"]), keep["shape"].ctypes.data, keep["P"].ctypes.data,
                      keep["Q"].ctypes.data, keep["vert"].ctypes.data, keep["xyz"].ctypes.data,
                      int(keep["xyz"].shape[0]), keep["curved"].ctypes.data, int(mesh["deformation"]),
-                     int(mesh.get("geometry", 0)))
+                     int(mesh.get("geometry", 0)), int(mesh.get("quadrature", 0)))
     h = _vp()
     _check(_lib.hp_mesh_create(ctypes.byref(d), int(device), ctypes.byref(h)), "hp_mesh_create")
     return h.value

@@ -45,9 +45,9 @@ from oracle import operators as ops
 U32 = 2.0 ** -24
 
 
-def eta_matrices(shape, P, Q):
+def eta_matrices(shape, P, Q, reduced=0):
     """A[c] (4, NQ, NP): B and d B / d eta_d at the points."""
-    ref = ops.reference(shape, P, Q)
+    ref = ops.reference(shape, P, Q, reduced)
     Tinv = np.linalg.inv(ref["T"])                                   # [l, a, d] = d xi_a / d eta_d
     Deta = np.einsum("alm,lad->dlm", np.stack(ref["Dxi"]), Tinv)
     return np.concatenate([ref["B"][None], Deta])
@@ -71,12 +71,12 @@ def tc_chain(mesh, x, lam, kind):
     """(|A|^T |M| |A| |x|)_m for every output coefficient."""
     co, _ = ops.layout(mesh)
     out = np.zeros(co[-1])
-    geometry = mesh.get("geometry", 0)
+    geometry, rq = mesh.get("geometry", 0), mesh.get("quadrature", 0)
     for (shape, P, Q, cv), el in ops._blocks(mesh).items():
         el = np.array(el)
         X = ops._verts(mesh, shape, el)
-        A = np.abs(eta_matrices(shape, P, Q))
-        six, _ = ops.geometric_factors_block(shape, P, Q, X, bool(cv), mesh["deformation"], geometry)
+        A = np.abs(eta_matrices(shape, P, Q, rq))
+        six, _ = ops.geometric_factors_block(shape, P, Q, X, bool(cv), mesh["deformation"], geometry, rq)
         M = _metric_abs(six, lam, kind)
         idx = co[el][:, None] + np.arange(co[el[0] + 1] - co[el[0]])[None, :]
         v = np.einsum("cln,en->ecl", A, np.abs(x[idx]))              # (Ne, 4, NQ)
@@ -118,7 +118,7 @@ def tc_bound(mesh, x, lam, kind, u):
     chain = tc_chain(mesh, x, lam, kind)
     for e in range(mesh["n_elem"]):
         NP = co[e + 1] - co[e]
-        NQ = int(mesh["Q"][e]) ** 3
+        NQ = ops.n_points(int(mesh["shape"][e]), int(mesh["Q"][e]), mesh.get("quadrature", 0))
         out[co[e]:co[e + 1]] = 1.1 * (5 * u + (NP + 4 * NQ) * U32) * chain[co[e]:co[e + 1]]
     return out
 
