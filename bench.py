@@ -55,9 +55,10 @@ N_MODES = (lambda P: (P + 1) ** 3, lambda P: (P + 1) ** 2 * (P + 2) // 2,
 # DRAM bytes (read + write) of one launch, measured by ncu on this workload
 # for the kernel named; a kernel whose code changed after the measurement is
 # left out (its traffic reads null)
-MEASURED_TRAFFIC = {"sf_kernel<pyr,P8,f64>": 371767040,           # profiles/sf_kernel_pyr_P8_fp64.md
-                    "tc_emat_kernel<tet,P8,bf16>": 99799040,      # profiles/tc_emat_kernel_tet_P8_bf16_mixed16.md
-                    "sf_kernel<pyr,P8,f32>": 185675520}          # profiles/sf_kernel_pyr_P8_fp32_mixed16.md
+MEASURED_TRAFFIC = {"sf_kernel<pyr,P8,f64>": 371879424,           # profiles/sf_kernel_pyr_P8_fp64.md
+                    "tc_emat_kernel<tet,P8,bf16>": 99670528,      # profiles/tc_emat_kernel_tet_P8_bf16_mixed16.md
+                    "tc_emat_kernel<pyr,P7,bf16>": 75625216,      # profiles/tc_emat_kernel_pyr_P7_bf16_mixed16.md
+                    "sf_kernel<pyr,P8,f32>": 185804800}          # profiles/sf_kernel_pyr_P8_fp32_mixed16.md
 
 
 # small, fixed cases for ncu captures (a few hundred MB on the device):
@@ -71,6 +72,7 @@ PROFILE_CASES = {
     # shape -1: the bench mesh itself (16^3 mixed curved cells) at order P
     "mesh16_bf16_P8": (-1, 8, 0, "ELEMAT", "BF16"),
     "mesh16_bf16_P4": (-1, 4, 0, "ELEMAT", "BF16"),
+    "mesh16_bf16_P7": (-1, 7, 0, "ELEMAT", "BF16"),
 }
 
 
