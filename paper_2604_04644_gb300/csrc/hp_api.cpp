@@ -386,7 +386,7 @@ hp_status ensure_tc(hp_mesh m, int es) {
     // FP16 metric factors (scaled per element) at every point in the tile-major
     // order the epilogue reads: from the curved factors or the affine records
     for (Block& b : m->blocks) {
-        if (b.d_geom_tc || n_modes(b.shape, b.P) > kTcMaxModes) continue;
+        if (b.d_geom_tc || n_modes(b.shape, b.P) > kTcMaxModes16) continue;
         const DeviceBlobs& db = m->blobs.at(b.shape * 16 + b.P);
         hp_status st = upload<uint16_t>(&b.d_geom_tc, nullptr, (size_t)tc_geom_halves(b.n_elem, db.tc_nch));
         if (!st) st = upload<float>(&b.d_gscale_tc, nullptr, (size_t)((b.n_elem + 127) / 128 * 128 * 2));
@@ -401,12 +401,13 @@ hp_status ensure_tc(hp_mesh m, int es) {
     return HP_OK;
 }
 
-bool tc_fits(const Block& b) { return n_modes(b.shape, b.P) <= kTcMaxModes; }
+// the tensor-core elemental matrix: 256 modes (TF32), 320 (BF16, streamed backward tiles)
+bool tc_fits(const Block& b, hp_dtype dt) { return n_modes(b.shape, b.P) <= (dt == HP_BF16 ? kTcMaxModes16 : kTcMaxModes); }
 bool tc_hyb_fits(const Block& b, hp_dtype dt) {
     return n_modes(b.shape, b.P) <= (dt == HP_BF16 ? kTcHybMaxModes : kTcHybMaxModesTF32);
 }
 bool tc_strategy_fits(const Block& b, hp_dtype dt, int k) {
-    return (k == HP_STRAT_ELEMAT && tc_fits(b)) || (k == HP_STRAT_HYBRID && tc_hyb_fits(b, dt));
+    return (k == HP_STRAT_ELEMAT && tc_fits(b, dt)) || (k == HP_STRAT_HYBRID && tc_hyb_fits(b, dt));
 }
 bool mat_fits(const Block& b) { return n_modes(b.shape, b.P) <= kMatMaxModes; }
 
@@ -417,7 +418,8 @@ bool mat_fits(const Block& b) { return n_modes(b.shape, b.P) <= kMatMaxModes; }
 // matrices are mass, Laplacian or Helmholtz in FP64 / FP32 (N_P <= 256)
 bool strategy_available(const hp_op_s* op, size_t i, int k) {
     if (op->mesh->quadrature)   // the reduced rule: elemental matrices only (tensor cores up to 256 modes)
-        return k == HP_STRAT_ELEMAT && (!(op->dtype == HP_TF32 || op->dtype == HP_BF16) || tc_fits(op->mesh->blocks[i]));
+        return k == HP_STRAT_ELEMAT &&
+               (!(op->dtype == HP_TF32 || op->dtype == HP_BF16) || tc_fits(op->mesh->blocks[i], op->dtype));
     if (k == HP_STRAT_SUMFAC) return true;
     if (needs_deriv_geom(op->kind)) return false;
     if (op->dtype == HP_TF32 || op->dtype == HP_BF16) return tc_strategy_fits(op->mesh->blocks[i], op->dtype, k);
@@ -657,13 +659,16 @@ cudaError_t launch_block(hp_op op, size_t bi, int tile, double lambda, const voi
         a.fwd_bytes = bf ? blob.tc_fwd16 : blob.tc_fwd;
         a.bwd_bytes = bf ? blob.tc_bwd16 : blob.tc_bwd;
         // BF16: one stage per chunk (its whole forward operand, read again by the
-        // backward MMAs); TF32: forward slices and backward tiles separately
-        a.stage_bytes = bf ? a.fwd_bytes : (std::max(4 * tc_chunk_points() * 128, a.bwd_bytes) + 1023) & ~1023;
+        // backward MMAs); TF32, and BF16 past 256 modes: forward slices and
+        // backward tiles separately
+        a.stream_bwd = bf && a.NPpad > kTcMaxModes;
+        a.stage_bytes = (bf && !a.stream_bwd) ? a.fwd_bytes
+                                              : (std::max(4 * tc_chunk_points() * 128, a.bwd_bytes) + 1023) & ~1023;
         a.err = op->d_err;
         // split for the graph's share: BF16 always; TF32 up to 16 point chunks
         // (measured on the 16^3 mesh: TF32 at P = 5..7 ran 9-13 % slower
         // unsplit, where its longer chunks keep more CTAs busy when split)
-        a.concurrent_tiles = (bf || a.nch <= 16) ? op->tc_concurrent_tiles : 0;
+        a.slot_share = (bi < op->tc_share.size()) ? op->tc_share[bi] : 0.0;
         a.part_out = nullptr;
         if (op->deterministic) {   // split tiles: partial outputs in a scratch of the op, summed in part order
             const int ns = tc_emat_nsplit(a);
@@ -1068,7 +1073,7 @@ hp_status hp_op_create(hp_mesh m, hp_opkind kind, hp_strategy strategy, hp_dtype
     if (m->quadrature) {
         bool ok = strategy == HP_STRAT_ELEMAT && (kind == HP_MASS || kind == HP_LAPLACIAN || kind == HP_HELMHOLTZ);
         if (ok && tcore)
-            for (const Block& b : m->blocks) ok = ok && tc_fits(b);
+            for (const Block& b : m->blocks) ok = ok && tc_fits(b, dtype);
         if (!ok) {
             set_error("hp_op_create: a reduced-rule mesh has the elemental-matrix mass, Laplacian and Helmholtz "
                       "operators (tensor cores: blocks of at most 256 modes)");
@@ -1343,14 +1348,28 @@ hp_status hp_op_apply_graph(hp_op op, double lambda, const void* in, void* out, 
         // the tensor-core blocks run concurrently in the graph: each splits its
         // tiles for its share of the GPU (the warm-up launches below size the
         // deterministic scratch with the same split)
-        struct ResetTiles {
+        struct ResetShare {
             hp_op o;
-            ~ResetTiles() { o->tc_concurrent_tiles = 0; }
-        } reset_tiles{op};
-        op->tc_concurrent_tiles = 0;
-        if (op->dtype == HP_TF32 || op->dtype == HP_BF16)
-            for (size_t i = 0; i < nb; ++i)
-                if (op->strat[i] == HP_STRAT_ELEMAT) op->tc_concurrent_tiles += (op->mesh->blocks[i].n_elem + 127) / 128;
+            ~ResetShare() { o->tc_share.clear(); }
+        } reset_share{op};
+        op->tc_share.assign(nb, 0.0);
+        if (op->dtype == HP_TF32 || op->dtype == HP_BF16) {
+            // work of a block: tiles x point chunks x (K_P + N_P), the forward and
+            // backward MMA widths; BF16 always, TF32 up to 16 chunks (measured on
+            // the 16^3 mesh: TF32 at P = 5..7 ran 9-13 % slower unsplit)
+            const bool bf = op->dtype == HP_BF16;
+            double total = 0.0;
+            for (size_t i = 0; i < nb; ++i) {
+                const Block& b = op->mesh->blocks[i];
+                if (op->strat[i] != HP_STRAT_ELEMAT) continue;
+                const DeviceBlobs& blob = op->mesh->blobs.at(b.shape * 16 + b.P);
+                if (!bf && blob.tc_nch > 16) continue;
+                op->tc_share[i] = (double)((b.n_elem + 127) / 128) * blob.tc_nch *
+                                  ((bf ? blob.tc_KP16 : blob.tc_KP) + blob.tc_NPpad);
+                total += op->tc_share[i];
+            }
+            for (double& w : op->tc_share) w = total > 0.0 ? w / total : 0.0;
+        }
         // first launches set kernel attributes outside the capture
         for (size_t i = 0; i < nb; ++i) {
             cudaError_t e = launch_block(op, i, op->tile[i], lambda, in, out, s);

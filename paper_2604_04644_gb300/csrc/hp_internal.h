@@ -143,9 +143,10 @@ struct hp_op_s {
     void* d_items = nullptr;                    // WorkItem list, by decreasing cost
     int* d_next = nullptr;                      // work-list counter
     int n_items = 0, wl_smem = 0, wl_grid = 0;
-    // while a graph of all blocks is captured: the tensor-core elemental-matrix
-    // blocks' total tile count, so that each splits its tiles for its share of the GPU
-    int64_t tc_concurrent_tiles = 0;
+    // while a graph of all blocks is captured: each tensor-core elemental-matrix
+    // block's share of the GPU (its tiles x chunks x (K_P + N_P) over all such
+    // blocks'), for which it splits its tiles; empty otherwise
+    std::vector<double> tc_share;
     // tensor-core hybrid blocks: u = B uhat and u' at every point of the mesh's
     // point layout (two FP32 vectors; blocks write disjoint ranges)
     float* hyb_u = nullptr;
@@ -252,7 +253,8 @@ struct TCArgs {
     int fwd_bytes, bwd_bytes, stage_bytes;
     int es;                            // operand bytes: 4 TF32, 2 BF16
     int nsplit, stages, ubufs;         // set by the launcher
-    int64_t concurrent_tiles;          // tiles of all tensor-core blocks launched together (0: this block alone)
+    double slot_share;                 // share of the GPU's CTA slots for this block in a concurrent graph (0: all)
+    int stream_bwd;                    // BF16 past 256 modes: stream the backward tiles (two output MMAs)
     float* part_out;                   // nullptr: split tiles add with atomics; else [nsplit][n_elem][NP]
                                        // partial outputs summed in part order (deterministic)
     unsigned int* err;
@@ -276,6 +278,7 @@ struct HybArgs {
 };
 cudaError_t tc_hyb_launch(const HybArgs& a, int mode, cudaStream_t s);
 constexpr int kTcMaxModes = 256;
+constexpr int kTcMaxModes16 = 320;      // BF16 elemental matrix with streamed backward tiles
 // the tensor-core hybrid: BF16 up to 512 modes; TF32 up to 352 (its U tile,
 // 128 x K_P x 4 bytes, and two ring stages must fit in shared memory)
 constexpr int kTcHybMaxModes = 512, kTcHybMaxModesTF32 = 352;

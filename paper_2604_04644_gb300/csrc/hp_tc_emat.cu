@@ -180,10 +180,15 @@ __device__ __forceinline__ void arrive_warp(uint64_t* bar) {
 }
 
 
-template <int ES, int EW>
+// SB (BF16 only): stream the backward tiles R_c like TF32 instead of reading
+// the forward stage again; the blocks of 257..320 modes, whose forward stages
+// are too large to hold kFwdBufs - 1 chunks, and whose output takes two
+// backward MMAs (N <= 256 each)
+template <int ES, int EW, bool SB = false>
 __global__ void __launch_bounds__(Epi<EW>::kThreads, Epi<EW>::kCtas) tc_emat_kernel(const __grid_constant__ TCArgs a) {
     using O = Op<ES>;
     using E = Epi<EW>;
+    constexpr bool kReuse = ES == 2 && !SB;   // the backward reads the forward stage (MN-major)
     constexpr int kGroups = E::kGroups, kPts = E::kPts, kRows = E::kRows;
     using GV = GVt<kPts>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -249,7 +254,7 @@ __global__ void __launch_bounds__(Epi<EW>::kThreads, Epi<EW>::kCtas) tc_emat_ker
                 chunk_range(w, kb, ke);
                 // the MMA issuer's order: forward of chunk t, backward of chunk t - (kFwdBufs - 1);
                 // BF16: one stage per chunk (all forward slices), read again by the backward
-                if constexpr (ES == 2) {
+                if constexpr (kReuse) {
                     for (int t = kb; t < ke && ok; ++t) put(a.img + (size_t)t * a.chunk_bytes, (uint32_t)a.fwd_bytes);
                     continue;
                 }
@@ -279,6 +284,11 @@ __global__ void __launch_bounds__(Epi<EW>::kThreads, Epi<EW>::kCtas) tc_emat_ker
             const uint32_t id_f = tc::instr_desc(O::FMT, 128, kNPT * (a.c1 - a.c0));
             const uint32_t id_b = tc::instr_desc(O::FMT, 128, a.NPpad);
             const uint32_t id_bt = id_b | (1u << 16);                     // B operand MN-major
+            // streamed backward past 256 modes: N = 256 then N = NPpad - 256, the
+            // second reading the tile from its row 256 on (K-major rows of VROW bytes)
+            const uint32_t nb0 = a.NPpad > 256 ? 256u : (uint32_t)a.NPpad, nb1 = (uint32_t)a.NPpad - nb0;
+            const uint32_t id_b0 = tc::instr_desc(O::FMT, 128, nb0), id_b1 = tc::instr_desc(O::FMT, 128, nb1 > 0 ? nb1 : 16);
+            constexpr uint32_t kHalf16 = (256 * O::VROW) >> 4;
             // descriptors are built once: an operand x bytes past a base adds x / 16
             // to the start-address field (shared addresses stay below 256 KB, so
             // the 14-bit field never carries)
@@ -310,7 +320,7 @@ __global__ void __launch_bounds__(Epi<EW>::kThreads, Epi<EW>::kCtas) tc_emat_ker
                         if (!wait_bar(&B->fwd_empty[fb.i], fb.ph ^ 1u, B, a.err)) { ok = false; break; }
                         // columns (fb*4 + c0)*16 .. of the accumulator = components c0..c1-1
                         const uint32_t d = tbase + (fb.i * 4 + (uint32_t)a.c0) * kNPT;
-                        if constexpr (ES == 2) {
+                        if constexpr (kReuse) {
                             // one ring stage per chunk holding every K slice
                             if (!wait_bar(&B->full[fs.i], fs.ph, B, a.err)) { ok = false; break; }
                             tc::fence_after();
@@ -346,7 +356,7 @@ __global__ void __launch_bounds__(Epi<EW>::kThreads, Epi<EW>::kCtas) tc_emat_ker
                         }
                         tc::fence_after();
                         const uint64_t dVb = dV + vb.i * 4 * v16;
-                        if constexpr (ES == 2) {
+                        if constexpr (kReuse) {
                             const uint64_t dRs = dRt + bs.i * st16;
                             for (int c = a.c0; c < a.c1; ++c)
                                 O::mma(tbase + kOutCol, dVb + (uint32_t)c * v16, dRs + (uint32_t)c * 128, id_bt,
@@ -359,9 +369,13 @@ __global__ void __launch_bounds__(Epi<EW>::kThreads, Epi<EW>::kCtas) tc_emat_ker
                                 tc::fence_after();
                                 const uint64_t dRs = dRb + fs.i * st16;
 #pragma unroll
-                                for (uint32_t s = 0; s < O::VROW / 32; ++s)
-                                    O::mma(tbase + kOutCol, dVb + (uint32_t)c * v16 + s * 2, dRs + s * 2, id_b,
-                                           !(k == kb && c == a.c0 && s == 0));
+                                for (uint32_t s = 0; s < O::VROW / 32; ++s) {
+                                    const uint32_t acc = !(k == kb && c == a.c0 && s == 0);
+                                    O::mma(tbase + kOutCol, dVb + (uint32_t)c * v16 + s * 2, dRs + s * 2, id_b0, acc);
+                                    if (nb1 > 0)
+                                        O::mma(tbase + kOutCol + 256, dVb + (uint32_t)c * v16 + s * 2, dRs + kHalf16 + s * 2,
+                                               id_b1, acc);
+                                }
                                 tc::commit(&B->empty[fs.i]);
                                 fs.next();
                             }
@@ -423,7 +437,8 @@ __global__ void __launch_bounds__(Epi<EW>::kThreads, Epi<EW>::kCtas) tc_emat_ker
         auto gather_u = [&](int j, int64_t offs) {
             unsigned char* dU = sU + (size_t)j * 128 * a.KP * ES;
             if (a.KP <= 128) gather_rows(std::integral_constant<int, 8>{}, std::integral_constant<int, 4>{}, dU, offs);
-            else gather_rows(std::integral_constant<int, 4>{}, std::integral_constant<int, kTcMaxModes / 32>{}, dU, offs);
+            else if (a.KP <= 256) gather_rows(std::integral_constant<int, 4>{}, std::integral_constant<int, 8>{}, dU, offs);
+            else gather_rows(std::integral_constant<int, 2>{}, std::integral_constant<int, kTcMaxModes16 / 32>{}, dU, offs);
             tc::fence_async_smem();
             arrive_warp(&B->u_full[j]);
         };
@@ -991,8 +1006,8 @@ int tc_stages(int KP, int stage_bytes, int es, int ubufs, int cap) {
 struct TcPlan {
     int ctas, ubufs, stages, smem;
 };
-TcPlan tc_plan(int KP, int NPpad, int stage_bytes, int es, bool allow2) {
-    const int need = es == 2 ? kFwdBufs + 1 : 2;    // BF16 holds a stage kFwdBufs - 1 chunks
+TcPlan tc_plan(int KP, int NPpad, int stage_bytes, int es, bool allow2, bool stream_bwd = false) {
+    const int need = (es == 2 && !stream_bwd) ? kFwdBufs + 1 : 2;    // BF16 holds a stage kFwdBufs - 1 chunks
     for (int ctas = 2; ctas >= 1; --ctas) {
         if (ctas == 2 && !(allow2 && es == 2 && NPpad <= kOutCol / 3 && kOutCol + NPpad <= 256)) continue;
         const int cap = ctas == 2 ? kSmemCap2 : kSmemCap1;
@@ -1036,13 +1051,14 @@ int tc_emat_nsplit(const TCArgs& a) {
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return 0;
-    const TcPlan pl = tc_plan(a.KP, a.NPpad, a.stage_bytes, a.es, ntiles >= 2 * (int64_t)sms);
+    const TcPlan pl = tc_plan(a.KP, a.NPpad, a.stage_bytes, a.es, ntiles >= 2 * (int64_t)sms, a.stream_bwd != 0);
     if (pl.stages == 0) return 0;
     // parts per tile: as many as keep every work item in one wave of the
     // launch's CTA slots (a ceiling would leave some CTAs a second item, and
     // the launch twice an item's time), at least four chunks a part
-    // (blocks launched together in a graph share the slots by their tiles)
-    const int64_t ns = std::max<int64_t>(1, (int64_t)sms * pl.ctas / std::max<int64_t>(ntiles, a.concurrent_tiles));
+    // (a block launched with others in a graph splits for its share of the slots)
+    const double slots = (double)sms * pl.ctas * (a.slot_share > 0.0 ? a.slot_share : 1.0);
+    const int64_t ns = std::max<int64_t>(1, (int64_t)(slots / (double)ntiles));
     const int64_t cap = a.nch / 4 > 1 ? a.nch / 4 : 1;
     return (int)(ns < cap ? ns : cap);
 }
@@ -1100,11 +1116,13 @@ cudaError_t tc_emat_launch(const TCArgs& a, cudaStream_t s) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const TcPlan pl = tc_plan(a.KP, a.NPpad, a.stage_bytes, a.es, ntiles >= 2 * (int64_t)sms);
+    if (a.NPpad > (a.stream_bwd ? kTcMaxModes16 : kTcMaxModes) || (a.stream_bwd && a.es != 2)) return cudaErrorInvalidValue;
+    const TcPlan pl = tc_plan(a.KP, a.NPpad, a.stage_bytes, a.es, ntiles >= 2 * (int64_t)sms, a.stream_bwd != 0);
     if (pl.stages == 0) return cudaErrorInvalidValue;
     b.ubufs = pl.ubufs;
     b.stages = pl.stages;
-    auto kern = a.es == 4 ? tc_emat_kernel<4, 16> : pl.ctas == 2 ? tc_emat_kernel<2, 8> : tc_emat_kernel<2, 16>;
+    auto kern = a.es == 4 ? tc_emat_kernel<4, 16> : a.stream_bwd ? tc_emat_kernel<2, 16, true>
+              : pl.ctas == 2 ? tc_emat_kernel<2, 8> : tc_emat_kernel<2, 16>;
     const int threads = pl.ctas == 2 ? Epi<8>::kThreads : Epi<16>::kThreads;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, pl.smem);
     if (e != cudaSuccess) return e;

@@ -11,7 +11,7 @@ well), so |error_m| <= 4 u (|A|^T |M| |A| |uhat|)_m to first order, plus FP32
 accumulation (~1e-7).  The ratio of that absolute sum to ||out||_inf is the
 cancellation factor; random-sign rounding errors keep the measured error near
 1 u, and 8 u allows a cancellation factor of 2 at full correlation.  Blocks whose mode
-count exceeds the tensor-memory budget (N_P > 256) run FP32 sum factorisation
+count exceeds the tensor-memory budget (N_P > 256; BF16: > 320) run FP32 sum factorisation
 and are held to the FP32 bound of test_gpu_parity.  BF16 (8 significant
 bits) takes the same argument with u = 2^-8: BF16_TOL = 8 u.
 """
@@ -30,6 +30,7 @@ TF32_TOL = 8 * TF32_U
 BF16_U = 2.0 ** -8          # 8 significant bits, round to nearest
 BF16_TOL = 8 * BF16_U
 MAX_TC_MODES = 256
+MAX_TC_MODES_PREC = {"tf32": 256, "bf16": 320}    # BF16 past 256 modes: streamed backward tiles, two output MMAs
 
 
 @pytest.fixture(scope="module")
@@ -90,13 +91,13 @@ def test_tensor_core_matches_oracle(hp, P, opname, prec):
     from oracle.basis import n_modes
     errs = per_shape_errors(mesh, co, y, ref)
     for s, err in errs.items():
-        tol = (TF32_TOL if prec == "tf32" else BF16_TOL) if n_modes(s, P) <= MAX_TC_MODES else fp32_tol(P)
+        tol = (TF32_TOL if prec == "tf32" else BF16_TOL) if n_modes(s, P) <= MAX_TC_MODES_PREC[prec] else fp32_tol(P)
         assert err <= tol, (s, err, tol)
     # per output: the first-order rounding bound of the form each block runs
     from tests import roundoff
     tc = roundoff.tc_bound(mesh, x32, 1.3, opname, TF32_U if prec == "tf32" else BF16_U)
     sf = roundoff.sf32_bound(mesh, x32, 1.3, opname)
-    fits = np.repeat([n_modes(int(s), P) <= MAX_TC_MODES for s in mesh["shape"]], np.diff(co))
+    fits = np.repeat([n_modes(int(s), P) <= MAX_TC_MODES_PREC[prec] for s in mesh["shape"]], np.diff(co))
     bound = np.where(fits, tc, sf)
     assert (np.abs(y - ref) <= bound).all(), np.max(np.abs(y - ref) / bound)
 
@@ -231,3 +232,31 @@ def test_deterministic_split_tiles_are_bitwise_reproducible(hp, dt):
     tol = TF32_TOL if dt == "tf32" else BF16_TOL
     assert rel_err(ys[0].astype(np.float64), ref) <= tol
     assert np.abs(ys[0] - ya.cpu().numpy()).max() <= 1e-5 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("shape,P,curved", [(2, 8, True), (1, 7, False), (2, 8, False)])
+def test_bf16_past_256_modes(hp, shape, P, curved):
+    """BF16 blocks of 257..320 modes (pyramid P8: 285, prism P7: 288): the
+    backward tiles are streamed and the output takes two MMAs (N = 256 and
+    N_P - 256); many tiles, sampled elements against the oracle, per-output
+    bound on a small mesh of the same block."""
+    mesh = inputs.replicated_mesh(shape, P, 2000 + 13, curved=curved)
+    co, _ = oracle_ops.layout(mesh)
+    x = inputs.random_coefficients(91, co)
+    y, strat = run_tc(hp, mesh, "helmholtz", x, 1.0, hp.HP_BF16)
+    assert strat.tolist() == [hp.HP_STRAT_ELEMAT]
+    rng = np.random.default_rng(5)
+    sample = np.unique(np.concatenate([rng.choice(mesh["n_elem"], 30, replace=False), [0, 127, 128, 2012]]))
+    x32 = x.astype(np.float32).astype(np.float64)
+    ref = oracle_ops.apply("helmholtz", mesh, x32, 1.0, elems=sample)
+    idx = np.concatenate([np.arange(co[e], co[e + 1]) for e in sample])
+    assert rel_err(y[idx], ref[idx]) <= BF16_TOL
+    small = inputs.replicated_mesh(shape, P, 37, curved=curved)
+    cs, _ = oracle_ops.layout(small)
+    xs = inputs.random_coefficients(92, cs)
+    ys, _ = run_tc(hp, small, "helmholtz", xs, 1.0, hp.HP_BF16)
+    xs32 = xs.astype(np.float32).astype(np.float64)
+    refs = oracle_ops.apply("helmholtz", small, xs32, 1.0)
+    from tests import roundoff
+    bound = roundoff.tc_bound(small, xs32, 1.0, "helmholtz", BF16_U)
+    assert (np.abs(ys - refs) <= bound).all(), np.max(np.abs(ys - refs) / bound)
