@@ -6,7 +6,7 @@ predicts, for every block of an operator, the log10 run time of each
 strategy the library builds, and the schedule takes the argmin
 (hp_op_schedule_mlp).  The network is trained on timings the library
 generates itself, by the library's own forward/backward/Adam kernels
-(hp_mlp_*).  Exhaustive measurement is the fallback and the judge of its
+(hp_mlp_*).  Exhaustive measurement is the fallback and the check on its
 mispredictions: per block alone (hp_op_schedule_exhaustive) or on the time of
 the whole concurrent graph (hp_op_schedule_graph).
 
