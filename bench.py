@@ -925,7 +925,9 @@ def run_block_table(local, reps=10):
                                     ("tf32_tc_hybrid", hp.HP_STRAT_HYBRID, hp.HP_TF32),
                                     ("bf16_tc_hybrid", hp.HP_STRAT_HYBRID, hp.HP_BF16)):
                 op = hp.hp_op_create(h, hp.HP_HELMHOLTZ, strat, dt)
-                if int(hp.hp_op_strategies(op, 1)[0]) != strat:    # not built for this block
+                try:   # the form itself, also where the operator starts the block on another one
+                    hp.hp_op_strategies(op, 1, [strat])
+                except hp.HpError:   # not built for this block
                     hp.hp_op_destroy(op)
                     line[name] = None
                     continue

@@ -194,11 +194,14 @@ hp_status hp_geom_copy(hp_mesh mesh, double* out7, double* out9);
  * HP_ADVECTION_DIFFUSION_REACTION); arrays passed to hp_op_apply are double (HP_FP64) or
  * float (HP_FP32, HP_TF32, HP_BF16).  HP_TF32 and HP_BF16 take HP_STRAT_ELEMAT (or AUTO)
  * or HP_STRAT_HYBRID and the kinds HP_MASS, HP_LAPLACIAN, HP_HELMHOLTZ: blocks
- * with at most 256 modes per element (TF32 elemental matrix), 320 (BF16
- * elemental matrix: past 256 modes the backward tiles are streamed and the
- * output takes two MMAs) or 512 (BF16 hybrid)
- * / 352 (TF32 hybrid) run the tensor-core form, larger ones FP32 sum
- * factorisation (hp_op_strategies reports which).  Errors: HP_ERR_ARG,
+ * with at most 256 modes per element (elemental matrix; BF16: 320, past 256
+ * with the backward tiles streamed and the output in two MMAs) or 512 (BF16
+ * hybrid) / 352 (TF32 hybrid) run the tensor-core form, larger ones FP32 sum
+ * factorisation (hp_op_strategies reports which).  BF16 also builds the
+ * elemental matrix for blocks of 321..512 modes (the output in parts of a
+ * tile that each repeat the forward); those blocks start on FP32 sum
+ * factorisation, measured faster on them, and hp_op_strategies or the
+ * schedulers can move them.  Errors: HP_ERR_ARG,
  * HP_ERR_UNSUPPORTED (combination not built), HP_ERR_GEOM / HP_ERR_CUDA from
  * the geometric factors it needs. */
 hp_status hp_op_create(hp_mesh mesh, hp_opkind kind, hp_strategy strategy, hp_dtype dtype,
@@ -266,7 +269,7 @@ hp_status hp_op_tiles(hp_op op, int* tiles, int64_t n_blocks, int set);
  * matrices at once.  HP_ERR_UNSUPPORTED for a dense strategy on a derivative
  * building block, for HP_STRAT_MATRIX outside those limits, and for an
  * HP_TF32 / HP_BF16 operator for anything but HP_STRAT_SUMFAC (FP32),
- * HP_STRAT_ELEMAT (tensor core, blocks of at most 256 modes; BF16: 320) or
+ * HP_STRAT_ELEMAT (tensor core, blocks of at most 256 modes; BF16: 512) or
  * HP_STRAT_HYBRID (tensor core, at most 512 modes in BF16, 352 in TF32).
  * Writing drops the op's captured graph. */
 hp_status hp_op_strategies(hp_op op, int* strategies, int64_t n_blocks, int set);

@@ -51,7 +51,7 @@ def _built(dtype, kind, shape, P, k):
     """Strategy column k is built for a block of (shape, P) of this operator."""
     npm = n_modes(shape, P)
     if dtype in _TC:
-        return (k == 0 or (k == 1 and npm <= (320 if dtype == hp.HP_BF16 else 256))
+        return (k == 0 or (k == 1 and npm <= (512 if dtype == hp.HP_BF16 else 256))
                 or (k == 2 and npm <= (512 if dtype == hp.HP_BF16 else 352)))
     if k == 3:
         return kind in (hp.HP_MASS, hp.HP_LAPLACIAN, hp.HP_HELMHOLTZ) and npm <= 256

@@ -385,9 +385,15 @@ hp_status ensure_tc(hp_mesh m, int es) {
     }
     // FP16 metric factors (scaled per element) at every point in the tile-major
     // order the epilogue reads: from the curved factors or the affine records
+    // (only the blocks this operand type's elemental matrix takes, whose
+    // images, and so their chunk count, were built above)
     for (Block& b : m->blocks) {
-        if (b.d_geom_tc || n_modes(b.shape, b.P) > kTcMaxModes16) continue;
+        if (b.d_geom_tc || n_modes(b.shape, b.P) > (es == 2 ? kTcMaxModes16 : kTcMaxModes)) continue;
         const DeviceBlobs& db = m->blobs.at(b.shape * 16 + b.P);
+        if (db.tc_nch <= 0) {   // unreachable: the image loop above set it
+            set_error("tensor-core geometry layout: no reference image for the block");
+            return HP_ERR_UNSUPPORTED;
+        }
         hp_status st = upload<uint16_t>(&b.d_geom_tc, nullptr, (size_t)tc_geom_halves(b.n_elem, db.tc_nch));
         if (!st) st = upload<float>(&b.d_gscale_tc, nullptr, (size_t)((b.n_elem + 127) / 128 * 128 * 2));
         if (st) return st;
@@ -1112,8 +1118,18 @@ hp_status hp_op_create(hp_mesh m, hp_opkind kind, hp_strategy strategy, hp_dtype
     op->tile.assign(m->blocks.size(), 0);
     op->strat.assign(m->blocks.size(), (int)strategy);
     if (tcore)   // blocks beyond the form's tensor-memory / shared-memory budget run FP32 sum factorisation
-        for (size_t i = 0; i < m->blocks.size(); ++i)
-            if (!tc_strategy_fits(m->blocks[i], dtype, strategy)) op->strat[i] = HP_STRAT_SUMFAC;
+        for (size_t i = 0; i < m->blocks.size(); ++i) {
+            const Block& b = m->blocks[i];
+            if (!tc_strategy_fits(b, dtype, strategy)) op->strat[i] = HP_STRAT_SUMFAC;
+            // BF16 elemental matrices past 320 modes (output in parts of a tile
+            // that each repeat the forward) are built but start on FP32 sum
+            // factorisation, measured faster on them (hex P6 / P7, prism P8:
+            // 1.4-1.7x alone; the 16^3 mesh's graph at P6 16.8 vs 25.3 GDOF/s);
+            // hp_op_strategies and the schedulers can move them.  A
+            // reduced-rule mesh has no sum factorisation: its blocks stay.
+            if (strategy == HP_STRAT_ELEMAT && !m->quadrature && n_modes(b.shape, b.P) > kTcDefaultMaxModes16)
+                op->strat[i] = HP_STRAT_SUMFAC;
+        }
     if (strategy == HP_STRAT_MATRIX)   // blocks beyond the stored-matrix size run sum factorisation
         for (size_t i = 0; i < m->blocks.size(); ++i)
             if (!mat_fits(m->blocks[i])) op->strat[i] = HP_STRAT_SUMFAC;

@@ -255,6 +255,7 @@ struct TCArgs {
     int nsplit, stages, ubufs;         // set by the launcher
     double slot_share;                 // share of the GPU's CTA slots for this block in a concurrent graph (0: all)
     int stream_bwd;                    // BF16 past 256 modes: stream the backward tiles (two output MMAs)
+    int nmpart, mwidth;                // output-mode parts of a tile and their width (set by the launcher)
     float* part_out;                   // nullptr: split tiles add with atomics; else [nsplit][n_elem][NP]
                                        // partial outputs summed in part order (deterministic)
     unsigned int* err;
@@ -278,7 +279,8 @@ struct HybArgs {
 };
 cudaError_t tc_hyb_launch(const HybArgs& a, int mode, cudaStream_t s);
 constexpr int kTcMaxModes = 256;
-constexpr int kTcMaxModes16 = 320;      // BF16 elemental matrix with streamed backward tiles
+constexpr int kTcMaxModes16 = 512;      // BF16 elemental matrix with streamed backward tiles (mode parts of <= 320)
+constexpr int kTcDefaultMaxModes16 = 320;   // BF16 blocks an elemental-matrix operator starts on the tensor cores
 // the tensor-core hybrid: BF16 up to 512 modes; TF32 up to 352 (its U tile,
 // 128 x K_P x 4 bytes, and two ring stages must fit in shared memory)
 constexpr int kTcHybMaxModes = 512, kTcHybMaxModesTF32 = 352;

@@ -47,6 +47,7 @@ constexpr int kNPT = 16;          // quadrature points per chunk
 constexpr int kMaxStages = 8;     // bulk-copy ring: as many stages (2..8) as fit in shared memory
 constexpr int kFwdBufs = 3;       // forward accumulators in flight: the forward MMAs run two chunks ahead
 constexpr int kOutCol = kFwdBufs * 4 * 16;   // TMEM column of the output accumulator
+constexpr int kOutColMax = 512 - kOutCol;    // output columns beside the forward accumulators
 constexpr int kSliceBytes = 4 * kNPT * 128;   // forward operand slice: 64 rows x 128 bytes of modes
 // metric-factor layout: runs of kGeoPts points, kGeoGroups runs per chunk
 constexpr int kGeoGroups = 4, kGeoPts = kNPT / kGeoGroups;
@@ -200,11 +201,17 @@ __global__ void __launch_bounds__(Epi<EW>::kThreads, Epi<EW>::kCtas) tc_emat_ker
     unsigned char* sR = sV + 8 * O::VBYTES;                            // ring
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nst = a.stages;
-    // work items: (tile of 128 elements, part of its point chunks); parts of one
-    // tile add their partial outputs (the output was zeroed first)
-    const int64_t nwork = (a.n_elem + 127) / 128 * a.nsplit;
+    // work items: (tile of 128 elements, part of its point chunks, range of
+    // output modes); chunk parts of one tile add their partial outputs (the
+    // output was zeroed first), mode parts write disjoint modes (BF16 past 320
+    // modes: each recomputes the forward and the metric of its chunks)
+    const int64_t per_tile = (int64_t)a.nsplit * a.nmpart;
+    const int64_t nwork = (a.n_elem + 127) / 128 * per_tile;
+    auto wtile = [&](int64_t w) { return w / per_tile; };
+    auto wpart = [&](int64_t w) { return (int)((w % per_tile) % a.nsplit); };
+    auto wmode0 = [&](int64_t w) { return (int)((w % per_tile) / a.nsplit) * a.mwidth; };
     auto chunk_range = [&](int64_t w, int& kb, int& ke) {
-        const int part = (int)(w % a.nsplit);
+        const int part = wpart(w);
         kb = (int)((int64_t)a.nch * part / a.nsplit);
         ke = (int)((int64_t)a.nch * (part + 1) / a.nsplit);
     };
@@ -284,10 +291,9 @@ __global__ void __launch_bounds__(Epi<EW>::kThreads, Epi<EW>::kCtas) tc_emat_ker
             const uint32_t id_f = tc::instr_desc(O::FMT, 128, kNPT * (a.c1 - a.c0));
             const uint32_t id_b = tc::instr_desc(O::FMT, 128, a.NPpad);
             const uint32_t id_bt = id_b | (1u << 16);                     // B operand MN-major
-            // streamed backward past 256 modes: N = 256 then N = NPpad - 256, the
-            // second reading the tile from its row 256 on (K-major rows of VROW bytes)
-            const uint32_t nb0 = a.NPpad > 256 ? 256u : (uint32_t)a.NPpad, nb1 = (uint32_t)a.NPpad - nb0;
-            const uint32_t id_b0 = tc::instr_desc(O::FMT, 128, nb0), id_b1 = tc::instr_desc(O::FMT, 128, nb1 > 0 ? nb1 : 16);
+            // streamed backward: a work item's output modes m0 .. m0 + mw - 1, as
+            // N = min(mw, 256) then N = mw - 256, reading the tile from its row m0
+            // (and m0 + 256) on (K-major rows of VROW bytes)
             constexpr uint32_t kHalf16 = (256 * O::VROW) >> 4;
             // descriptors are built once: an operand x bytes past a base adds x / 16
             // to the start-address field (shared addresses stay below 256 KB, so
@@ -311,6 +317,10 @@ __global__ void __launch_bounds__(Epi<EW>::kThreads, Epi<EW>::kCtas) tc_emat_ker
             for (int64_t w = blockIdx.x; w < nwork && ok; w += gridDim.x) {
                 int kb, ke;
                 chunk_range(w, kb, ke);
+                const uint32_t m0w = (uint32_t)wmode0(w), mww = (uint32_t)min(a.mwidth, a.NPpad - (int)m0w);
+                const uint32_t nb0 = mww > 256 ? 256u : mww, nb1 = mww - nb0;
+                const uint32_t id_b0 = tc::instr_desc(O::FMT, 128, nb0), id_b1 = tc::instr_desc(O::FMT, 128, nb1 > 0 ? nb1 : 16);
+                const uint32_t mo16 = (m0w * O::VROW) >> 4;
                 if (!wait_bar(&B->u_full[ub.i], ub.ph, B, a.err)) { ok = false; break; }
                 const uint64_t dUw = dU + ub.i * u16;
                 ub.next();
@@ -367,7 +377,7 @@ __global__ void __launch_bounds__(Epi<EW>::kThreads, Epi<EW>::kCtas) tc_emat_ker
                             for (int c = a.c0; c < a.c1 && ok; ++c) {
                                 if (!wait_bar(&B->full[fs.i], fs.ph, B, a.err)) { ok = false; break; }
                                 tc::fence_after();
-                                const uint64_t dRs = dRb + fs.i * st16;
+                                const uint64_t dRs = dRb + fs.i * st16 + mo16;
 #pragma unroll
                                 for (uint32_t s = 0; s < O::VROW / 32; ++s) {
                                     const uint32_t acc = !(k == kb && c == a.c0 && s == 0);
@@ -403,7 +413,7 @@ __global__ void __launch_bounds__(Epi<EW>::kThreads, Epi<EW>::kCtas) tc_emat_ker
         // coefficient offsets of rows kRows warp .. of work item wi's tile: lane
         // i < kRows holds row kRows warp + i's (-1 past the last element)
         auto row_offsets = [&](int64_t wi) -> int64_t {
-            const int64_t e = (wi / a.nsplit) * 128 + warp * kRows + lane;
+            const int64_t e = wtile(wi) * 128 + warp * kRows + lane;
             return (lane < kRows && e < a.n_elem) ? a.coeff_off[e] : (int64_t)-1;
         };
         // U of a tile into buffer j, coalesced: each warp copies the coefficient
@@ -438,7 +448,8 @@ __global__ void __launch_bounds__(Epi<EW>::kThreads, Epi<EW>::kCtas) tc_emat_ker
             unsigned char* dU = sU + (size_t)j * 128 * a.KP * ES;
             if (a.KP <= 128) gather_rows(std::integral_constant<int, 8>{}, std::integral_constant<int, 4>{}, dU, offs);
             else if (a.KP <= 256) gather_rows(std::integral_constant<int, 4>{}, std::integral_constant<int, 8>{}, dU, offs);
-            else gather_rows(std::integral_constant<int, 2>{}, std::integral_constant<int, kTcMaxModes16 / 32>{}, dU, offs);
+            else if (a.KP <= 320) gather_rows(std::integral_constant<int, 2>{}, std::integral_constant<int, 10>{}, dU, offs);
+            else gather_rows(std::integral_constant<int, 1>{}, std::integral_constant<int, kTcMaxModes16 / 32>{}, dU, offs);
             tc::fence_async_smem();
             arrive_warp(&B->u_full[j]);
         };
@@ -457,7 +468,8 @@ __global__ void __launch_bounds__(Epi<EW>::kThreads, Epi<EW>::kCtas) tc_emat_ker
         for (int64_t w = blockIdx.x; w < nwork && ok; w += gridDim.x, ++ntile) {
             int kb, ke;
             chunk_range(w, kb, ke);
-            const int64_t tile = w / a.nsplit;
+            const int64_t tile = wtile(w);
+            const int m0 = wmode0(w), mw = min(a.mwidth, a.NPpad - m0);   // this item's output modes
             const bool more = w + gridDim.x < nwork;
             const int64_t offs_next = more ? row_offsets(w + gridDim.x) : (int64_t)-1;
             // one U buffer: gathered once the previous tile's MMAs completed; two:
@@ -573,12 +585,12 @@ __global__ void __launch_bounds__(Epi<EW>::kThreads, Epi<EW>::kCtas) tc_emat_ker
             tc::fence_after();
             float* stage = reinterpret_cast<float*>(sV);
             constexpr int CB = 8 * O::VBYTES / (128 * 4);
-            for (int cb = 0; cb < a.NPpad; cb += CB) {
+            for (int cb = 0; cb < mw; cb += CB) {
                 // row r, columns h CB / kGroups .. of the pass; 16-byte chunks XOR-swizzled by row
 #pragma unroll
                 for (int c = 0; c < CB / kGroups; c += 16) {
                     const int cc = h * (CB / kGroups) + c;
-                    if (cb + cc < a.NPpad) {             // warp-uniform; NPpad is a multiple of 16
+                    if (cb + cc < mw) {                  // warp-uniform; mw is a multiple of 16
                         float v[16];
                         tc::ld_32x16(tbase + lane_base + (uint32_t)(kOutCol + cb + cc), v);
 #pragma unroll
@@ -593,12 +605,13 @@ __global__ void __launch_bounds__(Epi<EW>::kThreads, Epi<EW>::kCtas) tc_emat_ker
                     if (off < 0) continue;                  // warp-uniform
                     const int row = warp * kRows + i;
                     for (int m = lane; m < CB; m += 32) {
-                        if (cb + m >= a.NP) break;
+                        if (cb + m >= mw || m0 + cb + m >= a.NP) break;
                         const float val = stage[row * CB + (((m >> 2) ^ (row & 7)) << 2) + (m & 3)];
-                        if (a.nsplit == 1) a.out[off + cb + m] = val;
+                        const int mo = m0 + cb + m;
+                        if (a.nsplit == 1) a.out[off + mo] = val;
                         else if (a.part_out)   // fixed-order sum later: this part's own slot
-                            a.part_out[((w % a.nsplit) * a.n_elem + tile * 128 + row) * (int64_t)a.NP + cb + m] = val;
-                        else atomicAdd(a.out + off + cb + m, val);
+                            a.part_out[((int64_t)wpart(w) * a.n_elem + tile * 128 + row) * a.NP + mo] = val;
+                        else atomicAdd(a.out + off + mo, val);
                     }
                 }
                 if (!(ok = epi_sync())) break;
@@ -1045,6 +1058,19 @@ cudaError_t tc_geom_layout16(int shape, bool curved, const double* g, int NQp, i
 
 // point-chunk parts per tile: split until the grid covers the CTA slots (at
 // least 4 chunks per part); 0 on error
+// output-mode parts of a tile: BF16 past 320 modes splits its N_P output
+// columns into parts of at most 320 (multiples of 16) that fit the tensor
+// memory beside the forward accumulators; one part otherwise
+void tc_mode_parts(const TCArgs& a, int* nmp, int* mw) {
+    if (!a.stream_bwd || a.NPpad <= kOutColMax) {
+        *nmp = 1;
+        *mw = a.NPpad;
+        return;
+    }
+    *nmp = (a.NPpad + kOutColMax - 1) / kOutColMax;
+    *mw = ((a.NPpad + *nmp - 1) / *nmp + 15) & ~15;
+}
+
 int tc_emat_nsplit(const TCArgs& a) {
     const int64_t ntiles = (a.n_elem + 127) / 128;
     if (ntiles <= 0) return 1;
@@ -1057,8 +1083,10 @@ int tc_emat_nsplit(const TCArgs& a) {
     // launch's CTA slots (a ceiling would leave some CTAs a second item, and
     // the launch twice an item's time), at least four chunks a part
     // (a block launched with others in a graph splits for its share of the slots)
+    int nmp = 1, mw = 0;
+    tc_mode_parts(a, &nmp, &mw);
     const double slots = (double)sms * pl.ctas * (a.slot_share > 0.0 ? a.slot_share : 1.0);
-    const int64_t ns = std::max<int64_t>(1, (int64_t)(slots / (double)ntiles));
+    const int64_t ns = std::max<int64_t>(1, (int64_t)(slots / (double)(ntiles * nmp)));
     const int64_t cap = a.nch / 4 > 1 ? a.nch / 4 : 1;
     return (int)(ns < cap ? ns : cap);
 }
@@ -1129,11 +1157,12 @@ cudaError_t tc_emat_launch(const TCArgs& a, cudaStream_t s) {
     const int slots = sms * pl.ctas;
     b.nsplit = tc_emat_nsplit(a);
     if (b.nsplit < 1) return cudaErrorInvalidValue;
+    tc_mode_parts(a, &b.nmpart, &b.mwidth);
     const int64_t n = a.n_elem * a.NP;
     if (b.nsplit == 1) b.part_out = nullptr;
     if (b.nsplit > 1 && !b.part_out)   // atomics: the parts add into a zeroed output
         zero_coeffs_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a.out, a.coeff_off, a.n_elem, a.NP);
-    const int64_t nwork = ntiles * b.nsplit;
+    const int64_t nwork = ntiles * b.nsplit * b.nmpart;
     const int grid = (int)(nwork < slots ? nwork : slots);
     kern<<<grid, threads, pl.smem, s>>>(b);
     e = cudaGetLastError();

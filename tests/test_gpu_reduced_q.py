@@ -128,7 +128,7 @@ def test_reduced_rule_gating(hp):
         assert ei.value.status == hp.HP_ERR_UNSUPPORTED
     finally:
         hp.hp_mesh_destroy(h)
-    big = _mesh(6)                                  # hex P6: 343 modes, no tensor-core form
+    big = _mesh(8)                                  # hex P8: 729 modes, no tensor-core form
     h = hp.hp_mesh_create(big, 0)
     try:
         with pytest.raises(hp.HpError) as ei:

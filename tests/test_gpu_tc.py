@@ -30,7 +30,9 @@ TF32_TOL = 8 * TF32_U
 BF16_U = 2.0 ** -8          # 8 significant bits, round to nearest
 BF16_TOL = 8 * BF16_U
 MAX_TC_MODES = 256
-MAX_TC_MODES_PREC = {"tf32": 256, "bf16": 320}    # BF16 past 256 modes: streamed backward tiles, two output MMAs
+# blocks an elemental-matrix operator puts on the tensor cores by default (BF16
+# builds the form up to 512 modes, but those past 320 start on FP32 sum factorisation)
+MAX_TC_MODES_PREC = {"tf32": 256, "bf16": 320}
 
 
 @pytest.fixture(scope="module")
@@ -45,12 +47,14 @@ def n_blocks(mesh):
     return len(set(zip(mesh["shape"].tolist(), mesh["P"].tolist(), mesh["curved"].tolist())))
 
 
-def run_tc(hp, mesh, opname, x, lam, dtype=None):
+def run_tc(hp, mesh, opname, x, lam, dtype=None, force=False):
     h = hp.hp_mesh_create(mesh, 0)
     try:
         co, po, nc, nph = hp.hp_mesh_layout(h, mesh["n_elem"])
         op = hp.hp_op_create(h, OPS[opname], hp.HP_STRAT_ELEMAT, hp.HP_TF32 if dtype is None else dtype)
         try:
+            if force:   # every block on the tensor-core elemental matrix (the BF16 blocks past 256 modes)
+                hp.hp_op_strategies(op, n_blocks(mesh), np.full(n_blocks(mesh), hp.HP_STRAT_ELEMAT))
             strat = hp.hp_op_strategies(op, n_blocks(mesh))
             xt = torch.tensor(x, device="cuda:0", dtype=torch.float32)
             y = torch.full((nc,), float("nan"), device="cuda:0", dtype=torch.float32)
@@ -234,16 +238,21 @@ def test_deterministic_split_tiles_are_bitwise_reproducible(hp, dt):
     assert np.abs(ys[0] - ya.cpu().numpy()).max() <= 1e-5 * np.abs(ref).max()
 
 
-@pytest.mark.parametrize("shape,P,curved", [(2, 8, True), (1, 7, False), (2, 8, False)])
+@pytest.mark.parametrize("shape,P,curved", [(2, 8, True), (1, 7, False), (2, 8, False), (0, 6, True), (1, 8, False),
+                                            (0, 7, True)])
 def test_bf16_past_256_modes(hp, shape, P, curved):
-    """BF16 blocks of 257..320 modes (pyramid P8: 285, prism P7: 288): the
-    backward tiles are streamed and the output takes two MMAs (N = 256 and
-    N_P - 256); many tiles, sampled elements against the oracle, per-output
-    bound on a small mesh of the same block."""
+    """BF16 blocks past 256 modes: the backward tiles are streamed; up to 320
+    modes (pyramid P8: 285, prism P7: 288) the output takes two MMAs
+    (N = 256 and N_P - 256), past 320 (hex P6: 343, prism P8: 405, hex P7:
+    512) a tile's output modes are split into two work items of at most 320
+    that each recompute the forward.  Blocks past 320 modes start on FP32 sum
+    factorisation and are moved to the form here.  Many tiles, sampled
+    elements against the oracle, per-output bound on a small mesh of the same
+    block."""
     mesh = inputs.replicated_mesh(shape, P, 2000 + 13, curved=curved)
     co, _ = oracle_ops.layout(mesh)
     x = inputs.random_coefficients(91, co)
-    y, strat = run_tc(hp, mesh, "helmholtz", x, 1.0, hp.HP_BF16)
+    y, strat = run_tc(hp, mesh, "helmholtz", x, 1.0, hp.HP_BF16, force=True)
     assert strat.tolist() == [hp.HP_STRAT_ELEMAT]
     rng = np.random.default_rng(5)
     sample = np.unique(np.concatenate([rng.choice(mesh["n_elem"], 30, replace=False), [0, 127, 128, 2012]]))
@@ -254,7 +263,7 @@ def test_bf16_past_256_modes(hp, shape, P, curved):
     small = inputs.replicated_mesh(shape, P, 37, curved=curved)
     cs, _ = oracle_ops.layout(small)
     xs = inputs.random_coefficients(92, cs)
-    ys, _ = run_tc(hp, small, "helmholtz", xs, 1.0, hp.HP_BF16)
+    ys, _ = run_tc(hp, small, "helmholtz", xs, 1.0, hp.HP_BF16, force=True)
     xs32 = xs.astype(np.float32).astype(np.float64)
     refs = oracle_ops.apply("helmholtz", small, xs32, 1.0)
     from tests import roundoff
