@@ -79,9 +79,10 @@ struct Op {
     static constexpr int VBYTES = 128 * VROW;             // one V' tile
     static constexpr uint32_t VSW = ES == 4 ? tc::kSw64 : tc::kSw32;
     static constexpr uint32_t FMT = ES == 4 ? tc::kFmtTF32 : tc::kFmtBF16;
+    // issued by a whole converged warp (one elected lane issues)
     __device__ static void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
-        if constexpr (ES == 4) tc::mma_tf32(d, a, b, id, acc);
-        else tc::mma_bf16(d, a, b, id, acc);
+        if constexpr (ES == 4) tc::mma_tf32_w(d, a, b, id, acc);
+        else tc::mma_bf16_w(d, a, b, id, acc);
     }
     // byte offset of element (r, k) in a 128-byte swizzled row block
     __device__ static uint32_t off128(uint32_t r, uint32_t k) {
@@ -287,7 +288,9 @@ __global__ void __launch_bounds__(Epi<EW>::kThreads, Epi<EW>::kCtas) tc_emat_ker
         __syncwarp();
     } else if (warp == EW + 1) {
         // ---------------------------------------------------------------- MMA issuer
-        if (lane == 0) {
+        // the whole warp runs the loop (its waits warp-wide, so every decision
+        // is uniform) and one elected lane issues each MMA and commit
+        {
             const uint32_t id_f = tc::instr_desc(O::FMT, 128, kNPT * (a.c1 - a.c0));
             const uint32_t id_b = tc::instr_desc(O::FMT, 128, a.NPpad);
             const uint32_t id_bt = id_b | (1u << 16);                     // B operand MN-major
@@ -321,18 +324,18 @@ __global__ void __launch_bounds__(Epi<EW>::kThreads, Epi<EW>::kCtas) tc_emat_ker
                 const uint32_t nb0 = mww > 256 ? 256u : mww, nb1 = mww - nb0;
                 const uint32_t id_b0 = tc::instr_desc(O::FMT, 128, nb0), id_b1 = tc::instr_desc(O::FMT, 128, nb1 > 0 ? nb1 : 16);
                 const uint32_t mo16 = (m0w * O::VROW) >> 4;
-                if (!wait_bar(&B->u_full[ub.i], ub.ph, B, a.err)) { ok = false; break; }
+                if (!wait_warp(&B->u_full[ub.i], ub.ph, B, a.err)) { ok = false; break; }
                 const uint64_t dUw = dU + ub.i * u16;
                 ub.next();
                 // forward of chunk t, then backward of chunk t - (kFwdBufs - 1)
                 for (int t = kb; t < ke + kFwdBufs - 1 && ok; ++t) {
                     if (t < ke) {
-                        if (!wait_bar(&B->fwd_empty[fb.i], fb.ph ^ 1u, B, a.err)) { ok = false; break; }
+                        if (!wait_warp(&B->fwd_empty[fb.i], fb.ph ^ 1u, B, a.err)) { ok = false; break; }
                         // columns (fb*4 + c0)*16 .. of the accumulator = components c0..c1-1
                         const uint32_t d = tbase + (fb.i * 4 + (uint32_t)a.c0) * kNPT;
                         if constexpr (kReuse) {
                             // one ring stage per chunk holding every K slice
-                            if (!wait_bar(&B->full[fs.i], fs.ph, B, a.err)) { ok = false; break; }
+                            if (!wait_warp(&B->full[fs.i], fs.ph, B, a.err)) { ok = false; break; }
                             tc::fence_after();
                             const uint64_t dFs = dF + fs.i * st16;
                             for (uint32_t sl = 0; sl < nsl; ++sl)
@@ -343,25 +346,25 @@ __global__ void __launch_bounds__(Epi<EW>::kThreads, Epi<EW>::kCtas) tc_emat_ker
                         } else {
                             // one ring stage per K slice, released as soon as it is read
                             for (uint32_t sl = 0; sl < nsl && ok; ++sl) {
-                                if (!wait_bar(&B->full[fs.i], fs.ph, B, a.err)) { ok = false; break; }
+                                if (!wait_warp(&B->full[fs.i], fs.ph, B, a.err)) { ok = false; break; }
                                 tc::fence_after();
                                 const uint64_t dFs = dF + fs.i * st16;
 #pragma unroll
                                 for (uint32_t s = 0; s < 4; ++s)
                                     O::mma(d, dUw + (sl * 1024 + s * 2), dFs + s * 2, id_f, sl > 0 || s > 0);
-                                tc::commit(&B->empty[fs.i]);
+                                tc::commit_w(&B->empty[fs.i]);
                                 fs.next();
                             }
                             if (!ok) break;
                         }
-                        tc::commit(&B->fwd_full[fb.i]);
+                        tc::commit_w(&B->fwd_full[fb.i]);
                         fb.next();
                     }
                     const int k = t - (kFwdBufs - 1);
                     if (k >= kb) {
-                        if (!wait_bar(&B->vp_full[vb.i], vb.ph, B, a.err)) { ok = false; break; }
+                        if (!wait_warp(&B->vp_full[vb.i], vb.ph, B, a.err)) { ok = false; break; }
                         if (k == kb) {
-                            if (!wait_bar(&B->out_empty, (nout & 1u) ^ 1u, B, a.err)) { ok = false; break; }
+                            if (!wait_warp(&B->out_empty, (nout & 1u) ^ 1u, B, a.err)) { ok = false; break; }
                             ++nout;
                         }
                         tc::fence_after();
@@ -371,11 +374,11 @@ __global__ void __launch_bounds__(Epi<EW>::kThreads, Epi<EW>::kCtas) tc_emat_ker
                             for (int c = a.c0; c < a.c1; ++c)
                                 O::mma(tbase + kOutCol, dVb + (uint32_t)c * v16, dRs + (uint32_t)c * 128, id_bt,
                                        !(k == kb && c == a.c0));
-                            tc::commit(&B->empty[bs.i]);
+                            tc::commit_w(&B->empty[bs.i]);
                             bs.next();
                         } else {
                             for (int c = a.c0; c < a.c1 && ok; ++c) {
-                                if (!wait_bar(&B->full[fs.i], fs.ph, B, a.err)) { ok = false; break; }
+                                if (!wait_warp(&B->full[fs.i], fs.ph, B, a.err)) { ok = false; break; }
                                 tc::fence_after();
                                 const uint64_t dRs = dRb + fs.i * st16 + mo16;
 #pragma unroll
@@ -386,19 +389,19 @@ __global__ void __launch_bounds__(Epi<EW>::kThreads, Epi<EW>::kCtas) tc_emat_ker
                                         O::mma(tbase + kOutCol + 256, dVb + (uint32_t)c * v16 + s * 2, dRs + kHalf16 + s * 2,
                                                id_b1, acc);
                                 }
-                                tc::commit(&B->empty[fs.i]);
+                                tc::commit_w(&B->empty[fs.i]);
                                 fs.next();
                             }
                             if (!ok) break;
                         }
-                        tc::commit(&B->vp_empty[vb.i]);
+                        tc::commit_w(&B->vp_empty[vb.i]);
                         vb.next();
                     }
                 }
-                if (ok) tc::commit(&B->out_full);
+                if (ok) tc::commit_w(&B->out_full);
             }
-            // every MMA issued by this thread has completed before the CTA leaves
-            tc::commit(&B->drain);
+            // every MMA issued by this warp has completed before the CTA leaves
+            tc::commit_w(&B->drain);
             const uint64_t t0 = global_ns();
             while (!mbar_try_wait(&B->drain, 0) && global_ns() - t0 < kWaitLimitNs) {}
         }
@@ -641,7 +644,7 @@ __global__ void __launch_bounds__(Epi<EW>::kThreads, Epi<EW>::kCtas) tc_emat_ker
 // element from the other of two TMEM buffers, and while MODE 1 loads chunk
 // k+1's point values into registers for the other of two V' tiles.  MODE 1
 // accumulates all chunks into N_P columns (two MMAs of at most 256 columns
-// each past 256 modes).  128 threads, thread 0 issuing; every wait bounded,
+// each past 256 modes).  128 threads, warp 0 issuing (one elected lane); every wait bounded,
 // and copies or MMAs still in flight after a timeout are waited for (bounded)
 // before the CTA frees its tensor memory.
 constexpr int kHybSlice = kNPT * 128;       // component 0 of one K slice: 16 rows x 128 bytes
@@ -802,7 +805,7 @@ __global__ void __launch_bounds__(128) tc_hyb_kernel(const __grid_constant__ Hyb
             }
             wait_full(s);
             if (!ok) break;
-            if (tid == 0) {
+            if (warp == 0) {         // warp-issued MMAs (one elected lane)
                 tc::fence_after();
                 const uint64_t dFs = dF + (uint32_t)s * st16;
                 if (MODE == 0) {
@@ -826,7 +829,7 @@ __global__ void __launch_bounds__(128) tc_hyb_kernel(const __grid_constant__ Hyb
                         }
                     }
                 }
-                tc::commit(&B->mma[k & 1]);
+                tc::commit_w(&B->mma[k & 1]);
             }
             ml[k & 1] = true;
             if (k >= 1) {
