@@ -44,7 +44,7 @@ namespace hp {
 namespace {
 
 constexpr int kNPT = 16;          // quadrature points per chunk
-constexpr int kMaxStages = 8;     // bulk-copy ring: as many stages (2..8) as fit in shared memory
+constexpr int kMaxStages = 16;    // bulk-copy ring: as many stages (2..16) as fit in shared memory
 constexpr int kFwdBufs = 3;       // forward accumulators in flight: the forward MMAs run two chunks ahead
 constexpr int kOutCol = kFwdBufs * 4 * 16;   // TMEM column of the output accumulator
 constexpr int kOutColMax = 512 - kOutCol;    // output columns beside the forward accumulators
@@ -150,6 +150,7 @@ struct Bars {
     uint32_t tmem;
     int abort;
 };
+static_assert(sizeof(Bars) <= 1024, "the barriers sit in the first kilobyte of shared memory");
 
 // wait for `parity` of `bar`, giving up when another role aborted or after the
 // time limit (then this role aborts every role)
@@ -245,16 +246,14 @@ __global__ void __launch_bounds__(Epi<EW>::kThreads, Epi<EW>::kCtas) tc_emat_ker
         if (lane == 0) {
             int slot = 0;
             uint32_t pass = 0;
-            uint32_t last_parity[kMaxStages];
-            bool used[kMaxStages];
-            for (int i = 0; i < kMaxStages; ++i) { last_parity[i] = 0; used[i] = false; }
+            uint32_t last_parity = 0, used = 0;     // bit s: stage s's last pass, whether it was filled
             bool ok = true;
             auto put = [&](const unsigned char* src, uint32_t bytes) {
                 if (!wait_bar(&B->empty[slot], pass ^ 1u, B, a.err)) { ok = false; return; }
                 mbar_expect_tx(&B->full[slot], bytes);
                 bulk_g2s(sR + (size_t)slot * a.stage_bytes, src, bytes, &B->full[slot]);
-                used[slot] = true;
-                last_parity[slot] = pass;
+                used |= 1u << slot;
+                last_parity = (last_parity & ~(1u << slot)) | (pass << slot);
                 if (++slot == nst) { slot = 0; pass ^= 1u; }
             };
             for (int64_t w = blockIdx.x; w < nwork && ok; w += gridDim.x) {
@@ -280,9 +279,9 @@ __global__ void __launch_bounds__(Epi<EW>::kThreads, Epi<EW>::kCtas) tc_emat_ker
             }
             // no copy may still be landing when the CTA leaves
             for (int s = 0; s < nst; ++s)
-                if (used[s]) {
+                if ((used >> s) & 1u) {
                     const uint64_t t0 = global_ns();
-                    while (!mbar_try_wait(&B->full[s], last_parity[s]) && global_ns() - t0 < kWaitLimitNs) {}
+                    while (!mbar_try_wait(&B->full[s], (last_parity >> s) & 1u) && global_ns() - t0 < kWaitLimitNs) {}
                 }
         }
         __syncwarp();
@@ -588,6 +587,7 @@ __global__ void __launch_bounds__(Epi<EW>::kThreads, Epi<EW>::kCtas) tc_emat_ker
             tc::fence_after();
             float* stage = reinterpret_cast<float*>(sV);
             constexpr int CB = 8 * O::VBYTES / (128 * 4);
+            const int part = wpart(w);
             for (int cb = 0; cb < mw; cb += CB) {
                 // row r, columns h CB / kGroups .. of the pass; 16-byte chunks XOR-swizzled by row
 #pragma unroll
@@ -603,17 +603,21 @@ __global__ void __launch_bounds__(Epi<EW>::kThreads, Epi<EW>::kCtas) tc_emat_ker
                     }
                 }
                 if (!(ok = epi_sync())) break;
+                // every row and column of the pass unrolled, so that the loads and
+                // the stores or atomics of different rows are in flight together
+                // (one row at a time spent ~400 clocks a row waiting)
+#pragma unroll
                 for (int i = 0; i < kRows; ++i) {
                     const int64_t off = __shfl_sync(kAll, offs, i);
-                    if (off < 0) continue;                  // warp-uniform
                     const int row = warp * kRows + i;
-                    for (int m = lane; m < CB; m += 32) {
-                        if (cb + m >= mw || m0 + cb + m >= a.NP) break;
+#pragma unroll
+                    for (int j = 0; j < CB / 32; ++j) {
+                        const int m = lane + 32 * j, mo = m0 + cb + m;
                         const float val = stage[row * CB + (((m >> 2) ^ (row & 7)) << 2) + (m & 3)];
-                        const int mo = m0 + cb + m;
+                        if (off < 0 || cb + m >= mw || mo >= a.NP) continue;
                         if (a.nsplit == 1) a.out[off + mo] = val;
                         else if (a.part_out)   // fixed-order sum later: this part's own slot
-                            a.part_out[((int64_t)wpart(w) * a.n_elem + tile * 128 + row) * a.NP + mo] = val;
+                            a.part_out[((int64_t)part * a.n_elem + tile * 128 + row) * a.NP + mo] = val;
                         else atomicAdd(a.out + off + mo, val);
                     }
                 }
@@ -682,18 +686,19 @@ __global__ void __launch_bounds__(128) tc_hyb_kernel(const __grid_constant__ Hyb
     const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
     // barrier bookkeeping, identical in every thread: next phase, and whether a
     // copy (full) or an MMA group (mma) was issued and not yet waited for
-    uint32_t ph_full[kHybMaxStages] = {0, 0, 0}, ph_mma[2] = {0, 0};
-    bool fl[kHybMaxStages] = {false, false, false}, ml[2] = {false, false};
+    // (bit s of a mask per array, so that the bookkeeping stays in registers:
+    // an array indexed by the stage would live in local memory)
+    uint32_t ph_full = 0, ph_mma = 0, fl = 0, ml = 0;
     bool ok = true;
     auto wait_full = [&](int s) {
-        const bool w = mbar_wait_bounded(&B->full[s], ph_full[s], kWaitLimitNs);
-        if (w) { ph_full[s] ^= 1u; fl[s] = false; }
+        const bool w = mbar_wait_bounded(&B->full[s], (ph_full >> s) & 1u, kWaitLimitNs);
+        if (w) { ph_full ^= 1u << s; fl &= ~(1u << s); }
         else if (tid == 0) atomicOr(a.err, DERR_TIMEOUT);
         ok = (__syncthreads_and(w ? 1 : 0) != 0) && ok;
     };
     auto wait_mma = [&](int b) {
-        const bool w = mbar_wait_bounded(&B->mma[b], ph_mma[b], kWaitLimitNs);
-        if (w) { ph_mma[b] ^= 1u; ml[b] = false; }
+        const bool w = mbar_wait_bounded(&B->mma[b], (ph_mma >> b) & 1u, kWaitLimitNs);
+        if (w) { ph_mma ^= 1u << b; ml &= ~(1u << b); }
         else if (tid == 0) atomicOr(a.err, DERR_TIMEOUT);
         ok = (__syncthreads_and(w ? 1 : 0) != 0) && ok;
     };
@@ -713,7 +718,7 @@ __global__ void __launch_bounds__(128) tc_hyb_kernel(const __grid_constant__ Hyb
                     bulk_g2s(dst + sl * kHybSlice, src + (size_t)sl * kSliceBytes, kHybSlice, &B->full[s]);
             }
         }
-        fl[s] = true;
+        fl |= 1u << s;
     };
     const int64_t ntiles = (a.n_elem + 127) / 128;
     constexpr uint32_t hs16 = kHybSlice >> 4;
@@ -831,7 +836,7 @@ __global__ void __launch_bounds__(128) tc_hyb_kernel(const __grid_constant__ Hyb
                 }
                 tc::commit_w(&B->mma[k & 1]);
             }
-            ml[k & 1] = true;
+            ml |= 1u << (k & 1);
             if (k >= 1) {
                 // MMA k-1 done: its stage takes chunk k-1+S; MODE 0 stores its points
                 wait_mma((k - 1) & 1);
@@ -858,11 +863,13 @@ __global__ void __launch_bounds__(128) tc_hyb_kernel(const __grid_constant__ Hyb
         if (MODE == 0) {
             store_chunk(nch - 1);
         } else {
+            // the row's offset read once (a load per pass would wait behind the stores)
+            const int64_t ce = valid ? __ldg(a.coeff_off + e) : 0;
             for (int c = 0; c < a.NPpad; c += 16) {
                 float v[16];
                 tc::ld_32x16(tbase + lane_base + (uint32_t)c, v);
                 if (valid) {
-                    float* o = a.out + a.coeff_off[e] + c;
+                    float* o = a.out + ce + c;
 #pragma unroll
                     for (int i = 0; i < 16; ++i)
                         if (c + i < a.NP) o[i] = v[i];
@@ -874,9 +881,9 @@ __global__ void __launch_bounds__(128) tc_hyb_kernel(const __grid_constant__ Hyb
     }
     if (!ok) {      // nothing may still write shared or tensor memory when the CTA leaves
         for (int s = 0; s < S; ++s)
-            if (fl[s]) mbar_wait_bounded(&B->full[s], ph_full[s], kWaitLimitNs);
+            if ((fl >> s) & 1u) mbar_wait_bounded(&B->full[s], (ph_full >> s) & 1u, kWaitLimitNs);
         for (int b = 0; b < 2; ++b)
-            if (ml[b]) mbar_wait_bounded(&B->mma[b], ph_mma[b], kWaitLimitNs);
+            if ((ml >> b) & 1u) mbar_wait_bounded(&B->mma[b], (ph_mma >> b) & 1u, kWaitLimitNs);
     }
     tc::fence_before();
     __syncthreads();
