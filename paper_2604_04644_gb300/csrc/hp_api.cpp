@@ -665,10 +665,10 @@ cudaError_t launch_block(hp_op op, size_t bi, int tile, double lambda, const voi
         a.fwd_bytes = bf ? blob.tc_fwd16 : blob.tc_fwd;
         a.bwd_bytes = bf ? blob.tc_bwd16 : blob.tc_bwd;
         // BF16: one stage per chunk (its whole forward operand, read again by the
-        // backward MMAs); TF32, and BF16 past 256 modes: forward slices and
-        // backward tiles separately
-        a.stream_bwd = bf && a.NPpad > kTcMaxModes;
-        a.stage_bytes = (bf && !a.stream_bwd) ? a.fwd_bytes
+        // backward MMAs; past 256 modes the lean variant where it fits); TF32,
+        // and BF16 in mode parts: forward slices and backward tiles separately
+        a.variant = tc_variant(a.KP, a.NPpad, a.fwd_bytes, a.es);
+        a.stage_bytes = (bf && a.variant != 1) ? a.fwd_bytes
                                               : (std::max(4 * tc_chunk_points() * 128, a.bwd_bytes) + 1023) & ~1023;
         a.err = op->d_err;
         // split for the graph's share: BF16 always; TF32 up to 16 point chunks

@@ -254,7 +254,8 @@ struct TCArgs {
     int es;                            // operand bytes: 4 TF32, 2 BF16
     int nsplit, stages, ubufs;         // set by the launcher
     double slot_share;                 // share of the GPU's CTA slots for this block in a concurrent graph (0: all)
-    int stream_bwd;                    // BF16 past 256 modes: stream the backward tiles (two output MMAs)
+    int variant;                       // BF16 past 256 modes (tc_variant): 2 lean (two forward accumulators,
+                                       // one V' tile), 1 streamed backward tiles; 0 otherwise
     int nmpart, mwidth;                // output-mode parts of a tile and their width (set by the launcher)
     float* part_out;                   // nullptr: split tiles add with atomics; else [nsplit][n_elem][NP]
                                        // partial outputs summed in part order (deterministic)
@@ -262,6 +263,7 @@ struct TCArgs {
 };
 // parts per tile the launcher will use (0 on error): part_out needs nsplit * n_elem * NP floats
 int tc_emat_nsplit(const TCArgs& a);
+int tc_variant(int KP, int NPpad, int fwd_bytes, int es);   // TCArgs::variant of a block
 // hybrid strategy on the tensor cores (hp_tc_emat.cu): mode 0 u = B uhat
 // (coefficients -> the block's points in the phys layout), mode 1 out = B^T u'
 struct HybArgs {

@@ -183,15 +183,23 @@ __device__ __forceinline__ void arrive_warp(uint64_t* bar) {
 }
 
 
-// SB (BF16 only): stream the backward tiles R_c like TF32 instead of reading
-// the forward stage again; the blocks of 257..320 modes, whose forward stages
-// are too large to hold kFwdBufs - 1 chunks, and whose output takes two
-// backward MMAs (N <= 256 each)
-template <int ES, int EW, bool SB = false>
+// VAR (BF16 only): 0 the default (kFwdBufs forward accumulators, two V' tiles,
+// the backward reading each chunk's forward stage); 2 the lean form for blocks
+// of 257..320 modes, whose forward stages are too large to hold kFwdBufs - 1
+// chunks: two forward accumulators and one V' tile, so that the stages of two
+// chunks fit beside U (the output, N_P > 256, takes two backward MMAs of N =
+// 256 and 64, and is staged through U's buffer); 1 streams the backward tiles
+// R_c like TF32 (the mode parts past 320 modes)
+template <int ES, int EW, int VAR = 0>
 __global__ void __launch_bounds__(Epi<EW>::kThreads, Epi<EW>::kCtas) tc_emat_kernel(const __grid_constant__ TCArgs a) {
     using O = Op<ES>;
     using E = Epi<EW>;
+    constexpr bool SB = VAR == 1;
     constexpr bool kReuse = ES == 2 && !SB;   // the backward reads the forward stage (MN-major)
+    constexpr int kFB = VAR == 2 ? 2 : kFwdBufs;     // forward accumulators in flight
+    constexpr int kVB = VAR == 2 ? 1 : 2;            // V' tiles
+    constexpr int kOC = kFB * 4 * kNPT;              // TMEM column of the output accumulator
+    static_assert(kOC + (VAR == 2 ? 320 : 256) <= 512, "output accumulator beside the forward ones");
     constexpr int kGroups = E::kGroups, kPts = E::kPts, kRows = E::kRows;
     using GV = GVt<kPts>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -200,7 +208,7 @@ __global__ void __launch_bounds__(Epi<EW>::kThreads, Epi<EW>::kCtas) tc_emat_ker
     Bars* B = reinterpret_cast<Bars*>(smem);
     unsigned char* sU = smem + 1024;                                   // [ubufs][KP / KR][128 x 128 B], 128 B swizzle
     unsigned char* sV = sU + a.ubufs * 128 * a.KP * ES;                // [2][4][128 x 16], 64 / 32 B swizzle
-    unsigned char* sR = sV + 8 * O::VBYTES;                            // ring
+    unsigned char* sR = sV + kVB * 4 * O::VBYTES;                      // ring
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nst = a.stages;
     // work items: (tile of 128 elements, part of its point chunks, range of
@@ -221,11 +229,11 @@ __global__ void __launch_bounds__(Epi<EW>::kThreads, Epi<EW>::kCtas) tc_emat_ker
     if (tid == 0) {
         for (int s = 0; s < nst; ++s) { mbar_init(&B->full[s], 1); mbar_init(&B->empty[s], 1); }
         for (int j = 0; j < 2; ++j) mbar_init(&B->u_full[j], EW);
-        for (int b = 0; b < kFwdBufs; ++b) {
+        for (int b = 0; b < kFB; ++b) {
             mbar_init(&B->fwd_full[b], 1);
             mbar_init(&B->fwd_empty[b], EW);
         }
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < kVB; ++b) {
             mbar_init(&B->vp_full[b], EW);
             mbar_init(&B->vp_empty[b], 1);
         }
@@ -259,18 +267,18 @@ __global__ void __launch_bounds__(Epi<EW>::kThreads, Epi<EW>::kCtas) tc_emat_ker
             for (int64_t w = blockIdx.x; w < nwork && ok; w += gridDim.x) {
                 int kb, ke;
                 chunk_range(w, kb, ke);
-                // the MMA issuer's order: forward of chunk t, backward of chunk t - (kFwdBufs - 1);
+                // the MMA issuer's order: forward of chunk t, backward of chunk t - (kFB - 1);
                 // BF16: one stage per chunk (all forward slices), read again by the backward
                 if constexpr (kReuse) {
                     for (int t = kb; t < ke && ok; ++t) put(a.img + (size_t)t * a.chunk_bytes, (uint32_t)a.fwd_bytes);
                     continue;
                 }
-                for (int t = kb; t < ke + kFwdBufs - 1 && ok; ++t) {
+                for (int t = kb; t < ke + kFB - 1 && ok; ++t) {
                     if (t < ke) {
                         const unsigned char* base = a.img + (size_t)t * a.chunk_bytes;
                         for (int sl = 0; sl * O::KR < a.KP && ok; ++sl) put(base + (size_t)sl * kSliceBytes, kSliceBytes);
                     }
-                    const int kbw = t - (kFwdBufs - 1);
+                    const int kbw = t - (kFB - 1);
                     if (kbw >= kb) {
                         const unsigned char* base = a.img + (size_t)kbw * a.chunk_bytes + (size_t)a.fwd_bytes;
                         for (int c = a.c0; c < a.c1 && ok; ++c) put(base + (size_t)c * a.bwd_bytes, a.bwd_bytes);
@@ -291,8 +299,10 @@ __global__ void __launch_bounds__(Epi<EW>::kThreads, Epi<EW>::kCtas) tc_emat_ker
         // is uniform) and one elected lane issues each MMA and commit
         {
             const uint32_t id_f = tc::instr_desc(O::FMT, 128, kNPT * (a.c1 - a.c0));
-            const uint32_t id_b = tc::instr_desc(O::FMT, 128, a.NPpad);
-            const uint32_t id_bt = id_b | (1u << 16);                     // B operand MN-major
+            // BF16 backward from the forward stage (B operand MN-major): N = N_P, or
+            // past 256 modes N = 256 and then 64 (the fifth 64-mode atom, zero past N_P)
+            const uint32_t id_bt = tc::instr_desc(O::FMT, 128, a.NPpad > 256 ? 256 : a.NPpad) | (1u << 16);
+            const uint32_t id_bt1 = tc::instr_desc(O::FMT, 128, 64) | (1u << 16);
             // streamed backward: a work item's output modes m0 .. m0 + mw - 1, as
             // N = min(mw, 256) then N = mw - 256, reading the tile from its row m0
             // (and m0 + 256) on (K-major rows of VROW bytes)
@@ -313,7 +323,7 @@ __global__ void __launch_bounds__(Epi<EW>::kThreads, Epi<EW>::kCtas) tc_emat_ker
             constexpr uint32_t v16 = O::VBYTES >> 4, sl16 = kSliceBytes >> 4;
             // fb: forward accumulators, vb: V' tiles, fs / bs: ring stages taken by
             // the forward / released by the backward (BF16), ub: U buffers
-            Ring fb{kFwdBufs}, vb{2}, fs{(uint32_t)nst}, bs{(uint32_t)nst}, ub{(uint32_t)a.ubufs};
+            Ring fb{kFB}, vb{kVB}, fs{(uint32_t)nst}, bs{(uint32_t)nst}, ub{(uint32_t)a.ubufs};
             uint32_t nout = 0;
             bool ok = true;
             for (int64_t w = blockIdx.x; w < nwork && ok; w += gridDim.x) {
@@ -326,8 +336,8 @@ __global__ void __launch_bounds__(Epi<EW>::kThreads, Epi<EW>::kCtas) tc_emat_ker
                 if (!wait_warp(&B->u_full[ub.i], ub.ph, B, a.err)) { ok = false; break; }
                 const uint64_t dUw = dU + ub.i * u16;
                 ub.next();
-                // forward of chunk t, then backward of chunk t - (kFwdBufs - 1)
-                for (int t = kb; t < ke + kFwdBufs - 1 && ok; ++t) {
+                // forward of chunk t, then backward of chunk t - (kFB - 1)
+                for (int t = kb; t < ke + kFB - 1 && ok; ++t) {
                     if (t < ke) {
                         if (!wait_warp(&B->fwd_empty[fb.i], fb.ph ^ 1u, B, a.err)) { ok = false; break; }
                         // columns (fb*4 + c0)*16 .. of the accumulator = components c0..c1-1
@@ -359,7 +369,7 @@ __global__ void __launch_bounds__(Epi<EW>::kThreads, Epi<EW>::kCtas) tc_emat_ker
                         tc::commit_w(&B->fwd_full[fb.i]);
                         fb.next();
                     }
-                    const int k = t - (kFwdBufs - 1);
+                    const int k = t - (kFB - 1);
                     if (k >= kb) {
                         if (!wait_warp(&B->vp_full[vb.i], vb.ph, B, a.err)) { ok = false; break; }
                         if (k == kb) {
@@ -370,9 +380,13 @@ __global__ void __launch_bounds__(Epi<EW>::kThreads, Epi<EW>::kCtas) tc_emat_ker
                         const uint64_t dVb = dV + vb.i * 4 * v16;
                         if constexpr (kReuse) {
                             const uint64_t dRs = dRt + bs.i * st16;
-                            for (int c = a.c0; c < a.c1; ++c)
-                                O::mma(tbase + kOutCol, dVb + (uint32_t)c * v16, dRs + (uint32_t)c * 128, id_bt,
-                                       !(k == kb && c == a.c0));
+                            for (int c = a.c0; c < a.c1; ++c) {
+                                const uint32_t acc = !(k == kb && c == a.c0);
+                                O::mma(tbase + kOC, dVb + (uint32_t)c * v16, dRs + (uint32_t)c * 128, id_bt, acc);
+                                if (a.NPpad > 256)
+                                    O::mma(tbase + kOC + 256, dVb + (uint32_t)c * v16, dRs + (uint32_t)c * 128 + 4 * sl16,
+                                           id_bt1, acc);
+                            }
                             tc::commit_w(&B->empty[bs.i]);
                             bs.next();
                         } else {
@@ -383,9 +397,9 @@ __global__ void __launch_bounds__(Epi<EW>::kThreads, Epi<EW>::kCtas) tc_emat_ker
 #pragma unroll
                                 for (uint32_t s = 0; s < O::VROW / 32; ++s) {
                                     const uint32_t acc = !(k == kb && c == a.c0 && s == 0);
-                                    O::mma(tbase + kOutCol, dVb + (uint32_t)c * v16 + s * 2, dRs + s * 2, id_b0, acc);
+                                    O::mma(tbase + kOC, dVb + (uint32_t)c * v16 + s * 2, dRs + s * 2, id_b0, acc);
                                     if (nb1 > 0)
-                                        O::mma(tbase + kOutCol + 256, dVb + (uint32_t)c * v16 + s * 2, dRs + kHalf16 + s * 2,
+                                        O::mma(tbase + kOC + 256, dVb + (uint32_t)c * v16 + s * 2, dRs + kHalf16 + s * 2,
                                                id_b1, acc);
                                 }
                                 tc::commit_w(&B->empty[fs.i]);
@@ -501,8 +515,8 @@ __global__ void __launch_bounds__(Epi<EW>::kThreads, Epi<EW>::kCtas) tc_emat_ker
             // outside [c0, c1) are computed from unused columns and discarded)
             // after_metric runs once the factors Gh are consumed (one-set rotation)
             auto process = [&](int k, GV (&Gh)[7], auto&& after_metric) -> bool {
-                const uint32_t g = g0 + (uint32_t)(k - kb), b = g & 1u, use = g >> 1;
-                const uint32_t bf = g % kFwdBufs, usef = g / kFwdBufs;     // forward accumulator buffer
+                const uint32_t g = g0 + (uint32_t)(k - kb), b = g % kVB, use = g / kVB;
+                const uint32_t bf = g % kFB, usef = g / kFB;     // forward accumulator buffer
                 if (!wait_warp(&B->fwd_full[bf], usef & 1u, B, a.err)) return false;
                 tc::fence_after();
                 float v[4][kPts];
@@ -585,7 +599,11 @@ __global__ void __launch_bounds__(Epi<EW>::kThreads, Epi<EW>::kCtas) tc_emat_ker
             // that each warp stores whole coefficient rows (coalesced)
             if (!wait_warp(&B->out_full, ntile & 1u, B, a.err)) { ok = false; break; }
             tc::fence_after();
-            float* stage = reinterpret_cast<float*>(sV);
+            // staged through the two V' tiles, or (one V' tile) through this
+            // tile's U buffer, free once its MMAs completed (a next tile's U goes
+            // into the other buffer, or is gathered after the output)
+            float* stage = kVB == 2 ? reinterpret_cast<float*>(sV)
+                                    : reinterpret_cast<float*>(sU + (size_t)(a.ubufs == 2 ? (ntile & 1u) : 0u) * 128 * a.KP * ES);
             constexpr int CB = 8 * O::VBYTES / (128 * 4);
             const int part = wpart(w);
             for (int cb = 0; cb < mw; cb += CB) {
@@ -595,7 +613,7 @@ __global__ void __launch_bounds__(Epi<EW>::kThreads, Epi<EW>::kCtas) tc_emat_ker
                     const int cc = h * (CB / kGroups) + c;
                     if (cb + cc < mw) {                  // warp-uniform; mw is a multiple of 16
                         float v[16];
-                        tc::ld_32x16(tbase + lane_base + (uint32_t)(kOutCol + cb + cc), v);
+                        tc::ld_32x16(tbase + lane_base + (uint32_t)(kOC + cb + cc), v);
 #pragma unroll
                         for (int i = 0; i < 16; i += 4)
                             *reinterpret_cast<float4*>(stage + r * CB + ((((cc + i) >> 2) ^ (r & 7)) << 2)) =
@@ -1012,9 +1030,10 @@ cudaError_t geom16_shape(bool curved, const double* g, int NQp, int NQ, const do
 constexpr int kSmemCap1 = 227 * 1024, kSmemCap2 = 113 * 1024;
 constexpr int kSmemMin1 = 152 * 1024, kSmemMin2 = 77 * 1024;
 
-// ring stages (2..kMaxStages) that fit beside ubufs U buffers and the V' tiles
-int tc_stages(int KP, int stage_bytes, int es, int ubufs, int cap) {
-    const int base = 2048 + ubufs * 128 * KP * es + 8 * 128 * kNPT * es;   // alignment slack + barriers + U + V'
+// ring stages (2..kMaxStages) that fit beside ubufs U buffers and vbufs V' tiles
+// (four components each)
+int tc_stages(int KP, int stage_bytes, int es, int ubufs, int vbufs, int cap) {
+    const int base = 2048 + ubufs * 128 * KP * es + vbufs * 4 * 128 * kNPT * es;   // alignment slack + barriers + U + V'
     for (int st = kMaxStages; st >= 2; --st)
         if (base + st * stage_bytes <= cap) return st;
     return 0;
@@ -1029,22 +1048,34 @@ int tc_stages(int KP, int stage_bytes, int es, int ubufs, int cap) {
 struct TcPlan {
     int ctas, ubufs, stages, smem;
 };
-TcPlan tc_plan(int KP, int NPpad, int stage_bytes, int es, bool allow2, bool stream_bwd = false) {
-    const int need = (es == 2 && !stream_bwd) ? kFwdBufs + 1 : 2;    // BF16 holds a stage kFwdBufs - 1 chunks
+TcPlan tc_plan(int KP, int NPpad, int stage_bytes, int es, bool allow2, int variant = 0) {
+    // BF16 reading the forward stage again holds a stage through kFB - 1 chunks:
+    // kFB + 1 stages (kFB = 2 in the lean variant)
+    const int need = (es == 2 && variant != 1) ? (variant == 2 ? 3 : kFwdBufs + 1) : 2;
+    const int vbufs = variant == 2 ? 1 : 2;
     for (int ctas = 2; ctas >= 1; --ctas) {
-        if (ctas == 2 && !(allow2 && es == 2 && NPpad <= kOutCol / 3 && kOutCol + NPpad <= 256)) continue;
+        if (ctas == 2 && !(allow2 && es == 2 && variant == 0 && NPpad <= kOutCol / 3 && kOutCol + NPpad <= 256)) continue;
         const int cap = ctas == 2 ? kSmemCap2 : kSmemCap1;
-        const int s1 = tc_stages(KP, stage_bytes, es, 1, cap);
+        const int s1 = tc_stages(KP, stage_bytes, es, 1, vbufs, cap);
         if (s1 < need) continue;
-        const int s2 = tc_stages(KP, stage_bytes, es, 2, cap);
+        const int s2 = tc_stages(KP, stage_bytes, es, 2, vbufs, cap);
         const int ub = (s2 >= 6 || (s2 == s1 && s2 >= need)) ? 2 : 1;
         const int st = ub == 2 ? s2 : s1;
-        int smem = 2048 + ub * 128 * KP * es + 8 * 128 * kNPT * es + st * stage_bytes;
+        int smem = 2048 + ub * 128 * KP * es + vbufs * 4 * 128 * kNPT * es + st * stage_bytes;
         const int mn = ctas == 2 ? kSmemMin2 : kSmemMin1;
         if (smem < mn) smem = mn;
         return {ctas, ub, st, smem};
     }
     return {1, 1, 0, 0};
+}
+
+// BF16 variant of a block (`TCArgs::variant`): 0 up to 256 modes; 2, the lean
+// form, up to 320 modes where its plan fits an SM; 1 (streamed backward tiles,
+// mode parts) otherwise.  TF32: 0.
+int tc_variant(int KP, int NPpad, int fwd_bytes, int es) {
+    if (es != 2 || NPpad <= kTcMaxModes) return 0;
+    if (NPpad <= kOutColMax && tc_plan(KP, NPpad, fwd_bytes, es, false, 2).stages >= 3) return 2;
+    return 1;
 }
 
 int tc_chunk_points() { return kNPT; }
@@ -1072,7 +1103,7 @@ cudaError_t tc_geom_layout16(int shape, bool curved, const double* g, int NQp, i
 // columns into parts of at most 320 (multiples of 16) that fit the tensor
 // memory beside the forward accumulators; one part otherwise
 void tc_mode_parts(const TCArgs& a, int* nmp, int* mw) {
-    if (!a.stream_bwd || a.NPpad <= kOutColMax) {
+    if (a.variant != 1 || a.NPpad <= kOutColMax) {
         *nmp = 1;
         *mw = a.NPpad;
         return;
@@ -1087,7 +1118,7 @@ int tc_emat_nsplit(const TCArgs& a) {
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return 0;
-    const TcPlan pl = tc_plan(a.KP, a.NPpad, a.stage_bytes, a.es, ntiles >= 2 * (int64_t)sms, a.stream_bwd != 0);
+    const TcPlan pl = tc_plan(a.KP, a.NPpad, a.stage_bytes, a.es, ntiles >= 2 * (int64_t)sms, a.variant);
     if (pl.stages == 0) return 0;
     // parts per tile: as many as keep every work item in one wave of the
     // launch's CTA slots (a ceiling would leave some CTAs a second item, and
@@ -1154,12 +1185,14 @@ cudaError_t tc_emat_launch(const TCArgs& a, cudaStream_t s) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (a.NPpad > (a.stream_bwd ? kTcMaxModes16 : kTcMaxModes) || (a.stream_bwd && a.es != 2)) return cudaErrorInvalidValue;
-    const TcPlan pl = tc_plan(a.KP, a.NPpad, a.stage_bytes, a.es, ntiles >= 2 * (int64_t)sms, a.stream_bwd != 0);
+    if (a.NPpad > (a.variant ? kTcMaxModes16 : kTcMaxModes) || (a.variant && a.es != 2) || a.variant < 0 || a.variant > 2)
+        return cudaErrorInvalidValue;
+    const TcPlan pl = tc_plan(a.KP, a.NPpad, a.stage_bytes, a.es, ntiles >= 2 * (int64_t)sms, a.variant);
     if (pl.stages == 0) return cudaErrorInvalidValue;
     b.ubufs = pl.ubufs;
     b.stages = pl.stages;
-    auto kern = a.es == 4 ? tc_emat_kernel<4, 16> : a.stream_bwd ? tc_emat_kernel<2, 16, true>
+    auto kern = a.es == 4 ? tc_emat_kernel<4, 16> : a.variant == 2 ? tc_emat_kernel<2, 16, 2>
+              : a.variant == 1 ? tc_emat_kernel<2, 16, 1>
               : pl.ctas == 2 ? tc_emat_kernel<2, 8> : tc_emat_kernel<2, 16>;
     const int threads = pl.ctas == 2 ? Epi<8>::kThreads : Epi<16>::kThreads;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, pl.smem);
