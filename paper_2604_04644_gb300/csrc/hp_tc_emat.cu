@@ -464,8 +464,10 @@ __global__ void __launch_bounds__(Epi<EW>::kThreads, Epi<EW>::kCtas) tc_emat_ker
             unsigned char* dU = sU + (size_t)j * 128 * a.KP * ES;
             if (a.KP <= 128) gather_rows(std::integral_constant<int, 8>{}, std::integral_constant<int, 4>{}, dU, offs);
             else if (a.KP <= 256) gather_rows(std::integral_constant<int, 4>{}, std::integral_constant<int, 8>{}, dU, offs);
-            else if (a.KP <= 320) gather_rows(std::integral_constant<int, 2>{}, std::integral_constant<int, 10>{}, dU, offs);
-            else gather_rows(std::integral_constant<int, 1>{}, std::integral_constant<int, kTcMaxModes16 / 32>{}, dU, offs);
+            else if constexpr (ES == 2) {      // past 256 modes (BF16 only)
+                if (a.KP <= 320) gather_rows(std::integral_constant<int, 4>{}, std::integral_constant<int, 10>{}, dU, offs);
+                else gather_rows(std::integral_constant<int, 1>{}, std::integral_constant<int, kTcMaxModes16 / 32>{}, dU, offs);
+            }
             tc::fence_async_smem();
             arrive_warp(&B->u_full[j]);
         };
