@@ -23,7 +23,8 @@
 // read again as an MN-major operand, so no backward tiles are streamed).  Three forward
 // accumulators are in flight and the V' tiles are double-buffered, so the
 // forward MMAs run two chunks ahead of the metric and the metric of chunk k
-// overlaps the backward MMAs of chunk k-1.
+// overlaps the backward MMAs of chunk k-1 (the BF16 blocks of 257..320 modes:
+// two accumulators and one V' tile, so that their larger stages fit).
 // Roles: warps 0..EW-1 gather U, run the metric and write the outputs (warp
 // w reads TMEM lanes 32 (w mod 4).. and points kPts (w / 4).. of each chunk;
 // EW = 16, one CTA per SM: four warps per lane quarter, 4 points each, so each
@@ -46,7 +47,7 @@ namespace {
 constexpr int kNPT = 16;          // quadrature points per chunk
 constexpr int kMaxStages = 16;    // bulk-copy ring: as many stages (2..16) as fit in shared memory
 constexpr int kFwdBufs = 3;       // forward accumulators in flight: the forward MMAs run two chunks ahead
-constexpr int kOutCol = kFwdBufs * 4 * 16;   // TMEM column of the output accumulator
+constexpr int kOutCol = kFwdBufs * 4 * 16;   // TMEM column of the output accumulator (three forward buffers)
 constexpr int kOutColMax = 512 - kOutCol;    // output columns beside the forward accumulators
 constexpr int kSliceBytes = 4 * kNPT * 128;   // forward operand slice: 64 rows x 128 bytes of modes
 // metric-factor layout: runs of kGeoPts points, kGeoGroups runs per chunk
