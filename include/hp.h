@@ -255,9 +255,11 @@ hp_status hp_op_set_batching(hp_op op, int mode);
  * block.  Synchronises `stream`.  Results are bitwise identical for every tile. */
 hp_status hp_op_tune(hp_op op, double lambda, const void* in, void* out, void* stream);
 
-/* Read (set = 0) or write (set = 1) the tile variant (0..2) of each of the op's
- * n_blocks blocks (blocks in order of first appearance of (shape, P, curved) in
- * user element order).  HP_ERR_ARG if n_blocks does not match or a tile is out of range. */
+/* Read (set = 0) or write (set = 1) the tile variant (0..2: the 56, 20 and
+ * 110 KB budgets of hp_op_tune) of each of the op's n_blocks blocks (blocks in
+ * order of first appearance of (shape, P, curved) in user element order).  A
+ * new operator starts every block on tile 1.  HP_ERR_ARG if n_blocks does not
+ * match or a tile is out of range. */
 hp_status hp_op_tiles(hp_op op, int* tiles, int64_t n_blocks, int set);
 
 /* Read (set = 0) or write (set = 1) the implementation strategy of each block

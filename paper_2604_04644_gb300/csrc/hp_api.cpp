@@ -1115,7 +1115,11 @@ hp_status hp_op_create(hp_mesh m, hp_opkind kind, hp_strategy strategy, hp_dtype
     op->kind = kind;
     op->strategy = strategy;
     op->dtype = dtype;
-    op->tile.assign(m->blocks.size(), 0);
+    // every block starts on the 20 KB tile: block by block on GB300 it ran FP64
+    // and FP32 sum factorisation as fast as the 56 KB one or faster (more CTAs;
+    // P = 1..6 on the 16^3 mixed mesh, FP32 up to 26 % faster), the same from
+    // P = 7 in FP64 (one element a CTA either way); hp_op_tune times all three
+    op->tile.assign(m->blocks.size(), kDefaultTile);
     op->strat.assign(m->blocks.size(), (int)strategy);
     if (tcore)   // blocks beyond the form's tensor-memory / shared-memory budget run FP32 sum factorisation
         for (size_t i = 0; i < m->blocks.size(); ++i) {

@@ -339,5 +339,6 @@ cudaError_t mat_collect(const double* y, const int64_t* coeff_off, int64_t ne, i
 cudaError_t mat_apply(const void* Ht, const int64_t* coeff_off, int64_t ne, int NP, const void* in, void* out, bool f64,
                       cudaStream_t s);
 constexpr int kTiles = 3;
+constexpr int kDefaultTile = 1;      // the 20 KB shared-memory budget of kTileBudget
 
 }  // namespace hp
