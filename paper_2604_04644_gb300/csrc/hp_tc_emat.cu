@@ -138,6 +138,13 @@ struct Ring {
     }
 };
 
+// 8 bytes of the metric-factor stream: read once, so not kept in L1 (whose
+// storage shares the SM's shared-memory banks with the operand tiles)
+__device__ __forceinline__ uint2 ld_stream(const uint2* p) {
+    uint2 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
+    return v;
+}
 // an epilogue thread's NP FP16 metric factors of one factor: 8 bytes (4 points) or 16 (8 points)
 template <int NP>
 using GVt = std::conditional_t<NP == 8, uint4, uint2>;
@@ -507,9 +514,9 @@ __global__ void __launch_bounds__(Epi<EW>::kThreads, Epi<EW>::kCtas) tc_emat_ker
                     const uint2* q = gt + ((int64_t)k * 7 + f) * (kGeoGroups * 128);
                     const bool need = f == 6 || a.c1 > 1;
                     if constexpr (kPts == kGeoPts) {
-                        G[f] = need ? __ldg(q) : uint2{0u, 0u};
+                        G[f] = need ? ld_stream(q) : uint2{0u, 0u};
                     } else {
-                        const uint2 lo = need ? __ldg(q) : uint2{0u, 0u}, hi = need ? __ldg(q + 128) : uint2{0u, 0u};
+                        const uint2 lo = need ? ld_stream(q) : uint2{0u, 0u}, hi = need ? ld_stream(q + 128) : uint2{0u, 0u};
                         G[f] = make_uint4(lo.x, lo.y, hi.x, hi.y);
                     }
                 }
