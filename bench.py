@@ -56,10 +56,10 @@ N_MODES = (lambda P: (P + 1) ** 3, lambda P: (P + 1) ** 2 * (P + 2) // 2,
 # for the kernel named; a kernel whose code changed after the measurement is
 # left out (its traffic reads null)
 MEASURED_TRAFFIC = {"sf_kernel<pyr,P8,f64>": 372196352,           # profiles/sf_kernel_pyr_P8_fp64.md
-                    "tc_emat_kernel<tet,P8,bf16>": 99341056,      # profiles/tc_emat_kernel_tet_P8_bf16_mixed16.md
-                    "tc_emat_kernel<pyr,P7,bf16>": 75464704,      # profiles/tc_emat_kernel_pyr_P7_bf16_mixed16.md
+                    "tc_emat_kernel<tet,P8,bf16>": 99582720,      # profiles/tc_emat_kernel_tet_P8_bf16_mixed16.md
+                    "tc_emat_kernel<pyr,P7,bf16>": 75540224,      # profiles/tc_emat_kernel_pyr_P7_bf16_mixed16.md
                     "tc_emat_kernel<prism,P7,bf16>": 27841280,    # profiles/tc_emat_kernel_pyr_P7_bf16_mixed16.md
-                    "tc_emat_kernel<pyr,P8,bf16>": 106485504,     # profiles/tc_emat_kernel_pyr_P8_bf16_mixed16.md
+                    "tc_emat_kernel<pyr,P8,bf16>": 106597376,     # profiles/tc_emat_kernel_pyr_P8_bf16_mixed16.md
                     "sf_kernel<pyr,P8,f32>": 185804800}          # profiles/sf_kernel_pyr_P8_fp32_mixed16.md
 
 
