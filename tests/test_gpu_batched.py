@@ -80,6 +80,8 @@ def test_tiles_argument_checks(hp, padaptive):
     try:
         op = hp.hp_op_create(h, hp.HP_MASS)
         nb = n_blocks(padaptive)
+        # a new operator starts every block on tile 1 (the 20 KB budget)
+        assert (hp.hp_op_tiles(op, nb) == 1).all()
         with pytest.raises(hp.HpError):
             hp.hp_op_tiles(op, nb + 1)
         with pytest.raises(hp.HpError):
